@@ -1,0 +1,127 @@
+/*
+ * oracle.h -- plain FP64 CPU oracle for the Velocity Jumps (JUMP) MD path.
+ *
+ * TEST INFRASTRUCTURE. Only tests/, __graft_entry__.smoke() and bench.py's
+ * cpu_baseline / reference leg may load or call this library. The product
+ * path (the CUDA library behind include/md.h) never does, and the two share
+ * no code: this file and oracle.c are written independently from the paper
+ * ("Velocity Jumps for Molecular Dynamics", Gouraud et al., arXiv 2412.15073).
+ *
+ * Units: kcal/mol, Angstrom, ps, amu, elementary charge. The paper's F_i are
+ * gradients of U (Sec. 2.1, the decomposition of grad U); everything here that
+ * is called "grad" is a gradient, the force is its negative.
+ *
+ * Parity status (pins live in tests/test_oracle_*.py):
+ *   philox, uniforms ............ pinned (statistics)
+ *   pair potentials, gradients .. pinned (finite differences, closed forms)
+ *   Theta, G~ sampler ........... pinned (quadrature, exact CDF, KS test)
+ *   thinning (C', J') ........... pinned (survival laws, BPS bounce law)
+ *   JUMP invariance ............. pinned (Boltzmann law of a 2-body system)
+ *   BAOAB ....................... pinned (exact harmonic variance, Verlet order)
+ *   RESPA / RESPA1 drivers ...... pinned by reduction (n = 1 equals BAOAB)
+ */
+#ifndef MD_ORACLE_H
+#define MD_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    double box;          /* cubic periodic box edge (A) */
+    double r_cut;        /* r_E: outer cutoff of LJ and DSF Coulomb (A) */
+    double r_split;      /* r_c: short/long split radius (A) */
+    double h_switch;     /* h: width of the switch, chi goes 1 -> 0 on [r_c-h, r_c] */
+    double r_mid;        /* r_M: ring boundary; <= r_c-h or >= r_E means one ring */
+    double dsf_alpha;    /* DSF damping (1/A) */
+    double gamma;        /* friction (1/ps) */
+    double temperature;  /* K */
+    double eps0;         /* jump parameter: eps = eps0*|g| (adaptive) or eps0 (constant) */
+    double skin;         /* Verlet skin (A); lists are rebuilt when an atom moved > skin/2 */
+    int eps_mode;        /* 1 adaptive (the paper's choice), 0 constant */
+    uint32_t seed;       /* Philox key word 0 */
+    uint32_t replica;    /* Philox key word 1 */
+} or_params;
+
+typedef struct or_sys or_sys;
+
+/* Counters: [0] C' proposals [1] C' accepts [2] J' proposals [3] J' accepts
+ *           [4] sampler attempts [5] list rebuilds */
+#define OR_NCOUNTERS 6
+
+/* error flags (bitwise OR) */
+#define OR_E_BOUND   1u   /* thinning ratio p > 1: a rate bound was violated */
+#define OR_E_LIMIT   2u   /* sampler attempt cap or proposal cap reached */
+#define OR_E_NONFIN  4u   /* non-finite state */
+
+or_sys* or_create(int n, const or_params* p,
+                  const double* x, const double* v,
+                  const double* mass, const double* charge, const int* type,
+                  int ntypes, const double* lj_eps, const double* lj_sigma,
+                  int nbonds, const int* bonds, const double* bond_k, const double* bond_r0,
+                  int nangles, const int* angles, const double* angle_k, const double* angle_t0,
+                  int nexcl, const int* excl_pairs);
+void or_destroy(or_sys* s);
+void or_set_threads(int nthreads);
+int  or_get_threads(void);
+
+/* state */
+void    or_get_state(const or_sys* s, double* x, double* v, int* img, double* x_build);
+void    or_set_state(or_sys* s, const double* x, const double* v, const int* img,
+                     const double* x_build, int64_t step);
+int64_t or_step_count(const or_sys* s);
+void    or_counters(const or_sys* s, int64_t* out);
+uint32_t or_errors(const or_sys* s);
+
+/* forces: mode 0 full (bonded + all pairs), 1 bonded only, 2 nonbonded full,
+ * 3 nonbonded short (chi-weighted), 4 nonbonded long ((1-chi)-weighted),
+ * 5 F0 of JUMP (bonded + short). Brute force over all pairs, minimum image.
+ * grad is 3n (row-major xyz). energy (may be NULL) gets the matching energy. */
+void or_gradient(or_sys* s, int mode, double* grad, double* energy);
+/* full potential energy terms: [bond, angle, lj, coulomb] */
+void or_energy(or_sys* s, double* terms);
+/* per-atom gradient of the chosen mode for one atom only (O(N)) */
+void or_gradient_atom(or_sys* s, int mode, int i, double* g3);
+
+/* rate bounds: out[0] Lhat_M, out[1] Lhat_L (unit charges, per C q_i q_j),
+ * out[2] qmax, per atom LM/LL/LLJ arrays (may be NULL) */
+void or_bounds(const or_sys* s, double* out3, double* LM, double* LL, double* LLJ);
+
+/* jump lists: kind 0 ring M, 1 ring L, 2 LJ. counts[n]; list of one atom */
+void or_list_counts(const or_sys* s, int kind, int* counts);
+int  or_list_get(const or_sys* s, int kind, int i, int* out);
+/* force a rebuild now */
+void or_rebuild(or_sys* s);
+
+/* single-phase primitives (x fixed) for one atom, used by pins and by the
+ * sampled parity at full size. They read the lists of atom i. */
+void or_cprime_one(or_sys* s, int i, const double* v_in, const double* a_in, double tau2,
+                   uint32_t s0, int half, double* v_out, int64_t* nprop, int64_t* nacc);
+void or_jprime_one(or_sys* s, int i, const double* v_in, double tau2,
+                   uint32_t s0, int half, double* v_out, int64_t* nprop, int64_t* nacc);
+
+/* integrators (dt in fs) */
+int or_step_baoab(or_sys* s, int64_t nsteps, double dt_fs);
+int or_step_baoab_respa(or_sys* s, int64_t nouter, double dt_inner_fs, int n_inner);
+int or_step_baoab_respa1(or_sys* s, int64_t nouter, double dt_inner_fs, int m_mid, int n_outer);
+int or_step_jump(or_sys* s, int64_t nsteps, double dt_fs);
+int or_step_jump_respa(or_sys* s, int64_t nouter, double dt_inner_fs, int n_inner);
+int or_step_jump_respa1(or_sys* s, int64_t nouter, double dt_inner_fs, int m_mid, int n_outer);
+
+/* accepted-jump log: records (s, half, tag, atom, k, J) of every accepted jump */
+void    or_events_enable(or_sys* s, int64_t cap);
+int64_t or_events_get(const or_sys* s, int64_t* out6);
+
+/* primitives */
+void   or_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out);
+double or_theta(double eta);
+double or_sample_gtilde(double eta, uint32_t seed, uint32_t replica, uint32_t atom,
+                        uint32_t s0, int half, uint32_t k, int* attempts);
+double or_pair_dudr(const or_sys* s, int ti, int tj, double qiqj, double r, int weight);
+double or_pair_u(const or_sys* s, int ti, int tj, double qiqj, double r, int weight);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,307 @@
+"""Pins of the oracle's integrators and jump processes against laws that hold
+independently of the oracle: thinning survival laws (Sec. 2.4, exactness of
+Poisson thinning), the BPS bounce law (Sec. 2.2/3.2), invariance of the Gibbs
+measure (Sec. 2.2, the jump mechanism leaves mu invariant), exact harmonic
+configurational sampling of BAOAB (Leimkuhler & Matthews 2013), second order
+of velocity Verlet, and reductions between integrators (Sec. 2.3).
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate, stats
+
+from paper_2412_15073_gb300 import systems
+
+KB = 0.0019872042586
+KCAL_AMU = 418.4
+C_COUL = 332.0637
+
+
+def beta_of(T=300.0):
+    return 1.0 / (KB * T)
+
+
+# ------------------------------------------------------------ thinning laws
+def _ring_system(oracle_mod, eps_mode=1, eps0=0.1):
+    """Atom 0 with four charged partners in the jump rings (4.8, 5.2, 6.0, 8.0 A)."""
+    x = np.array([[10, 10, 10], [14.8, 10, 10], [10, 15.2, 10], [10, 10, 16.0], [4.34, 15.66, 10]])
+    w = systems.point_charges(x, 30.0, [0.5, -0.7, 0.4, -0.3, 0.6], [16.0, 1, 1, 1, 1])
+    return oracle_mod.Oracle(w, r_cut=9.0, r_split=5.0, h_switch=0.5, r_mid=5.5, dsf_alpha=0.2,
+                             skin=0.3, eps0=eps0, eps_mode=eps_mode, seed=21)
+
+
+def _pair_rates(o, v, eps_mode, eps0, beta, mt):
+    """sum_j lambda_ij(v) from the paper's per-pair rate (Sec. 3.1),
+    lambda = sqrt(beta)/(eps sqrt(m)) |F| Theta(eps sqrt(beta m) v.F/|F|), with
+    eps = eps0 |F| (adaptive) or eps0 (constant); F from the pinned pair
+    derivative of the long part."""
+    x, _, _, _ = o.state()
+    tot = 0.0
+    q = [0.5, -0.7, 0.4, -0.3, 0.6]
+    for j in range(1, 5):
+        d = x[0] - x[j]
+        r = np.linalg.norm(d)
+        F = o.pair_dudr(0, 0, q[0] * q[j], r, 2) * d / r
+        Fn = np.linalg.norm(F)
+        if Fn == 0:
+            continue
+        eps = eps0 * Fn if eps_mode == 1 else eps0
+        eta = eps * math.sqrt(beta * mt) * (v @ F) / Fn
+        th = eta * stats.norm.cdf(eta) + stats.norm.pdf(eta)
+        tot += math.sqrt(beta) / (eps * math.sqrt(mt)) * Fn * th
+    return tot
+
+
+@pytest.mark.parametrize("eps_mode", [1, 0])
+def test_cprime_first_jump_survival_a0(oracle_mod, eps_mode):
+    """With a = 0 the accepted jumps of the first event form a Poisson process
+    of rate sum_j lambda_ij(v): P(no jump in tau/2) = exp(-tau/2 sum lambda)."""
+    eps0 = 0.1 if eps_mode == 1 else 2.0
+    o = _ring_system(oracle_mod, eps_mode, eps0)
+    beta, mt = beta_of(), 16.0 / KCAL_AMU
+    v = np.array([3.0, -2.0, 4.0])
+    lam = _pair_rates(o, v, eps_mode, eps0, beta, mt)
+    tau2 = 1.0 / lam
+    n = 20000
+    none = 0
+    props = 0
+    for s0 in range(n):
+        vo, npr, na = o.cprime_one(0, v, np.zeros(3), tau2, s0, 0)
+        none += na == 0
+        props += npr
+    p_exp = math.exp(-tau2 * lam)
+    se = math.sqrt(p_exp * (1 - p_exp) / n)
+    assert abs(none / n - p_exp) < 4.5 * se, (none / n, p_exp)
+    assert o.errors == 0
+    assert props / n > lam * tau2   # a proper bound proposes more than it accepts
+
+
+def test_cprime_first_jump_survival_with_drift(oracle_mod):
+    """With a != 0, v(s) = v + s a until the first jump, so
+    P(no jump in tau/2) = exp(-int_0^{tau/2} sum_j lambda_ij(v + s a) ds)."""
+    o = _ring_system(oracle_mod)
+    beta, mt = beta_of(), 16.0 / KCAL_AMU
+    v = np.array([2.0, -1.0, 1.0])
+    a = np.array([-900.0, 1400.0, 600.0])
+    lam0 = _pair_rates(o, v, 1, 0.1, beta, mt)
+    tau2 = 1.2 / lam0
+    integ, _ = integrate.quad(lambda s: _pair_rates(o, v + s * a, 1, 0.1, beta, mt), 0, tau2)
+    n = 20000
+    none = 0
+    for s0 in range(n):
+        vo, npr, na = o.cprime_one(0, v, a, tau2, s0, 1)
+        none += na == 0
+        if na == 0:   # no jump: v ends exactly at v + tau/2 a
+            np.testing.assert_allclose(vo, v + tau2 * a, rtol=1e-12, atol=1e-12)
+    p_exp = math.exp(-integ)
+    se = math.sqrt(p_exp * (1 - p_exp) / n)
+    assert abs(none / n - p_exp) < 4.5 * se, (none / n, p_exp)
+
+
+def test_jprime_single_bounce_law(oracle_mod):
+    """BPS on one LJ pair with v.F > 0: at most one reflection, with
+    probability 1 - exp(-beta (v.F)_+ tau/2); |v| is preserved (Sec. 3.2)."""
+    x = np.array([[10, 10, 10], [16.2, 10, 10]])
+    w = systems.point_charges(x, 30.0, [0.0, 0.0], 16.0, lj_eps=0.155, lj_sigma=3.166)
+    o = oracle_mod.Oracle(w, r_cut=9.0, r_split=5.0, h_switch=0.5, skin=0.3, seed=5)
+    r = 6.2
+    F = o.pair_dudr(0, 0, 0.0, r, 2) * np.array([-1.0, 0, 0])    # grad_x0 of (1-chi)U_LJ
+    v = np.array([-4.0, 1.0, 0.5]) * (1 if F[0] < 0 else -1)
+    vF = v @ F
+    assert vF > 0
+    beta = beta_of()
+    tau2 = 0.7 / (beta * vF)
+    n = 20000
+    bounced = 0
+    for s0 in range(n):
+        vo, npr, na = o.jprime_one(0, v, tau2, s0, 0)
+        assert na <= 1
+        bounced += na
+        assert np.linalg.norm(vo) == pytest.approx(np.linalg.norm(v), rel=1e-14)
+        if na:
+            np.testing.assert_allclose(vo, v - 2 * vF / (F @ F) * F, rtol=1e-12)
+    p_exp = 1 - math.exp(-beta * vF * tau2)
+    se = math.sqrt(p_exp * (1 - p_exp) / n)
+    assert abs(bounced / n - p_exp) < 4.5 * se
+
+
+# ------------------------------------------------------------ invariance
+@pytest.mark.slow
+def test_jump_samples_boltzmann_two_body(oracle_mod):
+    """JUMP (C'J'AOAJ'C') on two charged LJ atoms: the pair distance follows
+    r^2 exp(-beta U(r)) (Gibbs invariance, Sec. 2.2), where U includes the
+    long-range part that only the jumps carry. The same data must reject the
+    law of the short part alone, which shows the jumps matter."""
+    oracle_mod.set_threads(1)
+    L = 12.0
+    beta = beta_of()
+    edges = np.linspace(2.6, 6.0, 18)
+    hists = []
+    o = None
+    for chain in range(8):
+        w = systems.point_charges(np.array([[1, 1, 1], [5, 1, 1]]), L, [0.2, -0.2], 4.0,
+                                  lj_eps=0.2, lj_sigma=3.0, seed=chain)
+        o = oracle_mod.Oracle(w, r_cut=5.5, r_split=3.5, h_switch=0.5, r_mid=4.2, dsf_alpha=0.2,
+                              gamma=5.0, skin=0.4, eps0=0.1, seed=100 + chain)
+        o.jump(2000)
+        rs = []
+        for _ in range(25000):
+            o.jump(20)
+            x = o.state()[0]
+            d = x[0] - x[1]
+            d -= L * np.round(d / L)
+            rs.append(math.sqrt(d @ d))
+        rs = np.array(rs)
+        rs = rs[rs < 6.0]
+        h, _ = np.histogram(rs, bins=edges)
+        hists.append(h / len(rs))
+        assert o.errors == 0
+    oracle_mod.set_threads(0)
+    hists = np.array(hists)
+    mean, se = hists.mean(0), hists.std(0, ddof=1) / math.sqrt(len(hists))
+
+    def law(weight):
+        pr = lambda r: r * r * math.exp(-beta * o.pair_u(0, 0, -0.04, r, weight))
+        Z = integrate.quad(pr, 0.5, 6.0, limit=200)[0]
+        return np.array([integrate.quad(pr, a, b)[0] / Z for a, b in zip(edges[:-1], edges[1:])])
+
+    z_full = (mean - law(0)) / se
+    z_short = (mean - law(1)) / se
+    assert np.abs(z_full).max() < 5.0, z_full
+    assert np.abs(z_short).max() > 15.0
+
+
+# ------------------------------------------------------------ BAOAB
+def test_baoab_exact_harmonic_configurations(oracle_mod):
+    """BAOAB samples the configurational law of a harmonic oscillator exactly
+    for any stable step (Leimkuhler & Matthews 2013): var(d) = kT/k per axis
+    for U = k/2 |x0 - x1|^2, here at omega dt = 1.45."""
+    oracle_mod.set_threads(1)
+    k = 100.0
+    w = systems.point_charges(np.array([[5, 5, 5], [5.05, 5, 5]]), 30.0, [0.0, 0.0], 1.0)
+    w.bonds = np.array([[0, 1]], dtype=np.int32)
+    w.bond_k = np.array([k])
+    w.bond_r0 = np.array([0.0])
+    w.excl = np.array([[0, 1]], dtype=np.int32)
+    var = []
+    for chain in range(4):
+        o = oracle_mod.Oracle(w, r_cut=9.0, gamma=20.0, skin=2.0, seed=chain)
+        o.baoab(500, dt_fs=5.0)
+        ds = []
+        for _ in range(20000):
+            o.baoab(5, dt_fs=5.0)
+            x = o.state()[0]
+            d = x[0] - x[1]
+            ds.append(d - 30.0 * np.round(d / 30.0))
+        var.append(np.var(np.array(ds)))
+    oracle_mod.set_threads(0)
+    target = KB * 300.0 / k
+    assert abs(np.mean(var) / target - 1) < 0.02, np.array(var) / target
+
+
+def test_verlet_energy_error_second_order(oracle_mod, water648):
+    """At gamma = 0 BAOAB is velocity Verlet: the RMS fluctuation of the total
+    energy scales as dt^2 (ratio ~ 4 when dt halves)."""
+    rms = []
+    for dt in (0.4, 0.2):
+        o = oracle_mod.Oracle(water648, r_cut=9.0, gamma=0.0, skin=0.3)
+        o.baoab(int(round(4 / dt)), dt_fs=dt)     # let the lattice start settle a little
+        H = []
+        for _ in range(int(round(16 / dt))):
+            o.baoab(1, dt_fs=dt)
+            _, v, _, _ = o.state()
+            ke = 0.5 * (water648.mass[:, None] * v * v).sum() / KCAL_AMU
+            H.append(ke + o.energy().sum())
+        rms.append(np.std(H))
+    ratio = rms[0] / rms[1]
+    assert 3.0 < ratio < 5.0, (rms, ratio)
+
+
+# ------------------------------------------------------------ reductions
+def test_jump_equals_baoab_without_jump_range(oracle_mod, water648):
+    """r_c - h >= r_E: chi = 1 on all pairs, the rings are empty, C' is the B
+    kick and J' does nothing; JUMP reproduces BAOAB bit for bit."""
+    a = oracle_mod.Oracle(water648, r_cut=9.0, r_split=9.6, h_switch=0.5, skin=0.3, seed=4)
+    b = oracle_mod.Oracle(water648, r_cut=9.0, r_split=9.6, h_switch=0.5, skin=0.3, seed=4)
+    assert a.list_counts(0).sum() == 0 and a.list_counts(1).sum() == 0 and a.list_counts(2).sum() == 0
+    a.jump(30)
+    b.baoab(30)
+    xa, va, _, _ = a.state()
+    xb, vb, _, _ = b.state()
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+
+
+def test_respa_one_inner_step_is_baoab(oracle_mod, water648):
+    """BAOAB-RESPA with n = 1 and BAOAB-RESPA1 with m = n = 1 are BAOAB, up to
+    the order in which the bonded and nonbonded kicks are added."""
+    ref = oracle_mod.Oracle(water648, r_cut=9.0, skin=0.3, seed=2)
+    ref.baoab(20)
+    xr, vr, _, _ = ref.state()
+    for how in ("respa", "respa1"):
+        o = oracle_mod.Oracle(water648, r_cut=9.0, skin=0.3, seed=2)
+        if how == "respa":
+            o.baoab_respa(20, 1.0, 1)
+        else:
+            o.baoab_respa1(20, 1.0, 1, 1)
+        x, v, _, _ = o.state()
+        assert np.abs(x - xr).max() < 1e-10
+        assert np.abs(v - vr).max() < 1e-8
+
+
+def test_jump_respa1_is_jump_respa_at_mid_level(oracle_mod, water648):
+    """Without a slow many-body force the JUMP-RESPA1 outer level is empty:
+    n_outer x n mid cycles of m inner steps equal JUMP-RESPA with n_inner = m."""
+    a = oracle_mod.Oracle(water648, r_cut=9.0, skin=0.3, seed=8)
+    b = oracle_mod.Oracle(water648, r_cut=9.0, skin=0.3, seed=8)
+    a.jump_respa1(3, 1.0, 2, 2)
+    b.jump_respa(6, 1.0, 2)
+    assert a.step == b.step == 12
+    xa, va, _, _ = a.state()
+    xb, vb, _, _ = b.state()
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+
+
+def test_jump_respa_one_inner_step_matches_jump_statistics(oracle_mod, water648):
+    """JUMP-RESPA with n_inner = 1 moves bonded forces from the C' drift into
+    B kicks; both keep the water box at the bath temperature over 200 fs and
+    run without bound violations."""
+    for how in ("jump", "respa"):
+        o = oracle_mod.Oracle(water648, r_cut=9.0, skin=0.3, seed=3)
+        o.jump(200) if how == "jump" else o.jump_respa(200, 1.0, 1)
+        assert o.errors == 0
+        _, v, _, _ = o.state()
+        T = (water648.mass[:, None] * v * v).sum() / KCAL_AMU / (3 * water648.n * KB)
+        assert 250 < T < 350
+
+
+def test_resume_is_bit_exact(oracle_mod, water648):
+    """Counter-based streams: 2k steps equal k steps, a save/restore of
+    (x, v, images, list-build positions, step), then k more."""
+    a = oracle_mod.Oracle(water648, r_cut=9.0, skin=0.3, seed=6)
+    a.jump(40)
+    xa, va, _, _ = a.state()
+    b = oracle_mod.Oracle(water648, r_cut=9.0, skin=0.3, seed=6)
+    b.jump(20)
+    x, v, img, xb = b.state()
+    c = oracle_mod.Oracle(water648, r_cut=9.0, skin=0.3, seed=6)
+    c.set_state(x, v, img, xb, step=20)
+    c.jump(20)
+    xc, vc, _, _ = c.state()
+    assert np.array_equal(xa, xc) and np.array_equal(va, vc)
+
+
+def test_event_log_and_rate_bound_hold_on_water(oracle_mod, water648):
+    """100 JUMP steps on 648 waters: no bound violation (p <= 1 always), an
+    event log that agrees with the counters, and sane jump statistics."""
+    o = oracle_mod.Oracle(water648, r_cut=9.0, skin=0.3, seed=1)
+    o.events_enable(1 << 22)
+    o.jump(100)
+    assert o.errors == 0
+    c = o.counters()
+    ev = o.events()
+    assert len(ev) == c[1] + c[3]
+    assert (ev[:, 2] == 2).sum() == c[1] and (ev[:, 2] == 3).sum() == c[3]
+    per_atom_step = c[0] / (648 * 100)
+    assert 20 < per_atom_step < 120
+    assert 0.05 < c[1] / c[0] < 0.6
