@@ -40,7 +40,7 @@ class Params(C.Structure):
     _fields_ = [("box", C.c_double), ("r_cut", C.c_double), ("r_split", C.c_double),
                 ("h_switch", C.c_double), ("r_mid", C.c_double), ("dsf_alpha", C.c_double),
                 ("gamma", C.c_double), ("temperature", C.c_double), ("eps0", C.c_double),
-                ("skin", C.c_double), ("eps_mode", C.c_int), ("seed", C.c_uint32),
+                ("skin", C.c_double), ("skin_outer", C.c_double), ("eps_mode", C.c_int), ("seed", C.c_uint32),
                 ("replica", C.c_uint32)]
 
 
@@ -61,8 +61,8 @@ def lib():
         L.or_destroy.argtypes = [vp]
         L.or_set_threads.argtypes = [i]
         L.or_get_threads.restype = i
-        L.or_get_state.argtypes = [vp, vp, vp, vp, vp]
-        L.or_set_state.argtypes = [vp, vp, vp, vp, vp, i64]
+        L.or_get_state.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.or_set_state.argtypes = [vp, vp, vp, vp, vp, vp, i64]
         L.or_step_count.restype = i64
         L.or_step_count.argtypes = [vp]
         L.or_counters.argtypes = [vp, vp]
@@ -129,11 +129,14 @@ class Oracle:
     """One system advanced by the oracle. `sys` is a systems.System."""
 
     def __init__(self, sys, r_cut=9.0, r_split=5.0, h_switch=0.5, r_mid=5.5, dsf_alpha=0.2,
-                 gamma=1.0, temperature=300.0, eps0=0.1, skin=0.3, eps_mode=1, seed=0, replica=0):
+                 gamma=1.0, temperature=300.0, eps0=0.1, skin=0.3, skin_outer=None, eps_mode=1,
+                 seed=0, replica=0):
         self.L = lib()
         self.n = sys.n
+        if skin_outer is None:
+            skin_outer = skin
         self.params = Params(sys.box, r_cut, r_split, h_switch, r_mid, dsf_alpha, gamma,
-                             temperature, eps0, skin, eps_mode, seed, replica)
+                             temperature, eps0, skin, skin_outer, eps_mode, seed, replica)
         a = lambda z, t: np.ascontiguousarray(z, dtype=t)
         self._keep = [a(sys.x, np.float64), a(sys.v, np.float64), a(sys.mass, np.float64),
                       a(sys.charge, np.float64), a(sys.type, np.int32), a(sys.lj_eps, np.float64),
@@ -153,19 +156,19 @@ class Oracle:
             self.h = None
 
     # state ---------------------------------------------------------------
-    def state(self):
+    def state(self, outer=False):
         x = np.zeros((self.n, 3)); v = np.zeros((self.n, 3))
         img = np.zeros((self.n, 3), dtype=np.int32); xb = np.zeros((self.n, 3))
-        self.L.or_get_state(self.h, _p(x), _p(v), _p(img), _p(xb))
-        return x, v, img, xb
+        xo = np.zeros((self.n, 3))
+        self.L.or_get_state(self.h, _p(x), _p(v), _p(img), _p(xb), _p(xo))
+        return (x, v, img, xb, xo) if outer else (x, v, img, xb)
 
-    def set_state(self, x, v, img=None, x_build=None, step=0):
-        x = np.ascontiguousarray(x, dtype=np.float64)
-        v = np.ascontiguousarray(v, dtype=np.float64)
-        img = None if img is None else np.ascontiguousarray(img, dtype=np.int32)
-        xb = None if x_build is None else np.ascontiguousarray(x_build, dtype=np.float64)
-        self.L.or_set_state(self.h, _p(x), _p(v), None if img is None else _p(img),
-                            None if xb is None else _p(xb), int(step))
+    def set_state(self, x, v, img=None, x_build=None, step=0, x_outer=None):
+        f = lambda z, t: None if z is None else np.ascontiguousarray(z, dtype=t)
+        x, v, img = f(x, np.float64), f(v, np.float64), f(img, np.int32)
+        xb, xo = f(x_build, np.float64), f(x_outer, np.float64)
+        q = lambda z: None if z is None else _p(z)
+        self.L.or_set_state(self.h, _p(x), _p(v), q(img), q(xb), q(xo), int(step))
 
     @property
     def step(self) -> int:

@@ -72,6 +72,8 @@ struct or_sys {
     double *LM, *LL, *LLJ;   /* per-atom rate bounds */
     or_list lists[K_NKIND];
     int ncell;
+    int *cellm;              /* cell of each atom at the last outer rebuild */
+    double *xo;              /* positions at the last outer rebuild */
     /* forces (as accelerations a = -grad/m~) */
     double *a0, *ab, *as, *al;
     int64_t step;
@@ -412,8 +414,11 @@ void or_bounds(const or_sys* s, double* out3, double* LM, double* LL, double* LL
 /* ======================================================================== */
 /* jump lists (Sec. 3.1 remark: middle and long neighbour lists with counts */
 /* N_M(i), N_L(i); Sec. 3.2: LJ partners). Membership by distance at the    */
-/* build positions widened by the skin; order: by (cell of j, j) on the     */
-/* grid of n_c = floor(L / (r_E + skin)) cells per edge.                    */
+/* build positions widened by the skin. Order: by (cell of j at the last    */
+/* outer rebuild, j) on the grid of n_c = floor(L / (r_E + skin_outer))     */
+/* cells per edge. An outer rebuild happens when some atom moved more than  */
+/* (skin_outer - skin)/2 since the last one; it only refreshes the cells    */
+/* that order the lists.                                                    */
 /* ======================================================================== */
 static int cell_of(const or_sys* s, int j)
 {
@@ -472,8 +477,7 @@ static void cj_push(cj_vec* v, int cell, int j)
 static void build_lists(or_sys* s)
 {
     int n = s->n;
-    int* cell = (int*)malloc(sizeof(int) * (size_t)n);
-    for (int j = 0; j < n; ++j) cell[j] = cell_of(s, j);
+    const int* cell = s->cellm;
     cj_vec* tmp = (cj_vec*)calloc((size_t)n * K_NKIND, sizeof(cj_vec));
     double hi = s->p.r_cut + s->p.skin;
 #pragma omp parallel for schedule(dynamic, 16)
@@ -507,28 +511,45 @@ static void build_lists(or_sys* s)
     }
     for (size_t t = 0; t < (size_t)n * K_NKIND; ++t) free(tmp[t].e);
     free(tmp);
-    free(cell);
     memcpy(s->xb, s->x, sizeof(double) * 3 * (size_t)n);
     s->cnt[5]++;
 }
 
-void or_rebuild(or_sys* s) { build_lists(s); }
-
-/* rebuild when some atom moved more than skin/2 since the last build */
-static void maybe_rebuild(or_sys* s)
+static void outer_rebuild(or_sys* s)
 {
-    double lim = 0.5 * s->p.skin;
-    int need = 0;
-    for (int i = 0; i < s->n && !need; ++i) {
+    for (int j = 0; j < s->n; ++j) s->cellm[j] = cell_of(s, j);
+    memcpy(s->xo, s->x, sizeof(double) * 3 * (size_t)s->n);
+}
+
+static double max_disp2(const or_sys* s, const double* ref)
+{
+    double m = 0.0;
+    for (int i = 0; i < s->n; ++i) {
         double d2 = 0.0;
         for (int c = 0; c < 3; ++c) {
-            double t = s->x[3 * i + c] - s->xb[3 * i + c];
+            double t = s->x[3 * i + c] - ref[3 * i + c];
             t -= s->L * nearbyint(t / s->L);
             d2 += t * t;
         }
-        if (d2 > lim * lim) need = 1;
+        if (d2 > m) m = d2;
     }
-    if (need) build_lists(s);
+    return m;
+}
+
+void or_rebuild(or_sys* s) { outer_rebuild(s); build_lists(s); }
+
+/* before each nonbonded evaluation: outer rebuild when some atom moved more
+ * than (skin_outer - skin)/2 since the last outer rebuild, list rebuild when
+ * some atom moved more than skin/2 since the last list build */
+static void maybe_rebuild(or_sys* s)
+{
+    double lo = 0.5 * (s->p.skin_outer - s->p.skin), li = 0.5 * s->p.skin;
+    if (max_disp2(s, s->xo) > lo * lo) {
+        outer_rebuild(s);
+        build_lists(s);
+    } else if (max_disp2(s, s->xb) > li * li) {
+        build_lists(s);
+    }
 }
 
 void or_list_counts(const or_sys* s, int kind, int* counts)
@@ -1158,14 +1179,18 @@ or_sys* or_create(int n, const or_params* p,
     s->LL = (double*)malloc(sizeof(double) * (size_t)n);
     s->LLJ = (double*)malloc(sizeof(double) * (size_t)n);
     compute_bounds(s);
-    int nc = (int)floor(s->L / (p->r_cut + p->skin));
+    if (s->p.skin_outer < s->p.skin) s->p.skin_outer = s->p.skin;
+    int nc = (int)floor(s->L / (s->p.r_cut + s->p.skin_outer));
     s->ncell = nc < 1 ? 1 : nc;
+    s->cellm = (int*)malloc(sizeof(int) * (size_t)n);
+    s->xo = (double*)malloc(sizeof(double) * n3);
     s->a0 = (double*)calloc(n3, sizeof(double));
     s->ab = (double*)calloc(n3, sizeof(double));
     s->as = (double*)calloc(n3, sizeof(double));
     s->al = (double*)calloc(n3, sizeof(double));
     wrap(s);
     memset(s->img, 0, sizeof(int) * n3);
+    outer_rebuild(s);
     build_lists(s);
     s->cnt[5] = 0;
     return s;
@@ -1183,6 +1208,7 @@ void or_destroy(or_sys* s)
     free(s->LM); free(s->LL); free(s->LLJ);
     for (int k = 0; k < K_NKIND; ++k) { free(s->lists[k].off); free(s->lists[k].idx); }
     free(s->a0); free(s->ab); free(s->as); free(s->al);
+    free(s->cellm); free(s->xo);
     free(s->ev);
     free(s);
 }
@@ -1205,30 +1231,32 @@ int or_get_threads(void)
 #endif
 }
 
-void or_get_state(const or_sys* s, double* x, double* v, int* img, double* x_build)
+void or_get_state(const or_sys* s, double* x, double* v, int* img, double* x_build,
+                  double* x_outer)
 {
     size_t n3 = 3 * (size_t)s->n;
     if (x) memcpy(x, s->x, sizeof(double) * n3);
     if (v) memcpy(v, s->v, sizeof(double) * n3);
     if (img) memcpy(img, s->img, sizeof(int) * n3);
     if (x_build) memcpy(x_build, s->xb, sizeof(double) * n3);
+    if (x_outer) memcpy(x_outer, s->xo, sizeof(double) * n3);
 }
 
-/* restore a state; with x_build the lists are rebuilt at x_build so that a
- * resumed run repeats the uninterrupted one */
+/* restore a state; with x_build (list build positions) and x_outer (outer
+ * rebuild positions) the lists are rebuilt as they were, so that a resumed
+ * run repeats the uninterrupted one */
 void or_set_state(or_sys* s, const double* x, const double* v, const int* img,
-                  const double* x_build, int64_t step)
+                  const double* x_build, const double* x_outer, int64_t step)
 {
     size_t n3 = 3 * (size_t)s->n;
-    if (x_build) {
-        memcpy(s->x, x_build, sizeof(double) * n3);
-        build_lists(s);
-        s->cnt[5]--;
-    }
+    memcpy(s->x, x_outer ? x_outer : (x_build ? x_build : x), sizeof(double) * n3);
+    outer_rebuild(s);
+    if (x_build) memcpy(s->x, x_build, sizeof(double) * n3);
+    build_lists(s);
+    s->cnt[5]--;
     memcpy(s->x, x, sizeof(double) * n3);
     memcpy(s->v, v, sizeof(double) * n3);
     if (img) memcpy(s->img, img, sizeof(int) * n3);
-    if (!x_build) { build_lists(s); s->cnt[5]--; }
     s->step = step;
 }
 

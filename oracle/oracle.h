@@ -39,6 +39,7 @@ typedef struct {
     double temperature;  /* K */
     double eps0;         /* jump parameter: eps = eps0*|g| (adaptive) or eps0 (constant) */
     double skin;         /* Verlet skin (A); lists are rebuilt when an atom moved > skin/2 */
+    double skin_outer;   /* skin of the outer candidate grid (>= skin); it fixes the list order */
     int eps_mode;        /* 1 adaptive (the paper's choice), 0 constant */
     uint32_t seed;       /* Philox key word 0 */
     uint32_t replica;    /* Philox key word 1 */
@@ -67,9 +68,10 @@ void or_set_threads(int nthreads);
 int  or_get_threads(void);
 
 /* state */
-void    or_get_state(const or_sys* s, double* x, double* v, int* img, double* x_build);
+void    or_get_state(const or_sys* s, double* x, double* v, int* img, double* x_build,
+                     double* x_outer);
 void    or_set_state(or_sys* s, const double* x, const double* v, const int* img,
-                     const double* x_build, int64_t step);
+                     const double* x_build, const double* x_outer, int64_t step);
 int64_t or_step_count(const or_sys* s);
 void    or_counters(const or_sys* s, int64_t* out);
 uint32_t or_errors(const or_sys* s);

@@ -277,15 +277,15 @@ def test_jump_respa_one_inner_step_matches_jump_statistics(oracle_mod, water648)
 
 def test_resume_is_bit_exact(oracle_mod, water648):
     """Counter-based streams: 2k steps equal k steps, a save/restore of
-    (x, v, images, list-build positions, step), then k more."""
-    a = oracle_mod.Oracle(water648, r_cut=9.0, skin=0.3, seed=6)
+    (x, v, images, list-build and outer-rebuild positions, step), then k more."""
+    a = oracle_mod.Oracle(water648, r_cut=9.0, skin=0.2, skin_outer=0.3, seed=6)
     a.jump(40)
     xa, va, _, _ = a.state()
-    b = oracle_mod.Oracle(water648, r_cut=9.0, skin=0.3, seed=6)
+    b = oracle_mod.Oracle(water648, r_cut=9.0, skin=0.2, skin_outer=0.3, seed=6)
     b.jump(20)
-    x, v, img, xb = b.state()
-    c = oracle_mod.Oracle(water648, r_cut=9.0, skin=0.3, seed=6)
-    c.set_state(x, v, img, xb, step=20)
+    x, v, img, xb, xo = b.state(outer=True)
+    c = oracle_mod.Oracle(water648, r_cut=9.0, skin=0.2, skin_outer=0.3, seed=6)
+    c.set_state(x, v, img, xb, step=20, x_outer=xo)
     c.jump(20)
     xc, vc, _, _ = c.state()
     assert np.array_equal(xa, xc) and np.array_equal(va, vc)
