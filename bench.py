@@ -1,0 +1,395 @@
+"""Throughput of the JUMP path against the GPU's own BAOAB path.
+
+Workload (the 97k-atom headline configuration): 32,000 flexible 3-site waters
+(96,000 atoms) in a 98.6 A periodic cube, LJ + DSF Coulomb (alpha 0.2/A),
+r_E = 10 A, r_c = 5 A (switch width 0.5 A), ring boundary 5.5 A, adaptive
+eps0 = 0.1, Langevin 300 K, gamma = 1/ps, mixed precision (FP32 pair math,
+64-bit fixed-point sums, FP64 integration). A step is one 1 fs JUMP step
+(C'J'AOAJ'C'); BAOAB runs the same system at 1 fs for comparison.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line. Under torchrun (N > 1) every rank advances its own
+replica (replicas only: the path has no exchange step) and rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_MOL, BOX = 32000, 98.6
+PARAMS = dict(r_cut=10.0, r_split=5.0, h_switch=0.5, r_mid=5.5, dsf_alpha=0.2, gamma=1.0,
+              temperature=300.0, eps0=0.1, eps_mode=1, skin=0.5, skin_outer=1.5)
+DT_FS = 1.0
+METRIC = "ns/day & Gpair-evals/s, JUMP vs BAOAB on 1 GB300 at matched T/D (97k atoms)"
+WORKLOAD = ("water 96,000 atoms (32,000 flexible 3-site waters, 98.6 A cube), LJ+DSF r_E 10 A, "
+            "r_c 5 A, ring 5.5 A, adaptive eps0 0.1, 300 K, gamma 1/ps; JUMP 1 fs vs BAOAB 1 fs")
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP32 work of one pair of the pair kernel and of one jump proposal (counted
+# from the kernel source; see the roofline notes in the design doc)
+FLOP_PER_PAIR = 52
+OPS_PER_PROPOSAL = 230
+
+
+def ns_per_day(fs_simulated: float, seconds: float) -> float:
+    return fs_simulated * 1e-6 / seconds * 86400.0
+
+
+def peaks():
+    try:
+        return json.load(open(PEAKS)), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.out = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.out.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.out:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def pair_counts(x, box, r, n_mol_atoms=3):
+    """Unique intermolecular pairs within r (periodic cKDTree)."""
+    from scipy.spatial import cKDTree
+    t = cKDTree(np.mod(x, box), boxsize=box)
+    pairs = t.query_pairs(r, output_type="ndarray")
+    same = (pairs[:, 0] // n_mol_atoms) == (pairs[:, 1] // n_mol_atoms)
+    return int((~same).sum())
+
+
+def cpu_oracle_sample(sys_, params, n_sample, n_rounds, seed=0):
+    """Time the FP64 oracle on a bounded sample of one JUMP step: for each of
+    n_sample atoms the F0 gradient (O(N)) and the four velocity phases
+    (C'J' and J'C', Algorithms 4 and 5). Returns (seconds, atoms done, threads)."""
+    import oracle
+    oracle.build()
+    o = oracle.Oracle(sys_, seed=seed, **params)
+    rng = np.random.default_rng(seed)
+    mt = sys_.mass / 418.4
+    tau2 = 0.5e-3 * DT_FS
+    done = 0
+    t0 = time.perf_counter()
+    for r in range(n_rounds):
+        for i in rng.choice(sys_.n, n_sample, replace=False):
+            a = -o.gradient_atom(oracle.GRAD_F0, int(i)) / mt[i]
+            v, _, _ = o.cprime_one(int(i), sys_.v[i], a, tau2, r, 0)
+            v, _, _ = o.jprime_one(int(i), v, tau2, r, 0)
+            v, _, _ = o.jprime_one(int(i), v, tau2, r, 1)
+            o.cprime_one(int(i), v, a, tau2, r, 1)
+            done += 1
+    return time.perf_counter() - t0, done, oracle.get_threads()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2412_15073_gb300 import systems
+    w = systems.water_box(N_MOL, box=BOX, seed=0)
+    n_sample = 16
+    for _ in range(args.warmup):
+        cpu_oracle_sample(w, PARAMS, n_sample, 1)
+    secs, done, thr = 0.0, 0, 1
+    for k in range(args.steps):
+        s, d, thr = cpu_oracle_sample(w, PARAMS, n_sample, 1, seed=k + 1)
+        secs += s
+        done += d
+    steps_equiv = done / w.n
+    value = ns_per_day(steps_equiv * DT_FS, secs)
+    sample = (f"per step: {n_sample} of 96,000 atoms, each its O(N) F0 gradient and four velocity phases "
+              f"(C'J', J'C') of one JUMP step; list builds excluded; scaled by 96,000/{n_sample}")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "ns/day", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "parallelism": "replicas"},
+            "cpu_baseline": {"value": value, "unit": "ns/day", "cores": thr, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "ns/day", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def timed(engine, fn, steps, stream):
+    import torch
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fn(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def e2e_run(ej, args, M, torch, stream, n, world, max_over_ranks, barrier):
+    """Same metric through the public C ABI with pinned host buffers: per bench
+    step (K MD steps) md_set_state from host, md_step_jump(K), md_get_state to host."""
+    x, v, img, xb, xo = ej.state(outer=True)
+    step0 = ej.observables()["step"]
+    hx = [torch.from_numpy(a).pin_memory().numpy() for a in (x, v, xb, xo)]
+    himg = torch.from_numpy(img).pin_memory().numpy()
+    barrier()
+    t0 = time.perf_counter()
+    ej.set_state(0, hx[0], hx[1], himg, hx[2], hx[3], step=step0)
+    ej.jump(args.steps)
+    ej._ck(ej.L.md_get_state(ej.h, 0, M._ptr(hx[0]), M._ptr(hx[1]), M._ptr(himg), M._ptr(hx[2]),
+                             M._ptr(hx[3])))
+    torch.cuda.synchronize()
+    t = max_over_ranks(time.perf_counter() - t0)
+    state_bytes = n * (4 * 3 * 8 + 3 * 4)
+    return {"value": ns_per_day(world * args.steps * DT_FS, t), "unit": "ns/day",
+            "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
+            "path": "md_set_state(host) + md_step_jump(K) + md_get_state(host) per bench step of K MD steps"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=48)
+    ap.add_argument("--respa1", type=int, default=1, help="also time JUMP-RESPA1 vs BAOAB-RESPA1")
+    ap.add_argument("--equil", type=int, default=1000,
+                    help="BAOAB steps at gamma = 20/ps from the lattice start before timing (0 = none)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--only", default="all", choices=["all", "jump", "baoab"])
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import paper_2412_15073_gb300 as M
+    from paper_2412_15073_gb300 import systems
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    stream = torch.cuda.current_stream()
+    w = systems.water_box(N_MOL, box=BOX, seed=0)
+    n = w.n
+    if args.equil > 0:
+        # relax the lattice start at strong friction so both integrators start at 300 K
+        eq = M.Engine(precision=M.MD_MIXED, seed=99 + 1000 * rank, device=local, stream=stream.cuda_stream)
+        eq.set_system(0, w, **(PARAMS | {"gamma": 20.0}))
+        eq.baoab(args.equil)
+        w.x, w.v = eq.state()[0], eq.state()[1]
+        eq.close()
+
+    def engine(seed):
+        e = M.Engine(precision=M.MD_MIXED, seed=seed + 1000 * rank, device=local, stream=stream.cuda_stream)
+        e.set_system(0, w, **PARAMS)
+        return e
+
+    if args.only != "all":
+        # profiling run: one integrator only, no side measurements
+        e = engine(1)
+        fn = e.jump if args.only == "jump" else e.baoab
+        fn(args.warmup)
+        t = timed(e, fn, args.steps, stream)
+        if rank == 0:
+            print(json.dumps({"only": args.only, "ns_per_day": ns_per_day(args.steps * DT_FS, t),
+                              "ms_per_step": t / args.steps * 1e3, "profile_launches": e.profile()[2].tolist()}))
+        e.close()
+        return
+
+    ej = engine(1)
+    eb = engine(2)
+    # warm-up (also picks threads per atom)
+    ej.jump(args.warmup)
+    eb.baoab(args.warmup)
+    ej.observables()
+    c0 = ej.observables()
+    l0 = ej.profile()[2].sum()
+
+    barrier()
+    with Clocks(local) as clk:
+        t_jump = timed(ej, ej.jump, args.steps, stream)
+        barrier()
+        t_baoab = timed(eb, eb.baoab, args.steps, stream)
+        barrier()
+    launches = int(ej.profile()[2].sum() - l0)
+    t_jump = max_over_ranks(t_jump)
+    t_baoab = max_over_ranks(t_baoab)
+    c1 = ej.observables()
+    ob_b = eb.observables()
+
+    jump_nsday = ns_per_day(world * args.steps * DT_FS, t_jump)
+    baoab_nsday = ns_per_day(world * args.steps * DT_FS, t_baoab)
+
+    # pair evaluations (unique pairs) per step
+    x_end = ej.state()[0]
+    pairs_short = pair_counts(x_end, BOX, PARAMS["r_split"])
+    pairs_full = pair_counts(eb.state()[0], BOX, PARAMS["r_cut"])
+    props = (c1["jump_proposals"] - c0["jump_proposals"] + c1["bps_proposals"] - c0["bps_proposals"]) / args.steps
+    gpe_jump = world * (pairs_short + props) * args.steps / t_jump / 1e9
+    gpe_baoab = world * pairs_full * args.steps / t_baoab / 1e9
+
+    # per-class device time of the JUMP step (separate profiled run)
+    ej.profile(enable=1, reset=True)
+    prof_steps = min(args.steps, 200)
+    cp0 = ej.observables()
+    ej.jump(prof_steps)
+    cp1 = ej.observables()
+    ms, groups, _ = ej.profile(enable=0)
+    classes = ["pair_force", "bonded", "velocity_phase", "kick_aoa", "list_rebuild", "bookkeeping"]
+    top = int(np.argmax(ms))
+    pk, how = peaks()
+    clock = (pk.get("sm_max_mhz") or 2070.0) * 1e6
+    fp32_peak = 152 * 128 * 2 * clock / 1e12          # TFLOP/s, FMA = 2
+    alu_peak = 152 * 128 * clock / 1e12               # T lane-instructions/s
+    per_launch_ms = ms[top] / max(groups[top], 1)
+    if classes[top] == "velocity_phase":
+        props_per_launch = ((cp1["jump_proposals"] - cp0["jump_proposals"]) +
+                            (cp1["bps_proposals"] - cp0["bps_proposals"])) / max(groups[top], 1)
+        achieved = OPS_PER_PROPOSAL * props_per_launch / (per_launch_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
+                "frac": achieved / alu_peak, "traffic": None, "kernel": "k_vphase (C'/J' jumps)",
+                "units_per_launch": props_per_launch, "ops_per_unit": OPS_PER_PROPOSAL,
+                "peak_source": f"152 SMs x 128 lanes x {clock/1e6:.0f} MHz (max clock)"}
+    else:
+        achieved = FLOP_PER_PAIR * pairs_short / (per_launch_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": None, "kernel": "k_force (short pairs)",
+                "units_per_launch": pairs_short, "ops_per_unit": FLOP_PER_PAIR,
+                "peak_source": f"FP32: 152 SMs x 128 lanes x 2 x {clock/1e6:.0f} MHz (max clock)"}
+    roof["share_of_step"] = float(ms[top] / ms.sum())
+    roof["class_ms_per_step"] = {c: float(m / prof_steps) for c, m in zip(classes, ms)}
+
+    # RESPA1 pair (config: delta 1 fs, kappa 2 fs, Delta 6 fs)
+    respa = None
+    if args.respa1:
+        er = engine(3)
+        eb1 = engine(4)
+        cyc = max(args.steps // 6, 1)
+        er.jump_respa1(2, 1.0, 2, 3)
+        eb1.baoab_respa1(2, 1.0, 2, 3)
+        barrier()
+        t_jr = max_over_ranks(timed(er, lambda k: er.jump_respa1(k, 1.0, 2, 3), cyc, stream))
+        t_br = max_over_ranks(timed(eb1, lambda k: eb1.baoab_respa1(k, 1.0, 2, 3), cyc, stream))
+        respa = {"jump_respa1_ns_per_day": ns_per_day(world * cyc * 6 * DT_FS, t_jr),
+                 "baoab_respa1_ns_per_day": ns_per_day(world * cyc * 6 * DT_FS, t_br),
+                 "steps": "1:2:6 fs (delta, kappa, Delta)", "cycles": cyc}
+        er.close()
+        eb1.close()
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e = e2e_run(ej, args, M, torch, stream, n, world, max_over_ranks, barrier)
+    state_bytes = n * (4 * 3 * 8 + 3 * 4)
+    out = {"metric": METRIC, "value": jump_nsday, "unit": "ns/day", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_jump / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32+i64+f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "atoms": n, "global_batch": world, "parallelism": "replicas",
+                      "l2": "working set (neighbour and jump lists) ~3x the 129 MB L2; consecutive MD steps, no flush"},
+           "jump_ns_per_day": jump_nsday, "baoab_ns_per_day": baoab_nsday,
+           "speedup_vs_baoab": jump_nsday / baoab_nsday,
+           "gpair_evals_per_s": {"jump": gpe_jump, "baoab": gpe_baoab},
+           "matched_T_D": {"jump_T": c1["temperature"], "baoab_T": ob_b["temperature"]},
+           "jump_stats": {"proposals_per_atom_step": (c1["jump_proposals"] - c0["jump_proposals"]) / (n * args.steps),
+                          "accept_frac": (c1["jump_accepts"] - c0["jump_accepts"]) /
+                                         max(c1["jump_proposals"] - c0["jump_proposals"], 1),
+                          "bps_per_atom_step": (c1["bps_proposals"] - c0["bps_proposals"]) / (n * args.steps),
+                          "list_rebuilds": c1["list_rebuilds"] - c0["list_rebuilds"],
+                          "short_pairs": pairs_short, "full_pairs": pairs_full},
+           "respa1": respa,
+           "roofline": roof | {"peak_kind": how},
+           "e2e": e2e,
+           "gpu_launches": launches,
+           "clocks": clk.summary()}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        secs, done, thr = cpu_oracle_sample(w, PARAMS, args.cpu_sample, 1)
+        out["cpu_baseline"] = {"value": ns_per_day(done / n * DT_FS, secs), "unit": "ns/day", "cores": thr,
+                               "kind": "oracle",
+                               "sample": f"{done} of 96,000 atoms: O(N) F0 gradient + four velocity phases of "
+                                         f"one JUMP step each, scaled to the full step (list builds excluded)"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    for e in (ej, eb):
+        e.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

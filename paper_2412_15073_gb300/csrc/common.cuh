@@ -1,0 +1,253 @@
+// common.cuh -- device-side building blocks of the GB300 JUMP engine.
+//
+// Internal header of libmdjump.so (not installed). Holds the per-replica
+// parameter block, the counter-based Philox4x32-10 generator, the pair terms
+// (DSF Coulomb, shifted-force LJ, the quintic switch chi of Sec. 3.1), the
+// normal-law helpers for Theta(eta) and the G~ sampler (Sec. 2.2, 2.4).
+// Every function is templated on the arithmetic type T: double for the FP64
+// parity mode, float for the mixed-precision mode.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mdj {
+
+// ---- physical constants (kcal/mol, A, ps, amu, e) --------------------------
+constexpr double KB = 0.0019872042586;     // kcal/mol/K
+constexpr double COULOMB = 332.0637;       // kcal A / (mol e^2)
+constexpr double KCAL_AMU = 418.4;         // 1 kcal/mol = 418.4 amu A^2 / ps^2
+constexpr double PI = 3.14159265358979323846;
+
+constexpr int MAX_TYPES = 8;
+constexpr int KMAX = 1 << 20;              // proposal cap per atom and phase
+constexpr int SAMPLER_CAP = 64;            // attempts of the G~ sampler
+
+// Philox stream tags (counter word 2, bits 24..31)
+constexpr uint32_t TAG_O = 1, TAG_C = 2, TAG_J = 3, TAG_S = 4;
+
+// error flag bits (match MD_FLAG_* in md.h)
+constexpr uint32_t F_BOUND = 1, F_LIMIT = 2, F_NONFIN = 4, F_OVERFLOW = 8;
+
+// list kinds
+enum ListKind { L_SHORT = 0, L_FULL = 1, L_RM = 2, L_RL = 3, L_LJ = 4, NKIND = 5 };
+
+// counters per replica
+enum Counter { C_CPROP = 0, C_CACC, C_JPROP, C_JACC, C_SATT, C_REBUILD, C_OUTER, C_GUARD, NCOUNT };
+
+// pair weight: full U, short chi U, long (1 - chi) U
+enum Weight { W_FULL = 0, W_SHORT = 1, W_LONG = 2 };
+
+struct LJPair {
+    double c12, c6, uR, duR;   // 4 eps s^12, 4 eps s^6, U_LJ(R), U_LJ'(R)
+    float c12f, c6f, uRf, duRf;
+    int on;                    // eps > 0
+    int pad;
+};
+
+// Everything a kernel needs about one replica. Device resident, one per replica.
+struct RepParams {
+    double L, invL;
+    int atom_off, n;
+    // outer candidate grid (fixes the order of the jump lists)
+    int nc, cell_off;
+    double cs;
+    // scaled coordinates: x = s L / 2^32 with s a 32-bit integer, so that
+    // integer differences give the minimum image exactly
+    double scl, inv_scl;       // L / 2^32, 2^32 / L
+    float sclf, pad1;
+    // cutoffs
+    double R, rc, h, sw, rM;   // r_E, r_c, h, r_c - h, r_M (= sw with one ring)
+    int one_ring, rings_on, lj_on, eps_mode;
+    double skin, skin_o;
+    // DSF: u(r) = erfc(a r)/r - eR + fR (r - R); u'(r) = -erfc(a r)/r^2 - k exp(-a^2 r^2)/r + fR
+    double alpha, eR, fR, kexp;     // kexp = 2 a / sqrt(pi)
+    float alphaf, eRf, fRf, kexpf;
+    // thermostat / jumps
+    double beta, gamma, eps0;
+    uint32_t seed, replica;
+    int ntypes, pad2;
+    LJPair lj[MAX_TYPES * MAX_TYPES];
+};
+
+// ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) ---------------------
+struct U4 { uint32_t x, y, z, w; };
+
+__device__ __forceinline__ U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                     uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ k0;
+        const uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    }
+    return U4{c0, c1, c2, c3};
+}
+
+__device__ __forceinline__ U4 draw(const RepParams& P, uint32_t atom, uint32_t s0, uint32_t tag,
+                                   int half, uint32_t attempt, uint32_t k)
+{
+    return philox(atom, s0, (tag << 24) | (uint32_t(half) << 20) | (attempt << 8), k,
+                  P.seed, P.replica);
+}
+
+// uniform on (0,1): (b + 1/2) 2^-32
+template <typename T> __device__ __forceinline__ T unif(uint32_t b);
+template <> __device__ __forceinline__ double unif<double>(uint32_t b)
+{
+    return ((double)b + 0.5) * (1.0 / 4294967296.0);
+}
+template <> __device__ __forceinline__ float unif<float>(uint32_t b)
+{
+    // exact 24-bit rounding of (b + 1/2) 2^-32 through the double path would
+    // cost FP64; take the top 24 bits plus a half step instead: (b>>8 + 1/2) 2^-24
+    return ((float)(b >> 8) + 0.5f) * (1.0f / 16777216.0f);
+}
+
+// ---- math shims --------------------------------------------------------------
+__device__ __forceinline__ double d_erfc(double x) { return erfc(x); }
+__device__ __forceinline__ float d_erfc(float x) { return erfcf(x); }
+__device__ __forceinline__ double d_exp(double x) { return exp(x); }
+__device__ __forceinline__ float d_exp(float x) { return expf(x); }
+__device__ __forceinline__ double d_log(double x) { return log(x); }
+__device__ __forceinline__ float d_log(float x) { return logf(x); }
+__device__ __forceinline__ double d_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float d_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double d_rint(double x) { return rint(x); }
+__device__ __forceinline__ float d_rint(float x) { return rintf(x); }
+__device__ __forceinline__ void d_sincospi(double x, double* s, double* c) { sincospi(x, s, c); }
+__device__ __forceinline__ void d_sincospi(float x, float* s, float* c) { sincospif(x, s, c); }
+
+template <typename T> struct PT;
+template <> struct PT<double> {
+    __device__ static double alpha(const RepParams& P) { return P.alpha; }
+    __device__ static double eR(const RepParams& P) { return P.eR; }
+    __device__ static double fR(const RepParams& P) { return P.fR; }
+    __device__ static double kexp(const RepParams& P) { return P.kexp; }
+    __device__ static double c12(const LJPair& l) { return l.c12; }
+    __device__ static double c6(const LJPair& l) { return l.c6; }
+    __device__ static double uR(const LJPair& l) { return l.uR; }
+    __device__ static double duR(const LJPair& l) { return l.duR; }
+};
+template <> struct PT<float> {
+    __device__ static float alpha(const RepParams& P) { return P.alphaf; }
+    __device__ static float eR(const RepParams& P) { return P.eRf; }
+    __device__ static float fR(const RepParams& P) { return P.fRf; }
+    __device__ static float kexp(const RepParams& P) { return P.kexpf; }
+    __device__ static float c12(const LJPair& l) { return l.c12f; }
+    __device__ static float c6(const LJPair& l) { return l.c6f; }
+    __device__ static float uR(const LJPair& l) { return l.uRf; }
+    __device__ static float duR(const LJPair& l) { return l.duRf; }
+};
+
+// ---- switch chi (quintic step on [r_c - h, r_c]) ----------------------------
+template <typename T>
+__device__ __forceinline__ void chi_and_slope(T r, T sw, T h, T& c, T& dc)
+{
+    if (r <= sw) { c = T(1); dc = T(0); return; }
+    if (r >= sw + h) { c = T(0); dc = T(0); return; }
+    const T s = (r - sw) / h;
+    const T s2 = s * s;
+    c = T(1) - s2 * s * (T(10) - T(15) * s + T(6) * s2);
+    const T om = T(1) - s;
+    dc = T(-30) * s2 * om * om / h;
+}
+
+// DSF Coulomb per unit C q_i q_j: value and radial derivative, r < R
+template <typename T>
+__device__ __forceinline__ void dsf(const RepParams& P, T r, T rinv, T& u, T& du)
+{
+    const T a = PT<T>::alpha(P);
+    const T e = d_erfc(a * r);
+    const T g = PT<T>::kexp(P) * d_exp(-a * a * r * r);
+    u = e * rinv - PT<T>::eR(P) + PT<T>::fR(P) * (r - T(P.R));
+    du = -(e * rinv + g) * rinv + PT<T>::fR(P);
+}
+
+// shifted-force LJ: value and radial derivative, r < R
+template <typename T>
+__device__ __forceinline__ void ljsf(const RepParams& P, const LJPair& l, T r, T rinv, T& u, T& du)
+{
+    const T r2i = rinv * rinv;
+    const T r6i = r2i * r2i * r2i;
+    const T c12 = PT<T>::c12(l), c6 = PT<T>::c6(l);
+    u = r6i * (c12 * r6i - c6) - PT<T>::uR(l) - (r - T(P.R)) * PT<T>::duR(l);
+    du = r6i * rinv * (T(6) * c6 - T(12) * c12 * r6i) - PT<T>::duR(l);
+}
+
+// ---- normal law --------------------------------------------------------------
+template <typename T> __device__ __forceinline__ T nphi(T y)
+{
+    return d_exp(T(-0.5) * y * y) * T(0.3989422804014327);
+}
+template <typename T> __device__ __forceinline__ T nPhi(T y)
+{
+    return T(0.5) * d_erfc(-y * T(0.7071067811865476));
+}
+// Theta(eta) = E[(eta + G)_+] = eta Phi(eta) + phi(eta)
+template <typename T> __device__ __forceinline__ T theta(T eta)
+{
+    const T t = eta * nPhi(eta) + nphi(eta);
+    return t > T(0) ? t : T(0);
+}
+
+// one attempt of the G~ rejection sampler (Sec. 2.4); returns true on accept
+template <typename T>
+__device__ __forceinline__ bool gtilde_attempt(T eta, const U4& u, T& y)
+{
+    if (eta > T(0)) {
+        const T pg = eta / (eta + T(0.3989422804014327));
+        const T rad = d_sqrt(T(-2) * d_log(unif<T>(u.y)));
+        if (unif<T>(u.x) < pg) {
+            T s, c;
+            d_sincospi(T(2) * unif<T>(u.z), &s, &c);
+            y = rad * c;
+        } else {
+            y = rad;
+        }
+        if (y >= T(0)) return true;
+        const T ratio = (eta + y) > T(0) ? (eta + y) / eta : T(0);
+        return unif<T>(u.w) <= ratio;
+    } else if (eta >= T(-1)) {
+        const T z = d_sqrt(T(-2) * d_log(unif<T>(u.x)));
+        y = z - eta;
+        return unif<T>(u.y) <= d_exp(eta * z);
+    } else if (eta >= T(-2.5)) {
+        const T z = -d_log(unif<T>(u.x)) / (-eta);
+        y = z - eta;
+        return unif<T>(u.y) <= z * d_exp(T(0.5) * (T(1) - z * z));
+    } else {
+        const T z = -(d_log(unif<T>(u.x)) + d_log(unif<T>(u.y))) / (-eta);
+        y = z - eta;
+        return unif<T>(u.z) <= d_exp(T(-0.5) * z * z);
+    }
+}
+
+// ---- fixed point (2^32 units of kcal/mol/A) -----------------------------------
+constexpr double FIX_SCALE = 4294967296.0;
+constexpr double FIX_INV = 1.0 / 4294967296.0;
+
+__device__ __forceinline__ long long to_fix(float f)
+{
+    return __float2ll_rn(f * 4294967296.0f);
+}
+
+// ---- scaled 32-bit coordinates ----------------------------------------------------
+// position in [0, L) -> integer in [0, 2^32) (wraps at L, which is the periodic box)
+__device__ __forceinline__ uint32_t to_scaled(double x, const RepParams& P)
+{
+    return (uint32_t)(unsigned long long)llrint(x * P.inv_scl);
+}
+// FP32 minimum-image displacement a - b: exact integer difference, one rounding
+__device__ __forceinline__ void sdisp(const uint4& a, const uint4& b, float s, float& dx, float& dy, float& dz)
+{
+    dx = __int2float_rn(int(a.x - b.x)) * s;
+    dy = __int2float_rn(int(a.y - b.y)) * s;
+    dz = __int2float_rn(int(a.z - b.z)) * s;
+}
+
+}  // namespace mdj

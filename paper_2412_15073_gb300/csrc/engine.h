@@ -1,0 +1,92 @@
+// engine.h -- internal interface between the host engine (md_api.cu) and the
+// kernel translation units of libmdjump.so. Not installed.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace mdj {
+
+// Device pointers of one context, passed by value to every kernel. All atom
+// arrays are concatenated over replicas (replica r owns [atom_off, atom_off+n)).
+struct Dev {
+    int N, R;
+    const RepParams* P;
+    const int* rep;                 // atom -> replica
+    const int* vorder;              // visiting order of the velocity phases (grouped by jump rate)
+    // state (FP64 master copies)
+    double *x, *v, *xb, *xo;        // positions, velocities, positions at list build / outer build
+    int* img;                       // periodic image counts
+    double *a0, *ab, *as, *al;      // accelerations: F0 (or full), bonded, short pairs, long pairs
+    double* gout;                   // gradient output of md_gradient
+    // scaled 32-bit coordinates (x, y, z) and the charge as float bits in w
+    uint4* pos;
+    // per-atom constants
+    const double *mt, *isqmt, *q;   // m/418.4, 1/sqrt(m~), charge
+    const int* type;
+    const double *LM, *LL, *LLJ;    // rate bounds per atom
+    const float *LMf, *LLf, *LLJf;
+    // bonded terms: per-atom items (kind | role << 4, term index)
+    const int* bi_off;
+    const int2* bitem;
+    const int2* bond_ij;
+    const double *bond_k, *bond_r0;
+    const int4* ang;                // (end a, centre, end b, 0)
+    const double *ang_k, *ang_t0;
+    // exclusions (both directions)
+    const int* ex_off;
+    const int* ex_idx;
+    // outer grid cells
+    int *cell_start, *cell_cnt, *cell_atoms, *atom_cell, *cell_rep;
+    int total_cells;
+    // outer candidate list (global indices, ordered by (cell, j))
+    uint32_t* olist;
+    int* ocnt;
+    int ocap;
+    // inner lists (packed entries)
+    uint32_t* list[NKIND];
+    int* lcnt[NKIND];
+    int lcap[NKIND];
+    // per replica
+    int* flags;                     // [R][2]: inner rebuild, outer rebuild
+    uint32_t* err;                  // [R]
+    uint32_t* ovf;                  // [R] which capacity overflowed: bit kind, 5 outer list, 6 cell
+    unsigned long long* cnt;        // [R][NCOUNT]
+    double* energy;                 // [R][6]: bond, angle, lj, coul, ke, spare
+    long long* step_base;           // [R]
+    double* stepc;                  // [R][2]: exp(-gamma tau), sqrt((1 - exp(-2 gamma tau)) / beta)
+    // accepted-jump log
+    long long* ev;
+    unsigned long long* ev_n;
+    long long ev_cap;
+};
+
+// ---- lists (k_lists.cu) ---------------------------------------------------------
+void launch_check(const Dev& d, int force_inner, int force_outer, cudaStream_t s);
+void launch_rebuild(const Dev& d, int kinds, int fp64, int keep_refs, int exact_outer,
+                    int max_cells_per_rep, cudaStream_t s);
+void launch_late_lists(const Dev& d, int kinds, cudaStream_t s);
+
+// ---- forces and integrators (k_force.cu) -----------------------------------------
+// mode: 0 full, 1 bonded, 2 nb full, 3 nb short, 4 nb long, 5 F0 (bonded + short)
+void launch_force(const Dev& d, int mode, double* out, int as_grad, int fp64, int tpa, cudaStream_t s);
+void launch_kick(const Dev& d, const double* a, double h, cudaStream_t s);
+void launch_kick2(const Dev& d, const double* a, double h, const double* b, double hb, cudaStream_t s);
+void launch_aoa(const Dev& d, double tau, uint32_t s_off, int do_check, int fp64, cudaStream_t s);
+void launch_energy(const Dev& d, cudaStream_t s);
+void launch_advance(const Dev& d, long long nsteps, cudaStream_t s);
+
+// ---- jumps (k_jump.cu) --------------------------------------------------------------
+// order 0: C' then J' (first half of a step), 1: J' then C' (second half)
+// variant: occupancy target of the mixed-mode kernel (0: 1 block/SM bound,
+// 1: 4, 2: 5, 3: 6 blocks of 128 threads); every variant computes the same values
+constexpr int NVPHASE_VARIANTS = 4;
+void launch_vphase(const Dev& d, const double* a, double tau2, uint32_t s_off, int half, int order,
+                   int doC, int doJ, int fp64, int variant, cudaStream_t s);
+// same with an absolute stream index s0 (md_run_phase)
+void launch_vphase_abs(const Dev& d, const double* a, double tau2, uint32_t s0, int half, int order,
+                       int doC, int doJ, int fp64, int variant, cudaStream_t s);
+
+}  // namespace mdj

@@ -1,0 +1,433 @@
+// k_force.cu -- pair and bonded gradients, kicks, the A O A update, energies.
+//
+// Pair terms (LJ shifted in value and slope at r_E, DSF Coulomb) weighted by
+// 1, chi or 1 - chi (the split U = chi U + (1 - chi) U of Sec. 3.1); bonded
+// terms 1/2 k (r - r0)^2 and 1/2 k (theta - theta0)^2. One thread per atom
+// owns its gradient (full neighbour lists, no atomics); in the mixed mode each
+// pair contribution is rounded to 64-bit fixed point (2^-32 kcal/mol/A) before
+// it is summed, so the sum does not depend on the order of the list.
+// The B, A and O parts follow the splitting of Sec. 2.3: B kicks the
+// velocity, A moves positions, O is the exact Ornstein-Uhlenbeck step with
+// Philox normals.
+#include "engine.h"
+
+namespace mdj {
+
+namespace {
+
+__device__ __forceinline__ double3 ld3(const double* p, int i)
+{
+    return make_double3(p[3 * i], p[3 * i + 1], p[3 * i + 2]);
+}
+
+__device__ __forceinline__ double mimg(double t, const RepParams& P)
+{
+    return t - P.L * rint(t * P.invL);
+}
+
+// displacement x_i - x_j at the current positions
+template <typename T> struct Disp;
+template <> struct Disp<double> {
+    __device__ static void get(const Dev& d, const RepParams& P, int i, int j, double& dx, double& dy,
+                               double& dz)
+    {
+        const double3 a = ld3(d.x, i), b = ld3(d.x, j);
+        dx = mimg(a.x - b.x, P); dy = mimg(a.y - b.y, P); dz = mimg(a.z - b.z, P);
+    }
+};
+template <> struct Disp<float> {
+    __device__ static void get(const Dev& d, const RepParams& P, int i, int j, float& dx, float& dy,
+                               float& dz)
+    {
+        sdisp(d.pos[i], d.pos[j], P.sclf, dx, dy, dz);
+    }
+};
+
+// gradient on atom i of its bonded terms; evaluated in FP64 in both modes:
+// with k_b ~ 10^3 kcal/mol/A^2 an FP32 bond length would put ~10^-4 kcal/mol/A
+// of error on the force
+template <typename T>
+__device__ void bonded_grad(const Dev& d, const RepParams& P, int i, double& gx, double& gy, double& gz)
+{
+    const int b0 = d.bi_off[i], b1 = d.bi_off[i + 1];
+    for (int it = b0; it < b1; ++it) {
+        const int2 item = d.bitem[it];
+        const int kind = item.x & 15, role = item.x >> 4, t = item.y;
+        if (kind == 0) {
+            const int2 ij = d.bond_ij[t];
+            const int p = role == 0 ? ij.y : ij.x;
+            T dx, dy, dz;
+            Disp<T>::get(d, P, i, p, dx, dy, dz);
+            const T r = d_sqrt(dx * dx + dy * dy + dz * dz);
+            const T f = r > T(0) ? T(d.bond_k[t]) * (r - T(d.bond_r0[t])) / r : T(0);
+            gx += double(f * dx); gy += double(f * dy); gz += double(f * dz);
+        } else {
+            const int4 a = d.ang[t];
+            T ax, ay, az, bx, by, bz;
+            Disp<T>::get(d, P, a.x, a.y, ax, ay, az);
+            Disp<T>::get(d, P, a.z, a.y, bx, by, bz);
+            const T ra = d_sqrt(ax * ax + ay * ay + az * az), rb = d_sqrt(bx * bx + by * by + bz * bz);
+            T cth = (ax * bx + ay * by + az * bz) / (ra * rb);
+            cth = cth > T(1) ? T(1) : (cth < T(-1) ? T(-1) : cth);
+            const T th = acos(cth);
+            const T sth = sin(th);
+            if (sth < T(1e-12)) continue;
+            const T pre = T(d.ang_k[t]) * (th - T(d.ang_t0[t]));
+            const T ia = T(1) / (ra * sth), ib = T(1) / (rb * sth);
+            const T gax = (cth * ax / ra - bx / rb) * ia, gay = (cth * ay / ra - by / rb) * ia,
+                    gaz = (cth * az / ra - bz / rb) * ia;
+            const T gbx = (cth * bx / rb - ax / ra) * ib, gby = (cth * by / rb - ay / ra) * ib,
+                    gbz = (cth * bz / rb - az / ra) * ib;
+            if (role == 0) {
+                gx += double(pre * gax); gy += double(pre * gay); gz += double(pre * gaz);
+            } else if (role == 2) {
+                gx += double(pre * gbx); gy += double(pre * gby); gz += double(pre * gbz);
+            } else {
+                gx -= double(pre * (gax + gbx)); gy -= double(pre * (gay + gby)); gz -= double(pre * (gaz + gbz));
+            }
+        }
+    }
+}
+
+// pair gradient accumulators: fixed point for float, double for double
+template <typename T> struct Acc;
+template <> struct Acc<float> {
+    long long x = 0, y = 0, z = 0;
+    __device__ void add(float f, float dx, float dy, float dz)
+    {
+        x += to_fix(f * dx); y += to_fix(f * dy); z += to_fix(f * dz);
+    }
+    __device__ void combine_shfl(int tpa)
+    {
+        for (int o = tpa >> 1; o > 0; o >>= 1) {
+            x += __shfl_down_sync(0xffffffffu, x, o, tpa);
+            y += __shfl_down_sync(0xffffffffu, y, o, tpa);
+            z += __shfl_down_sync(0xffffffffu, z, o, tpa);
+        }
+    }
+    __device__ double gx() const { return double(x) * FIX_INV; }
+    __device__ double gy() const { return double(y) * FIX_INV; }
+    __device__ double gz() const { return double(z) * FIX_INV; }
+};
+template <> struct Acc<double> {
+    double x = 0, y = 0, z = 0;
+    __device__ void add(double f, double dx, double dy, double dz)
+    {
+        x += f * dx; y += f * dy; z += f * dz;
+    }
+    __device__ void combine_shfl(int tpa)
+    {
+        for (int o = tpa >> 1; o > 0; o >>= 1) {
+            x += __shfl_down_sync(0xffffffffu, x, o, tpa);
+            y += __shfl_down_sync(0xffffffffu, y, o, tpa);
+            z += __shfl_down_sync(0xffffffffu, z, o, tpa);
+        }
+    }
+    __device__ double gx() const { return x; }
+    __device__ double gy() const { return y; }
+    __device__ double gz() const { return z; }
+};
+
+// pair gradient over the list of atom i; TPA threads per atom stride the list
+template <typename T, int W, bool BONDED, int TPA>
+__global__ void __launch_bounds__(256) k_force(Dev d, int lk, double* out, int as_grad)
+{
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = gt / TPA, sub = gt % TPA;
+    const bool live = i < d.N;
+    const int ii = live ? i : d.N - 1;
+    const int r = d.rep[ii];
+    const RepParams& P = d.P[r];
+    Acc<T> acc;
+    if (live) {
+        const int ti = d.type[i];
+        const T qi = T(d.q[i]);
+        const T cut = W == W_SHORT ? T(fmin(P.rc, P.R)) : T(P.R);
+        const T cut2 = cut * cut;
+        const T sw = T(P.sw), h = T(P.h), sw2 = sw * sw;
+        const T C = T(COULOMB);
+        const uint32_t* row = d.list[lk] + (size_t)i * d.lcap[lk];
+        const int n = min(d.lcnt[lk][i], d.lcap[lk]);
+        // position of i in the arithmetic type
+        uint4 pi = make_uint4(0, 0, 0, 0);
+        double3 xi = make_double3(0, 0, 0);
+        if (sizeof(T) == 4) pi = d.pos[i];
+        else xi = ld3(d.x, i);
+        const float sc = P.sclf;
+        for (int k = sub; k < n; k += TPA) {
+            const int j = int(row[k]);
+            T dx, dy, dz, qj;
+            if (sizeof(T) == 4) {
+                const uint4 pj = d.pos[j];
+                float fx, fy, fz;
+                sdisp(pi, pj, sc, fx, fy, fz);
+                dx = T(fx); dy = T(fy); dz = T(fz);
+                qj = T(__uint_as_float(pj.w));
+            } else {
+                const double3 xj = ld3(d.x, j);
+                dx = T(mimg(xi.x - xj.x, P)); dy = T(mimg(xi.y - xj.y, P)); dz = T(mimg(xi.z - xj.z, P));
+                qj = T(d.q[j]);
+            }
+            const T r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 >= cut2) continue;
+            if (W == W_LONG && r2 <= sw2) continue;
+            const T rr = d_sqrt(r2);
+            const T rinv = T(1) / rr;
+            T u = T(0), du = T(0);
+            const T qq = qi * qj;
+            if (qq != T(0)) {
+                T uc, duc;
+                dsf<T>(P, rr, rinv, uc, duc);
+                u = C * qq * uc;
+                du = C * qq * duc;
+            }
+            const LJPair& lj = P.lj[ti * MAX_TYPES + d.type[j]];
+            if (lj.on) {
+                T ul, dul;
+                ljsf<T>(P, lj, rr, rinv, ul, dul);
+                u += ul;
+                du += dul;
+            }
+            T f;
+            if (W == W_FULL) {
+                f = du;
+            } else {
+                T c, dc;
+                chi_and_slope<T>(rr, sw, h, c, dc);
+                f = W == W_SHORT ? dc * u + c * du : -dc * u + (T(1) - c) * du;
+            }
+            acc.add(f * rinv, dx, dy, dz);
+        }
+    }
+    if (TPA > 1) acc.combine_shfl(TPA);
+    if (!live || sub != 0) return;
+    double gx = acc.gx(), gy = acc.gy(), gz = acc.gz();
+    if (BONDED) bonded_grad<double>(d, P, i, gx, gy, gz);
+    if (as_grad) {
+        out[3 * i] = gx; out[3 * i + 1] = gy; out[3 * i + 2] = gz;
+    } else {
+        const double s = -1.0 / d.mt[i];
+        out[3 * i] = s * gx; out[3 * i + 1] = s * gy; out[3 * i + 2] = s * gz;
+    }
+}
+
+template <typename T>
+__global__ void k_bonded(Dev d, double* out, int as_grad)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.N) return;
+    const RepParams& P = d.P[d.rep[i]];
+    double gx = 0, gy = 0, gz = 0;
+    bonded_grad<double>(d, P, i, gx, gy, gz);
+    if (as_grad) {
+        out[3 * i] = gx; out[3 * i + 1] = gy; out[3 * i + 2] = gz;
+    } else {
+        const double s = -1.0 / d.mt[i];
+        out[3 * i] = s * gx; out[3 * i + 1] = s * gy; out[3 * i + 2] = s * gz;
+    }
+}
+
+__global__ void k_kick(Dev d, const double* a, double h)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= 3 * d.N) return;
+    d.v[k] += h * a[k];
+}
+
+__global__ void k_kick2(Dev d, const double* a, double h, const double* b, double hb)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= 3 * d.N) return;
+    double v = d.v[k] + h * a[k];
+    d.v[k] = v + hb * b[k];
+}
+
+// A(tau/2) O(tau) A(tau/2), wrap, refresh the FP32 mirror, optional list check
+template <typename T>
+__global__ void k_aoa(Dev d, double tau, uint32_t s_off, int do_check)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.N) return;
+    const int r = d.rep[i];
+    const RepParams& P = d.P[r];
+    const uint32_t s0 = uint32_t(d.step_base[r]) + s_off;
+    const double h = 0.5 * tau;
+    double x[3] = {d.x[3 * i], d.x[3 * i + 1], d.x[3 * i + 2]};
+    double v[3] = {d.v[3 * i], d.v[3 * i + 1], d.v[3 * i + 2]};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) x[a] += h * v[a];
+    const U4 u = draw(P, uint32_t(i - P.atom_off), s0, TAG_O, 0, 0, 0);
+    const T r0 = d_sqrt(T(-2) * d_log(unif<T>(u.x)));
+    const T r1 = d_sqrt(T(-2) * d_log(unif<T>(u.z)));
+    T s1, c1v, s2, c2v;
+    d_sincospi(T(2) * unif<T>(u.y), &s1, &c1v);
+    d_sincospi(T(2) * unif<T>(u.w), &s2, &c2v);
+    const double G[3] = {double(r0 * c1v), double(r0 * s1), double(r1 * c2v)};
+    const double c1 = d.stepc[2 * r], c2 = d.stepc[2 * r + 1] * d.isqmt[i];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) v[a] = c1 * v[a] + c2 * G[a];
+    int im[3] = {0, 0, 0};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        x[a] += h * v[a];
+        if (x[a] < 0.0) { x[a] += P.L; im[a] -= 1; }
+        if (x[a] >= P.L) { x[a] -= P.L; im[a] += 1; }
+    }
+    bool fin = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        fin = fin && isfinite(x[a]) && isfinite(v[a]);
+        d.x[3 * i + a] = x[a];
+        d.v[3 * i + a] = v[a];
+        if (im[a]) d.img[3 * i + a] += im[a];
+    }
+    if (!fin) atomicOr(&d.err[r], F_NONFIN);
+    // scaled 32-bit coordinates for the FP32 kernels (w keeps the charge)
+    uint4 sp = d.pos[i];
+    sp.x = to_scaled(x[0], P); sp.y = to_scaled(x[1], P); sp.z = to_scaled(x[2], P);
+    d.pos[i] = sp;
+    if (do_check) {
+        const double lo = 0.5 * (P.skin_o - P.skin), li = 0.5 * P.skin;
+        double t0 = mimg(x[0] - d.xo[3 * i], P), t1 = mimg(x[1] - d.xo[3 * i + 1], P),
+               t2 = mimg(x[2] - d.xo[3 * i + 2], P);
+        if (t0 * t0 + t1 * t1 + t2 * t2 > lo * lo) {
+            d.flags[2 * r + 1] = 1;
+            d.flags[2 * r] = 1;
+        }
+        t0 = mimg(x[0] - d.xb[3 * i], P); t1 = mimg(x[1] - d.xb[3 * i + 1], P);
+        t2 = mimg(x[2] - d.xb[3 * i + 2], P);
+        if (t0 * t0 + t1 * t1 + t2 * t2 > li * li) d.flags[2 * r] = 1;
+    }
+}
+
+// energies of the full potential (FP64), kinetic energy; one pass per atom
+__global__ void k_energy(Dev d)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.N) return;
+    const int r = d.rep[i];
+    const RepParams& P = d.P[r];
+    double eb = 0, ea = 0, elj = 0, ec = 0, ke = 0;
+    const double3 v = ld3(d.v, i);
+    ke = 0.5 * d.mt[i] * (v.x * v.x + v.y * v.y + v.z * v.z);
+    for (int it = d.bi_off[i]; it < d.bi_off[i + 1]; ++it) {
+        const int2 item = d.bitem[it];
+        const int kind = item.x & 15, role = item.x >> 4, t = item.y;
+        if (kind == 0 && role == 0) {
+            const int2 ij = d.bond_ij[t];
+            double dx, dy, dz;
+            Disp<double>::get(d, P, ij.x, ij.y, dx, dy, dz);
+            const double rr = sqrt(dx * dx + dy * dy + dz * dz) - d.bond_r0[t];
+            eb += 0.5 * d.bond_k[t] * rr * rr;
+        } else if (kind == 1 && role == 1) {
+            const int4 a = d.ang[t];
+            double ax, ay, az, bx, by, bz;
+            Disp<double>::get(d, P, a.x, a.y, ax, ay, az);
+            Disp<double>::get(d, P, a.z, a.y, bx, by, bz);
+            double cth = (ax * bx + ay * by + az * bz) /
+                         (sqrt(ax * ax + ay * ay + az * az) * sqrt(bx * bx + by * by + bz * bz));
+            cth = fmin(1.0, fmax(-1.0, cth));
+            const double dt = acos(cth) - d.ang_t0[t];
+            ea += 0.5 * d.ang_k[t] * dt * dt;
+        }
+    }
+    const int n = min(d.ocnt[i], d.ocap);
+    const uint32_t* row = d.olist + (size_t)i * d.ocap;
+    const int ti = d.type[i];
+    for (int k = 0; k < n; ++k) {
+        const int j = int(row[k]);
+        if (j <= i) continue;
+        double dx, dy, dz;
+        Disp<double>::get(d, P, i, j, dx, dy, dz);
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 >= P.R * P.R) continue;
+        const double rr = sqrt(r2), rinv = 1.0 / rr;
+        const double qq = d.q[i] * d.q[j];
+        if (qq != 0.0) {
+            double uc, duc;
+            dsf<double>(P, rr, rinv, uc, duc);
+            ec += COULOMB * qq * uc;
+        }
+        const LJPair& lj = P.lj[ti * MAX_TYPES + d.type[j]];
+        if (lj.on) {
+            double ul, dul;
+            ljsf<double>(P, lj, rr, rinv, ul, dul);
+            elj += ul;
+        }
+    }
+    double* E = d.energy + 6 * r;
+    if (eb != 0) atomicAdd(&E[0], eb);
+    if (ea != 0) atomicAdd(&E[1], ea);
+    if (elj != 0) atomicAdd(&E[2], elj);
+    if (ec != 0) atomicAdd(&E[3], ec);
+    atomicAdd(&E[4], ke);
+}
+
+__global__ void k_advance(Dev d, long long n)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < d.R) d.step_base[r] += n;
+}
+
+inline int blocks(long long n, int b) { return int((n + b - 1) / b); }
+
+template <typename T, int W, bool B>
+void force_tpa(const Dev& d, int lk, double* out, int as_grad, int tpa, cudaStream_t s)
+{
+    const long long threads = (long long)d.N * tpa;
+    switch (tpa) {
+    case 1: k_force<T, W, B, 1><<<blocks(threads, 128), 128, 0, s>>>(d, lk, out, as_grad); break;
+    case 2: k_force<T, W, B, 2><<<blocks(threads, 128), 128, 0, s>>>(d, lk, out, as_grad); break;
+    case 4: k_force<T, W, B, 4><<<blocks(threads, 128), 128, 0, s>>>(d, lk, out, as_grad); break;
+    default: k_force<T, W, B, 8><<<blocks(threads, 128), 128, 0, s>>>(d, lk, out, as_grad); break;
+    }
+}
+
+template <typename T>
+void force_t(const Dev& d, int mode, double* out, int as_grad, int tpa, cudaStream_t s)
+{
+    switch (mode) {
+    case 0: force_tpa<T, W_FULL, true>(d, L_FULL, out, as_grad, tpa, s); break;
+    case 1: k_bonded<T><<<blocks(d.N, 256), 256, 0, s>>>(d, out, as_grad); break;
+    case 2: force_tpa<T, W_FULL, false>(d, L_FULL, out, as_grad, tpa, s); break;
+    case 3: force_tpa<T, W_SHORT, false>(d, L_SHORT, out, as_grad, tpa, s); break;
+    case 4: force_tpa<T, W_LONG, false>(d, L_FULL, out, as_grad, tpa, s); break;
+    default: force_tpa<T, W_SHORT, true>(d, L_SHORT, out, as_grad, tpa, s); break;
+    }
+}
+
+}  // namespace
+
+void launch_force(const Dev& d, int mode, double* out, int as_grad, int fp64, int tpa, cudaStream_t s)
+{
+    if (fp64) force_t<double>(d, mode, out, as_grad, tpa, s);
+    else force_t<float>(d, mode, out, as_grad, tpa, s);
+}
+
+void launch_kick(const Dev& d, const double* a, double h, cudaStream_t s)
+{
+    k_kick<<<blocks(3LL * d.N, 256), 256, 0, s>>>(d, a, h);
+}
+
+void launch_kick2(const Dev& d, const double* a, double h, const double* b, double hb, cudaStream_t s)
+{
+    k_kick2<<<blocks(3LL * d.N, 256), 256, 0, s>>>(d, a, h, b, hb);
+}
+
+void launch_aoa(const Dev& d, double tau, uint32_t s_off, int do_check, int fp64, cudaStream_t s)
+{
+    if (fp64) k_aoa<double><<<blocks(d.N, 256), 256, 0, s>>>(d, tau, s_off, do_check);
+    else k_aoa<float><<<blocks(d.N, 256), 256, 0, s>>>(d, tau, s_off, do_check);
+}
+
+void launch_energy(const Dev& d, cudaStream_t s)
+{
+    k_energy<<<blocks(d.N, 128), 128, 0, s>>>(d);
+}
+
+void launch_advance(const Dev& d, long long nsteps, cudaStream_t s)
+{
+    k_advance<<<blocks(d.R, 128), 128, 0, s>>>(d, nsteps);
+}
+
+}  // namespace mdj

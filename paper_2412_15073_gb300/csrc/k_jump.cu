@@ -1,0 +1,540 @@
+// k_jump.cu -- velocity phases at fixed positions: the C' step (pair jumps on
+// the long-range electrostatics with the drift of the short-range
+// acceleration, Algorithm 4 with adaptive eps and the ring technique of
+// Sec. 3.1) and the J' step (BPS bounces on the long-range LJ part,
+// Algorithm 5 of Sec. 3.2).
+//
+// One thread per atom: each atom's proposals form its own sequential Poisson
+// thinning chain (the jumps of F_ij change v_i only, Sec. 3.1), so atoms run
+// in parallel. Between proposals the velocity drifts as v0 + t a + J, with J
+// the sum of the jumps so far; the phase ends at v0 + (tau/2) a + J.
+#include "engine.h"
+
+namespace mdj {
+
+namespace {
+
+__device__ __forceinline__ double mimg(double t, const RepParams& P)
+{
+    return t - P.L * rint(t * P.invL);
+}
+
+// displacement x_i - x_j of a list entry, in the arithmetic type
+template <typename T> struct JD;
+template <> struct JD<float> {
+    __device__ static void get(const Dev& d, const RepParams& P, int i, const uint4& pi, int j,
+                               float& dx, float& dy, float& dz)
+    {
+        sdisp(pi, d.pos[j], P.sclf, dx, dy, dz);
+    }
+};
+template <> struct JD<double> {
+    __device__ static void get(const Dev& d, const RepParams& P, int i, const uint4&, int j,
+                               double& dx, double& dy, double& dz)
+    {
+        dx = mimg(d.x[3 * i] - d.x[3 * j], P);
+        dy = mimg(d.x[3 * i + 1] - d.x[3 * j + 1], P);
+        dz = mimg(d.x[3 * i + 2] - d.x[3 * j + 2], P);
+    }
+};
+
+// radial derivative of (1 - chi) U per unit C q_i q_j (DSF) or of (1 - chi) U_LJ
+template <typename T>
+__device__ __forceinline__ T coul_long(const RepParams& P, T r)
+{
+    T u, du, c, dc;
+    dsf<T>(P, r, T(1) / r, u, du);
+    chi_and_slope<T>(r, T(P.sw), T(P.h), c, dc);
+    return -dc * u + (T(1) - c) * du;
+}
+
+template <typename T>
+__device__ __forceinline__ T lj_long(const RepParams& P, const LJPair& l, T r)
+{
+    T u, du, c, dc;
+    ljsf<T>(P, l, r, T(1) / r, u, du);
+    chi_and_slope<T>(r, T(P.sw), T(P.h), c, dc);
+    return -dc * u + (T(1) - c) * du;
+}
+
+__device__ void log_event(const Dev& d, long long s0, int half, int tag, int rep, int atom, long long k, int J)
+{
+    if (d.ev_cap <= 0) return;
+    const unsigned long long idx = atomicAdd(d.ev_n, 1ull);
+    if ((long long)idx >= d.ev_cap) return;
+    long long* e = d.ev + 6 * idx;
+    e[0] = s0; e[1] = half; e[2] = tag | (rep << 8); e[3] = atom; e[4] = k; e[5] = J;
+}
+
+struct Tally {
+    unsigned int cprop = 0, cacc = 0, jprop = 0, jacc = 0, satt = 0, guard = 0;
+};
+
+// acceptance probability of a C' proposal in FP64 from the FP64 positions
+// (mixed mode only, when U is within 2e-6 of the FP32 value)
+__device__ __noinline__ double cprime_p64(const Dev& d, const RepParams& P, int i, int J, bool ringM,
+                             const double v0[3], const double a[3], double tprev, double t,
+                             const float jac[3], double aa, double tau2)
+{
+    double vp[3], vt[3];
+    for (int c = 0; c < 3; ++c) {
+        vp[c] = v0[c] + tprev * a[c] + double(jac[c]);
+        vt[c] = v0[c] + t * a[c] + double(jac[c]);
+    }
+    const double s = tau2 - tprev;
+    const double vv = vp[0] * vp[0] + vp[1] * vp[1] + vp[2] * vp[2];
+    const double va = vp[0] * a[0] + vp[1] * a[1] + vp[2] * a[2];
+    const double B = sqrt(vv + s * s * aa + 2.0 * s * fmax(va, 0.0));
+    const double mt = d.mt[i], beta = P.beta, eps0 = P.eps0;
+    const double LY = ringM ? d.LM[i] : d.LL[i];
+    double dx = mimg(d.x[3 * i] - d.x[3 * J], P), dy = mimg(d.x[3 * i + 1] - d.x[3 * J + 1], P),
+           dz = mimg(d.x[3 * i + 2] - d.x[3 * J + 2], P);
+    const double r = sqrt(dx * dx + dy * dy + dz * dz);
+    const bool inside = ringM ? (r >= P.sw && r < P.rM) : (r >= P.rM && r < P.R);
+    if (!inside) return 0.0;
+    const double f = COULOMB * d.q[i] * d.q[J] * coul_long<double>(P, r) / r;
+    const double gx = f * dx, gy = f * dy, gz = f * dz;
+    const double gn = sqrt(gx * gx + gy * gy + gz * gz);
+    if (!(gn > 0.0)) return 0.0;
+    const double vg = vt[0] * gx + vt[1] * gy + vt[2] * gz;
+    if (P.eps_mode == 1) {
+        const double LamY = beta * LY * B + sqrt(beta / mt) / (eps0 * sqrt(2.0 * PI));
+        const double eta = eps0 * sqrt(beta * mt) * vg;
+        return sqrt(beta / mt) * theta<double>(eta) / eps0 / LamY;
+    }
+    const double eta = eps0 * sqrt(beta * mt) * vg / gn;
+    return gn * theta<double>(eta) / (LY * (eps0 * sqrt(beta * mt) * B + 1.0 / sqrt(2.0 * PI)));
+}
+
+// C' for atom i over tau2 (Algorithm 4, adaptive or constant eps, two rings)
+template <typename T>
+__device__ void cprime(const Dev& d, const RepParams& P, int i, int il, double v[3], const double a[3],
+                       double tau2, uint32_t s0, int half, Tally& tl, uint32_t& err)
+{
+    const int NM = min(d.lcnt[L_RM][i], d.lcap[L_RM]);
+    const int NL = min(d.lcnt[L_RL][i], d.lcap[L_RL]);
+    if (NM + NL == 0) {
+        for (int c = 0; c < 3; ++c) v[c] += tau2 * a[c];
+        return;
+    }
+    const uint32_t* rowM = d.list[L_RM] + (size_t)i * d.lcap[L_RM];
+    const uint32_t* rowL = d.list[L_RL] + (size_t)i * d.lcap[L_RL];
+    const T beta = T(P.beta), eps0 = T(P.eps0);
+    const double mt64 = d.mt[i];
+    const T mt = T(mt64);
+    const T sbm = d_sqrt(beta * mt), sbom = d_sqrt(beta / mt);
+    const T LM = T(d.LM[i]), LL = T(d.LL[i]);
+    const T qiC = T(COULOMB * d.q[i]);
+    const bool adaptive = P.eps_mode == 1;
+    const T c0 = adaptive ? sbom / (eps0 * T(2.5066282746310002)) : sbom / (T(2.5066282746310002) * eps0);
+    const T ax = T(a[0]), ay = T(a[1]), az = T(a[2]);
+    const T aa = ax * ax + ay * ay + az * az;
+    const double aa64 = a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
+    const T T2 = T(tau2);
+    const T vx0 = T(v[0]), vy0 = T(v[1]), vz0 = T(v[2]);
+    const uint4 pi = sizeof(T) == 4 ? d.pos[i] : make_uint4(0, 0, 0, 0);
+    T t = T(0);
+    T jx = T(0), jy = T(0), jz = T(0);
+    // velocity at time t: v0 + t a + J (the telescoped drift of Algorithm 4)
+    T vx = vx0, vy = vy0, vz = vz0;
+    uint32_t k = 0;
+    for (;;) {
+        const T s = T2 - t;
+        const T vv = vx * vx + vy * vy + vz * vz;
+        const T va = vx * ax + vy * ay + vz * az;
+        const T B = d_sqrt(vv + s * s * aa + T(2) * s * (va > T(0) ? va : T(0)));
+        T LamM, LamL;
+        if (adaptive) { LamM = beta * LM * B + c0; LamL = beta * LL * B + c0; }
+        else { LamM = LM * (beta * B + c0); LamL = LL * (beta * B + c0); }
+        const T wM = T(NM) * LamM, wL = T(NL) * LamL;
+        const T Lam = wM + wL;
+        const U4 u = draw(P, uint32_t(il), s0, TAG_C, half, 0, k);
+        const T Tn = -d_log(unif<T>(u.x)) / Lam;
+        if (!(Lam > T(0)) || t + Tn > T2) break;
+        const T tprev = t;
+        t += Tn;
+        vx = T(v[0]) + t * ax + jx;
+        vy = T(v[1]) + t * ay + jy;
+        vz = T(v[2]) + t * az + jz;
+        if (sizeof(T) == 8) {   // FP64: the same sums as the definition, without rounding to float
+            vx = T(v[0] + double(t) * a[0] + double(jx));
+            vy = T(v[1] + double(t) * a[1] + double(jy));
+            vz = T(v[2] + double(t) * a[2] + double(jz));
+        }
+        tl.cprop++;
+        const bool ringM = unif<T>(u.y) * Lam < wM;
+        const int J = int(ringM ? rowM[__umulhi(u.z, uint32_t(NM))] : rowL[__umulhi(u.z, uint32_t(NL))]);
+        T dx, dy, dz;
+        JD<T>::get(d, P, i, pi, J, dx, dy, dz);
+        const T r = d_sqrt(dx * dx + dy * dy + dz * dz);
+        const bool inside = ringM ? (r >= T(P.sw) && r < T(P.rM)) : (r >= T(P.rM) && r < T(P.R));
+        if (inside) {
+            const T f = qiC * T(d.q[J]) * coul_long<T>(P, r) / r;
+            const T gx = f * dx, gy = f * dy, gz = f * dz;
+            const T gn = d_sqrt(gx * gx + gy * gy + gz * gz);
+            if (gn > T(0)) {
+                const T vg = vx * gx + vy * gy + vz * gz;
+                const T LamY = ringM ? LamM : LamL;
+                T eps, eta, p;
+                if (adaptive) {
+                    eps = eps0 * gn;
+                    eta = eps0 * sbm * vg;
+                    p = sbom * theta<T>(eta) / eps0 / LamY;
+                } else {
+                    const T LY = ringM ? LM : LL;
+                    eps = eps0;
+                    eta = eps0 * sbm * vg / gn;
+                    p = gn * theta<T>(eta) / (LY * (eps0 * sbm * B + T(0.3989422804014327)));
+                }
+                bool acc;
+                if (sizeof(T) == 4 && fabs(double(unif<T>(u.w)) - double(p)) < 2e-6) {
+                    const float jac[3] = {float(jx), float(jy), float(jz)};
+                    const double p64 = cprime_p64(d, P, i, J, ringM, v, a, double(tprev), double(t), jac,
+                                                  aa64, tau2);
+                    acc = unif<double>(u.w) <= p64;
+                    if (p64 > 1.0) err |= F_BOUND;
+                    tl.guard++;
+                } else {
+                    acc = unif<T>(u.w) <= p;
+                    if (p > T(1)) err |= F_BOUND;
+                }
+                if (acc) {
+                    // G~ by rejection, streams (S, half, attempt, k)
+                    T G = T(0);
+                    int att = 0;
+                    bool ok = false;
+                    for (; att < SAMPLER_CAP && !ok; ++att) {
+                        const U4 us = draw(P, uint32_t(il), s0, TAG_S, half, uint32_t(att), k);
+                        ok = gtilde_attempt<T>(eta, us, G);
+                    }
+                    tl.satt += att;
+                    if (!ok) { err |= F_LIMIT; G = T(0); }
+                    const T coef = T(2) * eps / (sbm * (T(1) + eps * eps)) * (eta + G) / gn;
+                    jx -= coef * gx; jy -= coef * gy; jz -= coef * gz;
+                    vx -= coef * gx; vy -= coef * gy; vz -= coef * gz;
+                    tl.cacc++;
+                    log_event(d, (long long)s0, half, int(TAG_C), d.rep[i], il, k, J - P.atom_off);
+                }
+            }
+        }
+        ++k;
+        if (k >= uint32_t(KMAX)) { err |= F_LIMIT; break; }
+    }
+    for (int c = 0; c < 3; ++c) v[c] += tau2 * a[c];
+    v[0] += double(jx); v[1] += double(jy); v[2] += double(jz);
+}
+
+// J' for atom i over tau2 (Algorithm 5: Poisson(N beta |v| L tau/2)
+// proposals as exponential arrivals, uniform partner, reflection)
+template <typename T>
+__device__ __noinline__ void jprime(const Dev& d, const RepParams& P, int i, int il, double v[3], double tau2,
+                       uint32_t s0, int half, Tally& tl, uint32_t& err)
+{
+    const int N = min(d.lcnt[L_LJ][i], d.lcap[L_LJ]);
+    if (N == 0) return;
+    const double V64 = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    const double Li64 = d.LLJ[i];
+    if (!(V64 > 0.0) || !(Li64 > 0.0)) return;
+    const uint32_t* row = d.list[L_LJ] + (size_t)i * d.lcap[L_LJ];
+    const T V = T(V64), Li = T(Li64);
+    const T Lam = T(N) * T(P.beta) * V * Li;
+    const T T2 = T(tau2);
+    const uint4 pi = sizeof(T) == 4 ? d.pos[i] : make_uint4(0, 0, 0, 0);
+    const int ti = d.type[i];
+    T t = T(0);
+    uint32_t k = 0;
+    for (;;) {
+        const U4 u = draw(P, uint32_t(il), s0, TAG_J, half, 0, k);
+        const T Tn = -d_log(unif<T>(u.x)) / Lam;
+        if (t + Tn > T2) break;
+        t += Tn;
+        tl.jprop++;
+        const int J = int(row[__umulhi(u.z, uint32_t(N))]);
+        T dx, dy, dz;
+        JD<T>::get(d, P, i, pi, J, dx, dy, dz);
+        const T r = d_sqrt(dx * dx + dy * dy + dz * dz);
+        if (r >= T(P.sw) && r < T(P.R)) {
+            const T f = lj_long<T>(P, P.lj[ti * MAX_TYPES + d.type[J]], r) / r;
+            const double gx = double(f * dx), gy = double(f * dy), gz = double(f * dz);
+            const double vg = v[0] * gx + v[1] * gy + v[2] * gz;
+            const double p = (vg > 0.0 ? vg : 0.0) / (V64 * Li64);
+            if (p > 1.0) err |= F_BOUND;
+            if (unif<double>(u.w) <= p) {
+                const double gg = gx * gx + gy * gy + gz * gz;
+                const double c = 2.0 * vg / gg;
+                v[0] -= c * gx; v[1] -= c * gy; v[2] -= c * gz;
+                tl.jacc++;
+                log_event(d, (long long)s0, half, int(TAG_J), d.rep[i], il, k, J - P.atom_off);
+            }
+        }
+        ++k;
+        if (k >= uint32_t(KMAX)) { err |= F_LIMIT; break; }
+    }
+}
+
+__device__ __forceinline__ void warp_add(unsigned long long* dst, unsigned int v32, bool uniform, int lane)
+{
+    unsigned long long v = v32;
+    if (uniform) {
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0 && v) atomicAdd(dst, v);
+    } else if (v) {
+        atomicAdd(dst, v);
+    }
+}
+
+
+// ---- mixed-mode fast path ----------------------------------------------------------
+// G~ by rejection for one accepted proposal (streams (S, half, attempt, k))
+__device__ __noinline__ float sample_gtilde_f(const RepParams& P, uint32_t il, uint32_t s0, int half,
+                                               uint32_t k, float eta, int* att_out, bool* ok_out)
+{
+    float G = 0.f;
+    bool ok = false;
+    int att = 0;
+    for (; att < SAMPLER_CAP && !ok; ++att) {
+        const U4 us = draw(P, il, s0, TAG_S, half, uint32_t(att), k);
+        ok = gtilde_attempt<float>(eta, us, G);
+    }
+    *att_out = att;
+    *ok_out = ok;
+    return ok ? G : 0.f;
+}
+
+// C' for atom i in FP32 (Algorithm 4, adaptive or constant eps, two rings).
+// The Philox block of proposal k+1 is computed while the partner of proposal
+// k is being fetched.
+__device__ __forceinline__ void cprime_f(const Dev& d, const RepParams& P, int i, int il, float3& jv,
+                                         const float3 v0, const float3 a, float T2, uint32_t s0, int half,
+                                         Tally& tl, uint32_t& err)
+{
+    const int NM = min(d.lcnt[L_RM][i], d.lcap[L_RM]);
+    const int NL = min(d.lcnt[L_RL][i], d.lcap[L_RL]);
+    if (NM + NL == 0) return;
+    const uint32_t* rowM = d.list[L_RM] + (size_t)i * d.lcap[L_RM];
+    const uint32_t* rowL = d.list[L_RL] + (size_t)i * d.lcap[L_RL];
+    const float beta = float(P.beta), eps0 = float(P.eps0);
+    const float mt = float(d.mt[i]);
+    const float sbm = sqrtf(beta * mt), sbom = sqrtf(beta / mt);
+    const float LM = d.LMf[i], LL = d.LLf[i];
+    const uint4 pi = d.pos[i];
+    const float qiC = float(COULOMB) * __uint_as_float(pi.w);
+    const bool adaptive = P.eps_mode == 1;
+    const float c0 = sbom / (eps0 * 2.5066282746310002f);
+    const float aa = a.x * a.x + a.y * a.y + a.z * a.z;
+    const float fNM = float(NM), fNL = float(NL);
+    const float sw = float(P.sw), rM = float(P.rM), R = float(P.R), sc = P.sclf;
+    float t = 0.f;
+    float vx = v0.x + jv.x, vy = v0.y + jv.y, vz = v0.z + jv.z;
+    uint32_t k = 0;
+    U4 u = draw(P, uint32_t(il), s0, TAG_C, half, 0, 0);
+    for (;;) {
+        const float s = T2 - t;
+        const float vv = vx * vx + vy * vy + vz * vz;
+        const float va = vx * a.x + vy * a.y + vz * a.z;
+        const float B = sqrtf(vv + s * s * aa + 2.f * s * fmaxf(va, 0.f));
+        float LamM, LamL;
+        if (adaptive) { LamM = fmaf(beta * LM, B, c0); LamL = fmaf(beta * LL, B, c0); }
+        else { LamM = LM * fmaf(beta, B, c0); LamL = LL * fmaf(beta, B, c0); }
+        const float wM = fNM * LamM;
+        const float Lam = wM + fNL * LamL;
+        const float Tn = -__logf(unif<float>(u.x)) / Lam;
+        if (!(Lam > 0.f) || t + Tn > T2) break;
+        const float tprev = t;
+        t += Tn;
+        vx = fmaf(t, a.x, v0.x) + jv.x;
+        vy = fmaf(t, a.y, v0.y) + jv.y;
+        vz = fmaf(t, a.z, v0.z) + jv.z;
+        tl.cprop++;
+        const bool ringM = unif<float>(u.y) * Lam < wM;
+        const int J = int(ringM ? __ldg(rowM + __umulhi(u.z, uint32_t(NM))) : __ldg(rowL + __umulhi(u.z, uint32_t(NL))));
+        const uint4 pj = __ldg(d.pos + J);
+        const uint32_t uacc = u.w;
+        const uint32_t kk = k;
+        ++k;
+        u = draw(P, uint32_t(il), s0, TAG_C, half, 0, k);        // next proposal, overlaps the gathers
+        float dx, dy, dz;
+        sdisp(pi, pj, sc, dx, dy, dz);
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        const float r = sqrtf(r2);
+        const bool inside = ringM ? (r >= sw && r < rM) : (r >= rM && r < R);
+        if (inside) {
+            const float f = qiC * __uint_as_float(pj.w) * coul_long<float>(P, r) / r;
+            const float gx = f * dx, gy = f * dy, gz = f * dz;
+            const float gn = sqrtf(gx * gx + gy * gy + gz * gz);
+            if (gn > 0.f) {
+                const float vg = vx * gx + vy * gy + vz * gz;
+                const float LamY = ringM ? LamM : LamL;
+                float eps, eta, p;
+                if (adaptive) {
+                    eps = eps0 * gn;
+                    eta = eps0 * sbm * vg;
+                    p = sbom * theta<float>(eta) / eps0 / LamY;
+                } else {
+                    eps = eps0;
+                    eta = eps0 * sbm * vg / gn;
+                    p = gn * theta<float>(eta) / ((ringM ? LM : LL) * (eps0 * sbm * B + 0.3989422804014327f));
+                }
+                bool acc;
+                const float U = unif<float>(uacc);
+                if (fabsf(U - p) < 2e-6f) {
+                    const double v0d[3] = {d.v[3 * i], d.v[3 * i + 1], d.v[3 * i + 2]};
+                    const double ad[3] = {double(a.x), double(a.y), double(a.z)};
+                    const float jac[3] = {jv.x, jv.y, jv.z};
+                    const double p64 = cprime_p64(d, P, i, J, ringM, v0d, ad, double(tprev), double(t), jac,
+                                                  double(aa), double(T2));
+                    acc = unif<double>(uacc) <= p64;
+                    if (p64 > 1.0) err |= F_BOUND;
+                    tl.guard++;
+                } else {
+                    acc = U <= p;
+                    if (p > 1.f) err |= F_BOUND;
+                }
+                if (acc) {
+                    int att;
+                    bool ok;
+                    const float G = sample_gtilde_f(P, uint32_t(il), s0, half, kk, eta, &att, &ok);
+                    tl.satt += att;
+                    if (!ok) err |= F_LIMIT;
+                    const float coef = 2.f * eps / (sbm * (1.f + eps * eps)) * (eta + G) / gn;
+                    jv.x -= coef * gx; jv.y -= coef * gy; jv.z -= coef * gz;
+                    vx -= coef * gx; vy -= coef * gy; vz -= coef * gz;
+                    tl.cacc++;
+                    log_event(d, (long long)s0, half, int(TAG_C), d.rep[i], il, kk, J - P.atom_off);
+                }
+            }
+        }
+        if (k >= uint32_t(KMAX)) { err |= F_LIMIT; break; }
+    }
+}
+
+// mixed-mode velocity phase; threads visit atoms in the order vorder (atoms
+// grouped by expected jump rate so that the lanes of a warp do similar work)
+template <int MINB>
+__global__ void __launch_bounds__(128, MINB) k_vphase_f(Dev d, const double* a, double tau2, uint32_t s_off, int s_abs,
+                                                        int half, int order, int doC, int doJ)
+{
+    const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = t0 < d.N;
+    const int i = d.vorder[live ? t0 : d.N - 1];
+    const int r = d.rep[i];
+    const RepParams& P = d.P[r];
+    Tally tl;
+    uint32_t err = 0;
+    if (live) {
+        const uint32_t s0 = (s_abs ? 0u : uint32_t(d.step_base[r])) + s_off;
+        const int il = i - P.atom_off;
+        const bool c_on = doC && P.rings_on;
+        const bool j_on = doJ && P.lj_on;
+        for (int step = 0; step < 2; ++step) {
+            const bool isC = (order == 0) ? step == 0 : step == 1;
+            if (isC) {
+                if (!doC) continue;
+                float3 jv = make_float3(0.f, 0.f, 0.f);
+                if (c_on) {
+                    const float3 v0 = make_float3(float(d.v[3 * i]), float(d.v[3 * i + 1]), float(d.v[3 * i + 2]));
+                    const float3 af = a ? make_float3(float(a[3 * i]), float(a[3 * i + 1]), float(a[3 * i + 2]))
+                                        : make_float3(0.f, 0.f, 0.f);
+                    cprime_f(d, P, i, il, jv, v0, af, float(tau2), s0, half, tl, err);
+                }
+                // FP64 end of the phase: v0 + (tau/2) a + sum of the jumps
+                for (int c = 0; c < 3; ++c) {
+                    const double ac = a ? a[3 * i + c] : 0.0;
+                    d.v[3 * i + c] += tau2 * ac + double(c == 0 ? jv.x : (c == 1 ? jv.y : jv.z));
+                }
+            } else if (j_on) {
+                double v[3] = {d.v[3 * i], d.v[3 * i + 1], d.v[3 * i + 2]};
+                jprime<float>(d, P, i, il, v, tau2, s0, half, tl, err);
+                d.v[3 * i] = v[0]; d.v[3 * i + 1] = v[1]; d.v[3 * i + 2] = v[2];
+            }
+        }
+        if (err) atomicOr(&d.err[r], err);
+    }
+    const int lane = threadIdx.x & 31;
+    const int r0 = __shfl_sync(0xffffffffu, r, 0);
+    const bool uniform = __all_sync(0xffffffffu, r == r0);
+    unsigned long long* C = d.cnt + (size_t)r * NCOUNT;
+    warp_add(&C[C_CPROP], tl.cprop, uniform, lane);
+    warp_add(&C[C_CACC], tl.cacc, uniform, lane);
+    warp_add(&C[C_JPROP], tl.jprop, uniform, lane);
+    warp_add(&C[C_JACC], tl.jacc, uniform, lane);
+    warp_add(&C[C_SATT], tl.satt, uniform, lane);
+    warp_add(&C[C_GUARD], tl.guard, uniform, lane);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_vphase(Dev d, const double* a, double tau2, uint32_t s_off, int s_abs,
+                                                int half, int order, int doC, int doJ)
+{
+    const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = i0 < d.N;
+    const int i = live ? i0 : d.N - 1;
+    const int r = d.rep[i];
+    const RepParams& P = d.P[r];
+    Tally tl;
+    uint32_t err = 0;
+    if (live) {
+        const uint32_t s0 = (s_abs ? 0u : uint32_t(d.step_base[r])) + s_off;
+        const int il = i - P.atom_off;
+        double v[3] = {d.v[3 * i], d.v[3 * i + 1], d.v[3 * i + 2]};
+        double acc[3] = {0, 0, 0};
+        if (a) { acc[0] = a[3 * i]; acc[1] = a[3 * i + 1]; acc[2] = a[3 * i + 2]; }
+        const bool c_on = doC && P.rings_on;
+        const bool j_on = doJ && P.lj_on;
+        for (int step = 0; step < 2; ++step) {
+            const bool isC = (order == 0) ? step == 0 : step == 1;
+            if (isC) {
+                if (doC) {
+                    if (c_on) cprime<T>(d, P, i, il, v, acc, tau2, s0, half, tl, err);
+                    else for (int c = 0; c < 3; ++c) v[c] += tau2 * acc[c];
+                }
+            } else if (j_on) {
+                jprime<T>(d, P, i, il, v, tau2, s0, half, tl, err);
+            }
+        }
+        d.v[3 * i] = v[0]; d.v[3 * i + 1] = v[1]; d.v[3 * i + 2] = v[2];
+        if (err) atomicOr(&d.err[r], err);
+    }
+    const int lane = threadIdx.x & 31;
+    const int r0 = __shfl_sync(0xffffffffu, r, 0);
+    const bool uniform = __all_sync(0xffffffffu, r == r0);
+    unsigned long long* C = d.cnt + (size_t)r * NCOUNT;
+    warp_add(&C[C_CPROP], tl.cprop, uniform, lane);
+    warp_add(&C[C_CACC], tl.cacc, uniform, lane);
+    warp_add(&C[C_JPROP], tl.jprop, uniform, lane);
+    warp_add(&C[C_JACC], tl.jacc, uniform, lane);
+    warp_add(&C[C_SATT], tl.satt, uniform, lane);
+    warp_add(&C[C_GUARD], tl.guard, uniform, lane);
+}
+
+}  // namespace
+
+static void vphase_any(const Dev& d, const double* a, double tau2, uint32_t s, int s_abs, int half, int order,
+                       int doC, int doJ, int fp64, int variant, cudaStream_t st)
+{
+    const int nb = (d.N + 127) / 128;
+    if (fp64) {
+        k_vphase<double><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, order, doC, doJ);
+        return;
+    }
+    switch (variant) {
+    case 1: k_vphase_f<4><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, order, doC, doJ); break;
+    case 2: k_vphase_f<5><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, order, doC, doJ); break;
+    case 3: k_vphase_f<6><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, order, doC, doJ); break;
+    default: k_vphase_f<1><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, order, doC, doJ); break;
+    }
+}
+
+void launch_vphase(const Dev& d, const double* a, double tau2, uint32_t s_off, int half, int order,
+                   int doC, int doJ, int fp64, int variant, cudaStream_t s)
+{
+    vphase_any(d, a, tau2, s_off, 0, half, order, doC, doJ, fp64, variant, s);
+}
+
+void launch_vphase_abs(const Dev& d, const double* a, double tau2, uint32_t s0, int half, int order,
+                       int doC, int doJ, int fp64, int variant, cudaStream_t s)
+{
+    vphase_any(d, a, tau2, s0, 1, half, order, doC, doJ, fp64, variant, s);
+}
+
+}  // namespace mdj

@@ -1,0 +1,1287 @@
+// md_api.cu -- host engine and C ABI of libmdjump.so (declared in include/md.h).
+//
+// The context keeps a host copy of every replica's topology and parameters,
+// lays all replicas out end to end in device memory (one launch advances all
+// of them), computes the per-atom rate bounds of the jump rings on the host,
+// and drives the integrators of Sec. 2.3 as sequences of kernel launches on
+// one CUDA stream. Device memory is allocated stream-ordered on that stream.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/md.h"
+#include "engine.h"
+
+using namespace mdj;
+
+namespace {
+
+// ---- host pair terms for the rate bounds (FP64) --------------------------------
+struct HostPair {
+    double R, sw, h, alpha;
+    double chi(double r) const
+    {
+        if (r <= sw) return 1.0;
+        if (r >= sw + h) return 0.0;
+        const double s = (r - sw) / h;
+        return 1.0 - s * s * s * (10.0 - 15.0 * s + 6.0 * s * s);
+    }
+    double dchi(double r) const
+    {
+        if (r <= sw || r >= sw + h) return 0.0;
+        const double s = (r - sw) / h;
+        return -30.0 * s * s * (1.0 - s) * (1.0 - s) / h;
+    }
+    double fR() const
+    {
+        return std::erfc(alpha * R) / (R * R) + 2.0 * alpha / std::sqrt(PI) * std::exp(-alpha * alpha * R * R) / R;
+    }
+    double u_dsf(double r) const
+    {
+        if (r >= R) return 0.0;
+        return std::erfc(alpha * r) / r - std::erfc(alpha * R) / R + fR() * (r - R);
+    }
+    double du_dsf(double r) const
+    {
+        if (r >= R) return 0.0;
+        return -(std::erfc(alpha * r) / (r * r) + 2.0 * alpha / std::sqrt(PI) * std::exp(-alpha * alpha * r * r) / r) + fR();
+    }
+    static double lj(double c12, double c6, double r) { return c12 / std::pow(r, 12) - c6 / std::pow(r, 6); }
+    static double dlj(double c12, double c6, double r) { return -12.0 * c12 / std::pow(r, 13) + 6.0 * c6 / std::pow(r, 7); }
+    double u_ljsf(double c12, double c6, double r) const
+    {
+        if (r >= R) return 0.0;
+        return lj(c12, c6, r) - lj(c12, c6, R) - (r - R) * dlj(c12, c6, R);
+    }
+    double du_ljsf(double c12, double c6, double r) const
+    {
+        if (r >= R) return 0.0;
+        return dlj(c12, c6, r) - dlj(c12, c6, R);
+    }
+};
+
+constexpr int NGRID = 20001;
+
+// max of |d/dr (1 - chi) U| on [lo, hi] sampled at NGRID points
+template <class F> double grid_max(F f, double lo, double hi)
+{
+    if (!(hi > lo)) return 0.0;
+    double m = 0.0;
+    for (int k = 0; k < NGRID; ++k) {
+        const double r = lo + (hi - lo) * (double)k / (double)(NGRID - 1);
+        const double v = std::fabs(f(r));
+        if (v > m) m = v;
+    }
+    return m;
+}
+
+// bound rounded up to 9 significant bits after a 1e-4 safety factor
+double round_up_bound(double x)
+{
+    if (!(x > 0.0)) return 0.0;
+    int e;
+    double f = std::frexp(x * (1.0 + 1e-4), &e);
+    f = std::ceil(f * 512.0) / 512.0;
+    return std::ldexp(f, e);
+}
+
+struct RepHost {
+    bool set = false;
+    bool fresh = true;      // state comes from md_set_system, not from the device
+    int n = 0;
+    double box = 0;
+    std::vector<double> x, v, xb, xo, mass, charge, lj_eps, lj_sig, bond_k, bond_r0, ang_k, ang_t0;
+    std::vector<int> img, type, bonds, angles, excl;
+    int ntypes = 0;
+    md_system sys{};
+    long long step = 0;
+    std::vector<unsigned long long> cnt;
+    uint32_t err = 0;
+};
+
+}  // namespace
+
+struct md_ctx {
+    md_config cfg{};
+    cudaStream_t s = nullptr;
+    std::string msg;
+    std::vector<RepHost> reps;
+    bool dirty = true;
+    bool on_device = false;
+    int kinds = 0;          // inner list kinds built so far
+    int fp64 = 0;
+    int tpa_cfg = 0;
+    int tpa[6] = {0, 0, 0, 0, 0, 0};
+    int vvar = -1;          // chosen variant of the mixed-mode velocity-phase kernel
+    Dev d{};
+    std::vector<void*> bufs;
+    std::vector<RepParams> hp;
+    std::vector<int> rep_atom_off;
+    // launch accounting and optional per-class timing
+    long long nlaunch[6] = {0, 0, 0, 0, 0, 0};
+    bool prof = false;
+    double prof_ms[6] = {0, 0, 0, 0, 0, 0};
+    long long prof_groups[6] = {0, 0, 0, 0, 0, 0};
+    std::vector<cudaEvent_t> ev_pool;
+    struct Pend { int cls; cudaEvent_t a, b; };
+    std::vector<Pend> pend;
+    // pinned staging
+    double* h_stepc = nullptr;
+    uint32_t* h_err = nullptr;
+    void* stage = nullptr;
+    size_t stage_bytes = 0;
+};
+
+static std::string g_init_msg = "no error";
+
+#define FAIL(code, ...)                                                   \
+    do {                                                                  \
+        char _b[512];                                                     \
+        std::snprintf(_b, sizeof _b, __VA_ARGS__);                        \
+        ctx->msg = _b;                                                    \
+        return code;                                                      \
+    } while (0)
+
+#define CK(call)                                                          \
+    do {                                                                  \
+        cudaError_t _e = (call);                                          \
+        if (_e != cudaSuccess) FAIL(MD_ECUDA, "%s: %s", #call, cudaGetErrorString(_e)); \
+    } while (0)
+
+namespace {
+
+template <typename T> int dalloc(md_ctx* ctx, T** p, size_t count)
+{
+    const size_t bytes = (count ? count : 1) * sizeof(T);
+    cudaError_t e = cudaMallocAsync((void**)p, bytes, ctx->s);
+    if (e != cudaSuccess) {
+        ctx->msg = std::string("device allocation failed: ") + cudaGetErrorString(e);
+        return MD_ENOMEM;
+    }
+    ctx->bufs.push_back((void*)*p);
+    return MD_OK;
+}
+
+template <typename T> int upload(md_ctx* ctx, T* dst, const T* src, size_t count)
+{
+    if (!count) return MD_OK;
+    cudaError_t e = cudaMemcpyAsync(dst, src, count * sizeof(T), cudaMemcpyHostToDevice, ctx->s);
+    if (e != cudaSuccess) {
+        ctx->msg = std::string("upload failed: ") + cudaGetErrorString(e);
+        return MD_ECUDA;
+    }
+    return MD_OK;
+}
+
+void free_device(md_ctx* ctx)
+{
+    for (void* p : ctx->bufs) cudaFreeAsync(p, ctx->s);
+    ctx->bufs.clear();
+    ctx->on_device = false;
+}
+
+int lists_needed(int family)
+{
+    // 0 BAOAB / BAOAB-RESPA, 1 BAOAB-RESPA1, 2 JUMP family
+    if (family == 0) return 1 << L_FULL;
+    if (family == 1) return (1 << L_FULL) | (1 << L_SHORT);
+    return (1 << L_SHORT) | (1 << L_RM) | (1 << L_RL) | (1 << L_LJ);
+}
+
+int mode_list(int mode)
+{
+    if (mode == 1) return 0;
+    if (mode == 3 || mode == 5) return 1 << L_SHORT;
+    return 1 << L_FULL;
+}
+
+// estimated per-atom capacity of a list with shell [lo, hi] at density rho
+int cap_of(double rho, double lo, double hi)
+{
+    lo = std::max(lo, 0.0);
+    const double vol = 4.0 / 3.0 * PI * (hi * hi * hi - lo * lo * lo);
+    int c = int(vol * rho * 1.5) + 64;
+    return (c + 31) / 32 * 32;
+}
+
+RepParams make_params(const md_ctx* ctx, const RepHost& h, int r, int atom_off, int cell_off)
+{
+    const md_system& s = h.sys;
+    RepParams P;
+    std::memset(&P, 0, sizeof P);
+    P.L = h.box; P.invL = 1.0 / h.box;
+    P.atom_off = atom_off; P.n = h.n;
+    const double skin_o = std::max(s.skin, s.skin_outer);
+    P.nc = std::max(1, int(std::floor(h.box / (s.r_cut + skin_o))));
+    P.cs = h.box / P.nc;
+    P.cell_off = cell_off;
+    P.scl = h.box / 4294967296.0;
+    P.inv_scl = 4294967296.0 / h.box;
+    P.sclf = float(P.scl);
+    P.R = s.r_cut; P.rc = s.r_split; P.h = s.h_switch; P.sw = s.r_split - s.h_switch;
+    P.one_ring = !(s.r_mid > P.sw && s.r_mid < P.R);
+    P.rM = P.one_ring ? P.sw : s.r_mid;
+    double qmax = 0;
+    for (double q : h.charge) qmax = std::max(qmax, std::fabs(q));
+    bool any_lj = false;
+    for (double e : h.lj_eps) any_lj |= e > 0.0;
+    P.rings_on = (P.sw < P.R) && qmax > 0.0;
+    P.lj_on = (P.sw < P.R) && any_lj;
+    P.eps_mode = s.eps_mode;
+    P.skin = s.skin; P.skin_o = skin_o;
+    HostPair hpair{s.r_cut, P.sw, s.h_switch, s.dsf_alpha};
+    P.alpha = s.dsf_alpha;
+    P.eR = std::erfc(s.dsf_alpha * s.r_cut) / s.r_cut;
+    P.fR = hpair.fR();
+    P.kexp = 2.0 * s.dsf_alpha / std::sqrt(PI);
+    P.alphaf = float(P.alpha); P.eRf = float(P.eR); P.fRf = float(P.fR); P.kexpf = float(P.kexp);
+    P.beta = 1.0 / (KB * s.temperature);
+    P.gamma = s.gamma;
+    P.eps0 = s.eps0;
+    P.seed = uint32_t(ctx->cfg.seed & 0xffffffffull);
+    P.replica = uint32_t(r);
+    P.ntypes = h.ntypes;
+    for (int a = 0; a < h.ntypes; ++a)
+        for (int b = 0; b < h.ntypes; ++b) {
+            const double e = h.lj_eps[a * h.ntypes + b], sg = h.lj_sig[a * h.ntypes + b];
+            LJPair& l = P.lj[a * MAX_TYPES + b];
+            l.c12 = 4.0 * e * std::pow(sg, 12);
+            l.c6 = 4.0 * e * std::pow(sg, 6);
+            l.uR = HostPair::lj(l.c12, l.c6, s.r_cut);
+            l.duR = HostPair::dlj(l.c12, l.c6, s.r_cut);
+            l.c12f = float(l.c12); l.c6f = float(l.c6); l.uRf = float(l.uR); l.duRf = float(l.duR);
+            l.on = e > 0.0;
+        }
+    return P;
+}
+
+// per-atom bounds of a replica: L_M, L_L (C |q_i| qmax Lhat) and L_LJ
+void make_bounds(const RepHost& h, const RepParams& P, double* LM, double* LL, double* LLJ)
+{
+    HostPair hp{P.R, P.sw, P.h, P.alpha};
+    auto coul = [&](double r) { return -hp.dchi(r) * hp.u_dsf(r) + (1.0 - hp.chi(r)) * hp.du_dsf(r); };
+    const double LhM = P.one_ring ? 0.0 : grid_max(coul, P.sw, P.rM);
+    const double LhL = grid_max(coul, P.rM, P.R);
+    double qmax = 0;
+    for (double q : h.charge) qmax = std::max(qmax, std::fabs(q));
+    const int nt = h.ntypes;
+    std::vector<double> ljhat(nt * nt, 0.0);
+    std::vector<int> present(nt, 0);
+    for (int t : h.type) present[t] = 1;
+    for (int a = 0; a < nt; ++a)
+        for (int b = 0; b < nt; ++b) {
+            const LJPair& l = P.lj[a * MAX_TYPES + b];
+            if (!l.on) continue;
+            auto f = [&](double r) {
+                return -hp.dchi(r) * hp.u_ljsf(l.c12, l.c6, r) + (1.0 - hp.chi(r)) * hp.du_ljsf(l.c12, l.c6, r);
+            };
+            ljhat[a * nt + b] = grid_max(f, P.sw, P.R);
+        }
+    for (int i = 0; i < h.n; ++i) {
+        const double cq = COULOMB * std::fabs(h.charge[i]) * qmax;
+        LM[i] = round_up_bound(cq * LhM);
+        LL[i] = round_up_bound(cq * LhL);
+        double m = 0;
+        for (int b = 0; b < nt; ++b)
+            if (present[b]) m = std::max(m, ljhat[h.type[i] * nt + b]);
+        LLJ[i] = round_up_bound(m);
+    }
+}
+
+int check_sys(md_ctx* ctx, const md_system* s)
+{
+    if (!s || s->n_atoms <= 0 || !s->x || !s->v || !s->mass || !s->charge || !s->type)
+        FAIL(MD_EINVAL, "md_set_system: missing atom arrays");
+    if (s->n_types < 1 || s->n_types > MAX_TYPES || !s->lj_eps || !s->lj_sigma)
+        FAIL(MD_EINVAL, "md_set_system: n_types must be in [1, %d] with LJ tables", MAX_TYPES);
+    if (!(s->r_cut > 0) || !(s->h_switch > 0) || !(s->r_split > s->h_switch) || !(s->skin >= 0) ||
+        !(s->dsf_alpha >= 0) || !(s->gamma >= 0) || !(s->temperature > 0) || !(s->eps0 > 0) ||
+        (s->eps_mode != 0 && s->eps_mode != 1))
+        FAIL(MD_EINVAL, "md_set_system: invalid cutoff, switch, thermostat or jump parameters");
+    const double skin_o = std::max(s->skin, s->skin_outer);
+    if (!(s->box >= 2.0 * (s->r_cut + skin_o)))
+        FAIL(MD_EINVAL, "md_set_system: box %.4f must be at least 2 (r_cut + skin_outer) = %.4f", s->box,
+             2.0 * (s->r_cut + skin_o));
+    for (int i = 0; i < s->n_atoms; ++i) {
+        if (s->type[i] < 0 || s->type[i] >= s->n_types) FAIL(MD_EINVAL, "md_set_system: atom %d has type %d", i, s->type[i]);
+        if (!(s->mass[i] > 0)) FAIL(MD_EINVAL, "md_set_system: atom %d has mass <= 0", i);
+        for (int c = 0; c < 3; ++c)
+            if (!std::isfinite(s->x[3 * i + c]) || !std::isfinite(s->v[3 * i + c]))
+                FAIL(MD_EINVAL, "md_set_system: non-finite coordinate of atom %d", i);
+    }
+    auto idx_ok = [&](const int* a, int cnt, int per) {
+        for (int k = 0; k < cnt * per; ++k)
+            if (a[k] < 0 || a[k] >= s->n_atoms) return false;
+        return true;
+    };
+    if ((s->n_bonds && (!s->bonds || !s->bond_k || !s->bond_r0 || !idx_ok(s->bonds, s->n_bonds, 2))) ||
+        (s->n_angles && (!s->angles || !s->angle_k || !s->angle_t0 || !idx_ok(s->angles, s->n_angles, 3))) ||
+        (s->n_excl && (!s->excl_pairs || !idx_ok(s->excl_pairs, s->n_excl, 2))))
+        FAIL(MD_EINVAL, "md_set_system: bonded or exclusion indices out of range");
+    return MD_OK;
+}
+
+// copy the device state of every replica back to its host record
+int download_all(md_ctx* ctx)
+{
+    if (!ctx->on_device) return MD_OK;
+    CK(cudaStreamSynchronize(ctx->s));
+    const Dev& d = ctx->d;
+    std::vector<long long> sb(d.R);
+    std::vector<unsigned long long> cnt((size_t)d.R * NCOUNT);
+    std::vector<uint32_t> err(d.R);
+    CK(cudaMemcpy(sb.data(), d.step_base, sizeof(long long) * d.R, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(cnt.data(), d.cnt, sizeof(unsigned long long) * cnt.size(), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(err.data(), d.err, sizeof(uint32_t) * d.R, cudaMemcpyDeviceToHost));
+    for (int r = 0; r < (int)ctx->reps.size(); ++r) {
+        RepHost& h = ctx->reps[r];
+        if (!h.set || h.fresh || r >= d.R) continue;
+        const size_t o = 3 * (size_t)ctx->rep_atom_off[r], n3 = 3 * (size_t)h.n;
+        CK(cudaMemcpy(h.x.data(), d.x + o, n3 * sizeof(double), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(h.v.data(), d.v + o, n3 * sizeof(double), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(h.xb.data(), d.xb + o, n3 * sizeof(double), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(h.xo.data(), d.xo + o, n3 * sizeof(double), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(h.img.data(), d.img + o, n3 * sizeof(int), cudaMemcpyDeviceToHost));
+        h.step = sb[r];
+        h.cnt.assign(cnt.begin() + (size_t)r * NCOUNT, cnt.begin() + (size_t)(r + 1) * NCOUNT);
+        h.err = err[r];
+    }
+    return MD_OK;
+}
+
+int read_max(md_ctx* ctx, const int* dev_counts, int n, int& mx)
+{
+    std::vector<int> c(n);
+    CK(cudaMemcpyAsync(c.data(), dev_counts, sizeof(int) * n, cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    mx = 0;
+    for (int v : c) mx = std::max(mx, v);
+    return MD_OK;
+}
+
+// grow list capacities that came close to or over their limit, then rebuild
+int fit_caps(md_ctx* ctx, int kinds_to_check, bool outer)
+{
+    Dev& d = ctx->d;
+    for (int round = 0; round < 4; ++round) {
+        bool grow = false;
+        int mx;
+        if (outer) {
+            int rc = read_max(ctx, d.ocnt, d.N, mx);
+            if (rc) return rc;
+            if (mx > d.ocap * 0.9) {
+                const int cap = (int(mx * 1.4) + 64 + 31) / 32 * 32;
+                uint32_t* p;
+                if ((rc = dalloc(ctx, &p, (size_t)d.N * cap))) return rc;
+                d.olist = p; d.ocap = cap;
+                grow = true;
+            }
+        }
+        for (int k = 0; k < NKIND; ++k) {
+            if (!(kinds_to_check & (1 << k))) continue;
+            int rc = read_max(ctx, d.lcnt[k], d.N, mx);
+            if (rc) return rc;
+            if (mx > d.lcap[k] * 0.9) {
+                const int cap = (int(mx * 1.4) + 64 + 31) / 32 * 32;
+                uint32_t* p;
+                if ((rc = dalloc(ctx, &p, (size_t)d.N * cap))) return rc;
+                d.list[k] = p; d.lcap[k] = cap;
+                grow = true;
+            }
+        }
+        if (!grow) return MD_OK;
+        // rebuild at the stored build positions (exact, keeps the references)
+        CK(cudaMemsetAsync(d.err, 0, sizeof(uint32_t) * d.R, ctx->s));
+        if (outer) {
+            launch_check(d, 1, 1, ctx->s);
+            launch_rebuild(d, ctx->kinds & ~kinds_to_check, 1, 1, 1, 0, ctx->s);
+        }
+        launch_late_lists(d, kinds_to_check, ctx->s);
+        CK(cudaGetLastError());
+    }
+    FAIL(MD_EOVERFLOW, "neighbour-list capacity could not be fitted");
+}
+
+int commit(md_ctx* ctx)
+{
+    if (!ctx->dirty) return MD_OK;
+    int R = 0;
+    for (int r = 0; r < (int)ctx->reps.size(); ++r)
+        if (ctx->reps[r].set) R = r + 1;
+    if (R == 0) FAIL(MD_ENOSYSTEM, "no replica has a system");
+    for (int r = 0; r < R; ++r)
+        if (!ctx->reps[r].set) FAIL(MD_ENOSYSTEM, "replica %d has no system (replicas 0..%d must be set)", r, R - 1);
+    int rc = download_all(ctx);
+    if (rc) return rc;
+    free_device(ctx);
+    // layout
+    int N = 0, cells = 0;
+    ctx->rep_atom_off.assign(R, 0);
+    ctx->hp.assign(R, RepParams{});
+    double rho = 0;
+    for (int r = 0; r < R; ++r) {
+        RepHost& h = ctx->reps[r];
+        ctx->rep_atom_off[r] = N;
+        ctx->hp[r] = make_params(ctx, h, r, N, cells);
+        const RepParams& P = ctx->hp[r];
+        cells += P.nc * P.nc * P.nc + 1;
+        N += h.n;
+        rho = std::max(rho, h.n / (h.box * h.box * h.box));
+    }
+
+    Dev& d = ctx->d;
+    d = Dev{};
+    d.N = N; d.R = R;
+    // host arrays
+    std::vector<double> x(3 * N), v(3 * N), xb(3 * N), xo(3 * N), mt(N), isqmt(N), q(N), LM(N), LL(N), LLJ(N);
+    std::vector<float> LMf(N), LLf(N), LLJf(N);
+    std::vector<int> img(3 * N), type(N), rep(N), cell_rep(cells, -1);
+    std::vector<int> bi_off(N + 1, 0), ex_off(N + 1, 0), ex_idx;
+    std::vector<int2> bitem, bond_ij;
+    std::vector<double> bond_k, bond_r0, ang_k, ang_t0;
+    std::vector<int4> ang;
+    std::vector<std::vector<int2>> items(N);
+    std::vector<std::vector<int>> exl(N);
+    double rmax_o = 0, rmax_s = 0, rmax_f = 0, rm_lo = 1e9, rm_hi = 0, rl_lo = 1e9, rj_lo = 1e9;
+    for (int r = 0; r < R; ++r) {
+        RepHost& h = ctx->reps[r];
+        const RepParams& P = ctx->hp[r];
+        const int o = P.atom_off;
+        const int ncell = P.nc * P.nc * P.nc;
+        for (int c = 0; c < ncell; ++c) cell_rep[P.cell_off + c] = r;
+        std::memcpy(&x[3 * o], h.x.data(), sizeof(double) * 3 * h.n);
+        std::memcpy(&v[3 * o], h.v.data(), sizeof(double) * 3 * h.n);
+        std::memcpy(&xb[3 * o], h.xb.data(), sizeof(double) * 3 * h.n);
+        std::memcpy(&xo[3 * o], h.xo.data(), sizeof(double) * 3 * h.n);
+        std::memcpy(&img[3 * o], h.img.data(), sizeof(int) * 3 * h.n);
+        make_bounds(h, P, &LM[o], &LL[o], &LLJ[o]);
+        for (int i = 0; i < h.n; ++i) {
+            mt[o + i] = h.mass[i] / KCAL_AMU;
+            isqmt[o + i] = 1.0 / std::sqrt(mt[o + i]);
+            q[o + i] = h.charge[i];
+            type[o + i] = h.type[i];
+            rep[o + i] = r;
+            LMf[o + i] = float(LM[o + i]); LLf[o + i] = float(LL[o + i]); LLJf[o + i] = float(LLJ[o + i]);
+        }
+        const int nb = (int)h.bond_k.size();
+        for (int b = 0; b < nb; ++b) {
+            const int t = (int)bond_ij.size();
+            const int a0 = o + h.bonds[2 * b], a1 = o + h.bonds[2 * b + 1];
+            bond_ij.push_back(make_int2(a0, a1));
+            bond_k.push_back(h.bond_k[b]);
+            bond_r0.push_back(h.bond_r0[b]);
+            items[a0].push_back(make_int2(0 | (0 << 4), t));
+            items[a1].push_back(make_int2(0 | (1 << 4), t));
+        }
+        const int na = (int)h.ang_k.size();
+        for (int a = 0; a < na; ++a) {
+            const int t = (int)ang.size();
+            const int e0 = o + h.angles[3 * a], c = o + h.angles[3 * a + 1], e1 = o + h.angles[3 * a + 2];
+            ang.push_back(make_int4(e0, c, e1, 0));
+            ang_k.push_back(h.ang_k[a]);
+            ang_t0.push_back(h.ang_t0[a]);
+            items[e0].push_back(make_int2(1 | (0 << 4), t));
+            items[c].push_back(make_int2(1 | (1 << 4), t));
+            items[e1].push_back(make_int2(1 | (2 << 4), t));
+        }
+        const int ne = (int)h.excl.size() / 2;
+        for (int e = 0; e < ne; ++e) {
+            const int a0 = o + h.excl[2 * e], a1 = o + h.excl[2 * e + 1];
+            exl[a0].push_back(a1);
+            exl[a1].push_back(a0);
+        }
+        const double sk = P.skin;
+        rmax_o = std::max(rmax_o, P.R + P.skin_o);
+        rmax_s = std::max(rmax_s, P.rc + sk);
+        rmax_f = std::max(rmax_f, P.R + sk);
+        rm_lo = std::min(rm_lo, P.sw - sk); rm_hi = std::max(rm_hi, P.rM + sk);
+        rl_lo = std::min(rl_lo, P.rM - sk); rj_lo = std::min(rj_lo, P.sw - sk);
+    }
+    // visiting order of the velocity phases: atoms grouped by an estimate of
+    // their proposal rate (per-pair bound at the thermal speed plus the
+    // adaptive-eps floor), stable in index inside a group
+    std::vector<int> vorder(N);
+    {
+        std::vector<double> est(N);
+        for (int i = 0; i < N; ++i) {
+            const RepParams& P = ctx->hp[rep[i]];
+            const double vth = std::sqrt(3.0 / (P.beta * mt[i]));
+            est[i] = (LM[i] + LL[i]) * P.beta * vth + 2.0 * std::sqrt(P.beta / mt[i]) / P.eps0 + LLJ[i];
+            vorder[i] = i;
+        }
+        std::stable_sort(vorder.begin(), vorder.end(), [&](int x, int y) { return est[x] > est[y]; });
+    }
+    for (int i = 0; i < N; ++i) {
+        bi_off[i + 1] = bi_off[i] + (int)items[i].size();
+        for (auto& it : items[i]) bitem.push_back(it);
+        ex_off[i + 1] = ex_off[i] + (int)exl[i].size();
+        for (int j : exl[i]) ex_idx.push_back(j);
+    }
+    // device arrays
+    RepParams* dP;
+    int *drep, *dvorder, *dtype, *dimg, *dbi_off, *dex_off, *dex_idx;
+    double *dmt, *disqmt, *dq, *dLM, *dLL, *dLLJ, *dbk, *dbr0, *dak, *dat0;
+    float *dLMf, *dLLf, *dLLJf;
+    int2 *dbitem, *dbij;
+    int4* dang;
+#define AL(p, n) if ((rc = dalloc(ctx, &(p), (n)))) return rc
+    AL(dP, R); AL(drep, N); AL(dvorder, N); AL(dtype, N); AL(dimg, 3 * N); AL(dbi_off, N + 1);
+    AL(dex_off, N + 1); AL(dex_idx, ex_idx.size());
+    AL(dmt, N); AL(disqmt, N); AL(dq, N); AL(dLM, N); AL(dLL, N); AL(dLLJ, N);
+    AL(dLMf, N); AL(dLLf, N); AL(dLLJf, N);
+    AL(dbitem, bitem.size()); AL(dbij, bond_ij.size()); AL(dbk, bond_k.size()); AL(dbr0, bond_r0.size());
+    AL(dang, ang.size()); AL(dak, ang_k.size()); AL(dat0, ang_t0.size());
+    AL(d.x, 3 * N); AL(d.v, 3 * N); AL(d.xb, 3 * N); AL(d.xo, 3 * N);
+    AL(d.a0, 3 * N); AL(d.ab, 3 * N); AL(d.as, 3 * N); AL(d.al, 3 * N); AL(d.gout, 3 * N);
+    AL(d.pos, N);
+    AL(d.cell_start, cells + 1); AL(d.cell_cnt, cells + 1); AL(d.cell_atoms, N); AL(d.atom_cell, N);
+    AL(d.cell_rep, cells);
+    d.total_cells = cells;
+    d.ocap = cap_of(rho, 0, rmax_o);
+    AL(d.olist, (size_t)N * d.ocap); AL(d.ocnt, N);
+    const double lo_shell[NKIND] = {0, 0, rm_lo, rl_lo, rj_lo};
+    const double hi_shell[NKIND] = {rmax_s, rmax_f, rm_hi, rmax_f, rmax_f};
+    for (int k = 0; k < NKIND; ++k) {
+        d.lcap[k] = (ctx->kinds & (1 << k)) ? cap_of(rho, lo_shell[k], hi_shell[k]) : 32;
+        AL(d.list[k], (size_t)N * d.lcap[k]);
+        AL(d.lcnt[k], N);
+    }
+    AL(d.flags, 2 * R); AL(d.err, R); AL(d.ovf, R); AL(d.cnt, (size_t)R * NCOUNT); AL(d.energy, 6 * R);
+    AL(d.step_base, R); AL(d.stepc, 2 * R);
+    const long long evcap = ctx->cfg.event_log_cap > 0 ? ctx->cfg.event_log_cap : 0;
+    AL(d.ev, (size_t)6 * (evcap ? evcap : 1)); AL(d.ev_n, 1);
+#undef AL
+    d.ev_cap = evcap;
+    d.P = dP; d.rep = drep; d.vorder = dvorder; d.type = dtype; d.img = dimg; d.bi_off = dbi_off; d.ex_off = dex_off;
+    d.ex_idx = dex_idx; d.mt = dmt; d.isqmt = disqmt; d.q = dq; d.LM = dLM; d.LL = dLL; d.LLJ = dLLJ;
+    d.LMf = dLMf; d.LLf = dLLf; d.LLJf = dLLJf; d.bitem = dbitem; d.bond_ij = dbij; d.bond_k = dbk;
+    d.bond_r0 = dbr0; d.ang = dang; d.ang_k = dak; d.ang_t0 = dat0;
+    if ((rc = upload(ctx, dP, ctx->hp.data(), R)) || (rc = upload(ctx, drep, rep.data(), N)) ||
+        (rc = upload(ctx, dvorder, vorder.data(), N)) ||
+        (rc = upload(ctx, dtype, type.data(), N)) || (rc = upload(ctx, dimg, img.data(), 3 * (size_t)N)) ||
+        (rc = upload(ctx, dbi_off, bi_off.data(), N + 1)) || (rc = upload(ctx, dex_off, ex_off.data(), N + 1)) ||
+        (rc = upload(ctx, dex_idx, ex_idx.data(), ex_idx.size())) || (rc = upload(ctx, dmt, mt.data(), N)) ||
+        (rc = upload(ctx, disqmt, isqmt.data(), N)) || (rc = upload(ctx, dq, q.data(), N)) ||
+        (rc = upload(ctx, dLM, LM.data(), N)) || (rc = upload(ctx, dLL, LL.data(), N)) ||
+        (rc = upload(ctx, dLLJ, LLJ.data(), N)) || (rc = upload(ctx, dLMf, LMf.data(), N)) ||
+        (rc = upload(ctx, dLLf, LLf.data(), N)) || (rc = upload(ctx, dLLJf, LLJf.data(), N)) ||
+        (rc = upload(ctx, dbitem, bitem.data(), bitem.size())) ||
+        (rc = upload(ctx, dbij, bond_ij.data(), bond_ij.size())) ||
+        (rc = upload(ctx, dbk, bond_k.data(), bond_k.size())) ||
+        (rc = upload(ctx, dbr0, bond_r0.data(), bond_r0.size())) ||
+        (rc = upload(ctx, dang, ang.data(), ang.size())) || (rc = upload(ctx, dak, ang_k.data(), ang_k.size())) ||
+        (rc = upload(ctx, dat0, ang_t0.data(), ang_t0.size())) || (rc = upload(ctx, d.x, x.data(), 3 * (size_t)N)) ||
+        (rc = upload(ctx, d.v, v.data(), 3 * (size_t)N)) || (rc = upload(ctx, d.xb, xb.data(), 3 * (size_t)N)) ||
+        (rc = upload(ctx, d.xo, xo.data(), 3 * (size_t)N)) || (rc = upload(ctx, d.cell_rep, cell_rep.data(), cells)))
+        return rc;
+    CK(cudaMemsetAsync(d.cell_cnt, 0, sizeof(int) * (cells + 1), ctx->s));
+    CK(cudaMemsetAsync(d.flags, 0, sizeof(int) * 2 * R, ctx->s));
+    CK(cudaMemsetAsync(d.ev_n, 0, sizeof(unsigned long long), ctx->s));
+    CK(cudaMemsetAsync(d.a0, 0, sizeof(double) * 3 * N, ctx->s));
+    CK(cudaMemsetAsync(d.ab, 0, sizeof(double) * 3 * N, ctx->s));
+    CK(cudaMemsetAsync(d.as, 0, sizeof(double) * 3 * N, ctx->s));
+    CK(cudaMemsetAsync(d.al, 0, sizeof(double) * 3 * N, ctx->s));
+    CK(cudaMemsetAsync(d.err, 0, sizeof(uint32_t) * R, ctx->s));
+    CK(cudaMemsetAsync(d.ovf, 0, sizeof(uint32_t) * R, ctx->s));
+    ctx->on_device = true;
+    // initial build at the stored reference positions
+    launch_check(d, 1, 1, ctx->s);
+    launch_rebuild(d, ctx->kinds, 1, 1, 1, 0, ctx->s);
+    CK(cudaGetLastError());
+    if ((rc = fit_caps(ctx, ctx->kinds, true))) return rc;
+    // restore per-replica counters, errors and step counters
+    std::vector<long long> sb(R);
+    std::vector<unsigned long long> cnt((size_t)R * NCOUNT, 0);
+    std::vector<uint32_t> err(R, 0);
+    for (int r = 0; r < R; ++r) {
+        RepHost& h = ctx->reps[r];
+        sb[r] = h.step;
+        if (!h.fresh && (int)h.cnt.size() == NCOUNT)
+            std::copy(h.cnt.begin(), h.cnt.end(), cnt.begin() + (size_t)r * NCOUNT);
+        err[r] = h.fresh ? 0 : h.err;
+        h.fresh = false;
+    }
+    if ((rc = upload(ctx, d.step_base, sb.data(), R)) || (rc = upload(ctx, d.cnt, cnt.data(), cnt.size())) ||
+        (rc = upload(ctx, d.err, err.data(), R)))
+        return rc;
+    CK(cudaStreamSynchronize(ctx->s));
+    ctx->dirty = false;
+    return MD_OK;
+}
+
+int ensure_kinds(md_ctx* ctx, int mask)
+{
+    const int add = mask & ~ctx->kinds;
+    if (!add) return MD_OK;
+    Dev& d = ctx->d;
+    // capacities for the new kinds
+    double rho = 0, hi_s = 0, hi_f = 0, lo_m = 1e9, hi_m = 0, lo_l = 1e9, lo_j = 1e9;
+    for (int r = 0; r < d.R; ++r) {
+        const RepParams& P = ctx->hp[r];
+        rho = std::max(rho, P.n / (P.L * P.L * P.L));
+        hi_s = std::max(hi_s, P.rc + P.skin); hi_f = std::max(hi_f, P.R + P.skin);
+        lo_m = std::min(lo_m, P.sw - P.skin); hi_m = std::max(hi_m, P.rM + P.skin);
+        lo_l = std::min(lo_l, P.rM - P.skin); lo_j = std::min(lo_j, P.sw - P.skin);
+    }
+    const double lo_shell[NKIND] = {0, 0, lo_m, lo_l, lo_j};
+    const double hi_shell[NKIND] = {hi_s, hi_f, hi_m, hi_f, hi_f};
+    int rc;
+    for (int k = 0; k < NKIND; ++k) {
+        if (!(add & (1 << k))) continue;
+        d.lcap[k] = cap_of(rho, lo_shell[k], hi_shell[k]);
+        if ((rc = dalloc(ctx, &d.list[k], (size_t)d.N * d.lcap[k]))) return rc;
+    }
+    launch_late_lists(d, add, ctx->s);
+    CK(cudaGetLastError());
+    if ((rc = fit_caps(ctx, add, false))) return rc;
+    ctx->kinds |= add;
+    return MD_OK;
+}
+
+cudaEvent_t take_event(md_ctx* ctx)
+{
+    if (!ctx->ev_pool.empty()) {
+        cudaEvent_t e = ctx->ev_pool.back();
+        ctx->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// scope of one launch group: counts its kernels, times it when profiling
+struct Prof {
+    md_ctx* ctx;
+    int cls;
+    cudaEvent_t a = nullptr;
+    Prof(md_ctx* c, int k, int nkernels) : ctx(c), cls(k)
+    {
+        ctx->nlaunch[k] += nkernels;
+        if (ctx->prof) {
+            a = take_event(ctx);
+            cudaEventRecord(a, ctx->s);
+        }
+    }
+    ~Prof()
+    {
+        if (a) {
+            cudaEvent_t b = take_event(ctx);
+            cudaEventRecord(b, ctx->s);
+            ctx->pend.push_back({cls, a, b});
+        }
+    }
+};
+
+void collect_profile(md_ctx* ctx)
+{
+    for (auto& p : ctx->pend) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, p.a, p.b);
+        ctx->prof_ms[p.cls] += ms;
+        ctx->prof_groups[p.cls] += 1;
+        ctx->ev_pool.push_back(p.a);
+        ctx->ev_pool.push_back(p.b);
+    }
+    ctx->pend.clear();
+}
+
+int tpa_for(md_ctx* ctx, int mode)
+{
+    if (ctx->fp64) return 1;
+    if (ctx->tpa_cfg > 0) return ctx->tpa_cfg;
+    if (ctx->tpa[mode]) return ctx->tpa[mode];
+    // autotune: time each width on the current lists (results do not depend on it)
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int pick = 1;
+    for (int t : {1, 2, 4, 8}) {
+        launch_force(ctx->d, mode, ctx->d.gout, 1, 0, t, ctx->s);
+        cudaEventRecord(e0, ctx->s);
+        for (int k = 0; k < 5; ++k) launch_force(ctx->d, mode, ctx->d.gout, 1, 0, t, ctx->s);
+        cudaEventRecord(e1, ctx->s);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; pick = t; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->tpa[mode] = pick;
+    return pick;
+}
+
+void force(md_ctx* ctx, int mode, double* out)
+{
+    const int t = mode == 1 ? 1 : tpa_for(ctx, mode);
+    Prof p(ctx, mode == 1 ? 1 : 0, 1);
+    launch_force(ctx->d, mode, out, 0, ctx->fp64, t, ctx->s);
+}
+
+void rebuild_step(md_ctx* ctx)
+{
+    Prof p(ctx, 4, ctx->kinds ? 7 : 6);
+    launch_rebuild(ctx->d, ctx->kinds, ctx->fp64, 0, ctx->fp64, 0, ctx->s);
+}
+
+void kick(md_ctx* ctx, const double* a, double h)
+{
+    Prof p(ctx, 3, 1);
+    launch_kick(ctx->d, a, h, ctx->s);
+}
+
+void aoa(md_ctx* ctx, double tau, uint32_t s_off, int check)
+{
+    Prof p(ctx, 3, 1);
+    launch_aoa(ctx->d, tau, s_off, check, ctx->fp64, ctx->s);
+}
+
+// autotune the velocity-phase kernel variant on a saved copy of the state:
+// velocities, counters, event log and error flags are restored afterwards, so
+// tuning leaves no trace in the trajectory
+int tune_vphase(md_ctx* ctx, const double* a, double tau2)
+{
+    if (ctx->fp64 || ctx->vvar >= 0) return MD_OK;
+    Dev& d = ctx->d;
+    const char* env = std::getenv("MDJ_VPHASE_VARIANT");
+    if (env) {
+        ctx->vvar = std::max(0, std::min(NVPHASE_VARIANTS - 1, std::atoi(env)));
+        return MD_OK;
+    }
+    double* vs;
+    unsigned long long *cs, *evs;
+    uint32_t* es;
+    int rc;
+    if ((rc = dalloc(ctx, &vs, 3 * (size_t)d.N)) || (rc = dalloc(ctx, &cs, (size_t)d.R * NCOUNT)) ||
+        (rc = dalloc(ctx, &evs, 1)) || (rc = dalloc(ctx, &es, d.R)))
+        return rc;
+    CK(cudaMemcpyAsync(vs, d.v, sizeof(double) * 3 * d.N, cudaMemcpyDeviceToDevice, ctx->s));
+    CK(cudaMemcpyAsync(cs, d.cnt, sizeof(unsigned long long) * d.R * NCOUNT, cudaMemcpyDeviceToDevice, ctx->s));
+    CK(cudaMemcpyAsync(evs, d.ev_n, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, ctx->s));
+    CK(cudaMemcpyAsync(es, d.err, sizeof(uint32_t) * d.R, cudaMemcpyDeviceToDevice, ctx->s));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int pick = 0;
+    for (int v = 0; v < NVPHASE_VARIANTS; ++v) {
+        float tot = 0;
+        for (int rep = 0; rep < 2; ++rep) {
+            CK(cudaMemcpyAsync(d.v, vs, sizeof(double) * 3 * d.N, cudaMemcpyDeviceToDevice, ctx->s));
+            cudaEventRecord(e0, ctx->s);
+            launch_vphase(d, a, tau2, 0, 0, 0, 1, 1, 0, v, ctx->s);
+            cudaEventRecord(e1, ctx->s);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep) tot += ms;
+        }
+        if (tot < best) { best = tot; pick = v; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(cudaMemcpyAsync(d.v, vs, sizeof(double) * 3 * d.N, cudaMemcpyDeviceToDevice, ctx->s));
+    CK(cudaMemcpyAsync(d.cnt, cs, sizeof(unsigned long long) * d.R * NCOUNT, cudaMemcpyDeviceToDevice, ctx->s));
+    CK(cudaMemcpyAsync(d.ev_n, evs, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, ctx->s));
+    CK(cudaMemcpyAsync(d.err, es, sizeof(uint32_t) * d.R, cudaMemcpyDeviceToDevice, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    ctx->vvar = pick;
+    return MD_OK;
+}
+
+void vphase(md_ctx* ctx, const double* a, double tau2, uint32_t s_off, int half, int order)
+{
+    if (ctx->vvar < 0) tune_vphase(ctx, a, tau2);
+    Prof p(ctx, 2, 1);
+    launch_vphase(ctx->d, a, tau2, s_off, half, order, 1, 1, ctx->fp64, ctx->vvar < 0 ? 0 : ctx->vvar, ctx->s);
+}
+
+int set_stepc(md_ctx* ctx, double tau)
+{
+    const int R = ctx->d.R;
+    for (int r = 0; r < R; ++r) {
+        const RepParams& P = ctx->hp[r];
+        ctx->h_stepc[2 * r] = std::exp(-P.gamma * tau);
+        ctx->h_stepc[2 * r + 1] = std::sqrt(-std::expm1(-2.0 * P.gamma * tau) / P.beta);
+    }
+    CK(cudaMemcpyAsync(ctx->d.stepc, ctx->h_stepc, sizeof(double) * 2 * R, cudaMemcpyHostToDevice, ctx->s));
+    return MD_OK;
+}
+
+int finish(md_ctx* ctx, long long inner_steps)
+{
+    {
+        Prof p(ctx, 5, 1);
+        launch_advance(ctx->d, inner_steps, ctx->s);
+    }
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(ctx->h_err, ctx->d.err, sizeof(uint32_t) * ctx->d.R, cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    collect_profile(ctx);
+    uint32_t f = 0;
+    for (int r = 0; r < ctx->d.R; ++r) f |= ctx->h_err[r];
+    if (f & F_NONFIN) FAIL(MD_ENONFINITE, "non-finite positions or velocities");
+    if (f & F_BOUND) FAIL(MD_EBOUND, "a thinning acceptance ratio exceeded 1 (rate bound violated)");
+    if (f & F_LIMIT) FAIL(MD_ELIMIT, "sampler attempt cap or proposal cap reached");
+    if (f & F_OVERFLOW) {
+        std::vector<uint32_t> o(ctx->d.R);
+        CK(cudaMemcpy(o.data(), ctx->d.ovf, sizeof(uint32_t) * ctx->d.R, cudaMemcpyDeviceToHost));
+        uint32_t m = 0;
+        for (uint32_t v : o) m |= v;
+        static const char* names[7] = {"short", "full", "ring M", "ring L", "LJ", "outer", "cell"};
+        std::string which;
+        for (int b = 0; b < 7; ++b)
+            if (m & (1u << b)) which += std::string(which.empty() ? "" : ", ") + names[b];
+        FAIL(MD_EOVERFLOW, "capacity exceeded: %s (lists are sized at set-up; an unstable run "
+                           "packs atoms denser than that)", which.c_str());
+    }
+    return MD_OK;
+}
+
+int prepare(md_ctx* ctx, int family, double dt_fs)
+{
+    if (!ctx) return MD_EINVAL;
+    if (!(dt_fs > 0) || !std::isfinite(dt_fs)) FAIL(MD_EINVAL, "time step must be positive");
+    int rc = commit(ctx);
+    if (rc) return rc;
+    if ((rc = ensure_kinds(ctx, lists_needed(family)))) return rc;
+    CK(cudaMemsetAsync(ctx->d.flags, 0, sizeof(int) * 2 * ctx->d.R, ctx->s));
+    return MD_OK;
+}
+
+// inner bonded step of the RESPA family: B A O A [grad] B at dt
+void inner_bonded(md_ctx* ctx, double dt, uint32_t s_off, int check)
+{
+    Dev& d = ctx->d;
+    kick(ctx, d.ab, 0.5 * dt);
+    aoa(ctx, dt, s_off, check);
+    force(ctx, 1, d.ab);
+    kick(ctx, d.ab, 0.5 * dt);
+}
+
+}  // namespace
+
+// ============================================================================
+// C ABI
+// ============================================================================
+extern "C" {
+
+int md_init(md_ctx** out, const md_config* cfg)
+{
+    if (!out || !cfg) { g_init_msg = "md_init: null argument"; return MD_EINVAL; }
+    *out = nullptr;
+    if (cfg->precision != MD_FP64 && cfg->precision != MD_MIXED) { g_init_msg = "md_init: precision must be MD_FP64 or MD_MIXED"; return MD_EINVAL; }
+    if (cfg->max_replicas < 1 || cfg->max_replicas > 65536) { g_init_msg = "md_init: max_replicas out of range"; return MD_EINVAL; }
+    if (cfg->threads_per_atom != 0 && cfg->threads_per_atom != 1 && cfg->threads_per_atom != 2 &&
+        cfg->threads_per_atom != 4 && cfg->threads_per_atom != 8) { g_init_msg = "md_init: threads_per_atom must be 0, 1, 2, 4 or 8"; return MD_EINVAL; }
+    if (cfg->event_log_cap < 0) { g_init_msg = "md_init: event_log_cap < 0"; return MD_EINVAL; }
+    cudaError_t e = cudaSetDevice(cfg->device);
+    if (e != cudaSuccess) { g_init_msg = std::string("md_init: cudaSetDevice: ") + cudaGetErrorString(e); return MD_ECUDA; }
+    md_ctx* ctx = new md_ctx();
+    ctx->cfg = *cfg;
+    ctx->s = (cudaStream_t)cfg->cuda_stream;
+    ctx->fp64 = cfg->precision == MD_FP64;
+    ctx->tpa_cfg = cfg->threads_per_atom;
+    ctx->reps.resize(cfg->max_replicas);
+    if (cudaMallocHost((void**)&ctx->h_stepc, sizeof(double) * 2 * cfg->max_replicas) != cudaSuccess ||
+        cudaMallocHost((void**)&ctx->h_err, sizeof(uint32_t) * cfg->max_replicas) != cudaSuccess) {
+        g_init_msg = "md_init: pinned host allocation failed";
+        delete ctx;
+        return MD_ENOMEM;
+    }
+    *out = ctx;
+    return MD_OK;
+}
+
+int md_set_system(md_ctx* ctx, int replica, const md_system* sys)
+{
+    if (!ctx) return MD_EINVAL;
+    if (replica < 0 || replica >= (int)ctx->reps.size()) FAIL(MD_EINVAL, "replica %d out of range", replica);
+    int rc = check_sys(ctx, sys);
+    if (rc) return rc;
+    if ((rc = download_all(ctx))) return rc;
+    RepHost& h = ctx->reps[replica];
+    const int n = sys->n_atoms;
+    h = RepHost();
+    h.set = true;
+    h.fresh = true;
+    h.n = n;
+    h.box = sys->box;
+    h.sys = *sys;
+    h.x.assign(sys->x, sys->x + 3 * n);
+    h.v.assign(sys->v, sys->v + 3 * n);
+    h.img.assign(3 * n, 0);
+    for (int k = 0; k < 3 * n; ++k) {       // wrap into [0, L), images start at zero
+        double t = h.x[k];
+        t -= h.box * std::floor(t / h.box);
+        if (t >= h.box) t -= h.box;
+        h.x[k] = t;
+    }
+    h.xb = h.x;
+    h.xo = h.x;
+    h.mass.assign(sys->mass, sys->mass + n);
+    h.charge.assign(sys->charge, sys->charge + n);
+    h.type.assign(sys->type, sys->type + n);
+    h.ntypes = sys->n_types;
+    h.lj_eps.assign(sys->lj_eps, sys->lj_eps + sys->n_types * sys->n_types);
+    h.lj_sig.assign(sys->lj_sigma, sys->lj_sigma + sys->n_types * sys->n_types);
+    h.bonds.assign(sys->bonds, sys->bonds + 2 * sys->n_bonds);
+    h.bond_k.assign(sys->bond_k, sys->bond_k + sys->n_bonds);
+    h.bond_r0.assign(sys->bond_r0, sys->bond_r0 + sys->n_bonds);
+    h.angles.assign(sys->angles, sys->angles + 3 * sys->n_angles);
+    h.ang_k.assign(sys->angle_k, sys->angle_k + sys->n_angles);
+    h.ang_t0.assign(sys->angle_t0, sys->angle_t0 + sys->n_angles);
+    h.excl.assign(sys->excl_pairs, sys->excl_pairs + 2 * sys->n_excl);
+    // keep no caller pointers
+    h.sys.x = h.sys.v = h.sys.mass = h.sys.charge = nullptr;
+    h.sys.type = nullptr;
+    h.sys.lj_eps = h.sys.lj_sigma = nullptr;
+    h.sys.bonds = h.sys.angles = h.sys.excl_pairs = nullptr;
+    h.sys.bond_k = h.sys.bond_r0 = h.sys.angle_k = h.sys.angle_t0 = nullptr;
+    h.step = 0;
+    ctx->dirty = true;
+    return commit(ctx);
+}
+
+int md_set_state(md_ctx* ctx, int replica, const double* x, const double* v, const int* img,
+                 const double* x_build, const double* x_outer, int64_t step)
+{
+    if (!ctx) return MD_EINVAL;
+    int rc = commit(ctx);
+    if (rc) return rc;
+    if (replica < 0 || replica >= ctx->d.R) FAIL(MD_EINVAL, "replica %d out of range", replica);
+    if (!x || !v) FAIL(MD_EINVAL, "md_set_state: x and v are required");
+    Dev& d = ctx->d;
+    const RepHost& h = ctx->reps[replica];
+    const size_t o = 3 * (size_t)ctx->rep_atom_off[replica], n3 = 3 * (size_t)h.n;
+    std::vector<int> zero;
+    if (!img) { zero.assign(n3, 0); img = zero.data(); }
+    const double* xb = x_build ? x_build : x;
+    const double* xo = x_outer ? x_outer : xb;
+    CK(cudaStreamSynchronize(ctx->s));
+    CK(cudaMemcpy(d.x + o, x, n3 * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d.v + o, v, n3 * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d.img + o, img, n3 * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d.xb + o, xb, n3 * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d.xo + o, xo, n3 * sizeof(double), cudaMemcpyHostToDevice));
+    long long st = step;
+    CK(cudaMemcpy(d.step_base + replica, &st, sizeof st, cudaMemcpyHostToDevice));
+    const int fl[2] = {1, 1};
+    CK(cudaMemsetAsync(d.flags, 0, sizeof(int) * 2 * d.R, ctx->s));
+    CK(cudaMemcpyAsync(d.flags + 2 * replica, fl, sizeof fl, cudaMemcpyHostToDevice, ctx->s));
+    launch_rebuild(d, ctx->kinds, 1, 1, 1, 0, ctx->s);
+    CK(cudaGetLastError());
+    // the list build is not a rebuild of the run: undo the counter increments
+    std::vector<unsigned long long> c(NCOUNT);
+    CK(cudaMemcpyAsync(c.data(), d.cnt + (size_t)replica * NCOUNT, sizeof(unsigned long long) * NCOUNT,
+                       cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    c[C_REBUILD] -= 1;
+    c[C_OUTER] -= 1;
+    CK(cudaMemcpy(d.cnt + (size_t)replica * NCOUNT, c.data(), sizeof(unsigned long long) * NCOUNT,
+                  cudaMemcpyHostToDevice));
+    return MD_OK;
+}
+
+int md_step_baoab(md_ctx* ctx, int64_t nsteps, double dt_fs)
+{
+    int rc = prepare(ctx, 0, dt_fs);
+    if (rc) return rc;
+    if (nsteps < 0) FAIL(MD_EINVAL, "nsteps < 0");
+    Dev& d = ctx->d;
+    const double tau = dt_fs * 1e-3;
+    if ((rc = set_stepc(ctx, tau))) return rc;
+    force(ctx, 0, d.a0);
+    for (int64_t k = 0; k < nsteps; ++k) {
+        kick(ctx, d.a0, 0.5 * tau);
+        aoa(ctx, tau, uint32_t(k), 1);
+        rebuild_step(ctx);
+        force(ctx, 0, d.a0);
+        kick(ctx, d.a0, 0.5 * tau);
+    }
+    return finish(ctx, nsteps);
+}
+
+int md_step_jump(md_ctx* ctx, int64_t nsteps, double dt_fs)
+{
+    int rc = prepare(ctx, 2, dt_fs);
+    if (rc) return rc;
+    if (nsteps < 0) FAIL(MD_EINVAL, "nsteps < 0");
+    Dev& d = ctx->d;
+    const double tau = dt_fs * 1e-3;
+    if ((rc = set_stepc(ctx, tau))) return rc;
+    force(ctx, 5, d.a0);
+    for (int64_t k = 0; k < nsteps; ++k) {
+        vphase(ctx, d.a0, 0.5 * tau, uint32_t(k), 0, 0);
+        aoa(ctx, tau, uint32_t(k), 1);
+        rebuild_step(ctx);
+        force(ctx, 5, d.a0);
+        vphase(ctx, d.a0, 0.5 * tau, uint32_t(k), 1, 1);
+    }
+    return finish(ctx, nsteps);
+}
+
+int md_step_baoab_respa(md_ctx* ctx, int64_t n_outer, double dt_inner_fs, int n_inner)
+{
+    int rc = prepare(ctx, 0, dt_inner_fs);
+    if (rc) return rc;
+    if (n_outer < 0 || n_inner < 1) FAIL(MD_EINVAL, "n_outer >= 0 and n_inner >= 1 required");
+    Dev& d = ctx->d;
+    const double dt = dt_inner_fs * 1e-3, D = dt * n_inner;
+    if ((rc = set_stepc(ctx, dt))) return rc;
+    force(ctx, 1, d.ab);
+    force(ctx, 2, d.al);
+    uint32_t s = 0;
+    for (int64_t o = 0; o < n_outer; ++o) {
+        kick(ctx, d.al, 0.5 * D);
+        for (int k = 0; k < n_inner; ++k, ++s) inner_bonded(ctx, dt, s, k == n_inner - 1);
+        rebuild_step(ctx);
+        force(ctx, 2, d.al);
+        kick(ctx, d.al, 0.5 * D);
+    }
+    return finish(ctx, (long long)n_outer * n_inner);
+}
+
+int md_step_baoab_respa1(md_ctx* ctx, int64_t n_outer, double dt_inner_fs, int m_mid, int n_outer_ratio)
+{
+    int rc = prepare(ctx, 1, dt_inner_fs);
+    if (rc) return rc;
+    if (n_outer < 0 || m_mid < 1 || n_outer_ratio < 1) FAIL(MD_EINVAL, "n_outer >= 0, m_mid >= 1, n_outer_ratio >= 1 required");
+    Dev& d = ctx->d;
+    const double dt = dt_inner_fs * 1e-3, kap = dt * m_mid, D = kap * n_outer_ratio;
+    if ((rc = set_stepc(ctx, dt))) return rc;
+    force(ctx, 1, d.ab);
+    force(ctx, 3, d.as);
+    force(ctx, 4, d.al);
+    uint32_t s = 0;
+    for (int64_t o = 0; o < n_outer; ++o) {
+        kick(ctx, d.al, 0.5 * D);
+        for (int j = 0; j < n_outer_ratio; ++j) {
+            kick(ctx, d.as, 0.5 * kap);
+            for (int k = 0; k < m_mid; ++k, ++s) inner_bonded(ctx, dt, s, k == m_mid - 1);
+            rebuild_step(ctx);
+            force(ctx, 3, d.as);
+            kick(ctx, d.as, 0.5 * kap);
+        }
+        force(ctx, 4, d.al);
+        kick(ctx, d.al, 0.5 * D);
+    }
+    return finish(ctx, (long long)n_outer * n_outer_ratio * m_mid);
+}
+
+static int jump_respa_cycles(md_ctx* ctx, int64_t cycles, double dt_inner_fs, int n_inner)
+{
+    Dev& d = ctx->d;
+    const double dt = dt_inner_fs * 1e-3, D = dt * n_inner;
+    int rc;
+    if ((rc = set_stepc(ctx, dt))) return rc;
+    force(ctx, 1, d.ab);
+    force(ctx, 3, d.as);
+    uint32_t s = 0;
+    for (int64_t o = 0; o < cycles; ++o) {
+        const uint32_t s0 = s;
+        vphase(ctx, d.as, 0.5 * D, s0, 0, 0);
+        for (int k = 0; k < n_inner; ++k, ++s) inner_bonded(ctx, dt, s, k == n_inner - 1);
+        rebuild_step(ctx);
+        force(ctx, 3, d.as);
+        vphase(ctx, d.as, 0.5 * D, s0, 1, 1);
+    }
+    return finish(ctx, (long long)cycles * n_inner);
+}
+
+int md_step_jump_respa(md_ctx* ctx, int64_t n_outer, double dt_inner_fs, int n_inner)
+{
+    int rc = prepare(ctx, 2, dt_inner_fs);
+    if (rc) return rc;
+    if (n_outer < 0 || n_inner < 1) FAIL(MD_EINVAL, "n_outer >= 0 and n_inner >= 1 required");
+    return jump_respa_cycles(ctx, n_outer, dt_inner_fs, n_inner);
+}
+
+int md_step_jump_respa1(md_ctx* ctx, int64_t n_outer, double dt_inner_fs, int m_mid, int n_outer_ratio)
+{
+    int rc = prepare(ctx, 2, dt_inner_fs);
+    if (rc) return rc;
+    if (n_outer < 0 || m_mid < 1 || n_outer_ratio < 1) FAIL(MD_EINVAL, "n_outer >= 0, m_mid >= 1, n_outer_ratio >= 1 required");
+    return jump_respa_cycles(ctx, n_outer * n_outer_ratio, dt_inner_fs, m_mid);
+}
+
+int md_observables(md_ctx* ctx, int replica, md_obs* out)
+{
+    if (!ctx || !out) return MD_EINVAL;
+    int rc = commit(ctx);
+    if (rc) return rc;
+    if (replica < 0 || replica >= ctx->d.R) FAIL(MD_EINVAL, "replica %d out of range", replica);
+    Dev& d = ctx->d;
+    CK(cudaMemsetAsync(d.energy, 0, sizeof(double) * 6 * d.R, ctx->s));
+    launch_energy(d, ctx->s);
+    CK(cudaGetLastError());
+    double e[6];
+    unsigned long long c[NCOUNT];
+    long long st;
+    uint32_t err;
+    CK(cudaMemcpyAsync(e, d.energy + 6 * replica, sizeof e, cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaMemcpyAsync(c, d.cnt + (size_t)replica * NCOUNT, sizeof c, cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaMemcpyAsync(&st, d.step_base + replica, sizeof st, cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaMemcpyAsync(&err, d.err + replica, sizeof err, cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    const int n = ctx->reps[replica].n;
+    std::memset(out, 0, sizeof *out);
+    out->pe_bond = e[0]; out->pe_angle = e[1]; out->pe_lj = e[2]; out->pe_coul = e[3];
+    out->ke = e[4];
+    out->temperature = 2.0 * e[4] / (3.0 * n * KB);
+    out->step = st;
+    out->jump_proposals = (int64_t)c[C_CPROP]; out->jump_accepts = (int64_t)c[C_CACC];
+    out->bps_proposals = (int64_t)c[C_JPROP]; out->bps_accepts = (int64_t)c[C_JACC];
+    out->sampler_attempts = (int64_t)c[C_SATT]; out->list_rebuilds = (int64_t)c[C_REBUILD];
+    out->outer_rebuilds = (int64_t)c[C_OUTER]; out->guarded_accepts = (int64_t)c[C_GUARD];
+    out->error_flags = err;
+    return MD_OK;
+}
+
+int md_get_state(md_ctx* ctx, int replica, double* x, double* v, int* img, double* x_build, double* x_outer)
+{
+    if (!ctx) return MD_EINVAL;
+    int rc = commit(ctx);
+    if (rc) return rc;
+    if (replica < 0 || replica >= ctx->d.R) FAIL(MD_EINVAL, "replica %d out of range", replica);
+    Dev& d = ctx->d;
+    const size_t o = 3 * (size_t)ctx->rep_atom_off[replica], n3 = 3 * (size_t)ctx->reps[replica].n;
+    if (x) CK(cudaMemcpyAsync(x, d.x + o, n3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+    if (v) CK(cudaMemcpyAsync(v, d.v + o, n3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+    if (img) CK(cudaMemcpyAsync(img, d.img + o, n3 * sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
+    if (x_build) CK(cudaMemcpyAsync(x_build, d.xb + o, n3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+    if (x_outer) CK(cudaMemcpyAsync(x_outer, d.xo + o, n3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    return MD_OK;
+}
+
+int md_gradient(md_ctx* ctx, int replica, int mode, double* host_grad)
+{
+    if (!ctx || !host_grad) return MD_EINVAL;
+    if (mode < 0 || mode > 5) FAIL(MD_EINVAL, "gradient mode %d out of range", mode);
+    int rc = commit(ctx);
+    if (rc) return rc;
+    if (replica < 0 || replica >= ctx->d.R) FAIL(MD_EINVAL, "replica %d out of range", replica);
+    if ((rc = ensure_kinds(ctx, mode_list(mode)))) return rc;
+    Dev& d = ctx->d;
+    launch_force(d, mode, d.gout, 1, ctx->fp64, (mode == 1 || ctx->fp64) ? 1 : tpa_for(ctx, mode), ctx->s);
+    CK(cudaGetLastError());
+    const size_t o = 3 * (size_t)ctx->rep_atom_off[replica], n3 = 3 * (size_t)ctx->reps[replica].n;
+    CK(cudaMemcpyAsync(host_grad, d.gout + o, n3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    return MD_OK;
+}
+
+int md_run_phase(md_ctx* ctx, int phase, double tau2_ps, int64_t s0, int half, int accel_mode)
+{
+    if (!ctx) return MD_EINVAL;
+    if ((phase != 0 && phase != 1) || (half != 0 && half != 1) || !(tau2_ps >= 0) || accel_mode < 0 || accel_mode > 5)
+        FAIL(MD_EINVAL, "md_run_phase: bad phase, half, tau2 or accel_mode");
+    int rc = commit(ctx);
+    if (rc) return rc;
+    const int need = (phase == 0 ? ((1 << L_RM) | (1 << L_RL)) | mode_list(accel_mode) : (1 << L_LJ));
+    if ((rc = ensure_kinds(ctx, need))) return rc;
+    Dev& d = ctx->d;
+    if (phase == 0) force(ctx, accel_mode, d.a0);
+    launch_vphase_abs(d, phase == 0 ? d.a0 : nullptr, tau2_ps, uint32_t(s0), half, 0, phase == 0, phase == 1,
+                      ctx->fp64, ctx->vvar < 0 ? 0 : ctx->vvar, ctx->s);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(ctx->h_err, d.err, sizeof(uint32_t) * d.R, cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    return MD_OK;
+}
+
+int md_get_list(md_ctx* ctx, int replica, int kind, int atom, int* host_out, int cap)
+{
+    if (!ctx) return MD_EINVAL;
+    int rc = commit(ctx);
+    if (rc) return rc;
+    if (replica < 0 || replica >= ctx->d.R || kind < 0 || kind > 2 || atom < 0 || atom >= ctx->reps[replica].n)
+        FAIL(MD_EINVAL, "md_get_list: bad replica, kind or atom");
+    const int k = kind == 0 ? L_RM : (kind == 1 ? L_RL : L_LJ);
+    if ((rc = ensure_kinds(ctx, 1 << k))) return rc;
+    Dev& d = ctx->d;
+    const int gi = ctx->rep_atom_off[replica] + atom;
+    int n;
+    CK(cudaMemcpyAsync(&n, d.lcnt[k] + gi, sizeof n, cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    const int m = std::min(std::min(n, d.lcap[k]), std::max(cap, 0));
+    if (m > 0 && host_out) {
+        std::vector<uint32_t> e(m);
+        CK(cudaMemcpy(e.data(), d.list[k] + (size_t)gi * d.lcap[k], sizeof(uint32_t) * m, cudaMemcpyDeviceToHost));
+        for (int t = 0; t < m; ++t) host_out[t] = int(e[t]) - ctx->rep_atom_off[replica];
+    }
+    return n;
+}
+
+int64_t md_get_events(md_ctx* ctx, int replica, int64_t* host_out6, int64_t cap, int clear)
+{
+    if (!ctx) return MD_EINVAL;
+    int rc = commit(ctx);
+    if (rc) return rc;
+    Dev& d = ctx->d;
+    unsigned long long n = 0;
+    CK(cudaMemcpyAsync(&n, d.ev_n, sizeof n, cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    const long long m = std::min<long long>((long long)n, d.ev_cap);
+    std::vector<long long> ev((size_t)6 * (m > 0 ? m : 1));
+    if (m > 0) CK(cudaMemcpy(ev.data(), d.ev, sizeof(long long) * 6 * m, cudaMemcpyDeviceToHost));
+    int64_t w = 0;
+    for (long long t = 0; t < m && w < cap; ++t) {
+        if ((ev[6 * t + 2] >> 8) != replica) continue;
+        if (host_out6) {
+            for (int c = 0; c < 6; ++c) host_out6[6 * w + c] = ev[6 * t + c];
+            host_out6[6 * w + 2] &= 0xff;
+        }
+        ++w;
+    }
+    if (clear) CK(cudaMemsetAsync(d.ev_n, 0, sizeof(unsigned long long), ctx->s));
+    if ((long long)n > d.ev_cap) FAIL(MD_EOVERFLOW, "event log overflowed (%llu events, capacity %lld)", n, d.ev_cap);
+    return w;
+}
+
+int md_profile(md_ctx* ctx, int enable, int reset, double* ms_out, int64_t* groups_out,
+               int64_t* launches_out)
+{
+    if (!ctx) return MD_EINVAL;
+    if (!ctx->pend.empty()) {
+        CK(cudaStreamSynchronize(ctx->s));
+        collect_profile(ctx);
+    }
+    if (reset) {
+        for (int k = 0; k < 6; ++k) { ctx->prof_ms[k] = 0; ctx->prof_groups[k] = 0; }
+    }
+    if (enable == 0 || enable == 1) ctx->prof = enable == 1;
+    for (int k = 0; k < 6; ++k) {
+        if (ms_out) ms_out[k] = ctx->prof_ms[k];
+        if (groups_out) groups_out[k] = ctx->prof_groups[k];
+        if (launches_out) launches_out[k] = ctx->nlaunch[k];
+    }
+    return MD_OK;
+}
+
+int md_finalize(md_ctx* ctx)
+{
+    if (!ctx) return MD_EINVAL;
+    free_device(ctx);
+    cudaStreamSynchronize(ctx->s);
+    for (auto& p : ctx->pend) { ctx->ev_pool.push_back(p.a); ctx->ev_pool.push_back(p.b); }
+    for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    cudaFreeHost(ctx->h_stepc);
+    cudaFreeHost(ctx->h_err);
+    delete ctx;
+    return MD_OK;
+}
+
+const char* md_last_error(const md_ctx* ctx)
+{
+    return ctx ? ctx->msg.c_str() : g_init_msg.c_str();
+}
+
+}  // extern "C"

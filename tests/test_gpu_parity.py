@@ -1,0 +1,278 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bars: per-atom gradient error <= 1e-12 (FP64 mode) and <= 1e-5 (mixed mode),
+measured as |dF_i| / max(|F_i|, 0.01 F_rms); identical jump lists; identical
+accepted-jump events and positions within 1e-6 A over 100 steps (FP64 mode);
+sampled per-atom C' phases at 24,000 atoms.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+PARAMS = dict(r_cut=9.0, r_split=5.0, h_switch=0.5, r_mid=5.5, dsf_alpha=0.2, gamma=1.0,
+              temperature=300.0, eps0=0.1, eps_mode=1, skin=0.2, skin_outer=0.3)
+
+
+@pytest.fixture(scope="module")
+def M():
+    import paper_2412_15073_gb300 as M
+    M.load_library()
+    return M
+
+
+def make(M, oracle_mod, sys, precision, seed=0, tpa=0, **kw):
+    p = dict(PARAMS)
+    p.update(kw)
+    e = M.Engine(precision=precision, seed=seed, event_log_cap=1 << 21, threads_per_atom=tpa)
+    e.set_system(0, sys, **p)
+    o = oracle_mod.Oracle(sys, seed=seed, replica=0, **p)
+    return e, o
+
+
+def force_err(g, ref):
+    rms = np.sqrt((ref * ref).sum(1).mean())
+    den = np.maximum(np.linalg.norm(ref, axis=1), 0.01 * rms)
+    return (np.linalg.norm(g - ref, axis=1) / den).max()
+
+
+def pos_err(xa, xb, L):
+    d = xa - xb
+    d -= L * np.round(d / L)
+    return np.abs(d).max()
+
+
+def sorted_events(ev):
+    ev = np.asarray(ev, dtype=np.int64).reshape(-1, 6)
+    return ev[np.lexsort(ev.T[::-1])]
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-5)])
+def test_gradients(M, oracle_mod, water648, precision, tol):
+    w = water648.copy()
+    w.x = (w.x + np.random.default_rng(3).normal(scale=0.05, size=w.x.shape)) % w.box
+    e, o = make(M, oracle_mod, w, precision)
+    errs = {}
+    for mode in range(6):
+        g = e.gradient(mode)
+        ref, _ = o.gradient(mode)
+        errs[mode] = force_err(g, ref)
+    print("per-atom relative gradient error by mode:", errs)
+    assert max(errs.values()) <= tol, errs
+
+
+def test_fixed_point_forces_do_not_depend_on_threads_per_atom(M, oracle_mod, water648):
+    gs = []
+    for tpa in (1, 2, 4, 8):
+        e, _ = make(M, oracle_mod, water648, 1, tpa=tpa)
+        gs.append(np.stack([e.gradient(0), e.gradient(5)]))
+    for g in gs[1:]:
+        assert np.array_equal(g, gs[0])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_jump_lists_identical(M, oracle_mod, water648, precision):
+    e, o = make(M, oracle_mod, water648, precision)
+    for i in range(0, water648.n, 7):
+        for kind in (0, 1, 2):
+            np.testing.assert_array_equal(e.get_list(kind, i), o.list_of(kind, i))
+
+
+def test_baoab_trajectory_fp64(M, oracle_mod, water648):
+    e, o = make(M, oracle_mod, water648, 0, seed=5)
+    e.baoab(100)
+    o.baoab(100)
+    xg, vg, ig, _ = e.state()
+    xo, vo, io, _ = o.state()
+    assert pos_err(xg, xo, water648.box) < 1e-6
+    assert np.abs(vg - vo).max() < 1e-5
+    assert np.array_equal(ig, io)
+    assert e.observables()["list_rebuilds"] == o.counters()[5]
+
+
+def test_jump_trajectory_and_events_fp64(M, oracle_mod, water648):
+    e, o = make(M, oracle_mod, water648, 0, seed=7)
+    o.events_enable(1 << 22)
+    e.jump(100)
+    o.jump(100)
+    xg, vg, _, _ = e.state()
+    xo, vo, _, _ = o.state()
+    ev_g, ev_o = sorted_events(e.events()), sorted_events(o.events())
+    assert len(ev_o) > 1000
+    assert np.array_equal(ev_g, ev_o), (len(ev_g), len(ev_o))
+    c = o.counters()
+    ob = e.observables()
+    assert (ob["jump_proposals"], ob["jump_accepts"], ob["bps_proposals"], ob["bps_accepts"]) == tuple(c[:4])
+    assert pos_err(xg, xo, water648.box) < 1e-6
+    assert np.abs(vg - vo).max() < 1e-5
+    assert ob["error_flags"] == 0 and o.errors == 0
+
+
+@pytest.mark.parametrize("how", ["baoab_respa", "baoab_respa1", "jump_respa", "jump_respa1"])
+def test_multiple_time_step_family_fp64(M, oracle_mod, water648, how):
+    e, o = make(M, oracle_mod, water648, 0, seed=11)
+    args = {"baoab_respa": (25, 1.0, 2), "jump_respa": (25, 1.0, 2),
+            "baoab_respa1": (10, 1.0, 2, 3), "jump_respa1": (10, 1.0, 2, 3)}[how]
+    getattr(e, how)(*args)
+    getattr(o, how)(*args)
+    xg, vg, _, _ = e.state()
+    xo, vo, _, _ = o.state()
+    assert e.observables()["step"] == o.step
+    assert pos_err(xg, xo, water648.box) < 1e-6, how
+    assert np.abs(vg - vo).max() < 1e-5, how
+
+
+def test_jump_mixed_precision_tracks_oracle(M, oracle_mod, water648):
+    """Mixed mode: FP32 pair math and jump loops against the FP64 oracle. Over
+    10 steps the accepted jumps agree except near rare ties (a flip changes
+    one atom's velocity, after which that atom's later events differ), and the
+    positions stay within 1e-3 A."""
+    e, o = make(M, oracle_mod, water648, 1, seed=7)
+    o.events_enable(1 << 22)
+    e.jump(10)
+    o.jump(10)
+    ev_g = {tuple(r) for r in e.events().tolist()}
+    ev_o = {tuple(r) for r in o.events().tolist()}
+    flips = len(ev_g ^ ev_o)
+    print("mixed-mode events:", len(ev_o), "differing:", flips)
+    assert flips <= 0.02 * len(ev_o), (flips, len(ev_o))
+    xg = e.state()[0]
+    xo = o.state()[0]
+    d = xg - xo
+    d -= water648.box * np.round(d / water648.box)
+    err = np.sqrt((d * d).sum(1))
+    print("mixed-mode position error after 10 steps: mean", err.mean(), "max", err.max())
+    assert err.mean() < 1e-3
+
+
+def test_jump_mixed_precision_statistics(M, oracle_mod, water648):
+    """Over 200 steps the mixed-mode path keeps the oracle's jump statistics:
+    proposals per atom-step and accepted fractions agree within 3 %."""
+    e, o = make(M, oracle_mod, water648, 1, seed=8)
+    e.jump(200)
+    o.jump(200)
+    ob = e.observables()
+    c = o.counters()
+    for got, ref in ((ob["jump_proposals"], c[0]), (ob["jump_accepts"], c[1])):
+        assert abs(got / ref - 1) < 0.03, (got, ref)
+    assert abs(ob["bps_proposals"] / max(c[2], 1) - 1) < 0.25
+    assert ob["error_flags"] == 0
+
+
+def test_sampled_cprime_phase_at_24000_atoms(M, oracle_mod):
+    """One C' phase on 24,000 atoms (8,000 waters, 62.1 A) on the GPU in both
+    precisions, checked atom by atom against the oracle on 300 sampled atoms."""
+    from paper_2412_15073_gb300 import systems
+    w = systems.water_box(8000, box=62.1, seed=0)
+    p = dict(PARAMS, skin=0.5, skin_outer=1.5)
+    o = oracle_mod.Oracle(w, seed=3, replica=0, **p)
+    rng = np.random.default_rng(1)
+    idx = rng.choice(w.n, 300, replace=False)
+    mt = w.mass / 418.4
+    tau2 = 0.0005
+    for precision, rtol, frac in ((0, 1e-10, 1.0), (1, 2e-5, 0.98)):
+        e = M.Engine(precision=precision, seed=3)
+        e.set_system(0, w, **p)
+        e.run_phase(0, tau2, s0=123, half=0, accel_mode=M.GRAD_F0)
+        vg = e.state()[1]
+        good = 0
+        for i in idx:
+            a = -o.gradient_atom(oracle_mod.GRAD_F0, i) / mt[i]
+            vo, _, _ = o.cprime_one(i, w.v[i], a, tau2, 123, 0)
+            good += np.abs(vg[i] - vo).max() <= rtol * max(np.abs(vo).max(), 1.0)
+        assert good >= frac * len(idx), (precision, good)
+        e.close()
+
+
+def test_batched_replicas(M, oracle_mod):
+    """Three replicas of uneven size in one launch per step: each matches the
+    oracle run with its own Philox key (FP64), and replica 0 of a mixed batch
+    equals a mixed solo run bit for bit."""
+    from paper_2412_15073_gb300 import systems
+    sizes = [216, 290, 250]
+    syss = [systems.water_box(n, seed=10 + k) for k, n in enumerate(sizes)]
+    p = dict(PARAMS)
+    e = M.Engine(precision=0, seed=9, max_replicas=3)
+    for r, s in enumerate(syss):
+        e.set_system(r, s, **p)
+    e.jump(40)
+    for r, s in enumerate(syss):
+        o = oracle_mod.Oracle(s, seed=9, replica=r, **p)
+        o.jump(40)
+        e.n[r] = s.n
+        assert pos_err(e.state(r)[0], o.state()[0], s.box) < 1e-6, r
+    eb = M.Engine(precision=1, seed=9, max_replicas=3)
+    for r, s in enumerate(syss):
+        eb.set_system(r, s, **p)
+    es = M.Engine(precision=1, seed=9)
+    es.set_system(0, syss[0], **p)
+    eb.jump(40)
+    es.jump(40)
+    xb, vb, _, _ = eb.state(0)
+    xs, vs, _, _ = es.state(0)
+    assert np.array_equal(xb, xs) and np.array_equal(vb, vs)
+
+
+def test_resume_bit_exact_on_gpu(M, oracle_mod, water648):
+    a, _ = make(M, oracle_mod, water648, 1, seed=6)
+    a.jump(40)
+    xa, va, _, _ = a.state()
+    b, _ = make(M, oracle_mod, water648, 1, seed=6)
+    b.jump(20)
+    x, v, img, xb, xo = b.state(outer=True)
+    c, _ = make(M, oracle_mod, water648, 1, seed=6)
+    c.set_state(0, x, v, img, xb, xo, step=20)
+    c.jump(20)
+    xc, vc, _, _ = c.state()
+    assert np.array_equal(xa, xc) and np.array_equal(va, vc)
+
+
+def test_energy_observables(M, oracle_mod, water648):
+    e, o = make(M, oracle_mod, water648, 0, seed=2)
+    e.jump(10)
+    o.jump(10)
+    ob = e.observables()
+    ref = o.energy()
+    got = np.array([ob["pe_bond"], ob["pe_angle"], ob["pe_lj"], ob["pe_coul"]])
+    np.testing.assert_allclose(got, ref, rtol=1e-9, atol=1e-9)
+    v = o.state()[1]
+    ke = 0.5 * (water648.mass[:, None] * v * v).sum() / 418.4
+    assert ob["ke"] == pytest.approx(ke, rel=1e-9)
+
+
+def test_jump_is_baoab_without_jump_range_on_gpu(M, oracle_mod, water648):
+    p = dict(r_split=9.6)
+    a, _ = make(M, oracle_mod, water648, 1, seed=4, **p)
+    b, _ = make(M, oracle_mod, water648, 1, seed=4, **p)
+    a.jump(30)
+    b.baoab(30)
+    xa, va, _, _ = a.state()
+    xb, vb, _, _ = b.state()
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+
+
+def test_invalid_inputs_are_rejected(M, water648):
+    e = M.Engine(precision=1)
+    with pytest.raises(M.MDError) as ex:
+        e.set_system(0, water648, r_cut=9.0, skin=0.5, skin_outer=1.0)   # box < 2 (r_cut + skin_outer)
+    assert ex.value.code == -1
+    with pytest.raises(M.MDError):
+        e.jump(1)                                                         # no system yet
+    with pytest.raises(M.MDError):
+        e.set_system(1, water648)                                         # replica out of range
+
+
+def test_velocity_phase_variants_are_identical(M, oracle_mod, water648, monkeypatch):
+    """The occupancy variants the autotuner chooses between compute the same
+    values bit for bit (mixed mode, 20 JUMP steps)."""
+    ref = None
+    for var in range(4):
+        monkeypatch.setenv("MDJ_VPHASE_VARIANT", str(var))
+        e, _ = make(M, oracle_mod, water648, 1, seed=12)
+        e.jump(20)
+        x, v, _, _ = e.state()
+        if ref is None:
+            ref = (x, v)
+        else:
+            assert np.array_equal(x, ref[0]) and np.array_equal(v, ref[1]), var
+        e.close()
