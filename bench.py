@@ -334,22 +334,25 @@ def main():
     roof["share_of_step"] = float(ms[top] / ms.sum())
     roof["class_ms_per_step"] = {c: float(m / prof_steps) for c, m in zip(classes, ms)}
 
-    # RESPA1 pair (config: delta 1 fs, kappa 2 fs, Delta 6 fs)
+    # RESPA1 pair: delta 1 fs (bonded), kappa 2 fs (short pairs, and the jumps of
+    # JUMP-RESPA1), Delta 4 fs (BAOAB-RESPA1 long pairs)
     respa = None
     if args.respa1:
-        er = engine(3)
-        eb1 = engine(4)
-        cyc = max(args.steps // 6, 1)
-        er.jump_respa1(2, 1.0, 2, 3)
-        eb1.baoab_respa1(2, 1.0, 2, 3)
-        barrier()
-        t_jr = max_over_ranks(timed(er, lambda k: er.jump_respa1(k, 1.0, 2, 3), cyc, stream))
-        t_br = max_over_ranks(timed(eb1, lambda k: eb1.baoab_respa1(k, 1.0, 2, 3), cyc, stream))
-        respa = {"jump_respa1_ns_per_day": ns_per_day(world * cyc * 6 * DT_FS, t_jr),
-                 "baoab_respa1_ns_per_day": ns_per_day(world * cyc * 6 * DT_FS, t_br),
-                 "steps": "1:2:6 fs (delta, kappa, Delta)", "cycles": cyc}
-        er.close()
-        eb1.close()
+        m_mid, n_out = 2, 2
+        per_cycle = m_mid * n_out
+        cyc = max(args.steps // per_cycle, 1)
+        respa = {"steps": f"1:{m_mid}:{m_mid * n_out} fs (delta, kappa, Delta)", "cycles": cyc}
+        for name, seed, meth in (("jump_respa1", 3, "jump_respa1"), ("baoab_respa1", 4, "baoab_respa1")):
+            e = engine(seed)
+            try:
+                getattr(e, meth)(2, 1.0, m_mid, n_out)
+                barrier()
+                t = max_over_ranks(timed(e, lambda k: getattr(e, meth)(k, 1.0, m_mid, n_out), cyc, stream))
+                respa[name + "_ns_per_day"] = ns_per_day(world * cyc * per_cycle * DT_FS, t)
+                respa[name + "_T"] = e.observables()["temperature"]
+            except M.MDError as ex:
+                respa[name + "_error"] = str(ex)
+            e.close()
 
     # end to end through the public API with host buffers
     e2e = None

@@ -55,7 +55,7 @@ struct RepParams {
     // scaled coordinates: x = s L / 2^32 with s a 32-bit integer, so that
     // integer differences give the minimum image exactly
     double scl, inv_scl;       // L / 2^32, 2^32 / L
-    float sclf, pad1;
+    float sclf, sclf_lo;       // L / 2^32 as a sum of two floats (hi + lo)
     // cutoffs
     double R, rc, h, sw, rM;   // r_E, r_c, h, r_c - h, r_M (= sw with one ring)
     int one_ring, rings_on, lj_on, eps_mode;
@@ -242,12 +242,18 @@ __device__ __forceinline__ uint32_t to_scaled(double x, const RepParams& P)
 {
     return (uint32_t)(unsigned long long)llrint(x * P.inv_scl);
 }
-// FP32 minimum-image displacement a - b: exact integer difference, one rounding
-__device__ __forceinline__ void sdisp(const uint4& a, const uint4& b, float s, float& dx, float& dy, float& dz)
+// FP32 minimum-image displacement a - b: exact integer difference, rounded
+// once to FP32 and scaled by L / 2^32 carried as two floats (no systematic
+// scale error)
+__device__ __forceinline__ void sdisp(const uint4& a, const uint4& b, float s, float slo, float& dx, float& dy,
+                                      float& dz)
 {
-    dx = __int2float_rn(int(a.x - b.x)) * s;
-    dy = __int2float_rn(int(a.y - b.y)) * s;
-    dz = __int2float_rn(int(a.z - b.z)) * s;
+    const float fx = __int2float_rn(int(a.x - b.x));
+    const float fy = __int2float_rn(int(a.y - b.y));
+    const float fz = __int2float_rn(int(a.z - b.z));
+    dx = fmaf(fx, s, fx * slo);
+    dy = fmaf(fy, s, fy * slo);
+    dz = fmaf(fz, s, fz * slo);
 }
 
 }  // namespace mdj

@@ -35,6 +35,9 @@ struct Dev {
     const double *bond_k, *bond_r0;
     const int4* ang;                // (end a, centre, end b, 0)
     const double *ang_k, *ang_t0;
+    int nbond, nang;
+    double* bterm;                  // per bond: gradient on its first atom (3)
+    double* aterm;                  // per angle: gradients on its two ends (6)
     // exclusions (both directions)
     const int* ex_off;
     const int* ex_idx;
@@ -71,7 +74,8 @@ void launch_late_lists(const Dev& d, int kinds, cudaStream_t s);
 
 // ---- forces and integrators (k_force.cu) -----------------------------------------
 // mode: 0 full, 1 bonded, 2 nb full, 3 nb short, 4 nb long, 5 F0 (bonded + short)
-void launch_force(const Dev& d, int mode, double* out, int as_grad, int fp64, int tpa, cudaStream_t s);
+// returns the number of kernels launched
+int launch_force(const Dev& d, int mode, double* out, int as_grad, int fp64, int tpa, cudaStream_t s);
 void launch_kick(const Dev& d, const double* a, double h, cudaStream_t s);
 void launch_kick2(const Dev& d, const double* a, double h, const double* b, double hb, cudaStream_t s);
 void launch_aoa(const Dev& d, double tau, uint32_t s_off, int do_check, int fp64, cudaStream_t s);

@@ -39,52 +39,65 @@ template <> struct Disp<float> {
     __device__ static void get(const Dev& d, const RepParams& P, int i, int j, float& dx, float& dy,
                                float& dz)
     {
-        sdisp(d.pos[i], d.pos[j], P.sclf, dx, dy, dz);
+        sdisp(d.pos[i], d.pos[j], P.sclf, P.sclf_lo, dx, dy, dz);
     }
 };
 
-// gradient on atom i of its bonded terms; evaluated in FP64 in both modes:
-// with k_b ~ 10^3 kcal/mol/A^2 an FP32 bond length would put ~10^-4 kcal/mol/A
-// of error on the force
-template <typename T>
-__device__ void bonded_grad(const Dev& d, const RepParams& P, int i, double& gx, double& gy, double& gz)
+// bonded terms, one thread per term, FP64 in both modes (with k_b ~ 10^3
+// kcal/mol/A^2 an FP32 bond length would put ~10^-4 kcal/mol/A of error on
+// the force); the per-term gradients are gathered per atom afterwards, so
+// every atom sums its terms in a fixed order
+__global__ void k_bonded_terms(Dev d)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < d.nbond) {
+        const int2 ij = d.bond_ij[t];
+        const RepParams& P = d.P[d.rep[ij.x]];
+        double dx, dy, dz;
+        Disp<double>::get(d, P, ij.x, ij.y, dx, dy, dz);
+        const double r = sqrt(dx * dx + dy * dy + dz * dz);
+        const double f = r > 0.0 ? d.bond_k[t] * (r - d.bond_r0[t]) / r : 0.0;
+        d.bterm[3 * t] = f * dx; d.bterm[3 * t + 1] = f * dy; d.bterm[3 * t + 2] = f * dz;
+        return;
+    }
+    const int ta = t - d.nbond;
+    if (ta >= d.nang) return;
+    const int4 a = d.ang[ta];
+    const RepParams& P = d.P[d.rep[a.y]];
+    double ax, ay, az, bx, by, bz;
+    Disp<double>::get(d, P, a.x, a.y, ax, ay, az);
+    Disp<double>::get(d, P, a.z, a.y, bx, by, bz);
+    const double ra = sqrt(ax * ax + ay * ay + az * az), rb = sqrt(bx * bx + by * by + bz * bz);
+    double cth = (ax * bx + ay * by + az * bz) / (ra * rb);
+    cth = fmin(1.0, fmax(-1.0, cth));
+    const double th = acos(cth);
+    const double sth = sin(th);
+    double* o = d.aterm + 6 * (size_t)ta;
+    if (sth < 1e-12) {
+        for (int c = 0; c < 6; ++c) o[c] = 0.0;
+        return;
+    }
+    const double pre = d.ang_k[ta] * (th - d.ang_t0[ta]);
+    const double ia = pre / (ra * sth), ib = pre / (rb * sth);
+    o[0] = (cth * ax / ra - bx / rb) * ia; o[1] = (cth * ay / ra - by / rb) * ia; o[2] = (cth * az / ra - bz / rb) * ia;
+    o[3] = (cth * bx / rb - ax / ra) * ib; o[4] = (cth * by / rb - ay / ra) * ib; o[5] = (cth * bz / rb - az / ra) * ib;
+}
+
+// sum of the bonded gradients on atom i (items in a fixed order)
+__device__ __forceinline__ void bonded_gather(const Dev& d, int i, double& gx, double& gy, double& gz)
 {
     const int b0 = d.bi_off[i], b1 = d.bi_off[i + 1];
     for (int it = b0; it < b1; ++it) {
         const int2 item = d.bitem[it];
         const int kind = item.x & 15, role = item.x >> 4, t = item.y;
         if (kind == 0) {
-            const int2 ij = d.bond_ij[t];
-            const int p = role == 0 ? ij.y : ij.x;
-            T dx, dy, dz;
-            Disp<T>::get(d, P, i, p, dx, dy, dz);
-            const T r = d_sqrt(dx * dx + dy * dy + dz * dz);
-            const T f = r > T(0) ? T(d.bond_k[t]) * (r - T(d.bond_r0[t])) / r : T(0);
-            gx += double(f * dx); gy += double(f * dy); gz += double(f * dz);
+            const double sgn = role == 0 ? 1.0 : -1.0;
+            gx += sgn * d.bterm[3 * t]; gy += sgn * d.bterm[3 * t + 1]; gz += sgn * d.bterm[3 * t + 2];
         } else {
-            const int4 a = d.ang[t];
-            T ax, ay, az, bx, by, bz;
-            Disp<T>::get(d, P, a.x, a.y, ax, ay, az);
-            Disp<T>::get(d, P, a.z, a.y, bx, by, bz);
-            const T ra = d_sqrt(ax * ax + ay * ay + az * az), rb = d_sqrt(bx * bx + by * by + bz * bz);
-            T cth = (ax * bx + ay * by + az * bz) / (ra * rb);
-            cth = cth > T(1) ? T(1) : (cth < T(-1) ? T(-1) : cth);
-            const T th = acos(cth);
-            const T sth = sin(th);
-            if (sth < T(1e-12)) continue;
-            const T pre = T(d.ang_k[t]) * (th - T(d.ang_t0[t]));
-            const T ia = T(1) / (ra * sth), ib = T(1) / (rb * sth);
-            const T gax = (cth * ax / ra - bx / rb) * ia, gay = (cth * ay / ra - by / rb) * ia,
-                    gaz = (cth * az / ra - bz / rb) * ia;
-            const T gbx = (cth * bx / rb - ax / ra) * ib, gby = (cth * by / rb - ay / ra) * ib,
-                    gbz = (cth * bz / rb - az / ra) * ib;
-            if (role == 0) {
-                gx += double(pre * gax); gy += double(pre * gay); gz += double(pre * gaz);
-            } else if (role == 2) {
-                gx += double(pre * gbx); gy += double(pre * gby); gz += double(pre * gbz);
-            } else {
-                gx -= double(pre * (gax + gbx)); gy -= double(pre * (gay + gby)); gz -= double(pre * (gaz + gbz));
-            }
+            const double* o = d.aterm + 6 * (size_t)t;
+            if (role == 0) { gx += o[0]; gy += o[1]; gz += o[2]; }
+            else if (role == 2) { gx += o[3]; gy += o[4]; gz += o[5]; }
+            else { gx -= o[0] + o[3]; gy -= o[1] + o[4]; gz -= o[2] + o[5]; }
         }
     }
 }
@@ -160,7 +173,7 @@ __global__ void __launch_bounds__(256) k_force(Dev d, int lk, double* out, int a
             if (sizeof(T) == 4) {
                 const uint4 pj = d.pos[j];
                 float fx, fy, fz;
-                sdisp(pi, pj, sc, fx, fy, fz);
+                sdisp(pi, pj, sc, P.sclf_lo, fx, fy, fz);
                 dx = T(fx); dy = T(fy); dz = T(fz);
                 qj = T(__uint_as_float(pj.w));
             } else {
@@ -202,7 +215,7 @@ __global__ void __launch_bounds__(256) k_force(Dev d, int lk, double* out, int a
     if (TPA > 1) acc.combine_shfl(TPA);
     if (!live || sub != 0) return;
     double gx = acc.gx(), gy = acc.gy(), gz = acc.gz();
-    if (BONDED) bonded_grad<double>(d, P, i, gx, gy, gz);
+    if (BONDED) bonded_gather(d, i, gx, gy, gz);
     if (as_grad) {
         out[3 * i] = gx; out[3 * i + 1] = gy; out[3 * i + 2] = gz;
     } else {
@@ -211,14 +224,12 @@ __global__ void __launch_bounds__(256) k_force(Dev d, int lk, double* out, int a
     }
 }
 
-template <typename T>
 __global__ void k_bonded(Dev d, double* out, int as_grad)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.N) return;
-    const RepParams& P = d.P[d.rep[i]];
     double gx = 0, gy = 0, gz = 0;
-    bonded_grad<double>(d, P, i, gx, gy, gz);
+    bonded_gather(d, i, gx, gy, gz);
     if (as_grad) {
         out[3 * i] = gx; out[3 * i + 1] = gy; out[3 * i + 2] = gz;
     } else {
@@ -384,24 +395,28 @@ void force_tpa(const Dev& d, int lk, double* out, int as_grad, int tpa, cudaStre
 }
 
 template <typename T>
-void force_t(const Dev& d, int mode, double* out, int as_grad, int tpa, cudaStream_t s)
+int force_t(const Dev& d, int mode, double* out, int as_grad, int tpa, cudaStream_t s)
 {
+    const bool bonded = mode == 0 || mode == 1 || mode == 5;
+    if (bonded && d.nbond + d.nang > 0)
+        k_bonded_terms<<<blocks(d.nbond + d.nang, 128), 128, 0, s>>>(d);
+    const int nk = (bonded && d.nbond + d.nang > 0) ? 2 : 1;
     switch (mode) {
     case 0: force_tpa<T, W_FULL, true>(d, L_FULL, out, as_grad, tpa, s); break;
-    case 1: k_bonded<T><<<blocks(d.N, 256), 256, 0, s>>>(d, out, as_grad); break;
+    case 1: k_bonded<<<blocks(d.N, 256), 256, 0, s>>>(d, out, as_grad); break;
     case 2: force_tpa<T, W_FULL, false>(d, L_FULL, out, as_grad, tpa, s); break;
     case 3: force_tpa<T, W_SHORT, false>(d, L_SHORT, out, as_grad, tpa, s); break;
     case 4: force_tpa<T, W_LONG, false>(d, L_FULL, out, as_grad, tpa, s); break;
     default: force_tpa<T, W_SHORT, true>(d, L_SHORT, out, as_grad, tpa, s); break;
     }
+    return nk;
 }
 
 }  // namespace
 
-void launch_force(const Dev& d, int mode, double* out, int as_grad, int fp64, int tpa, cudaStream_t s)
+int launch_force(const Dev& d, int mode, double* out, int as_grad, int fp64, int tpa, cudaStream_t s)
 {
-    if (fp64) force_t<double>(d, mode, out, as_grad, tpa, s);
-    else force_t<float>(d, mode, out, as_grad, tpa, s);
+    return fp64 ? force_t<double>(d, mode, out, as_grad, tpa, s) : force_t<float>(d, mode, out, as_grad, tpa, s);
 }
 
 void launch_kick(const Dev& d, const double* a, double h, cudaStream_t s)

@@ -25,7 +25,7 @@ template <> struct JD<float> {
     __device__ static void get(const Dev& d, const RepParams& P, int i, const uint4& pi, int j,
                                float& dx, float& dy, float& dz)
     {
-        sdisp(pi, d.pos[j], P.sclf, dx, dy, dz);
+        sdisp(pi, d.pos[j], P.sclf, P.sclf_lo, dx, dy, dz);
     }
 };
 template <> struct JD<double> {
@@ -354,7 +354,7 @@ __device__ __forceinline__ void cprime_f(const Dev& d, const RepParams& P, int i
         ++k;
         u = draw(P, uint32_t(il), s0, TAG_C, half, 0, k);        // next proposal, overlaps the gathers
         float dx, dy, dz;
-        sdisp(pi, pj, sc, dx, dy, dz);
+        sdisp(pi, pj, sc, P.sclf_lo, dx, dy, dz);
         const float r2 = dx * dx + dy * dy + dz * dz;
         const float r = sqrtf(r2);
         const bool inside = ringM ? (r >= sw && r < rM) : (r >= rM && r < R);
@@ -437,10 +437,12 @@ __global__ void __launch_bounds__(128, MINB) k_vphase_f(Dev d, const double* a, 
                                         : make_float3(0.f, 0.f, 0.f);
                     cprime_f(d, P, i, il, jv, v0, af, float(tau2), s0, half, tl, err);
                 }
-                // FP64 end of the phase: v0 + (tau/2) a + sum of the jumps
+                // FP64 end of the phase: (v0 + (tau/2) a) + sum of the jumps; the
+                // first sum rounds like a B kick, so a phase without jumps is one
                 for (int c = 0; c < 3; ++c) {
                     const double ac = a ? a[3 * i + c] : 0.0;
-                    d.v[3 * i + c] += tau2 * ac + double(c == 0 ? jv.x : (c == 1 ? jv.y : jv.z));
+                    const double vn = fma(tau2, ac, d.v[3 * i + c]);
+                    d.v[3 * i + c] = vn + double(c == 0 ? jv.x : (c == 1 ? jv.y : jv.z));
                 }
             } else if (j_on) {
                 double v[3] = {d.v[3 * i], d.v[3 * i + 1], d.v[3 * i + 2]};

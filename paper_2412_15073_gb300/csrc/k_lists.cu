@@ -41,7 +41,7 @@ __device__ __forceinline__ double dist2_fp64(const double* X, int i, int j, cons
 __device__ __forceinline__ float sdist2(const Dev& d, const RepParams& P, const uint4& pi, int j)
 {
     float dx, dy, dz;
-    sdisp(pi, d.pos[j], P.sclf, dx, dy, dz);
+    sdisp(pi, d.pos[j], P.sclf, P.sclf_lo, dx, dy, dz);
     return dx * dx + dy * dy + dz * dz;
 }
 
@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(OUTER_THREADS) k_outer_cells(Dev d, int exact)
                                 ok = dist2_fp64(d.xo, i, j, P) < ro * ro;
                             } else {
                                 float dx, dy, dz;
-                                sdisp(pi, cpos[k], P.sclf, dx, dy, dz);
+                                sdisp(pi, cpos[k], P.sclf, P.sclf_lo, dx, dy, dz);
                                 ok = dx * dx + dy * dy + dz * dz < r2of;
                             }
                             if (ok) ok = !is_excluded(d, i, j);
@@ -355,7 +355,7 @@ __global__ void k_inner_lists(Dev d, int kinds, int exact, int late)
     if (!late && !d.flags[2 * r]) return;
     const RepParams& P = d.P[r];
     const uint4 pi = d.pos[i];
-    const double qi = d.q[i];
+    const float qi = __uint_as_float(pi.w);
     const int ti = d.type[i];
     const double sk = P.skin;
     const double lo_m = fmax(0.0, P.sw - sk), hi_m = P.rM + sk;
@@ -380,7 +380,8 @@ __global__ void k_inner_lists(Dev d, int kinds, int exact, int late)
         if (k < n_o) {
             const int j = (int)orow[k];
             entry = (uint32_t)j;
-            const bool qq = qi * d.q[j] != 0.0;
+            const uint4 pj = d.pos[j];
+            const bool qq = qi != 0.f && __uint_as_float(pj.w) != 0.f;
             const bool ljp = lj_on && P.lj[ti * MAX_TYPES + d.type[j]].on;
             if (exact) {
                 const double r2 = dist2_fp64(d.xb, i, j, P);
@@ -390,7 +391,9 @@ __global__ void k_inner_lists(Dev d, int kinds, int exact, int late)
                 m[L_RL] = ringl_on && qq && r2 >= b2[2] && r2 < b2[3];
                 m[L_LJ] = ljp && r2 >= b2[4] && r2 < b2[5];
             } else {
-                const float r2 = sdist2(d, P, pi, j);
+                float dx, dy, dz;
+                sdisp(pi, pj, P.sclf, P.sclf_lo, dx, dy, dz);
+                const float r2 = dx * dx + dy * dy + dz * dz;
                 m[L_SHORT] = r2 < r2s;
                 m[L_FULL] = r2 < r2f;
                 // ring and LJ membership decides which partner a jump picks:

@@ -222,6 +222,7 @@ RepParams make_params(const md_ctx* ctx, const RepHost& h, int r, int atom_off, 
     P.scl = h.box / 4294967296.0;
     P.inv_scl = 4294967296.0 / h.box;
     P.sclf = float(P.scl);
+    P.sclf_lo = float(P.scl - double(P.sclf));
     P.R = s.r_cut; P.rc = s.r_split; P.h = s.h_switch; P.sw = s.r_split - s.h_switch;
     P.one_ring = !(s.r_mid > P.sw && s.r_mid < P.R);
     P.rM = P.one_ring ? P.sw : s.r_mid;
@@ -535,6 +536,9 @@ int commit(md_ctx* ctx)
     AL(dLMf, N); AL(dLLf, N); AL(dLLJf, N);
     AL(dbitem, bitem.size()); AL(dbij, bond_ij.size()); AL(dbk, bond_k.size()); AL(dbr0, bond_r0.size());
     AL(dang, ang.size()); AL(dak, ang_k.size()); AL(dat0, ang_t0.size());
+    AL(d.bterm, 3 * bond_k.size()); AL(d.aterm, 6 * ang_k.size());
+    d.nbond = (int)bond_k.size();
+    d.nang = (int)ang_k.size();
     AL(d.x, 3 * N); AL(d.v, 3 * N); AL(d.xb, 3 * N); AL(d.xo, 3 * N);
     AL(d.a0, 3 * N); AL(d.ab, 3 * N); AL(d.as, 3 * N); AL(d.al, 3 * N); AL(d.gout, 3 * N);
     AL(d.pos, N);
@@ -720,7 +724,8 @@ int tpa_for(md_ctx* ctx, int mode)
 void force(md_ctx* ctx, int mode, double* out)
 {
     const int t = mode == 1 ? 1 : tpa_for(ctx, mode);
-    Prof p(ctx, mode == 1 ? 1 : 0, 1);
+    const bool bonded = mode == 0 || mode == 1 || mode == 5;
+    Prof p(ctx, mode == 1 ? 1 : 0, (bonded && ctx->d.nbond + ctx->d.nang > 0) ? 2 : 1);
     launch_force(ctx->d, mode, out, 0, ctx->fp64, t, ctx->s);
 }
 
