@@ -198,6 +198,45 @@ int64_t md_get_events(md_ctx* ctx, int replica, int64_t* host_out6, int64_t cap,
 int md_profile(md_ctx* ctx, int enable, int reset, double* ms_out, int64_t* groups_out,
                int64_t* launches_out);
 
+/* Nonbonded gradient without allocation.
+ *
+ * The paper has no counterpart: this is a service entry point for callers
+ * that cannot allocate device memory. Examples are a host framework whose own
+ * allocator has reserved the GPU's memory and forbids other allocations, and
+ * a real-time loop that cannot afford the device-wide synchronisation that
+ * cudaMalloc / cudaFree imply. Such callers pass their own device arrays for
+ * inputs and output; the call itself allocates nothing (no cudaMalloc,
+ * cudaFree or allocating library routine).
+ *
+ * It computes, for one periodic cubic system, the gradient of the LJ + DSF
+ * pair potential with weight 0 full, 1 short (chi U), 2 long ((1 - chi) U),
+ * the same quantity as md_gradient modes 2, 3 and 4, in FP64, from a cell
+ * grid built on every call. Pairs whose d_mol entries are equal are excluded
+ * (d_mol may be NULL: no exclusions).
+ *   d_x (3n doubles, A), d_charge (n doubles, e), d_type (n ints), d_mol
+ *   (n ints or NULL), d_grad (3n doubles, output): device pointers of the
+ *   current device; lj_eps, lj_sigma: host arrays of n_types^2 doubles.
+ *   r_cut, r_split, h_switch, dsf_alpha: as in md_system; box >= 2 r_cut.
+ *   cuda_stream: the stream the kernels run on (NULL = default stream).
+ * Returns MD_OK or MD_EINVAL (null pointer, n_atoms outside
+ * [1, MD_NOALLOC_MAX_ATOMS], more than MD_NOALLOC_MAX_CELLS cells of edge
+ * >= r_cut, bad parameters) or MD_ECUDA; the message is md_last_error(NULL).
+ *
+ * Scratch: one static device array (about 1.4 MB, every GPU that loads the
+ * library holds it until the process exits) shared by all calls. It keeps the
+ * last call's contents; each call clears what must start at zero. Calls that
+ * overlap on the GPU (different streams, or different host threads on the
+ * same device) race on it and must be serialised by the caller. The first
+ * call on a device looks up the array's device address with
+ * cudaGetSymbolAddress (once per device, with that device current); make that
+ * first call before any stream capture. */
+#define MD_NOALLOC_MAX_ATOMS 131072
+#define MD_NOALLOC_MAX_CELLS 32768
+int md_nb_gradient_noalloc(const double* d_x, const double* d_charge, const int* d_type, const int* d_mol,
+                           int n_atoms, double box, int n_types, const double* lj_eps, const double* lj_sigma,
+                           double r_cut, double r_split, double h_switch, double dsf_alpha, int weight,
+                           double* d_grad, void* cuda_stream);
+
 /* Release every device buffer and the context. */
 int md_finalize(md_ctx* ctx);
 

@@ -27,7 +27,7 @@ ERRORS = {-1: "MD_EINVAL", -2: "MD_ECUDA", -3: "MD_EOVERFLOW", -4: "MD_EBOUND",
 SYMBOLS = ["md_init", "md_set_system", "md_set_state", "md_step_baoab", "md_step_baoab_respa",
            "md_step_baoab_respa1", "md_step_jump", "md_step_jump_respa", "md_step_jump_respa1",
            "md_observables", "md_get_state", "md_gradient", "md_run_phase", "md_get_list",
-           "md_get_events", "md_profile", "md_finalize", "md_last_error"]
+           "md_get_events", "md_profile", "md_nb_gradient_noalloc", "md_finalize", "md_last_error"]
 
 
 class MDError(RuntimeError):
@@ -97,6 +97,7 @@ def load_library(path: str = LIB_PATH):
     L.md_get_events.restype = i64
     L.md_get_events.argtypes = [vp, i, vp, i64, i]
     L.md_profile.argtypes = [vp, i, i, vp, vp, vp]
+    L.md_nb_gradient_noalloc.argtypes = [vp, vp, vp, vp, i, d, i, vp, vp, d, d, d, d, i, vp, vp]
     L.md_finalize.argtypes = [vp]
     L.md_last_error.restype = C.c_char_p
     L.md_last_error.argtypes = [vp]

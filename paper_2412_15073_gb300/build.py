@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libmdjump.so")
 BUILD_DIR = os.path.join(HERE, "_build")
-SOURCES = ["md_api.cu", "k_lists.cu", "k_force.cu", "k_jump.cu"]
+SOURCES = ["md_api.cu", "k_lists.cu", "k_force.cu", "k_jump.cu", "noalloc.cu"]
 HEADERS = ["common.cuh", "engine.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",

@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -137,6 +138,16 @@ struct md_ctx {
 };
 
 static std::string g_init_msg = "no error";
+static std::mutex g_msg_mutex;
+
+namespace mdj {
+// message of the last failed call that has no context (md_init, the no-allocation entry)
+void set_global_error(const std::string& msg)
+{
+    std::lock_guard<std::mutex> lock(g_msg_mutex);
+    g_init_msg = msg;
+}
+}
 
 #define FAIL(code, ...)                                                   \
     do {                                                                  \
