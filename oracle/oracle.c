@@ -415,7 +415,7 @@ void or_bounds(const or_sys* s, double* out3, double* LM, double* LL, double* LL
 /* jump lists (Sec. 3.1 remark: middle and long neighbour lists with counts */
 /* N_M(i), N_L(i); Sec. 3.2: LJ partners). Membership by distance at the    */
 /* build positions widened by the skin. Order: by (cell of j at the last    */
-/* outer rebuild, j) on the grid of n_c = floor(L / (r_E + skin_outer))     */
+/* outer rebuild, j) on the grid of n_c = floor(2 L / (r_E + skin_outer))   */
 /* cells per edge. An outer rebuild happens when some atom moved more than  */
 /* (skin_outer - skin)/2 since the last one; it only refreshes the cells    */
 /* that order the lists.                                                    */
@@ -1180,7 +1180,7 @@ or_sys* or_create(int n, const or_params* p,
     s->LLJ = (double*)malloc(sizeof(double) * (size_t)n);
     compute_bounds(s);
     if (s->p.skin_outer < s->p.skin) s->p.skin_outer = s->p.skin;
-    int nc = (int)floor(s->L / (s->p.r_cut + s->p.skin_outer));
+    int nc = (int)floor(2.0 * s->L / (s->p.r_cut + s->p.skin_outer));
     s->ncell = nc < 1 ? 1 : nc;
     s->cellm = (int*)malloc(sizeof(int) * (size_t)n);
     s->xo = (double*)malloc(sizeof(double) * n3);

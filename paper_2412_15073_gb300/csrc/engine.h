@@ -84,9 +84,11 @@ void launch_advance(const Dev& d, long long nsteps, cudaStream_t s);
 
 // ---- jumps (k_jump.cu) --------------------------------------------------------------
 // order 0: C' then J' (first half of a step), 1: J' then C' (second half)
-// variant: occupancy target of the mixed-mode kernel (0: 1 block/SM bound,
-// 1: 4, 2: 5, 3: 6 blocks of 128 threads); every variant computes the same values
-constexpr int NVPHASE_VARIANTS = 4;
+// variant of the mixed-mode kernel: occupancy targets of 1, 4, 5, 6 blocks of
+// 128 threads (0-3), and the same with deferred G~ draws (4-7: an accepted
+// proposal waits until 8 lanes of the warp wait, then they draw together).
+// Every variant computes the same values.
+constexpr int NVPHASE_VARIANTS = 8;
 void launch_vphase(const Dev& d, const double* a, double tau2, uint32_t s_off, int half, int order,
                    int doC, int doJ, int fp64, int variant, cudaStream_t s);
 // same with an absolute stream index s0 (md_run_phase)

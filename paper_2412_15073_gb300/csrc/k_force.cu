@@ -35,13 +35,6 @@ template <> struct Disp<double> {
         dx = mimg(a.x - b.x, P); dy = mimg(a.y - b.y, P); dz = mimg(a.z - b.z, P);
     }
 };
-template <> struct Disp<float> {
-    __device__ static void get(const Dev& d, const RepParams& P, int i, int j, float& dx, float& dy,
-                               float& dz)
-    {
-        sdisp(d.pos[i], d.pos[j], P.sclf, P.sclf_lo, dx, dy, dz);
-    }
-};
 
 // bonded terms, one thread per term, FP64 in both modes (with k_b ~ 10^3
 // kcal/mol/A^2 an FP32 bond length would put ~10^-4 kcal/mol/A of error on

@@ -304,6 +304,7 @@ __device__ __noinline__ float sample_gtilde_f(const RepParams& P, uint32_t il, u
 // C' for atom i in FP32 (Algorithm 4, adaptive or constant eps, two rings).
 // The Philox block of proposal k+1 is computed while the partner of proposal
 // k is being fetched.
+template <bool DEFER>
 __device__ __forceinline__ void cprime_f(const Dev& d, const RepParams& P, int i, int il, float3& jv,
                                          const float3 v0, const float3 a, float T2, uint32_t s0, int half,
                                          Tally& tl, uint32_t& err)
@@ -328,7 +329,34 @@ __device__ __forceinline__ void cprime_f(const Dev& d, const RepParams& P, int i
     float vx = v0.x + jv.x, vy = v0.y + jv.y, vz = v0.z + jv.z;
     uint32_t k = 0;
     U4 u = draw(P, uint32_t(il), s0, TAG_C, half, 0, 0);
+    // accepted proposal waiting for its G~ draw (DEFER: draws are made
+    // together once 8 lanes wait or only waiting lanes remain)
+    bool pending = false;
+    float pgx = 0.f, pgy = 0.f, pgz = 0.f, pgn = 1.f, peta = 0.f, peps = 0.f;
+    uint32_t pk = 0;
+    int pJ = 0;
     for (;;) {
+        if (DEFER) {
+            const unsigned act = __activemask();
+            const unsigned waiting = __ballot_sync(act, pending);
+            if (__popc(waiting) >= 8 || waiting == act) {
+                if (pending) {
+                    int att;
+                    bool ok;
+                    const float G = sample_gtilde_f(P, uint32_t(il), s0, half, pk, peta, &att, &ok);
+                    tl.satt += att;
+                    if (!ok) err |= F_LIMIT;
+                    const float coef = 2.f * peps / (sbm * (1.f + peps * peps)) * (peta + G) / pgn;
+                    jv.x -= coef * pgx; jv.y -= coef * pgy; jv.z -= coef * pgz;
+                    vx -= coef * pgx; vy -= coef * pgy; vz -= coef * pgz;
+                    tl.cacc++;
+                    log_event(d, (long long)s0, half, int(TAG_C), d.rep[i], il, pk, pJ - P.atom_off);
+                    pending = false;
+                }
+                continue;
+            }
+            if (pending) continue;
+        }
         const float s = T2 - t;
         const float vv = vx * vx + vy * vy + vz * vz;
         const float va = vx * a.x + vy * a.y + vz * a.z;
@@ -390,7 +418,10 @@ __device__ __forceinline__ void cprime_f(const Dev& d, const RepParams& P, int i
                     acc = U <= p;
                     if (p > 1.f) err |= F_BOUND;
                 }
-                if (acc) {
+                if (acc && DEFER) {
+                    pending = true;
+                    pgx = gx; pgy = gy; pgz = gz; pgn = gn; peta = eta; peps = eps; pk = kk; pJ = J;
+                } else if (acc) {
                     int att;
                     bool ok;
                     const float G = sample_gtilde_f(P, uint32_t(il), s0, half, kk, eta, &att, &ok);
@@ -410,7 +441,7 @@ __device__ __forceinline__ void cprime_f(const Dev& d, const RepParams& P, int i
 
 // mixed-mode velocity phase; threads visit atoms in the order vorder (atoms
 // grouped by expected jump rate so that the lanes of a warp do similar work)
-template <int MINB>
+template <int MINB, bool DEFER>
 __global__ void __launch_bounds__(128, MINB) k_vphase_f(Dev d, const double* a, double tau2, uint32_t s_off, int s_abs,
                                                         int half, int order, int doC, int doJ)
 {
@@ -435,7 +466,7 @@ __global__ void __launch_bounds__(128, MINB) k_vphase_f(Dev d, const double* a, 
                     const float3 v0 = make_float3(float(d.v[3 * i]), float(d.v[3 * i + 1]), float(d.v[3 * i + 2]));
                     const float3 af = a ? make_float3(float(a[3 * i]), float(a[3 * i + 1]), float(a[3 * i + 2]))
                                         : make_float3(0.f, 0.f, 0.f);
-                    cprime_f(d, P, i, il, jv, v0, af, float(tau2), s0, half, tl, err);
+                    cprime_f<DEFER>(d, P, i, il, jv, v0, af, float(tau2), s0, half, tl, err);
                 }
                 // FP64 end of the phase: (v0 + (tau/2) a) + sum of the jumps; the
                 // first sum rounds like a B kick, so a phase without jumps is one
@@ -520,10 +551,14 @@ static void vphase_any(const Dev& d, const double* a, double tau2, uint32_t s, i
         return;
     }
     switch (variant) {
-    case 1: k_vphase_f<4><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, order, doC, doJ); break;
-    case 2: k_vphase_f<5><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, order, doC, doJ); break;
-    case 3: k_vphase_f<6><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, order, doC, doJ); break;
-    default: k_vphase_f<1><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, order, doC, doJ); break;
+    case 1: k_vphase_f<4, false><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, order, doC, doJ); break;
+    case 2: k_vphase_f<5, false><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, order, doC, doJ); break;
+    case 3: k_vphase_f<6, false><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, order, doC, doJ); break;
+    case 4: k_vphase_f<1, true><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, order, doC, doJ); break;
+    case 5: k_vphase_f<4, true><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, order, doC, doJ); break;
+    case 6: k_vphase_f<5, true><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, order, doC, doJ); break;
+    case 7: k_vphase_f<6, true><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, order, doC, doJ); break;
+    default: k_vphase_f<1, false><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, order, doC, doJ); break;
     }
 }
 

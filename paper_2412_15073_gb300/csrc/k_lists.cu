@@ -38,20 +38,6 @@ __device__ __forceinline__ double dist2_fp64(const double* X, int i, int j, cons
     return dx * dx + dy * dy + dz * dz;
 }
 
-__device__ __forceinline__ float sdist2(const Dev& d, const RepParams& P, const uint4& pi, int j)
-{
-    float dx, dy, dz;
-    sdisp(pi, d.pos[j], P.sclf, P.sclf_lo, dx, dy, dz);
-    return dx * dx + dy * dy + dz * dz;
-}
-
-__device__ __forceinline__ bool is_excluded(const Dev& d, int i, int j)
-{
-    const int e0 = d.ex_off[i], e1 = d.ex_off[i + 1];
-    for (int e = e0; e < e1; ++e)
-        if (d.ex_idx[e] == j) return true;
-    return false;
-}
 
 // ---- displacement check -------------------------------------------------------
 __global__ void k_check(Dev d, int force_inner, int force_outer)
@@ -191,162 +177,120 @@ __global__ void k_cell_sort(Dev d)
     if (lane == 0) d.cell_cnt[c] = 0;
 }
 
-// one block per cell: the candidates of the (sorted) neighbour cells are staged
-// in shared memory once per cell, in (cell, j) order, and every warp scans them
-// for one atom of the cell at a time. Neighbour cells whose box lies farther
-// than r_E + skin_outer from the atom are skipped.
-constexpr int OCAP = 4096;                  // staged candidates per chunk
-constexpr int OUTER_THREADS = 256;
-constexpr int OUTER_SMEM = OCAP * (16 + 4) + 1024 * 4;
+// one warp per group of up to 32 atoms of a cell (one atom per lane). The
+// candidates of each neighbour cell (cells visited in increasing linear index,
+// atoms of a cell in increasing index) are loaded 32 at a time, one per lane,
+// and passed to every lane by shuffles; each lane appends its matches to its
+// own list, which therefore comes out in (cell, j) order. Cells have an edge
+// of at least (r_E + skin_outer)/2, so the neighbourhood is +-2 cells per axis.
+constexpr int OUTER_WARPS = 4;
+constexpr int OUTER_GROUPS = 2;                           // warps per cell; each loops over its groups
 
-__global__ void __launch_bounds__(OUTER_THREADS) k_outer_cells(Dev d, int exact)
+__global__ void __launch_bounds__(32 * OUTER_WARPS) k_outer_cells(Dev d, int exact)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    uint4* cpos = (uint4*)smem;
-    int* cidx = (int*)(cpos + OCAP);
-    int* acnt = cidx + OCAP;                // running list length of each atom of the cell
-    __shared__ int nb[27], nboff[27], nbstart[27], nbsize[27], nbpre[28];
-    __shared__ int nnb;
-    const int c = blockIdx.x;
+    __shared__ int nbs[OUTER_WARPS][125];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int task = blockIdx.x * OUTER_WARPS + w;       // (cell, first group of 32 atoms)
+    const int c = task / OUTER_GROUPS, group0 = task % OUTER_GROUPS;
     if (c >= d.total_cells) return;
     const int r = d.cell_rep[c];
     if (r < 0 || !d.flags[2 * r + 1]) return;
+    const int s_i = d.cell_start[c], e_i = d.cell_start[c + 1];
+    const int natoms = e_i - s_i;
+    if (group0 == 0 && natoms > 1024 && lane == 0) { atomicOr(&d.err[r], F_OVERFLOW); atomicOr(&d.ovf[r], 1u << 6); }
+    const int nlim = min(natoms, 1024);
+    if (group0 * 32 >= nlim) return;
     const RepParams& P = d.P[r];
     const int nc = P.nc;
     const int lin = c - P.cell_off;
     const int cc[3] = {lin % nc, (lin / nc) % nc, lin / (nc * nc)};
-    const int nax = nc >= 3 ? 3 : nc;
+    const int nax = nc >= 5 ? 5 : nc;
     const int ncell = nax * nax * nax;
-    const int s_i = d.cell_start[c], e_i = d.cell_start[c + 1];
-    const int natoms = e_i - s_i;
-    if (natoms > 1024) {
-        if (threadIdx.x == 0) { atomicOr(&d.err[r], F_OVERFLOW); atomicOr(&d.ovf[r], 1u << 6); }
-        return;
-    }
-    if (natoms == 0) return;
-    // neighbour cells in increasing linear index, with their offset code
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
-        int mine = 0, off = 0;
-        if (lane < ncell) {
-            const int q[3] = {lane % nax, (lane / nax) % nax, lane / (nax * nax)};
-            int cv[3];
+    // neighbour cells in increasing linear index
+    for (int t = lane; t < ncell; t += 32) {
+        const int q[3] = {t % nax, (t / nax) % nax, t / (nax * nax)};
+        int cv[3];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) cv[a] = nc >= 3 ? (cc[a] + q[a] - 1 + nc) % nc : q[a];
-            mine = (cv[2] * nc + cv[1]) * nc + cv[0];
-            off = nc >= 3 ? (q[0] | (q[1] << 2) | (q[2] << 4)) : 0x3f;   // 0x3f: no pruning
-            nb[lane] = mine;
-        }
-        __syncwarp();
-        int rank = 0;
-        for (int m = 0; m < ncell; ++m) rank += nb[m] < mine;
-        __syncwarp();
-        if (lane < ncell) {
-            nb[rank] = mine;
-            nboff[rank] = off;
-        }
-        __syncwarp();
-        if (lane < ncell) {
-            const int gc = P.cell_off + nb[lane];
-            nbstart[lane] = d.cell_start[gc];
-            nbsize[lane] = d.cell_start[gc + 1] - d.cell_start[gc];
-        }
-        __syncwarp();
-        if (lane == 0) {
-            int acc = 0;
-            for (int m = 0; m < ncell; ++m) { nbpre[m] = acc; acc += nbsize[m]; }
-            nbpre[ncell] = acc;
-            nnb = ncell;
-        }
+        for (int a = 0; a < 3; ++a) cv[a] = nc >= 5 ? (cc[a] + q[a] - 2 + nc) % nc : q[a];
+        nbs[w][t] = (cv[2] * nc + cv[1]) * nc + cv[0];
     }
-    for (int a = threadIdx.x; a < natoms; a += blockDim.x) acnt[a] = 0;
-    __syncthreads();
-    const int total = nbpre[nnb];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncwarp();
+    int mine[4], rk[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int t = lane + 32 * u;
+        mine[u] = t < ncell ? nbs[w][t] : 0;
+        rk[u] = 0;
+        if (t < ncell)
+            for (int m = 0; m < ncell; ++m) rk[u] += nbs[w][m] < mine[u];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+        if (lane + 32 * u < ncell) nbs[w][rk[u]] = mine[u];
+    __syncwarp();
+    for (int group = group0; group * 32 < nlim; group += OUTER_GROUPS) {
+    // this lane's atom
+    const int ai = group * 32 + lane;
+    const bool live = ai < natoms;
+    const int i = live ? d.cell_atoms[s_i + ai] : -1;
+    const uint4 pi = live ? d.pos[i] : make_uint4(0, 0, 0, 0);
+    int ex[4] = {-1, -1, -1, -1};
+    int e0 = 0, e1 = 0;
+    if (live) {
+        e0 = d.ex_off[i];
+        e1 = d.ex_off[i + 1];
+        for (int e = e0; e < e1 && e - e0 < 4; ++e) ex[e - e0] = d.ex_idx[e];
+    }
     const double ro = P.R + P.skin_o;
     const float r2of = float(ro * ro * (1.0 + 4e-6));
-    const float rof = float(ro * (1.0 + 2e-6));
-    const float csf = float(P.cs);
-    for (int base = 0; base < total; base += OCAP) {
-        const int len = min(OCAP, total - base);
-        // stage candidates [base, base + len) in (cell, j) order
-        for (int k = threadIdx.x; k < len; k += blockDim.x) {
-            const int g = base + k;
-            int m = 0;
-            while (nbpre[m + 1] <= g) ++m;
-            const int j = d.cell_atoms[nbstart[m] + (g - nbpre[m])];
-            cidx[k] = j;
-            cpos[k] = d.pos[j];
-        }
-        __syncthreads();
-        for (int a = w; a < natoms; a += nw) {
-            const int i = d.cell_atoms[s_i + a];
-            const uint4 pi = d.pos[i];
-            // position of i inside its cell, per axis (for the pruning of far cells)
-            float f3[3];
-            {
-                const double3 xo = ld3(d.xo, i);
-                const double xx[3] = {xo.x, xo.y, xo.z};
-#pragma unroll
-                for (int q = 0; q < 3; ++q) f3[q] = float(xx[q] - cc[q] * P.cs);
-            }
-            uint32_t* row = d.olist + (size_t)i * d.ocap;
-            int cnt = acnt[a];
-            for (int m = 0; m < nnb; ++m) {
-                const int lo = max(nbpre[m], base) - base, hi = min(nbpre[m + 1], base + len) - base;
-                if (lo >= hi) continue;
-                const int oc = nboff[m];
-                if (oc != 0x3f) {
-                    float dd2 = 0.f;
-#pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                        const int o = (oc >> (2 * q)) & 3;      // 0: cell below, 1: same, 2: above
-                        const float t = o == 0 ? f3[q] : (o == 2 ? csf - f3[q] : 0.f);
-                        dd2 += t > 0.f ? t * t : 0.f;
-                    }
-                    if (dd2 > rof * rof) continue;
+    const double r2o = ro * ro;
+    uint32_t* row = live ? d.olist + (size_t)i * d.ocap : nullptr;
+    int cnt = 0;
+    for (int m = 0; m < ncell; ++m) {
+        const int gc = P.cell_off + nbs[w][m];
+        const int cs0 = d.cell_start[gc], cs1 = d.cell_start[gc + 1];
+        for (int base = cs0; base < cs1; base += 32) {
+            const int nh = min(32, cs1 - base);
+            const int cand = lane < nh ? d.cell_atoms[base + lane] : 0;
+            const uint4 cp = lane < nh ? d.pos[cand] : make_uint4(0, 0, 0, 0);
+            for (int t = 0; t < nh; ++t) {
+                const int j = __shfl_sync(0xffffffffu, cand, t);
+                uint4 pj;
+                pj.x = __shfl_sync(0xffffffffu, cp.x, t);
+                pj.y = __shfl_sync(0xffffffffu, cp.y, t);
+                pj.z = __shfl_sync(0xffffffffu, cp.z, t);
+                if (!live || j == i) continue;
+                bool ok;
+                if (exact) {
+                    ok = dist2_fp64(d.xo, i, j, P) < r2o;
+                } else {
+                    float dx, dy, dz;
+                    sdisp(pi, pj, P.sclf, P.sclf_lo, dx, dy, dz);
+                    ok = dx * dx + dy * dy + dz * dz < r2of;
                 }
-                for (int k0 = lo; k0 < hi; k0 += 32) {
-                    const int k = k0 + lane;
-                    bool ok = false;
-                    int j = -1;
-                    if (k < hi) {
-                        j = cidx[k];
-                        if (j != i) {
-                            if (exact) {
-                                ok = dist2_fp64(d.xo, i, j, P) < ro * ro;
-                            } else {
-                                float dx, dy, dz;
-                                sdisp(pi, cpos[k], P.sclf, P.sclf_lo, dx, dy, dz);
-                                ok = dx * dx + dy * dy + dz * dz < r2of;
-                            }
-                            if (ok) ok = !is_excluded(d, i, j);
-                        }
-                    }
-                    const unsigned b = __ballot_sync(0xffffffffu, ok);
-                    const int pos = cnt + __popc(b & ((1u << lane) - 1u));
-                    if (ok && pos < d.ocap) row[pos] = (uint32_t)j;
-                    cnt += __popc(b);
-                }
+                if (!ok) continue;
+                bool exc = j == ex[0] || j == ex[1] || j == ex[2] || j == ex[3];
+                if (!exc && e1 - e0 > 4)
+                    for (int e = e0 + 4; e < e1; ++e) exc |= d.ex_idx[e] == j;
+                if (exc) continue;
+                if (cnt < d.ocap) row[cnt] = (uint32_t)j;
+                ++cnt;
             }
-            if (lane == 0) acnt[a] = cnt;
-            __syncwarp();
         }
-        __syncthreads();
     }
-    for (int a = threadIdx.x; a < natoms; a += blockDim.x) {
-        const int i = d.cell_atoms[s_i + a];
-        const int cnt = acnt[a];
+    if (live) {
         d.ocnt[i] = cnt;
         if (cnt > d.ocap) {
             atomicOr(&d.err[r], F_OVERFLOW);
             atomicOr(&d.ovf[r], 1u << 5);
         }
     }
+    }
 }
 
-// one warp per atom: filter the outer list into the inner lists
-__global__ void k_inner_lists(Dev d, int kinds, int exact, int late)
+// one warp per atom: filter the outer list into the inner lists, keeping its order
+__global__ void __launch_bounds__(32 * WARPS) k_inner_lists(Dev d, int kinds, int exact, int late)
 {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = blockIdx.x * WARPS + w;
@@ -357,38 +301,44 @@ __global__ void k_inner_lists(Dev d, int kinds, int exact, int late)
     const uint4 pi = d.pos[i];
     const float qi = __uint_as_float(pi.w);
     const int ti = d.type[i];
+    const bool want_s = kinds & (1 << L_SHORT), want_f = kinds & (1 << L_FULL);
+    const bool want_m = (kinds & (1 << L_RM)) && P.rings_on && !P.one_ring && qi != 0.f;
+    const bool want_l = (kinds & (1 << L_RL)) && P.rings_on && P.rM < P.R && qi != 0.f;
+    const bool want_j = (kinds & (1 << L_LJ)) && P.lj_on;
+    const bool shells = want_m || want_l || want_j;
+    unsigned ljmask = 0;
+    if (want_j)
+        for (int t = 0; t < P.ntypes; ++t) ljmask |= (P.lj[ti * MAX_TYPES + t].on ? 1u : 0u) << t;
     const double sk = P.skin;
     const double lo_m = fmax(0.0, P.sw - sk), hi_m = P.rM + sk;
     const double lo_l = P.rM - sk, hi_l = P.R + sk;
     const double lo_j = fmax(0.0, P.sw - sk), hi_j = P.R + sk;
-    // ring and LJ shell limits (squared), FP64 and FP32 copies
     const double b2[6] = {lo_m * lo_m, hi_m * hi_m, lo_l * lo_l, hi_l * hi_l, lo_j * lo_j, hi_j * hi_j};
     float b2f[6];
 #pragma unroll
     for (int t = 0; t < 6; ++t) b2f[t] = float(b2[t]);
     const float r2s = float((P.rc + sk) * (P.rc + sk)), r2f = float((P.R + sk) * (P.R + sk));
-    const bool ringm_on = P.rings_on && !P.one_ring;
-    const bool ringl_on = P.rings_on && P.rM < P.R;
-    const bool lj_on = P.lj_on;
+    uint32_t* rows[NKIND];
+#pragma unroll
+    for (int k = 0; k < NKIND; ++k) rows[k] = d.list[k] + (size_t)i * d.lcap[k];
     int cnt[NKIND] = {0, 0, 0, 0, 0};
-    const int n_o = d.ocnt[i] < d.ocap ? d.ocnt[i] : d.ocap;
+    const int n_o = min(d.ocnt[i], d.ocap);
     const uint32_t* orow = d.olist + (size_t)i * d.ocap;
     for (int base = 0; base < n_o; base += 32) {
         const int k = base + lane;
         bool m[NKIND] = {false, false, false, false, false};
-        uint32_t entry = 0;
+        uint32_t j = 0;
         if (k < n_o) {
-            const int j = (int)orow[k];
-            entry = (uint32_t)j;
+            j = orow[k];
             const uint4 pj = d.pos[j];
-            const bool qq = qi != 0.f && __uint_as_float(pj.w) != 0.f;
-            const bool ljp = lj_on && P.lj[ti * MAX_TYPES + d.type[j]].on;
+            const bool qq = __uint_as_float(pj.w) != 0.f;
+            const bool ljp = want_j && ((ljmask >> d.type[j]) & 1u);
             if (exact) {
-                const double r2 = dist2_fp64(d.xb, i, j, P);
+                const double r2 = dist2_fp64(d.xb, i, (int)j, P);
                 m[L_SHORT] = r2 < double(r2s);
                 m[L_FULL] = r2 < double(r2f);
-                m[L_RM] = ringm_on && qq && r2 >= b2[0] && r2 < b2[1];
-                m[L_RL] = ringl_on && qq && r2 >= b2[2] && r2 < b2[3];
+                m[L_RM] = want_m && qq && r2 >= b2[0] && r2 < b2[1];
+                m[L_RL] = want_l && qq && r2 >= b2[2] && r2 < b2[3];
                 m[L_LJ] = ljp && r2 >= b2[4] && r2 < b2[5];
             } else {
                 float dx, dy, dz;
@@ -396,32 +346,36 @@ __global__ void k_inner_lists(Dev d, int kinds, int exact, int late)
                 const float r2 = dx * dx + dy * dy + dz * dz;
                 m[L_SHORT] = r2 < r2s;
                 m[L_FULL] = r2 < r2f;
-                // ring and LJ membership decides which partner a jump picks:
-                // within 2e-5 (relative, in r^2) of a shell limit it is decided in FP64
-                bool near = false;
+                if (shells) {
+                    // ring and LJ membership decides which partner a jump picks:
+                    // within 2e-5 (relative, in r^2) of a shell limit it is decided in FP64
+                    bool near = false;
 #pragma unroll
-                for (int t = 0; t < 6; ++t) near |= fabsf(r2 - b2f[t]) < 2e-5f * b2f[t] + 1e-6f;
-                if (near) {
-                    const double r2d = dist2_fp64(d.xb, i, j, P);
-                    m[L_RM] = ringm_on && qq && r2d >= b2[0] && r2d < b2[1];
-                    m[L_RL] = ringl_on && qq && r2d >= b2[2] && r2d < b2[3];
-                    m[L_LJ] = ljp && r2d >= b2[4] && r2d < b2[5];
-                } else {
-                    m[L_RM] = ringm_on && qq && r2 >= b2f[0] && r2 < b2f[1];
-                    m[L_RL] = ringl_on && qq && r2 >= b2f[2] && r2 < b2f[3];
-                    m[L_LJ] = ljp && r2 >= b2f[4] && r2 < b2f[5];
+                    for (int t = 0; t < 6; ++t) near |= fabsf(r2 - b2f[t]) < 2e-5f * b2f[t] + 1e-6f;
+                    if (near) {
+                        const double r2d = dist2_fp64(d.xb, i, (int)j, P);
+                        m[L_RM] = want_m && qq && r2d >= b2[0] && r2d < b2[1];
+                        m[L_RL] = want_l && qq && r2d >= b2[2] && r2d < b2[3];
+                        m[L_LJ] = ljp && r2d >= b2[4] && r2d < b2[5];
+                    } else {
+                        m[L_RM] = want_m && qq && r2 >= b2f[0] && r2 < b2f[1];
+                        m[L_RL] = want_l && qq && r2 >= b2f[2] && r2 < b2f[3];
+                        m[L_LJ] = ljp && r2 >= b2f[4] && r2 < b2f[5];
+                    }
                 }
             }
         }
+        const unsigned below = (1u << lane) - 1u;
 #pragma unroll
         for (int kind = 0; kind < NKIND; ++kind) {
             if (!(kinds & (1 << kind))) continue;
             const unsigned b = __ballot_sync(0xffffffffu, m[kind]);
-            const int pos = cnt[kind] + __popc(b & ((1u << lane) - 1u));
-            if (m[kind] && pos < d.lcap[kind]) d.list[kind][(size_t)i * d.lcap[kind] + pos] = entry;
+            const int pos = cnt[kind] + __popc(b & below);
+            if (m[kind] && pos < d.lcap[kind]) rows[kind][pos] = j;
             cnt[kind] += __popc(b);
         }
     }
+    (void)want_s; (void)want_f;
     if (lane == 0) {
 #pragma unroll
         for (int kind = 0; kind < NKIND; ++kind) {
@@ -461,12 +415,9 @@ void launch_rebuild(const Dev& d, int kinds, int exact, int keep_refs, int exact
     k_cell_scan<<<d.R, 1024, 0, s>>>(d);
     k_cell_fill<<<blocks(d.N, 256), 256, 0, s>>>(d);
     k_cell_sort<<<blocks(d.total_cells, WARPS), 32 * WARPS, 0, s>>>(d);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_outer_cells, cudaFuncAttributeMaxDynamicSharedMemorySize, OUTER_SMEM);
-        attr = true;
-    }
-    k_outer_cells<<<d.total_cells, OUTER_THREADS, OUTER_SMEM, s>>>(d, exact_outer);
+    // OUTER_GROUPS warps per cell, each looping over its groups of 32 atoms
+    const long long tasks = (long long)d.total_cells * OUTER_GROUPS;
+    k_outer_cells<<<(int)((tasks + OUTER_WARPS - 1) / OUTER_WARPS), 32 * OUTER_WARPS, 0, s>>>(d, exact_outer);
     if (kinds) k_inner_lists<<<blocks(d.N, WARPS), 32 * WARPS, 0, s>>>(d, kinds, exact, 0);
     k_flags_clear<<<blocks(d.R, 128), 128, 0, s>>>(d);
 }

@@ -227,7 +227,7 @@ RepParams make_params(const md_ctx* ctx, const RepHost& h, int r, int atom_off, 
     P.L = h.box; P.invL = 1.0 / h.box;
     P.atom_off = atom_off; P.n = h.n;
     const double skin_o = std::max(s.skin, s.skin_outer);
-    P.nc = std::max(1, int(std::floor(h.box / (s.r_cut + skin_o))));
+    P.nc = std::max(1, int(std::floor(2.0 * h.box / (s.r_cut + skin_o))));
     P.cs = h.box / P.nc;
     P.cell_off = cell_off;
     P.scl = h.box / 4294967296.0;
@@ -513,9 +513,9 @@ int commit(md_ctx* ctx)
         rm_lo = std::min(rm_lo, P.sw - sk); rm_hi = std::max(rm_hi, P.rM + sk);
         rl_lo = std::min(rl_lo, P.rM - sk); rj_lo = std::min(rj_lo, P.sw - sk);
     }
-    // visiting order of the velocity phases: atoms grouped by an estimate of
-    // their proposal rate (per-pair bound at the thermal speed plus the
-    // adaptive-eps floor), stable in index inside a group
+    // visiting order of the velocity phases: by replica, then grouped by an
+    // estimate of the proposal rate (per-pair bound at the thermal speed plus
+    // the adaptive-eps floor), stable in index inside a group
     std::vector<int> vorder(N);
     {
         std::vector<double> est(N);
@@ -525,7 +525,9 @@ int commit(md_ctx* ctx)
             est[i] = (LM[i] + LL[i]) * P.beta * vth + 2.0 * std::sqrt(P.beta / mt[i]) / P.eps0 + LLJ[i];
             vorder[i] = i;
         }
-        std::stable_sort(vorder.begin(), vorder.end(), [&](int x, int y) { return est[x] > est[y]; });
+        std::stable_sort(vorder.begin(), vorder.end(), [&](int x, int y) {
+            return rep[x] != rep[y] ? rep[x] < rep[y] : est[x] > est[y];
+        });
     }
     for (int i = 0; i < N; ++i) {
         bi_off[i + 1] = bi_off[i] + (int)items[i].size();

@@ -204,13 +204,13 @@ def test_gradient_modes_add_up(oracle_mod, water648):
 def test_jump_lists_definition(oracle_mod, water648):
     """Ring lists hold exactly the non-excluded partners with q_i q_j != 0 in
     the skin-widened rings, ordered by (cell of j at the outer rebuild, j) on
-    the grid of floor(L / (r_E + skin_outer)) cells; checked with numpy."""
+    the grid of floor(2 L / (r_E + skin_outer)) cells; checked with numpy."""
     skin = 0.2
     o = oracle_mod.Oracle(water648, r_cut=9.0, r_split=5.0, h_switch=0.5, r_mid=5.5, skin=skin,
                           skin_outer=0.3)
     x = water648.x
     L = water648.box
-    nc = int(math.floor(L / (9.0 + 0.3)))
+    nc = int(math.floor(2 * L / (9.0 + 0.3)))
     cs = L / nc
     cell = np.minimum((x // cs).astype(int), nc - 1)
     lin = (cell[:, 2] * nc + cell[:, 1]) * nc + cell[:, 0]
