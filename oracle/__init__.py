@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB = os.path.join(HERE, "liboracle.so")
 
 GRAD_FULL, GRAD_BONDED, GRAD_NB_FULL, GRAD_NB_SHORT, GRAD_NB_LONG, GRAD_F0 = range(6)
-KIND_RING_M, KIND_RING_L, KIND_LJ = range(3)
+KIND_RING_M, KIND_RING_L, KIND_LJ = 0, 1, 4     # ring y is kind y (0..3); LJ partners kind 4
 E_BOUND, E_LIMIT, E_NONFIN = 1, 2, 4
 
 
@@ -40,7 +40,8 @@ class Params(C.Structure):
     _fields_ = [("box", C.c_double), ("r_cut", C.c_double), ("r_split", C.c_double),
                 ("h_switch", C.c_double), ("r_mid", C.c_double), ("dsf_alpha", C.c_double),
                 ("gamma", C.c_double), ("temperature", C.c_double), ("eps0", C.c_double),
-                ("skin", C.c_double), ("skin_outer", C.c_double), ("eps_mode", C.c_int), ("seed", C.c_uint32),
+                ("skin", C.c_double), ("skin_outer", C.c_double), ("eps_mode", C.c_int),
+                ("n_rings", C.c_int), ("ring_r", C.c_double * 3), ("seed", C.c_uint32),
                 ("replica", C.c_uint32)]
 
 
@@ -71,7 +72,7 @@ def lib():
         L.or_gradient.argtypes = [vp, i, vp, vp]
         L.or_gradient_atom.argtypes = [vp, i, i, vp]
         L.or_energy.argtypes = [vp, vp]
-        L.or_bounds.argtypes = [vp, vp, vp, vp, vp]
+        L.or_bounds.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.or_list_counts.argtypes = [vp, i, vp]
         L.or_list_get.restype = i
         L.or_list_get.argtypes = [vp, i, i, vp]
@@ -130,13 +131,16 @@ class Oracle:
 
     def __init__(self, sys, r_cut=9.0, r_split=5.0, h_switch=0.5, r_mid=5.5, dsf_alpha=0.2,
                  gamma=1.0, temperature=300.0, eps0=0.1, skin=0.3, skin_outer=None, eps_mode=1,
-                 seed=0, replica=0):
+                 seed=0, replica=0, ring_r=None):
         self.L = lib()
         self.n = sys.n
         if skin_outer is None:
             skin_outer = skin
+        rr = list(ring_r or [])
+        n_rings = len(rr) + 1 if ring_r is not None else 0
         self.params = Params(sys.box, r_cut, r_split, h_switch, r_mid, dsf_alpha, gamma,
-                             temperature, eps0, skin, skin_outer, eps_mode, seed, replica)
+                             temperature, eps0, skin, skin_outer, eps_mode, n_rings,
+                             (C.c_double * 3)(*(rr + [0.0] * (3 - len(rr)))), seed, replica)
         a = lambda z, t: np.ascontiguousarray(z, dtype=t)
         self._keep = [a(sys.x, np.float64), a(sys.v, np.float64), a(sys.mass, np.float64),
                       a(sys.charge, np.float64), a(sys.type, np.int32), a(sys.lj_eps, np.float64),
@@ -206,9 +210,11 @@ class Oracle:
         return self.L.or_pair_u(self.h, ti, tj, float(qiqj), float(r), weight)
 
     def bounds(self):
-        o = np.zeros(3); LM = np.zeros(self.n); LL = np.zeros(self.n); LJ = np.zeros(self.n)
-        self.L.or_bounds(self.h, _p(o), _p(LM), _p(LL), _p(LJ))
-        return o, LM, LL, LJ
+        """(lhat[4], qmax, ring edges, n_rings, LY (n x 4), LLJ (n))"""
+        lhat = np.zeros(4); q = np.zeros(1); edges = np.zeros(5); nr = C.c_int(0)
+        LY = np.zeros((self.n, 4)); LJ = np.zeros(self.n)
+        self.L.or_bounds(self.h, _p(lhat), _p(q), _p(edges), C.byref(nr), _p(LY), _p(LJ))
+        return lhat, float(q[0]), edges[:nr.value + 1], nr.value, LY, LJ
 
     # lists ---------------------------------------------------------------
     def list_counts(self, kind):

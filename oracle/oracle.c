@@ -46,7 +46,8 @@
 #define TAG_S 4u
 
 enum { W_FULL = 0, W_SHORT = 1, W_LONG = 2 };
-enum { K_RINGM = 0, K_RINGL = 1, K_LJ = 2, K_NKIND = 3 };
+#define OR_MAX_RINGS 4
+enum { K_LJ = 4, K_NKIND = 5 };            /* kinds 0..3: rings, 4: LJ partners */
 
 typedef struct { int *off, *idx; int cap; } or_list;
 
@@ -66,10 +67,10 @@ struct or_sys {
     int *exoff, *exidx;      /* per-atom excluded partners */
     /* derived */
     double beta;
-    double rM;               /* effective ring boundary */
-    int one_ring;
-    double LhatM, LhatL, qmax;
-    double *LM, *LL, *LLJ;   /* per-atom rate bounds */
+    int nr;                              /* number of rings */
+    double edge[OR_MAX_RINGS + 1];       /* ring edges: r_c - h, ..., r_E */
+    double lhat[OR_MAX_RINGS], qmax;
+    double *LY, *LLJ;                    /* per-atom rate bounds (n x 4), LJ bound */
     or_list lists[K_NKIND];
     int ncell;
     int *cellm;              /* cell of each atom at the last outer rebuild */
@@ -334,7 +335,8 @@ static int excluded(const or_sys* s, int i, int j)
 
 /* ======================================================================== */
 /* bounds on |F_ij| (Sec. 3.1: analytic bounds uniform in j; ring technique */
-/* bounds L_M on [r_c-h, r_M] and L_L on [r_M, r_E]). Reading: grid max,    */
+/* bounds L_M on [r_c-h, r_M] and L_L on [r_M, r_E], generalised to rings   */
+/* with edges r_c-h = e_0 < e_1 < ... < e_n = r_E). Reading: grid max,      */
 /* times (1 + 1e-4), rounded up to 9 significant bits.                      */
 /* ======================================================================== */
 static double round_up_bound(double x)
@@ -375,10 +377,18 @@ static double grid_max_lj(const or_sys* s, double e, double sg, double lo, doubl
 static void compute_bounds(or_sys* s)
 {
     double lo = s->p.r_split - s->p.h_switch, R = s->p.r_cut;
-    s->one_ring = !(s->p.r_mid > lo && s->p.r_mid < R);
-    s->rM = s->one_ring ? lo : s->p.r_mid;
-    s->LhatM = s->one_ring ? 0.0 : grid_max_coul(s, lo, s->rM);
-    s->LhatL = grid_max_coul(s, s->rM, R);
+    /* ring edges */
+    s->edge[0] = lo;
+    if (s->p.n_rings >= 1) {
+        s->nr = s->p.n_rings > OR_MAX_RINGS ? OR_MAX_RINGS : s->p.n_rings;
+        for (int y = 1; y < s->nr; ++y) s->edge[y] = s->p.ring_r[y - 1];
+    } else {
+        s->nr = (s->p.r_mid > lo && s->p.r_mid < R) ? 2 : 1;
+        if (s->nr == 2) s->edge[1] = s->p.r_mid;
+    }
+    s->edge[s->nr] = R;
+    for (int y = 0; y < s->nr; ++y) s->lhat[y] = grid_max_coul(s, s->edge[y], s->edge[y + 1]);
+    for (int y = s->nr; y < OR_MAX_RINGS; ++y) s->lhat[y] = 0.0;
     s->qmax = 0.0;
     for (int i = 0; i < s->n; ++i) if (fabs(s->q[i]) > s->qmax) s->qmax = fabs(s->q[i]);
     int nt = s->ntypes;
@@ -390,8 +400,8 @@ static void compute_bounds(or_sys* s)
             ljhat[a * nt + b] = grid_max_lj(s, s->eps[a * nt + b], s->sig[a * nt + b], lo, R);
     for (int i = 0; i < s->n; ++i) {
         double cq = OR_COULOMB * fabs(s->q[i]) * s->qmax;
-        s->LM[i] = round_up_bound(cq * s->LhatM);
-        s->LL[i] = round_up_bound(cq * s->LhatL);
+        for (int y = 0; y < OR_MAX_RINGS; ++y)
+            s->LY[OR_MAX_RINGS * i + y] = y < s->nr ? round_up_bound(cq * s->lhat[y]) : 0.0;
         double m = 0.0;
         for (int b = 0; b < nt; ++b)
             if (present[b] && ljhat[s->type[i] * nt + b] > m) m = ljhat[s->type[i] * nt + b];
@@ -401,19 +411,21 @@ static void compute_bounds(or_sys* s)
     free(present);
 }
 
-void or_bounds(const or_sys* s, double* out3, double* LM, double* LL, double* LLJ)
+void or_bounds(const or_sys* s, double* lhat, double* qmax, double* edges, int* nrings, double* LY, double* LLJ)
 {
-    if (out3) { out3[0] = s->LhatM; out3[1] = s->LhatL; out3[2] = s->qmax; }
+    if (lhat) for (int y = 0; y < OR_MAX_RINGS; ++y) lhat[y] = s->lhat[y];
+    if (qmax) *qmax = s->qmax;
+    if (edges) for (int y = 0; y <= OR_MAX_RINGS; ++y) edges[y] = y <= s->nr ? s->edge[y] : 0.0;
+    if (nrings) *nrings = s->nr;
     for (int i = 0; i < s->n; ++i) {
-        if (LM) LM[i] = s->LM[i];
-        if (LL) LL[i] = s->LL[i];
+        if (LY) for (int y = 0; y < OR_MAX_RINGS; ++y) LY[OR_MAX_RINGS * i + y] = s->LY[OR_MAX_RINGS * i + y];
         if (LLJ) LLJ[i] = s->LLJ[i];
     }
 }
-
 /* ======================================================================== */
 /* jump lists (Sec. 3.1 remark: middle and long neighbour lists with counts */
-/* N_M(i), N_L(i); Sec. 3.2: LJ partners). Membership by distance at the    */
+/* N_M(i), N_L(i), one list per ring; Sec. 3.2: LJ partners). Membership by */
+/* distance at the    */
 /* build positions widened by the skin. Order: by (cell of j at the last    */
 /* outer rebuild, j) on the grid of n_c = floor(2 L / (r_E + skin_outer))   */
 /* cells per edge. An outer rebuild happens when some atom moved more than  */
@@ -447,12 +459,9 @@ static int in_kind(const or_sys* s, int kind, int i, int j, double r2)
 {
     double lo, hi;
     double sk = s->p.skin, sw = s->p.r_split - s->p.h_switch, R = s->p.r_cut;
-    if (kind == K_RINGM) {
-        if (s->one_ring || s->q[i] * s->q[j] == 0.0) return 0;
-        lo = sw - sk; hi = s->rM + sk;
-    } else if (kind == K_RINGL) {
-        if (s->rM >= R || s->q[i] * s->q[j] == 0.0) return 0;
-        lo = s->rM - sk; hi = R + sk;
+    if (kind < OR_MAX_RINGS) {
+        if (kind >= s->nr || sw >= R || s->q[i] * s->q[j] == 0.0) return 0;
+        lo = s->edge[kind] - sk; hi = s->edge[kind + 1] + sk;
     } else {
         if (sw >= R || s->eps[s->type[i] * s->ntypes + s->type[j]] == 0.0) return 0;
         lo = sw - sk; hi = R + sk;
@@ -756,44 +765,49 @@ static void log_event(or_sys* s, int64_t s0, int half, int tag, int atom, int64_
 }
 
 /* ======================================================================== */
-/* Step C' for one atom (Algorithm 4, adaptive eps, ring technique).       */
+/* Step C' for one atom (Algorithm 4, adaptive eps, ring technique with     */
+/* any number of rings up to four).                                         */
 /* x is fixed, a = -grad U_short / m~ is the drift between jumps.           */
 /* ======================================================================== */
 static void cprime_atom(or_sys* s, int i, double* v, const double* a, double tau2,
                         uint32_t s0, int half, int64_t* nprop, int64_t* nacc, int64_t* natt,
                         uint32_t* err)
 {
-    const or_list* lm = &s->lists[K_RINGM];
-    const or_list* ll = &s->lists[K_RINGL];
-    int NM = lm->off[i + 1] - lm->off[i];
-    int NL = ll->off[i + 1] - ll->off[i];
+    int nr = s->nr;
+    int N[OR_MAX_RINGS];
+    int ntot = 0;
+    for (int y = 0; y < nr; ++y) {
+        const or_list* l = &s->lists[y];
+        N[y] = l->off[i + 1] - l->off[i];
+        ntot += N[y];
+    }
     double beta = s->beta, mt = s->mt[i], eps0 = s->p.eps0;
-    double lo = s->p.r_split - s->p.h_switch, R = s->p.r_cut;
     double t = 0.0;
     uint32_t k = 0;
-    if (NM + NL == 0) {
+    if (ntot == 0) {
         for (int c = 0; c < 3; ++c) v[c] += tau2 * a[c];
         return;
     }
+    const double* LY = &s->LY[OR_MAX_RINGS * i];
     double aa = a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
     for (;;) {
-        /* bound on |v| over the rest of the phase, then the rate bound */
+        /* bound on |v| over the rest of the phase, then the rate bound per ring */
         double sr = tau2 - t;
         double vv = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
         double va = v[0] * a[0] + v[1] * a[1] + v[2] * a[2];
         double B = sqrt(vv + sr * sr * aa + 2.0 * sr * (va > 0.0 ? va : 0.0));
-        double LamM, LamL;
-        if (s->p.eps_mode == 1) {
-            double c0 = sqrt(beta / mt) / (eps0 * sqrt(2.0 * OR_PI));
-            LamM = beta * s->LM[i] * B + c0;
-            LamL = beta * s->LL[i] * B + c0;
-        } else {
-            double c0 = sqrt(beta / (2.0 * OR_PI * mt)) / eps0;
-            LamM = s->LM[i] * (beta * B + c0);
-            LamL = s->LL[i] * (beta * B + c0);
+        double LamY[OR_MAX_RINGS], w[OR_MAX_RINGS], Lam = 0.0;
+        for (int y = 0; y < nr; ++y) {
+            if (s->p.eps_mode == 1) {
+                double c0 = sqrt(beta / mt) / (eps0 * sqrt(2.0 * OR_PI));
+                LamY[y] = beta * LY[y] * B + c0;
+            } else {
+                double c0 = sqrt(beta / (2.0 * OR_PI * mt)) / eps0;
+                LamY[y] = LY[y] * (beta * B + c0);
+            }
+            w[y] = (double)N[y] * LamY[y];
+            Lam += w[y];
         }
-        double wM = (double)NM * LamM, wL = (double)NL * LamL;
-        double Lam = wM + wL;
         uint32_t u[4];
         draw(s, (uint32_t)i, s0, TAG_C, half, 0, k, u);
         double T = -log(unif(u[0])) / Lam;
@@ -804,16 +818,20 @@ static void cprime_atom(or_sys* s, int i, double* v, const double* a, double tau
         t += T;
         for (int c = 0; c < 3; ++c) v[c] += T * a[c];
         (*nprop)++;
-        /* ring Y with probability w_Y / Lam, then J uniform in ring Y */
-        int ringM = unif(u[1]) * Lam < wM;
-        int J = ringM ? lm->idx[lm->off[i] + pick(u[2], NM)]
-                      : ll->idx[ll->off[i] + pick(u[2], NL)];
-        double LamY = ringM ? LamM : LamL;
-        double LY = ringM ? s->LM[i] : s->LL[i];
+        /* ring Y with probability w_Y / Lam (first ring whose cumulative
+         * weight exceeds U1 Lam), then J uniform in ring Y */
+        double target = unif(u[1]) * Lam, cum = 0.0;
+        int Y = nr - 1;
+        for (int y = 0; y < nr; ++y) {
+            cum += w[y];
+            if (target < cum) { Y = y; break; }
+        }
+        const or_list* lY = &s->lists[Y];
+        int J = lY->idx[lY->off[i] + pick(u[2], N[Y])];
         double d[3];
         minimage(s, i, J, d);
         double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-        int inside = ringM ? (r >= lo && r < s->rM) : (r >= s->rM && r < R);
+        int inside = r >= s->edge[Y] && r < s->edge[Y + 1];
         double g[3] = { 0.0, 0.0, 0.0 };
         if (inside) {
             double f = OR_COULOMB * s->q[i] * s->q[J] * coul_long_dudr(s, r) / r;
@@ -826,11 +844,11 @@ static void cprime_atom(or_sys* s, int i, double* v, const double* a, double tau
             if (s->p.eps_mode == 1) {
                 eps = eps0 * gn;
                 eta = eps0 * sqrt(beta * mt) * vg;
-                p = sqrt(beta / mt) * or_theta(eta) / eps0 / LamY;
+                p = sqrt(beta / mt) * or_theta(eta) / eps0 / LamY[Y];
             } else {
                 eps = eps0;
                 eta = eps0 * sqrt(beta * mt) * vg / gn;
-                p = gn * or_theta(eta) / (LY * (eps0 * sqrt(beta * mt) * B + 1.0 / sqrt(2.0 * OR_PI)));
+                p = gn * or_theta(eta) / (LY[Y] * (eps0 * sqrt(beta * mt) * B + 1.0 / sqrt(2.0 * OR_PI)));
             }
             if (p > 1.0) *err |= OR_E_BOUND;
             if (unif(u[3]) <= p) {
@@ -1175,8 +1193,7 @@ or_sys* or_create(int n, const or_params* p,
     }
     free(fill);
     s->beta = 1.0 / (OR_KB * p->temperature);
-    s->LM = (double*)malloc(sizeof(double) * (size_t)n);
-    s->LL = (double*)malloc(sizeof(double) * (size_t)n);
+    s->LY = (double*)malloc(sizeof(double) * OR_MAX_RINGS * (size_t)n);
     s->LLJ = (double*)malloc(sizeof(double) * (size_t)n);
     compute_bounds(s);
     if (s->p.skin_outer < s->p.skin) s->p.skin_outer = s->p.skin;
@@ -1205,7 +1222,7 @@ void or_destroy(or_sys* s)
     free(s->bonds); free(s->bk); free(s->br0);
     free(s->angles); free(s->ak); free(s->at0);
     free(s->exoff); free(s->exidx);
-    free(s->LM); free(s->LL); free(s->LLJ);
+    free(s->LY); free(s->LLJ);
     for (int k = 0; k < K_NKIND; ++k) { free(s->lists[k].off); free(s->lists[k].idx); }
     free(s->a0); free(s->ab); free(s->as); free(s->al);
     free(s->cellm); free(s->xo);

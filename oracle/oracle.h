@@ -33,7 +33,7 @@ typedef struct {
     double r_cut;        /* r_E: outer cutoff of LJ and DSF Coulomb (A) */
     double r_split;      /* r_c: short/long split radius (A) */
     double h_switch;     /* h: width of the switch, chi goes 1 -> 0 on [r_c-h, r_c] */
-    double r_mid;        /* r_M: ring boundary; <= r_c-h or >= r_E means one ring */
+    double r_mid;        /* r_M: ring boundary when n_rings == 0; <= r_c-h or >= r_E means one ring */
     double dsf_alpha;    /* DSF damping (1/A) */
     double gamma;        /* friction (1/ps) */
     double temperature;  /* K */
@@ -41,6 +41,8 @@ typedef struct {
     double skin;         /* Verlet skin (A); lists are rebuilt when an atom moved > skin/2 */
     double skin_outer;   /* skin of the outer candidate grid (>= skin); it fixes the list order */
     int eps_mode;        /* 1 adaptive (the paper's choice), 0 constant */
+    int n_rings;         /* 0: rings from r_mid; 1..4: ring edges r_c-h, ring_r[0..n-2], r_E */
+    double ring_r[3];    /* interior ring edges, increasing, inside (r_c-h, r_E) */
     uint32_t seed;       /* Philox key word 0 */
     uint32_t replica;    /* Philox key word 1 */
 } or_params;
@@ -86,11 +88,12 @@ void or_energy(or_sys* s, double* terms);
 /* per-atom gradient of the chosen mode for one atom only (O(N)) */
 void or_gradient_atom(or_sys* s, int mode, int i, double* g3);
 
-/* rate bounds: out[0] Lhat_M, out[1] Lhat_L (unit charges, per C q_i q_j),
- * out[2] qmax, per atom LM/LL/LLJ arrays (may be NULL) */
-void or_bounds(const or_sys* s, double* out3, double* LM, double* LL, double* LLJ);
+/* rate bounds: lhat[4] the per-ring max of |d/dr (1-chi) u_DSF| (unit
+ * charges, per C q_i q_j), qmax, edges[5] the ring edges, nrings; per atom
+ * LY (n x 4, row-major) and LLJ arrays (any may be NULL) */
+void or_bounds(const or_sys* s, double* lhat, double* qmax, double* edges, int* nrings, double* LY, double* LLJ);
 
-/* jump lists: kind 0 ring M, 1 ring L, 2 LJ. counts[n]; list of one atom */
+/* jump lists: kind 0..3 ring 0..3 (inner to outer), 4 LJ. counts[n]; list of one atom */
 void or_list_counts(const or_sys* s, int kind, int* counts);
 int  or_list_get(const or_sys* s, int kind, int i, int* out);
 /* force a rebuild now */

@@ -23,12 +23,12 @@ def beta_of(T=300.0):
 
 
 # ------------------------------------------------------------ thinning laws
-def _ring_system(oracle_mod, eps_mode=1, eps0=0.1):
+def _ring_system(oracle_mod, eps_mode=1, eps0=0.1, ring_r=None):
     """Atom 0 with four charged partners in the jump rings (4.8, 5.2, 6.0, 8.0 A)."""
     x = np.array([[10, 10, 10], [14.8, 10, 10], [10, 15.2, 10], [10, 10, 16.0], [4.34, 15.66, 10]])
     w = systems.point_charges(x, 30.0, [0.5, -0.7, 0.4, -0.3, 0.6], [16.0, 1, 1, 1, 1])
     return oracle_mod.Oracle(w, r_cut=9.0, r_split=5.0, h_switch=0.5, r_mid=5.5, dsf_alpha=0.2,
-                             skin=0.3, eps0=eps0, eps_mode=eps_mode, seed=21)
+                             skin=0.3, eps0=eps0, eps_mode=eps_mode, seed=21, ring_r=ring_r)
 
 
 def _pair_rates(o, v, eps_mode, eps0, beta, mt):
@@ -53,12 +53,13 @@ def _pair_rates(o, v, eps_mode, eps0, beta, mt):
     return tot
 
 
-@pytest.mark.parametrize("eps_mode", [1, 0])
-def test_cprime_first_jump_survival_a0(oracle_mod, eps_mode):
+@pytest.mark.parametrize("eps_mode,rings", [(1, None), (0, None), (1, [5.0, 5.5, 7.0]), (0, [5.0, 7.0])])
+def test_cprime_first_jump_survival_a0(oracle_mod, eps_mode, rings):
     """With a = 0 the accepted jumps of the first event form a Poisson process
-    of rate sum_j lambda_ij(v): P(no jump in tau/2) = exp(-tau/2 sum lambda)."""
+    of rate sum_j lambda_ij(v): P(no jump in tau/2) = exp(-tau/2 sum lambda),
+    whatever the ring partition of the bound (two rings, or three and four)."""
     eps0 = 0.1 if eps_mode == 1 else 2.0
-    o = _ring_system(oracle_mod, eps_mode, eps0)
+    o = _ring_system(oracle_mod, eps_mode, eps0, rings)
     beta, mt = beta_of(), 16.0 / KCAL_AMU
     v = np.array([3.0, -2.0, 4.0])
     lam = _pair_rates(o, v, eps_mode, eps0, beta, mt)

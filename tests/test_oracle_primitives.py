@@ -147,9 +147,10 @@ def test_bounds_dominate_long_gradient(oracle_mod):
     x = np.array([[0, 0, 0], [7, 0, 0], [0, 7, 0]])
     o = oracle_mod.Oracle(systems.point_charges(x, 40.0, [1.0, -1.0, 0.5], 16.0),
                           r_cut=9.0, r_split=5.0, h_switch=0.5, r_mid=5.5, dsf_alpha=0.2)
-    (LhM, LhL, qmax), LM, LL, _ = o.bounds()
+    lhat, qmax, edges, nr, LY, _ = o.bounds()
+    assert nr == 2 and np.allclose(edges, [4.5, 5.5, 9.0])
     f = lambda r: abs(o.pair_dudr(0, 0, 1.0 / C_COUL, r, 2))
-    for lo, hi, Lh, Lat in ((4.5, 5.5, LhM, LM[0]), (5.5, 9.0, LhL, LL[0])):
+    for lo, hi, Lh, Lat in ((4.5, 5.5, lhat[0], LY[0, 0]), (5.5, 9.0, lhat[1], LY[0, 1])):
         rr = np.linspace(lo, hi, 77777)[1:-1] + 1.3e-6
         m = max(f(r) for r in rr)
         opt = __import__("scipy.optimize", fromlist=["x"]).minimize_scalar(
@@ -161,6 +162,27 @@ def test_bounds_dominate_long_gradient(oracle_mod):
         exact = C_COUL * 1.0 * qmax * m
         assert exact * (1 + 1e-4) <= Lat <= exact * 1.003
     assert qmax == 1.0
+
+
+def test_four_ring_bounds_and_lists(oracle_mod, water648):
+    """Rings with edges r_c-h, 5.0, 5.5, 7.0, r_E: each ring's bound dominates
+    |d/dr (1-chi) U| on its shell, bounds shrink outward, and every partner of
+    the two-ring lists appears in the ring lists covering its distance."""
+    o = oracle_mod.Oracle(water648, r_cut=9.0, r_split=5.0, h_switch=0.5, skin=0.2, skin_outer=0.3,
+                          ring_r=[5.0, 5.5, 7.0])
+    lhat, qmax, edges, nr, LY, _ = o.bounds()
+    assert nr == 4 and np.allclose(edges, [4.5, 5.0, 5.5, 7.0, 9.0])
+    f = lambda r: abs(o.pair_dudr(1, 1, 1.0 / C_COUL, r, 2))   # H-H: Coulomb only
+    for y in range(4):
+        rr = np.linspace(edges[y], edges[y + 1], 5001)
+        assert lhat[y] >= max(f(r) for r in rr) * (1 - 1e-6)
+    assert lhat[0] > lhat[1] > lhat[2] > lhat[3]
+    two = oracle_mod.Oracle(water648, r_cut=9.0, r_split=5.0, h_switch=0.5, r_mid=5.5, skin=0.2, skin_outer=0.3)
+    for i in (0, 1, 200):
+        four = set()
+        for y in range(4):
+            four |= set(o.list_of(y, i).tolist())
+        assert set(two.list_of(0, i).tolist()) | set(two.list_of(1, i).tolist()) == four
 
 
 # ---------------------------------------------------------------- forces
@@ -223,8 +245,8 @@ def test_jump_lists_definition(oracle_mod, water648):
         ok = (np.arange(water648.n) != i) & (mol != mol[i])
         for kind, lo, hi, extra in ((0, 4.5 - skin, 5.5 + skin, True),
                                     (1, 5.5 - skin, 9.0 + skin, True),
-                                    (2, 4.5 - skin, 9.0 + skin, water648.type == 0)):
-            if kind == 2 and water648.type[i] != 0:
+                                    (4, 4.5 - skin, 9.0 + skin, water648.type == 0)):
+            if kind == 4 and water648.type[i] != 0:
                 extra = np.zeros_like(ok)
             sel = np.flatnonzero(ok & (r >= lo) & (r < hi) & extra)
             sel = sel[np.lexsort((sel, lin[sel]))]
