@@ -101,6 +101,8 @@ typedef struct {
     int eps_mode;      /* 1: adaptive eps = eps0 |F_ij| (the paper's choice), 0: constant eps = eps0 */
     double skin;       /* list skin (A): lists are rebuilt when an atom moved more than skin/2 */
     double skin_outer; /* outer candidate skin (A, >= skin); it also fixes the order of the jump lists */
+    int n_rings;       /* 0: rings from r_mid; 1..4: rings with edges r_c-h, ring_r[0..n_rings-2], r_E */
+    double ring_r[3];  /* interior ring edges (A), strictly increasing inside (r_c-h, r_E); MD_EINVAL otherwise */
 } md_system;
 
 typedef struct {
@@ -174,7 +176,8 @@ int md_gradient(md_ctx* ctx, int replica, int mode, double* host_grad);
  * streams exactly as inside the integrators. Applies to every replica. */
 int md_run_phase(md_ctx* ctx, int phase, double tau2_ps, int64_t s0, int half, int accel_mode);
 
-/* Jump list of one atom: kind 0 ring M, 1 ring L, 2 LJ. Writes up to cap
+/* Jump list of one atom: kind 0..3 ring 0..3 (inner to outer; rings past the
+ * system's ring count are empty), 4 LJ. Writes up to cap
  * partner indices (local to the replica, in list order) into host_out and
  * returns the list length (or a negative error). */
 int md_get_list(md_ctx* ctx, int replica, int kind, int atom, int* host_out, int cap);

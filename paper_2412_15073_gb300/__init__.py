@@ -54,7 +54,8 @@ class MdSystem(C.Structure):
                 ("r_cut", C.c_double), ("r_split", C.c_double), ("h_switch", C.c_double),
                 ("r_mid", C.c_double), ("dsf_alpha", C.c_double), ("gamma", C.c_double),
                 ("temperature", C.c_double), ("eps0", C.c_double), ("eps_mode", C.c_int),
-                ("skin", C.c_double), ("skin_outer", C.c_double)]
+                ("skin", C.c_double), ("skin_outer", C.c_double),
+                ("n_rings", C.c_int), ("ring_r", C.c_double * 3)]
 
 
 class MdObs(C.Structure):
@@ -120,7 +121,10 @@ def _current_stream():
 
 
 DEFAULTS = dict(r_cut=9.0, r_split=5.0, h_switch=0.5, r_mid=5.5, dsf_alpha=0.2, gamma=1.0,
-                temperature=300.0, eps0=0.1, eps_mode=1, skin=0.3, skin_outer=None)
+                temperature=300.0, eps0=0.1, eps_mode=1, skin=0.3, skin_outer=None, ring_r=None)
+
+
+KIND_RING0, KIND_LJ = 0, 4
 
 
 class Engine:
@@ -176,6 +180,14 @@ class Engine:
                      _ptr(keep["excl"]), p["r_cut"], p["r_split"], p["h_switch"], p["r_mid"],
                      p["dsf_alpha"], p["gamma"], p["temperature"], p["eps0"], p["eps_mode"],
                      p["skin"], p["skin_outer"])
+        # ring_r: interior ring edges; None keeps the rings of r_mid
+        if p["ring_r"] is not None:
+            rr = [float(z) for z in p["ring_r"]]
+            if len(rr) > 3:
+                raise ValueError("at most 3 interior ring edges (4 rings)")
+            s.n_rings = len(rr) + 1
+            for k, z in enumerate(rr):
+                s.ring_r[k] = z
         self._ck(self.L.md_set_system(self.h, replica, C.byref(s)))
         self.n[replica] = sys.n
 
@@ -223,6 +235,7 @@ class Engine:
         self._ck(self.L.md_run_phase(self.h, int(phase), float(tau2_ps), int(s0), int(half), int(accel_mode)))
 
     def get_list(self, kind, atom, replica=0, cap=4096):
+        """Jump list of one atom: kind 0..3 ring 0..3 (inner to outer), 4 LJ."""
         out = np.zeros(cap, dtype=np.int32)
         n = self._ck(self.L.md_get_list(self.h, replica, kind, atom, _ptr(out), cap))
         return out[:min(n, cap)]

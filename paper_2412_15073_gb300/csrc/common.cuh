@@ -29,8 +29,9 @@ constexpr uint32_t TAG_O = 1, TAG_C = 2, TAG_J = 3, TAG_S = 4;
 // error flag bits (match MD_FLAG_* in md.h)
 constexpr uint32_t F_BOUND = 1, F_LIMIT = 2, F_NONFIN = 4, F_OVERFLOW = 8;
 
-// list kinds
-enum ListKind { L_SHORT = 0, L_FULL = 1, L_RM = 2, L_RL = 3, L_LJ = 4, NKIND = 5 };
+// list kinds: short and full neighbour lists, up to four jump rings, LJ partners
+constexpr int MAX_RINGS = 4;
+enum ListKind { L_SHORT = 0, L_FULL = 1, L_R0 = 2, L_LJ = L_R0 + MAX_RINGS, NKIND = L_LJ + 1 };
 
 // counters per replica
 enum Counter { C_CPROP = 0, C_CACC, C_JPROP, C_JACC, C_SATT, C_REBUILD, C_OUTER, C_GUARD, NCOUNT };
@@ -57,8 +58,10 @@ struct RepParams {
     double scl, inv_scl;       // L / 2^32, 2^32 / L
     float sclf, sclf_lo;       // L / 2^32 as a sum of two floats (hi + lo)
     // cutoffs
-    double R, rc, h, sw, rM;   // r_E, r_c, h, r_c - h, r_M (= sw with one ring)
-    int one_ring, rings_on, lj_on, eps_mode;
+    double R, rc, h, sw;       // r_E, r_c, h, r_c - h
+    double edge[MAX_RINGS + 1];// ring edges: sw = edge[0] < ... < edge[nr] = R
+    float edgef[MAX_RINGS + 1];
+    int nr, rings_on, lj_on, eps_mode;
     double skin, skin_o;
     // DSF: u(r) = erfc(a r)/r - eR + fR (r - R); u'(r) = -erfc(a r)/r^2 - k exp(-a^2 r^2)/r + fR
     double alpha, eR, fR, kexp;     // kexp = 2 a / sqrt(pi)

@@ -26,8 +26,8 @@ struct Dev {
     // per-atom constants
     const double *mt, *isqmt, *q;   // m/418.4, 1/sqrt(m~), charge
     const int* type;
-    const double *LM, *LL, *LLJ;    // rate bounds per atom
-    const float *LMf, *LLf, *LLJf;
+    const double *LY, *LLJ;         // rate bounds per atom: rings (n x MAX_RINGS), LJ
+    const float *LYf, *LLJf;
     // bonded terms: per-atom items (kind | role << 4, term index)
     const int* bi_off;
     const int2* bitem;

@@ -72,7 +72,7 @@ struct Tally {
 
 // acceptance probability of a C' proposal in FP64 from the FP64 positions
 // (mixed mode only, when U is within 2e-6 of the FP32 value)
-__device__ __noinline__ double cprime_p64(const Dev& d, const RepParams& P, int i, int J, bool ringM,
+__device__ __noinline__ double cprime_p64(const Dev& d, const RepParams& P, int i, int J, int Y,
                              const double v0[3], const double a[3], double tprev, double t,
                              const float jac[3], double aa, double tau2)
 {
@@ -86,12 +86,11 @@ __device__ __noinline__ double cprime_p64(const Dev& d, const RepParams& P, int 
     const double va = vp[0] * a[0] + vp[1] * a[1] + vp[2] * a[2];
     const double B = sqrt(vv + s * s * aa + 2.0 * s * fmax(va, 0.0));
     const double mt = d.mt[i], beta = P.beta, eps0 = P.eps0;
-    const double LY = ringM ? d.LM[i] : d.LL[i];
+    const double LY = d.LY[MAX_RINGS * i + Y];
     double dx = mimg(d.x[3 * i] - d.x[3 * J], P), dy = mimg(d.x[3 * i + 1] - d.x[3 * J + 1], P),
            dz = mimg(d.x[3 * i + 2] - d.x[3 * J + 2], P);
     const double r = sqrt(dx * dx + dy * dy + dz * dz);
-    const bool inside = ringM ? (r >= P.sw && r < P.rM) : (r >= P.rM && r < P.R);
-    if (!inside) return 0.0;
+    if (!(r >= P.edge[Y] && r < P.edge[Y + 1])) return 0.0;
     const double f = COULOMB * d.q[i] * d.q[J] * coul_long<double>(P, r) / r;
     const double gx = f * dx, gy = f * dy, gz = f * dz;
     const double gn = sqrt(gx * gx + gy * gy + gz * gz);
@@ -106,24 +105,60 @@ __device__ __noinline__ double cprime_p64(const Dev& d, const RepParams& P, int 
     return gn * theta<double>(eta) / (LY * (eps0 * sqrt(beta * mt) * B + 1.0 / sqrt(2.0 * PI)));
 }
 
-// C' for atom i over tau2 (Algorithm 4, adaptive or constant eps, two rings)
+static_assert(MAX_RINGS == 4, "ring selection below is written for four ring slots");
+
+// v[Y] for a ring index held in a register (selects instead of indexing local memory)
+template <typename A>
+__device__ __forceinline__ A ring_sel(const A (&v)[MAX_RINGS], int Y)
+{
+    return Y == 0 ? v[0] : (Y == 1 ? v[1] : (Y == 2 ? v[2] : v[3]));
+}
+
+// partner counts of the rings of atom i (0 for ring slots past the replica's count)
+__device__ __forceinline__ int ring_counts(const Dev& d, const RepParams& P, int i, int (&N)[MAX_RINGS])
+{
+    int ntot = 0;
+#pragma unroll
+    for (int y = 0; y < MAX_RINGS; ++y) {
+        N[y] = y < P.nr ? min(d.lcnt[L_R0 + y][i], d.lcap[L_R0 + y]) : 0;
+        ntot += N[y];
+    }
+    return ntot;
+}
+
+// ring of a proposal: the first ring whose cumulative weight exceeds U Lam
+// (ring Y with probability w_Y / Lam, Sec. 3.1 ring technique)
+template <typename T>
+__device__ __forceinline__ int ring_pick(const T (&w)[MAX_RINGS], T target, int nr)
+{
+    int Y = nr - 1;
+    bool found = false;
+    T cum = T(0);
+#pragma unroll
+    for (int y = 0; y < MAX_RINGS; ++y) {
+        cum += w[y];
+        if (!found && y < nr && target < cum) { Y = y; found = true; }
+    }
+    return Y;
+}
+
+// C' for atom i over tau2 (Algorithm 4, adaptive or constant eps, up to four rings)
 template <typename T>
 __device__ void cprime(const Dev& d, const RepParams& P, int i, int il, double v[3], const double a[3],
                        double tau2, uint32_t s0, int half, Tally& tl, uint32_t& err)
 {
-    const int NM = min(d.lcnt[L_RM][i], d.lcap[L_RM]);
-    const int NL = min(d.lcnt[L_RL][i], d.lcap[L_RL]);
-    if (NM + NL == 0) {
+    int N[MAX_RINGS];
+    if (ring_counts(d, P, i, N) == 0) {
         for (int c = 0; c < 3; ++c) v[c] += tau2 * a[c];
         return;
     }
-    const uint32_t* rowM = d.list[L_RM] + (size_t)i * d.lcap[L_RM];
-    const uint32_t* rowL = d.list[L_RL] + (size_t)i * d.lcap[L_RL];
     const T beta = T(P.beta), eps0 = T(P.eps0);
     const double mt64 = d.mt[i];
     const T mt = T(mt64);
     const T sbm = d_sqrt(beta * mt), sbom = d_sqrt(beta / mt);
-    const T LM = T(d.LM[i]), LL = T(d.LL[i]);
+    T LYv[MAX_RINGS];
+#pragma unroll
+    for (int y = 0; y < MAX_RINGS; ++y) LYv[y] = T(d.LY[MAX_RINGS * i + y]);
     const T qiC = T(COULOMB * d.q[i]);
     const bool adaptive = P.eps_mode == 1;
     const T c0 = adaptive ? sbom / (eps0 * T(2.5066282746310002)) : sbom / (T(2.5066282746310002) * eps0);
@@ -143,11 +178,13 @@ __device__ void cprime(const Dev& d, const RepParams& P, int i, int il, double v
         const T vv = vx * vx + vy * vy + vz * vz;
         const T va = vx * ax + vy * ay + vz * az;
         const T B = d_sqrt(vv + s * s * aa + T(2) * s * (va > T(0) ? va : T(0)));
-        T LamM, LamL;
-        if (adaptive) { LamM = beta * LM * B + c0; LamL = beta * LL * B + c0; }
-        else { LamM = LM * (beta * B + c0); LamL = LL * (beta * B + c0); }
-        const T wM = T(NM) * LamM, wL = T(NL) * LamL;
-        const T Lam = wM + wL;
+        T LamYv[MAX_RINGS], w[MAX_RINGS], Lam = T(0);
+#pragma unroll
+        for (int y = 0; y < MAX_RINGS; ++y) {
+            LamYv[y] = adaptive ? beta * LYv[y] * B + c0 : LYv[y] * (beta * B + c0);
+            w[y] = T(N[y]) * LamYv[y];
+            Lam += w[y];
+        }
         const U4 u = draw(P, uint32_t(il), s0, TAG_C, half, 0, k);
         const T Tn = -d_log(unif<T>(u.x)) / Lam;
         if (!(Lam > T(0)) || t + Tn > T2) break;
@@ -162,26 +199,27 @@ __device__ void cprime(const Dev& d, const RepParams& P, int i, int il, double v
             vz = T(v[2] + double(t) * a[2] + double(jz));
         }
         tl.cprop++;
-        const bool ringM = unif<T>(u.y) * Lam < wM;
-        const int J = int(ringM ? rowM[__umulhi(u.z, uint32_t(NM))] : rowL[__umulhi(u.z, uint32_t(NL))]);
+        const int Y = ring_pick<T>(w, unif<T>(u.y) * Lam, P.nr);
+        const uint32_t* row = d.list[L_R0 + Y] + (size_t)i * d.lcap[L_R0 + Y];
+        const int J = int(row[__umulhi(u.z, uint32_t(ring_sel(N, Y)))]);
         T dx, dy, dz;
         JD<T>::get(d, P, i, pi, J, dx, dy, dz);
         const T r = d_sqrt(dx * dx + dy * dy + dz * dz);
-        const bool inside = ringM ? (r >= T(P.sw) && r < T(P.rM)) : (r >= T(P.rM) && r < T(P.R));
+        const bool inside = r >= T(P.edge[Y]) && r < T(P.edge[Y + 1]);
         if (inside) {
             const T f = qiC * T(d.q[J]) * coul_long<T>(P, r) / r;
             const T gx = f * dx, gy = f * dy, gz = f * dz;
             const T gn = d_sqrt(gx * gx + gy * gy + gz * gz);
             if (gn > T(0)) {
                 const T vg = vx * gx + vy * gy + vz * gz;
-                const T LamY = ringM ? LamM : LamL;
+                const T LamY = ring_sel(LamYv, Y);
                 T eps, eta, p;
                 if (adaptive) {
                     eps = eps0 * gn;
                     eta = eps0 * sbm * vg;
                     p = sbom * theta<T>(eta) / eps0 / LamY;
                 } else {
-                    const T LY = ringM ? LM : LL;
+                    const T LY = ring_sel(LYv, Y);
                     eps = eps0;
                     eta = eps0 * sbm * vg / gn;
                     p = gn * theta<T>(eta) / (LY * (eps0 * sbm * B + T(0.3989422804014327)));
@@ -189,7 +227,7 @@ __device__ void cprime(const Dev& d, const RepParams& P, int i, int il, double v
                 bool acc;
                 if (sizeof(T) == 4 && fabs(double(unif<T>(u.w)) - double(p)) < 2e-6) {
                     const float jac[3] = {float(jx), float(jy), float(jz)};
-                    const double p64 = cprime_p64(d, P, i, J, ringM, v, a, double(tprev), double(t), jac,
+                    const double p64 = cprime_p64(d, P, i, J, Y, v, a, double(tprev), double(t), jac,
                                                   aa64, tau2);
                     acc = unif<double>(u.w) <= p64;
                     if (p64 > 1.0) err |= F_BOUND;
@@ -301,7 +339,7 @@ __device__ __noinline__ float sample_gtilde_f(const RepParams& P, uint32_t il, u
     return ok ? G : 0.f;
 }
 
-// C' for atom i in FP32 (Algorithm 4, adaptive or constant eps, two rings).
+// C' for atom i in FP32 (Algorithm 4, adaptive or constant eps, up to four rings).
 // The Philox block of proposal k+1 is computed while the partner of proposal
 // k is being fetched.
 template <bool DEFER>
@@ -309,22 +347,22 @@ __device__ __forceinline__ void cprime_f(const Dev& d, const RepParams& P, int i
                                          const float3 v0, const float3 a, float T2, uint32_t s0, int half,
                                          Tally& tl, uint32_t& err)
 {
-    const int NM = min(d.lcnt[L_RM][i], d.lcap[L_RM]);
-    const int NL = min(d.lcnt[L_RL][i], d.lcap[L_RL]);
-    if (NM + NL == 0) return;
-    const uint32_t* rowM = d.list[L_RM] + (size_t)i * d.lcap[L_RM];
-    const uint32_t* rowL = d.list[L_RL] + (size_t)i * d.lcap[L_RL];
+    int N[MAX_RINGS];
+    if (ring_counts(d, P, i, N) == 0) return;
     const float beta = float(P.beta), eps0 = float(P.eps0);
     const float mt = float(d.mt[i]);
     const float sbm = sqrtf(beta * mt), sbom = sqrtf(beta / mt);
-    const float LM = d.LMf[i], LL = d.LLf[i];
+    const float4 ly4 = __ldg(reinterpret_cast<const float4*>(d.LYf) + i);
+    const float LYv[MAX_RINGS] = {ly4.x, ly4.y, ly4.z, ly4.w};
+    float fN[MAX_RINGS];
+#pragma unroll
+    for (int y = 0; y < MAX_RINGS; ++y) fN[y] = float(N[y]);
     const uint4 pi = d.pos[i];
     const float qiC = float(COULOMB) * __uint_as_float(pi.w);
     const bool adaptive = P.eps_mode == 1;
     const float c0 = sbom / (eps0 * 2.5066282746310002f);
     const float aa = a.x * a.x + a.y * a.y + a.z * a.z;
-    const float fNM = float(NM), fNL = float(NL);
-    const float sw = float(P.sw), rM = float(P.rM), R = float(P.R), sc = P.sclf;
+    const float sc = P.sclf;
     float t = 0.f;
     float vx = v0.x + jv.x, vy = v0.y + jv.y, vz = v0.z + jv.z;
     uint32_t k = 0;
@@ -361,11 +399,13 @@ __device__ __forceinline__ void cprime_f(const Dev& d, const RepParams& P, int i
         const float vv = vx * vx + vy * vy + vz * vz;
         const float va = vx * a.x + vy * a.y + vz * a.z;
         const float B = sqrtf(vv + s * s * aa + 2.f * s * fmaxf(va, 0.f));
-        float LamM, LamL;
-        if (adaptive) { LamM = fmaf(beta * LM, B, c0); LamL = fmaf(beta * LL, B, c0); }
-        else { LamM = LM * fmaf(beta, B, c0); LamL = LL * fmaf(beta, B, c0); }
-        const float wM = fNM * LamM;
-        const float Lam = wM + fNL * LamL;
+        float LamYv[MAX_RINGS], w[MAX_RINGS], Lam = 0.f;
+#pragma unroll
+        for (int y = 0; y < MAX_RINGS; ++y) {
+            LamYv[y] = adaptive ? fmaf(beta * LYv[y], B, c0) : LYv[y] * fmaf(beta, B, c0);
+            w[y] = fN[y] * LamYv[y];
+            Lam += w[y];
+        }
         const float Tn = -__logf(unif<float>(u.x)) / Lam;
         if (!(Lam > 0.f) || t + Tn > T2) break;
         const float tprev = t;
@@ -374,8 +414,9 @@ __device__ __forceinline__ void cprime_f(const Dev& d, const RepParams& P, int i
         vy = fmaf(t, a.y, v0.y) + jv.y;
         vz = fmaf(t, a.z, v0.z) + jv.z;
         tl.cprop++;
-        const bool ringM = unif<float>(u.y) * Lam < wM;
-        const int J = int(ringM ? __ldg(rowM + __umulhi(u.z, uint32_t(NM))) : __ldg(rowL + __umulhi(u.z, uint32_t(NL))));
+        const int Y = ring_pick<float>(w, unif<float>(u.y) * Lam, P.nr);
+        const uint32_t* row = d.list[L_R0 + Y] + (size_t)i * d.lcap[L_R0 + Y];
+        const int J = int(__ldg(row + __umulhi(u.z, uint32_t(ring_sel(N, Y)))));
         const uint4 pj = __ldg(d.pos + J);
         const uint32_t uacc = u.w;
         const uint32_t kk = k;
@@ -385,14 +426,14 @@ __device__ __forceinline__ void cprime_f(const Dev& d, const RepParams& P, int i
         sdisp(pi, pj, sc, P.sclf_lo, dx, dy, dz);
         const float r2 = dx * dx + dy * dy + dz * dz;
         const float r = sqrtf(r2);
-        const bool inside = ringM ? (r >= sw && r < rM) : (r >= rM && r < R);
+        const bool inside = r >= P.edgef[Y] && r < P.edgef[Y + 1];
         if (inside) {
             const float f = qiC * __uint_as_float(pj.w) * coul_long<float>(P, r) / r;
             const float gx = f * dx, gy = f * dy, gz = f * dz;
             const float gn = sqrtf(gx * gx + gy * gy + gz * gz);
             if (gn > 0.f) {
                 const float vg = vx * gx + vy * gy + vz * gz;
-                const float LamY = ringM ? LamM : LamL;
+                const float LamY = ring_sel(LamYv, Y);
                 float eps, eta, p;
                 if (adaptive) {
                     eps = eps0 * gn;
@@ -401,7 +442,7 @@ __device__ __forceinline__ void cprime_f(const Dev& d, const RepParams& P, int i
                 } else {
                     eps = eps0;
                     eta = eps0 * sbm * vg / gn;
-                    p = gn * theta<float>(eta) / ((ringM ? LM : LL) * (eps0 * sbm * B + 0.3989422804014327f));
+                    p = gn * theta<float>(eta) / (ring_sel(LYv, Y) * (eps0 * sbm * B + 0.3989422804014327f));
                 }
                 bool acc;
                 const float U = unif<float>(uacc);
@@ -409,7 +450,7 @@ __device__ __forceinline__ void cprime_f(const Dev& d, const RepParams& P, int i
                     const double v0d[3] = {d.v[3 * i], d.v[3 * i + 1], d.v[3 * i + 2]};
                     const double ad[3] = {double(a.x), double(a.y), double(a.z)};
                     const float jac[3] = {jv.x, jv.y, jv.z};
-                    const double p64 = cprime_p64(d, P, i, J, ringM, v0d, ad, double(tprev), double(t), jac,
+                    const double p64 = cprime_p64(d, P, i, J, Y, v0d, ad, double(tprev), double(t), jac,
                                                   double(aa), double(T2));
                     acc = unif<double>(uacc) <= p64;
                     if (p64 > 1.0) err |= F_BOUND;

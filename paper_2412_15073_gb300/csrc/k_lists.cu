@@ -302,31 +302,42 @@ __global__ void __launch_bounds__(32 * WARPS) k_inner_lists(Dev d, int kinds, in
     const float qi = __uint_as_float(pi.w);
     const int ti = d.type[i];
     const bool want_s = kinds & (1 << L_SHORT), want_f = kinds & (1 << L_FULL);
-    const bool want_m = (kinds & (1 << L_RM)) && P.rings_on && !P.one_ring && qi != 0.f;
-    const bool want_l = (kinds & (1 << L_RL)) && P.rings_on && P.rM < P.R && qi != 0.f;
+    // rings (y < nr) and LJ partners, skin-widened shells of the build positions
+    bool want_r[MAX_RINGS];
+    bool any_ring = false;
+#pragma unroll
+    for (int y = 0; y < MAX_RINGS; ++y) {
+        want_r[y] = (kinds & (1 << (L_R0 + y))) && y < P.nr && P.rings_on && qi != 0.f;
+        any_ring |= want_r[y];
+    }
     const bool want_j = (kinds & (1 << L_LJ)) && P.lj_on;
-    const bool shells = want_m || want_l || want_j;
+    const bool shells = any_ring || want_j;
     unsigned ljmask = 0;
     if (want_j)
         for (int t = 0; t < P.ntypes; ++t) ljmask |= (P.lj[ti * MAX_TYPES + t].on ? 1u : 0u) << t;
     const double sk = P.skin;
-    const double lo_m = fmax(0.0, P.sw - sk), hi_m = P.rM + sk;
-    const double lo_l = P.rM - sk, hi_l = P.R + sk;
-    const double lo_j = fmax(0.0, P.sw - sk), hi_j = P.R + sk;
-    const double b2[6] = {lo_m * lo_m, hi_m * hi_m, lo_l * lo_l, hi_l * hi_l, lo_j * lo_j, hi_j * hi_j};
-    float b2f[6];
+    // squared shell limits: ring y [edge_y - skin, edge_{y+1} + skin), LJ [sw - skin, R + skin)
+    double lo2[MAX_RINGS + 1], hi2[MAX_RINGS + 1];
+    float lo2f[MAX_RINGS + 1], hi2f[MAX_RINGS + 1];
 #pragma unroll
-    for (int t = 0; t < 6; ++t) b2f[t] = float(b2[t]);
+    for (int y = 0; y <= MAX_RINGS; ++y) {
+        double lo, hi;
+        if (y < MAX_RINGS) { lo = y < P.nr ? P.edge[y] - sk : 0.0; hi = y < P.nr ? P.edge[y + 1] + sk : 0.0; }
+        else { lo = P.sw - sk; hi = P.R + sk; }
+        lo = fmax(lo, 0.0);
+        lo2[y] = lo * lo; hi2[y] = hi * hi;
+        lo2f[y] = float(lo2[y]); hi2f[y] = float(hi2[y]);
+    }
     const float r2s = float((P.rc + sk) * (P.rc + sk)), r2f = float((P.R + sk) * (P.R + sk));
     uint32_t* rows[NKIND];
 #pragma unroll
     for (int k = 0; k < NKIND; ++k) rows[k] = d.list[k] + (size_t)i * d.lcap[k];
-    int cnt[NKIND] = {0, 0, 0, 0, 0};
+    int cnt[NKIND] = {};
     const int n_o = min(d.ocnt[i], d.ocap);
     const uint32_t* orow = d.olist + (size_t)i * d.ocap;
     for (int base = 0; base < n_o; base += 32) {
         const int k = base + lane;
-        bool m[NKIND] = {false, false, false, false, false};
+        bool m[NKIND] = {};
         uint32_t j = 0;
         if (k < n_o) {
             j = orow[k];
@@ -337,9 +348,9 @@ __global__ void __launch_bounds__(32 * WARPS) k_inner_lists(Dev d, int kinds, in
                 const double r2 = dist2_fp64(d.xb, i, (int)j, P);
                 m[L_SHORT] = r2 < double(r2s);
                 m[L_FULL] = r2 < double(r2f);
-                m[L_RM] = want_m && qq && r2 >= b2[0] && r2 < b2[1];
-                m[L_RL] = want_l && qq && r2 >= b2[2] && r2 < b2[3];
-                m[L_LJ] = ljp && r2 >= b2[4] && r2 < b2[5];
+#pragma unroll
+                for (int y = 0; y < MAX_RINGS; ++y) m[L_R0 + y] = want_r[y] && qq && r2 >= lo2[y] && r2 < hi2[y];
+                m[L_LJ] = ljp && r2 >= lo2[MAX_RINGS] && r2 < hi2[MAX_RINGS];
             } else {
                 float dx, dy, dz;
                 sdisp(pi, pj, P.sclf, P.sclf_lo, dx, dy, dz);
@@ -351,16 +362,20 @@ __global__ void __launch_bounds__(32 * WARPS) k_inner_lists(Dev d, int kinds, in
                     // within 2e-5 (relative, in r^2) of a shell limit it is decided in FP64
                     bool near = false;
 #pragma unroll
-                    for (int t = 0; t < 6; ++t) near |= fabsf(r2 - b2f[t]) < 2e-5f * b2f[t] + 1e-6f;
+                    for (int y = 0; y <= MAX_RINGS; ++y)
+                        near |= fabsf(r2 - lo2f[y]) < 2e-5f * lo2f[y] + 1e-6f ||
+                                fabsf(r2 - hi2f[y]) < 2e-5f * hi2f[y] + 1e-6f;
                     if (near) {
                         const double r2d = dist2_fp64(d.xb, i, (int)j, P);
-                        m[L_RM] = want_m && qq && r2d >= b2[0] && r2d < b2[1];
-                        m[L_RL] = want_l && qq && r2d >= b2[2] && r2d < b2[3];
-                        m[L_LJ] = ljp && r2d >= b2[4] && r2d < b2[5];
+#pragma unroll
+                        for (int y = 0; y < MAX_RINGS; ++y)
+                            m[L_R0 + y] = want_r[y] && qq && r2d >= lo2[y] && r2d < hi2[y];
+                        m[L_LJ] = ljp && r2d >= lo2[MAX_RINGS] && r2d < hi2[MAX_RINGS];
                     } else {
-                        m[L_RM] = want_m && qq && r2 >= b2f[0] && r2 < b2f[1];
-                        m[L_RL] = want_l && qq && r2 >= b2f[2] && r2 < b2f[3];
-                        m[L_LJ] = ljp && r2 >= b2f[4] && r2 < b2f[5];
+#pragma unroll
+                        for (int y = 0; y < MAX_RINGS; ++y)
+                            m[L_R0 + y] = want_r[y] && qq && r2 >= lo2f[y] && r2 < hi2f[y];
+                        m[L_LJ] = ljp && r2 >= lo2f[MAX_RINGS] && r2 < hi2f[MAX_RINGS];
                     }
                 }
             }

@@ -200,7 +200,9 @@ int lists_needed(int family)
     // 0 BAOAB / BAOAB-RESPA, 1 BAOAB-RESPA1, 2 JUMP family
     if (family == 0) return 1 << L_FULL;
     if (family == 1) return (1 << L_FULL) | (1 << L_SHORT);
-    return (1 << L_SHORT) | (1 << L_RM) | (1 << L_RL) | (1 << L_LJ);
+    int k = (1 << L_SHORT) | (1 << L_LJ);
+    for (int y = 0; y < MAX_RINGS; ++y) k |= 1 << (L_R0 + y);
+    return k;
 }
 
 int mode_list(int mode)
@@ -219,6 +221,31 @@ int cap_of(double rho, double lo, double hi)
     return (c + 31) / 32 * 32;
 }
 
+// skin-widened shell [lo, hi) of list kind k in one replica (hi <= lo: empty)
+void shell_of(const RepParams& P, int k, double& lo, double& hi)
+{
+    const double sk = P.skin;
+    lo = 0.0; hi = 0.0;
+    if (k == L_SHORT) hi = P.rc + sk;
+    else if (k == L_FULL) hi = P.R + sk;
+    else if (k == L_LJ) { lo = P.sw - sk; hi = P.R + sk; }
+    else if (k - L_R0 < P.nr) { lo = P.edge[k - L_R0] - sk; hi = P.edge[k - L_R0 + 1] + sk; }
+}
+
+// per-atom capacity of list kind k over all replicas (32 when every shell is empty)
+int kind_cap(const md_ctx* ctx, int k)
+{
+    double rho = 0, lo = 1e300, hi = 0;
+    for (const RepParams& P : ctx->hp) {
+        double a, b;
+        shell_of(P, k, a, b);
+        if (b <= a) continue;
+        rho = std::max(rho, P.n / (P.L * P.L * P.L));
+        lo = std::min(lo, a); hi = std::max(hi, b);
+    }
+    return hi > 0 ? cap_of(rho, lo, hi) : 32;
+}
+
 RepParams make_params(const md_ctx* ctx, const RepHost& h, int r, int atom_off, int cell_off)
 {
     const md_system& s = h.sys;
@@ -235,8 +262,19 @@ RepParams make_params(const md_ctx* ctx, const RepHost& h, int r, int atom_off, 
     P.sclf = float(P.scl);
     P.sclf_lo = float(P.scl - double(P.sclf));
     P.R = s.r_cut; P.rc = s.r_split; P.h = s.h_switch; P.sw = s.r_split - s.h_switch;
-    P.one_ring = !(s.r_mid > P.sw && s.r_mid < P.R);
-    P.rM = P.one_ring ? P.sw : s.r_mid;
+    // ring edges (Sec. 3.1 ring technique): explicit interior edges, else r_M
+    // when it lies inside (r_c - h, r_E), else one ring
+    P.edge[0] = P.sw;
+    if (s.n_rings >= 1) {
+        P.nr = std::min(s.n_rings, MAX_RINGS);
+        for (int y = 1; y < P.nr; ++y) P.edge[y] = s.ring_r[y - 1];
+    } else {
+        P.nr = (s.r_mid > P.sw && s.r_mid < P.R) ? 2 : 1;
+        if (P.nr == 2) P.edge[1] = s.r_mid;
+    }
+    P.edge[P.nr] = P.R;
+    for (int y = P.nr + 1; y <= MAX_RINGS; ++y) P.edge[y] = P.R;
+    for (int y = 0; y <= MAX_RINGS; ++y) P.edgef[y] = float(P.edge[y]);
     double qmax = 0;
     for (double q : h.charge) qmax = std::max(qmax, std::fabs(q));
     bool any_lj = false;
@@ -271,13 +309,13 @@ RepParams make_params(const md_ctx* ctx, const RepHost& h, int r, int atom_off, 
     return P;
 }
 
-// per-atom bounds of a replica: L_M, L_L (C |q_i| qmax Lhat) and L_LJ
-void make_bounds(const RepHost& h, const RepParams& P, double* LM, double* LL, double* LLJ)
+// per-atom bounds of a replica: L_Y per ring (C |q_i| qmax Lhat_Y, n x MAX_RINGS) and L_LJ
+void make_bounds(const RepHost& h, const RepParams& P, double* LY, double* LLJ)
 {
     HostPair hp{P.R, P.sw, P.h, P.alpha};
     auto coul = [&](double r) { return -hp.dchi(r) * hp.u_dsf(r) + (1.0 - hp.chi(r)) * hp.du_dsf(r); };
-    const double LhM = P.one_ring ? 0.0 : grid_max(coul, P.sw, P.rM);
-    const double LhL = grid_max(coul, P.rM, P.R);
+    double Lh[MAX_RINGS] = {};
+    for (int y = 0; y < P.nr; ++y) Lh[y] = grid_max(coul, P.edge[y], P.edge[y + 1]);
     double qmax = 0;
     for (double q : h.charge) qmax = std::max(qmax, std::fabs(q));
     const int nt = h.ntypes;
@@ -295,8 +333,8 @@ void make_bounds(const RepHost& h, const RepParams& P, double* LM, double* LL, d
         }
     for (int i = 0; i < h.n; ++i) {
         const double cq = COULOMB * std::fabs(h.charge[i]) * qmax;
-        LM[i] = round_up_bound(cq * LhM);
-        LL[i] = round_up_bound(cq * LhL);
+        for (int y = 0; y < MAX_RINGS; ++y)
+            LY[MAX_RINGS * i + y] = y < P.nr ? round_up_bound(cq * Lh[y]) : 0.0;
         double m = 0;
         for (int b = 0; b < nt; ++b)
             if (present[b]) m = std::max(m, ljhat[h.type[i] * nt + b]);
@@ -314,6 +352,13 @@ int check_sys(md_ctx* ctx, const md_system* s)
         !(s->dsf_alpha >= 0) || !(s->gamma >= 0) || !(s->temperature > 0) || !(s->eps0 > 0) ||
         (s->eps_mode != 0 && s->eps_mode != 1))
         FAIL(MD_EINVAL, "md_set_system: invalid cutoff, switch, thermostat or jump parameters");
+    if (s->n_rings < 0 || s->n_rings > MAX_RINGS)
+        FAIL(MD_EINVAL, "md_set_system: n_rings must be in [0, %d]", MAX_RINGS);
+    for (int y = 1; y < s->n_rings; ++y) {
+        const double lo = y == 1 ? s->r_split - s->h_switch : s->ring_r[y - 2];
+        if (!(s->ring_r[y - 1] > lo && s->ring_r[y - 1] < s->r_cut))
+            FAIL(MD_EINVAL, "md_set_system: ring_r must increase strictly inside (r_split - h_switch, r_cut)");
+    }
     const double skin_o = std::max(s->skin, s->skin_outer);
     if (!(s->box >= 2.0 * (s->r_cut + skin_o)))
         FAIL(MD_EINVAL, "md_set_system: box %.4f must be at least 2 (r_cut + skin_outer) = %.4f", s->box,
@@ -449,8 +494,8 @@ int commit(md_ctx* ctx)
     d = Dev{};
     d.N = N; d.R = R;
     // host arrays
-    std::vector<double> x(3 * N), v(3 * N), xb(3 * N), xo(3 * N), mt(N), isqmt(N), q(N), LM(N), LL(N), LLJ(N);
-    std::vector<float> LMf(N), LLf(N), LLJf(N);
+    std::vector<double> x(3 * N), v(3 * N), xb(3 * N), xo(3 * N), mt(N), isqmt(N), q(N), LY(MAX_RINGS * N), LLJ(N);
+    std::vector<float> LYf(MAX_RINGS * N), LLJf(N);
     std::vector<int> img(3 * N), type(N), rep(N), cell_rep(cells, -1);
     std::vector<int> bi_off(N + 1, 0), ex_off(N + 1, 0), ex_idx;
     std::vector<int2> bitem, bond_ij;
@@ -458,7 +503,7 @@ int commit(md_ctx* ctx)
     std::vector<int4> ang;
     std::vector<std::vector<int2>> items(N);
     std::vector<std::vector<int>> exl(N);
-    double rmax_o = 0, rmax_s = 0, rmax_f = 0, rm_lo = 1e9, rm_hi = 0, rl_lo = 1e9, rj_lo = 1e9;
+    double rmax_o = 0;
     for (int r = 0; r < R; ++r) {
         RepHost& h = ctx->reps[r];
         const RepParams& P = ctx->hp[r];
@@ -470,14 +515,15 @@ int commit(md_ctx* ctx)
         std::memcpy(&xb[3 * o], h.xb.data(), sizeof(double) * 3 * h.n);
         std::memcpy(&xo[3 * o], h.xo.data(), sizeof(double) * 3 * h.n);
         std::memcpy(&img[3 * o], h.img.data(), sizeof(int) * 3 * h.n);
-        make_bounds(h, P, &LM[o], &LL[o], &LLJ[o]);
+        make_bounds(h, P, &LY[MAX_RINGS * o], &LLJ[o]);
         for (int i = 0; i < h.n; ++i) {
             mt[o + i] = h.mass[i] / KCAL_AMU;
             isqmt[o + i] = 1.0 / std::sqrt(mt[o + i]);
             q[o + i] = h.charge[i];
             type[o + i] = h.type[i];
             rep[o + i] = r;
-            LMf[o + i] = float(LM[o + i]); LLf[o + i] = float(LL[o + i]); LLJf[o + i] = float(LLJ[o + i]);
+            for (int y = 0; y < MAX_RINGS; ++y) LYf[MAX_RINGS * (o + i) + y] = float(LY[MAX_RINGS * (o + i) + y]);
+            LLJf[o + i] = float(LLJ[o + i]);
         }
         const int nb = (int)h.bond_k.size();
         for (int b = 0; b < nb; ++b) {
@@ -506,12 +552,7 @@ int commit(md_ctx* ctx)
             exl[a0].push_back(a1);
             exl[a1].push_back(a0);
         }
-        const double sk = P.skin;
         rmax_o = std::max(rmax_o, P.R + P.skin_o);
-        rmax_s = std::max(rmax_s, P.rc + sk);
-        rmax_f = std::max(rmax_f, P.R + sk);
-        rm_lo = std::min(rm_lo, P.sw - sk); rm_hi = std::max(rm_hi, P.rM + sk);
-        rl_lo = std::min(rl_lo, P.rM - sk); rj_lo = std::min(rj_lo, P.sw - sk);
     }
     // visiting order of the velocity phases: by replica, then grouped by an
     // estimate of the proposal rate (per-pair bound at the thermal speed plus
@@ -522,7 +563,9 @@ int commit(md_ctx* ctx)
         for (int i = 0; i < N; ++i) {
             const RepParams& P = ctx->hp[rep[i]];
             const double vth = std::sqrt(3.0 / (P.beta * mt[i]));
-            est[i] = (LM[i] + LL[i]) * P.beta * vth + 2.0 * std::sqrt(P.beta / mt[i]) / P.eps0 + LLJ[i];
+            double ly = 0;
+            for (int y = 0; y < MAX_RINGS; ++y) ly += LY[MAX_RINGS * i + y];
+            est[i] = ly * P.beta * vth + 2.0 * std::sqrt(P.beta / mt[i]) / P.eps0 + LLJ[i];
             vorder[i] = i;
         }
         std::stable_sort(vorder.begin(), vorder.end(), [&](int x, int y) {
@@ -538,15 +581,15 @@ int commit(md_ctx* ctx)
     // device arrays
     RepParams* dP;
     int *drep, *dvorder, *dtype, *dimg, *dbi_off, *dex_off, *dex_idx;
-    double *dmt, *disqmt, *dq, *dLM, *dLL, *dLLJ, *dbk, *dbr0, *dak, *dat0;
-    float *dLMf, *dLLf, *dLLJf;
+    double *dmt, *disqmt, *dq, *dLY, *dLLJ, *dbk, *dbr0, *dak, *dat0;
+    float *dLYf, *dLLJf;
     int2 *dbitem, *dbij;
     int4* dang;
 #define AL(p, n) if ((rc = dalloc(ctx, &(p), (n)))) return rc
     AL(dP, R); AL(drep, N); AL(dvorder, N); AL(dtype, N); AL(dimg, 3 * N); AL(dbi_off, N + 1);
     AL(dex_off, N + 1); AL(dex_idx, ex_idx.size());
-    AL(dmt, N); AL(disqmt, N); AL(dq, N); AL(dLM, N); AL(dLL, N); AL(dLLJ, N);
-    AL(dLMf, N); AL(dLLf, N); AL(dLLJf, N);
+    AL(dmt, N); AL(disqmt, N); AL(dq, N); AL(dLY, MAX_RINGS * N); AL(dLLJ, N);
+    AL(dLYf, MAX_RINGS * N); AL(dLLJf, N);
     AL(dbitem, bitem.size()); AL(dbij, bond_ij.size()); AL(dbk, bond_k.size()); AL(dbr0, bond_r0.size());
     AL(dang, ang.size()); AL(dak, ang_k.size()); AL(dat0, ang_t0.size());
     AL(d.bterm, 3 * bond_k.size()); AL(d.aterm, 6 * ang_k.size());
@@ -560,10 +603,8 @@ int commit(md_ctx* ctx)
     d.total_cells = cells;
     d.ocap = cap_of(rho, 0, rmax_o);
     AL(d.olist, (size_t)N * d.ocap); AL(d.ocnt, N);
-    const double lo_shell[NKIND] = {0, 0, rm_lo, rl_lo, rj_lo};
-    const double hi_shell[NKIND] = {rmax_s, rmax_f, rm_hi, rmax_f, rmax_f};
     for (int k = 0; k < NKIND; ++k) {
-        d.lcap[k] = (ctx->kinds & (1 << k)) ? cap_of(rho, lo_shell[k], hi_shell[k]) : 32;
+        d.lcap[k] = (ctx->kinds & (1 << k)) ? kind_cap(ctx, k) : 32;
         AL(d.list[k], (size_t)N * d.lcap[k]);
         AL(d.lcnt[k], N);
     }
@@ -574,8 +615,8 @@ int commit(md_ctx* ctx)
 #undef AL
     d.ev_cap = evcap;
     d.P = dP; d.rep = drep; d.vorder = dvorder; d.type = dtype; d.img = dimg; d.bi_off = dbi_off; d.ex_off = dex_off;
-    d.ex_idx = dex_idx; d.mt = dmt; d.isqmt = disqmt; d.q = dq; d.LM = dLM; d.LL = dLL; d.LLJ = dLLJ;
-    d.LMf = dLMf; d.LLf = dLLf; d.LLJf = dLLJf; d.bitem = dbitem; d.bond_ij = dbij; d.bond_k = dbk;
+    d.ex_idx = dex_idx; d.mt = dmt; d.isqmt = disqmt; d.q = dq; d.LY = dLY; d.LLJ = dLLJ;
+    d.LYf = dLYf; d.LLJf = dLLJf; d.bitem = dbitem; d.bond_ij = dbij; d.bond_k = dbk;
     d.bond_r0 = dbr0; d.ang = dang; d.ang_k = dak; d.ang_t0 = dat0;
     if ((rc = upload(ctx, dP, ctx->hp.data(), R)) || (rc = upload(ctx, drep, rep.data(), N)) ||
         (rc = upload(ctx, dvorder, vorder.data(), N)) ||
@@ -583,9 +624,8 @@ int commit(md_ctx* ctx)
         (rc = upload(ctx, dbi_off, bi_off.data(), N + 1)) || (rc = upload(ctx, dex_off, ex_off.data(), N + 1)) ||
         (rc = upload(ctx, dex_idx, ex_idx.data(), ex_idx.size())) || (rc = upload(ctx, dmt, mt.data(), N)) ||
         (rc = upload(ctx, disqmt, isqmt.data(), N)) || (rc = upload(ctx, dq, q.data(), N)) ||
-        (rc = upload(ctx, dLM, LM.data(), N)) || (rc = upload(ctx, dLL, LL.data(), N)) ||
-        (rc = upload(ctx, dLLJ, LLJ.data(), N)) || (rc = upload(ctx, dLMf, LMf.data(), N)) ||
-        (rc = upload(ctx, dLLf, LLf.data(), N)) || (rc = upload(ctx, dLLJf, LLJf.data(), N)) ||
+        (rc = upload(ctx, dLY, LY.data(), (size_t)MAX_RINGS * N)) || (rc = upload(ctx, dLLJ, LLJ.data(), N)) ||
+        (rc = upload(ctx, dLYf, LYf.data(), (size_t)MAX_RINGS * N)) || (rc = upload(ctx, dLLJf, LLJf.data(), N)) ||
         (rc = upload(ctx, dbitem, bitem.data(), bitem.size())) ||
         (rc = upload(ctx, dbij, bond_ij.data(), bond_ij.size())) ||
         (rc = upload(ctx, dbk, bond_k.data(), bond_k.size())) ||
@@ -636,20 +676,10 @@ int ensure_kinds(md_ctx* ctx, int mask)
     if (!add) return MD_OK;
     Dev& d = ctx->d;
     // capacities for the new kinds
-    double rho = 0, hi_s = 0, hi_f = 0, lo_m = 1e9, hi_m = 0, lo_l = 1e9, lo_j = 1e9;
-    for (int r = 0; r < d.R; ++r) {
-        const RepParams& P = ctx->hp[r];
-        rho = std::max(rho, P.n / (P.L * P.L * P.L));
-        hi_s = std::max(hi_s, P.rc + P.skin); hi_f = std::max(hi_f, P.R + P.skin);
-        lo_m = std::min(lo_m, P.sw - P.skin); hi_m = std::max(hi_m, P.rM + P.skin);
-        lo_l = std::min(lo_l, P.rM - P.skin); lo_j = std::min(lo_j, P.sw - P.skin);
-    }
-    const double lo_shell[NKIND] = {0, 0, lo_m, lo_l, lo_j};
-    const double hi_shell[NKIND] = {hi_s, hi_f, hi_m, hi_f, hi_f};
     int rc;
     for (int k = 0; k < NKIND; ++k) {
         if (!(add & (1 << k))) continue;
-        d.lcap[k] = cap_of(rho, lo_shell[k], hi_shell[k]);
+        d.lcap[k] = kind_cap(ctx, k);
         if ((rc = dalloc(ctx, &d.list[k], (size_t)d.N * d.lcap[k]))) return rc;
     }
     launch_late_lists(d, add, ctx->s);
@@ -1203,7 +1233,9 @@ int md_run_phase(md_ctx* ctx, int phase, double tau2_ps, int64_t s0, int half, i
         FAIL(MD_EINVAL, "md_run_phase: bad phase, half, tau2 or accel_mode");
     int rc = commit(ctx);
     if (rc) return rc;
-    const int need = (phase == 0 ? ((1 << L_RM) | (1 << L_RL)) | mode_list(accel_mode) : (1 << L_LJ));
+    int rings = 0;
+    for (int y = 0; y < MAX_RINGS; ++y) rings |= 1 << (L_R0 + y);
+    const int need = (phase == 0 ? rings | mode_list(accel_mode) : (1 << L_LJ));
     if ((rc = ensure_kinds(ctx, need))) return rc;
     Dev& d = ctx->d;
     if (phase == 0) force(ctx, accel_mode, d.a0);
@@ -1220,9 +1252,10 @@ int md_get_list(md_ctx* ctx, int replica, int kind, int atom, int* host_out, int
     if (!ctx) return MD_EINVAL;
     int rc = commit(ctx);
     if (rc) return rc;
-    if (replica < 0 || replica >= ctx->d.R || kind < 0 || kind > 2 || atom < 0 || atom >= ctx->reps[replica].n)
+    if (replica < 0 || replica >= ctx->d.R || kind < 0 || kind > MAX_RINGS || atom < 0 ||
+        atom >= ctx->reps[replica].n)
         FAIL(MD_EINVAL, "md_get_list: bad replica, kind or atom");
-    const int k = kind == 0 ? L_RM : (kind == 1 ? L_RL : L_LJ);
+    const int k = kind < MAX_RINGS ? L_R0 + kind : L_LJ;
     if ((rc = ensure_kinds(ctx, 1 << k))) return rc;
     Dev& d = ctx->d;
     const int gi = ctx->rep_atom_off[replica] + atom;

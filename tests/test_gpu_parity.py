@@ -77,12 +77,21 @@ def test_fixed_point_forces_do_not_depend_on_threads_per_atom(M, oracle_mod, wat
         assert np.array_equal(g, gs[0])
 
 
+RINGS = [None, [], [4.8, 6.0, 7.5]]     # rings of r_mid (two), one ring, four rings
+
+
+@pytest.mark.parametrize("ring_r", RINGS)
 @pytest.mark.parametrize("precision", [0, 1])
-def test_jump_lists_identical(M, oracle_mod, water648, precision):
-    e, o = make(M, oracle_mod, water648, precision)
+def test_jump_lists_identical(M, oracle_mod, water648, precision, ring_r):
+    e, o = make(M, oracle_mod, water648, precision, ring_r=ring_r)
+    nonempty = np.zeros(5, dtype=int)
     for i in range(0, water648.n, 7):
-        for kind in (0, 1, 2):
-            np.testing.assert_array_equal(e.get_list(kind, i), o.list_of(kind, i))
+        for kind in range(5):       # rings 0..3, LJ
+            lg = e.get_list(kind, i)
+            np.testing.assert_array_equal(lg, o.list_of(kind, i))
+            nonempty[kind] += len(lg) > 0
+    n_rings = 2 if ring_r is None else len(ring_r) + 1
+    assert (nonempty[:n_rings] > 0).all() and (nonempty[n_rings:4] == 0).all() and nonempty[4] > 0
 
 
 def test_baoab_trajectory_fp64(M, oracle_mod, water648):
@@ -97,8 +106,9 @@ def test_baoab_trajectory_fp64(M, oracle_mod, water648):
     assert e.observables()["list_rebuilds"] == o.counters()[5]
 
 
-def test_jump_trajectory_and_events_fp64(M, oracle_mod, water648):
-    e, o = make(M, oracle_mod, water648, 0, seed=7)
+@pytest.mark.parametrize("ring_r", RINGS)
+def test_jump_trajectory_and_events_fp64(M, oracle_mod, water648, ring_r):
+    e, o = make(M, oracle_mod, water648, 0, seed=7, ring_r=ring_r)
     o.events_enable(1 << 22)
     e.jump(100)
     o.jump(100)
@@ -152,10 +162,11 @@ def test_jump_mixed_precision_tracks_oracle(M, oracle_mod, water648):
     assert err.mean() < 1e-3
 
 
-def test_jump_mixed_precision_statistics(M, oracle_mod, water648):
+@pytest.mark.parametrize("ring_r", [None, [4.8, 6.0, 7.5]])
+def test_jump_mixed_precision_statistics(M, oracle_mod, water648, ring_r):
     """Over 200 steps the mixed-mode path keeps the oracle's jump statistics:
     proposals per atom-step and accepted fractions agree within 3 %."""
-    e, o = make(M, oracle_mod, water648, 1, seed=8)
+    e, o = make(M, oracle_mod, water648, 1, seed=8, ring_r=ring_r)
     e.jump(200)
     o.jump(200)
     ob = e.observables()
@@ -166,12 +177,13 @@ def test_jump_mixed_precision_statistics(M, oracle_mod, water648):
     assert ob["error_flags"] == 0
 
 
-def test_sampled_cprime_phase_at_24000_atoms(M, oracle_mod):
+@pytest.mark.parametrize("ring_r", [None, [5.0, 5.5, 7.0]])
+def test_sampled_cprime_phase_at_24000_atoms(M, oracle_mod, ring_r):
     """One C' phase on 24,000 atoms (8,000 waters, 62.1 A) on the GPU in both
     precisions, checked atom by atom against the oracle on 300 sampled atoms."""
     from paper_2412_15073_gb300 import systems
     w = systems.water_box(8000, box=62.1, seed=0)
-    p = dict(PARAMS, skin=0.5, skin_outer=1.5)
+    p = dict(PARAMS, skin=0.5, skin_outer=1.5, ring_r=ring_r)
     o = oracle_mod.Oracle(w, seed=3, replica=0, **p)
     rng = np.random.default_rng(1)
     idx = rng.choice(w.n, 300, replace=False)
@@ -267,6 +279,9 @@ def test_invalid_inputs_are_rejected(M, water648):
         e.jump(1)                                                         # no system yet
     with pytest.raises(M.MDError):
         e.set_system(1, water648)                                         # replica out of range
+    for bad in ([6.0, 5.5], [4.0], [9.5], [5.0, 5.5, 6.0, 7.0]):
+        with pytest.raises((M.MDError, ValueError)):
+            e.set_system(0, water648, ring_r=bad)                        # ring edges not inside (r_c-h, r_E)
 
 
 def test_velocity_phase_variants_are_identical(M, oracle_mod, water648, monkeypatch):
