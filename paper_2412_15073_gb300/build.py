@@ -15,6 +15,9 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libmdjump.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 SOURCES = ["md_api.cu", "k_lists.cu", "k_force.cu", "k_jump.cu", "noalloc.cu"]
+# the velocity-phase kernel comes in several occupancy variants that must give
+# identical results: no mul/add contraction there, every FMA is written out
+PER_FILE = {"k_jump.cu": ["-fmad=false"]}
 HEADERS = ["common.cuh", "engine.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
@@ -47,7 +50,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
         o = os.path.join(BUILD_DIR, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + hdrs):
-            jobs.append([nvcc(), *flags, "-c", s, "-o", o])
+            jobs.append([nvcc(), *flags, *PER_FILE.get(src, []), "-c", s, "-o", o])
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:

@@ -15,7 +15,8 @@ struct Dev {
     int N, R;
     const RepParams* P;
     const int* rep;                 // atom -> replica
-    const int* vorder;              // visiting order of the velocity phases (grouped by jump rate)
+    int* vorder;                    // visiting order of the velocity phases (grouped by jump rate)
+    int *vkey, *vhist, *vofs;       // rate sort: bucket per atom, counts and offsets per (replica, bucket)
     // state (FP64 master copies)
     double *x, *v, *xb, *xo;        // positions, velocities, positions at list build / outer build
     int* img;                       // periodic image counts
@@ -84,11 +85,11 @@ void launch_advance(const Dev& d, long long nsteps, cudaStream_t s);
 
 // ---- jumps (k_jump.cu) --------------------------------------------------------------
 // order 0: C' then J' (first half of a step), 1: J' then C' (second half)
-// variant of the mixed-mode kernel: occupancy targets of 1, 4, 5, 6 blocks of
-// 128 threads (0-3), and the same with deferred G~ draws (4-7: an accepted
-// proposal waits until 8 lanes of the warp wait, then they draw together).
-// Every variant computes the same values.
-constexpr int NVPHASE_VARIANTS = 8;
+// variant of the mixed-mode kernel: occupancy targets of 3, 4, 5, 6 blocks of
+// 128 threads. Every variant computes the same values. In mixed mode a C'
+// phase first orders the atoms by their expected number of proposals.
+constexpr int NVPHASE_VARIANTS = 4;
+constexpr int RATE_BUCKETS = 128;
 void launch_vphase(const Dev& d, const double* a, double tau2, uint32_t s_off, int half, int order,
                    int doC, int doJ, int fp64, int variant, cudaStream_t s);
 // same with an absolute stream index s0 (md_run_phase)

@@ -339,17 +339,63 @@ __device__ __noinline__ float sample_gtilde_f(const RepParams& P, uint32_t il, u
     return ok ? G : 0.f;
 }
 
+// radial derivative of (1 - chi) U_DSF per unit C q_i q_j in FP32, from
+// per-replica constants held in registers (r >= r_c - h, the jump range)
+__device__ __forceinline__ float coul_long_f(float r, float rinv, float alpha, float kexp, float eR, float fR,
+                                             float R, float sw, float h)
+{
+    const float e = erfcf(alpha * r);
+    const float g = kexp * expf(-alpha * alpha * r * r);
+    const float du = -(e * rinv + g) * rinv + fR;
+    if (r >= sw + h) return du;                 // chi = 0 past the switch
+    const float u = e * rinv - eR + fR * (r - R);
+    float c, dc;
+    chi_and_slope<float>(r, sw, h, c, dc);
+    return -dc * u + (1.f - c) * du;
+}
+
+// ring of a proposal in FP32; a target that rounds up to Lam falls back to the
+// outermost ring with weight (never to an empty ring)
+__device__ __forceinline__ int ring_pick_f(const float (&w)[MAX_RINGS], float target, int nr)
+{
+    int Y = -1, last = 0;
+    float cum = 0.f;
+#pragma unroll
+    for (int y = 0; y < MAX_RINGS; ++y) {
+        cum += w[y];
+        if (y < nr && w[y] > 0.f) last = y;
+        if (Y < 0 && y < nr && target < cum) Y = y;
+    }
+    return Y < 0 ? last : Y;
+}
+
 // C' for atom i in FP32 (Algorithm 4, adaptive or constant eps, up to four rings).
-// The Philox block of proposal k+1 is computed while the partner of proposal
-// k is being fetched.
-template <bool DEFER>
+// Software-pipelined: right after proposal k is placed in time, the bound at
+// the new state and the ring of proposal k+1 are computed and the list entry
+// of k+1 is fetched; its position is fetched once proposal k is decided. If
+// proposal k jumps, the bound and ring of k+1 are recomputed (and the entry
+// refetched when the ring changed), so the sequence is that of Algorithm 4.
 __device__ __forceinline__ void cprime_f(const Dev& d, const RepParams& P, int i, int il, float3& jv,
                                          const float3 v0, const float3 a, float T2, uint32_t s0, int half,
                                          Tally& tl, uint32_t& err)
 {
     int N[MAX_RINGS];
     if (ring_counts(d, P, i, N) == 0) return;
+    // per-replica constants in registers (the loop may store events, after
+    // which loads through P would be repeated)
+    const float sc = P.sclf, sclo = P.sclf_lo;
+    const uint32_t key0 = P.seed, key1 = P.replica;
+    const int nr = P.nr;
+    float elo[MAX_RINGS], ehi[MAX_RINGS];     // ring y is [elo[y], ehi[y])
+#pragma unroll
+    for (int y = 0; y < MAX_RINGS; ++y) { elo[y] = P.edgef[y]; ehi[y] = P.edgef[y + 1]; }
+    const float alpha = P.alphaf, kexp = P.kexpf, eR = P.eRf, fR = P.fRf;
+    const float R = float(P.R), sw = float(P.sw), h = float(P.h);
     const float beta = float(P.beta), eps0 = float(P.eps0);
+    const bool adaptive = P.eps_mode == 1;
+    const int atom_off = P.atom_off;
+    const uint32_t ctag = (uint32_t(TAG_C) << 24) | (uint32_t(half) << 20);
+
     const float mt = float(d.mt[i]);
     const float sbm = sqrtf(beta * mt), sbom = sqrtf(beta / mt);
     const float4 ly4 = __ldg(reinterpret_cast<const float4*>(d.LYf) + i);
@@ -359,54 +405,39 @@ __device__ __forceinline__ void cprime_f(const Dev& d, const RepParams& P, int i
     for (int y = 0; y < MAX_RINGS; ++y) fN[y] = float(N[y]);
     const uint4 pi = d.pos[i];
     const float qiC = float(COULOMB) * __uint_as_float(pi.w);
-    const bool adaptive = P.eps_mode == 1;
     const float c0 = sbom / (eps0 * 2.5066282746310002f);
     const float aa = a.x * a.x + a.y * a.y + a.z * a.z;
-    const float sc = P.sclf;
+
     float t = 0.f;
     float vx = v0.x + jv.x, vy = v0.y + jv.y, vz = v0.z + jv.z;
-    uint32_t k = 0;
-    U4 u = draw(P, uint32_t(il), s0, TAG_C, half, 0, 0);
-    // accepted proposal waiting for its G~ draw (DEFER: draws are made
-    // together once 8 lanes wait or only waiting lanes remain)
-    bool pending = false;
-    float pgx = 0.f, pgy = 0.f, pgz = 0.f, pgn = 1.f, peta = 0.f, peps = 0.f;
-    uint32_t pk = 0;
-    int pJ = 0;
-    for (;;) {
-        if (DEFER) {
-            const unsigned act = __activemask();
-            const unsigned waiting = __ballot_sync(act, pending);
-            if (__popc(waiting) >= 8 || waiting == act) {
-                if (pending) {
-                    int att;
-                    bool ok;
-                    const float G = sample_gtilde_f(P, uint32_t(il), s0, half, pk, peta, &att, &ok);
-                    tl.satt += att;
-                    if (!ok) err |= F_LIMIT;
-                    const float coef = 2.f * peps / (sbm * (1.f + peps * peps)) * (peta + G) / pgn;
-                    jv.x -= coef * pgx; jv.y -= coef * pgy; jv.z -= coef * pgz;
-                    vx -= coef * pgx; vy -= coef * pgy; vz -= coef * pgz;
-                    tl.cacc++;
-                    log_event(d, (long long)s0, half, int(TAG_C), d.rep[i], il, pk, pJ - P.atom_off);
-                    pending = false;
-                }
-                continue;
-            }
-            if (pending) continue;
-        }
+    // bound at the current state: B, per-ring Lam_Y and weights, total Lam
+    float B, Lam, LamYv[MAX_RINGS], w[MAX_RINGS];
+    auto bound = [&]() {
         const float s = T2 - t;
         const float vv = vx * vx + vy * vy + vz * vz;
         const float va = vx * a.x + vy * a.y + vz * a.z;
-        const float B = sqrtf(vv + s * s * aa + 2.f * s * fmaxf(va, 0.f));
-        float LamYv[MAX_RINGS], w[MAX_RINGS], Lam = 0.f;
+        B = sqrtf(vv + s * s * aa + 2.f * s * fmaxf(va, 0.f));
+        Lam = 0.f;
 #pragma unroll
         for (int y = 0; y < MAX_RINGS; ++y) {
             LamYv[y] = adaptive ? fmaf(beta * LYv[y], B, c0) : LYv[y] * fmaf(beta, B, c0);
             w[y] = fN[y] * LamYv[y];
             Lam += w[y];
         }
-        const float Tn = -__logf(unif<float>(u.x)) / Lam;
+    };
+    auto entry = [&](int Y, uint32_t uz) -> uint32_t {
+        const uint32_t* row = d.list[L_R0 + Y] + (size_t)i * d.lcap[L_R0 + Y];
+        return __ldg(row + __umulhi(uz, uint32_t(ring_sel(N, Y))));
+    };
+    uint32_t k = 0;
+    U4 u = philox(uint32_t(il), s0, ctag, 0, key0, key1);
+    bound();
+    int Yn = ring_pick_f(w, unif<float>(u.y) * Lam, nr);
+    uint32_t Jn = entry(Yn, u.z);
+    uint4 pjn = __ldg(d.pos + Jn);
+    for (;;) {
+        // proposal k: its time, ring Yn, partner Jn and position pjn are ready
+        const float Tn = __fdividef(-__logf(unif<float>(u.x)), Lam);
         if (!(Lam > 0.f) || t + Tn > T2) break;
         const float tprev = t;
         t += Tn;
@@ -414,35 +445,40 @@ __device__ __forceinline__ void cprime_f(const Dev& d, const RepParams& P, int i
         vy = fmaf(t, a.y, v0.y) + jv.y;
         vz = fmaf(t, a.z, v0.z) + jv.z;
         tl.cprop++;
-        const int Y = ring_pick<float>(w, unif<float>(u.y) * Lam, P.nr);
-        const uint32_t* row = d.list[L_R0 + Y] + (size_t)i * d.lcap[L_R0 + Y];
-        const int J = int(__ldg(row + __umulhi(u.z, uint32_t(ring_sel(N, Y)))));
-        const uint4 pj = __ldg(d.pos + J);
+        const int Y = Yn;
+        const int J = int(Jn);
+        const uint4 pj = pjn;
+        const float Bk = B, LamYk = ring_sel(LamYv, Y), LYk = ring_sel(LYv, Y);
+        const float lo = ring_sel(elo, Y), hi = ring_sel(ehi, Y);
         const uint32_t uacc = u.w;
         const uint32_t kk = k;
         ++k;
-        u = draw(P, uint32_t(il), s0, TAG_C, half, 0, k);        // next proposal, overlaps the gathers
+        // next proposal: draw, bound at the new state, ring and list entry
+        u = philox(uint32_t(il), s0, ctag, k, key0, key1);
+        bound();
+        Yn = ring_pick_f(w, unif<float>(u.y) * Lam, nr);
+        Jn = entry(Yn, u.z);
+        // decide proposal kk
         float dx, dy, dz;
-        sdisp(pi, pj, sc, P.sclf_lo, dx, dy, dz);
+        sdisp(pi, pj, sc, sclo, dx, dy, dz);
         const float r2 = dx * dx + dy * dy + dz * dz;
-        const float r = sqrtf(r2);
-        const bool inside = r >= P.edgef[Y] && r < P.edgef[Y + 1];
-        if (inside) {
-            const float f = qiC * __uint_as_float(pj.w) * coul_long<float>(P, r) / r;
+        const float rinv = rsqrtf(r2);
+        const float r = r2 * rinv;
+        if (r >= lo && r < hi) {
+            const float f = qiC * __uint_as_float(pj.w) * coul_long_f(r, rinv, alpha, kexp, eR, fR, R, sw, h) * rinv;
             const float gx = f * dx, gy = f * dy, gz = f * dz;
-            const float gn = sqrtf(gx * gx + gy * gy + gz * gz);
+            const float gn = fabsf(f) * r;
             if (gn > 0.f) {
                 const float vg = vx * gx + vy * gy + vz * gz;
-                const float LamY = ring_sel(LamYv, Y);
                 float eps, eta, p;
                 if (adaptive) {
                     eps = eps0 * gn;
                     eta = eps0 * sbm * vg;
-                    p = sbom * theta<float>(eta) / eps0 / LamY;
+                    p = __fdividef(sbom * theta<float>(eta), eps0 * LamYk);
                 } else {
                     eps = eps0;
-                    eta = eps0 * sbm * vg / gn;
-                    p = gn * theta<float>(eta) / (ring_sel(LYv, Y) * (eps0 * sbm * B + 0.3989422804014327f));
+                    eta = __fdividef(eps0 * sbm * vg, gn);
+                    p = __fdividef(gn * theta<float>(eta), LYk * (eps0 * sbm * Bk + 0.3989422804014327f));
                 }
                 bool acc;
                 const float U = unif<float>(uacc);
@@ -459,10 +495,7 @@ __device__ __forceinline__ void cprime_f(const Dev& d, const RepParams& P, int i
                     acc = U <= p;
                     if (p > 1.f) err |= F_BOUND;
                 }
-                if (acc && DEFER) {
-                    pending = true;
-                    pgx = gx; pgy = gy; pgz = gz; pgn = gn; peta = eta; peps = eps; pk = kk; pJ = J;
-                } else if (acc) {
+                if (acc) {
                     int att;
                     bool ok;
                     const float G = sample_gtilde_f(P, uint32_t(il), s0, half, kk, eta, &att, &ok);
@@ -472,17 +505,22 @@ __device__ __forceinline__ void cprime_f(const Dev& d, const RepParams& P, int i
                     jv.x -= coef * gx; jv.y -= coef * gy; jv.z -= coef * gz;
                     vx -= coef * gx; vy -= coef * gy; vz -= coef * gz;
                     tl.cacc++;
-                    log_event(d, (long long)s0, half, int(TAG_C), d.rep[i], il, kk, J - P.atom_off);
+                    log_event(d, (long long)s0, half, int(TAG_C), d.rep[i], il, kk, J - atom_off);
+                    // the velocity changed: bound and ring of the next proposal again
+                    bound();
+                    const int Y2 = ring_pick_f(w, unif<float>(u.y) * Lam, nr);
+                    if (Y2 != Yn) { Yn = Y2; Jn = entry(Yn, u.z); }
                 }
             }
         }
+        pjn = __ldg(d.pos + Jn);
         if (k >= uint32_t(KMAX)) { err |= F_LIMIT; break; }
     }
 }
 
 // mixed-mode velocity phase; threads visit atoms in the order vorder (atoms
 // grouped by expected jump rate so that the lanes of a warp do similar work)
-template <int MINB, bool DEFER>
+template <int MINB>
 __global__ void __launch_bounds__(128, MINB) k_vphase_f(Dev d, const double* a, double tau2, uint32_t s_off, int s_abs,
                                                         int half, int order, int doC, int doJ)
 {
@@ -507,7 +545,7 @@ __global__ void __launch_bounds__(128, MINB) k_vphase_f(Dev d, const double* a, 
                     const float3 v0 = make_float3(float(d.v[3 * i]), float(d.v[3 * i + 1]), float(d.v[3 * i + 2]));
                     const float3 af = a ? make_float3(float(a[3 * i]), float(a[3 * i + 1]), float(a[3 * i + 2]))
                                         : make_float3(0.f, 0.f, 0.f);
-                    cprime_f<DEFER>(d, P, i, il, jv, v0, af, float(tau2), s0, half, tl, err);
+                    cprime_f(d, P, i, il, jv, v0, af, float(tau2), s0, half, tl, err);
                 }
                 // FP64 end of the phase: (v0 + (tau/2) a) + sum of the jumps; the
                 // first sum rounds like a B kick, so a phase without jumps is one
@@ -581,7 +619,96 @@ __global__ void __launch_bounds__(128) k_vphase(Dev d, const double* a, double t
     warp_add(&C[C_GUARD], tl.guard, uniform, lane);
 }
 
+// expected number of C' proposals of atom i in the coming phase (the bound
+// Lam at its start times tau/2), as a bucket; high rates get low keys
+__global__ void k_rate_key(Dev d, const double* a, double tau2)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.N) return;
+    const int r = d.rep[i];
+    const RepParams& P = d.P[r];
+    int N[MAX_RINGS];
+    float mu = 0.f;
+    if (P.rings_on && ring_counts(d, P, i, N) > 0) {
+        const float vx = float(d.v[3 * i]), vy = float(d.v[3 * i + 1]), vz = float(d.v[3 * i + 2]);
+        const float ax = a ? float(a[3 * i]) : 0.f, ay = a ? float(a[3 * i + 1]) : 0.f, az = a ? float(a[3 * i + 2]) : 0.f;
+        const float s = float(tau2);
+        const float va = vx * ax + vy * ay + vz * az;
+        const float B = sqrtf(vx * vx + vy * vy + vz * vz + s * s * (ax * ax + ay * ay + az * az) + 2.f * s * fmaxf(va, 0.f));
+        const float beta = float(P.beta), mt = float(d.mt[i]);
+        const float c0 = sqrtf(beta / mt) / (float(P.eps0) * 2.5066282746310002f);
+        const float4 ly = __ldg(reinterpret_cast<const float4*>(d.LYf) + i);
+        const float LYv[MAX_RINGS] = {ly.x, ly.y, ly.z, ly.w};
+        float lam = 0.f;
+#pragma unroll
+        for (int y = 0; y < MAX_RINGS; ++y)
+            lam += float(N[y]) * (P.eps_mode == 1 ? beta * LYv[y] * B + c0 : LYv[y] * (beta * B + c0));
+        mu = lam * s;
+    }
+    const int b = min(RATE_BUCKETS - 1, int(mu * 0.5f));
+    const int key = r * RATE_BUCKETS + (RATE_BUCKETS - 1 - b);
+    d.vkey[i] = key;
+    atomicAdd(&d.vhist[key], 1);
+}
+
+// exclusive scan of the bucket counts into offsets (one block); clears the counts
+__global__ void __launch_bounds__(1024) k_rate_scan(Dev d)
+{
+    __shared__ int warp_tot[32];
+    __shared__ int carry;
+    const int nk = d.R * RATE_BUCKETS;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nk; base += 1024) {
+        const int k = base + threadIdx.x;
+        const int c = k < nk ? d.vhist[k] : 0;
+        int x = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_tot[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            int w = warp_tot[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            warp_tot[lane] = w;
+        }
+        __syncthreads();
+        const int before = carry + (wid ? warp_tot[wid - 1] : 0) + x - c;
+        if (k < nk) { d.vofs[k] = before; d.vhist[k] = 0; }
+        __syncthreads();
+        if (threadIdx.x == 1023) carry = before + c;
+        __syncthreads();
+    }
+}
+
+__global__ void k_rate_scatter(Dev d)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.N) return;
+    d.vorder[atomicAdd(&d.vofs[d.vkey[i]], 1)] = i;
+}
+
 }  // namespace
+
+// visiting order of a mixed-mode C' phase: atoms by replica, then by their
+// expected number of proposals (descending), so that the lanes of a warp run
+// chains of similar length. The order within a bucket does not matter: each
+// atom's chain depends on its own counter-based draws only.
+static void rate_order(const Dev& d, const double* a, double tau2, cudaStream_t st)
+{
+    const int nb = (d.N + 255) / 256;
+    k_rate_key<<<nb, 256, 0, st>>>(d, a, tau2);
+    k_rate_scan<<<1, 1024, 0, st>>>(d);
+    k_rate_scatter<<<nb, 256, 0, st>>>(d);
+}
 
 static void vphase_any(const Dev& d, const double* a, double tau2, uint32_t s, int s_abs, int half, int order,
                        int doC, int doJ, int fp64, int variant, cudaStream_t st)
@@ -591,15 +718,12 @@ static void vphase_any(const Dev& d, const double* a, double tau2, uint32_t s, i
         k_vphase<double><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, order, doC, doJ);
         return;
     }
+    if (doC) rate_order(d, a, tau2, st);
     switch (variant) {
-    case 1: k_vphase_f<4, false><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, order, doC, doJ); break;
-    case 2: k_vphase_f<5, false><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, order, doC, doJ); break;
-    case 3: k_vphase_f<6, false><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, order, doC, doJ); break;
-    case 4: k_vphase_f<1, true><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, order, doC, doJ); break;
-    case 5: k_vphase_f<4, true><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, order, doC, doJ); break;
-    case 6: k_vphase_f<5, true><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, order, doC, doJ); break;
-    case 7: k_vphase_f<6, true><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, order, doC, doJ); break;
-    default: k_vphase_f<1, false><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, order, doC, doJ); break;
+    case 1: k_vphase_f<4><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, order, doC, doJ); break;
+    case 2: k_vphase_f<5><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, order, doC, doJ); break;
+    case 3: k_vphase_f<6><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, order, doC, doJ); break;
+    default: k_vphase_f<3><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, order, doC, doJ); break;
     }
 }
 

@@ -610,6 +610,7 @@ int commit(md_ctx* ctx)
     }
     AL(d.flags, 2 * R); AL(d.err, R); AL(d.ovf, R); AL(d.cnt, (size_t)R * NCOUNT); AL(d.energy, 6 * R);
     AL(d.step_base, R); AL(d.stepc, 2 * R);
+    AL(d.vkey, N); AL(d.vhist, (size_t)R * RATE_BUCKETS); AL(d.vofs, (size_t)R * RATE_BUCKETS);
     const long long evcap = ctx->cfg.event_log_cap > 0 ? ctx->cfg.event_log_cap : 0;
     AL(d.ev, (size_t)6 * (evcap ? evcap : 1)); AL(d.ev_n, 1);
 #undef AL
@@ -644,6 +645,7 @@ int commit(md_ctx* ctx)
     CK(cudaMemsetAsync(d.al, 0, sizeof(double) * 3 * N, ctx->s));
     CK(cudaMemsetAsync(d.err, 0, sizeof(uint32_t) * R, ctx->s));
     CK(cudaMemsetAsync(d.ovf, 0, sizeof(uint32_t) * R, ctx->s));
+    CK(cudaMemsetAsync(d.vhist, 0, sizeof(int) * R * RATE_BUCKETS, ctx->s));
     ctx->on_device = true;
     // initial build at the stored reference positions
     launch_check(d, 1, 1, ctx->s);
@@ -846,7 +848,7 @@ int tune_vphase(md_ctx* ctx, const double* a, double tau2)
 void vphase(md_ctx* ctx, const double* a, double tau2, uint32_t s_off, int half, int order)
 {
     if (ctx->vvar < 0) tune_vphase(ctx, a, tau2);
-    Prof p(ctx, 2, 1);
+    Prof p(ctx, 2, ctx->fp64 ? 1 : 4);
     launch_vphase(ctx->d, a, tau2, s_off, half, order, 1, 1, ctx->fp64, ctx->vvar < 0 ? 0 : ctx->vvar, ctx->s);
 }
 
@@ -1239,8 +1241,11 @@ int md_run_phase(md_ctx* ctx, int phase, double tau2_ps, int64_t s0, int half, i
     if ((rc = ensure_kinds(ctx, need))) return rc;
     Dev& d = ctx->d;
     if (phase == 0) force(ctx, accel_mode, d.a0);
-    launch_vphase_abs(d, phase == 0 ? d.a0 : nullptr, tau2_ps, uint32_t(s0), half, 0, phase == 0, phase == 1,
-                      ctx->fp64, ctx->vvar < 0 ? 0 : ctx->vvar, ctx->s);
+    {
+        Prof p(ctx, 2, (ctx->fp64 || phase == 1) ? 1 : 4);
+        launch_vphase_abs(d, phase == 0 ? d.a0 : nullptr, tau2_ps, uint32_t(s0), half, 0, phase == 0, phase == 1,
+                          ctx->fp64, ctx->vvar < 0 ? 0 : ctx->vvar, ctx->s);
+    }
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(ctx->h_err, d.err, sizeof(uint32_t) * d.R, cudaMemcpyDeviceToHost, ctx->s));
     CK(cudaStreamSynchronize(ctx->s));
