@@ -70,8 +70,22 @@ struct RepParams {
     double beta, gamma, eps0;
     uint32_t seed, replica;
     int ntypes, pad2;
+    // shell table of the inner list build: bins of r^2 on [0, (r_E + skin_outer)^2)
+    float shell_invw;          // bins per A^2
+    int pad3;
+    // squared limits of the ring (y < MAX_RINGS) and LJ (y = MAX_RINGS) shells:
+    // [lo2, hi2) widened by the skin; empty shells have lo2 = hi2 = 0
+    double shell_lo2[MAX_RINGS + 1], shell_hi2[MAX_RINGS + 1];
+    float shell_lo2f[MAX_RINGS + 1], shell_hi2f[MAX_RINGS + 1];
+    float r2s, r2f;            // (r_c + skin)^2, (r_E + skin)^2: short and full lists
     LJPair lj[MAX_TYPES * MAX_TYPES];
 };
+
+// shell table: per bin of r^2, the ring and LJ lists that contain the whole
+// bin (bit = list kind), or SHELL_AMB when a ring or LJ shell limit lies
+// within the bin or its tolerance margin (decided in FP64 then)
+constexpr int SHELL_BINS = 2048;
+constexpr uint16_t SHELL_AMB = 0x8000;
 
 // ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) ---------------------
 struct U4 { uint32_t x, y, z, w; };

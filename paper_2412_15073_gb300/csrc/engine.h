@@ -49,6 +49,7 @@ struct Dev {
     uint32_t* olist;
     int* ocnt;
     int ocap;
+    const uint16_t* shell_tab;      // [R][SHELL_BINS]
     // inner lists (packed entries)
     uint32_t* list[NKIND];
     int* lcnt[NKIND];

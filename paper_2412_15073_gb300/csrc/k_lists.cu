@@ -289,7 +289,10 @@ __global__ void __launch_bounds__(32 * OUTER_WARPS) k_outer_cells(Dev d, int exa
     }
 }
 
-// one warp per atom: filter the outer list into the inner lists, keeping its order
+// one warp per atom: filter the outer list into the inner lists, keeping its
+// order. Ring and LJ membership (which decides the partner a jump picks) comes
+// from the replica's shell table; candidates in a bin that holds a shell limit
+// are decided in FP64 from the build positions, as in exact mode.
 __global__ void __launch_bounds__(32 * WARPS) k_inner_lists(Dev d, int kinds, int exact, int late)
 {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -301,96 +304,92 @@ __global__ void __launch_bounds__(32 * WARPS) k_inner_lists(Dev d, int kinds, in
     const uint4 pi = d.pos[i];
     const float qi = __uint_as_float(pi.w);
     const int ti = d.type[i];
-    const bool want_s = kinds & (1 << L_SHORT), want_f = kinds & (1 << L_FULL);
-    // rings (y < nr) and LJ partners, skin-widened shells of the build positions
-    bool want_r[MAX_RINGS];
-    bool any_ring = false;
+    constexpr uint32_t RING_BITS = ((1u << MAX_RINGS) - 1u) << L_R0;
+    // lists this atom takes: rings (y < nr) need a charge, LJ an LJ type pair
+    uint32_t want = uint32_t(kinds) & ((1u << L_SHORT) | (1u << L_FULL));
 #pragma unroll
-    for (int y = 0; y < MAX_RINGS; ++y) {
-        want_r[y] = (kinds & (1 << (L_R0 + y))) && y < P.nr && P.rings_on && qi != 0.f;
-        any_ring |= want_r[y];
-    }
-    const bool want_j = (kinds & (1 << L_LJ)) && P.lj_on;
-    const bool shells = any_ring || want_j;
+    for (int y = 0; y < MAX_RINGS; ++y)
+        if ((kinds & (1 << (L_R0 + y))) && y < P.nr && P.rings_on && qi != 0.f) want |= 1u << (L_R0 + y);
     unsigned ljmask = 0;
-    if (want_j)
+    if ((kinds & (1 << L_LJ)) && P.lj_on) {
         for (int t = 0; t < P.ntypes; ++t) ljmask |= (P.lj[ti * MAX_TYPES + t].on ? 1u : 0u) << t;
-    const double sk = P.skin;
-    // squared shell limits: ring y [edge_y - skin, edge_{y+1} + skin), LJ [sw - skin, R + skin)
-    double lo2[MAX_RINGS + 1], hi2[MAX_RINGS + 1];
-    float lo2f[MAX_RINGS + 1], hi2f[MAX_RINGS + 1];
-#pragma unroll
-    for (int y = 0; y <= MAX_RINGS; ++y) {
-        double lo, hi;
-        if (y < MAX_RINGS) { lo = y < P.nr ? P.edge[y] - sk : 0.0; hi = y < P.nr ? P.edge[y + 1] + sk : 0.0; }
-        else { lo = P.sw - sk; hi = P.R + sk; }
-        lo = fmax(lo, 0.0);
-        lo2[y] = lo * lo; hi2[y] = hi * hi;
-        lo2f[y] = float(lo2[y]); hi2f[y] = float(hi2[y]);
+        if (ljmask) want |= 1u << L_LJ;
     }
-    const float r2s = float((P.rc + sk) * (P.rc + sk)), r2f = float((P.R + sk) * (P.R + sk));
-    uint32_t* rows[NKIND];
-#pragma unroll
-    for (int k = 0; k < NKIND; ++k) rows[k] = d.list[k] + (size_t)i * d.lcap[k];
+    const bool need_type = (want >> L_LJ) & 1u;
+    const float r2s = P.r2s, r2f = P.r2f;
+    const uint16_t* tab = d.shell_tab + (size_t)r * SHELL_BINS;
+    const float invw = P.shell_invw;
+    const float sc = P.sclf, sclo = P.sclf_lo;
     int cnt[NKIND] = {};
     const int n_o = min(d.ocnt[i], d.ocap);
     const uint32_t* orow = d.olist + (size_t)i * d.ocap;
+    // three batches of 32 candidates in flight: the entries of batch b+2 and
+    // the positions (and types) of batch b+1 load while batch b is filtered
+    uint32_t j1 = lane < n_o ? __ldg(orow + lane) : 0u;
+    uint32_t j2 = lane + 32 < n_o ? __ldg(orow + lane + 32) : 0u;
+    uint4 p1 = lane < n_o ? d.pos[j1] : make_uint4(0, 0, 0, 0);
+    int t1 = (lane < n_o && need_type) ? __ldg(d.type + j1) : 0;
     for (int base = 0; base < n_o; base += 32) {
         const int k = base + lane;
-        bool m[NKIND] = {};
-        uint32_t j = 0;
+        const uint32_t j = j1;
+        const uint4 pj = p1;
+        const int tj = t1;
+        j1 = j2;
+        if (k + 64 < n_o) j2 = __ldg(orow + k + 64);
+        if (k + 32 < n_o) {
+            p1 = d.pos[j1];
+            if (need_type) t1 = __ldg(d.type + j1);
+        }
+        uint32_t m = 0;
         if (k < n_o) {
-            j = orow[k];
-            const uint4 pj = d.pos[j];
-            const bool qq = __uint_as_float(pj.w) != 0.f;
-            const bool ljp = want_j && ((ljmask >> d.type[j]) & 1u);
-            if (exact) {
-                const double r2 = dist2_fp64(d.xb, i, (int)j, P);
-                m[L_SHORT] = r2 < double(r2s);
-                m[L_FULL] = r2 < double(r2f);
-#pragma unroll
-                for (int y = 0; y < MAX_RINGS; ++y) m[L_R0 + y] = want_r[y] && qq && r2 >= lo2[y] && r2 < hi2[y];
-                m[L_LJ] = ljp && r2 >= lo2[MAX_RINGS] && r2 < hi2[MAX_RINGS];
-            } else {
+            uint32_t cand = want;
+            if (__uint_as_float(pj.w) == 0.f) cand &= ~RING_BITS;
+            if (need_type && !((ljmask >> tj) & 1u)) cand &= ~(1u << L_LJ);
+            bool fp64 = exact != 0;
+            if (!fp64) {
                 float dx, dy, dz;
-                sdisp(pi, pj, P.sclf, P.sclf_lo, dx, dy, dz);
+                sdisp(pi, pj, sc, sclo, dx, dy, dz);
                 const float r2 = dx * dx + dy * dy + dz * dz;
-                m[L_SHORT] = r2 < r2s;
-                m[L_FULL] = r2 < r2f;
-                if (shells) {
-                    // ring and LJ membership decides which partner a jump picks:
-                    // within 2e-5 (relative, in r^2) of a shell limit it is decided in FP64
+                m = (r2 < r2s ? 1u << L_SHORT : 0u) | (r2 < r2f ? 1u << L_FULL : 0u);
+                const uint16_t t = __ldg(tab + min(SHELL_BINS - 1, int(r2 * invw)));
+                if (!(t & SHELL_AMB)) {
+                    m |= t;
+                } else if (cand & ~((1u << L_SHORT) | (1u << L_FULL))) {
+                    // a shell limit is near this bin: decide in FP32 unless r^2 is
+                    // within 2e-6 (relative) of a limit, far above its FP32 error
                     bool near = false;
 #pragma unroll
-                    for (int y = 0; y <= MAX_RINGS; ++y)
-                        near |= fabsf(r2 - lo2f[y]) < 2e-5f * lo2f[y] + 1e-6f ||
-                                fabsf(r2 - hi2f[y]) < 2e-5f * hi2f[y] + 1e-6f;
+                    for (int y = 0; y <= MAX_RINGS; ++y) {
+                        const float lo = P.shell_lo2f[y], hi = P.shell_hi2f[y];
+                        near |= fabsf(r2 - lo) <= 2e-6f * lo + 1e-7f || fabsf(r2 - hi) <= 2e-6f * hi + 1e-7f;
+                        if (r2 >= lo && r2 < hi) m |= 1u << (y < MAX_RINGS ? L_R0 + y : L_LJ);
+                    }
                     if (near) {
-                        const double r2d = dist2_fp64(d.xb, i, (int)j, P);
-#pragma unroll
-                        for (int y = 0; y < MAX_RINGS; ++y)
-                            m[L_R0 + y] = want_r[y] && qq && r2d >= lo2[y] && r2d < hi2[y];
-                        m[L_LJ] = ljp && r2d >= lo2[MAX_RINGS] && r2d < hi2[MAX_RINGS];
-                    } else {
-#pragma unroll
-                        for (int y = 0; y < MAX_RINGS; ++y)
-                            m[L_R0 + y] = want_r[y] && qq && r2 >= lo2f[y] && r2 < hi2f[y];
-                        m[L_LJ] = ljp && r2 >= lo2f[MAX_RINGS] && r2 < hi2f[MAX_RINGS];
+                        fp64 = true;
+                        m &= (1u << L_SHORT) | (1u << L_FULL);
                     }
                 }
             }
+            if (fp64) {
+                const double r2 = dist2_fp64(d.xb, i, (int)j, P);
+                if (exact) m = (r2 < double(r2s) ? 1u << L_SHORT : 0u) | (r2 < double(r2f) ? 1u << L_FULL : 0u);
+#pragma unroll
+                for (int y = 0; y <= MAX_RINGS; ++y)
+                    if (r2 >= P.shell_lo2[y] && r2 < P.shell_hi2[y]) m |= 1u << (y < MAX_RINGS ? L_R0 + y : L_LJ);
+            }
+            m &= cand;
         }
         const unsigned below = (1u << lane) - 1u;
 #pragma unroll
         for (int kind = 0; kind < NKIND; ++kind) {
-            if (!(kinds & (1 << kind))) continue;
-            const unsigned b = __ballot_sync(0xffffffffu, m[kind]);
+            if (!((want >> kind) & 1u)) continue;        // warp-uniform: one atom per warp
+            const bool in = (m >> kind) & 1u;
+            const unsigned b = __ballot_sync(0xffffffffu, in);
             const int pos = cnt[kind] + __popc(b & below);
-            if (m[kind] && pos < d.lcap[kind]) rows[kind][pos] = j;
+            if (in && pos < d.lcap[kind]) d.list[kind][(size_t)i * d.lcap[kind] + pos] = j;
             cnt[kind] += __popc(b);
         }
     }
-    (void)want_s; (void)want_f;
     if (lane == 0) {
 #pragma unroll
         for (int kind = 0; kind < NKIND; ++kind) {

@@ -246,6 +246,39 @@ int kind_cap(const md_ctx* ctx, int k)
     return hi > 0 ? cap_of(rho, lo, hi) : 32;
 }
 
+// shell table of one replica (see SHELL_BINS): bins of r^2 over [0, (r_E +
+// skin_outer)^2); a bin is ambiguous when a ring or LJ shell limit lies within
+// it or within a margin of 2e-5 r^2 + 1e-6 A^2 of it (far wider than the FP32
+// error of r^2), otherwise it lists the ring and LJ kinds that contain it
+void make_shell_table(const RepParams& P, uint16_t* tab)
+{
+    const double r2max = (P.R + P.skin_o) * (P.R + P.skin_o);
+    const double w = r2max / SHELL_BINS;
+    double lo2[NKIND], hi2[NKIND];
+    bool use[NKIND];
+    for (int k = 0; k < NKIND; ++k) {
+        double lo, hi;
+        shell_of(P, k, lo, hi);
+        lo = std::max(lo, 0.0);
+        use[k] = k != L_SHORT && k != L_FULL && hi > lo;
+        lo2[k] = lo * lo;
+        hi2[k] = hi * hi;
+    }
+    for (int b = 0; b < SHELL_BINS; ++b) {
+        const double a = b * w, e = b == SHELL_BINS - 1 ? 1e300 : (b + 1) * w;
+        const double ma = 2e-5 * a + 1e-6, me = 2e-5 * std::min(e, 1e30) + 1e-6;
+        uint16_t t = 0;
+        bool amb = b == SHELL_BINS - 1;
+        for (int k = 0; k < NKIND; ++k) {
+            if (!use[k]) continue;
+            for (double lim : {lo2[k], hi2[k]})
+                if (lim > 0.0 && lim >= a - ma && lim <= e + me) amb = true;
+            if (lo2[k] <= a && e <= hi2[k]) t |= uint16_t(1u << k);
+        }
+        tab[b] = amb ? SHELL_AMB : t;
+    }
+}
+
 RepParams make_params(const md_ctx* ctx, const RepHost& h, int r, int atom_off, int cell_off)
 {
     const md_system& s = h.sys;
@@ -289,6 +322,17 @@ RepParams make_params(const md_ctx* ctx, const RepHost& h, int r, int atom_off, 
     P.fR = hpair.fR();
     P.kexp = 2.0 * s.dsf_alpha / std::sqrt(PI);
     P.alphaf = float(P.alpha); P.eRf = float(P.eR); P.fRf = float(P.fR); P.kexpf = float(P.kexp);
+    P.shell_invw = float(SHELL_BINS / ((s.r_cut + skin_o) * (s.r_cut + skin_o)));
+    for (int y = 0; y <= MAX_RINGS; ++y) {
+        double lo, hi;
+        if (y < MAX_RINGS) { lo = y < P.nr ? P.edge[y] - s.skin : 0.0; hi = y < P.nr ? P.edge[y + 1] + s.skin : 0.0; }
+        else { lo = P.sw - s.skin; hi = P.R + s.skin; }
+        lo = std::max(lo, 0.0);
+        P.shell_lo2[y] = lo * lo; P.shell_hi2[y] = hi * hi;
+        P.shell_lo2f[y] = float(P.shell_lo2[y]); P.shell_hi2f[y] = float(P.shell_hi2[y]);
+    }
+    P.r2s = float((s.r_split + s.skin) * (s.r_split + s.skin));
+    P.r2f = float((s.r_cut + s.skin) * (s.r_cut + s.skin));
     P.beta = 1.0 / (KB * s.temperature);
     P.gamma = s.gamma;
     P.eps0 = s.eps0;
@@ -611,6 +655,12 @@ int commit(md_ctx* ctx)
     AL(d.flags, 2 * R); AL(d.err, R); AL(d.ovf, R); AL(d.cnt, (size_t)R * NCOUNT); AL(d.energy, 6 * R);
     AL(d.step_base, R); AL(d.stepc, 2 * R);
     AL(d.vkey, N); AL(d.vhist, (size_t)R * RATE_BUCKETS); AL(d.vofs, (size_t)R * RATE_BUCKETS);
+    uint16_t* dtab;
+    AL(dtab, (size_t)R * SHELL_BINS);
+    d.shell_tab = dtab;
+    std::vector<uint16_t> tab((size_t)R * SHELL_BINS);
+    for (int r = 0; r < R; ++r) make_shell_table(ctx->hp[r], &tab[(size_t)r * SHELL_BINS]);
+    if ((rc = upload(ctx, dtab, tab.data(), tab.size()))) return rc;
     const long long evcap = ctx->cfg.event_log_cap > 0 ? ctx->cfg.event_log_cap : 0;
     AL(d.ev, (size_t)6 * (evcap ? evcap : 1)); AL(d.ev_n, 1);
 #undef AL
