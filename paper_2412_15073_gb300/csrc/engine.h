@@ -86,9 +86,10 @@ void launch_advance(const Dev& d, long long nsteps, cudaStream_t s);
 
 // ---- jumps (k_jump.cu) --------------------------------------------------------------
 // order 0: C' then J' (first half of a step), 1: J' then C' (second half)
-// variant of the mixed-mode kernel: occupancy targets of 3, 4, 5, 6 blocks of
-// 128 threads. Every variant computes the same values. In mixed mode a C'
-// phase first orders the atoms by their expected number of proposals.
+// variant of the mixed-mode C' kernel: occupancy targets of 3, 4, 5, 6 blocks
+// of 128 threads. Every variant computes the same values. In mixed mode a C'
+// phase first orders the atoms by their expected number of proposals, and
+// J' runs as a kernel of its own.
 constexpr int NVPHASE_VARIANTS = 4;
 constexpr int RATE_BUCKETS = 128;
 void launch_vphase(const Dev& d, const double* a, double tau2, uint32_t s_off, int half, int order,

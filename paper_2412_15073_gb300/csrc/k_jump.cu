@@ -324,7 +324,7 @@ __device__ __forceinline__ void warp_add(unsigned long long* dst, unsigned int v
 
 // ---- mixed-mode fast path ----------------------------------------------------------
 // G~ by rejection for one accepted proposal (streams (S, half, attempt, k))
-__device__ __noinline__ float sample_gtilde_f(const RepParams& P, uint32_t il, uint32_t s0, int half,
+__device__ __forceinline__ float sample_gtilde_f(const RepParams& P, uint32_t il, uint32_t s0, int half,
                                                uint32_t k, float eta, int* att_out, bool* ok_out)
 {
     float G = 0.f;
@@ -518,11 +518,12 @@ __device__ __forceinline__ void cprime_f(const Dev& d, const RepParams& P, int i
     }
 }
 
-// mixed-mode velocity phase; threads visit atoms in the order vorder (atoms
-// grouped by expected jump rate so that the lanes of a warp do similar work)
+// mixed-mode C' phase; threads visit atoms in the order vorder (atoms
+// ordered by expected number of proposals so that the lanes of a warp do
+// similar work). J' runs in its own kernel (k_jphase_f) before or after.
 template <int MINB>
-__global__ void __launch_bounds__(128, MINB) k_vphase_f(Dev d, const double* a, double tau2, uint32_t s_off, int s_abs,
-                                                        int half, int order, int doC, int doJ)
+__global__ void __launch_bounds__(128, MINB) k_cphase_f(Dev d, const double* a, double tau2, uint32_t s_off, int s_abs,
+                                                        int half)
 {
     const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = t0 < d.N;
@@ -534,31 +535,19 @@ __global__ void __launch_bounds__(128, MINB) k_vphase_f(Dev d, const double* a, 
     if (live) {
         const uint32_t s0 = (s_abs ? 0u : uint32_t(d.step_base[r])) + s_off;
         const int il = i - P.atom_off;
-        const bool c_on = doC && P.rings_on;
-        const bool j_on = doJ && P.lj_on;
-        for (int step = 0; step < 2; ++step) {
-            const bool isC = (order == 0) ? step == 0 : step == 1;
-            if (isC) {
-                if (!doC) continue;
-                float3 jv = make_float3(0.f, 0.f, 0.f);
-                if (c_on) {
-                    const float3 v0 = make_float3(float(d.v[3 * i]), float(d.v[3 * i + 1]), float(d.v[3 * i + 2]));
-                    const float3 af = a ? make_float3(float(a[3 * i]), float(a[3 * i + 1]), float(a[3 * i + 2]))
-                                        : make_float3(0.f, 0.f, 0.f);
-                    cprime_f(d, P, i, il, jv, v0, af, float(tau2), s0, half, tl, err);
-                }
-                // FP64 end of the phase: (v0 + (tau/2) a) + sum of the jumps; the
-                // first sum rounds like a B kick, so a phase without jumps is one
-                for (int c = 0; c < 3; ++c) {
-                    const double ac = a ? a[3 * i + c] : 0.0;
-                    const double vn = fma(tau2, ac, d.v[3 * i + c]);
-                    d.v[3 * i + c] = vn + double(c == 0 ? jv.x : (c == 1 ? jv.y : jv.z));
-                }
-            } else if (j_on) {
-                double v[3] = {d.v[3 * i], d.v[3 * i + 1], d.v[3 * i + 2]};
-                jprime<float>(d, P, i, il, v, tau2, s0, half, tl, err);
-                d.v[3 * i] = v[0]; d.v[3 * i + 1] = v[1]; d.v[3 * i + 2] = v[2];
-            }
+        float3 jv = make_float3(0.f, 0.f, 0.f);
+        if (P.rings_on) {
+            const float3 v0 = make_float3(float(d.v[3 * i]), float(d.v[3 * i + 1]), float(d.v[3 * i + 2]));
+            const float3 af = a ? make_float3(float(a[3 * i]), float(a[3 * i + 1]), float(a[3 * i + 2]))
+                                : make_float3(0.f, 0.f, 0.f);
+            cprime_f(d, P, i, il, jv, v0, af, float(tau2), s0, half, tl, err);
+        }
+        // FP64 end of the phase: (v0 + (tau/2) a) + sum of the jumps; the
+        // first sum rounds like a B kick, so a phase without jumps is one
+        for (int c = 0; c < 3; ++c) {
+            const double ac = a ? a[3 * i + c] : 0.0;
+            const double vn = fma(tau2, ac, d.v[3 * i + c]);
+            d.v[3 * i + c] = vn + double(c == 0 ? jv.x : (c == 1 ? jv.y : jv.z));
         }
         if (err) atomicOr(&d.err[r], err);
     }
@@ -568,10 +557,33 @@ __global__ void __launch_bounds__(128, MINB) k_vphase_f(Dev d, const double* a, 
     unsigned long long* C = d.cnt + (size_t)r * NCOUNT;
     warp_add(&C[C_CPROP], tl.cprop, uniform, lane);
     warp_add(&C[C_CACC], tl.cacc, uniform, lane);
-    warp_add(&C[C_JPROP], tl.jprop, uniform, lane);
-    warp_add(&C[C_JACC], tl.jacc, uniform, lane);
     warp_add(&C[C_SATT], tl.satt, uniform, lane);
     warp_add(&C[C_GUARD], tl.guard, uniform, lane);
+}
+
+// mixed-mode J' phase: one thread per atom (BPS bounces, FP64 velocity)
+__global__ void __launch_bounds__(128) k_jphase_f(Dev d, double tau2, uint32_t s_off, int s_abs, int half)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = i < d.N;
+    const int ic = live ? i : d.N - 1;
+    const int r = d.rep[ic];
+    const RepParams& P = d.P[r];
+    Tally tl;
+    uint32_t err = 0;
+    if (live && P.lj_on) {
+        const uint32_t s0 = (s_abs ? 0u : uint32_t(d.step_base[r])) + s_off;
+        double v[3] = {d.v[3 * i], d.v[3 * i + 1], d.v[3 * i + 2]};
+        jprime<float>(d, P, i, i - P.atom_off, v, tau2, s0, half, tl, err);
+        d.v[3 * i] = v[0]; d.v[3 * i + 1] = v[1]; d.v[3 * i + 2] = v[2];
+        if (err) atomicOr(&d.err[r], err);
+    }
+    const int lane = threadIdx.x & 31;
+    const int r0 = __shfl_sync(0xffffffffu, r, 0);
+    const bool uniform = __all_sync(0xffffffffu, r == r0);
+    unsigned long long* C = d.cnt + (size_t)r * NCOUNT;
+    warp_add(&C[C_JPROP], tl.jprop, uniform, lane);
+    warp_add(&C[C_JACC], tl.jacc, uniform, lane);
 }
 
 template <typename T>
@@ -718,13 +730,18 @@ static void vphase_any(const Dev& d, const double* a, double tau2, uint32_t s, i
         k_vphase<double><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, order, doC, doJ);
         return;
     }
-    if (doC) rate_order(d, a, tau2, st);
-    switch (variant) {
-    case 1: k_vphase_f<4><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, order, doC, doJ); break;
-    case 2: k_vphase_f<5><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, order, doC, doJ); break;
-    case 3: k_vphase_f<6><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, order, doC, doJ); break;
-    default: k_vphase_f<3><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, order, doC, doJ); break;
+    // order 0: C' then J'; 1: J' then C'
+    if (doJ && order == 1) k_jphase_f<<<(d.N + 127) / 128, 128, 0, st>>>(d, tau2, s, s_abs, half);
+    if (doC) {
+        rate_order(d, a, tau2, st);
+        switch (variant) {
+        case 1: k_cphase_f<4><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half); break;
+        case 2: k_cphase_f<5><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half); break;
+        case 3: k_cphase_f<6><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half); break;
+        default: k_cphase_f<3><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half); break;
+        }
     }
+    if (doJ && order == 0) k_jphase_f<<<(d.N + 127) / 128, 128, 0, st>>>(d, tau2, s, s_abs, half);
 }
 
 void launch_vphase(const Dev& d, const double* a, double tau2, uint32_t s_off, int half, int order,

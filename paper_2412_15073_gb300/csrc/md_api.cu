@@ -898,7 +898,7 @@ int tune_vphase(md_ctx* ctx, const double* a, double tau2)
 void vphase(md_ctx* ctx, const double* a, double tau2, uint32_t s_off, int half, int order)
 {
     if (ctx->vvar < 0) tune_vphase(ctx, a, tau2);
-    Prof p(ctx, 2, ctx->fp64 ? 1 : 4);
+    Prof p(ctx, 2, ctx->fp64 ? 1 : 5);
     launch_vphase(ctx->d, a, tau2, s_off, half, order, 1, 1, ctx->fp64, ctx->vvar < 0 ? 0 : ctx->vvar, ctx->s);
 }
 
@@ -1292,7 +1292,7 @@ int md_run_phase(md_ctx* ctx, int phase, double tau2_ps, int64_t s0, int half, i
     Dev& d = ctx->d;
     if (phase == 0) force(ctx, accel_mode, d.a0);
     {
-        Prof p(ctx, 2, (ctx->fp64 || phase == 1) ? 1 : 4);
+        Prof p(ctx, 2, (ctx->fp64 || phase == 1) ? 1 : 4);   // phase 0: rate order (3) + C'; phase 1: J' only
         launch_vphase_abs(d, phase == 0 ? d.a0 : nullptr, tau2_ps, uint32_t(s0), half, 0, phase == 0, phase == 1,
                           ctx->fp64, ctx->vvar < 0 ? 0 : ctx->vvar, ctx->s);
     }
