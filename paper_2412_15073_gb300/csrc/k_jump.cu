@@ -521,9 +521,13 @@ __device__ __forceinline__ void cprime_f(const Dev& d, const RepParams& P, int i
 // mixed-mode C' phase; threads visit atoms in the order vorder (atoms
 // ordered by expected number of proposals so that the lanes of a warp do
 // similar work). J' runs in its own kernel (k_jphase_f) before or after.
+// npass = 2 runs two consecutive C' phases at the same positions: the second
+// half of the step at s_off (half 1) and the first half of the next step at
+// s_off2 (half 0), which are adjacent in the C'J'AOAJ'C' sequence when no J'
+// acts between them (the J' phases of the two steps run before and after).
 template <int MINB>
 __global__ void __launch_bounds__(128, MINB) k_cphase_f(Dev d, const double* a, double tau2, uint32_t s_off, int s_abs,
-                                                        int half)
+                                                        int half, int npass, uint32_t s_off2)
 {
     const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = t0 < d.N;
@@ -533,22 +537,28 @@ __global__ void __launch_bounds__(128, MINB) k_cphase_f(Dev d, const double* a, 
     Tally tl;
     uint32_t err = 0;
     if (live) {
-        const uint32_t s0 = (s_abs ? 0u : uint32_t(d.step_base[r])) + s_off;
         const int il = i - P.atom_off;
-        float3 jv = make_float3(0.f, 0.f, 0.f);
-        if (P.rings_on) {
-            const float3 v0 = make_float3(float(d.v[3 * i]), float(d.v[3 * i + 1]), float(d.v[3 * i + 2]));
-            const float3 af = a ? make_float3(float(a[3 * i]), float(a[3 * i + 1]), float(a[3 * i + 2]))
-                                : make_float3(0.f, 0.f, 0.f);
-            cprime_f(d, P, i, il, jv, v0, af, float(tau2), s0, half, tl, err);
+        double v[3] = {d.v[3 * i], d.v[3 * i + 1], d.v[3 * i + 2]};
+        const double ad[3] = {a ? a[3 * i] : 0.0, a ? a[3 * i + 1] : 0.0, a ? a[3 * i + 2] : 0.0};
+        for (int pass = 0; pass < npass; ++pass) {
+            const uint32_t s0 = (s_abs ? 0u : uint32_t(d.step_base[r])) + (pass ? s_off2 : s_off);
+            const int hp = pass ? 0 : half;
+            float3 jv = make_float3(0.f, 0.f, 0.f);
+            if (P.rings_on) {
+                const float3 v0 = make_float3(float(v[0]), float(v[1]), float(v[2]));
+                const float3 af = make_float3(float(ad[0]), float(ad[1]), float(ad[2]));
+                if (pass) {
+                    d.v[3 * i] = v[0]; d.v[3 * i + 1] = v[1]; d.v[3 * i + 2] = v[2];   // read by the FP64 guard
+                }
+                cprime_f(d, P, i, il, jv, v0, af, float(tau2), s0, hp, tl, err);
+            }
+            // FP64 end of the phase: (v0 + (tau/2) a) + sum of the jumps; the
+            // first sum rounds like a B kick, so a phase without jumps is one
+            v[0] = fma(tau2, ad[0], v[0]) + double(jv.x);
+            v[1] = fma(tau2, ad[1], v[1]) + double(jv.y);
+            v[2] = fma(tau2, ad[2], v[2]) + double(jv.z);
         }
-        // FP64 end of the phase: (v0 + (tau/2) a) + sum of the jumps; the
-        // first sum rounds like a B kick, so a phase without jumps is one
-        for (int c = 0; c < 3; ++c) {
-            const double ac = a ? a[3 * i + c] : 0.0;
-            const double vn = fma(tau2, ac, d.v[3 * i + c]);
-            d.v[3 * i + c] = vn + double(c == 0 ? jv.x : (c == 1 ? jv.y : jv.z));
-        }
+        d.v[3 * i] = v[0]; d.v[3 * i + 1] = v[1]; d.v[3 * i + 2] = v[2];
         if (err) atomicOr(&d.err[r], err);
     }
     const int lane = threadIdx.x & 31;
@@ -722,38 +732,40 @@ static void rate_order(const Dev& d, const double* a, double tau2, cudaStream_t 
     k_rate_scatter<<<nb, 256, 0, st>>>(d);
 }
 
-static void vphase_any(const Dev& d, const double* a, double tau2, uint32_t s, int s_abs, int half, int order,
-                       int doC, int doJ, int fp64, int variant, cudaStream_t st)
+static void vphase_any(const Dev& d, const double* a, double tau2, uint32_t s, uint32_t s2, int s_abs, int half,
+                       int order, int doC, int doJ, int fp64, int variant, cudaStream_t st)
 {
     const int nb = (d.N + 127) / 128;
     if (fp64) {
         k_vphase<double><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, order, doC, doJ);
         return;
     }
-    // order 0: C' then J'; 1: J' then C'
-    if (doJ && order == 1) k_jphase_f<<<(d.N + 127) / 128, 128, 0, st>>>(d, tau2, s, s_abs, half);
+    // order 0: C' then J'; 1: J' then C'; 2: J' (s, 1), C' (s, 1), C' (s2, 0), J' (s2, 0)
+    if (doJ && order >= 1) k_jphase_f<<<(d.N + 127) / 128, 128, 0, st>>>(d, tau2, s, s_abs, half);
     if (doC) {
-        rate_order(d, a, tau2, st);
+        const int npass = order == 2 ? 2 : 1;
+        rate_order(d, a, tau2 * npass, st);
         switch (variant) {
-        case 1: k_cphase_f<4><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half); break;
-        case 2: k_cphase_f<5><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half); break;
-        case 3: k_cphase_f<6><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half); break;
-        default: k_cphase_f<3><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half); break;
+        case 1: k_cphase_f<4><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, npass, s2); break;
+        case 2: k_cphase_f<5><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, npass, s2); break;
+        case 3: k_cphase_f<6><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, npass, s2); break;
+        default: k_cphase_f<3><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, npass, s2); break;
         }
     }
     if (doJ && order == 0) k_jphase_f<<<(d.N + 127) / 128, 128, 0, st>>>(d, tau2, s, s_abs, half);
+    if (doJ && order == 2) k_jphase_f<<<(d.N + 127) / 128, 128, 0, st>>>(d, tau2, s2, s_abs, 0);
 }
 
 void launch_vphase(const Dev& d, const double* a, double tau2, uint32_t s_off, int half, int order,
-                   int doC, int doJ, int fp64, int variant, cudaStream_t s)
+                   int doC, int doJ, int fp64, int variant, cudaStream_t s, uint32_t s_off2)
 {
-    vphase_any(d, a, tau2, s_off, 0, half, order, doC, doJ, fp64, variant, s);
+    vphase_any(d, a, tau2, s_off, s_off2, 0, half, order, doC, doJ, fp64, variant, s);
 }
 
 void launch_vphase_abs(const Dev& d, const double* a, double tau2, uint32_t s0, int half, int order,
                        int doC, int doJ, int fp64, int variant, cudaStream_t s)
 {
-    vphase_any(d, a, tau2, s0, 1, half, order, doC, doJ, fp64, variant, s);
+    vphase_any(d, a, tau2, s0, 0, 1, half, order, doC, doJ, fp64, variant, s);
 }
 
 }  // namespace mdj

@@ -895,11 +895,12 @@ int tune_vphase(md_ctx* ctx, const double* a, double tau2)
     return MD_OK;
 }
 
-void vphase(md_ctx* ctx, const double* a, double tau2, uint32_t s_off, int half, int order)
+void vphase(md_ctx* ctx, const double* a, double tau2, uint32_t s_off, int half, int order, uint32_t s_off2 = 0)
 {
     if (ctx->vvar < 0) tune_vphase(ctx, a, tau2);
-    Prof p(ctx, 2, ctx->fp64 ? 1 : 5);
-    launch_vphase(ctx->d, a, tau2, s_off, half, order, 1, 1, ctx->fp64, ctx->vvar < 0 ? 0 : ctx->vvar, ctx->s);
+    Prof p(ctx, 2, ctx->fp64 ? 1 : (order == 2 ? 6 : 5));
+    launch_vphase(ctx->d, a, tau2, s_off, half, order, 1, 1, ctx->fp64, ctx->vvar < 0 ? 0 : ctx->vvar, ctx->s,
+                  s_off2);
 }
 
 int set_stepc(md_ctx* ctx, double tau)
@@ -1117,12 +1118,17 @@ int md_step_jump(md_ctx* ctx, int64_t nsteps, double dt_fs)
     const double tau = dt_fs * 1e-3;
     if ((rc = set_stepc(ctx, tau))) return rc;
     force(ctx, 5, d.a0);
+    // C'J' A O A [F0] J'C', step after step. In mixed mode the C' of the second
+    // half of step k and the C' of the first half of step k+1 (adjacent, at the
+    // same positions and acceleration) run in one launch.
+    const bool fuse = !ctx->fp64;
     for (int64_t k = 0; k < nsteps; ++k) {
-        vphase(ctx, d.a0, 0.5 * tau, uint32_t(k), 0, 0);
+        if (k == 0 || !fuse) vphase(ctx, d.a0, 0.5 * tau, uint32_t(k), 0, 0);
         aoa(ctx, tau, uint32_t(k), 1);
         rebuild_step(ctx);
         force(ctx, 5, d.a0);
-        vphase(ctx, d.a0, 0.5 * tau, uint32_t(k), 1, 1);
+        if (fuse && k + 1 < nsteps) vphase(ctx, d.a0, 0.5 * tau, uint32_t(k), 1, 2, uint32_t(k + 1));
+        else vphase(ctx, d.a0, 0.5 * tau, uint32_t(k), 1, 1);
     }
     return finish(ctx, nsteps);
 }
@@ -1184,13 +1190,16 @@ static int jump_respa_cycles(md_ctx* ctx, int64_t cycles, double dt_inner_fs, in
     force(ctx, 1, d.ab);
     force(ctx, 3, d.as);
     uint32_t s = 0;
+    // as in md_step_jump, adjacent C' phases of consecutive cycles share a launch in mixed mode
+    const bool fuse = !ctx->fp64;
     for (int64_t o = 0; o < cycles; ++o) {
         const uint32_t s0 = s;
-        vphase(ctx, d.as, 0.5 * D, s0, 0, 0);
+        if (o == 0 || !fuse) vphase(ctx, d.as, 0.5 * D, s0, 0, 0);
         for (int k = 0; k < n_inner; ++k, ++s) inner_bonded(ctx, dt, s, k == n_inner - 1);
         rebuild_step(ctx);
         force(ctx, 3, d.as);
-        vphase(ctx, d.as, 0.5 * D, s0, 1, 1);
+        if (fuse && o + 1 < cycles) vphase(ctx, d.as, 0.5 * D, s0, 1, 2, s);
+        else vphase(ctx, d.as, 0.5 * D, s0, 1, 1);
     }
     return finish(ctx, (long long)cycles * n_inner);
 }

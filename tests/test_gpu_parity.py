@@ -298,3 +298,25 @@ def test_velocity_phase_variants_are_identical(M, oracle_mod, water648, monkeypa
         else:
             assert np.array_equal(x, ref[0]) and np.array_equal(v, ref[1]), var
         e.close()
+
+
+@pytest.mark.parametrize("how", ["jump", "jump_respa"])
+def test_fused_cprime_pairs_equal_single_phases(M, oracle_mod, water648, how):
+    """Mixed mode runs the adjacent C' phases of consecutive steps in one
+    launch; that must give the same values bit for bit as one call per step
+    (where every phase has a launch of its own)."""
+    a, _ = make(M, oracle_mod, water648, 1, seed=13)
+    b, _ = make(M, oracle_mod, water648, 1, seed=13)
+    if how == "jump":
+        a.jump(12)
+        for _ in range(12):
+            b.jump(1)
+    else:
+        a.jump_respa(6, 1.0, 2)
+        for _ in range(6):
+            b.jump_respa(1, 1.0, 2)
+    xa, va, _, _ = a.state()
+    xb, vb, _, _ = b.state()
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+    oa, ob = a.observables(), b.observables()
+    assert oa["jump_proposals"] == ob["jump_proposals"] and oa["jump_accepts"] == ob["jump_accepts"]
