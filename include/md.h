@@ -73,6 +73,10 @@ typedef struct {
     int max_replicas;      /* replicas advanced together by each md_step_* call (>= 1) */
     int64_t event_log_cap; /* capacity of the accepted-jump log (0 = off) */
     int threads_per_atom;  /* pair kernel: 0 = autotune at the first step, else 1, 2, 4 or 8 */
+    int no_graphs;         /* 0: md_step_* calls of 32 or more steps replay CUDA graphs of 16-step
+                            * (or one-cycle) chunks, captured once per time step and system layout
+                            * on a private stream ordered after cuda_stream; nonzero: plain launches.
+                            * Results are identical either way. */
 } md_config;
 
 /* One periodic system (cubic box). All pointers are host pointers, copied. */

@@ -39,7 +39,7 @@ class MDError(RuntimeError):
 class MdConfig(C.Structure):
     _fields_ = [("precision", C.c_int), ("seed", C.c_uint64), ("device", C.c_int),
                 ("cuda_stream", C.c_void_p), ("max_replicas", C.c_int),
-                ("event_log_cap", C.c_int64), ("threads_per_atom", C.c_int)]
+                ("event_log_cap", C.c_int64), ("threads_per_atom", C.c_int), ("no_graphs", C.c_int)]
 
 
 class MdSystem(C.Structure):
@@ -131,11 +131,12 @@ class Engine:
     """One md_ctx: a batch of replicas advanced together on one GPU."""
 
     def __init__(self, precision=MD_MIXED, seed=0, device=0, stream=None, max_replicas=1,
-                 event_log_cap=0, threads_per_atom=0):
+                 event_log_cap=0, threads_per_atom=0, graphs=True):
         self.L = load_library()
         if stream is None:
             stream = _current_stream()
-        self.cfg = MdConfig(precision, seed, device, stream, max_replicas, event_log_cap, threads_per_atom)
+        self.cfg = MdConfig(precision, seed, device, stream, max_replicas, event_log_cap, threads_per_atom,
+                            0 if graphs else 1)
         h = C.c_void_p()
         rc = self.L.md_init(C.byref(h), C.byref(self.cfg))
         if rc != 0:

@@ -85,6 +85,10 @@ struct RepParams {
 // bin (bit = list kind), or SHELL_AMB when a ring or LJ shell limit lies
 // within the bin or its tolerance margin (decided in FP64 then)
 constexpr int SHELL_BINS = 2048;
+
+// bits of the per-replica overflow word: list kind k sets bit k; these two
+// are the outer candidate list and a cell above the in-block sort capacity
+constexpr uint32_t OVF_OUTER = 1u << 16, OVF_CELL = 1u << 17;
 constexpr uint16_t SHELL_AMB = 0x8000;
 
 // ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) ---------------------

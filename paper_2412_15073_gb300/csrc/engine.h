@@ -57,7 +57,7 @@ struct Dev {
     // per replica
     int* flags;                     // [R][2]: inner rebuild, outer rebuild
     uint32_t* err;                  // [R]
-    uint32_t* ovf;                  // [R] which capacity overflowed: bit kind, 5 outer list, 6 cell
+    uint32_t* ovf;                  // [R] which capacity overflowed: bit = list kind, OVF_OUTER, OVF_CELL
     unsigned long long* cnt;        // [R][NCOUNT]
     double* energy;                 // [R][6]: bond, angle, lj, coul, ke, spare
     long long* step_base;           // [R]

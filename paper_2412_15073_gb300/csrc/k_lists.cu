@@ -163,7 +163,7 @@ __global__ void k_cell_sort(Dev d)
     if (r < 0 || !d.flags[2 * r + 1]) return;
     const int s = d.cell_start[c], e = d.cell_start[c + 1], n = e - s;
     if (n > SORT_CAP) {
-        if (lane == 0) { atomicOr(&d.err[r], F_OVERFLOW); atomicOr(&d.ovf[r], 1u << 6); d.cell_cnt[c] = 0; }
+        if (lane == 0) { atomicOr(&d.err[r], F_OVERFLOW); atomicOr(&d.ovf[r], OVF_CELL); d.cell_cnt[c] = 0; }
         return;
     }
     for (int k = lane; k < n; k += 32) buf[w][k] = d.cell_atoms[s + k];
@@ -189,6 +189,7 @@ constexpr int OUTER_GROUPS = 2;                           // warps per cell; eac
 __global__ void __launch_bounds__(32 * OUTER_WARPS) k_outer_cells(Dev d, int exact)
 {
     __shared__ int nbs[OUTER_WARPS][125];
+    __shared__ uint4 stage[OUTER_WARPS][32];      // (x, y, z, j) of 32 candidates
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int task = blockIdx.x * OUTER_WARPS + w;       // (cell, first group of 32 atoms)
     const int c = task / OUTER_GROUPS, group0 = task % OUTER_GROUPS;
@@ -197,7 +198,7 @@ __global__ void __launch_bounds__(32 * OUTER_WARPS) k_outer_cells(Dev d, int exa
     if (r < 0 || !d.flags[2 * r + 1]) return;
     const int s_i = d.cell_start[c], e_i = d.cell_start[c + 1];
     const int natoms = e_i - s_i;
-    if (group0 == 0 && natoms > 1024 && lane == 0) { atomicOr(&d.err[r], F_OVERFLOW); atomicOr(&d.ovf[r], 1u << 6); }
+    if (group0 == 0 && natoms > 1024 && lane == 0) { atomicOr(&d.err[r], F_OVERFLOW); atomicOr(&d.ovf[r], OVF_CELL); }
     const int nlim = min(natoms, 1024);
     if (group0 * 32 >= nlim) return;
     const RepParams& P = d.P[r];
@@ -243,7 +244,9 @@ __global__ void __launch_bounds__(32 * OUTER_WARPS) k_outer_cells(Dev d, int exa
         for (int e = e0; e < e1 && e - e0 < 4; ++e) ex[e - e0] = d.ex_idx[e];
     }
     const double ro = P.R + P.skin_o;
-    const float r2of = float(ro * ro * (1.0 + 4e-6));
+    // FP32 test in units of the scaled coordinates (no scale multiplies),
+    // widened by 4e-6 so that rounding never drops a partner
+    const float r2ou = float(ro * ro * (1.0 + 4e-6) * P.inv_scl * P.inv_scl);
     const double r2o = ro * ro;
     uint32_t* row = live ? d.olist + (size_t)i * d.ocap : nullptr;
     int cnt = 0;
@@ -252,22 +255,24 @@ __global__ void __launch_bounds__(32 * OUTER_WARPS) k_outer_cells(Dev d, int exa
         const int cs0 = d.cell_start[gc], cs1 = d.cell_start[gc + 1];
         for (int base = cs0; base < cs1; base += 32) {
             const int nh = min(32, cs1 - base);
-            const int cand = lane < nh ? d.cell_atoms[base + lane] : 0;
-            const uint4 cp = lane < nh ? d.pos[cand] : make_uint4(0, 0, 0, 0);
+            __syncwarp();
+            if (lane < nh) {
+                const int cand = d.cell_atoms[base + lane];
+                const uint4 cp = d.pos[cand];
+                stage[w][lane] = make_uint4(cp.x, cp.y, cp.z, uint32_t(cand));
+            }
+            __syncwarp();
+            if (!live) continue;
             for (int t = 0; t < nh; ++t) {
-                const int j = __shfl_sync(0xffffffffu, cand, t);
-                uint4 pj;
-                pj.x = __shfl_sync(0xffffffffu, cp.x, t);
-                pj.y = __shfl_sync(0xffffffffu, cp.y, t);
-                pj.z = __shfl_sync(0xffffffffu, cp.z, t);
-                if (!live || j == i) continue;
+                const uint4 pj = stage[w][t];
+                const int j = int(pj.w);
+                if (j == i) continue;
                 bool ok;
                 if (exact) {
                     ok = dist2_fp64(d.xo, i, j, P) < r2o;
                 } else {
-                    float dx, dy, dz;
-                    sdisp(pi, pj, P.sclf, P.sclf_lo, dx, dy, dz);
-                    ok = dx * dx + dy * dy + dz * dz < r2of;
+                    const float dx = float(int(pi.x - pj.x)), dy = float(int(pi.y - pj.y)), dz = float(int(pi.z - pj.z));
+                    ok = dx * dx + dy * dy + dz * dz < r2ou;
                 }
                 if (!ok) continue;
                 bool exc = j == ex[0] || j == ex[1] || j == ex[2] || j == ex[3];
@@ -283,7 +288,7 @@ __global__ void __launch_bounds__(32 * OUTER_WARPS) k_outer_cells(Dev d, int exa
         d.ocnt[i] = cnt;
         if (cnt > d.ocap) {
             atomicOr(&d.err[r], F_OVERFLOW);
-            atomicOr(&d.ovf[r], 1u << 5);
+            atomicOr(&d.ovf[r], OVF_OUTER);
         }
     }
     }

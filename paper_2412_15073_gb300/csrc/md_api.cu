@@ -130,6 +130,14 @@ struct md_ctx {
     std::vector<cudaEvent_t> ev_pool;
     struct Pend { int cls; cudaEvent_t a, b; };
     std::vector<Pend> pend;
+    // CUDA graphs of driver chunks (see run_units); gen changes whenever the
+    // device layout does, which invalidates every captured graph
+    cudaStream_t gs = nullptr;
+    long long gen = 0;
+    struct Graph { long long gen; int key; double tau; int n_inner, units; cudaGraphExec_t exec;
+                   long long launches[6]; };
+    std::vector<Graph> graphs;
+    bool graphs_broken = false;
     // pinned staging
     double* h_stepc = nullptr;
     uint32_t* h_err = nullptr;
@@ -174,6 +182,7 @@ template <typename T> int dalloc(md_ctx* ctx, T** p, size_t count)
         return MD_ENOMEM;
     }
     ctx->bufs.push_back((void*)*p);
+    ctx->gen++;
     return MD_OK;
 }
 
@@ -935,10 +944,13 @@ int finish(md_ctx* ctx, long long inner_steps)
         CK(cudaMemcpy(o.data(), ctx->d.ovf, sizeof(uint32_t) * ctx->d.R, cudaMemcpyDeviceToHost));
         uint32_t m = 0;
         for (uint32_t v : o) m |= v;
-        static const char* names[7] = {"short", "full", "ring M", "ring L", "LJ", "outer", "cell"};
+        static const char* names[NKIND] = {"short", "full", "ring 0", "ring 1", "ring 2", "ring 3", "LJ"};
+        static_assert(NKIND == 7, "list kind names");
         std::string which;
-        for (int b = 0; b < 7; ++b)
+        for (int b = 0; b < NKIND; ++b)
             if (m & (1u << b)) which += std::string(which.empty() ? "" : ", ") + names[b];
+        if (m & OVF_OUTER) which += std::string(which.empty() ? "" : ", ") + "outer";
+        if (m & OVF_CELL) which += std::string(which.empty() ? "" : ", ") + "cell";
         FAIL(MD_EOVERFLOW, "capacity exceeded: %s (lists are sized at set-up; an unstable run "
                            "packs atoms denser than that)", which.c_str());
     }
@@ -954,6 +966,90 @@ int prepare(md_ctx* ctx, int family, double dt_fs)
     if ((rc = ensure_kinds(ctx, lists_needed(family)))) return rc;
     CK(cudaMemsetAsync(ctx->d.flags, 0, sizeof(int) * 2 * ctx->d.R, ctx->s));
     return MD_OK;
+}
+
+// ---- CUDA graphs ------------------------------------------------------------
+void drop_graphs(md_ctx* ctx)
+{
+    for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.exec);
+    ctx->graphs.clear();
+}
+
+// Runs `units` units of a driver (a step, or a RESPA cycle of spu inner
+// steps). body(u0, n) issues n units whose random streams are offset from
+// the replicas' step bases by u0 units. With graphs on, the first unit runs
+// as plain launches (it runs the autotuners, which time real launches) and
+// advances the step bases; then chunks of G units replay a graph captured
+// once (the chunk at offset 0, then the step bases advanced by G units);
+// the rest runs plainly at offset 0 and finish() advances the step bases
+// past it. The streams, and so the results, are those of a plain run.
+template <typename Body>
+int run_units(md_ctx* ctx, int key, double tau, int spu, long long units, Body body)
+{
+    Dev& d = ctx->d;
+    const long long G = std::max(1, 16 / spu);
+    long long done = 0;
+    if (!ctx->cfg.no_graphs && !ctx->prof && !ctx->graphs_broken && units >= 2 * G + 1) {
+        body(0, 1);
+        launch_advance(d, spu, ctx->s);
+        ctx->nlaunch[5] += 1;
+        done = 1;
+        const md_ctx::Graph* g = nullptr;
+        for (const auto& x : ctx->graphs)
+            if (x.gen == ctx->gen && x.key == key && x.tau == tau && x.n_inner == spu && x.units == G) g = &x;
+        if (!g) {
+            if (!ctx->gs) CK(cudaStreamCreateWithFlags(&ctx->gs, cudaStreamNonBlocking));
+            // capture on the private stream (the caller's may be the legacy default stream)
+            cudaEvent_t e = take_event(ctx);
+            CK(cudaEventRecord(e, ctx->s));
+            CK(cudaStreamWaitEvent(ctx->gs, e, 0));
+            ctx->ev_pool.push_back(e);
+            cudaStream_t s0 = ctx->s;
+            long long before[6];
+            std::copy(ctx->nlaunch, ctx->nlaunch + 6, before);
+            cudaGraph_t graph = nullptr;
+            cudaGraphExec_t exec = nullptr;
+            ctx->s = ctx->gs;
+            cudaError_t ce = cudaStreamBeginCapture(ctx->gs, cudaStreamCaptureModeThreadLocal);
+            if (ce == cudaSuccess) {
+                body(0, G);
+                launch_advance(d, G * spu, ctx->s);
+                ce = cudaStreamEndCapture(ctx->gs, &graph);
+            }
+            ctx->s = s0;
+            if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            if (ce != cudaSuccess) {
+                // no graph: fall back to plain launches for good
+                cudaGetLastError();
+                ctx->graphs_broken = true;
+                std::copy(before, before + 6, ctx->nlaunch);
+                CK(cudaStreamSynchronize(ctx->gs));
+            } else {
+                md_ctx::Graph ng{ctx->gen, key, tau, spu, (int)G, exec, {}};
+                for (int c = 0; c < 6; ++c) ng.launches[c] = ctx->nlaunch[c] - before[c] + (c == 5 ? 1 : 0);
+                std::copy(before, before + 6, ctx->nlaunch);
+                ctx->graphs.push_back(ng);
+                g = &ctx->graphs.back();
+            }
+        }
+        if (g) {
+            cudaEvent_t e = take_event(ctx);
+            CK(cudaEventRecord(e, ctx->s));
+            CK(cudaStreamWaitEvent(ctx->gs, e, 0));
+            while (units - done >= G) {
+                CK(cudaGraphLaunch(g->exec, ctx->gs));
+                for (int c = 0; c < 6; ++c) ctx->nlaunch[c] += g->launches[c];
+                done += G;
+            }
+            CK(cudaEventRecord(e, ctx->gs));
+            CK(cudaStreamWaitEvent(ctx->s, e, 0));
+            ctx->ev_pool.push_back(e);
+        }
+    }
+    // the step bases already count the units done above: offsets restart at 0
+    body(0, units - done);
+    return finish(ctx, (units - done) * spu);
 }
 
 // inner bonded step of the RESPA family: B A O A [grad] B at dt
@@ -1099,14 +1195,15 @@ int md_step_baoab(md_ctx* ctx, int64_t nsteps, double dt_fs)
     const double tau = dt_fs * 1e-3;
     if ((rc = set_stepc(ctx, tau))) return rc;
     force(ctx, 0, d.a0);
-    for (int64_t k = 0; k < nsteps; ++k) {
-        kick(ctx, d.a0, 0.5 * tau);
-        aoa(ctx, tau, uint32_t(k), 1);
-        rebuild_step(ctx);
-        force(ctx, 0, d.a0);
-        kick(ctx, d.a0, 0.5 * tau);
-    }
-    return finish(ctx, nsteps);
+    return run_units(ctx, 0, tau, 1, nsteps, [&](long long u0, long long n) {
+        for (long long k = u0; k < u0 + n; ++k) {
+            kick(ctx, d.a0, 0.5 * tau);
+            aoa(ctx, tau, uint32_t(k), 1);
+            rebuild_step(ctx);
+            force(ctx, 0, d.a0);
+            kick(ctx, d.a0, 0.5 * tau);
+        }
+    });
 }
 
 int md_step_jump(md_ctx* ctx, int64_t nsteps, double dt_fs)
@@ -1122,15 +1219,16 @@ int md_step_jump(md_ctx* ctx, int64_t nsteps, double dt_fs)
     // half of step k and the C' of the first half of step k+1 (adjacent, at the
     // same positions and acceleration) run in one launch.
     const bool fuse = !ctx->fp64;
-    for (int64_t k = 0; k < nsteps; ++k) {
-        if (k == 0 || !fuse) vphase(ctx, d.a0, 0.5 * tau, uint32_t(k), 0, 0);
-        aoa(ctx, tau, uint32_t(k), 1);
-        rebuild_step(ctx);
-        force(ctx, 5, d.a0);
-        if (fuse && k + 1 < nsteps) vphase(ctx, d.a0, 0.5 * tau, uint32_t(k), 1, 2, uint32_t(k + 1));
-        else vphase(ctx, d.a0, 0.5 * tau, uint32_t(k), 1, 1);
-    }
-    return finish(ctx, nsteps);
+    return run_units(ctx, 1, tau, 1, nsteps, [&](long long u0, long long n) {
+        for (long long k = u0; k < u0 + n; ++k) {
+            if (k == u0 || !fuse) vphase(ctx, d.a0, 0.5 * tau, uint32_t(k), 0, 0);
+            aoa(ctx, tau, uint32_t(k), 1);
+            rebuild_step(ctx);
+            force(ctx, 5, d.a0);
+            if (fuse && k + 1 < u0 + n) vphase(ctx, d.a0, 0.5 * tau, uint32_t(k), 1, 2, uint32_t(k + 1));
+            else vphase(ctx, d.a0, 0.5 * tau, uint32_t(k), 1, 1);
+        }
+    });
 }
 
 int md_step_baoab_respa(md_ctx* ctx, int64_t n_outer, double dt_inner_fs, int n_inner)
@@ -1143,15 +1241,16 @@ int md_step_baoab_respa(md_ctx* ctx, int64_t n_outer, double dt_inner_fs, int n_
     if ((rc = set_stepc(ctx, dt))) return rc;
     force(ctx, 1, d.ab);
     force(ctx, 2, d.al);
-    uint32_t s = 0;
-    for (int64_t o = 0; o < n_outer; ++o) {
-        kick(ctx, d.al, 0.5 * D);
-        for (int k = 0; k < n_inner; ++k, ++s) inner_bonded(ctx, dt, s, k == n_inner - 1);
-        rebuild_step(ctx);
-        force(ctx, 2, d.al);
-        kick(ctx, d.al, 0.5 * D);
-    }
-    return finish(ctx, (long long)n_outer * n_inner);
+    return run_units(ctx, 2, dt, n_inner, n_outer, [&](long long u0, long long n) {
+        uint32_t s = uint32_t(u0 * n_inner);
+        for (long long o = 0; o < n; ++o) {
+            kick(ctx, d.al, 0.5 * D);
+            for (int k = 0; k < n_inner; ++k, ++s) inner_bonded(ctx, dt, s, k == n_inner - 1);
+            rebuild_step(ctx);
+            force(ctx, 2, d.al);
+            kick(ctx, d.al, 0.5 * D);
+        }
+    });
 }
 
 int md_step_baoab_respa1(md_ctx* ctx, int64_t n_outer, double dt_inner_fs, int m_mid, int n_outer_ratio)
@@ -1165,20 +1264,22 @@ int md_step_baoab_respa1(md_ctx* ctx, int64_t n_outer, double dt_inner_fs, int m
     force(ctx, 1, d.ab);
     force(ctx, 3, d.as);
     force(ctx, 4, d.al);
-    uint32_t s = 0;
-    for (int64_t o = 0; o < n_outer; ++o) {
-        kick(ctx, d.al, 0.5 * D);
-        for (int j = 0; j < n_outer_ratio; ++j) {
-            kick(ctx, d.as, 0.5 * kap);
-            for (int k = 0; k < m_mid; ++k, ++s) inner_bonded(ctx, dt, s, k == m_mid - 1);
-            rebuild_step(ctx);
-            force(ctx, 3, d.as);
-            kick(ctx, d.as, 0.5 * kap);
+    const int spu = n_outer_ratio * m_mid;
+    return run_units(ctx, 3 | (m_mid << 8), dt, spu, n_outer, [&](long long u0, long long n) {
+        uint32_t s = uint32_t(u0 * spu);
+        for (long long o = 0; o < n; ++o) {
+            kick(ctx, d.al, 0.5 * D);
+            for (int j = 0; j < n_outer_ratio; ++j) {
+                kick(ctx, d.as, 0.5 * kap);
+                for (int k = 0; k < m_mid; ++k, ++s) inner_bonded(ctx, dt, s, k == m_mid - 1);
+                rebuild_step(ctx);
+                force(ctx, 3, d.as);
+                kick(ctx, d.as, 0.5 * kap);
+            }
+            force(ctx, 4, d.al);
+            kick(ctx, d.al, 0.5 * D);
         }
-        force(ctx, 4, d.al);
-        kick(ctx, d.al, 0.5 * D);
-    }
-    return finish(ctx, (long long)n_outer * n_outer_ratio * m_mid);
+    });
 }
 
 static int jump_respa_cycles(md_ctx* ctx, int64_t cycles, double dt_inner_fs, int n_inner)
@@ -1189,19 +1290,20 @@ static int jump_respa_cycles(md_ctx* ctx, int64_t cycles, double dt_inner_fs, in
     if ((rc = set_stepc(ctx, dt))) return rc;
     force(ctx, 1, d.ab);
     force(ctx, 3, d.as);
-    uint32_t s = 0;
     // as in md_step_jump, adjacent C' phases of consecutive cycles share a launch in mixed mode
     const bool fuse = !ctx->fp64;
-    for (int64_t o = 0; o < cycles; ++o) {
-        const uint32_t s0 = s;
-        if (o == 0 || !fuse) vphase(ctx, d.as, 0.5 * D, s0, 0, 0);
-        for (int k = 0; k < n_inner; ++k, ++s) inner_bonded(ctx, dt, s, k == n_inner - 1);
-        rebuild_step(ctx);
-        force(ctx, 3, d.as);
-        if (fuse && o + 1 < cycles) vphase(ctx, d.as, 0.5 * D, s0, 1, 2, s);
-        else vphase(ctx, d.as, 0.5 * D, s0, 1, 1);
-    }
-    return finish(ctx, (long long)cycles * n_inner);
+    return run_units(ctx, 4, dt, n_inner, cycles, [&](long long u0, long long n) {
+        uint32_t s = uint32_t(u0 * n_inner);
+        for (long long o = 0; o < n; ++o) {
+            const uint32_t s0 = s;
+            if (o == 0 || !fuse) vphase(ctx, d.as, 0.5 * D, s0, 0, 0);
+            for (int k = 0; k < n_inner; ++k, ++s) inner_bonded(ctx, dt, s, k == n_inner - 1);
+            rebuild_step(ctx);
+            force(ctx, 3, d.as);
+            if (fuse && o + 1 < n) vphase(ctx, d.as, 0.5 * D, s0, 1, 2, s);
+            else vphase(ctx, d.as, 0.5 * D, s0, 1, 1);
+        }
+    });
 }
 
 int md_step_jump_respa(md_ctx* ctx, int64_t n_outer, double dt_inner_fs, int n_inner)
@@ -1384,8 +1486,11 @@ int md_profile(md_ctx* ctx, int enable, int reset, double* ms_out, int64_t* grou
 int md_finalize(md_ctx* ctx)
 {
     if (!ctx) return MD_EINVAL;
+    if (ctx->gs) cudaStreamSynchronize(ctx->gs);
+    drop_graphs(ctx);
     free_device(ctx);
     cudaStreamSynchronize(ctx->s);
+    if (ctx->gs) cudaStreamDestroy(ctx->gs);
     for (auto& p : ctx->pend) { ctx->ev_pool.push_back(p.a); ctx->ev_pool.push_back(p.b); }
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     cudaFreeHost(ctx->h_stepc);

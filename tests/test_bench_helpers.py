@@ -1,0 +1,29 @@
+"""Host-side helpers of bench.py that need no GPU: the diffusion estimate."""
+import numpy as np
+
+import bench
+
+
+class FakeEngine:
+    """Brownian walkers in a periodic box, wrapped like the engine wraps
+    positions (x in [0, L), image counts in img)."""
+
+    def __init__(self, n, box, D, dt_fs, seed=0):
+        self.rng = np.random.default_rng(seed)
+        self.box, self.D, self.dt = box, D, dt_fs * 1e-3
+        self.u = self.rng.uniform(0, box, size=(n, 3))          # unwrapped
+
+    def step(self, k):
+        self.u += self.rng.normal(scale=np.sqrt(2 * self.D * self.dt * k), size=self.u.shape)
+
+    def state(self):
+        img = np.floor(self.u / self.box).astype(np.int32)
+        x = self.u - img * self.box
+        return x, np.zeros_like(x), img, x
+
+
+def test_diffusion_estimate_recovers_brownian_D():
+    D = 0.25                                                    # A^2/ps = 2.5e-5 cm^2/s
+    e = FakeEngine(3 * 4000, 20.0, D, 1.0)
+    got = bench.diffusion(e, e.step, 2000, 100, 20.0, 1.0)
+    assert abs(got / 2.5 - 1) < 0.05, got

@@ -320,3 +320,25 @@ def test_fused_cprime_pairs_equal_single_phases(M, oracle_mod, water648, how):
     assert np.array_equal(xa, xb) and np.array_equal(va, vb)
     oa, ob = a.observables(), b.observables()
     assert oa["jump_proposals"] == ob["jump_proposals"] and oa["jump_accepts"] == ob["jump_accepts"]
+
+
+@pytest.mark.parametrize("how,args", [("jump", (40,)), ("baoab", (40,)), ("jump_respa", (20, 1.0, 2)),
+                                      ("baoab_respa1", (12, 1.0, 2, 2)), ("jump_respa1", (12, 1.0, 2, 2))])
+def test_graph_replays_equal_plain_launches(M, oracle_mod, water648, how, args):
+    """Long calls replay CUDA graphs of 16-step chunks; the trajectory, the
+    counters and the step count equal those of plain launches, and a second
+    call reuses the graph and continues the same trajectory."""
+    runs = []
+    for graphs in (True, False):
+        e = M.Engine(precision=1, seed=21, event_log_cap=0, graphs=graphs)
+        e.set_system(0, water648, **PARAMS)
+        getattr(e, how)(*args)
+        getattr(e, how)(*args)
+        x, v, img, _ = e.state()
+        ob = e.observables()
+        runs.append((x, v, img, ob))
+        e.close()
+    (xa, va, ia, oa), (xb, vb, ib, ob) = runs
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb) and np.array_equal(ia, ib)
+    for k in ("step", "jump_proposals", "jump_accepts", "bps_proposals", "list_rebuilds"):
+        assert oa[k] == ob[k], k
