@@ -518,16 +518,18 @@ __device__ __forceinline__ void cprime_f(const Dev& d, const RepParams& P, int i
     }
 }
 
-// mixed-mode C' phase; threads visit atoms in the order vorder (atoms
+// mixed-mode velocity phase; threads visit atoms in the order vorder (atoms
 // ordered by expected number of proposals so that the lanes of a warp do
-// similar work). J' runs in its own kernel (k_jphase_f) before or after.
+// similar work). jmode places the J' phases (LJ bounces) around the C'
+// passes: 0 none, 1 after (s_off, half), 2 before (s_off, half), 3 before
+// (s_off, half) and after (s_off2, 0).
 // npass = 2 runs two consecutive C' phases at the same positions: the second
 // half of the step at s_off (half 1) and the first half of the next step at
 // s_off2 (half 0), which are adjacent in the C'J'AOAJ'C' sequence when no J'
 // acts between them (the J' phases of the two steps run before and after).
 template <int MINB>
 __global__ void __launch_bounds__(128, MINB) k_cphase_f(Dev d, const double* a, double tau2, uint32_t s_off, int s_abs,
-                                                        int half, int npass, uint32_t s_off2)
+                                                        int half, int npass, uint32_t s_off2, int jmode)
 {
     const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = t0 < d.N;
@@ -538,18 +540,19 @@ __global__ void __launch_bounds__(128, MINB) k_cphase_f(Dev d, const double* a, 
     uint32_t err = 0;
     if (live) {
         const int il = i - P.atom_off;
+        const uint32_t sb = s_abs ? 0u : uint32_t(d.step_base[r]);
         double v[3] = {d.v[3 * i], d.v[3 * i + 1], d.v[3 * i + 2]};
         const double ad[3] = {a ? a[3 * i] : 0.0, a ? a[3 * i + 1] : 0.0, a ? a[3 * i + 2] : 0.0};
+        if ((jmode & 2) && P.lj_on) jprime<float>(d, P, i, il, v, tau2, sb + s_off, half, tl, err);
         for (int pass = 0; pass < npass; ++pass) {
-            const uint32_t s0 = (s_abs ? 0u : uint32_t(d.step_base[r])) + (pass ? s_off2 : s_off);
+            const uint32_t s0 = sb + (pass ? s_off2 : s_off);
             const int hp = pass ? 0 : half;
             float3 jv = make_float3(0.f, 0.f, 0.f);
             if (P.rings_on) {
                 const float3 v0 = make_float3(float(v[0]), float(v[1]), float(v[2]));
                 const float3 af = make_float3(float(ad[0]), float(ad[1]), float(ad[2]));
-                if (pass) {
-                    d.v[3 * i] = v[0]; d.v[3 * i + 1] = v[1]; d.v[3 * i + 2] = v[2];   // read by the FP64 guard
-                }
+                // the FP64 guard of an acceptance reads the velocity at the start of the pass
+                d.v[3 * i] = v[0]; d.v[3 * i + 1] = v[1]; d.v[3 * i + 2] = v[2];
                 cprime_f(d, P, i, il, jv, v0, af, float(tau2), s0, hp, tl, err);
             }
             // FP64 end of the phase: (v0 + (tau/2) a) + sum of the jumps; the
@@ -558,6 +561,8 @@ __global__ void __launch_bounds__(128, MINB) k_cphase_f(Dev d, const double* a, 
             v[1] = fma(tau2, ad[1], v[1]) + double(jv.y);
             v[2] = fma(tau2, ad[2], v[2]) + double(jv.z);
         }
+        if (jmode & 1 && P.lj_on)
+            jprime<float>(d, P, i, il, v, tau2, sb + (jmode == 3 ? s_off2 : s_off), jmode == 3 ? 0 : half, tl, err);
         d.v[3 * i] = v[0]; d.v[3 * i + 1] = v[1]; d.v[3 * i + 2] = v[2];
         if (err) atomicOr(&d.err[r], err);
     }
@@ -569,6 +574,8 @@ __global__ void __launch_bounds__(128, MINB) k_cphase_f(Dev d, const double* a, 
     warp_add(&C[C_CACC], tl.cacc, uniform, lane);
     warp_add(&C[C_SATT], tl.satt, uniform, lane);
     warp_add(&C[C_GUARD], tl.guard, uniform, lane);
+    warp_add(&C[C_JPROP], tl.jprop, uniform, lane);
+    warp_add(&C[C_JACC], tl.jacc, uniform, lane);
 }
 
 // mixed-mode J' phase: one thread per atom (BPS bounces, FP64 velocity)
@@ -667,10 +674,12 @@ __global__ void k_rate_key(Dev d, const double* a, double tau2)
             lam += float(N[y]) * (P.eps_mode == 1 ? beta * LYv[y] * B + c0 : LYv[y] * (beta * B + c0));
         mu = lam * s;
     }
-    const int b = min(RATE_BUCKETS - 1, int(mu * 0.5f));
+    const int b = min(RATE_BUCKETS - 1, int(mu * 0.25f));
     const int key = r * RATE_BUCKETS + (RATE_BUCKETS - 1 - b);
     d.vkey[i] = key;
-    atomicAdd(&d.vhist[key], 1);
+    // one atomic per distinct key in the warp
+    const unsigned peers = __match_any_sync(__activemask(), key);
+    if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&d.vhist[key], __popc(peers));
 }
 
 // exclusive scan of the bucket counts into offsets (one block); clears the counts
@@ -715,7 +724,13 @@ __global__ void k_rate_scatter(Dev d)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.N) return;
-    d.vorder[atomicAdd(&d.vofs[d.vkey[i]], 1)] = i;
+    const int key = d.vkey[i];
+    const unsigned peers = __match_any_sync(__activemask(), key);
+    const int lane = threadIdx.x & 31, lead = __ffs(peers) - 1;
+    int base = 0;
+    if (lane == lead) base = atomicAdd(&d.vofs[key], __popc(peers));
+    base = __shfl_sync(peers, base, lead);
+    d.vorder[base + __popc(peers & ((1u << lane) - 1u))] = i;
 }
 
 }  // namespace
@@ -741,19 +756,19 @@ static void vphase_any(const Dev& d, const double* a, double tau2, uint32_t s, u
         return;
     }
     // order 0: C' then J'; 1: J' then C'; 2: J' (s, 1), C' (s, 1), C' (s2, 0), J' (s2, 0)
-    if (doJ && order >= 1) k_jphase_f<<<(d.N + 127) / 128, 128, 0, st>>>(d, tau2, s, s_abs, half);
-    if (doC) {
-        const int npass = order == 2 ? 2 : 1;
-        rate_order(d, a, tau2 * npass, st);
-        switch (variant) {
-        case 1: k_cphase_f<4><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, npass, s2); break;
-        case 2: k_cphase_f<5><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, npass, s2); break;
-        case 3: k_cphase_f<6><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, npass, s2); break;
-        default: k_cphase_f<3><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, npass, s2); break;
-        }
+    if (!doC) {
+        if (doJ) k_jphase_f<<<(d.N + 127) / 128, 128, 0, st>>>(d, tau2, s, s_abs, half);
+        return;
     }
-    if (doJ && order == 0) k_jphase_f<<<(d.N + 127) / 128, 128, 0, st>>>(d, tau2, s, s_abs, half);
-    if (doJ && order == 2) k_jphase_f<<<(d.N + 127) / 128, 128, 0, st>>>(d, tau2, s2, s_abs, 0);
+    const int npass = order == 2 ? 2 : 1;
+    const int jmode = !doJ ? 0 : (order == 0 ? 1 : (order == 1 ? 2 : 3));
+    rate_order(d, a, tau2 * npass, st);
+    switch (variant) {
+    case 1: k_cphase_f<4><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, npass, s2, jmode); break;
+    case 2: k_cphase_f<5><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, npass, s2, jmode); break;
+    case 3: k_cphase_f<6><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, npass, s2, jmode); break;
+    default: k_cphase_f<3><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, npass, s2, jmode); break;
+    }
 }
 
 void launch_vphase(const Dev& d, const double* a, double tau2, uint32_t s_off, int half, int order,

@@ -907,7 +907,7 @@ int tune_vphase(md_ctx* ctx, const double* a, double tau2)
 void vphase(md_ctx* ctx, const double* a, double tau2, uint32_t s_off, int half, int order, uint32_t s_off2 = 0)
 {
     if (ctx->vvar < 0) tune_vphase(ctx, a, tau2);
-    Prof p(ctx, 2, ctx->fp64 ? 1 : (order == 2 ? 6 : 5));
+    Prof p(ctx, 2, ctx->fp64 ? 1 : 4);   // mixed: rate order (3 kernels) + the velocity-phase kernel
     launch_vphase(ctx->d, a, tau2, s_off, half, order, 1, 1, ctx->fp64, ctx->vvar < 0 ? 0 : ctx->vvar, ctx->s,
                   s_off2);
 }
