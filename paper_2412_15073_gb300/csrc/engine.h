@@ -92,11 +92,13 @@ void launch_advance(const Dev& d, long long nsteps, cudaStream_t s);
 // J' runs as a kernel of its own.
 constexpr int NVPHASE_VARIANTS = 4;
 constexpr int RATE_BUCKETS = 128;
-// order 2 (mixed mode only): J' (s_off, half 1), C' (s_off, 1), C' (s_off2, 0), J' (s_off2, 0)
+// order 2 (mixed mode only): J' (s_off, half 1), C' (s_off, 1), C' (s_off2, 0), J' (s_off2, 0).
+// hp0: host copy of the parameters of replica 0 when the context holds one
+// replica (its constants then travel as a kernel parameter), else null.
 void launch_vphase(const Dev& d, const double* a, double tau2, uint32_t s_off, int half, int order,
-                   int doC, int doJ, int fp64, int variant, cudaStream_t s, uint32_t s_off2 = 0);
+                   int doC, int doJ, int fp64, int variant, cudaStream_t s, uint32_t s_off2, const RepParams* hp0);
 // same with an absolute stream index s0 (md_run_phase)
 void launch_vphase_abs(const Dev& d, const double* a, double tau2, uint32_t s0, int half, int order,
-                       int doC, int doJ, int fp64, int variant, cudaStream_t s);
+                       int doC, int doJ, int fp64, int variant, cudaStream_t s, const RepParams* hp0);
 
 }  // namespace mdj

@@ -354,19 +354,29 @@ __device__ __forceinline__ float coul_long_f(float r, float rinv, float alpha, f
     return -dc * u + (1.f - c) * du;
 }
 
-// ring of a proposal in FP32; a target that rounds up to Lam falls back to the
-// outermost ring with weight (never to an empty ring)
-__device__ __forceinline__ int ring_pick_f(const float (&w)[MAX_RINGS], float target, int nr)
+// per-replica constants of the FP32 C' loop. A single-system launch passes
+// them as a grid-constant kernel parameter (read straight from the constant
+// bank, no registers); batched launches copy them from RepParams.
+struct JC {
+    float sc, sclo;                        // L / 2^32 as two floats
+    uint32_t key0, key1;                   // Philox key (seed, replica)
+    int nr, atom_off, adaptive, pad;
+    float elo[MAX_RINGS], ehi[MAX_RINGS];  // ring y is [elo[y], ehi[y])
+    float alpha, kexp, eR, fR, R, sw, h;   // DSF and switch
+    float beta, eps0;
+};
+
+__host__ __device__ inline JC make_jc(const RepParams& P)
 {
-    int Y = -1, last = 0;
-    float cum = 0.f;
-#pragma unroll
-    for (int y = 0; y < MAX_RINGS; ++y) {
-        cum += w[y];
-        if (y < nr && w[y] > 0.f) last = y;
-        if (Y < 0 && y < nr && target < cum) Y = y;
-    }
-    return Y < 0 ? last : Y;
+    JC c;
+    c.sc = P.sclf; c.sclo = P.sclf_lo;
+    c.key0 = P.seed; c.key1 = P.replica;
+    c.nr = P.nr; c.atom_off = P.atom_off; c.adaptive = P.eps_mode == 1; c.pad = 0;
+    for (int y = 0; y < MAX_RINGS; ++y) { c.elo[y] = P.edgef[y]; c.ehi[y] = P.edgef[y + 1]; }
+    c.alpha = P.alphaf; c.kexp = P.kexpf; c.eR = P.eRf; c.fR = P.fRf;
+    c.R = float(P.R); c.sw = float(P.sw); c.h = float(P.h);
+    c.beta = float(P.beta); c.eps0 = float(P.eps0);
+    return c;
 }
 
 // C' for atom i in FP32 (Algorithm 4, adaptive or constant eps, up to four rings).
@@ -375,43 +385,35 @@ __device__ __forceinline__ int ring_pick_f(const float (&w)[MAX_RINGS], float ta
 // of k+1 is fetched; its position is fetched once proposal k is decided. If
 // proposal k jumps, the bound and ring of k+1 are recomputed (and the entry
 // refetched when the ring changed), so the sequence is that of Algorithm 4.
-__device__ __forceinline__ void cprime_f(const Dev& d, const RepParams& P, int i, int il, float3& jv,
+// Only B and Lam of the bound are kept; ring weights are recomputed from B.
+__device__ __forceinline__ void cprime_f(const Dev& d, const JC& c, const RepParams& P, int i, int il, float3& jv,
                                          const float3 v0, const float3 a, float T2, uint32_t s0, int half,
                                          Tally& tl, uint32_t& err)
 {
     int N[MAX_RINGS];
     if (ring_counts(d, P, i, N) == 0) return;
-    // per-replica constants in registers (the loop may store events, after
-    // which loads through P would be repeated)
-    const float sc = P.sclf, sclo = P.sclf_lo;
-    const uint32_t key0 = P.seed, key1 = P.replica;
-    const int nr = P.nr;
-    float elo[MAX_RINGS], ehi[MAX_RINGS];     // ring y is [elo[y], ehi[y])
-#pragma unroll
-    for (int y = 0; y < MAX_RINGS; ++y) { elo[y] = P.edgef[y]; ehi[y] = P.edgef[y + 1]; }
-    const float alpha = P.alphaf, kexp = P.kexpf, eR = P.eRf, fR = P.fRf;
-    const float R = float(P.R), sw = float(P.sw), h = float(P.h);
-    const float beta = float(P.beta), eps0 = float(P.eps0);
-    const bool adaptive = P.eps_mode == 1;
-    const int atom_off = P.atom_off;
     const uint32_t ctag = (uint32_t(TAG_C) << 24) | (uint32_t(half) << 20);
-
     const float mt = float(d.mt[i]);
-    const float sbm = sqrtf(beta * mt), sbom = sqrtf(beta / mt);
+    const float sbm = sqrtf(c.beta * mt), sbom = sqrtf(c.beta / mt);
     const float4 ly4 = __ldg(reinterpret_cast<const float4*>(d.LYf) + i);
     const float LYv[MAX_RINGS] = {ly4.x, ly4.y, ly4.z, ly4.w};
-    float fN[MAX_RINGS];
-#pragma unroll
-    for (int y = 0; y < MAX_RINGS; ++y) fN[y] = float(N[y]);
     const uint4 pi = d.pos[i];
     const float qiC = float(COULOMB) * __uint_as_float(pi.w);
-    const float c0 = sbom / (eps0 * 2.5066282746310002f);
+    const float c0 = sbom / (c.eps0 * 2.5066282746310002f);
     const float aa = a.x * a.x + a.y * a.y + a.z * a.z;
 
     float t = 0.f;
     float vx = v0.x + jv.x, vy = v0.y + jv.y, vz = v0.z + jv.z;
-    // bound at the current state: B, per-ring Lam_Y and weights, total Lam
-    float B, Lam, LamYv[MAX_RINGS], w[MAX_RINGS];
+    // per-pair rate bound of ring y at speed bound B
+    auto lamy = [&](int y, float B) -> float {
+        return c.adaptive ? fmaf(c.beta * LYv[y], B, c0) : LYv[y] * fmaf(c.beta, B, c0);
+    };
+    auto lamy_sel = [&](int Y, float B) -> float {
+        const float L = ring_sel(LYv, Y);
+        return c.adaptive ? fmaf(c.beta * L, B, c0) : L * fmaf(c.beta, B, c0);
+    };
+    // bound at the current state: B and Lam = sum_y N_y Lam_y
+    float B, Lam;
     auto bound = [&]() {
         const float s = T2 - t;
         const float vv = vx * vx + vy * vy + vz * vz;
@@ -419,20 +421,31 @@ __device__ __forceinline__ void cprime_f(const Dev& d, const RepParams& P, int i
         B = sqrtf(vv + s * s * aa + 2.f * s * fmaxf(va, 0.f));
         Lam = 0.f;
 #pragma unroll
+        for (int y = 0; y < MAX_RINGS; ++y) Lam += float(N[y]) * lamy(y, B);
+    };
+    // ring of a proposal: first ring whose cumulative weight exceeds U Lam;
+    // a target that rounds up to Lam falls back to the outermost ring with weight
+    auto pick = [&](uint32_t uy) -> int {
+        const float target = unif<float>(uy) * Lam;
+        int Y = -1, last = 0;
+        float cum = 0.f;
+#pragma unroll
         for (int y = 0; y < MAX_RINGS; ++y) {
-            LamYv[y] = adaptive ? fmaf(beta * LYv[y], B, c0) : LYv[y] * fmaf(beta, B, c0);
-            w[y] = fN[y] * LamYv[y];
-            Lam += w[y];
+            const float wy = float(N[y]) * lamy(y, B);
+            cum += wy;
+            if (y < c.nr && wy > 0.f) last = y;
+            if (Y < 0 && y < c.nr && target < cum) Y = y;
         }
+        return Y < 0 ? last : Y;
     };
     auto entry = [&](int Y, uint32_t uz) -> uint32_t {
         const uint32_t* row = d.list[L_R0 + Y] + (size_t)i * d.lcap[L_R0 + Y];
         return __ldg(row + __umulhi(uz, uint32_t(ring_sel(N, Y))));
     };
     uint32_t k = 0;
-    U4 u = philox(uint32_t(il), s0, ctag, 0, key0, key1);
+    U4 u = philox(uint32_t(il), s0, ctag, 0, c.key0, c.key1);
     bound();
-    int Yn = ring_pick_f(w, unif<float>(u.y) * Lam, nr);
+    int Yn = pick(u.y);
     uint32_t Jn = entry(Yn, u.z);
     uint4 pjn = __ldg(d.pos + Jn);
     for (;;) {
@@ -448,37 +461,37 @@ __device__ __forceinline__ void cprime_f(const Dev& d, const RepParams& P, int i
         const int Y = Yn;
         const int J = int(Jn);
         const uint4 pj = pjn;
-        const float Bk = B, LamYk = ring_sel(LamYv, Y), LYk = ring_sel(LYv, Y);
-        const float lo = ring_sel(elo, Y), hi = ring_sel(ehi, Y);
+        const float Bk = B;
         const uint32_t uacc = u.w;
         const uint32_t kk = k;
         ++k;
         // next proposal: draw, bound at the new state, ring and list entry
-        u = philox(uint32_t(il), s0, ctag, k, key0, key1);
+        u = philox(uint32_t(il), s0, ctag, k, c.key0, c.key1);
         bound();
-        Yn = ring_pick_f(w, unif<float>(u.y) * Lam, nr);
+        Yn = pick(u.y);
         Jn = entry(Yn, u.z);
         // decide proposal kk
         float dx, dy, dz;
-        sdisp(pi, pj, sc, sclo, dx, dy, dz);
+        sdisp(pi, pj, c.sc, c.sclo, dx, dy, dz);
         const float r2 = dx * dx + dy * dy + dz * dz;
         const float rinv = rsqrtf(r2);
         const float r = r2 * rinv;
-        if (r >= lo && r < hi) {
-            const float f = qiC * __uint_as_float(pj.w) * coul_long_f(r, rinv, alpha, kexp, eR, fR, R, sw, h) * rinv;
+        if (r >= ring_sel(c.elo, Y) && r < ring_sel(c.ehi, Y)) {
+            const float f = qiC * __uint_as_float(pj.w) *
+                            coul_long_f(r, rinv, c.alpha, c.kexp, c.eR, c.fR, c.R, c.sw, c.h) * rinv;
             const float gx = f * dx, gy = f * dy, gz = f * dz;
             const float gn = fabsf(f) * r;
             if (gn > 0.f) {
                 const float vg = vx * gx + vy * gy + vz * gz;
                 float eps, eta, p;
-                if (adaptive) {
-                    eps = eps0 * gn;
-                    eta = eps0 * sbm * vg;
-                    p = __fdividef(sbom * theta<float>(eta), eps0 * LamYk);
+                if (c.adaptive) {
+                    eps = c.eps0 * gn;
+                    eta = c.eps0 * sbm * vg;
+                    p = __fdividef(sbom * theta<float>(eta), c.eps0 * lamy_sel(Y, Bk));
                 } else {
-                    eps = eps0;
-                    eta = __fdividef(eps0 * sbm * vg, gn);
-                    p = __fdividef(gn * theta<float>(eta), LYk * (eps0 * sbm * Bk + 0.3989422804014327f));
+                    eps = c.eps0;
+                    eta = __fdividef(c.eps0 * sbm * vg, gn);
+                    p = __fdividef(gn * theta<float>(eta), ring_sel(LYv, Y) * (c.eps0 * sbm * Bk + 0.3989422804014327f));
                 }
                 bool acc;
                 const float U = unif<float>(uacc);
@@ -505,10 +518,10 @@ __device__ __forceinline__ void cprime_f(const Dev& d, const RepParams& P, int i
                     jv.x -= coef * gx; jv.y -= coef * gy; jv.z -= coef * gz;
                     vx -= coef * gx; vy -= coef * gy; vz -= coef * gz;
                     tl.cacc++;
-                    log_event(d, (long long)s0, half, int(TAG_C), d.rep[i], il, kk, J - atom_off);
+                    log_event(d, (long long)s0, half, int(TAG_C), d.rep[i], il, kk, J - c.atom_off);
                     // the velocity changed: bound and ring of the next proposal again
                     bound();
-                    const int Y2 = ring_pick_f(w, unif<float>(u.y) * Lam, nr);
+                    const int Y2 = pick(u.y);
                     if (Y2 != Yn) { Yn = Y2; Jn = entry(Yn, u.z); }
                 }
             }
@@ -527,9 +540,10 @@ __device__ __forceinline__ void cprime_f(const Dev& d, const RepParams& P, int i
 // half of the step at s_off (half 1) and the first half of the next step at
 // s_off2 (half 0), which are adjacent in the C'J'AOAJ'C' sequence when no J'
 // acts between them (the J' phases of the two steps run before and after).
-template <int MINB>
-__global__ void __launch_bounds__(128, MINB) k_cphase_f(Dev d, const double* a, double tau2, uint32_t s_off, int s_abs,
-                                                        int half, int npass, uint32_t s_off2, int jmode)
+template <int MINB, bool SINGLE>
+__global__ void __launch_bounds__(128, MINB) k_cphase_f(Dev d, const __grid_constant__ JC jc0, const double* a,
+                                                        double tau2, uint32_t s_off, int s_abs, int half, int npass,
+                                                        uint32_t s_off2, int jmode)
 {
     const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = t0 < d.N;
@@ -553,7 +567,12 @@ __global__ void __launch_bounds__(128, MINB) k_cphase_f(Dev d, const double* a, 
                 const float3 af = make_float3(float(ad[0]), float(ad[1]), float(ad[2]));
                 // the FP64 guard of an acceptance reads the velocity at the start of the pass
                 d.v[3 * i] = v[0]; d.v[3 * i + 1] = v[1]; d.v[3 * i + 2] = v[2];
-                cprime_f(d, P, i, il, jv, v0, af, float(tau2), s0, hp, tl, err);
+                if (SINGLE) {
+                    cprime_f(d, jc0, P, i, il, jv, v0, af, float(tau2), s0, hp, tl, err);
+                } else {
+                    const JC jc = make_jc(P);
+                    cprime_f(d, jc, P, i, il, jv, v0, af, float(tau2), s0, hp, tl, err);
+                }
             }
             // FP64 end of the phase: (v0 + (tau/2) a) + sum of the jumps; the
             // first sum rounds like a B kick, so a phase without jumps is one
@@ -748,7 +767,7 @@ static void rate_order(const Dev& d, const double* a, double tau2, cudaStream_t 
 }
 
 static void vphase_any(const Dev& d, const double* a, double tau2, uint32_t s, uint32_t s2, int s_abs, int half,
-                       int order, int doC, int doJ, int fp64, int variant, cudaStream_t st)
+                       int order, int doC, int doJ, int fp64, int variant, cudaStream_t st, const RepParams* hp0)
 {
     const int nb = (d.N + 127) / 128;
     if (fp64) {
@@ -763,24 +782,35 @@ static void vphase_any(const Dev& d, const double* a, double tau2, uint32_t s, u
     const int npass = order == 2 ? 2 : 1;
     const int jmode = !doJ ? 0 : (order == 0 ? 1 : (order == 1 ? 2 : 3));
     rate_order(d, a, tau2 * npass, st);
-    switch (variant) {
-    case 1: k_cphase_f<4><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, npass, s2, jmode); break;
-    case 2: k_cphase_f<5><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, npass, s2, jmode); break;
-    case 3: k_cphase_f<6><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, npass, s2, jmode); break;
-    default: k_cphase_f<3><<<nb, 128, 0, st>>>(d, a, tau2, s, s_abs, half, npass, s2, jmode); break;
+    if (hp0) {
+        const JC jc = make_jc(*hp0);
+        switch (variant) {
+        case 1: k_cphase_f<4, true><<<nb, 128, 0, st>>>(d, jc, a, tau2, s, s_abs, half, npass, s2, jmode); break;
+        case 2: k_cphase_f<5, true><<<nb, 128, 0, st>>>(d, jc, a, tau2, s, s_abs, half, npass, s2, jmode); break;
+        case 3: k_cphase_f<6, true><<<nb, 128, 0, st>>>(d, jc, a, tau2, s, s_abs, half, npass, s2, jmode); break;
+        default: k_cphase_f<3, true><<<nb, 128, 0, st>>>(d, jc, a, tau2, s, s_abs, half, npass, s2, jmode); break;
+        }
+    } else {
+        const JC jc{};
+        switch (variant) {
+        case 1: k_cphase_f<4, false><<<nb, 128, 0, st>>>(d, jc, a, tau2, s, s_abs, half, npass, s2, jmode); break;
+        case 2: k_cphase_f<5, false><<<nb, 128, 0, st>>>(d, jc, a, tau2, s, s_abs, half, npass, s2, jmode); break;
+        case 3: k_cphase_f<6, false><<<nb, 128, 0, st>>>(d, jc, a, tau2, s, s_abs, half, npass, s2, jmode); break;
+        default: k_cphase_f<3, false><<<nb, 128, 0, st>>>(d, jc, a, tau2, s, s_abs, half, npass, s2, jmode); break;
+        }
     }
 }
 
 void launch_vphase(const Dev& d, const double* a, double tau2, uint32_t s_off, int half, int order,
-                   int doC, int doJ, int fp64, int variant, cudaStream_t s, uint32_t s_off2)
+                   int doC, int doJ, int fp64, int variant, cudaStream_t s, uint32_t s_off2, const RepParams* hp0)
 {
-    vphase_any(d, a, tau2, s_off, s_off2, 0, half, order, doC, doJ, fp64, variant, s);
+    vphase_any(d, a, tau2, s_off, s_off2, 0, half, order, doC, doJ, fp64, variant, s, hp0);
 }
 
 void launch_vphase_abs(const Dev& d, const double* a, double tau2, uint32_t s0, int half, int order,
-                       int doC, int doJ, int fp64, int variant, cudaStream_t s)
+                       int doC, int doJ, int fp64, int variant, cudaStream_t s, const RepParams* hp0)
 {
-    vphase_any(d, a, tau2, s0, 0, 1, half, order, doC, doJ, fp64, variant, s);
+    vphase_any(d, a, tau2, s0, 0, 1, half, order, doC, doJ, fp64, variant, s, hp0);
 }
 
 }  // namespace mdj

@@ -851,6 +851,12 @@ void aoa(md_ctx* ctx, double tau, uint32_t s_off, int check)
     launch_aoa(ctx->d, tau, s_off, check, ctx->fp64, ctx->s);
 }
 
+// parameters of the only replica, for launches that pass them by value
+const RepParams* single_params(const md_ctx* ctx)
+{
+    return ctx->d.R == 1 ? &ctx->hp[0] : nullptr;
+}
+
 // autotune the velocity-phase kernel variant on a saved copy of the state:
 // velocities, counters, event log and error flags are restored afterwards, so
 // tuning leaves no trace in the trajectory
@@ -884,7 +890,7 @@ int tune_vphase(md_ctx* ctx, const double* a, double tau2)
         for (int rep = 0; rep < 2; ++rep) {
             CK(cudaMemcpyAsync(d.v, vs, sizeof(double) * 3 * d.N, cudaMemcpyDeviceToDevice, ctx->s));
             cudaEventRecord(e0, ctx->s);
-            launch_vphase(d, a, tau2, 0, 0, 0, 1, 1, 0, v, ctx->s);
+            launch_vphase(d, a, tau2, 0, 0, 0, 1, 1, 0, v, ctx->s, 0, single_params(ctx));
             cudaEventRecord(e1, ctx->s);
             cudaEventSynchronize(e1);
             float ms = 0;
@@ -909,7 +915,7 @@ void vphase(md_ctx* ctx, const double* a, double tau2, uint32_t s_off, int half,
     if (ctx->vvar < 0) tune_vphase(ctx, a, tau2);
     Prof p(ctx, 2, ctx->fp64 ? 1 : 4);   // mixed: rate order (3 kernels) + the velocity-phase kernel
     launch_vphase(ctx->d, a, tau2, s_off, half, order, 1, 1, ctx->fp64, ctx->vvar < 0 ? 0 : ctx->vvar, ctx->s,
-                  s_off2);
+                  s_off2, single_params(ctx));
 }
 
 int set_stepc(md_ctx* ctx, double tau)
@@ -1405,7 +1411,7 @@ int md_run_phase(md_ctx* ctx, int phase, double tau2_ps, int64_t s0, int half, i
     {
         Prof p(ctx, 2, (ctx->fp64 || phase == 1) ? 1 : 4);   // phase 0: rate order (3) + C'; phase 1: J' only
         launch_vphase_abs(d, phase == 0 ? d.a0 : nullptr, tau2_ps, uint32_t(s0), half, 0, phase == 0, phase == 1,
-                          ctx->fp64, ctx->vvar < 0 ? 0 : ctx->vvar, ctx->s);
+                          ctx->fp64, ctx->vvar < 0 ? 0 : ctx->vvar, ctx->s, single_params(ctx));
     }
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(ctx->h_err, d.err, sizeof(uint32_t) * d.R, cudaMemcpyDeviceToHost, ctx->s));
