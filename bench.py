@@ -42,10 +42,15 @@ METRIC = "ns/day & Gpair-evals/s, JUMP vs BAOAB on 1 GB300 at matched T/D (97k a
 WORKLOAD = ("water 96,000 atoms (32,000 flexible 3-site waters, 98.6 A cube), LJ+DSF r_E 10 A, "
             "r_c 5 A, rings at 5.25/6/7.5 A, adaptive eps0 0.1, 300 K, gamma 1/ps; JUMP 1 fs vs BAOAB 1 fs")
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# FP32 work of one pair of the pair kernel and of one jump proposal (counted
-# from the kernel source; see the roofline notes in the design doc)
+# FP32 work of one pair of the pair kernel (min image, r^2, erfc/exp, DSF, LJ,
+# switch, fixed point) and of one jump proposal (Philox rounds, log, bound,
+# ring pick, gathers, pair gradient, Theta, accept), counted from the kernels
 FLOP_PER_PAIR = 52
 OPS_PER_PROPOSAL = 230
+# DRAM bytes per C' proposal of the velocity-phase kernel: one ncu capture
+# (--set full) of a single-phase launch of this workload read 233.2 MB and
+# wrote 13.6 MB for 3.57 M proposals; scaled to a launch by its proposals
+TRAFFIC_PER_PROPOSAL = (233.197e6 + 13.631e6) / 3.574e6
 
 
 def ns_per_day(fs_simulated: float, seconds: float) -> float:
@@ -353,7 +358,9 @@ def main():
                             (cp1["bps_proposals"] - cp0["bps_proposals"])) / max(groups[top], 1)
         achieved = OPS_PER_PROPOSAL * props_per_launch / (per_launch_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
-                "frac": achieved / alu_peak, "traffic": None, "kernel": "k_vphase (C'/J' jumps)",
+                "frac": achieved / alu_peak, "traffic": TRAFFIC_PER_PROPOSAL * props_per_launch,
+                "traffic_note": "bytes per launch, scaled from one ncu capture by proposals",
+                "kernel": "k_cphase_f (C' pairs and J')",
                 "units_per_launch": props_per_launch, "ops_per_unit": OPS_PER_PROPOSAL,
                 "peak_source": f"152 SMs x 128 lanes x {clock/1e6:.0f} MHz (max clock)"}
     else:

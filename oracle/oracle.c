@@ -13,7 +13,7 @@
  *   Sec. 2.4  Poisson thinning, Algorithms 1-3, rejection sampling of G~
  *   Sec. 3.1  pair jumps for direct electrostatics, Algorithm 4, ring technique
  *   Sec. 3.2  Lennard-Jones BPS jumps, Algorithm 5
- * Readings where the paper is silent (documented in the design doc):
+ * Readings where the paper is silent:
  *   electrostatics: damped shifted force (DSF) Coulomb in place of Ewald;
  *   switch chi: quintic smoothstep on [r_c-h, r_c];
  *   rate bounds: numerical max of |d/dr (1-chi)U| on a grid, rounded up;
