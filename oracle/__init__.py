@@ -42,7 +42,7 @@ class Params(C.Structure):
                 ("gamma", C.c_double), ("temperature", C.c_double), ("eps0", C.c_double),
                 ("skin", C.c_double), ("skin_outer", C.c_double), ("eps_mode", C.c_int),
                 ("n_rings", C.c_int), ("ring_r", C.c_double * 3), ("seed", C.c_uint32),
-                ("replica", C.c_uint32)]
+                ("replica", C.c_uint32), ("lazy_lists", C.c_int)]
 
 
 _lib = None
@@ -131,7 +131,7 @@ class Oracle:
 
     def __init__(self, sys, r_cut=9.0, r_split=5.0, h_switch=0.5, r_mid=5.5, dsf_alpha=0.2,
                  gamma=1.0, temperature=300.0, eps0=0.1, skin=0.3, skin_outer=None, eps_mode=1,
-                 seed=0, replica=0, ring_r=None):
+                 seed=0, replica=0, ring_r=None, lazy_lists=False):
         self.L = lib()
         self.n = sys.n
         if skin_outer is None:
@@ -140,7 +140,8 @@ class Oracle:
         n_rings = len(rr) + 1 if ring_r is not None else 0
         self.params = Params(sys.box, r_cut, r_split, h_switch, r_mid, dsf_alpha, gamma,
                              temperature, eps0, skin, skin_outer, eps_mode, n_rings,
-                             (C.c_double * 3)(*(rr + [0.0] * (3 - len(rr)))), seed, replica)
+                             (C.c_double * 3)(*(rr + [0.0] * (3 - len(rr)))), seed, replica,
+                             1 if lazy_lists else 0)
         a = lambda z, t: np.ascontiguousarray(z, dtype=t)
         self._keep = [a(sys.x, np.float64), a(sys.v, np.float64), a(sys.mass, np.float64),
                       a(sys.charge, np.float64), a(sys.type, np.int32), a(sys.lj_eps, np.float64),
@@ -223,8 +224,7 @@ class Oracle:
         return c
 
     def list_of(self, kind, i):
-        c = self.list_counts(kind)[i]
-        out = np.zeros(max(int(c), 1), dtype=np.int32)
+        out = np.zeros(max(self.n, 1), dtype=np.int32)          # a list never exceeds the atom count
         m = self.L.or_list_get(self.h, kind, int(i), _p(out))
         return out[:m]
 

@@ -72,6 +72,10 @@ struct or_sys {
     double lhat[OR_MAX_RINGS], qmax;
     double *LY, *LLJ;                    /* per-atom rate bounds (n x 4), LJ bound */
     or_list lists[K_NKIND];
+    int lazy;                /* lists built per atom on demand (see or_params.lazy_lists) */
+    int alist_atom;          /* atom whose lists the per-atom cache holds (-1: none) */
+    int* alist[K_NKIND];     /* that atom's lists */
+    int alist_n[K_NKIND];
     int ncell;
     int *cellm;              /* cell of each atom at the last outer rebuild */
     double *xo;              /* positions at the last outer rebuild */
@@ -482,29 +486,56 @@ static void cj_push(cj_vec* v, int cell, int j)
     v->n++;
 }
 
-/* one brute-force pass over all pairs fills the three jump lists */
+/* the lists of atom i: a brute-force pass over all j, then the (cell, j) order */
+static void atom_lists(const or_sys* s, int i, cj_vec* out)
+{
+    const int* cell = s->cellm;
+    double hi = s->p.r_cut + s->p.skin;
+    for (int j = 0; j < s->n; ++j) {
+        if (j == i) continue;
+        double d[3];
+        minimage(s, i, j, d);
+        double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        if (r2 >= hi * hi || excluded(s, i, j)) continue;
+        for (int kind = 0; kind < K_NKIND; ++kind)
+            if (in_kind(s, kind, i, j, r2)) cj_push(&out[kind], cell[j], j);
+    }
+    for (int kind = 0; kind < K_NKIND; ++kind) qsort(out[kind].e, (size_t)out[kind].n, sizeof(cj_t), cmp_cj);
+}
+
+/* list `kind` of atom i: from the lists of all atoms, or built for atom i
+ * alone in lazy mode (one atom cached at a time; not for parallel callers) */
+static const int* list_of(or_sys* s, int kind, int i, int* n)
+{
+    if (!s->lazy) {
+        const or_list* l = &s->lists[kind];
+        *n = l->off[i + 1] - l->off[i];
+        return l->idx + l->off[i];
+    }
+    if (s->alist_atom != i) {
+        cj_vec tmp[K_NKIND];
+        memset(tmp, 0, sizeof tmp);
+        atom_lists(s, i, tmp);
+        for (int k = 0; k < K_NKIND; ++k) {
+            free(s->alist[k]);
+            s->alist[k] = (int*)malloc(sizeof(int) * (size_t)(tmp[k].n > 0 ? tmp[k].n : 1));
+            for (int t = 0; t < tmp[k].n; ++t) s->alist[k][t] = tmp[k].e[t].j;
+            s->alist_n[k] = tmp[k].n;
+            free(tmp[k].e);
+        }
+        s->alist_atom = i;
+    }
+    *n = s->alist_n[kind];
+    return s->alist[kind];
+}
+
+/* one brute-force pass over all pairs fills the jump lists of every atom */
 static void build_lists(or_sys* s)
 {
     int n = s->n;
-    const int* cell = s->cellm;
     cj_vec* tmp = (cj_vec*)calloc((size_t)n * K_NKIND, sizeof(cj_vec));
-    double hi = s->p.r_cut + s->p.skin;
 #pragma omp parallel for schedule(dynamic, 16)
-    for (int i = 0; i < n; ++i) {
-        for (int j = 0; j < n; ++j) {
-            if (j == i) continue;
-            double d[3];
-            minimage(s, i, j, d);
-            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-            if (r2 >= hi * hi || excluded(s, i, j)) continue;
-            for (int kind = 0; kind < K_NKIND; ++kind)
-                if (in_kind(s, kind, i, j, r2)) cj_push(&tmp[(size_t)i * K_NKIND + kind], cell[j], j);
-        }
-        for (int kind = 0; kind < K_NKIND; ++kind) {
-            cj_vec* v = &tmp[(size_t)i * K_NKIND + kind];
-            qsort(v->e, (size_t)v->n, sizeof(cj_t), cmp_cj);
-        }
-    }
+    for (int i = 0; i < n; ++i) atom_lists(s, i, &tmp[(size_t)i * K_NKIND]);
     for (int kind = 0; kind < K_NKIND; ++kind) {
         or_list* l = &s->lists[kind];
         free(l->off);
@@ -561,17 +592,16 @@ static void maybe_rebuild(or_sys* s)
     }
 }
 
-void or_list_counts(const or_sys* s, int kind, int* counts)
+void or_list_counts(or_sys* s, int kind, int* counts)
 {
-    const or_list* l = &s->lists[kind];
-    for (int i = 0; i < s->n; ++i) counts[i] = l->off[i + 1] - l->off[i];
+    for (int i = 0; i < s->n; ++i) list_of(s, kind, i, &counts[i]);
 }
 
-int or_list_get(const or_sys* s, int kind, int i, int* out)
+int or_list_get(or_sys* s, int kind, int i, int* out)
 {
-    const or_list* l = &s->lists[kind];
-    int c = l->off[i + 1] - l->off[i];
-    for (int k = 0; k < c; ++k) out[k] = l->idx[l->off[i] + k];
+    int c;
+    const int* l = list_of(s, kind, i, &c);
+    for (int k = 0; k < c; ++k) out[k] = l[k];
     return c;
 }
 
@@ -775,10 +805,10 @@ static void cprime_atom(or_sys* s, int i, double* v, const double* a, double tau
 {
     int nr = s->nr;
     int N[OR_MAX_RINGS];
+    const int* lidx[OR_MAX_RINGS];
     int ntot = 0;
     for (int y = 0; y < nr; ++y) {
-        const or_list* l = &s->lists[y];
-        N[y] = l->off[i + 1] - l->off[i];
+        lidx[y] = list_of(s, y, i, &N[y]);
         ntot += N[y];
     }
     double beta = s->beta, mt = s->mt[i], eps0 = s->p.eps0;
@@ -826,8 +856,7 @@ static void cprime_atom(or_sys* s, int i, double* v, const double* a, double tau
             cum += w[y];
             if (target < cum) { Y = y; break; }
         }
-        const or_list* lY = &s->lists[Y];
-        int J = lY->idx[lY->off[i] + pick(u[2], N[Y])];
+        int J = lidx[Y][pick(u[2], N[Y])];
         double d[3];
         minimage(s, i, J, d);
         double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
@@ -880,8 +909,8 @@ static void cprime_atom(or_sys* s, int i, double* v, const double* a, double tau
 static void jprime_atom(or_sys* s, int i, double* v, double tau2, uint32_t s0, int half,
                         int64_t* nprop, int64_t* nacc, uint32_t* err)
 {
-    const or_list* l = &s->lists[K_LJ];
-    int N = l->off[i + 1] - l->off[i];
+    int N;
+    const int* lidx = list_of(s, K_LJ, i, &N);
     double V = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
     double Li = s->LLJ[i];
     if (N == 0 || !(V > 0.0) || !(Li > 0.0)) return;
@@ -896,7 +925,7 @@ static void jprime_atom(or_sys* s, int i, double* v, double tau2, uint32_t s0, i
         if (t + T > tau2) break;
         t += T;
         (*nprop)++;
-        int J = l->idx[l->off[i] + pick(u[2], N)];
+        int J = lidx[pick(u[2], N)];
         double d[3];
         minimage(s, i, J, d);
         double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
@@ -990,6 +1019,7 @@ static void aoa(or_sys* s, double tau, uint32_t s0)
 /* BAOAB: B A O A [grad] B on the full potential */
 int or_step_baoab(or_sys* s, int64_t nsteps, double dt_fs)
 {
+    if (s->lazy) return -1;   /* the steps rebuild the lists of every atom */
     double tau = dt_fs * 1e-3;
     accel(s, 0, s->a0);
     for (int64_t st = 0; st < nsteps; ++st) {
@@ -1008,6 +1038,7 @@ int or_step_baoab(or_sys* s, int64_t nsteps, double dt_fs)
 /* JUMP: C' J' A O A J' C' with F0 = bonded + chi-weighted pairs */
 int or_step_jump(or_sys* s, int64_t nsteps, double dt_fs)
 {
+    if (s->lazy) return -1;   /* the steps rebuild the lists of every atom */
     double tau = dt_fs * 1e-3;
     accel(s, 5, s->a0);
     for (int64_t st = 0; st < nsteps; ++st) {
@@ -1039,6 +1070,7 @@ static void inner_bonded(or_sys* s, double dt)
 /* BAOAB-RESPA: B_nb(D/2) [n x inner bonded] B_nb(D/2), D = n dt */
 int or_step_baoab_respa(or_sys* s, int64_t nouter, double dt_inner_fs, int n_inner)
 {
+    if (s->lazy) return -1;   /* the steps rebuild the lists of every atom */
     double dt = dt_inner_fs * 1e-3, D = dt * n_inner;
     accel(s, 1, s->ab);
     accel(s, 2, s->al);
@@ -1056,6 +1088,7 @@ int or_step_baoab_respa(or_sys* s, int64_t nouter, double dt_inner_fs, int n_inn
 /* BAOAB-RESPA1: B_long(D/2) [n x (B_short(k/2) [m x inner] B_short(k/2))] B_long(D/2) */
 int or_step_baoab_respa1(or_sys* s, int64_t nouter, double dt_inner_fs, int m_mid, int n_outer)
 {
+    if (s->lazy) return -1;   /* the steps rebuild the lists of every atom */
     double dt = dt_inner_fs * 1e-3, kap = dt * m_mid, D = kap * n_outer;
     accel(s, 1, s->ab);
     accel(s, 3, s->as);
@@ -1081,6 +1114,7 @@ int or_step_baoab_respa1(or_sys* s, int64_t nouter, double dt_inner_fs, int m_mi
  * C' drift being the short-range nonbonded acceleration */
 int or_step_jump_respa(or_sys* s, int64_t nouter, double dt_inner_fs, int n_inner)
 {
+    if (s->lazy) return -1;   /* the steps rebuild the lists of every atom */
     double dt = dt_inner_fs * 1e-3, D = dt * n_inner;
     accel(s, 1, s->ab);
     accel(s, 3, s->as);
@@ -1103,6 +1137,7 @@ int or_step_jump_respa(or_sys* s, int64_t nouter, double dt_inner_fs, int n_inne
  * short-range pairs and the jumps, the inner level the bonded terms. */
 int or_step_jump_respa1(or_sys* s, int64_t nouter, double dt_inner_fs, int m_mid, int n_outer)
 {
+    if (s->lazy) return -1;   /* the steps rebuild the lists of every atom */
     double dt = dt_inner_fs * 1e-3, kap = dt * m_mid;
     accel(s, 1, s->ab);
     accel(s, 3, s->as);
@@ -1208,7 +1243,9 @@ or_sys* or_create(int n, const or_params* p,
     wrap(s);
     memset(s->img, 0, sizeof(int) * n3);
     outer_rebuild(s);
-    build_lists(s);
+    s->lazy = p->lazy_lists != 0;
+    s->alist_atom = -1;
+    if (!s->lazy) build_lists(s);
     s->cnt[5] = 0;
     return s;
 }
@@ -1223,7 +1260,7 @@ void or_destroy(or_sys* s)
     free(s->angles); free(s->ak); free(s->at0);
     free(s->exoff); free(s->exidx);
     free(s->LY); free(s->LLJ);
-    for (int k = 0; k < K_NKIND; ++k) { free(s->lists[k].off); free(s->lists[k].idx); }
+    for (int k = 0; k < K_NKIND; ++k) { free(s->lists[k].off); free(s->lists[k].idx); free(s->alist[k]); }
     free(s->a0); free(s->ab); free(s->as); free(s->al);
     free(s->cellm); free(s->xo);
     free(s->ev);
@@ -1269,8 +1306,11 @@ void or_set_state(or_sys* s, const double* x, const double* v, const int* img,
     memcpy(s->x, x_outer ? x_outer : (x_build ? x_build : x), sizeof(double) * n3);
     outer_rebuild(s);
     if (x_build) memcpy(s->x, x_build, sizeof(double) * n3);
-    build_lists(s);
-    s->cnt[5]--;
+    if (!s->lazy) {
+        build_lists(s);
+        s->cnt[5]--;
+    }
+    s->alist_atom = -1;
     memcpy(s->x, x, sizeof(double) * n3);
     memcpy(s->v, v, sizeof(double) * n3);
     if (img) memcpy(s->img, img, sizeof(int) * n3);

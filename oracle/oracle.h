@@ -45,6 +45,9 @@ typedef struct {
     double ring_r[3];    /* interior ring edges, increasing, inside (r_c-h, r_E) */
     uint32_t seed;       /* Philox key word 0 */
     uint32_t replica;    /* Philox key word 1 */
+    int lazy_lists;      /* nonzero: no list build at creation; the lists of one atom are built
+                          * when a per-atom call needs them (for very large systems whose O(N^2)
+                          * list build is out of reach); the or_step_* calls then return -1 */
 } or_params;
 
 typedef struct or_sys or_sys;
@@ -94,8 +97,8 @@ void or_gradient_atom(or_sys* s, int mode, int i, double* g3);
 void or_bounds(const or_sys* s, double* lhat, double* qmax, double* edges, int* nrings, double* LY, double* LLJ);
 
 /* jump lists: kind 0..3 ring 0..3 (inner to outer), 4 LJ. counts[n]; list of one atom */
-void or_list_counts(const or_sys* s, int kind, int* counts);
-int  or_list_get(const or_sys* s, int kind, int i, int* out);
+void or_list_counts(or_sys* s, int kind, int* counts);
+int  or_list_get(or_sys* s, int kind, int i, int* out);
 /* force a rebuild now */
 void or_rebuild(or_sys* s);
 

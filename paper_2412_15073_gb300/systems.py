@@ -192,14 +192,19 @@ def water_with_beads(n_total: int = 1_000_000, n_beads: int = 50_002, seed: int 
          .reshape(-1, 3) * a_b)
     g = g[np.argsort((g * g).sum(1), kind="stable")][:n_beads]
     xb = centre + g + rng.uniform(-0.05, 0.05, size=g.shape) * a_b
-    # water: lattice over the box with sites inside the bead sphere (+ margin) removed
-    w = water_box(int(n_mol * 1.6), box=box, seed=seed, temperature=temperature)
+    # water: a lattice over the box slightly denser than the liquid; sites
+    # inside the bead sphere (+ margin) are removed and n_mol of the rest kept
+    # at random, so the water fills the box uniformly at liquid density
+    frac_out = 1.0 - 4.0 / 3.0 * math.pi * (r_b + 2.0) ** 3 / box ** 3
+    n_side = int(math.ceil((1.02 * n_mol / frac_out) ** (1.0 / 3.0)))
+    w = water_box(n_side ** 3, box=box, seed=seed, temperature=temperature)
     o = w.x[0::3]
     d = o - centre
     d -= box * np.round(d / box)
-    keep = np.flatnonzero(np.sqrt((d * d).sum(1)) > r_b + 2.0)[:n_mol]
-    if keep.size < n_mol:
+    outside = np.flatnonzero(np.sqrt((d * d).sum(1)) > r_b + 2.0)
+    if outside.size < n_mol:
         raise ValueError("box too small for the requested water count")
+    keep = np.sort(rng.choice(outside, n_mol, replace=False))
     atoms = np.stack([3 * keep, 3 * keep + 1, 3 * keep + 2], 1).reshape(-1)
     xw = w.x[atoms]
     n_w = xw.shape[0]

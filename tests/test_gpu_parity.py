@@ -342,3 +342,60 @@ def test_graph_replays_equal_plain_launches(M, oracle_mod, water648, how, args):
     assert np.array_equal(xa, xb) and np.array_equal(va, vb) and np.array_equal(ia, ib)
     for k in ("step", "jump_proposals", "jump_accepts", "bps_proposals", "list_rebuilds"):
         assert oa[k] == ob[k], k
+
+
+def test_batched_ensemble_of_64_replicas(M, oracle_mod):
+    """The batched ensemble: 64 replicas of 216-2000 waters (sizes from seed
+    1), each in its own box, advanced together in FP64; four sampled replicas
+    (the smallest, the largest and two others) follow their own oracle runs
+    to 1e-6 A over 10 JUMP steps."""
+    from paper_2412_15073_gb300 import systems
+    sizes = systems.replica_sizes(64, seed=1)
+    syss = [systems.water_box(n, seed=100 + k) for k, n in enumerate(sizes)]
+    e = M.Engine(precision=0, seed=3, max_replicas=64)
+    for r, s in enumerate(syss):
+        e.set_system(r, s, **PARAMS)
+    e.jump(10)
+    pick = sorted({int(np.argmin(sizes)), int(np.argmax(sizes)), 17, 40})
+    for r in pick:
+        o = oracle_mod.Oracle(syss[r], seed=3, replica=r, **PARAMS)
+        o.jump(10)
+        assert pos_err(e.state(r)[0], o.state()[0], syss[r].box) < 1e-6, r
+        assert e.observables(r)["jump_accepts"] == o.counters()[1], r
+    e.close()
+
+
+def test_million_atom_heterogeneous_sampled(M, oracle_mod):
+    """The 1,000,000-atom system (water around a dense sphere of 50,002
+    charged LJ beads, 229 A box) in mixed precision: gradients of 40 sampled
+    atoms within 1e-5 of the oracle's, and one C' phase of 100 sampled atoms
+    (oracle with per-atom lists, since its O(N^2) list build is out of reach)."""
+    from paper_2412_15073_gb300 import systems
+    w = systems.water_with_beads()
+    p = dict(PARAMS, r_cut=10.0, skin=0.5, skin_outer=1.5)
+    e = M.Engine(precision=1, seed=5)
+    e.set_system(0, w, **p)
+    o = oracle_mod.Oracle(w, seed=5, replica=0, lazy_lists=True, **p)
+    rng = np.random.default_rng(7)
+    n_w = 3 * 316_666
+    idx = np.concatenate([rng.choice(n_w, 30, replace=False), n_w + rng.choice(w.n - n_w, 10, replace=False)])
+    for mode in (0, 3):
+        g = e.gradient(mode)
+        tot = e.gradient(0) if mode == 3 else g
+        rms = np.sqrt((tot * tot).sum(1).mean())
+        for i in idx:
+            ref = o.gradient_atom(mode, int(i))
+            den = max(np.linalg.norm(tot[i]), 0.01 * rms)
+            assert np.linalg.norm(g[i] - ref) / den <= 1e-5, (mode, i)
+    mt = w.mass / 418.4
+    tau2 = 0.0005
+    e.run_phase(0, tau2, s0=11, half=0, accel_mode=M.GRAD_F0)
+    vg = e.state()[1]
+    good = 0
+    sample = rng.choice(w.n, 100, replace=False)
+    for i in sample:
+        a = -o.gradient_atom(oracle_mod.GRAD_F0, int(i)) / mt[i]
+        vo, _, _ = o.cprime_one(int(i), w.v[i], a, tau2, 11, 0)
+        good += np.abs(vg[i] - vo).max() <= 2e-5 * max(np.abs(vo).max(), 1.0)
+    assert good >= 97, good
+    e.close()

@@ -251,3 +251,21 @@ def test_jump_lists_definition(oracle_mod, water648):
             sel = np.flatnonzero(ok & (r >= lo) & (r < hi) & extra)
             sel = sel[np.lexsort((sel, lin[sel]))]
             np.testing.assert_array_equal(o.list_of(kind, i), sel)
+
+
+def test_lazy_lists_equal_full_lists(oracle_mod, water648):
+    """Per-atom lists built on demand (the mode for systems whose O(N^2)
+    list build is out of reach) equal the lists built for all atoms, and a
+    per-atom C' phase gives the same result in both modes; stepping is
+    refused in lazy mode."""
+    p = dict(r_cut=9.0, r_split=5.0, h_switch=0.5, skin=0.2, skin_outer=0.3, ring_r=[5.0, 6.0])
+    full = oracle_mod.Oracle(water648, **p)
+    lazy = oracle_mod.Oracle(water648, lazy_lists=True, **p)
+    mt = water648.mass / 418.4
+    for i in (0, 1, 2, 300, 647):
+        for kind in (0, 1, 2, 3, 4):
+            np.testing.assert_array_equal(lazy.list_of(kind, i), full.list_of(kind, i))
+        a = -full.gradient_atom(oracle_mod.GRAD_F0, i) / mt[i]
+        assert np.array_equal(full.cprime_one(i, water648.v[i], a, 5e-4, 7, 0)[0],
+                              lazy.cprime_one(i, water648.v[i], a, 5e-4, 7, 0)[0])
+    assert lazy.L.or_step_jump(lazy.h, 1, 1.0) == -1
