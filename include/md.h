@@ -107,6 +107,9 @@ typedef struct {
     double skin_outer; /* outer candidate skin (A, >= skin); it also fixes the order of the jump lists */
     int n_rings;       /* 0: rings from r_mid; 1..4: rings with edges r_c-h, ring_r[0..n_rings-2], r_E */
     double ring_r[3];  /* interior ring edges (A), strictly increasing inside (r_c-h, r_E); MD_EINVAL otherwise */
+    int lj_long_mode;  /* 0: the long-range LJ part (1-chi) U_LJ jumps (BPS, J', Sec. 3.2);
+                        * 1: it is deterministic in F0, as in the paper's GPU runs (Sec. 4):
+                        * gradient modes 3 and 5 carry the whole LJ, mode 4 only (1-chi) Coulomb */
 } md_system;
 
 typedef struct {
@@ -157,6 +160,12 @@ int md_step_baoab(md_ctx* ctx, int64_t nsteps, double dt_fs);
 int md_step_baoab_respa(md_ctx* ctx, int64_t n_outer, double dt_inner_fs, int n_inner);
 int md_step_baoab_respa1(md_ctx* ctx, int64_t n_outer, double dt_inner_fs, int m_mid, int n_outer_ratio);
 int md_step_jump(md_ctx* ctx, int64_t nsteps, double dt_fs);
+
+/* The BJAOAJB splitting of Sec. 2.3 with the same jump mechanisms: B(dt/2)
+ * with F0, the jump processes alone over dt/2 (Coulomb pair jumps with no
+ * drift, then LJ bounces), A(dt/2) O(dt) A(dt/2), F0, LJ bounces, pair jumps,
+ * B(dt/2). Same streams and counters as md_step_jump. */
+int md_step_bjaoajb(md_ctx* ctx, int64_t nsteps, double dt_fs);
 int md_step_jump_respa(md_ctx* ctx, int64_t n_outer, double dt_inner_fs, int n_inner);
 int md_step_jump_respa1(md_ctx* ctx, int64_t n_outer, double dt_inner_fs, int m_mid, int n_outer_ratio);
 

@@ -42,7 +42,7 @@ class Params(C.Structure):
                 ("gamma", C.c_double), ("temperature", C.c_double), ("eps0", C.c_double),
                 ("skin", C.c_double), ("skin_outer", C.c_double), ("eps_mode", C.c_int),
                 ("n_rings", C.c_int), ("ring_r", C.c_double * 3), ("seed", C.c_uint32),
-                ("replica", C.c_uint32), ("lazy_lists", C.c_int)]
+                ("replica", C.c_uint32), ("lazy_lists", C.c_int), ("lj_long_mode", C.c_int)]
 
 
 _lib = None
@@ -79,7 +79,7 @@ def lib():
         L.or_rebuild.argtypes = [vp]
         L.or_cprime_one.argtypes = [vp, i, vp, vp, d, u32, i, vp, vp, vp]
         L.or_jprime_one.argtypes = [vp, i, vp, d, u32, i, vp, vp, vp]
-        for name in ("or_step_baoab", "or_step_jump"):
+        for name in ("or_step_baoab", "or_step_jump", "or_step_bjaoajb"):
             getattr(L, name).restype = i
             getattr(L, name).argtypes = [vp, i64, d]
         for name in ("or_step_baoab_respa", "or_step_jump_respa"):
@@ -131,7 +131,7 @@ class Oracle:
 
     def __init__(self, sys, r_cut=9.0, r_split=5.0, h_switch=0.5, r_mid=5.5, dsf_alpha=0.2,
                  gamma=1.0, temperature=300.0, eps0=0.1, skin=0.3, skin_outer=None, eps_mode=1,
-                 seed=0, replica=0, ring_r=None, lazy_lists=False):
+                 seed=0, replica=0, ring_r=None, lazy_lists=False, lj_long_mode=0):
         self.L = lib()
         self.n = sys.n
         if skin_outer is None:
@@ -141,7 +141,7 @@ class Oracle:
         self.params = Params(sys.box, r_cut, r_split, h_switch, r_mid, dsf_alpha, gamma,
                              temperature, eps0, skin, skin_outer, eps_mode, n_rings,
                              (C.c_double * 3)(*(rr + [0.0] * (3 - len(rr)))), seed, replica,
-                             1 if lazy_lists else 0)
+                             1 if lazy_lists else 0, int(lj_long_mode))
         a = lambda z, t: np.ascontiguousarray(z, dtype=t)
         self._keep = [a(sys.x, np.float64), a(sys.v, np.float64), a(sys.mass, np.float64),
                       a(sys.charge, np.float64), a(sys.type, np.int32), a(sys.lj_eps, np.float64),
@@ -252,6 +252,9 @@ class Oracle:
 
     def jump(self, nsteps, dt_fs=1.0):
         return self.L.or_step_jump(self.h, int(nsteps), float(dt_fs))
+
+    def bjaoajb(self, nsteps, dt_fs=1.0):
+        return self.L.or_step_bjaoajb(self.h, int(nsteps), float(dt_fs))
 
     def baoab_respa(self, nouter, dt_inner_fs=1.0, n_inner=2):
         return self.L.or_step_baoab_respa(self.h, int(nouter), float(dt_inner_fs), int(n_inner))

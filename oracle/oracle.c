@@ -667,9 +667,17 @@ static void nonbonded_atom(const or_sys* s, int i, int weight, double* g3, doubl
         double uc = OR_COULOMB * s->q[i] * s->q[j] * u_dsf(s, r);
         double duc = OR_COULOMB * s->q[i] * s->q[j] * du_dsf(s, r);
         double ul = u_ljsf(s, e, sg, r), dul = du_ljsf(s, e, sg, r);
-        double f = wdudr(s, uc + ul, duc + dul, r, weight) / r;
+        double f;
+        if (s->p.lj_long_mode && weight != W_FULL) {
+            /* LJ wholly deterministic: all of it in the short part, none in the long */
+            double flj = weight == W_SHORT ? dul : 0.0;
+            f = (wdudr(s, uc, duc, r, weight) + flj) / r;
+            elj += weight == W_SHORT ? ul : 0.0;
+        } else {
+            f = wdudr(s, uc + ul, duc + dul, r, weight) / r;
+            elj += wu(s, ul, r, weight);
+        }
         gx += f * d[0]; gy += f * d[1]; gz += f * d[2];
-        elj += wu(s, ul, r, weight);
         ec += wu(s, uc, r, weight);
     }
     g3[0] = gx; g3[1] = gy; g3[2] = gz;
@@ -963,6 +971,7 @@ static void cphase(or_sys* s, const double* a, double tau2, uint32_t s0, int hal
 
 static void jphase(or_sys* s, double tau2, uint32_t s0, int half)
 {
+    if (s->p.lj_long_mode) return;   /* the LJ long part is deterministic: no LJ jump mechanism */
     int64_t np = 0, na = 0;
     uint32_t err = 0;
 #pragma omp parallel for schedule(dynamic, 16) reduction(+:np,na) reduction(|:err)
@@ -1052,6 +1061,30 @@ int or_step_jump(or_sys* s, int64_t nsteps, double dt_fs)
         cphase(s, s->a0, 0.5 * tau, s0, 1);
         s->step++;
     }
+    check_finite(s);
+    return (int)s->err;
+}
+
+int or_step_bjaoajb(or_sys* s, int64_t nsteps, double dt_fs)
+{
+    if (s->lazy) return -1;
+    double tau = dt_fs * 1e-3;
+    double* zero = (double*)calloc(3 * (size_t)s->n, sizeof(double));
+    accel(s, 5, s->a0);
+    for (int64_t st = 0; st < nsteps; ++st) {
+        uint32_t s0 = (uint32_t)s->step;
+        kick(s, s->a0, 0.5 * tau);
+        cphase(s, zero, 0.5 * tau, s0, 0);
+        jphase(s, 0.5 * tau, s0, 0);
+        aoa(s, tau, s0);
+        maybe_rebuild(s);
+        accel(s, 5, s->a0);
+        jphase(s, 0.5 * tau, s0, 1);
+        cphase(s, zero, 0.5 * tau, s0, 1);
+        kick(s, s->a0, 0.5 * tau);
+        s->step++;
+    }
+    free(zero);
     check_finite(s);
     return (int)s->err;
 }

@@ -48,6 +48,9 @@ typedef struct {
     int lazy_lists;      /* nonzero: no list build at creation; the lists of one atom are built
                           * when a per-atom call needs them (for very large systems whose O(N^2)
                           * list build is out of reach); the or_step_* calls then return -1 */
+    int lj_long_mode;    /* 0: the long-range LJ part (1-chi) U_LJ is handled by BPS jumps (J');
+                          * 1: it is deterministic, in F0 (the paper's GPU runs): gradient modes
+                          * 3 and 5 carry the whole LJ, mode 4 only (1-chi) Coulomb, no J' */
 } or_params;
 
 typedef struct or_sys or_sys;
@@ -114,6 +117,9 @@ int or_step_baoab(or_sys* s, int64_t nsteps, double dt_fs);
 int or_step_baoab_respa(or_sys* s, int64_t nouter, double dt_inner_fs, int n_inner);
 int or_step_baoab_respa1(or_sys* s, int64_t nouter, double dt_inner_fs, int m_mid, int n_outer);
 int or_step_jump(or_sys* s, int64_t nsteps, double dt_fs);
+/* BJAOAJB (Sec. 2.3): B(dt/2) with F0, then the jump processes alone over
+ * dt/2 (C' with zero drift, then J'), A O A, F0, J', C' (zero drift), B. */
+int or_step_bjaoajb(or_sys* s, int64_t nsteps, double dt_fs);
 int or_step_jump_respa(or_sys* s, int64_t nouter, double dt_inner_fs, int n_inner);
 int or_step_jump_respa1(or_sys* s, int64_t nouter, double dt_inner_fs, int m_mid, int n_outer);
 

@@ -25,7 +25,7 @@ ERRORS = {-1: "MD_EINVAL", -2: "MD_ECUDA", -3: "MD_EOVERFLOW", -4: "MD_EBOUND",
 
 # exported symbols of include/md.h
 SYMBOLS = ["md_init", "md_set_system", "md_set_state", "md_step_baoab", "md_step_baoab_respa",
-           "md_step_baoab_respa1", "md_step_jump", "md_step_jump_respa", "md_step_jump_respa1",
+           "md_step_baoab_respa1", "md_step_jump", "md_step_bjaoajb", "md_step_jump_respa", "md_step_jump_respa1",
            "md_observables", "md_get_state", "md_gradient", "md_run_phase", "md_get_list",
            "md_get_events", "md_profile", "md_nb_gradient_noalloc", "md_finalize", "md_last_error"]
 
@@ -55,7 +55,7 @@ class MdSystem(C.Structure):
                 ("r_mid", C.c_double), ("dsf_alpha", C.c_double), ("gamma", C.c_double),
                 ("temperature", C.c_double), ("eps0", C.c_double), ("eps_mode", C.c_int),
                 ("skin", C.c_double), ("skin_outer", C.c_double),
-                ("n_rings", C.c_int), ("ring_r", C.c_double * 3)]
+                ("n_rings", C.c_int), ("ring_r", C.c_double * 3), ("lj_long_mode", C.c_int)]
 
 
 class MdObs(C.Structure):
@@ -84,7 +84,7 @@ def load_library(path: str = LIB_PATH):
     L.md_init.argtypes = [P(vp), P(MdConfig)]
     L.md_set_system.argtypes = [vp, i, P(MdSystem)]
     L.md_set_state.argtypes = [vp, i, vp, vp, vp, vp, vp, i64]
-    for n in ("md_step_baoab", "md_step_jump"):
+    for n in ("md_step_baoab", "md_step_jump", "md_step_bjaoajb"):
         getattr(L, n).argtypes = [vp, i64, d]
     for n in ("md_step_baoab_respa", "md_step_jump_respa"):
         getattr(L, n).argtypes = [vp, i64, d, i]
@@ -121,7 +121,7 @@ def _current_stream():
 
 
 DEFAULTS = dict(r_cut=9.0, r_split=5.0, h_switch=0.5, r_mid=5.5, dsf_alpha=0.2, gamma=1.0,
-                temperature=300.0, eps0=0.1, eps_mode=1, skin=0.3, skin_outer=None, ring_r=None)
+                temperature=300.0, eps0=0.1, eps_mode=1, skin=0.3, skin_outer=None, ring_r=None, lj_long_mode=0)
 
 
 KIND_RING0, KIND_LJ = 0, 4
@@ -189,6 +189,7 @@ class Engine:
             s.n_rings = len(rr) + 1
             for k, z in enumerate(rr):
                 s.ring_r[k] = z
+        s.lj_long_mode = int(p["lj_long_mode"])
         self._ck(self.L.md_set_system(self.h, replica, C.byref(s)))
         self.n[replica] = sys.n
 
@@ -202,6 +203,9 @@ class Engine:
 
     def jump(self, nsteps, dt_fs=1.0):
         return self._ck(self.L.md_step_jump(self.h, int(nsteps), float(dt_fs)))
+
+    def bjaoajb(self, nsteps, dt_fs=1.0):
+        return self._ck(self.L.md_step_bjaoajb(self.h, int(nsteps), float(dt_fs)))
 
     def baoab_respa(self, n_outer, dt_inner_fs=1.0, n_inner=2):
         return self._ck(self.L.md_step_baoab_respa(self.h, int(n_outer), float(dt_inner_fs), int(n_inner)))

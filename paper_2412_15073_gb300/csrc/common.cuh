@@ -62,6 +62,7 @@ struct RepParams {
     double edge[MAX_RINGS + 1];// ring edges: sw = edge[0] < ... < edge[nr] = R
     float edgef[MAX_RINGS + 1];
     int nr, rings_on, lj_on, eps_mode;
+    int lj_long, lj_jump;      // LJ long part deterministic in F0; LJ bounces (J') on
     double skin, skin_o;
     // DSF: u(r) = erfc(a r)/r - eR + fR (r - R); u'(r) = -erfc(a r)/r^2 - k exp(-a^2 r^2)/r + fR
     double alpha, eR, fR, kexp;     // kexp = 2 a / sqrt(pi)

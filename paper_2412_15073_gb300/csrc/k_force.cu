@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(256) k_force(Dev d, int lk, double* out, int a
                 du = C * qq * duc;
             }
             const LJPair& lj = P.lj[ti * MAX_TYPES + d.type[j]];
-            if (lj.on) {
+            if (lj.on && !(W == W_LONG && P.lj_long)) {    // deterministic LJ long part: not in the long weight
                 T ul, dul;
                 ljsf<T>(P, lj, rr, rinv, ul, dul);
                 u += ul;
@@ -203,6 +203,35 @@ __global__ void __launch_bounds__(256) k_force(Dev d, int lk, double* out, int a
                 f = W == W_SHORT ? dc * u + c * du : -dc * u + (T(1) - c) * du;
             }
             acc.add(f * rinv, dx, dy, dz);
+        }
+        if (W == W_SHORT && P.lj_long) {
+            // the (1 - chi) LJ part over the LJ list: with the chi part above,
+            // the whole LJ is deterministic (the paper's GPU runs)
+            const uint32_t* lrow = d.list[L_LJ] + (size_t)i * d.lcap[L_LJ];
+            const int nl = min(d.lcnt[L_LJ][i], d.lcap[L_LJ]);
+            const T R2 = T(P.R) * T(P.R);
+            for (int k = sub; k < nl; k += TPA) {
+                const int j = int(lrow[k]);
+                T dx, dy, dz;
+                if (sizeof(T) == 4) {
+                    float fx, fy, fz;
+                    sdisp(pi, d.pos[j], sc, P.sclf_lo, fx, fy, fz);
+                    dx = T(fx); dy = T(fy); dz = T(fz);
+                } else {
+                    const double3 xj = ld3(d.x, j);
+                    dx = T(mimg(xi.x - xj.x, P)); dy = T(mimg(xi.y - xj.y, P)); dz = T(mimg(xi.z - xj.z, P));
+                }
+                const T r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 >= R2 || r2 <= sw2) continue;
+                const LJPair& lj = P.lj[ti * MAX_TYPES + d.type[j]];
+                if (!lj.on) continue;
+                const T rr = d_sqrt(r2);
+                const T rinv = T(1) / rr;
+                T ul, dul, c, dc;
+                ljsf<T>(P, lj, rr, rinv, ul, dul);
+                chi_and_slope<T>(rr, sw, h, c, dc);
+                acc.add((-dc * ul + (T(1) - c) * dul) * rinv, dx, dy, dz);
+            }
         }
     }
     if (TPA > 1) acc.combine_shfl(TPA);

@@ -557,7 +557,7 @@ __global__ void __launch_bounds__(128, MINB) k_cphase_f(Dev d, const __grid_cons
         const uint32_t sb = s_abs ? 0u : uint32_t(d.step_base[r]);
         double v[3] = {d.v[3 * i], d.v[3 * i + 1], d.v[3 * i + 2]};
         const double ad[3] = {a ? a[3 * i] : 0.0, a ? a[3 * i + 1] : 0.0, a ? a[3 * i + 2] : 0.0};
-        if ((jmode & 2) && P.lj_on) jprime<float>(d, P, i, il, v, tau2, sb + s_off, half, tl, err);
+        if ((jmode & 2) && P.lj_jump) jprime<float>(d, P, i, il, v, tau2, sb + s_off, half, tl, err);
         for (int pass = 0; pass < npass; ++pass) {
             const uint32_t s0 = sb + (pass ? s_off2 : s_off);
             const int hp = pass ? 0 : half;
@@ -580,7 +580,7 @@ __global__ void __launch_bounds__(128, MINB) k_cphase_f(Dev d, const __grid_cons
             v[1] = fma(tau2, ad[1], v[1]) + double(jv.y);
             v[2] = fma(tau2, ad[2], v[2]) + double(jv.z);
         }
-        if (jmode & 1 && P.lj_on)
+        if (jmode & 1 && P.lj_jump)
             jprime<float>(d, P, i, il, v, tau2, sb + (jmode == 3 ? s_off2 : s_off), jmode == 3 ? 0 : half, tl, err);
         d.v[3 * i] = v[0]; d.v[3 * i + 1] = v[1]; d.v[3 * i + 2] = v[2];
         if (err) atomicOr(&d.err[r], err);
@@ -607,7 +607,7 @@ __global__ void __launch_bounds__(128) k_jphase_f(Dev d, double tau2, uint32_t s
     const RepParams& P = d.P[r];
     Tally tl;
     uint32_t err = 0;
-    if (live && P.lj_on) {
+    if (live && P.lj_jump) {
         const uint32_t s0 = (s_abs ? 0u : uint32_t(d.step_base[r])) + s_off;
         double v[3] = {d.v[3 * i], d.v[3 * i + 1], d.v[3 * i + 2]};
         jprime<float>(d, P, i, i - P.atom_off, v, tau2, s0, half, tl, err);
@@ -640,7 +640,7 @@ __global__ void __launch_bounds__(128) k_vphase(Dev d, const double* a, double t
         double acc[3] = {0, 0, 0};
         if (a) { acc[0] = a[3 * i]; acc[1] = a[3 * i + 1]; acc[2] = a[3 * i + 2]; }
         const bool c_on = doC && P.rings_on;
-        const bool j_on = doJ && P.lj_on;
+        const bool j_on = doJ && P.lj_jump;
         for (int step = 0; step < 2; ++step) {
             const bool isC = (order == 0) ? step == 0 : step == 1;
             if (isC) {

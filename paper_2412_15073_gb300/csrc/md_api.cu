@@ -204,20 +204,30 @@ void free_device(md_ctx* ctx)
     ctx->on_device = false;
 }
 
-int lists_needed(int family)
+// does some replica keep the LJ long part deterministic (its short gradient
+// then also runs over the LJ list)?
+bool any_lj_long(const md_ctx* ctx)
+{
+    for (const RepParams& P : ctx->hp)
+        if (P.lj_long) return true;
+    return false;
+}
+
+int lists_needed(const md_ctx* ctx, int family)
 {
     // 0 BAOAB / BAOAB-RESPA, 1 BAOAB-RESPA1, 2 JUMP family
+    const int lj = any_lj_long(ctx) ? 1 << L_LJ : 0;
     if (family == 0) return 1 << L_FULL;
-    if (family == 1) return (1 << L_FULL) | (1 << L_SHORT);
+    if (family == 1) return (1 << L_FULL) | (1 << L_SHORT) | lj;
     int k = (1 << L_SHORT) | (1 << L_LJ);
     for (int y = 0; y < MAX_RINGS; ++y) k |= 1 << (L_R0 + y);
     return k;
 }
 
-int mode_list(int mode)
+int mode_list(const md_ctx* ctx, int mode)
 {
     if (mode == 1) return 0;
-    if (mode == 3 || mode == 5) return 1 << L_SHORT;
+    if (mode == 3 || mode == 5) return (1 << L_SHORT) | (any_lj_long(ctx) ? 1 << L_LJ : 0);
     return 1 << L_FULL;
 }
 
@@ -323,6 +333,8 @@ RepParams make_params(const md_ctx* ctx, const RepHost& h, int r, int atom_off, 
     for (double e : h.lj_eps) any_lj |= e > 0.0;
     P.rings_on = (P.sw < P.R) && qmax > 0.0;
     P.lj_on = (P.sw < P.R) && any_lj;
+    P.lj_long = s.lj_long_mode != 0;
+    P.lj_jump = P.lj_on && !P.lj_long;
     P.eps_mode = s.eps_mode;
     P.skin = s.skin; P.skin_o = skin_o;
     HostPair hpair{s.r_cut, P.sw, s.h_switch, s.dsf_alpha};
@@ -405,6 +417,8 @@ int check_sys(md_ctx* ctx, const md_system* s)
         !(s->dsf_alpha >= 0) || !(s->gamma >= 0) || !(s->temperature > 0) || !(s->eps0 > 0) ||
         (s->eps_mode != 0 && s->eps_mode != 1))
         FAIL(MD_EINVAL, "md_set_system: invalid cutoff, switch, thermostat or jump parameters");
+    if (s->lj_long_mode != 0 && s->lj_long_mode != 1)
+        FAIL(MD_EINVAL, "md_set_system: lj_long_mode must be 0 or 1");
     if (s->n_rings < 0 || s->n_rings > MAX_RINGS)
         FAIL(MD_EINVAL, "md_set_system: n_rings must be in [0, %d]", MAX_RINGS);
     for (int y = 1; y < s->n_rings; ++y) {
@@ -969,7 +983,7 @@ int prepare(md_ctx* ctx, int family, double dt_fs)
     if (!(dt_fs > 0) || !std::isfinite(dt_fs)) FAIL(MD_EINVAL, "time step must be positive");
     int rc = commit(ctx);
     if (rc) return rc;
-    if ((rc = ensure_kinds(ctx, lists_needed(family)))) return rc;
+    if ((rc = ensure_kinds(ctx, lists_needed(ctx, family)))) return rc;
     CK(cudaMemsetAsync(ctx->d.flags, 0, sizeof(int) * 2 * ctx->d.R, ctx->s));
     return MD_OK;
 }
@@ -1237,6 +1251,29 @@ int md_step_jump(md_ctx* ctx, int64_t nsteps, double dt_fs)
     });
 }
 
+int md_step_bjaoajb(md_ctx* ctx, int64_t nsteps, double dt_fs)
+{
+    int rc = prepare(ctx, 2, dt_fs);
+    if (rc) return rc;
+    if (nsteps < 0) FAIL(MD_EINVAL, "nsteps < 0");
+    Dev& d = ctx->d;
+    const double tau = dt_fs * 1e-3;
+    if ((rc = set_stepc(ctx, tau))) return rc;
+    force(ctx, 5, d.a0);
+    // B J A O A [F0] J B: the velocity phases run the jump processes alone (no drift)
+    return run_units(ctx, 5, tau, 1, nsteps, [&](long long u0, long long n) {
+        for (long long k = u0; k < u0 + n; ++k) {
+            kick(ctx, d.a0, 0.5 * tau);
+            vphase(ctx, nullptr, 0.5 * tau, uint32_t(k), 0, 0);
+            aoa(ctx, tau, uint32_t(k), 1);
+            rebuild_step(ctx);
+            force(ctx, 5, d.a0);
+            vphase(ctx, nullptr, 0.5 * tau, uint32_t(k), 1, 1);
+            kick(ctx, d.a0, 0.5 * tau);
+        }
+    });
+}
+
 int md_step_baoab_respa(md_ctx* ctx, int64_t n_outer, double dt_inner_fs, int n_inner)
 {
     int rc = prepare(ctx, 0, dt_inner_fs);
@@ -1385,7 +1422,7 @@ int md_gradient(md_ctx* ctx, int replica, int mode, double* host_grad)
     int rc = commit(ctx);
     if (rc) return rc;
     if (replica < 0 || replica >= ctx->d.R) FAIL(MD_EINVAL, "replica %d out of range", replica);
-    if ((rc = ensure_kinds(ctx, mode_list(mode)))) return rc;
+    if ((rc = ensure_kinds(ctx, mode_list(ctx, mode)))) return rc;
     Dev& d = ctx->d;
     launch_force(d, mode, d.gout, 1, ctx->fp64, (mode == 1 || ctx->fp64) ? 1 : tpa_for(ctx, mode), ctx->s);
     CK(cudaGetLastError());
@@ -1404,7 +1441,7 @@ int md_run_phase(md_ctx* ctx, int phase, double tau2_ps, int64_t s0, int half, i
     if (rc) return rc;
     int rings = 0;
     for (int y = 0; y < MAX_RINGS; ++y) rings |= 1 << (L_R0 + y);
-    const int need = (phase == 0 ? rings | mode_list(accel_mode) : (1 << L_LJ));
+    const int need = (phase == 0 ? rings | mode_list(ctx, accel_mode) : (1 << L_LJ));
     if ((rc = ensure_kinds(ctx, need))) return rc;
     Dev& d = ctx->d;
     if (phase == 0) force(ctx, accel_mode, d.a0);

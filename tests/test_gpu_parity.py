@@ -399,3 +399,48 @@ def test_million_atom_heterogeneous_sampled(M, oracle_mod):
         good += np.abs(vg[i] - vo).max() <= 2e-5 * max(np.abs(vo).max(), 1.0)
     assert good >= 97, good
     e.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-5)])
+def test_lj_long_mode_gradients(M, oracle_mod, water648, precision, tol):
+    """The paper's GPU variant (LJ long part deterministic in F0): gradient
+    modes 3, 4 and 5 against the oracle's, measured against the total force."""
+    w = water648.copy()
+    w.x = (w.x + np.random.default_rng(3).normal(scale=0.05, size=w.x.shape)) % w.box
+    e, o = make(M, oracle_mod, w, precision, lj_long_mode=1)
+    total, _ = o.gradient(0)
+    for mode in (0, 3, 4, 5):
+        ref, _ = o.gradient(mode)
+        err = force_err(e.gradient(mode), ref, total if mode in (3, 4) else None)
+        assert err <= tol, (mode, err)
+
+
+@pytest.mark.parametrize("how,kw", [("jump", dict(lj_long_mode=1)), ("bjaoajb", {}),
+                                    ("bjaoajb", dict(lj_long_mode=1))])
+def test_variant_trajectories_fp64(M, oracle_mod, water648, how, kw):
+    """JUMP with the deterministic LJ long part, and the BJAOAJB splitting,
+    follow the oracle in FP64: identical accepted-jump events and positions
+    within 1e-6 A over 60 steps; no LJ bounces when the LJ long part is
+    deterministic."""
+    e, o = make(M, oracle_mod, water648, 0, seed=9, **kw)
+    o.events_enable(1 << 22)
+    getattr(e, how)(60)
+    getattr(o, how)(60)
+    assert np.array_equal(sorted_events(e.events()), sorted_events(o.events()))
+    assert pos_err(e.state()[0], o.state()[0], water648.box) < 1e-6
+    ob = e.observables()
+    assert ob["jump_accepts"] == o.counters()[1] > 0
+    if kw.get("lj_long_mode"):
+        assert ob["bps_proposals"] == 0
+
+
+def test_bjaoajb_graphs_and_mixed(M, oracle_mod, water648):
+    """Mixed-mode BJAOAJB: graph replays equal plain launches bit for bit."""
+    runs = []
+    for graphs in (True, False):
+        e = M.Engine(precision=1, seed=23, graphs=graphs)
+        e.set_system(0, water648, **PARAMS)
+        e.bjaoajb(40)
+        runs.append(e.state()[:2])
+        e.close()
+    assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])

@@ -306,3 +306,54 @@ def test_event_log_and_rate_bound_hold_on_water(oracle_mod, water648):
     per_atom_step = c[0] / (648 * 100)
     assert 20 < per_atom_step < 120
     assert 0.05 < c[1] / c[0] < 0.6
+
+
+def test_lj_long_mode_moves_the_lj_long_part_into_f0(oracle_mod, water648):
+    """With the LJ long part deterministic (the paper's GPU runs), the short
+    gradient gains exactly what the long one loses, the total is unchanged,
+    the moved part is the (1-chi) LJ gradient alone, and JUMP proposes no
+    LJ bounces."""
+    w = water648.copy()
+    w.x = (w.x + np.random.default_rng(2).normal(scale=0.05, size=w.x.shape)) % w.box
+    p = dict(r_cut=9.0, r_split=5.0, h_switch=0.5, skin=0.2, skin_outer=0.3)
+    a = oracle_mod.Oracle(w, **p)
+    b = oracle_mod.Oracle(w, lj_long_mode=1, **p)
+    g = {(o, m): o.gradient(m)[0] for o in (a, b) for m in (0, 3, 4, 5)}
+    assert np.allclose(g[(a, 0)], g[(b, 0)], rtol=0, atol=1e-12)
+    moved = g[(b, 3)] - g[(a, 3)]
+    assert np.allclose(moved, g[(a, 4)] - g[(b, 4)], rtol=0, atol=1e-10)
+    assert np.allclose(g[(b, 5)] - g[(a, 5)], moved, rtol=0, atol=1e-10)
+    # the moved part: (1-chi) LJ summed over O-O pairs (water has LJ on O only)
+    oxy = np.flatnonzero(w.type == 0)
+    i = int(oxy[3])
+    ref = np.zeros(3)
+    for j in oxy:
+        if j == i or j // 3 == i // 3:
+            continue
+        d = w.x[i] - w.x[j]
+        d -= w.box * np.round(d / w.box)
+        r = np.linalg.norm(d)
+        if r < 9.0:
+            ref += a.pair_dudr(0, 0, 0.0, r, 2) * d / r
+    assert np.allclose(moved[i], ref, rtol=1e-10, atol=1e-12)
+    b.jump(5)
+    assert b.counters()[2] == 0 and b.counters()[0] > 0
+
+
+def test_bjaoajb_is_baoab_without_jumps_and_keeps_temperature(oracle_mod, water648):
+    """BJAOAJB with empty jump ranges is BAOAB on F0 = full force bit for bit;
+    with jumps it keeps the temperature of the water box near 300 K."""
+    p = dict(r_cut=9.0, r_split=9.6, h_switch=0.5, skin=0.2, skin_outer=0.3)
+    a = oracle_mod.Oracle(water648, seed=4, **p)
+    b = oracle_mod.Oracle(water648, seed=4, **p)
+    a.bjaoajb(20)
+    b.baoab(20)
+    xa, va, _, _ = a.state()
+    xb, vb, _, _ = b.state()
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+    c = oracle_mod.Oracle(water648, seed=4, r_cut=9.0, r_split=5.0, h_switch=0.5, skin=0.2, skin_outer=0.3)
+    assert c.bjaoajb(60) == 0
+    assert c.counters()[1] > 0
+    v = c.state()[1]
+    T = (water648.mass[:, None] * v * v).sum() / 418.4 / (3 * water648.n * 0.0019872042586)
+    assert 240 < T < 360, T
