@@ -198,6 +198,47 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+class Ranks:
+    """Ranks of a multi-GPU run (one process per GPU, RANK / WORLD_SIZE /
+    LOCAL_RANK from the launcher). Each rank advances its own replica: there is
+    no data-path collective, only a barrier around the timed region and the
+    maximum of the measured times over ranks."""
+
+    def __init__(self, backend="nccl"):
+        import torch
+        self.torch = torch
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.cuda = backend == "nccl"
+        self.dist = None
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend)
+            self.dist = dist
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+        if self.cuda:
+            self.torch.cuda.synchronize()
+
+    def max(self, x: float) -> float:
+        if self.dist is None:
+            return x
+        t = self.torch.tensor([x], dtype=self.torch.float64, device="cuda" if self.cuda else "cpu")
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def seed(self, base: int) -> int:
+        """Philox seed of this rank's replica."""
+        return base + 1000 * self.rank
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.destroy_process_group()
+
+
 def timed(engine, fn, steps, stream):
     import torch
     torch.cuda.synchronize()
@@ -256,40 +297,24 @@ def main():
     import paper_2412_15073_gb300 as M
     from paper_2412_15073_gb300 import systems
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    ranks = Ranks("nccl")
+    world, rank, local = ranks.world, ranks.rank, ranks.local
+    barrier, max_over_ranks = ranks.barrier, ranks.max
 
     stream = torch.cuda.current_stream()
     w = systems.water_box(N_MOL, box=BOX, seed=0)
     n = w.n
     if args.equil > 0:
         # relax the lattice start at strong friction so both integrators start at 300 K
-        eq = M.Engine(precision=M.MD_MIXED, seed=99 + 1000 * rank, device=local, stream=stream.cuda_stream)
+        eq = M.Engine(precision=M.MD_MIXED, seed=ranks.seed(99), device=local, stream=stream.cuda_stream)
         eq.set_system(0, w, **(PARAMS | {"gamma": 20.0}))
         eq.baoab(args.equil)
         w.x, w.v = eq.state()[0], eq.state()[1]
         eq.close()
 
     def engine(seed, params):
-        e = M.Engine(precision=M.MD_MIXED, seed=seed + 1000 * rank, device=local, stream=stream.cuda_stream)
+        e = M.Engine(precision=M.MD_MIXED, seed=ranks.seed(seed), device=local, stream=stream.cuda_stream)
         e.set_system(0, w, **params)
         return e
 
@@ -444,8 +469,7 @@ def main():
         print(json.dumps(out), flush=True)
     for e in (ej, eb):
         e.close()
-    if dist is not None:
-        dist.destroy_process_group()
+    ranks.close()
 
 
 if __name__ == "__main__":
