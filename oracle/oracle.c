@@ -17,7 +17,7 @@
  *   electrostatics: damped shifted force (DSF) Coulomb in place of Ewald;
  *   switch chi: quintic smoothstep on [r_c-h, r_c];
  *   rate bounds: numerical max of |d/dr (1-chi)U| on a grid, rounded up;
- *   acceptance p = lambda / bar-lambda_Y with the sqrt(beta) the listing omits;
+ *   acceptance p = lambda / bar-lambda_Y, with the sqrt(beta) that Algorithm 4 omits;
  *   adaptive eps: eps = eps0 |g| in the rate, bound and kernel;
  *   the jump partner J is drawn before eta is formed.
  */
