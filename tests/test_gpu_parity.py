@@ -478,3 +478,55 @@ def test_plain_648_atom_workload_1000_steps_fp64(M, oracle_mod, how):
     if how == "jump":
         for got, ref in ((ob["jump_proposals"], c[0]), (ob["jump_accepts"], c[1])):
             assert abs(got / ref - 1) < 0.02, (got, ref)
+
+
+def _rdf_oo(frames, box, rmax=9.0, dr=0.05):
+    from scipy.spatial import cKDTree
+    edges = np.arange(0.0, rmax + dr, dr)
+    h = np.zeros(len(edges) - 1)
+    n_o = frames[0].shape[0] // 3
+    for x in frames:
+        o = np.mod(x[::3], box)
+        p = cKDTree(o, boxsize=box).query_pairs(rmax, output_type="ndarray")
+        d = o[p[:, 0]] - o[p[:, 1]]
+        d -= box * np.round(d / box)
+        h += np.histogram(np.sqrt((d * d).sum(1)), edges)[0]
+    shell = 4.0 / 3.0 * np.pi * (edges[1:] ** 3 - edges[:-1] ** 3)
+    ideal = shell * n_o / box ** 3 * n_o / 2 * len(frames)
+    return h / ideal, dr, rmax
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("how", ["baoab", "jump"])
+def test_mixed_precision_long_run_observables(M, how):
+    """24,000-atom water, 3000 steps from one equilibrated state in mixed
+    precision and in FP64 (the FP64 mode follows the oracle event for event;
+    the oracle itself cannot run this long at this size): mean temperature
+    within 0.5 %, O-O radial distribution L1 distance <= 1e-2, and (BAOAB)
+    oxygen self-diffusion within 5 %."""
+    import bench
+    from paper_2412_15073_gb300 import systems
+    w = systems.water_box(8000, box=62.1, seed=0)
+    p = dict(PARAMS, skin=0.5, skin_outer=1.5)
+    eq = M.Engine(precision=1, seed=31)
+    eq.set_system(0, w, **(p | {"gamma": 20.0}))
+    eq.baoab(500)
+    w.x, w.v = eq.state()[0], eq.state()[1]
+    eq.close()
+    res = {}
+    for prec in (0, 1):
+        e = M.Engine(precision=prec, seed=32)
+        e.set_system(0, w, **p)
+        fn = getattr(e, how)
+        T, frames = [], []
+        D = bench.diffusion(e, lambda k: (fn(k), T.append(e.observables()["temperature"]),
+                                          frames.append(e.state()[0])), 3000, 150, w.box, 1.0)
+        res[prec] = (np.mean(T), _rdf_oo(frames[::2], w.box), D)
+        e.close()
+    (T64, (g64, dr, rmax), D64), (T32, (g32, _, _), D32) = res[0], res[1]
+    l1 = np.abs(g32 - g64).sum() * dr / rmax
+    print(f"{how}: T {T32:.2f} vs {T64:.2f} K, RDF L1 {l1:.2e}, D {D32:.3f} vs {D64:.3f}")
+    assert abs(T32 / T64 - 1) < 0.005
+    assert l1 <= 1e-2
+    if how == "baoab":
+        assert abs(D32 / D64 - 1) < 0.05
