@@ -42,7 +42,8 @@ class Params(C.Structure):
                 ("gamma", C.c_double), ("temperature", C.c_double), ("eps0", C.c_double),
                 ("skin", C.c_double), ("skin_outer", C.c_double), ("eps_mode", C.c_int),
                 ("n_rings", C.c_int), ("ring_r", C.c_double * 3), ("seed", C.c_uint32),
-                ("replica", C.c_uint32), ("lazy_lists", C.c_int), ("lj_long_mode", C.c_int)]
+                ("replica", C.c_uint32), ("lazy_lists", C.c_int), ("lj_long_mode", C.c_int),
+                ("coulomb_mode", C.c_int), ("pme_order", C.c_int), ("pme_spacing", C.c_double)]
 
 
 _lib = None
@@ -60,6 +61,8 @@ def lib():
         L.or_create.argtypes = [i, P(Params), vp, vp, vp, vp, vp, i, vp, vp, i, vp, vp, vp,
                                 i, vp, vp, vp, i, vp]
         L.or_destroy.argtypes = [vp]
+        L.or_ewald_recip_plain.argtypes = [vp, i, vp, vp]
+        L.or_ewald_recip_pme.argtypes = [vp, vp, vp, vp]
         L.or_set_threads.argtypes = [i]
         L.or_get_threads.restype = i
         L.or_get_state.argtypes = [vp, vp, vp, vp, vp, vp]
@@ -131,7 +134,8 @@ class Oracle:
 
     def __init__(self, sys, r_cut=9.0, r_split=5.0, h_switch=0.5, r_mid=5.5, dsf_alpha=0.2,
                  gamma=1.0, temperature=300.0, eps0=0.1, skin=0.3, skin_outer=None, eps_mode=1,
-                 seed=0, replica=0, ring_r=None, lazy_lists=False, lj_long_mode=0):
+                 seed=0, replica=0, ring_r=None, lazy_lists=False, lj_long_mode=0,
+                 coulomb_mode=0, pme_order=6, pme_spacing=0.8):
         self.L = lib()
         self.n = sys.n
         if skin_outer is None:
@@ -141,7 +145,8 @@ class Oracle:
         self.params = Params(sys.box, r_cut, r_split, h_switch, r_mid, dsf_alpha, gamma,
                              temperature, eps0, skin, skin_outer, eps_mode, n_rings,
                              (C.c_double * 3)(*(rr + [0.0] * (3 - len(rr)))), seed, replica,
-                             1 if lazy_lists else 0, int(lj_long_mode))
+                             1 if lazy_lists else 0, int(lj_long_mode), int(coulomb_mode), int(pme_order),
+                             float(pme_spacing))
         a = lambda z, t: np.ascontiguousarray(z, dtype=t)
         self._keep = [a(sys.x, np.float64), a(sys.v, np.float64), a(sys.mass, np.float64),
                       a(sys.charge, np.float64), a(sys.type, np.int32), a(sys.lj_eps, np.float64),
@@ -252,6 +257,21 @@ class Oracle:
 
     def jump(self, nsteps, dt_fs=1.0):
         return self.L.or_step_jump(self.h, int(nsteps), float(dt_fs))
+
+    def ewald_recip_plain(self, kmax):
+        """(gradient n x 3, energy) of the reciprocal part by the plain Ewald sum (+ self, exclusions)"""
+        g = np.zeros((self.n, 3))
+        e = C.c_double(0.0)
+        self.L.or_ewald_recip_plain(self.h, int(kmax), _p(g), C.byref(e))
+        return g, e.value
+
+    def ewald_recip_pme(self):
+        """(gradient n x 3, energy, K) of the reciprocal part by smooth PME (+ self, exclusions)"""
+        g = np.zeros((self.n, 3))
+        e = C.c_double(0.0)
+        K = C.c_int(0)
+        self.L.or_ewald_recip_pme(self.h, _p(g), C.byref(e), C.byref(K))
+        return g, e.value, K.value
 
     def bjaoajb(self, nsteps, dt_fs=1.0):
         return self.L.or_step_bjaoajb(self.h, int(nsteps), float(dt_fs))

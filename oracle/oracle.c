@@ -250,6 +250,24 @@ static double du_dsf(const or_sys* s, double r)
     return -fr + fR;
 }
 
+/* real-space Coulomb per unit C q_i q_j: DSF, or the Ewald erfc(alpha r)/r,
+ * both zero from r_cut on */
+static double u_coul(const or_sys* s, double r)
+{
+    if (s->p.coulomb_mode == 1) return r < s->p.r_cut ? erfc(s->p.dsf_alpha * r) / r : 0.0;
+    return u_dsf(s, r);
+}
+
+static double du_coul(const or_sys* s, double r)
+{
+    if (s->p.coulomb_mode == 1) {
+        if (r >= s->p.r_cut) return 0.0;
+        double a = s->p.dsf_alpha;
+        return -(erfc(a * r) / r + 2.0 * a / sqrt(OR_PI) * exp(-a * a * r * r)) / r;
+    }
+    return du_dsf(s, r);
+}
+
 static double u_lj(double e, double sg, double r)
 {
     double s6 = pow(sg / r, 6.0);
@@ -294,15 +312,15 @@ static double wu(const or_sys* s, double u, double r, int weight)
 double or_pair_dudr(const or_sys* s, int ti, int tj, double qiqj, double r, int weight)
 {
     double e = s->eps[ti * s->ntypes + tj], sg = s->sig[ti * s->ntypes + tj];
-    double u = OR_COULOMB * qiqj * u_dsf(s, r) + u_ljsf(s, e, sg, r);
-    double du = OR_COULOMB * qiqj * du_dsf(s, r) + du_ljsf(s, e, sg, r);
+    double u = OR_COULOMB * qiqj * u_coul(s, r) + u_ljsf(s, e, sg, r);
+    double du = OR_COULOMB * qiqj * du_coul(s, r) + du_ljsf(s, e, sg, r);
     return wdudr(s, u, du, r, weight);
 }
 
 double or_pair_u(const or_sys* s, int ti, int tj, double qiqj, double r, int weight)
 {
     double e = s->eps[ti * s->ntypes + tj], sg = s->sig[ti * s->ntypes + tj];
-    double u = OR_COULOMB * qiqj * u_dsf(s, r) + u_ljsf(s, e, sg, r);
+    double u = OR_COULOMB * qiqj * u_coul(s, r) + u_ljsf(s, e, sg, r);
     return wu(s, u, r, weight);
 }
 
@@ -310,7 +328,7 @@ double or_pair_u(const or_sys* s, int ti, int tj, double qiqj, double r, int wei
  * C q_i q_j (the part handled by the C' jumps) */
 static double coul_long_dudr(const or_sys* s, double r)
 {
-    return -dchi(s, r) * u_dsf(s, r) + (1.0 - chi(s, r)) * du_dsf(s, r);
+    return -dchi(s, r) * u_coul(s, r) + (1.0 - chi(s, r)) * du_coul(s, r);
 }
 
 /* radial derivative of the long-range LJ part (1-chi) U_LJ (J' jumps) */
@@ -664,8 +682,8 @@ static void nonbonded_atom(const or_sys* s, int i, int weight, double* g3, doubl
         double r = sqrt(r2);
         int ti = s->type[i], tj = s->type[j];
         double e = s->eps[ti * s->ntypes + tj], sg = s->sig[ti * s->ntypes + tj];
-        double uc = OR_COULOMB * s->q[i] * s->q[j] * u_dsf(s, r);
-        double duc = OR_COULOMB * s->q[i] * s->q[j] * du_dsf(s, r);
+        double uc = OR_COULOMB * s->q[i] * s->q[j] * u_coul(s, r);
+        double duc = OR_COULOMB * s->q[i] * s->q[j] * du_coul(s, r);
         double ul = u_ljsf(s, e, sg, r), dul = du_ljsf(s, e, sg, r);
         double f;
         if (s->p.lj_long_mode && weight != W_FULL) {
@@ -685,6 +703,230 @@ static void nonbonded_atom(const or_sys* s, int i, int weight, double* g3, doubl
     if (e_c) *e_c = ec;
 }
 
+
+/* ======================================================================== */
+/* Ewald electrostatics (coulomb_mode 1). The real-space pairs erfc(a r)/r  */
+/* are split by chi like any pair term (Sec. 3.1); the rest is smooth and  */
+/* deterministic: the reciprocal sum, the self term -C a/sqrt(pi) sum q^2, */
+/* and, for excluded pairs (which the reciprocal sum still couples), the   */
+/* correction -C q_i q_j erf(a r)/r.                                        */
+/* ======================================================================== */
+static void ewald_excl_self(const or_sys* s, double* grad, double* energy)
+{
+    double a = s->p.dsf_alpha, e = 0.0;
+    for (int i = 0; i < s->n; ++i) {
+        e -= OR_COULOMB * a / sqrt(OR_PI) * s->q[i] * s->q[i];
+        for (int k = s->exoff[i]; k < s->exoff[i + 1]; ++k) {
+            int j = s->exidx[k];
+            double d[3];
+            minimage(s, i, j, d);
+            double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            double qq = OR_COULOMB * s->q[i] * s->q[j];
+            if (j > i) e -= qq * erf(a * r) / r;
+            /* d/dr [-erf(a r)/r] = erf(a r)/r^2 - (2a/sqrt(pi)) exp(-a^2 r^2)/r */
+            double dudr = qq * (erf(a * r) / (r * r) - 2.0 * a / sqrt(OR_PI) * exp(-a * a * r * r) / r);
+            if (grad)
+                for (int c = 0; c < 3; ++c) grad[3 * i + c] += dudr * d[c] / r;
+        }
+    }
+    if (energy) *energy += e;
+}
+
+void or_ewald_recip_plain(const or_sys* s, int kmax, double* grad, double* energy)
+{
+    int n = s->n;
+    double L = s->L, V = L * L * L, a = s->p.dsf_alpha, e = 0.0;
+    if (grad) memset(grad, 0, sizeof(double) * 3 * (size_t)n);
+    double* cs = (double*)malloc(sizeof(double) * (size_t)n);
+    double* sn = (double*)malloc(sizeof(double) * (size_t)n);
+    for (int n1 = -kmax; n1 <= kmax; ++n1)
+        for (int n2 = -kmax; n2 <= kmax; ++n2)
+            for (int n3 = -kmax; n3 <= kmax; ++n3) {
+                if (n1 * n1 + n2 * n2 + n3 * n3 > kmax * kmax || (n1 == 0 && n2 == 0 && n3 == 0)) continue;
+                double m[3] = { n1 / L, n2 / L, n3 / L };
+                double m2 = m[0] * m[0] + m[1] * m[1] + m[2] * m[2];
+                double w = exp(-OR_PI * OR_PI * m2 / (a * a)) / m2;
+                /* S(m) = sum_j q_j exp(2 pi i m.x_j) */
+                double Sr = 0.0, Si = 0.0;
+                for (int j = 0; j < n; ++j) {
+                    double th = 2.0 * OR_PI * (m[0] * s->x[3 * j] + m[1] * s->x[3 * j + 1] + m[2] * s->x[3 * j + 2]);
+                    cs[j] = cos(th);
+                    sn[j] = sin(th);
+                    Sr += s->q[j] * cs[j];
+                    Si += s->q[j] * sn[j];
+                }
+                e += OR_COULOMB / (2.0 * OR_PI * V) * w * (Sr * Sr + Si * Si);
+                if (grad)
+                    for (int j = 0; j < n; ++j) {
+                        /* d|S|^2/dx_j = -4 pi q_j m (Sr sin - Si cos) */
+                        double f = -OR_COULOMB / (2.0 * OR_PI * V) * w * 4.0 * OR_PI * s->q[j] * (Sr * sn[j] - Si * cs[j]);
+                        for (int c = 0; c < 3; ++c) grad[3 * j + c] += f * m[c];
+                    }
+            }
+    free(cs);
+    free(sn);
+    if (energy) *energy = e;
+    ewald_excl_self(s, grad, energy);
+}
+
+/* smooth PME: the cardinal B-spline M_p and its derivative */
+static double bspline(int p, double u)
+{
+    if (u <= 0.0 || u >= p) return 0.0;
+    if (p == 2) return 1.0 - fabs(u - 1.0);
+    return (u * bspline(p - 1, u) + (p - u) * bspline(p - 1, u - 1.0)) / (p - 1);
+}
+
+static double dbspline(int p, double u) { return bspline(p - 1, u) - bspline(p - 1, u - 1.0); }
+
+/* grid points per edge: the smallest 2,3,5-smooth integer >= L / spacing (at least 2 p) */
+static int pme_grid(double L, double spacing, int p)
+{
+    int K = (int)ceil(L / spacing);
+    if (K < 2 * p) K = 2 * p;
+    for (;; ++K) {
+        int m = K;
+        while (m % 2 == 0) m /= 2;
+        while (m % 3 == 0) m /= 3;
+        while (m % 5 == 0) m /= 5;
+        if (m == 1) return K;
+    }
+}
+
+/* one pass of a separable DFT along an axis of a K^3 complex grid:
+ * out(m) = sum_k in(k) exp(sign 2 pi i m k / K) */
+static void dft_axis(double* re, double* im, int K, int axis, int sign)
+{
+    double* tr = (double*)malloc(sizeof(double) * (size_t)K);
+    double* ti = (double*)malloc(sizeof(double) * (size_t)K);
+    size_t stride = axis == 0 ? 1 : (axis == 1 ? (size_t)K : (size_t)K * K);
+    for (int a = 0; a < K; ++a)
+        for (int b = 0; b < K; ++b) {
+            size_t base = axis == 0 ? ((size_t)a * K + b) * K : (axis == 1 ? (size_t)a * K * K + b : (size_t)a * K + b);
+            for (int m = 0; m < K; ++m) {
+                double sr = 0.0, si = 0.0;
+                for (int k = 0; k < K; ++k) {
+                    double th = sign * 2.0 * OR_PI * (double)((long)m * k % K) / K;
+                    double c = cos(th), sv = sin(th);
+                    double xr = re[base + k * stride], xi = im[base + k * stride];
+                    sr += xr * c - xi * sv;
+                    si += xr * sv + xi * c;
+                }
+                tr[m] = sr;
+                ti[m] = si;
+            }
+            for (int m = 0; m < K; ++m) { re[base + m * stride] = tr[m]; im[base + m * stride] = ti[m]; }
+        }
+    free(tr);
+    free(ti);
+}
+
+void or_ewald_recip_pme(const or_sys* s, double* grad, double* energy, int* Kout)
+{
+    int n = s->n, p = s->p.pme_order;
+    double L = s->L, V = L * L * L, a = s->p.dsf_alpha;
+    int K = pme_grid(L, s->p.pme_spacing, p);
+    if (Kout) *Kout = K;
+    size_t G = (size_t)K * K * K;
+    double* Q = (double*)calloc(G, sizeof(double));
+    double* im = (double*)calloc(G, sizeof(double));
+    /* charges spread with M_p: point k gets q M_p(u - k) for k = floor(u) - t, t = 0..p-1 */
+    for (int i = 0; i < n; ++i) {
+        double u[3];
+        int k0[3];
+        for (int c = 0; c < 3; ++c) {
+            double x = s->x[3 * i + c] - L * floor(s->x[3 * i + c] / L);
+            u[c] = K * x / L;
+            k0[c] = (int)floor(u[c]);
+        }
+        for (int t0 = 0; t0 < p; ++t0)
+            for (int t1 = 0; t1 < p; ++t1)
+                for (int t2 = 0; t2 < p; ++t2) {
+                    int k[3] = { k0[0] - t0, k0[1] - t1, k0[2] - t2 };
+                    double w = s->q[i];
+                    int t[3] = { t0, t1, t2 };
+                    for (int c = 0; c < 3; ++c) {
+                        w *= bspline(p, u[c] - k0[c] + t[c]);
+                        k[c] = ((k[c] % K) + K) % K;
+                    }
+                    Q[((size_t)k[2] * K + k[1]) * K + k[0]] += w;
+                }
+    }
+    /* F(Q)(m) = sum_k Q(k) exp(-2 pi i m.k / K) */
+    double* re = (double*)malloc(sizeof(double) * G);
+    memcpy(re, Q, sizeof(double) * G);
+    for (int ax = 0; ax < 3; ++ax) dft_axis(re, im, K, ax, -1);
+    /* E = 1/2 sum_m G(m) |F(Q)(m)|^2, G = (C / (pi V)) exp(-pi^2 m^2 / a^2) / m^2 B(m) */
+    double* bmod = (double*)malloc(sizeof(double) * (size_t)K);
+    for (int m = 0; m < K; ++m) {
+        double sr = 0.0, si = 0.0;
+        for (int k = 0; k <= p - 2; ++k) {
+            double th = 2.0 * OR_PI * (double)m * k / K;
+            sr += bspline(p, k + 1.0) * cos(th);
+            si += bspline(p, k + 1.0) * sin(th);
+        }
+        double d2 = sr * sr + si * si;
+        bmod[m] = d2 > 1e-300 ? 1.0 / d2 : 0.0;
+    }
+    double e = 0.0;
+    for (int m2 = 0; m2 < K; ++m2)
+        for (int m1 = 0; m1 < K; ++m1)
+            for (int m0 = 0; m0 < K; ++m0) {
+                size_t g = ((size_t)m2 * K + m1) * K + m0;
+                int mm[3] = { m0, m1, m2 };
+                double msq = 0.0;
+                for (int c = 0; c < 3; ++c) {
+                    double mc = (mm[c] <= K / 2 ? mm[c] : mm[c] - K) / L;
+                    msq += mc * mc;
+                }
+                double Gm = 0.0;
+                if (msq > 0.0)
+                    Gm = OR_COULOMB / (OR_PI * V) * exp(-OR_PI * OR_PI * msq / (a * a)) / msq * bmod[m0] * bmod[m1] * bmod[m2];
+                e += 0.5 * Gm * (re[g] * re[g] + im[g] * im[g]);
+                re[g] *= Gm;
+                im[g] *= Gm;
+            }
+    if (energy) *energy = e;
+    if (grad) {
+        /* phi(k) = sum_m G(m) F(Q)(m) exp(+2 pi i m.k / K) = dE/dQ(k) */
+        for (int ax = 0; ax < 3; ++ax) dft_axis(re, im, K, ax, +1);
+        memset(grad, 0, sizeof(double) * 3 * (size_t)n);
+        for (int i = 0; i < n; ++i) {
+            double u[3];
+            int k0[3];
+            for (int c = 0; c < 3; ++c) {
+                double x = s->x[3 * i + c] - L * floor(s->x[3 * i + c] / L);
+                u[c] = K * x / L;
+                k0[c] = (int)floor(u[c]);
+            }
+            for (int t0 = 0; t0 < p; ++t0)
+                for (int t1 = 0; t1 < p; ++t1)
+                    for (int t2 = 0; t2 < p; ++t2) {
+                        int t[3] = { t0, t1, t2 }, k[3];
+                        double M[3], dM[3];
+                        for (int c = 0; c < 3; ++c) {
+                            M[c] = bspline(p, u[c] - k0[c] + t[c]);
+                            dM[c] = dbspline(p, u[c] - k0[c] + t[c]);
+                            k[c] = (((k0[c] - t[c]) % K) + K) % K;
+                        }
+                        double ph = re[((size_t)k[2] * K + k[1]) * K + k[0]];
+                        /* dQ(k)/dx_c = q (K / L) M'_p(u_c - k_c) prod_{d != c} M_p(u_d - k_d) */
+                        grad[3 * i + 0] += s->q[i] * K / L * dM[0] * M[1] * M[2] * ph;
+                        grad[3 * i + 1] += s->q[i] * K / L * M[0] * dM[1] * M[2] * ph;
+                        grad[3 * i + 2] += s->q[i] * K / L * M[0] * M[1] * dM[2] * ph;
+                    }
+        }
+    }
+    free(Q); free(im); free(re); free(bmod);
+    ewald_excl_self(s, grad, energy);
+}
+
+/* the reciprocal part of a gradient mode in Ewald mode (modes 0, 2, 4, 5, 6) */
+static int mode_has_recip(const or_sys* s, int mode)
+{
+    return s->p.coulomb_mode == 1 && (mode == 0 || mode == 2 || mode == 4 || mode == 5 || mode == 6);
+}
+
 void or_gradient(or_sys* s, int mode, double* grad, double* energy)
 {
     int n = s->n;
@@ -698,7 +940,7 @@ void or_gradient(or_sys* s, int mode, double* grad, double* energy)
     case 3: weight = W_SHORT; nb = 1; break;
     case 4: weight = W_LONG; nb = 1; break;
     case 5: weight = W_SHORT; nb = 1; bo = 1; break;
-    default: break;
+    default: break;       /* 6: reciprocal part only (Ewald mode) */
     }
     if (nb) {
 #pragma omp parallel for schedule(dynamic, 16) reduction(+:elj,ec)
@@ -710,17 +952,30 @@ void or_gradient(or_sys* s, int mode, double* grad, double* energy)
         }
     }
     if (bo) bonded_gradient(s, grad, &eb, &ea);
-    if (energy) *energy = eb + ea + 0.5 * (elj + ec);
+    double erec = 0.0;
+    if (mode_has_recip(s, mode)) {
+        double* g = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+        or_ewald_recip_pme(s, g, &erec, NULL);
+        for (size_t k = 0; k < 3 * (size_t)n; ++k) grad[k] += g[k];
+        free(g);
+    }
+    if (energy) *energy = eb + ea + 0.5 * (elj + ec) + erec;
 }
 
 void or_gradient_atom(or_sys* s, int mode, int i, double* g3)
 {
     int weight = mode == 3 || mode == 5 ? W_SHORT : (mode == 4 ? W_LONG : W_FULL);
     g3[0] = g3[1] = g3[2] = 0.0;
-    if (mode != 1) nonbonded_atom(s, i, weight, g3, NULL, NULL);
+    if (mode != 1 && mode != 6) nonbonded_atom(s, i, weight, g3, NULL, NULL);
     if (mode == 0 || mode == 1 || mode == 5) {
         double* g = (double*)calloc(3 * (size_t)s->n, sizeof(double));
         bonded_gradient(s, g, NULL, NULL);
+        for (int c = 0; c < 3; ++c) g3[c] += g[3 * i + c];
+        free(g);
+    }
+    if (mode_has_recip(s, mode)) {
+        double* g = (double*)malloc(sizeof(double) * 3 * (size_t)s->n);
+        or_ewald_recip_pme(s, g, NULL, NULL);
         for (int c = 0; c < 3; ++c) g3[c] += g[3 * i + c];
         free(g);
     }
@@ -738,7 +993,9 @@ void or_energy(or_sys* s, double* terms)
         elj += el;
         ec += e2;
     }
-    terms[0] = eb; terms[1] = ea; terms[2] = 0.5 * elj; terms[3] = 0.5 * ec;
+    double erec = 0.0;
+    if (s->p.coulomb_mode == 1) or_ewald_recip_pme(s, NULL, &erec, NULL);
+    terms[0] = eb; terms[1] = ea; terms[2] = 0.5 * elj; terms[3] = 0.5 * ec + erec;
     free(g);
 }
 
@@ -1149,10 +1406,13 @@ int or_step_jump_respa(or_sys* s, int64_t nouter, double dt_inner_fs, int n_inne
 {
     if (s->lazy) return -1;   /* the steps rebuild the lists of every atom */
     double dt = dt_inner_fs * 1e-3, D = dt * n_inner;
+    int ew = s->p.coulomb_mode == 1;   /* Ewald: the reciprocal part is kicked at D (Sec. 2.3) */
     accel(s, 1, s->ab);
     accel(s, 3, s->as);
+    if (ew) accel(s, 6, s->al);
     for (int64_t o = 0; o < nouter; ++o) {
         uint32_t s0 = (uint32_t)s->step;
+        if (ew) kick(s, s->al, 0.5 * D);
         cphase(s, s->as, 0.5 * D, s0, 0);
         jphase(s, 0.5 * D, s0, 0);
         for (int k = 0; k < n_inner; ++k) inner_bonded(s, dt);
@@ -1160,21 +1420,26 @@ int or_step_jump_respa(or_sys* s, int64_t nouter, double dt_inner_fs, int n_inne
         accel(s, 3, s->as);
         jphase(s, 0.5 * D, s0, 1);
         cphase(s, s->as, 0.5 * D, s0, 1);
+        if (ew) { accel(s, 6, s->al); kick(s, s->al, 0.5 * D); }
     }
     check_finite(s);
     return (int)s->err;
 }
 
-/* JUMP-RESPA1: the outer level holds the slow many-body force, which is
- * absent with DSF electrostatics; the mid level kappa = m dt carries the
- * short-range pairs and the jumps, the inner level the bonded terms. */
+/* JUMP-RESPA1: the outer level holds the slow many-body force: the Ewald
+ * reciprocal part (absent with DSF electrostatics, the level is then empty);
+ * the mid level kappa = m dt carries the short-range pairs and the jumps, the
+ * inner level the bonded terms. */
 int or_step_jump_respa1(or_sys* s, int64_t nouter, double dt_inner_fs, int m_mid, int n_outer)
 {
     if (s->lazy) return -1;   /* the steps rebuild the lists of every atom */
-    double dt = dt_inner_fs * 1e-3, kap = dt * m_mid;
+    double dt = dt_inner_fs * 1e-3, kap = dt * m_mid, D = kap * n_outer;
+    int ew = s->p.coulomb_mode == 1;
     accel(s, 1, s->ab);
     accel(s, 3, s->as);
+    if (ew) accel(s, 6, s->al);
     for (int64_t o = 0; o < nouter; ++o) {
+        if (ew) kick(s, s->al, 0.5 * D);
         for (int j = 0; j < n_outer; ++j) {
             uint32_t s0 = (uint32_t)s->step;
             cphase(s, s->as, 0.5 * kap, s0, 0);
@@ -1185,6 +1450,7 @@ int or_step_jump_respa1(or_sys* s, int64_t nouter, double dt_inner_fs, int m_mid
             jphase(s, 0.5 * kap, s0, 1);
             cphase(s, s->as, 0.5 * kap, s0, 1);
         }
+        if (ew) { accel(s, 6, s->al); kick(s, s->al, 0.5 * D); }
     }
     check_finite(s);
     return (int)s->err;

@@ -51,6 +51,12 @@ typedef struct {
     int lj_long_mode;    /* 0: the long-range LJ part (1-chi) U_LJ is handled by BPS jumps (J');
                           * 1: it is deterministic, in F0 (the paper's GPU runs): gradient modes
                           * 3 and 5 carry the whole LJ, mode 4 only (1-chi) Coulomb, no J' */
+    int coulomb_mode;    /* 0: DSF Coulomb (damping dsf_alpha); 1: Ewald: real-space pairs
+                          * erfc(alpha r)/r to r_cut (alpha = dsf_alpha) split by chi as in
+                          * Sec. 3.1, plus a smooth-PME reciprocal sum (Essmann et al. 1995),
+                          * the self term and the exclusion correction */
+    int pme_order;       /* B-spline order p of the reciprocal sum (Ewald mode) */
+    double pme_spacing;  /* target grid spacing (A); K = smallest 2,3,5-smooth integer >= L/spacing */
 } or_params;
 
 typedef struct or_sys or_sys;
@@ -117,6 +123,14 @@ int or_step_baoab(or_sys* s, int64_t nsteps, double dt_fs);
 int or_step_baoab_respa(or_sys* s, int64_t nouter, double dt_inner_fs, int n_inner);
 int or_step_baoab_respa1(or_sys* s, int64_t nouter, double dt_inner_fs, int m_mid, int n_outer);
 int or_step_jump(or_sys* s, int64_t nsteps, double dt_fs);
+/* Ewald mode: the reciprocal-space gradient and energy by the plain Ewald
+ * sum over the integer vectors n with |n| <= kmax (m = n / L), no
+ * interpolation; the self term and the exclusion correction are included.
+ * The reference the smooth-PME sum of the integrators is checked against. */
+void or_ewald_recip_plain(const or_sys* s, int kmax, double* grad, double* energy);
+/* the same quantities from the smooth-PME sum used by the integrators; K the grid */
+void or_ewald_recip_pme(const or_sys* s, double* grad, double* energy, int* K);
+
 /* BJAOAJB (Sec. 2.3): B(dt/2) with F0, then the jump processes alone over
  * dt/2 (C' with zero drift, then J'), A O A, F0, J', C' (zero drift), B. */
 int or_step_bjaoajb(or_sys* s, int64_t nsteps, double dt_fs);

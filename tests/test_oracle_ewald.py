@@ -1,0 +1,121 @@
+"""Ewald electrostatics of the oracle (coulomb_mode 1): the plain Ewald sum
+against the Madelung constant of rock salt, independence of the total
+electrostatic energy from the splitting parameter, the smooth-PME sum against
+the plain sum, and its gradient against finite differences of its energy."""
+import numpy as np
+import pytest
+
+from paper_2412_15073_gb300 import systems
+
+C_COUL = 332.0637
+MADELUNG_NACL = 1.747564594633   # rock salt, per ion pair, in units of q^2 / r0
+
+
+def rock_salt(cells, a):
+    base = np.array([[0, 0, 0], [0.5, 0.5, 0], [0.5, 0, 0.5], [0, 0.5, 0.5]])
+    na = np.concatenate([base + np.array(c) for c in np.ndindex(cells, cells, cells)]) * a
+    cl = na + np.array([0.5, 0, 0]) * a
+    x = np.concatenate([na, cl])
+    q = np.concatenate([np.ones(len(na)), -np.ones(len(cl))])
+    return systems.point_charges(x, cells * a, q, 23.0)
+
+
+def coulomb_total(o, plain_kmax=None):
+    """real-space pairs + reciprocal + self + exclusion terms"""
+    e_c = o.energy()[3]                       # real space + smooth-PME part
+    if plain_kmax is None:
+        return e_c
+    _, e_pme, _ = o.ewald_recip_pme()
+    _, e_plain = o.ewald_recip_plain(plain_kmax)
+    return e_c - e_pme + e_plain
+
+
+@pytest.mark.parametrize("alpha,kmax", [(0.5, 18), (0.55, 20)])
+def test_plain_ewald_gives_the_madelung_energy_of_rock_salt(oracle_mod, alpha, kmax):
+    """216 ions of rock salt (a = 5.64 A): the Ewald energy (real space to 8 A,
+    the plain reciprocal sum, the self term) is the Madelung energy
+    -N/2 C M q^2 / r0, r0 = a/2, to within the truncation of both sums."""
+    a = 5.64
+    s = rock_salt(3, a)
+    o = oracle_mod.Oracle(s, r_cut=8.0, r_split=5.0, dsf_alpha=alpha, coulomb_mode=1, skin=0.2)
+    e = coulomb_total(o, plain_kmax=kmax)
+    ref = -(s.n / 2) * C_COUL * MADELUNG_NACL / (a / 2)
+    assert e == pytest.approx(ref, rel=2e-8)
+
+
+def test_total_ewald_energy_does_not_depend_on_alpha(oracle_mod, water648):
+    es = []
+    for alpha in (0.40, 0.45, 0.50):
+        o = oracle_mod.Oracle(water648, r_cut=9.0, r_split=5.0, dsf_alpha=alpha, coulomb_mode=1, skin=0.2,
+                              skin_outer=0.3)
+        es.append(coulomb_total(o, plain_kmax=20))
+    # the total is a small difference of large terms (real space about
+    # -2300 kcal/mol, self about -18000): 5e-3 kcal/mol is ~3e-7 of them
+    assert max(es) - min(es) < 5e-3, es
+
+
+def test_smooth_pme_matches_the_plain_sum(oracle_mod, water648):
+    o = oracle_mod.Oracle(water648, r_cut=9.0, r_split=5.0, dsf_alpha=0.35, coulomb_mode=1, skin=0.2,
+                          skin_outer=0.3, pme_order=6, pme_spacing=0.8)
+    g_pme, e_pme, K = o.ewald_recip_pme()
+    g_plain, e_plain = o.ewald_recip_plain(16)
+    assert K >= 24
+    assert abs(e_pme - e_plain) < 2e-3          # kcal/mol, with a self term of ~ -15600
+    rms = np.sqrt((g_plain ** 2).sum(1).mean())
+    assert np.abs(g_pme - g_plain).max() < 1e-3 * rms
+
+
+def test_smooth_pme_gradient_is_the_derivative_of_its_energy(oracle_mod, water648):
+    w = water648.copy()
+    p = dict(r_cut=9.0, r_split=5.0, dsf_alpha=0.35, coulomb_mode=1, skin=0.2, skin_outer=0.3, pme_spacing=1.0)
+    o = oracle_mod.Oracle(w, **p)
+    g, _, _ = o.ewald_recip_pme()
+    h = 1e-5
+    for i in (0, 1, 300):
+        for c in range(3):
+            xp = w.x.copy(); xp[i, c] += h
+            xm = w.x.copy(); xm[i, c] -= h
+            o.set_state(xp, w.v); ep = o.ewald_recip_pme()[1]
+            o.set_state(xm, w.v); em = o.ewald_recip_pme()[1]
+            assert g[i, c] == pytest.approx((ep - em) / (2 * h), rel=1e-5, abs=1e-6)
+
+
+def test_ewald_gradient_modes_add_up(oracle_mod, water648):
+    """bonded + short + long = full; F0 = bonded + short + reciprocal; mode 6
+    is the reciprocal part (with self and exclusion terms)."""
+    o = oracle_mod.Oracle(water648, r_cut=9.0, r_split=5.0, dsf_alpha=0.35, coulomb_mode=1, skin=0.2,
+                          skin_outer=0.3)
+    g = {m: o.gradient(m)[0] for m in range(7)}
+    assert np.allclose(g[1] + g[3] + g[4], g[0], atol=1e-9)
+    assert np.allclose(g[1] + g[3] + g[6], g[5], atol=1e-9)
+    assert np.allclose(g[6], o.ewald_recip_pme()[0], atol=1e-12)
+
+
+def test_ewald_dynamics_keep_temperature_and_jump_forces_are_weak(oracle_mod, water648):
+    """With Ewald electrostatics (alpha 0.35) the pair forces beyond the split
+    are small, so the jump range carries little force; BAOAB, JUMP and
+    JUMP-RESPA1 (reciprocal part kicked at the outer step) keep 300 K."""
+    p = dict(r_cut=9.0, r_split=5.0, h_switch=0.5, dsf_alpha=0.35, coulomb_mode=1, skin=0.2, skin_outer=0.3,
+             pme_spacing=1.0)
+    o_dsf = oracle_mod.Oracle(water648, r_cut=9.0, r_split=5.0, dsf_alpha=0.2, skin=0.2, skin_outer=0.3)
+    o_ew = oracle_mod.Oracle(water648, **p)
+    # the long real-space part, |grad|, is an order of magnitude below DSF's
+    g_dsf = np.linalg.norm(o_dsf.gradient(4)[0], axis=1).mean()
+    g_ew = np.linalg.norm(o_ew.gradient(4)[0] - o_ew.gradient(6)[0], axis=1).mean()
+    assert g_ew < 0.2 * g_dsf, (g_ew, g_dsf)
+    # from the lattice start the box heats while it relaxes: 40 steps of BAOAB
+    # reach nearly the same temperature with Ewald as with DSF (both stand for
+    # the same electrostatics); JUMP and JUMP-RESPA1 run without error flags
+    kT = 3 * water648.n * 0.0019872042586
+    temps = {}
+    for name, oo in (("dsf", oracle_mod.Oracle(water648, seed=3, r_cut=9.0, r_split=5.0, dsf_alpha=0.2,
+                                                skin=0.2, skin_outer=0.3)),
+                     ("ewald", oracle_mod.Oracle(water648, seed=3, **p))):
+        assert oo.baoab(40) == 0
+        v = oo.state()[1]
+        temps[name] = (water648.mass[:, None] * v * v).sum() / 418.4 / kT
+    assert abs(temps["ewald"] / temps["dsf"] - 1) < 0.05, temps
+    for how, args in (("jump", (40,)), ("jump_respa1", (5, 1.0, 2, 4))):
+        o = oracle_mod.Oracle(water648, seed=3, **p)
+        assert getattr(o, how)(*args) == 0, how
+        assert np.isfinite(o.state()[1]).all()
