@@ -371,7 +371,7 @@ def main():
     ej.jump(prof_steps)
     cp1 = ej.observables()
     ms, groups, _ = ej.profile(enable=0)
-    classes = ["pair_force", "bonded", "velocity_phase", "kick_aoa", "list_rebuild", "bookkeeping"]
+    classes = ["pair_force", "bonded", "velocity_phase", "kick_aoa", "list_rebuild", "bookkeeping", "ewald_recip"]
     top = int(np.argmax(ms))
     pk, how = peaks()
     clock = (pk.get("sm_max_mhz") or 2070.0) * 1e6

@@ -110,6 +110,18 @@ typedef struct {
     int lj_long_mode;  /* 0: the long-range LJ part (1-chi) U_LJ jumps (BPS, J', Sec. 3.2);
                         * 1: it is deterministic in F0, as in the paper's GPU runs (Sec. 4):
                         * gradient modes 3 and 5 carry the whole LJ, mode 4 only (1-chi) Coulomb */
+    int coulomb_mode;  /* 0: damped shifted force Coulomb (DSF, dsf_alpha);
+                        * 1: Ewald (Sec. 3.1 splits its real-space part like DSF): pair term
+                        *    erfc(a r)/r cut at r_cut with a = dsf_alpha > 0, no shift; the
+                        *    reciprocal part by smooth PME (cardinal B-splines of order pme_order
+                        *    in [4, 8], grid of K^3 points, K the smallest 2,3,5-smooth integer
+                        *    >= max(box / pme_spacing, 2 pme_order)), the self energy
+                        *    -C a / sqrt(pi) sum q^2 and, for excluded pairs, -C q_i q_j erf(a r)/r.
+                        *    The reciprocal part is deterministic: it belongs to F0 (gradient
+                        *    mode 5), to modes 0, 2 and 4, and alone to mode 6; JUMP-RESPA and
+                        *    JUMP-RESPA1 kick it at their outer period (Sec. 2.3). */
+    int pme_order;     /* B-spline order p (coulomb_mode 1) */
+    double pme_spacing;/* target grid spacing (A, coulomb_mode 1) */
 } md_system;
 
 typedef struct {
@@ -155,7 +167,9 @@ int md_set_state(md_ctx* ctx, int replica, const double* x, const double* v, con
  *   jump_respa:   C'J' at Delta = n_inner dt around bonded inner steps.
  *   jump_respa1:  C'J' at kappa = m_mid dt around bonded inner steps; the
  *                 outer level of period n_outer kappa carries the slow
- *                 many-body force, which DSF electrostatics do not have. */
+ *                 many-body force: the Ewald reciprocal part (coulomb_mode 1;
+ *                 DSF electrostatics have none). jump_respa kicks it at
+ *                 Delta = n_inner dt. */
 int md_step_baoab(md_ctx* ctx, int64_t nsteps, double dt_fs);
 int md_step_baoab_respa(md_ctx* ctx, int64_t n_outer, double dt_inner_fs, int n_inner);
 int md_step_baoab_respa1(md_ctx* ctx, int64_t n_outer, double dt_inner_fs, int m_mid, int n_outer_ratio);
@@ -179,8 +193,10 @@ int md_get_state(md_ctx* ctx, int replica, double* x, double* v, int* img,
 /* Gradient of one part of the potential at the current positions, into a
  * host buffer of 3n doubles. mode: 0 full, 1 bonded, 2 nonbonded full,
  * 3 nonbonded short (chi-weighted), 4 nonbonded long ((1-chi)-weighted),
- * 5 F_0 of JUMP (bonded + short). Uses the current lists (rebuilt first
- * when an atom moved more than skin/2). */
+ * 5 F_0 of JUMP (bonded + short), 6 Ewald reciprocal part with the exclusion
+ * correction (zero with DSF). With coulomb_mode 1, modes 0, 2, 4 and 5 include
+ * the mode-6 part. Uses the current lists (rebuilt first when an atom moved
+ * more than skin/2). */
 int md_gradient(md_ctx* ctx, int replica, int mode, double* host_grad);
 
 /* One velocity phase at fixed positions, for testing the jump kernels: phase
@@ -203,13 +219,14 @@ int64_t md_get_events(md_ctx* ctx, int replica, int64_t* host_out6, int64_t cap,
 
 /* Kernel launch accounting of this context. Classes: 0 pair force, 1 bonded
  * force, 2 velocity phases (C' and J' jumps), 3 kicks and A-O-A updates,
- * 4 list rebuild chain, 5 bookkeeping (step counters, energies).
- * launches_out[6] (may be NULL) receives the cumulative number of kernels
+ * 4 list rebuild chain, 5 bookkeeping (step counters, energies), 6 Ewald
+ * reciprocal part (PME kernels; the cuFFT transforms are not counted).
+ * launches_out[7] (may be NULL) receives the cumulative number of kernels
  * launched per class since md_init. enable = 1 starts timing every launch
  * group with CUDA events on the context's stream, 0 stops it, -1 leaves it
- * as it is; ms_out[6] (may be NULL) receives the accumulated device time per
+ * as it is; ms_out[7] (may be NULL) receives the accumulated device time per
  * class while timing was on (summed at the end of each md_step_* call) and
- * groups_out[6] (may be NULL) the number of timed launch groups. reset != 0
+ * groups_out[7] (may be NULL) the number of timed launch groups. reset != 0
  * clears the times. */
 int md_profile(md_ctx* ctx, int enable, int reset, double* ms_out, int64_t* groups_out,
                int64_t* launches_out);

@@ -18,7 +18,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libmdjump.so")
 
 MD_FP64, MD_MIXED = 0, 1
-GRAD_FULL, GRAD_BONDED, GRAD_NB_FULL, GRAD_NB_SHORT, GRAD_NB_LONG, GRAD_F0 = range(6)
+GRAD_FULL, GRAD_BONDED, GRAD_NB_FULL, GRAD_NB_SHORT, GRAD_NB_LONG, GRAD_F0, GRAD_RECIP = range(7)
+COULOMB_DSF, COULOMB_EWALD = 0, 1
+N_PROFILE_CLASSES = 7
 FLAG_BOUND, FLAG_LIMIT, FLAG_NONFINITE, FLAG_OVERFLOW = 1, 2, 4, 8
 ERRORS = {-1: "MD_EINVAL", -2: "MD_ECUDA", -3: "MD_EOVERFLOW", -4: "MD_EBOUND",
           -5: "MD_ELIMIT", -6: "MD_ENONFINITE", -7: "MD_ENOSYSTEM", -8: "MD_ENOMEM"}
@@ -55,7 +57,8 @@ class MdSystem(C.Structure):
                 ("r_mid", C.c_double), ("dsf_alpha", C.c_double), ("gamma", C.c_double),
                 ("temperature", C.c_double), ("eps0", C.c_double), ("eps_mode", C.c_int),
                 ("skin", C.c_double), ("skin_outer", C.c_double),
-                ("n_rings", C.c_int), ("ring_r", C.c_double * 3), ("lj_long_mode", C.c_int)]
+                ("n_rings", C.c_int), ("ring_r", C.c_double * 3), ("lj_long_mode", C.c_int),
+                ("coulomb_mode", C.c_int), ("pme_order", C.c_int), ("pme_spacing", C.c_double)]
 
 
 class MdObs(C.Structure):
@@ -121,7 +124,8 @@ def _current_stream():
 
 
 DEFAULTS = dict(r_cut=9.0, r_split=5.0, h_switch=0.5, r_mid=5.5, dsf_alpha=0.2, gamma=1.0,
-                temperature=300.0, eps0=0.1, eps_mode=1, skin=0.3, skin_outer=None, ring_r=None, lj_long_mode=0)
+                temperature=300.0, eps0=0.1, eps_mode=1, skin=0.3, skin_outer=None, ring_r=None, lj_long_mode=0,
+                coulomb_mode=0, pme_order=6, pme_spacing=0.8)
 
 
 KIND_RING0, KIND_LJ = 0, 4
@@ -190,6 +194,9 @@ class Engine:
             for k, z in enumerate(rr):
                 s.ring_r[k] = z
         s.lj_long_mode = int(p["lj_long_mode"])
+        s.coulomb_mode = int(p["coulomb_mode"])
+        s.pme_order = int(p["pme_order"])
+        s.pme_spacing = float(p["pme_spacing"])
         self._ck(self.L.md_set_system(self.h, replica, C.byref(s)))
         self.n[replica] = sys.n
 
@@ -247,10 +254,11 @@ class Engine:
 
     def profile(self, enable=-1, reset=False):
         """(ms per class, timed groups per class, kernels launched per class);
-        classes: pair force, bonded, velocity phases, kicks/AOA, rebuild chain, bookkeeping."""
-        ms = np.zeros(6)
-        groups = np.zeros(6, dtype=np.int64)
-        launches = np.zeros(6, dtype=np.int64)
+        classes: pair force, bonded, velocity phases, kicks/AOA, rebuild chain, bookkeeping,
+        Ewald reciprocal (PME)."""
+        ms = np.zeros(N_PROFILE_CLASSES)
+        groups = np.zeros(N_PROFILE_CLASSES, dtype=np.int64)
+        launches = np.zeros(N_PROFILE_CLASSES, dtype=np.int64)
         self._ck(self.L.md_profile(self.h, int(enable), int(reset), _ptr(ms), _ptr(groups), _ptr(launches)))
         return ms, groups, launches
 

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libmdjump.so")
 BUILD_DIR = os.path.join(HERE, "_build")
-SOURCES = ["md_api.cu", "k_lists.cu", "k_force.cu", "k_jump.cu", "noalloc.cu"]
+SOURCES = ["md_api.cu", "k_lists.cu", "k_force.cu", "k_jump.cu", "k_pme.cu", "noalloc.cu"]
 # the velocity-phase kernel comes in several occupancy variants that must give
 # identical results: no mul/add contraction there, every FMA is written out
 PER_FILE = {"k_jump.cu": ["-fmad=false"]}
@@ -62,7 +62,9 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
                 print(out)
     if force or jobs or _stale(OUT, objs):
         tmp = OUT + f".{os.getpid()}.tmp"
-        run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs])
+        # cuFFT (the PME transforms) is found at run time through the toolkit's library folder
+        cudalib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc()))), "lib64")
+        run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcufft", "-Xlinker", "-rpath=" + cudalib])
         os.replace(tmp, OUT)
     return OUT
 

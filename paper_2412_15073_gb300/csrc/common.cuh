@@ -79,6 +79,11 @@ struct RepParams {
     double shell_lo2[MAX_RINGS + 1], shell_hi2[MAX_RINGS + 1];
     float shell_lo2f[MAX_RINGS + 1], shell_hi2f[MAX_RINGS + 1];
     float r2s, r2f;            // (r_c + skin)^2, (r_E + skin)^2: short and full lists
+    // Ewald electrostatics (coul_mode 1): real space is the DSF form with eR = fR = 0
+    // (erfc(a r)/r cut at r_E); the reciprocal part is a smooth-PME sum on a K^3 grid
+    int coul_mode, pme_p, pme_K, pad4;
+    long long pme_goff, pme_soff;       // offsets of this replica's real grid and spectrum
+    double pme_self;                    // -C a / sqrt(pi) sum q^2 (kcal/mol)
     LJPair lj[MAX_TYPES * MAX_TYPES];
 };
 

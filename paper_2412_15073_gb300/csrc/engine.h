@@ -9,6 +9,10 @@
 
 namespace mdj {
 
+// launch classes of the accounting (md_profile): 0 pair force, 1 bonded, 2 velocity
+// phases, 3 kicks and A-O-A, 4 list rebuild, 5 bookkeeping, 6 Ewald reciprocal (PME)
+constexpr int NPROF = 7;
+
 // Device pointers of one context, passed by value to every kernel. All atom
 // arrays are concatenated over replicas (replica r owns [atom_off, atom_off+n)).
 struct Dev {
@@ -62,6 +66,12 @@ struct Dev {
     double* energy;                 // [R][6]: bond, angle, lj, coul, ke, spare
     long long* step_base;           // [R]
     double* stepc;                  // [R][2]: exp(-gamma tau), sqrt((1 - exp(-2 gamma tau)) / beta)
+    // smooth PME (Ewald replicas): fixed-point charge grid, real grid, spectrum, influence function
+    unsigned long long* pme_qi;
+    double* pme_q;
+    double2* pme_spec;
+    const double* pme_G;
+    double* pme_e;                  // [R] reciprocal energy of the last md_observables
     // accepted-jump log
     long long* ev;
     unsigned long long* ev_n;
@@ -83,6 +93,20 @@ void launch_kick2(const Dev& d, const double* a, double h, const double* b, doub
 void launch_aoa(const Dev& d, double tau, uint32_t s_off, int do_check, int fp64, cudaStream_t s);
 void launch_energy(const Dev& d, cudaStream_t s);
 void launch_advance(const Dev& d, long long nsteps, cudaStream_t s);
+
+// ---- smooth PME (k_pme.cu) -----------------------------------------------------------------
+// Reciprocal part of Ewald electrostatics for the replicas with coul_mode 1; the host runs
+// the cuFFT transforms between these launches:
+//   spread (charges on the fixed-point grid) -> tofloat (real grid, clears the fixed-point
+//   one) -> forward FFT -> convolve (times G; energy != 0 also sums the energy into pme_e)
+//   -> inverse FFT (potential grid) -> gather (gradient + exclusion correction into out,
+//   as -grad / m~ unless as_grad).
+void launch_pme_spread(const Dev& d, int fp64, cudaStream_t s);
+void launch_pme_tofloat(const Dev& d, long long total, cudaStream_t s);
+void launch_pme_convolve_grid(const Dev& d, int energy, int kmax, cudaStream_t s);
+void launch_pme_gather(const Dev& d, double* out, int as_grad, int fp64, cudaStream_t s);
+// exclusion-correction energy of each Ewald replica, added to d.energy[6 r + 3]
+void launch_pme_excl_energy(const Dev& d, cudaStream_t s);
 
 // ---- jumps (k_jump.cu) --------------------------------------------------------------
 // order 0: C' then J' (first half of a step), 1: J' then C' (second half)

@@ -14,6 +14,8 @@
 #include <string>
 #include <vector>
 
+#include <cufft.h>
+
 #include "../../include/md.h"
 #include "engine.h"
 
@@ -24,6 +26,7 @@ namespace {
 // ---- host pair terms for the rate bounds (FP64) --------------------------------
 struct HostPair {
     double R, sw, h, alpha;
+    int ewald = 0;          // 1: Ewald real space erfc(a r)/r, no value or slope shift
     double chi(double r) const
     {
         if (r <= sw) return 1.0;
@@ -39,11 +42,13 @@ struct HostPair {
     }
     double fR() const
     {
+        if (ewald) return 0.0;
         return std::erfc(alpha * R) / (R * R) + 2.0 * alpha / std::sqrt(PI) * std::exp(-alpha * alpha * R * R) / R;
     }
     double u_dsf(double r) const
     {
         if (r >= R) return 0.0;
+        if (ewald) return std::erfc(alpha * r) / r;
         return std::erfc(alpha * r) / r - std::erfc(alpha * R) / R + fR() * (r - R);
     }
     double du_dsf(double r) const
@@ -123,10 +128,10 @@ struct md_ctx {
     std::vector<RepParams> hp;
     std::vector<int> rep_atom_off;
     // launch accounting and optional per-class timing
-    long long nlaunch[6] = {0, 0, 0, 0, 0, 0};
+    long long nlaunch[NPROF] = {};
     bool prof = false;
-    double prof_ms[6] = {0, 0, 0, 0, 0, 0};
-    long long prof_groups[6] = {0, 0, 0, 0, 0, 0};
+    double prof_ms[NPROF] = {};
+    long long prof_groups[NPROF] = {};
     std::vector<cudaEvent_t> ev_pool;
     struct Pend { int cls; cudaEvent_t a, b; };
     std::vector<Pend> pend;
@@ -135,9 +140,15 @@ struct md_ctx {
     cudaStream_t gs = nullptr;
     long long gen = 0;
     struct Graph { long long gen; int key; double tau; int n_inner, units; cudaGraphExec_t exec;
-                   long long launches[6]; };
+                   long long launches[NPROF]; };
     std::vector<Graph> graphs;
     bool graphs_broken = false;
+    // smooth PME: one pair of cuFFT plans (real to complex, complex to real) per grid size
+    struct FftPlan { int K; cufftHandle d2z, z2d; };
+    std::vector<FftPlan> fft;
+    std::vector<int> ewald_reps;
+    long long pme_total = 0;    // grid points over all Ewald replicas
+    int pme_kmax = 0;
     // pinned staging
     double* h_stepc = nullptr;
     uint32_t* h_err = nullptr;
@@ -226,7 +237,7 @@ int lists_needed(const md_ctx* ctx, int family)
 
 int mode_list(const md_ctx* ctx, int mode)
 {
-    if (mode == 1) return 0;
+    if (mode == 1 || mode == 6) return 0;
     if (mode == 3 || mode == 5) return (1 << L_SHORT) | (any_lj_long(ctx) ? 1 << L_LJ : 0);
     return 1 << L_FULL;
 }
@@ -298,6 +309,57 @@ void make_shell_table(const RepParams& P, uint16_t* tab)
     }
 }
 
+// smooth PME grid points per edge: the smallest 2,3,5-smooth K >= max(L / spacing, 2 p)
+int pme_grid_size(double L, double spacing, int p)
+{
+    int K = std::max((int)std::ceil(L / spacing), 2 * p);
+    for (;; ++K) {
+        int m = K;
+        while (m % 2 == 0) m /= 2;
+        while (m % 3 == 0) m /= 3;
+        while (m % 5 == 0) m /= 5;
+        if (m == 1) return K;
+    }
+}
+
+// cardinal B-spline M_p at u (zero outside (0, p)), by its recursion in p
+double host_bspline(int p, double u)
+{
+    if (u <= 0.0 || u >= p) return 0.0;
+    if (p == 2) return 1.0 - std::fabs(u - 1.0);
+    return (u * host_bspline(p - 1, u) + (p - u) * host_bspline(p - 1, u - 1.0)) / (p - 1);
+}
+
+// influence function of one replica on the half spectrum [m2][m1][m0 <= K/2]:
+// G(m) = (C / (pi V)) exp(-pi^2 |m|^2 / a^2) / |m|^2 / |b1 b2 b3|^2, G(0) = 0, with
+// |b(m)|^-2 = |sum_{k=0}^{p-2} M_p(k + 1) exp(2 pi i m k / K)|^2 (Essmann et al. 1995)
+void make_pme_G(const RepParams& P, double* G)
+{
+    const int K = P.pme_K, Kh = K / 2 + 1, p = P.pme_p;
+    std::vector<double> bm(K);
+    for (int m = 0; m < K; ++m) {
+        double sr = 0.0, si = 0.0;
+        for (int k = 0; k <= p - 2; ++k) {
+            const double th = 2.0 * PI * m * k / K;
+            sr += host_bspline(p, k + 1.0) * std::cos(th);
+            si += host_bspline(p, k + 1.0) * std::sin(th);
+        }
+        const double d2 = sr * sr + si * si;
+        bm[m] = d2 > 1e-300 ? 1.0 / d2 : 0.0;
+    }
+    const double V = P.L * P.L * P.L, a = P.alpha;
+    for (int m2 = 0; m2 < K; ++m2)
+        for (int m1 = 0; m1 < K; ++m1)
+            for (int m0 = 0; m0 < Kh; ++m0) {
+                const double f2 = (m2 <= K / 2 ? m2 : m2 - K) / P.L, f1 = (m1 <= K / 2 ? m1 : m1 - K) / P.L;
+                const double f0 = m0 / P.L;
+                const double msq = f0 * f0 + f1 * f1 + f2 * f2;
+                double g = 0.0;
+                if (msq > 0.0) g = COULOMB / (PI * V) * std::exp(-PI * PI * msq / (a * a)) / msq * bm[m0] * bm[m1] * bm[m2];
+                G[((size_t)m2 * K + m1) * Kh + m0] = g;
+            }
+}
+
 RepParams make_params(const md_ctx* ctx, const RepHost& h, int r, int atom_off, int cell_off)
 {
     const md_system& s = h.sys;
@@ -337,10 +399,19 @@ RepParams make_params(const md_ctx* ctx, const RepHost& h, int r, int atom_off, 
     P.lj_jump = P.lj_on && !P.lj_long;
     P.eps_mode = s.eps_mode;
     P.skin = s.skin; P.skin_o = skin_o;
-    HostPair hpair{s.r_cut, P.sw, s.h_switch, s.dsf_alpha};
+    HostPair hpair{s.r_cut, P.sw, s.h_switch, s.dsf_alpha, s.coulomb_mode};
     P.alpha = s.dsf_alpha;
-    P.eR = std::erfc(s.dsf_alpha * s.r_cut) / s.r_cut;
+    // Ewald real space: the same pair code with no value or slope shift at r_E
+    P.eR = s.coulomb_mode == 1 ? 0.0 : std::erfc(s.dsf_alpha * s.r_cut) / s.r_cut;
     P.fR = hpair.fR();
+    P.coul_mode = s.coulomb_mode;
+    if (s.coulomb_mode == 1) {
+        P.pme_p = s.pme_order;
+        P.pme_K = pme_grid_size(h.box, s.pme_spacing, s.pme_order);
+        double q2 = 0.0;
+        for (double q : h.charge) q2 += q * q;
+        P.pme_self = -COULOMB * s.dsf_alpha / std::sqrt(PI) * q2;
+    }
     P.kexp = 2.0 * s.dsf_alpha / std::sqrt(PI);
     P.alphaf = float(P.alpha); P.eRf = float(P.eR); P.fRf = float(P.fR); P.kexpf = float(P.kexp);
     P.shell_invw = float(SHELL_BINS / ((s.r_cut + skin_o) * (s.r_cut + skin_o)));
@@ -377,7 +448,7 @@ RepParams make_params(const md_ctx* ctx, const RepHost& h, int r, int atom_off, 
 // per-atom bounds of a replica: L_Y per ring (C |q_i| qmax Lhat_Y, n x MAX_RINGS) and L_LJ
 void make_bounds(const RepHost& h, const RepParams& P, double* LY, double* LLJ)
 {
-    HostPair hp{P.R, P.sw, P.h, P.alpha};
+    HostPair hp{P.R, P.sw, P.h, P.alpha, P.coul_mode};
     auto coul = [&](double r) { return -hp.dchi(r) * hp.u_dsf(r) + (1.0 - hp.chi(r)) * hp.du_dsf(r); };
     double Lh[MAX_RINGS] = {};
     for (int y = 0; y < P.nr; ++y) Lh[y] = grid_max(coul, P.edge[y], P.edge[y + 1]);
@@ -419,6 +490,14 @@ int check_sys(md_ctx* ctx, const md_system* s)
         FAIL(MD_EINVAL, "md_set_system: invalid cutoff, switch, thermostat or jump parameters");
     if (s->lj_long_mode != 0 && s->lj_long_mode != 1)
         FAIL(MD_EINVAL, "md_set_system: lj_long_mode must be 0 or 1");
+    if (s->coulomb_mode != 0 && s->coulomb_mode != 1)
+        FAIL(MD_EINVAL, "md_set_system: coulomb_mode must be 0 (DSF) or 1 (Ewald)");
+    if (s->coulomb_mode == 1) {
+        if (!(s->dsf_alpha > 0) || s->pme_order < 4 || s->pme_order > 8 || !(s->pme_spacing > 0))
+            FAIL(MD_EINVAL, "md_set_system: Ewald needs dsf_alpha > 0, pme_order in [4, 8], pme_spacing > 0");
+        if (!(s->box / s->pme_spacing <= 1024))
+            FAIL(MD_EINVAL, "md_set_system: PME grid above 1024 points per edge");
+    }
     if (s->n_rings < 0 || s->n_rings > MAX_RINGS)
         FAIL(MD_EINVAL, "md_set_system: n_rings must be in [0, %d]", MAX_RINGS);
     for (int y = 1; y < s->n_rings; ++y) {
@@ -678,6 +757,46 @@ int commit(md_ctx* ctx)
     AL(d.flags, 2 * R); AL(d.err, R); AL(d.ovf, R); AL(d.cnt, (size_t)R * NCOUNT); AL(d.energy, 6 * R);
     AL(d.step_base, R); AL(d.stepc, 2 * R);
     AL(d.vkey, N); AL(d.vhist, (size_t)R * RATE_BUCKETS); AL(d.vofs, (size_t)R * RATE_BUCKETS);
+    // smooth PME grids of the Ewald replicas, each part starting on a 512-byte boundary
+    ctx->ewald_reps.clear();
+    long long gtot = 0, stot = 0;
+    ctx->pme_kmax = 0;
+    for (int r = 0; r < R; ++r) {
+        RepParams& P = ctx->hp[r];
+        if (P.coul_mode != 1) continue;
+        const long long K = P.pme_K;
+        P.pme_goff = gtot;
+        P.pme_soff = stot;
+        gtot += (K * K * K + 63) / 64 * 64;
+        stot += (K * K * (K / 2 + 1) + 31) / 32 * 32;
+        ctx->ewald_reps.push_back(r);
+        ctx->pme_kmax = std::max(ctx->pme_kmax, P.pme_K);
+    }
+    ctx->pme_total = gtot;
+    {
+        double* dG;
+        AL(d.pme_qi, gtot); AL(d.pme_q, gtot); AL(d.pme_spec, stot); AL(dG, stot); AL(d.pme_e, R);
+        d.pme_G = dG;
+        if (gtot) {
+            std::vector<double> G(stot, 0.0);
+            for (int r : ctx->ewald_reps) make_pme_G(ctx->hp[r], &G[ctx->hp[r].pme_soff]);
+            if ((rc = upload(ctx, dG, G.data(), G.size()))) return rc;
+            CK(cudaMemsetAsync(d.pme_qi, 0, sizeof(unsigned long long) * gtot, ctx->s));
+        }
+        for (int r : ctx->ewald_reps) {
+            const int K = ctx->hp[r].pme_K;
+            bool have = false;
+            for (auto& f : ctx->fft) have |= f.K == K;
+            if (have) continue;
+            md_ctx::FftPlan f{K, 0, 0};
+            if (cufftPlan3d(&f.d2z, K, K, K, CUFFT_D2Z) != CUFFT_SUCCESS) FAIL(MD_ECUDA, "cufftPlan3d (D2Z, K = %d) failed", K);
+            if (cufftPlan3d(&f.z2d, K, K, K, CUFFT_Z2D) != CUFFT_SUCCESS) {
+                cufftDestroy(f.d2z);
+                FAIL(MD_ECUDA, "cufftPlan3d (Z2D, K = %d) failed", K);
+            }
+            ctx->fft.push_back(f);
+        }
+    }
     uint16_t* dtab;
     AL(dtab, (size_t)R * SHELL_BINS);
     d.shell_tab = dtab;
@@ -839,13 +958,62 @@ int tpa_for(md_ctx* ctx, int mode)
     return pick;
 }
 
-void force(md_ctx* ctx, int mode, double* out)
+// does gradient mode `mode` carry the Ewald reciprocal part in some replica?
+bool mode_has_recip(const md_ctx* ctx, int mode)
 {
-    const int t = mode == 1 ? 1 : tpa_for(ctx, mode);
-    const bool bonded = mode == 0 || mode == 1 || mode == 5;
-    Prof p(ctx, mode == 1 ? 1 : 0, (bonded && ctx->d.nbond + ctx->d.nang > 0) ? 2 : 1);
-    launch_force(ctx->d, mode, out, 0, ctx->fp64, t, ctx->s);
+    return !ctx->ewald_reps.empty() && (mode == 0 || mode == 2 || mode == 4 || mode == 5 || mode == 6);
 }
+
+const md_ctx::FftPlan* fft_plan(const md_ctx* ctx, int K)
+{
+    for (const auto& f : ctx->fft)
+        if (f.K == K) return &f;
+    return nullptr;
+}
+
+// smooth PME on every Ewald replica: with out, the gradient (added to out, as
+// -grad / m~ unless as_grad); with energy, the reciprocal energies into d.pme_e
+int pme(md_ctx* ctx, double* out, int as_grad, int energy)
+{
+    Dev& d = ctx->d;
+    Prof p(ctx, 6, 3 + (out ? 1 : 0));
+    launch_pme_spread(d, ctx->fp64, ctx->s);
+    launch_pme_tofloat(d, ctx->pme_total, ctx->s);
+    for (int r : ctx->ewald_reps) {
+        const RepParams& P = ctx->hp[r];
+        const md_ctx::FftPlan* f = fft_plan(ctx, P.pme_K);
+        if (cufftSetStream(f->d2z, ctx->s) != CUFFT_SUCCESS ||
+            cufftExecD2Z(f->d2z, d.pme_q + P.pme_goff, (cufftDoubleComplex*)(d.pme_spec + P.pme_soff)) != CUFFT_SUCCESS)
+            FAIL(MD_ECUDA, "cuFFT forward transform failed");
+    }
+    launch_pme_convolve_grid(d, energy, ctx->pme_kmax, ctx->s);
+    if (!out) return MD_OK;
+    for (int r : ctx->ewald_reps) {
+        const RepParams& P = ctx->hp[r];
+        const md_ctx::FftPlan* f = fft_plan(ctx, P.pme_K);
+        if (cufftSetStream(f->z2d, ctx->s) != CUFFT_SUCCESS ||
+            cufftExecZ2D(f->z2d, (cufftDoubleComplex*)(d.pme_spec + P.pme_soff), d.pme_q + P.pme_goff) != CUFFT_SUCCESS)
+            FAIL(MD_ECUDA, "cuFFT inverse transform failed");
+    }
+    launch_pme_gather(d, out, as_grad, ctx->fp64, ctx->s);
+    return MD_OK;
+}
+
+// gradient mode into out (as -grad / m~ unless as_grad); mode 6 = the reciprocal part alone
+void force_into(md_ctx* ctx, int mode, double* out, int as_grad)
+{
+    if (mode == 6) {
+        cudaMemsetAsync(out, 0, sizeof(double) * 3 * (size_t)ctx->d.N, ctx->s);
+    } else {
+        const int t = mode == 1 ? 1 : tpa_for(ctx, mode);
+        const bool bonded = mode == 0 || mode == 1 || mode == 5;
+        Prof p(ctx, mode == 1 ? 1 : 0, (bonded && ctx->d.nbond + ctx->d.nang > 0) ? 2 : 1);
+        launch_force(ctx->d, mode, out, as_grad, ctx->fp64, t, ctx->s);
+    }
+    if (mode_has_recip(ctx, mode)) pme(ctx, out, as_grad, 0);
+}
+
+void force(md_ctx* ctx, int mode, double* out) { force_into(ctx, mode, out, 0); }
 
 void rebuild_step(md_ctx* ctx)
 {
@@ -1025,8 +1193,8 @@ int run_units(md_ctx* ctx, int key, double tau, int spu, long long units, Body b
             CK(cudaStreamWaitEvent(ctx->gs, e, 0));
             ctx->ev_pool.push_back(e);
             cudaStream_t s0 = ctx->s;
-            long long before[6];
-            std::copy(ctx->nlaunch, ctx->nlaunch + 6, before);
+            long long before[NPROF];
+            std::copy(ctx->nlaunch, ctx->nlaunch + NPROF, before);
             cudaGraph_t graph = nullptr;
             cudaGraphExec_t exec = nullptr;
             ctx->s = ctx->gs;
@@ -1043,12 +1211,12 @@ int run_units(md_ctx* ctx, int key, double tau, int spu, long long units, Body b
                 // no graph: fall back to plain launches for good
                 cudaGetLastError();
                 ctx->graphs_broken = true;
-                std::copy(before, before + 6, ctx->nlaunch);
+                std::copy(before, before + NPROF, ctx->nlaunch);
                 CK(cudaStreamSynchronize(ctx->gs));
             } else {
                 md_ctx::Graph ng{ctx->gen, key, tau, spu, (int)G, exec, {}};
-                for (int c = 0; c < 6; ++c) ng.launches[c] = ctx->nlaunch[c] - before[c] + (c == 5 ? 1 : 0);
-                std::copy(before, before + 6, ctx->nlaunch);
+                for (int c = 0; c < NPROF; ++c) ng.launches[c] = ctx->nlaunch[c] - before[c] + (c == 5 ? 1 : 0);
+                std::copy(before, before + NPROF, ctx->nlaunch);
                 ctx->graphs.push_back(ng);
                 g = &ctx->graphs.back();
             }
@@ -1059,7 +1227,7 @@ int run_units(md_ctx* ctx, int key, double tau, int spu, long long units, Body b
             CK(cudaStreamWaitEvent(ctx->gs, e, 0));
             while (units - done >= G) {
                 CK(cudaGraphLaunch(g->exec, ctx->gs));
-                for (int c = 0; c < 6; ++c) ctx->nlaunch[c] += g->launches[c];
+                for (int c = 0; c < NPROF; ++c) ctx->nlaunch[c] += g->launches[c];
                 done += G;
             }
             CK(cudaEventRecord(e, ctx->gs));
@@ -1325,26 +1493,45 @@ int md_step_baoab_respa1(md_ctx* ctx, int64_t n_outer, double dt_inner_fs, int m
     });
 }
 
-static int jump_respa_cycles(md_ctx* ctx, int64_t cycles, double dt_inner_fs, int n_inner)
+// JUMP-RESPA (ratio 1, outer period Delta = n_inner dt) and JUMP-RESPA1
+// (mid period kappa = n_inner dt, outer Delta = ratio kappa): C'J' at the mid
+// level around bonded inner steps; the Ewald reciprocal part, when a replica
+// has one, is kicked at the outer level around each group of `ratio` cycles.
+static int jump_respa_cycles(md_ctx* ctx, int64_t n_outer, double dt_inner_fs, int n_inner, int ratio)
 {
     Dev& d = ctx->d;
-    const double dt = dt_inner_fs * 1e-3, D = dt * n_inner;
+    const bool ew = !ctx->ewald_reps.empty();
+    const double dt = dt_inner_fs * 1e-3, kap = dt * n_inner, D = kap * ratio;
     int rc;
     if ((rc = set_stepc(ctx, dt))) return rc;
     force(ctx, 1, d.ab);
     force(ctx, 3, d.as);
-    // as in md_step_jump, adjacent C' phases of consecutive cycles share a launch in mixed mode
+    if (ew) force(ctx, 6, d.al);
+    // with no outer force a unit is one mid cycle; else one outer step of ratio cycles
+    const int per = ew ? ratio : 1;
+    const long long units = ew ? n_outer : n_outer * ratio;
+    // as in md_step_jump, adjacent C' phases of consecutive cycles share a launch in
+    // mixed mode (not across an outer kick, which changes the velocities in between)
     const bool fuse = !ctx->fp64;
-    return run_units(ctx, 4, dt, n_inner, cycles, [&](long long u0, long long n) {
-        uint32_t s = uint32_t(u0 * n_inner);
+    return run_units(ctx, 4 | (n_inner << 8), dt, per * n_inner, units, [&](long long u0, long long n) {
+        uint32_t s = uint32_t(u0 * per * n_inner);
         for (long long o = 0; o < n; ++o) {
-            const uint32_t s0 = s;
-            if (o == 0 || !fuse) vphase(ctx, d.as, 0.5 * D, s0, 0, 0);
-            for (int k = 0; k < n_inner; ++k, ++s) inner_bonded(ctx, dt, s, k == n_inner - 1);
-            rebuild_step(ctx);
-            force(ctx, 3, d.as);
-            if (fuse && o + 1 < n) vphase(ctx, d.as, 0.5 * D, s0, 1, 2, s);
-            else vphase(ctx, d.as, 0.5 * D, s0, 1, 1);
+            if (ew) kick(ctx, d.al, 0.5 * D);
+            for (int j = 0; j < per; ++j) {
+                const uint32_t s0 = s;
+                const bool carried = fuse && (ew ? j > 0 : o > 0);
+                const bool pass_on = fuse && (ew ? j + 1 < per : o + 1 < n);
+                if (!carried) vphase(ctx, d.as, 0.5 * kap, s0, 0, 0);
+                for (int k = 0; k < n_inner; ++k, ++s) inner_bonded(ctx, dt, s, k == n_inner - 1);
+                rebuild_step(ctx);
+                force(ctx, 3, d.as);
+                if (pass_on) vphase(ctx, d.as, 0.5 * kap, s0, 1, 2, s);
+                else vphase(ctx, d.as, 0.5 * kap, s0, 1, 1);
+            }
+            if (ew) {
+                force(ctx, 6, d.al);
+                kick(ctx, d.al, 0.5 * D);
+            }
         }
     });
 }
@@ -1354,7 +1541,7 @@ int md_step_jump_respa(md_ctx* ctx, int64_t n_outer, double dt_inner_fs, int n_i
     int rc = prepare(ctx, 2, dt_inner_fs);
     if (rc) return rc;
     if (n_outer < 0 || n_inner < 1) FAIL(MD_EINVAL, "n_outer >= 0 and n_inner >= 1 required");
-    return jump_respa_cycles(ctx, n_outer, dt_inner_fs, n_inner);
+    return jump_respa_cycles(ctx, n_outer, dt_inner_fs, n_inner, 1);
 }
 
 int md_step_jump_respa1(md_ctx* ctx, int64_t n_outer, double dt_inner_fs, int m_mid, int n_outer_ratio)
@@ -1362,7 +1549,7 @@ int md_step_jump_respa1(md_ctx* ctx, int64_t n_outer, double dt_inner_fs, int m_
     int rc = prepare(ctx, 2, dt_inner_fs);
     if (rc) return rc;
     if (n_outer < 0 || m_mid < 1 || n_outer_ratio < 1) FAIL(MD_EINVAL, "n_outer >= 0, m_mid >= 1, n_outer_ratio >= 1 required");
-    return jump_respa_cycles(ctx, n_outer * n_outer_ratio, dt_inner_fs, m_mid);
+    return jump_respa_cycles(ctx, n_outer, dt_inner_fs, m_mid, n_outer_ratio);
 }
 
 int md_observables(md_ctx* ctx, int replica, md_obs* out)
@@ -1374,6 +1561,14 @@ int md_observables(md_ctx* ctx, int replica, md_obs* out)
     Dev& d = ctx->d;
     CK(cudaMemsetAsync(d.energy, 0, sizeof(double) * 6 * d.R, ctx->s));
     launch_energy(d, ctx->s);
+    double erec = 0.0;
+    const bool ew = ctx->hp[replica].coul_mode == 1;
+    if (ew) {
+        CK(cudaMemsetAsync(d.pme_e, 0, sizeof(double) * d.R, ctx->s));
+        if ((rc = pme(ctx, nullptr, 0, 1))) return rc;
+        launch_pme_excl_energy(d, ctx->s);
+        CK(cudaMemcpyAsync(&erec, d.pme_e + replica, sizeof erec, cudaMemcpyDeviceToHost, ctx->s));
+    }
     CK(cudaGetLastError());
     double e[6];
     unsigned long long c[NCOUNT];
@@ -1387,6 +1582,7 @@ int md_observables(md_ctx* ctx, int replica, md_obs* out)
     const int n = ctx->reps[replica].n;
     std::memset(out, 0, sizeof *out);
     out->pe_bond = e[0]; out->pe_angle = e[1]; out->pe_lj = e[2]; out->pe_coul = e[3];
+    if (ew) out->pe_coul += erec + ctx->hp[replica].pme_self;
     out->ke = e[4];
     out->temperature = 2.0 * e[4] / (3.0 * n * KB);
     out->step = st;
@@ -1418,13 +1614,13 @@ int md_get_state(md_ctx* ctx, int replica, double* x, double* v, int* img, doubl
 int md_gradient(md_ctx* ctx, int replica, int mode, double* host_grad)
 {
     if (!ctx || !host_grad) return MD_EINVAL;
-    if (mode < 0 || mode > 5) FAIL(MD_EINVAL, "gradient mode %d out of range", mode);
+    if (mode < 0 || mode > 6) FAIL(MD_EINVAL, "gradient mode %d out of range", mode);
     int rc = commit(ctx);
     if (rc) return rc;
     if (replica < 0 || replica >= ctx->d.R) FAIL(MD_EINVAL, "replica %d out of range", replica);
     if ((rc = ensure_kinds(ctx, mode_list(ctx, mode)))) return rc;
     Dev& d = ctx->d;
-    launch_force(d, mode, d.gout, 1, ctx->fp64, (mode == 1 || ctx->fp64) ? 1 : tpa_for(ctx, mode), ctx->s);
+    force_into(ctx, mode, d.gout, 1);
     CK(cudaGetLastError());
     const size_t o = 3 * (size_t)ctx->rep_atom_off[replica], n3 = 3 * (size_t)ctx->reps[replica].n;
     CK(cudaMemcpyAsync(host_grad, d.gout + o, n3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
@@ -1515,10 +1711,10 @@ int md_profile(md_ctx* ctx, int enable, int reset, double* ms_out, int64_t* grou
         collect_profile(ctx);
     }
     if (reset) {
-        for (int k = 0; k < 6; ++k) { ctx->prof_ms[k] = 0; ctx->prof_groups[k] = 0; }
+        for (int k = 0; k < NPROF; ++k) { ctx->prof_ms[k] = 0; ctx->prof_groups[k] = 0; }
     }
     if (enable == 0 || enable == 1) ctx->prof = enable == 1;
-    for (int k = 0; k < 6; ++k) {
+    for (int k = 0; k < NPROF; ++k) {
         if (ms_out) ms_out[k] = ctx->prof_ms[k];
         if (groups_out) groups_out[k] = ctx->prof_groups[k];
         if (launches_out) launches_out[k] = ctx->nlaunch[k];
@@ -1533,6 +1729,7 @@ int md_finalize(md_ctx* ctx)
     drop_graphs(ctx);
     free_device(ctx);
     cudaStreamSynchronize(ctx->s);
+    for (auto& f : ctx->fft) { cufftDestroy(f.d2z); cufftDestroy(f.z2d); }
     if (ctx->gs) cudaStreamDestroy(ctx->gs);
     for (auto& p : ctx->pend) { ctx->ev_pool.push_back(p.a); ctx->ev_pool.push_back(p.b); }
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
