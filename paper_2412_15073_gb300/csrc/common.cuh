@@ -81,7 +81,9 @@ struct RepParams {
     float r2s, r2f;            // (r_c + skin)^2, (r_E + skin)^2: short and full lists
     // Ewald electrostatics (coul_mode 1): real space is the DSF form with eR = fR = 0
     // (erfc(a r)/r cut at r_E); the reciprocal part is a smooth-PME sum on a K^3 grid
-    int coul_mode, pme_p, pme_K, pad4;
+    int coul_mode, pme_p, pme_K;
+    int pme_nb, pme_boff;               // bricks of PME_BRICK^3 grid points per edge, first brick
+    int pad4;
     long long pme_goff, pme_soff;       // offsets of this replica's real grid and spectrum
     double pme_self;                    // -C a / sqrt(pi) sum q^2 (kcal/mol)
     LJPair lj[MAX_TYPES * MAX_TYPES];
@@ -91,6 +93,9 @@ struct RepParams {
 // bin (bit = list kind), or SHELL_AMB when a ring or LJ shell limit lies
 // within the bin or its tolerance margin (decided in FP64 then)
 constexpr int SHELL_BINS = 2048;
+// smooth PME: the grid is processed in bricks of PME_BRICK^3 points; atoms are
+// binned by the brick that holds floor(u), u = K x / L
+constexpr int PME_BRICK = 8;
 
 // bits of the per-replica overflow word: list kind k sets bit k; these two
 // are the outer candidate list and a cell above the in-block sort capacity

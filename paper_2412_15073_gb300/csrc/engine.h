@@ -71,7 +71,12 @@ struct Dev {
     double* pme_q;
     double2* pme_spec;
     const double* pme_G;
+    const float* pme_Gf;            // G in FP32 (mixed mode; pme_q and pme_spec then hold FP32 data)
     double* pme_e;                  // [R] reciprocal energy of the last md_observables
+    int *pme_brick, *pme_slot, *pme_sorted;   // per atom: brick, slot in it; atoms ordered by brick
+    int *pme_bcnt, *pme_bstart;     // per brick: atom count, first sorted position ([nbricks + 1])
+    const int* pme_brick_rep;       // brick -> replica
+    int pme_nbricks;
     // accepted-jump log
     long long* ev;
     unsigned long long* ev_n;
@@ -97,14 +102,17 @@ void launch_advance(const Dev& d, long long nsteps, cudaStream_t s);
 // ---- smooth PME (k_pme.cu) -----------------------------------------------------------------
 // Reciprocal part of Ewald electrostatics for the replicas with coul_mode 1; the host runs
 // the cuFFT transforms between these launches:
-//   spread (charges on the fixed-point grid) -> tofloat (real grid, clears the fixed-point
-//   one) -> forward FFT -> convolve (times G; energy != 0 also sums the energy into pme_e)
-//   -> inverse FFT (potential grid) -> gather (gradient + exclusion correction into out,
-//   as -grad / m~ unless as_grad).
-void launch_pme_spread(const Dev& d, int fp64, cudaStream_t s);
-void launch_pme_tofloat(const Dev& d, long long total, cudaStream_t s);
-void launch_pme_convolve_grid(const Dev& d, int energy, int kmax, cudaStream_t s);
-void launch_pme_gather(const Dev& d, double* out, int as_grad, int fp64, cudaStream_t s);
+//   bin (atoms ordered by grid brick, 3 kernels) -> spread (per brick in shared memory, then
+//   added to the fixed-point grid) -> tofloat (real grid; clears the fixed-point one)
+//   -> forward FFT -> convolve (times G; energy != 0 also sums the energy into pme_e)
+//   -> inverse FFT (potential grid) -> gather (per brick: gradient + exclusion correction
+//   added to out, as -grad / m~ unless as_grad).
+// spread and gather run once per B-spline order present (order: its replicas only).
+void launch_pme_bin(const Dev& d, int fp64, cudaStream_t s);
+void launch_pme_spread(const Dev& d, int order, int fp64, cudaStream_t s);
+void launch_pme_tofloat(const Dev& d, long long total, int fp64, cudaStream_t s);
+void launch_pme_convolve_grid(const Dev& d, int energy, long long max_spec, int fp64, cudaStream_t s);
+void launch_pme_gather(const Dev& d, int order, double* out, int as_grad, int fp64, cudaStream_t s);
 // exclusion-correction energy of each Ewald replica, added to d.energy[6 r + 3]
 void launch_pme_excl_energy(const Dev& d, cudaStream_t s);
 

@@ -147,8 +147,9 @@ struct md_ctx {
     struct FftPlan { int K; cufftHandle d2z, z2d; };
     std::vector<FftPlan> fft;
     std::vector<int> ewald_reps;
-    long long pme_total = 0;    // grid points over all Ewald replicas
-    int pme_kmax = 0;
+    std::vector<int> pme_orders;    // B-spline orders present
+    long long pme_total = 0;        // grid points over all Ewald replicas
+    long long pme_max_spec = 0;     // largest half spectrum
     // pinned staging
     double* h_stepc = nullptr;
     uint32_t* h_err = nullptr;
@@ -759,28 +760,52 @@ int commit(md_ctx* ctx)
     AL(d.vkey, N); AL(d.vhist, (size_t)R * RATE_BUCKETS); AL(d.vofs, (size_t)R * RATE_BUCKETS);
     // smooth PME grids of the Ewald replicas, each part starting on a 512-byte boundary
     ctx->ewald_reps.clear();
+    ctx->pme_orders.clear();
     long long gtot = 0, stot = 0;
-    ctx->pme_kmax = 0;
+    int nbricks = 0;
+    ctx->pme_max_spec = 0;
     for (int r = 0; r < R; ++r) {
         RepParams& P = ctx->hp[r];
         if (P.coul_mode != 1) continue;
         const long long K = P.pme_K;
         P.pme_goff = gtot;
         P.pme_soff = stot;
+        P.pme_nb = (P.pme_K + PME_BRICK - 1) / PME_BRICK;
+        P.pme_boff = nbricks;
+        nbricks += P.pme_nb * P.pme_nb * P.pme_nb;
         gtot += (K * K * K + 63) / 64 * 64;
         stot += (K * K * (K / 2 + 1) + 31) / 32 * 32;
         ctx->ewald_reps.push_back(r);
-        ctx->pme_kmax = std::max(ctx->pme_kmax, P.pme_K);
+        ctx->pme_max_spec = std::max(ctx->pme_max_spec, K * K * (K / 2 + 1));
+        if (std::find(ctx->pme_orders.begin(), ctx->pme_orders.end(), P.pme_p) == ctx->pme_orders.end())
+            ctx->pme_orders.push_back(P.pme_p);
     }
     ctx->pme_total = gtot;
     {
         double* dG;
-        AL(d.pme_qi, gtot); AL(d.pme_q, gtot); AL(d.pme_spec, stot); AL(dG, stot); AL(d.pme_e, R);
+        float* dGf;
+        int* dbrep;
+        AL(d.pme_qi, gtot); AL(d.pme_q, gtot); AL(d.pme_spec, stot); AL(dG, stot); AL(dGf, stot); AL(d.pme_e, R);
+        AL(d.pme_brick, N); AL(d.pme_slot, N); AL(d.pme_sorted, N);
+        AL(d.pme_bcnt, nbricks); AL(d.pme_bstart, nbricks + 1); AL(dbrep, nbricks);
         d.pme_G = dG;
+        d.pme_Gf = dGf;
+        d.pme_brick_rep = dbrep;
+        d.pme_nbricks = nbricks;
+        if (nbricks) {
+            std::vector<int> brep(nbricks);
+            for (int r : ctx->ewald_reps) {
+                const RepParams& P = ctx->hp[r];
+                for (int b = 0; b < P.pme_nb * P.pme_nb * P.pme_nb; ++b) brep[P.pme_boff + b] = r;
+            }
+            if ((rc = upload(ctx, dbrep, brep.data(), brep.size()))) return rc;
+            CK(cudaMemsetAsync(d.pme_bcnt, 0, sizeof(int) * nbricks, ctx->s));
+        }
         if (gtot) {
             std::vector<double> G(stot, 0.0);
             for (int r : ctx->ewald_reps) make_pme_G(ctx->hp[r], &G[ctx->hp[r].pme_soff]);
-            if ((rc = upload(ctx, dG, G.data(), G.size()))) return rc;
+            std::vector<float> Gf(G.begin(), G.end());
+            if ((rc = upload(ctx, dG, G.data(), G.size())) || (rc = upload(ctx, dGf, Gf.data(), Gf.size()))) return rc;
             CK(cudaMemsetAsync(d.pme_qi, 0, sizeof(unsigned long long) * gtot, ctx->s));
         }
         for (int r : ctx->ewald_reps) {
@@ -788,11 +813,13 @@ int commit(md_ctx* ctx)
             bool have = false;
             for (auto& f : ctx->fft) have |= f.K == K;
             if (have) continue;
+            // FP64 transforms in FP64 mode, FP32 in mixed mode
             md_ctx::FftPlan f{K, 0, 0};
-            if (cufftPlan3d(&f.d2z, K, K, K, CUFFT_D2Z) != CUFFT_SUCCESS) FAIL(MD_ECUDA, "cufftPlan3d (D2Z, K = %d) failed", K);
-            if (cufftPlan3d(&f.z2d, K, K, K, CUFFT_Z2D) != CUFFT_SUCCESS) {
+            const cufftType fw = ctx->fp64 ? CUFFT_D2Z : CUFFT_R2C, bw = ctx->fp64 ? CUFFT_Z2D : CUFFT_C2R;
+            if (cufftPlan3d(&f.d2z, K, K, K, fw) != CUFFT_SUCCESS) FAIL(MD_ECUDA, "cufftPlan3d (forward, K = %d) failed", K);
+            if (cufftPlan3d(&f.z2d, K, K, K, bw) != CUFFT_SUCCESS) {
                 cufftDestroy(f.d2z);
-                FAIL(MD_ECUDA, "cufftPlan3d (Z2D, K = %d) failed", K);
+                FAIL(MD_ECUDA, "cufftPlan3d (inverse, K = %d) failed", K);
             }
             ctx->fft.push_back(f);
         }
@@ -976,26 +1003,33 @@ const md_ctx::FftPlan* fft_plan(const md_ctx* ctx, int K)
 int pme(md_ctx* ctx, double* out, int as_grad, int energy)
 {
     Dev& d = ctx->d;
-    Prof p(ctx, 6, 3 + (out ? 1 : 0));
-    launch_pme_spread(d, ctx->fp64, ctx->s);
-    launch_pme_tofloat(d, ctx->pme_total, ctx->s);
+    const int no = (int)ctx->pme_orders.size();
+    Prof p(ctx, 6, 5 + no + (out ? no : 0));
+    launch_pme_bin(d, ctx->fp64, ctx->s);
+    for (int order : ctx->pme_orders) launch_pme_spread(d, order, ctx->fp64, ctx->s);
+    launch_pme_tofloat(d, ctx->pme_total, ctx->fp64, ctx->s);
+    // the FP32 grids of mixed mode live in the same buffers, at the same element offsets
+    float* qf = reinterpret_cast<float*>(d.pme_q);
+    cufftComplex* sf = reinterpret_cast<cufftComplex*>(d.pme_spec);
     for (int r : ctx->ewald_reps) {
         const RepParams& P = ctx->hp[r];
         const md_ctx::FftPlan* f = fft_plan(ctx, P.pme_K);
-        if (cufftSetStream(f->d2z, ctx->s) != CUFFT_SUCCESS ||
-            cufftExecD2Z(f->d2z, d.pme_q + P.pme_goff, (cufftDoubleComplex*)(d.pme_spec + P.pme_soff)) != CUFFT_SUCCESS)
-            FAIL(MD_ECUDA, "cuFFT forward transform failed");
+        const cufftResult e = cufftSetStream(f->d2z, ctx->s) != CUFFT_SUCCESS ? CUFFT_INTERNAL_ERROR
+            : ctx->fp64 ? cufftExecD2Z(f->d2z, d.pme_q + P.pme_goff, (cufftDoubleComplex*)(d.pme_spec + P.pme_soff))
+                        : cufftExecR2C(f->d2z, qf + P.pme_goff, sf + P.pme_soff);
+        if (e != CUFFT_SUCCESS) FAIL(MD_ECUDA, "cuFFT forward transform failed (%d)", (int)e);
     }
-    launch_pme_convolve_grid(d, energy, ctx->pme_kmax, ctx->s);
+    launch_pme_convolve_grid(d, energy, ctx->pme_max_spec, ctx->fp64, ctx->s);
     if (!out) return MD_OK;
     for (int r : ctx->ewald_reps) {
         const RepParams& P = ctx->hp[r];
         const md_ctx::FftPlan* f = fft_plan(ctx, P.pme_K);
-        if (cufftSetStream(f->z2d, ctx->s) != CUFFT_SUCCESS ||
-            cufftExecZ2D(f->z2d, (cufftDoubleComplex*)(d.pme_spec + P.pme_soff), d.pme_q + P.pme_goff) != CUFFT_SUCCESS)
-            FAIL(MD_ECUDA, "cuFFT inverse transform failed");
+        const cufftResult e = cufftSetStream(f->z2d, ctx->s) != CUFFT_SUCCESS ? CUFFT_INTERNAL_ERROR
+            : ctx->fp64 ? cufftExecZ2D(f->z2d, (cufftDoubleComplex*)(d.pme_spec + P.pme_soff), d.pme_q + P.pme_goff)
+                        : cufftExecC2R(f->z2d, sf + P.pme_soff, qf + P.pme_goff);
+        if (e != CUFFT_SUCCESS) FAIL(MD_ECUDA, "cuFFT inverse transform failed (%d)", (int)e);
     }
-    launch_pme_gather(d, out, as_grad, ctx->fp64, ctx->s);
+    for (int order : ctx->pme_orders) launch_pme_gather(d, order, out, as_grad, ctx->fp64, ctx->s);
     return MD_OK;
 }
 

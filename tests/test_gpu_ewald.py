@@ -42,8 +42,9 @@ def perturbed(w, seed=3):
     return w
 
 
-# spacing 0.8 A gives K = 24 on the 18.6 A box, 0.7 A an odd K = 27
-@pytest.mark.parametrize("spacing,order", [(0.8, 6), (0.7, 4), (0.8, 8)])
+# spacing 0.8 A gives K = 24 on the 18.6 A box, 0.7 A an odd K = 27, 1.6 A
+# K = 12, where the 13-point region of a grid brick wraps onto itself
+@pytest.mark.parametrize("spacing,order", [(0.8, 6), (0.7, 4), (0.8, 8), (1.6, 6)])
 @pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-5)])
 def test_ewald_gradients(M, oracle_mod, water648, precision, tol, spacing, order):
     w = perturbed(water648)
