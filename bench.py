@@ -37,11 +37,20 @@ PARAMS = dict(r_cut=10.0, r_split=5.0, h_switch=0.5, r_mid=5.5, dsf_alpha=0.2, g
 # BAOAB takes the 0.5 A skin that minimises its pair-force plus rebuild time
 JUMP_PARAMS = PARAMS | dict(ring_r=[5.25, 6.0, 7.5], skin=0.3)
 BAOAB_PARAMS = PARAMS
-DT_FS = 1.0
-METRIC = "ns/day & Gpair-evals/s, JUMP vs BAOAB on 1 GB300 at matched T/D (97k atoms)"
-WORKLOAD = ("water 96,000 atoms (32,000 flexible 3-site waters, 98.6 A cube), LJ+DSF r_E 10 A, "
-            "r_c 5 A, rings at 5.25/6/7.5 A, adaptive eps0 0.1, 300 K, gamma 1/ps; JUMP 1 fs vs BAOAB 1 fs")
+# Ewald regime (the paper's electrostatics and its 96,000-atom JUMP settings):
+# real space erfc(a r)/r to r_E = 10 A with a = 0.42/A, smooth PME (order 6,
+# 0.8 A grid: K = 125), short-range split r_c = 6 A (rings at 6.25 / 7 / 8.5 A).
+# The jumps replace only the (1 - chi) real-space part, whose forces the
+# reciprocal sum has made weak; as in the paper's GPU runs the long-range LJ
+# part is deterministic (lj_long_mode 1: LJ bounces reflect velocities and
+# slow diffusion). Multiple-time-step levels 1:2:6 fs as in the paper.
+EWALD = dict(dsf_alpha=0.42, coulomb_mode=1, pme_order=6, pme_spacing=0.8, r_split=6.0)
+EWALD_EPS0 = [0.1, 1.0]
+EWALD_JUMP_PARAMS = JUMP_PARAMS | EWALD | dict(ring_r=[6.25, 7.0, 8.5], lj_long_mode=1)
+EWALD_BAOAB_PARAMS = BAOAB_PARAMS | EWALD
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# launch classes of md_profile
+CLASSES = ["pair_force", "bonded", "velocity_phase", "kick_aoa", "list_rebuild", "bookkeeping", "ewald_recip"]
 # FP32 work of one pair of the pair kernel (min image, r^2, erfc/exp, DSF, LJ,
 # switch, fixed point) and of one jump proposal (Philox rounds, log, bound,
 # ring pick, gathers, pair gradient, Theta, accept), counted from the kernels
@@ -272,6 +281,75 @@ def e2e_run(ej, args, M, torch, stream, n, world, max_over_ranks, barrier):
             "path": "md_set_state(host) + md_step_jump(K) + md_get_state(host) per bench step of K MD steps"}
 
 
+def ewald_leg(args, M, engine, timed, stream, world, max_over_ranks, barrier):
+    """JUMP-RESPA1 against BAOAB-RESPA1 under Ewald electrostatics (smooth PME
+    at the outer level of both): ns/day, temperature and oxygen self-diffusion
+    of each, on the same equilibrated start. delta 1 fs (bonded), kappa 2 fs
+    (short pairs, and the jumps of JUMP-RESPA1), Delta = 6 fs (reciprocal part;
+    plus the long real-space pairs for BAOAB-RESPA1, also run at Delta = 4 fs)."""
+    m_mid = 2
+    ew = dict(EWALD)
+    if args.ewald_alpha:
+        ew["dsf_alpha"] = args.ewald_alpha
+    if args.ewald_spacing:
+        ew["pme_spacing"] = args.ewald_spacing
+    jp, bp = EWALD_JUMP_PARAMS | ew, EWALD_BAOAB_PARAMS | ew
+    if args.ewald_lj_long is not None:
+        jp = jp | {"lj_long_mode": args.ewald_lj_long}
+    if args.ewald_split:
+        rc = args.ewald_split
+        jp = jp | {"r_split": rc, "ring_r": [rc + 0.25, rc + 1.0, rc + 2.5]}
+        bp = bp | {"r_split": rc}
+    res = {"electrostatics": "Ewald: erfc(a r)/r to 10 A, a = %.2f/A, smooth PME order %d, %.2f A grid"
+                             % (ew["dsf_alpha"], ew["pme_order"], ew["pme_spacing"]),
+           "split": {"r_c": jp["r_split"], "h": jp["h_switch"], "rings": jp["ring_r"],
+                     "lj_long_mode": jp["lj_long_mode"]},
+           "levels": "delta 1 fs, kappa 2 fs, Delta 6 fs (BAOAB-RESPA1 also 4 fs)"}
+    eps_list = args.ewald_eps0 or EWALD_EPS0
+    runs = [(f"jump_respa1_eps{e:g}", 5, "jump_respa1", 3, jp | {"eps0": e}) for e in eps_list]
+    runs += [(f"baoab_respa1_D{2 * q}", 6, "baoab_respa1", q, bp) for q in (3, 2)]
+    for name, seed, meth, n_out, params in runs:
+        per_cycle = m_mid * n_out
+        cyc = max(args.steps // per_cycle, 1)
+        e = engine(seed, params)
+        run = lambda k, e=e, meth=meth, n_out=n_out: getattr(e, meth)(k, 1.0, m_mid, n_out)
+        try:
+            run(max(1, 120 // per_cycle))           # settle in the Ewald force field
+            c0 = e.observables()
+            barrier()
+            t = max_over_ranks(timed(e, run, cyc, stream))
+            c1 = e.observables()
+            T = c1["temperature"]
+            r = {"ns_per_day": ns_per_day(world * cyc * per_cycle * DT_FS, t),
+                 "ms_per_fs": t / (cyc * per_cycle) * 1e3, "T": T,
+                 "stable": bool(abs(T / PARAMS["temperature"] - 1) < 0.1)}
+            if meth == "jump_respa1":
+                r["proposals_per_atom_fs"] = (c1["jump_proposals"] - c0["jump_proposals"]) / (e.n[0] * cyc * per_cycle)
+            # device time per launch class (CUDA events around each launch group, plain launches)
+            pc = max(1, 240 // per_cycle)
+            e.profile(enable=1, reset=True)
+            run(pc)
+            ms, _, _ = e.profile(enable=0)
+            r["class_ms_per_fs"] = {c: round(float(m) / (pc * per_cycle), 4) for c, m in zip(CLASSES, ms)}
+            if args.dsteps > 0 and r["stable"]:
+                every = 96                          # a multiple of both cycle lengths (4 and 6 fs)
+                r["D"] = diffusion(e, lambda k: run(k // per_cycle), args.dsteps // every * every, every, BOX, DT_FS)
+            res[name] = r
+        except M.MDError as ex:
+            res[name] = {"error": str(ex), "stable": False}
+        e.close()
+    b = res.get("baoab_respa1_D6", {})
+    if not b.get("stable"):
+        b = res.get("baoab_respa1_D4", {})
+    for k in list(res):
+        if k.startswith("jump_respa1") and "ns_per_day" in res[k] and b.get("ns_per_day"):
+            res[k]["speedup_vs_baoab_respa1"] = res[k]["ns_per_day"] / b["ns_per_day"]
+            if "D" in res[k] and b.get("D"):
+                res[k]["D_ratio"] = res[k]["D"] / b["D"]
+    res["D_unit"] = "1e-5 cm^2/s"
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -284,9 +362,19 @@ def main():
     ap.add_argument("--equil", type=int, default=1000,
                     help="BAOAB steps at gamma = 20/ps from the lattice start before timing (0 = none)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--dsteps", type=int, default=2000,
+    ap.add_argument("--dsteps", type=int, default=4000,
                     help="steps of each integrator for the diffusion constant (0 = skip)")
-    ap.add_argument("--only", default="all", choices=["all", "jump", "baoab"])
+    ap.add_argument("--only", default="all", choices=["all", "jump", "baoab", "ewald"])
+    ap.add_argument("--ewald", type=int, default=1,
+                    help="also compare JUMP-RESPA1 with BAOAB-RESPA1 under Ewald electrostatics")
+    ap.add_argument("--ewald-eps0", type=float, nargs="*", default=None,
+                    help="eps0 values of the Ewald JUMP-RESPA1 runs (default EWALD_EPS0)")
+    ap.add_argument("--ewald-alpha", type=float, default=None, help="Ewald splitting parameter (1/A)")
+    ap.add_argument("--ewald-spacing", type=float, default=None, help="PME grid spacing (A)")
+    ap.add_argument("--ewald-lj-long", type=int, default=None,
+                    help="lj_long_mode of the Ewald JUMP runs (default 1, the paper's GPU setting)")
+    ap.add_argument("--ewald-split", type=float, default=None,
+                    help="short-range split r_c of the Ewald runs (A); rings move with it")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -317,6 +405,13 @@ def main():
         e = M.Engine(precision=M.MD_MIXED, seed=ranks.seed(seed), device=local, stream=stream.cuda_stream)
         e.set_system(0, w, **params)
         return e
+
+    if args.only == "ewald":
+        out = ewald_leg(args, M, engine, timed, stream, world, max_over_ranks, barrier)
+        if rank == 0:
+            print(json.dumps({"ewald": out}), flush=True)
+        ranks.close()
+        return
 
     if args.only != "all":
         # profiling run: one integrator only, no side measurements
@@ -371,7 +466,7 @@ def main():
     ej.jump(prof_steps)
     cp1 = ej.observables()
     ms, groups, _ = ej.profile(enable=0)
-    classes = ["pair_force", "bonded", "velocity_phase", "kick_aoa", "list_rebuild", "bookkeeping", "ewald_recip"]
+    classes = CLASSES
     top = int(np.argmax(ms))
     pk, how = peaks()
     clock = (pk.get("sm_max_mhz") or 2070.0) * 1e6
@@ -431,6 +526,10 @@ def main():
                "unit": "1e-5 cm^2/s", "window_ps": args.dsteps * DT_FS * 1e-3,
                "method": "O atoms, Einstein MSD over all origins, fit over 20-80 % of the lags"}
 
+    ewald = None
+    if args.ewald:
+        ewald = ewald_leg(args, M, engine, timed, stream, world, max_over_ranks, barrier)
+
     # end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
@@ -455,6 +554,7 @@ def main():
                           "list_rebuilds": c1["list_rebuilds"] - c0["list_rebuilds"],
                           "short_pairs": pairs_short, "full_pairs": pairs_full},
            "respa1": respa,
+           "ewald": ewald,
            "roofline": roof | {"peak_kind": how},
            "e2e": e2e,
            "gpu_launches": launches,

@@ -92,6 +92,13 @@ struct RepParams {
 // shell table: per bin of r^2, the ring and LJ lists that contain the whole
 // bin (bit = list kind), or SHELL_AMB when a ring or LJ shell limit lies
 // within the bin or its tolerance margin (decided in FP64 then)
+// FP32 acceptance ratios: as eta -> 0 (pairs whose force is tiny beside the
+// 1/(eps0 sqrt(2 pi)) floor of the adaptive bound) the exact p tends to 1 from
+// below by less than FP32 rounding, and the FP32 quotient can land a few ulps
+// above 1. Such a p is no evidence of a violated bound: the decision is exact
+// anyway (U within 2e-6 of p is decided again in FP64, where the check is
+// strict), so the FP32 check flags p above 1 + P_TOL32 only.
+constexpr float P_TOL32 = 4e-6f;
 constexpr int SHELL_BINS = 2048;
 // smooth PME: the grid is processed in bricks of PME_BRICK^3 points; atoms are
 // binned by the brick that holds floor(u), u = K x / L

@@ -234,7 +234,7 @@ __device__ void cprime(const Dev& d, const RepParams& P, int i, int il, double v
                     tl.guard++;
                 } else {
                     acc = unif<T>(u.w) <= p;
-                    if (p > T(1)) err |= F_BOUND;
+                    if (p > T(1) + (sizeof(T) == 4 ? T(P_TOL32) : T(0))) err |= F_BOUND;
                 }
                 if (acc) {
                     // G~ by rejection, streams (S, half, attempt, k)
@@ -506,7 +506,7 @@ __device__ __forceinline__ void cprime_f(const Dev& d, const JC& c, const RepPar
                     tl.guard++;
                 } else {
                     acc = U <= p;
-                    if (p > 1.f) err |= F_BOUND;
+                    if (p > 1.f + P_TOL32) err |= F_BOUND;
                 }
                 if (acc) {
                     int att;

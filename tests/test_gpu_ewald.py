@@ -160,3 +160,22 @@ def test_ewald_nve_energy_error_is_second_order(M, oracle_mod, water648, precisi
     print("NVE largest total-energy excursion (kcal/mol) by dt:", drift)
     assert 3.2 < drift[0.25] / drift[0.125] < 4.8, drift
     assert drift[0.125] < 1e-3 * abs(es[0]) + 3.0, drift
+
+
+def test_ewald_weak_force_regime(M, oracle_mod, water648):
+    """the paper's 96,000-atom setting (a = 0.42/A, short cutoff 6 A, eps0 =
+    0.01): jumped forces of 1e-6 kcal/mol/A at the outer ring, acceptance
+    ratios within 1e-8 of 1. FP64: events identical to the oracle and no bound
+    flag; mixed: no bound flag either, though its FP32 ratios round above 1"""
+    kw = dict(dsf_alpha=0.42, r_split=6.0, ring_r=[6.25, 7.0, 8.5], eps0=0.01)
+    e, o = make(M, oracle_mod, water648, 0, seed=17, **kw)
+    o.events_enable(1 << 23)
+    e.jump(10)
+    o.jump(10)
+    assert o.errors == 0 and e.observables()["error_flags"] == 0
+    assert np.array_equal(sorted_events(e.events()), sorted_events(o.events()))
+    assert pos_err(e.state()[0], o.state()[0], water648.box) < 1e-6
+    em, _ = make(M, oracle_mod, water648, 1, seed=17, **kw)
+    em.jump_respa1(40, 1.0, 2, 3)
+    ob = em.observables()
+    assert ob["error_flags"] == 0 and ob["jump_proposals"] > 0
