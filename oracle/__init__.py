@@ -94,6 +94,11 @@ def lib():
         L.or_events_enable.argtypes = [vp, i64]
         L.or_events_get.restype = i64
         L.or_events_get.argtypes = [vp, vp]
+        L.or_vrec_enable.argtypes = [vp, i64]
+        L.or_vrec_get.restype = i64
+        L.or_vrec_get.argtypes = [vp, vp]
+        L.or_vacf.argtypes = [vp, vp, i, i64, i64, vp]
+        L.or_vacf_spectrum.argtypes = [vp, i64, vp]
         L.or_philox.argtypes = [vp, vp, vp]
         L.or_theta.restype = d
         L.or_theta.argtypes = [d]
@@ -288,6 +293,17 @@ class Oracle:
     def jump_respa1(self, nouter, dt_inner_fs=1.0, m_mid=2, n_outer=2):
         return self.L.or_step_jump_respa1(self.h, int(nouter), float(dt_inner_fs), int(m_mid), int(n_outer))
 
+    # velocity record -----------------------------------------------------
+    def vrec_enable(self, cap):
+        self.L.or_vrec_enable(self.h, int(cap))
+
+    def vrec(self) -> np.ndarray:
+        """the stored velocities, T x n x 3"""
+        T = self.L.or_vrec_get(self.h, None)
+        out = np.zeros((max(T, 1), self.n, 3))
+        self.L.or_vrec_get(self.h, _p(out))
+        return out[:T]
+
     # events --------------------------------------------------------------
     def events_enable(self, cap=1 << 20):
         self.L.or_events_enable(self.h, int(cap))
@@ -297,6 +313,24 @@ class Oracle:
         out = np.zeros((max(n, 1), 6), dtype=np.int64)
         self.L.or_events_get(self.h, _p(out))
         return out[:n]
+
+
+def vacf(v, mass, nlags):
+    """Mass-weighted velocity autocorrelation of a series v[T, n, 3] (or[T, 3n])
+    by its definition: C(k) = sum_t sum_i m_i v_i(t).v_i(t+k) / (T - k)."""
+    mass = np.ascontiguousarray(mass, dtype=np.float64)
+    v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1, len(mass) * 3)
+    out = np.zeros(int(nlags))
+    lib().or_vacf(_p(v), _p(mass), len(mass), v.shape[0], int(nlags), _p(out))
+    return out
+
+
+def vacf_spectrum(C):
+    """Hann-windowed cosine transform of an autocorrelation (see or_vacf_spectrum)."""
+    C = np.ascontiguousarray(C, dtype=np.float64)
+    S = np.zeros(len(C))
+    lib().or_vacf_spectrum(_p(C), len(C), _p(S))
+    return S
 
 
 def set_threads(n: int):

@@ -87,7 +87,18 @@ struct or_sys {
     /* event log */
     int64_t ev_cap, ev_n;
     int64_t *ev;
+    /* velocity record for spectra: v after each innermost step */
+    int64_t vr_cap, vr_n;
+    double* vr;
 };
+
+/* store v as the state after the innermost step that just ended (up to vr_cap samples) */
+static void vrec(or_sys* s)
+{
+    if (s->vr && s->vr_n < s->vr_cap)
+        memcpy(s->vr + 3 * (size_t)s->n * (size_t)s->vr_n, s->v, sizeof(double) * 3 * (size_t)s->n);
+    if (s->vr) s->vr_n++;
+}
 
 /* ======================================================================== */
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two     */
@@ -1296,6 +1307,7 @@ int or_step_baoab(or_sys* s, int64_t nsteps, double dt_fs)
         accel(s, 0, s->a0);
         kick(s, s->a0, 0.5 * tau);
         s->step++;
+        vrec(s);
     }
     check_finite(s);
     return (int)s->err;
@@ -1317,6 +1329,7 @@ int or_step_jump(or_sys* s, int64_t nsteps, double dt_fs)
         jphase(s, 0.5 * tau, s0, 1);
         cphase(s, s->a0, 0.5 * tau, s0, 1);
         s->step++;
+        vrec(s);
     }
     check_finite(s);
     return (int)s->err;
@@ -1340,6 +1353,7 @@ int or_step_bjaoajb(or_sys* s, int64_t nsteps, double dt_fs)
         cphase(s, zero, 0.5 * tau, s0, 1);
         kick(s, s->a0, 0.5 * tau);
         s->step++;
+        vrec(s);
     }
     free(zero);
     check_finite(s);
@@ -1347,7 +1361,7 @@ int or_step_bjaoajb(or_sys* s, int64_t nsteps, double dt_fs)
 }
 
 /* innermost RESPA step on the bonded force: B A O A [grad] B */
-static void inner_bonded(or_sys* s, double dt)
+static void inner_bonded(or_sys* s, double dt, int record)
 {
     uint32_t s0 = (uint32_t)s->step;
     kick(s, s->ab, 0.5 * dt);
@@ -1355,6 +1369,7 @@ static void inner_bonded(or_sys* s, double dt)
     accel(s, 1, s->ab);
     kick(s, s->ab, 0.5 * dt);
     s->step++;
+    if (record) vrec(s);
 }
 
 /* BAOAB-RESPA: B_nb(D/2) [n x inner bonded] B_nb(D/2), D = n dt */
@@ -1366,10 +1381,11 @@ int or_step_baoab_respa(or_sys* s, int64_t nouter, double dt_inner_fs, int n_inn
     accel(s, 2, s->al);
     for (int64_t o = 0; o < nouter; ++o) {
         kick(s, s->al, 0.5 * D);
-        for (int k = 0; k < n_inner; ++k) inner_bonded(s, dt);
+        for (int k = 0; k < n_inner; ++k) inner_bonded(s, dt, k < n_inner - 1);
         maybe_rebuild(s);
         accel(s, 2, s->al);
         kick(s, s->al, 0.5 * D);
+        vrec(s);
     }
     check_finite(s);
     return (int)s->err;
@@ -1387,14 +1403,16 @@ int or_step_baoab_respa1(or_sys* s, int64_t nouter, double dt_inner_fs, int m_mi
         kick(s, s->al, 0.5 * D);
         for (int j = 0; j < n_outer; ++j) {
             kick(s, s->as, 0.5 * kap);
-            for (int k = 0; k < m_mid; ++k) inner_bonded(s, dt);
+            for (int k = 0; k < m_mid; ++k) inner_bonded(s, dt, k < m_mid - 1);
             maybe_rebuild(s);
             accel(s, 3, s->as);
             kick(s, s->as, 0.5 * kap);
+            if (j < n_outer - 1) vrec(s);
         }
         maybe_rebuild(s);
         accel(s, 4, s->al);
         kick(s, s->al, 0.5 * D);
+        vrec(s);
     }
     check_finite(s);
     return (int)s->err;
@@ -1415,12 +1433,13 @@ int or_step_jump_respa(or_sys* s, int64_t nouter, double dt_inner_fs, int n_inne
         if (ew) kick(s, s->al, 0.5 * D);
         cphase(s, s->as, 0.5 * D, s0, 0);
         jphase(s, 0.5 * D, s0, 0);
-        for (int k = 0; k < n_inner; ++k) inner_bonded(s, dt);
+        for (int k = 0; k < n_inner; ++k) inner_bonded(s, dt, k < n_inner - 1);
         maybe_rebuild(s);
         accel(s, 3, s->as);
         jphase(s, 0.5 * D, s0, 1);
         cphase(s, s->as, 0.5 * D, s0, 1);
         if (ew) { accel(s, 6, s->al); kick(s, s->al, 0.5 * D); }
+        vrec(s);
     }
     check_finite(s);
     return (int)s->err;
@@ -1444,13 +1463,15 @@ int or_step_jump_respa1(or_sys* s, int64_t nouter, double dt_inner_fs, int m_mid
             uint32_t s0 = (uint32_t)s->step;
             cphase(s, s->as, 0.5 * kap, s0, 0);
             jphase(s, 0.5 * kap, s0, 0);
-            for (int k = 0; k < m_mid; ++k) inner_bonded(s, dt);
+            for (int k = 0; k < m_mid; ++k) inner_bonded(s, dt, k < m_mid - 1);
             maybe_rebuild(s);
             accel(s, 3, s->as);
             jphase(s, 0.5 * kap, s0, 1);
             cphase(s, s->as, 0.5 * kap, s0, 1);
+            if (j < n_outer - 1) vrec(s);
         }
         if (ew) { accel(s, 6, s->al); kick(s, s->al, 0.5 * D); }
+        vrec(s);
     }
     check_finite(s);
     return (int)s->err;
@@ -1562,6 +1583,7 @@ void or_destroy(or_sys* s)
     for (int k = 0; k < K_NKIND; ++k) { free(s->lists[k].off); free(s->lists[k].idx); free(s->alist[k]); }
     free(s->a0); free(s->ab); free(s->as); free(s->al);
     free(s->cellm); free(s->xo);
+    free(s->vr);
     free(s->ev);
     free(s);
 }
@@ -1637,4 +1659,53 @@ int64_t or_events_get(const or_sys* s, int64_t* out6)
 {
     if (out6 && s->ev_n) memcpy(out6, s->ev, sizeof(int64_t) * 6 * (size_t)s->ev_n);
     return s->ev_n;
+}
+
+void or_vrec_enable(or_sys* s, int64_t cap)
+{
+    free(s->vr);
+    s->vr = cap > 0 ? (double*)malloc(sizeof(double) * 3 * (size_t)s->n * (size_t)cap) : NULL;
+    s->vr_cap = cap;
+    s->vr_n = 0;
+}
+
+int64_t or_vrec_get(const or_sys* s, double* out)
+{
+    const int64_t k = s->vr_n < s->vr_cap ? s->vr_n : s->vr_cap;
+    if (out && k) memcpy(out, s->vr, sizeof(double) * 3 * (size_t)s->n * (size_t)k);
+    return k;
+}
+
+/* mass-weighted velocity autocorrelation, by its definition: the average
+ * over the time origins t of sum_i m_i v_i(t) . v_i(t + k) */
+void or_vacf(const double* v, const double* mass, int n, int64_t T, int64_t nlags, double* out)
+{
+    for (int64_t k = 0; k < nlags; ++k) {
+        double acc = 0.0;
+        if (k < T) {
+            for (int64_t t = 0; t + k < T; ++t) {
+                const double* a = v + 3 * (size_t)n * (size_t)t;
+                const double* b = v + 3 * (size_t)n * (size_t)(t + k);
+                for (int i = 0; i < n; ++i)
+                    acc += mass[i] * (a[3 * i] * b[3 * i] + a[3 * i + 1] * b[3 * i + 1] + a[3 * i + 2] * b[3 * i + 2]);
+            }
+            acc /= (double)(T - k);
+        }
+        out[k] = acc;
+    }
+}
+
+/* Hann-windowed cosine transform of an autocorrelation C(0..K-1):
+ * S_j = C(0) + 2 sum_{k=1}^{K-1} w_k C(k) cos(pi j k / K), w_k = (1 + cos(pi k / K)) / 2,
+ * j = 0..K-1; with samples dt apart, bin j is the frequency j / (2 K dt) */
+void or_vacf_spectrum(const double* C, int64_t K, double* S)
+{
+    for (int64_t j = 0; j < K; ++j) {
+        double acc = C[0];
+        for (int64_t k = 1; k < K; ++k) {
+            const double w = 0.5 * (1.0 + cos(OR_PI * (double)k / (double)K));
+            acc += 2.0 * w * C[k] * cos(OR_PI * (double)((j * k) % (2 * K)) / (double)K);
+        }
+        S[j] = acc;
+    }
 }

@@ -141,6 +141,19 @@ int or_step_jump_respa1(or_sys* s, int64_t nouter, double dt_inner_fs, int m_mid
 void    or_events_enable(or_sys* s, int64_t cap);
 int64_t or_events_get(const or_sys* s, int64_t* out6);
 
+/* velocity record for spectra (Sec. 4, the velocity autocorrelation spectra
+ * of the multiple-time-step integrators): v after each innermost step, taken
+ * after the closing kicks and phases of every level that ends at that step;
+ * at most cap samples are kept (later ones are counted, not stored) */
+void    or_vrec_enable(or_sys* s, int64_t cap);
+int64_t or_vrec_get(const or_sys* s, double* out);     /* T x 3n; returns T */
+/* mass-weighted VACF of a series v[T][n][3]: out[k] = (1 / (T - k))
+ * sum_{t=0}^{T-1-k} sum_i m_i v_i(t) . v_i(t + k), k < nlags (0 for k >= T) */
+void or_vacf(const double* v, const double* mass, int n, int64_t T, int64_t nlags, double* out);
+/* Hann-windowed cosine transform S_j = C(0) + 2 sum_{k=1}^{K-1} w_k C(k) cos(pi j k / K),
+ * w_k = (1 + cos(pi k / K)) / 2, j < K */
+void or_vacf_spectrum(const double* C, int64_t K, double* S);
+
 /* primitives */
 void   or_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out);
 double or_theta(double eta);
