@@ -270,6 +270,31 @@ int md_nb_gradient_noalloc(const double* d_x, const double* d_charge, const int*
                            double r_cut, double r_split, double h_switch, double dsf_alpha, int weight,
                            double* d_grad, void* cuda_stream);
 
+/* Velocity record for spectra (Sec. 4: the velocity autocorrelation spectra
+ * that show the resonances of the multiple-time-step integrators). From this
+ * call on, every md_step_* call stores the velocities of all atoms of all
+ * replicas after each innermost step, taken after the closing kicks and
+ * phases of every level that ends at that step, until n_samples steps are
+ * stored (later steps are not stored). Adjacent C' phases of JUMP and
+ * JUMP-RESPA(1) then run as separate launches (same results). The record
+ * holds n_samples x 3N values on the device (FP64 in MD_FP64, FP32 in
+ * MD_MIXED). n_samples = 0 ends the record; md_set_system, md_set_state and a
+ * new md_vacf_start end it too. Errors: MD_EINVAL, MD_ENOMEM, MD_ECUDA. */
+int md_vacf_start(md_ctx* ctx, int64_t n_samples);
+
+/* Mass-weighted velocity autocorrelation of one replica from the record:
+ *   vacf_out[k] = (1 / (T - k)) sum_{t=0}^{T-1-k} sum_i m_i v_i(t) . v_i(t + k)
+ * (amu A^2 / ps^2, 0 for k >= T), k < n_lags, T = samples stored (*n_stored;
+ * 0 when nothing is recorded), computed on the device through FFTs of the
+ * zero-padded series (Wiener-Khinchin, exact up to rounding); and its
+ * Hann-windowed cosine transform
+ *   spectrum_out[j] = C(0) + 2 sum_{k=1}^{K-1} w_k C(k) cos(pi j k / K),
+ *   w_k = (1 + cos(pi k / K)) / 2, K = n_lags, j < K,
+ * whose bin j is the frequency j / (2 K dt) for samples dt apart. Host
+ * buffers of n_lags doubles; either may be NULL. Synchronises the stream. */
+int md_vacf_get(md_ctx* ctx, int replica, int64_t n_lags, double* vacf_out, double* spectrum_out,
+                int64_t* n_stored);
+
 /* Release every device buffer and the context. */
 int md_finalize(md_ctx* ctx);
 

@@ -29,7 +29,8 @@ ERRORS = {-1: "MD_EINVAL", -2: "MD_ECUDA", -3: "MD_EOVERFLOW", -4: "MD_EBOUND",
 SYMBOLS = ["md_init", "md_set_system", "md_set_state", "md_step_baoab", "md_step_baoab_respa",
            "md_step_baoab_respa1", "md_step_jump", "md_step_bjaoajb", "md_step_jump_respa", "md_step_jump_respa1",
            "md_observables", "md_get_state", "md_gradient", "md_run_phase", "md_get_list",
-           "md_get_events", "md_profile", "md_nb_gradient_noalloc", "md_finalize", "md_last_error"]
+           "md_get_events", "md_profile", "md_vacf_start", "md_vacf_get", "md_nb_gradient_noalloc",
+           "md_finalize", "md_last_error"]
 
 
 class MDError(RuntimeError):
@@ -101,6 +102,8 @@ def load_library(path: str = LIB_PATH):
     L.md_get_events.restype = i64
     L.md_get_events.argtypes = [vp, i, vp, i64, i]
     L.md_profile.argtypes = [vp, i, i, vp, vp, vp]
+    L.md_vacf_start.argtypes = [vp, i64]
+    L.md_vacf_get.argtypes = [vp, i, i64, vp, vp, P(C.c_int64)]
     L.md_nb_gradient_noalloc.argtypes = [vp, vp, vp, vp, i, d, i, vp, vp, d, d, d, d, i, vp, vp]
     L.md_finalize.argtypes = [vp]
     L.md_last_error.restype = C.c_char_p
@@ -261,6 +264,18 @@ class Engine:
         launches = np.zeros(N_PROFILE_CLASSES, dtype=np.int64)
         self._ck(self.L.md_profile(self.h, int(enable), int(reset), _ptr(ms), _ptr(groups), _ptr(launches)))
         return ms, groups, launches
+
+    def vacf_start(self, n_samples):
+        """record v after every innermost step (n_samples steps at most; 0 ends the record)"""
+        self._ck(self.L.md_vacf_start(self.h, int(n_samples)))
+
+    def vacf(self, n_lags, replica=0):
+        """(mass-weighted VACF C(k), its Hann-windowed cosine transform S(j), samples stored)"""
+        c = np.zeros(int(n_lags))
+        sp = np.zeros(int(n_lags))
+        t = C.c_int64(0)
+        self._ck(self.L.md_vacf_get(self.h, replica, int(n_lags), _ptr(c), _ptr(sp), C.byref(t)))
+        return c, sp, t.value
 
     def events(self, replica=0, cap=1 << 22, clear=True) -> np.ndarray:
         out = np.zeros((cap, 6), dtype=np.int64)

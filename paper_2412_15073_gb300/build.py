@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libmdjump.so")
 BUILD_DIR = os.path.join(HERE, "_build")
-SOURCES = ["md_api.cu", "k_lists.cu", "k_force.cu", "k_jump.cu", "k_pme.cu", "noalloc.cu"]
+SOURCES = ["md_api.cu", "k_lists.cu", "k_force.cu", "k_jump.cu", "k_pme.cu", "k_vacf.cu", "noalloc.cu"]
 # the velocity-phase kernel comes in several occupancy variants that must give
 # identical results: no mul/add contraction there, every FMA is written out
 PER_FILE = {"k_jump.cu": ["-fmad=false"]}

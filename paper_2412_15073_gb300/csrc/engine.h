@@ -116,6 +116,19 @@ void launch_pme_gather(const Dev& d, int order, double* out, int as_grad, int fp
 // exclusion-correction energy of each Ewald replica, added to d.energy[6 r + 3]
 void launch_pme_excl_energy(const Dev& d, cudaStream_t s);
 
+// ---- velocity record and autocorrelation (k_vacf.cu) -----------------------------------
+// record: v into row step_base[0] + s_local - origin of buf (skipped outside [0, cap))
+void launch_vacf_record(const Dev& d, void* buf, int fp64, long long origin, long long cap, uint32_t s_local,
+                        cudaStream_t s);
+// series s0 .. s0 + nb of a [T][n3] record into zero-padded [nb][2T] rows
+void launch_vacf_gather(const void* buf, void* pad, int fp64, long long T, int n3, int s0, int nb, cudaStream_t s);
+// P(j) += sum over the nb transformed series of m~ |X(j)|^2, j < nj
+void launch_vacf_power(const void* X, int fp64, const double* mass_of_atom, int s0, int nb, long long nj, double* P,
+                       cudaStream_t s);
+void launch_vacf_to_complex(const double* P, double2* Z, long long nj, cudaStream_t s);
+void launch_vacf_finish(const double* r, double* C, long long T, long long nlags, cudaStream_t s);
+void launch_vacf_spectrum(const double* C, double* S, long long K, cudaStream_t s);
+
 // ---- jumps (k_jump.cu) --------------------------------------------------------------
 // order 0: C' then J' (first half of a step), 1: J' then C' (second half)
 // variant of the mixed-mode C' kernel: occupancy targets of 3, 4, 5, 6 blocks

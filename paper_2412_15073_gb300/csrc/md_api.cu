@@ -150,6 +150,9 @@ struct md_ctx {
     std::vector<int> pme_orders;    // B-spline orders present
     long long pme_total = 0;        // grid points over all Ewald replicas
     long long pme_max_spec = 0;     // largest half spectrum
+    // velocity record (md_vacf_start): [cap][3N] values, FP64 or FP32 as the precision
+    void* vr = nullptr;
+    long long vr_cap = 0, vr_origin = 0;
     // pinned staging
     double* h_stepc = nullptr;
     uint32_t* h_err = nullptr;
@@ -207,6 +210,15 @@ template <typename T> int upload(md_ctx* ctx, T* dst, const T* src, size_t count
         return MD_ECUDA;
     }
     return MD_OK;
+}
+
+// end a velocity record (its buffer is freed; captured graphs that record are dropped)
+void vacf_stop(md_ctx* ctx)
+{
+    if (ctx->vr) cudaFreeAsync(ctx->vr, ctx->s);
+    ctx->vr = nullptr;
+    ctx->vr_cap = 0;
+    ctx->gen++;
 }
 
 void free_device(md_ctx* ctx)
@@ -621,6 +633,7 @@ int commit(md_ctx* ctx)
         if (!ctx->reps[r].set) FAIL(MD_ENOSYSTEM, "replica %d has no system (replicas 0..%d must be set)", r, R - 1);
     int rc = download_all(ctx);
     if (rc) return rc;
+    vacf_stop(ctx);
     free_device(ctx);
     // layout
     int N = 0, cells = 0;
@@ -1274,6 +1287,14 @@ int run_units(md_ctx* ctx, int key, double tau, int spu, long long units, Body b
     return finish(ctx, (units - done) * spu);
 }
 
+// velocity record of the innermost step s_off (relative to the step bases) that just ended
+void record(md_ctx* ctx, uint32_t s_off)
+{
+    if (!ctx->vr) return;
+    Prof p(ctx, 5, 1);
+    launch_vacf_record(ctx->d, ctx->vr, ctx->fp64, ctx->vr_origin, ctx->vr_cap, s_off, ctx->s);
+}
+
 // inner bonded step of the RESPA family: B A O A [grad] B at dt
 void inner_bonded(md_ctx* ctx, double dt, uint32_t s_off, int check)
 {
@@ -1377,6 +1398,7 @@ int md_set_state(md_ctx* ctx, int replica, const double* x, const double* v, con
     if (replica < 0 || replica >= ctx->d.R) FAIL(MD_EINVAL, "replica %d out of range", replica);
     if (!x || !v) FAIL(MD_EINVAL, "md_set_state: x and v are required");
     Dev& d = ctx->d;
+    vacf_stop(ctx);     // the record assumes uninterrupted steps
     const RepHost& h = ctx->reps[replica];
     const size_t o = 3 * (size_t)ctx->rep_atom_off[replica], n3 = 3 * (size_t)h.n;
     std::vector<int> zero;
@@ -1424,6 +1446,7 @@ int md_step_baoab(md_ctx* ctx, int64_t nsteps, double dt_fs)
             rebuild_step(ctx);
             force(ctx, 0, d.a0);
             kick(ctx, d.a0, 0.5 * tau);
+            record(ctx, uint32_t(k));
         }
     });
 }
@@ -1439,8 +1462,9 @@ int md_step_jump(md_ctx* ctx, int64_t nsteps, double dt_fs)
     force(ctx, 5, d.a0);
     // C'J' A O A [F0] J'C', step after step. In mixed mode the C' of the second
     // half of step k and the C' of the first half of step k+1 (adjacent, at the
-    // same positions and acceleration) run in one launch.
-    const bool fuse = !ctx->fp64;
+    // same positions and acceleration) run in one launch, unless velocities are
+    // recorded between the two.
+    const bool fuse = !ctx->fp64 && !ctx->vr;
     return run_units(ctx, 1, tau, 1, nsteps, [&](long long u0, long long n) {
         for (long long k = u0; k < u0 + n; ++k) {
             if (k == u0 || !fuse) vphase(ctx, d.a0, 0.5 * tau, uint32_t(k), 0, 0);
@@ -1449,6 +1473,7 @@ int md_step_jump(md_ctx* ctx, int64_t nsteps, double dt_fs)
             force(ctx, 5, d.a0);
             if (fuse && k + 1 < u0 + n) vphase(ctx, d.a0, 0.5 * tau, uint32_t(k), 1, 2, uint32_t(k + 1));
             else vphase(ctx, d.a0, 0.5 * tau, uint32_t(k), 1, 1);
+            record(ctx, uint32_t(k));
         }
     });
 }
@@ -1472,6 +1497,7 @@ int md_step_bjaoajb(md_ctx* ctx, int64_t nsteps, double dt_fs)
             force(ctx, 5, d.a0);
             vphase(ctx, nullptr, 0.5 * tau, uint32_t(k), 1, 1);
             kick(ctx, d.a0, 0.5 * tau);
+            record(ctx, uint32_t(k));
         }
     });
 }
@@ -1490,10 +1516,14 @@ int md_step_baoab_respa(md_ctx* ctx, int64_t n_outer, double dt_inner_fs, int n_
         uint32_t s = uint32_t(u0 * n_inner);
         for (long long o = 0; o < n; ++o) {
             kick(ctx, d.al, 0.5 * D);
-            for (int k = 0; k < n_inner; ++k, ++s) inner_bonded(ctx, dt, s, k == n_inner - 1);
+            for (int k = 0; k < n_inner; ++k, ++s) {
+                inner_bonded(ctx, dt, s, k == n_inner - 1);
+                if (k < n_inner - 1) record(ctx, s);
+            }
             rebuild_step(ctx);
             force(ctx, 2, d.al);
             kick(ctx, d.al, 0.5 * D);
+            record(ctx, s - 1);
         }
     });
 }
@@ -1516,13 +1546,18 @@ int md_step_baoab_respa1(md_ctx* ctx, int64_t n_outer, double dt_inner_fs, int m
             kick(ctx, d.al, 0.5 * D);
             for (int j = 0; j < n_outer_ratio; ++j) {
                 kick(ctx, d.as, 0.5 * kap);
-                for (int k = 0; k < m_mid; ++k, ++s) inner_bonded(ctx, dt, s, k == m_mid - 1);
+                for (int k = 0; k < m_mid; ++k, ++s) {
+                    inner_bonded(ctx, dt, s, k == m_mid - 1);
+                    if (k < m_mid - 1) record(ctx, s);
+                }
                 rebuild_step(ctx);
                 force(ctx, 3, d.as);
                 kick(ctx, d.as, 0.5 * kap);
+                if (j < n_outer_ratio - 1) record(ctx, s - 1);
             }
             force(ctx, 4, d.al);
             kick(ctx, d.al, 0.5 * D);
+            record(ctx, s - 1);
         }
     });
 }
@@ -1546,7 +1581,7 @@ static int jump_respa_cycles(md_ctx* ctx, int64_t n_outer, double dt_inner_fs, i
     const long long units = ew ? n_outer : n_outer * ratio;
     // as in md_step_jump, adjacent C' phases of consecutive cycles share a launch in
     // mixed mode (not across an outer kick, which changes the velocities in between)
-    const bool fuse = !ctx->fp64;
+    const bool fuse = !ctx->fp64 && !ctx->vr;
     return run_units(ctx, 4 | (n_inner << 8), dt, per * n_inner, units, [&](long long u0, long long n) {
         uint32_t s = uint32_t(u0 * per * n_inner);
         for (long long o = 0; o < n; ++o) {
@@ -1556,16 +1591,21 @@ static int jump_respa_cycles(md_ctx* ctx, int64_t n_outer, double dt_inner_fs, i
                 const bool carried = fuse && (ew ? j > 0 : o > 0);
                 const bool pass_on = fuse && (ew ? j + 1 < per : o + 1 < n);
                 if (!carried) vphase(ctx, d.as, 0.5 * kap, s0, 0, 0);
-                for (int k = 0; k < n_inner; ++k, ++s) inner_bonded(ctx, dt, s, k == n_inner - 1);
+                for (int k = 0; k < n_inner; ++k, ++s) {
+                    inner_bonded(ctx, dt, s, k == n_inner - 1);
+                    if (k < n_inner - 1) record(ctx, s);
+                }
                 rebuild_step(ctx);
                 force(ctx, 3, d.as);
                 if (pass_on) vphase(ctx, d.as, 0.5 * kap, s0, 1, 2, s);
                 else vphase(ctx, d.as, 0.5 * kap, s0, 1, 1);
+                if (j < per - 1) record(ctx, s - 1);
             }
             if (ew) {
                 force(ctx, 6, d.al);
                 kick(ctx, d.al, 0.5 * D);
             }
+            record(ctx, s - 1);
         }
     });
 }
@@ -1756,11 +1796,111 @@ int md_profile(md_ctx* ctx, int enable, int reset, double* ms_out, int64_t* grou
     return MD_OK;
 }
 
+int md_vacf_start(md_ctx* ctx, int64_t n_samples)
+{
+    if (!ctx) return MD_EINVAL;
+    if (n_samples < 0) FAIL(MD_EINVAL, "md_vacf_start: n_samples < 0");
+    int rc = commit(ctx);
+    if (rc) return rc;
+    vacf_stop(ctx);
+    if (n_samples == 0) return MD_OK;
+    const size_t bytes = (size_t)n_samples * 3 * (size_t)ctx->d.N * (ctx->fp64 ? sizeof(double) : sizeof(float));
+    if (cudaMallocAsync(&ctx->vr, bytes, ctx->s) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->vr = nullptr;
+        FAIL(MD_ENOMEM, "md_vacf_start: %zu bytes for %lld samples", bytes, (long long)n_samples);
+    }
+    long long sb = 0;
+    CK(cudaMemcpyAsync(&sb, ctx->d.step_base, sizeof sb, cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    ctx->vr_cap = n_samples;
+    ctx->vr_origin = sb;
+    return MD_OK;
+}
+
+int md_vacf_get(md_ctx* ctx, int replica, int64_t n_lags, double* vacf_out, double* spectrum_out, int64_t* n_stored)
+{
+    if (!ctx) return MD_EINVAL;
+    if (n_lags < 1) FAIL(MD_EINVAL, "md_vacf_get: n_lags < 1");
+    int rc = commit(ctx);
+    if (rc) return rc;
+    if (replica < 0 || replica >= ctx->d.R) FAIL(MD_EINVAL, "replica %d out of range", replica);
+    Dev& d = ctx->d;
+    long long T = 0;
+    if (ctx->vr) {
+        long long sb = 0;
+        CK(cudaMemcpyAsync(&sb, d.step_base, sizeof sb, cudaMemcpyDeviceToHost, ctx->s));
+        CK(cudaStreamSynchronize(ctx->s));
+        T = std::max(0LL, std::min(ctx->vr_cap, sb - ctx->vr_origin));
+    }
+    if (n_stored) *n_stored = T;
+    if (T == 0) {
+        if (vacf_out) std::fill(vacf_out, vacf_out + n_lags, 0.0);
+        if (spectrum_out) std::fill(spectrum_out, spectrum_out + n_lags, 0.0);
+        return MD_OK;
+    }
+    const int fp64 = ctx->fp64;
+    const size_t e = fp64 ? sizeof(double) : sizeof(float);
+    const int n3 = 3 * d.N, s_lo = 3 * ctx->rep_atom_off[replica], s_hi = s_lo + 3 * ctx->reps[replica].n;
+    const long long nj = T + 1;
+    // series per transform batch: about 2 GB of padded input and spectrum at most
+    const int nb = (int)std::max(1LL, std::min((long long)(s_hi - s_lo), (long long)(2e9 / (4.0 * T * e))));
+    void *pad = nullptr, *X = nullptr;
+    double *P = nullptr, *r = nullptr, *C = nullptr, *S = nullptr;
+    double2* Z = nullptr;
+    cufftHandle fw = 0, bw = 0;
+    auto cleanup = [&]() {
+        if (fw) cufftDestroy(fw);
+        if (bw) cufftDestroy(bw);
+        for (void* p : {pad, X, (void*)P, (void*)r, (void*)C, (void*)S, (void*)Z})
+            if (p) cudaFreeAsync(p, ctx->s);
+    };
+    auto fail = [&](const char* what) {
+        cleanup();
+        cudaGetLastError();
+        FAIL(MD_ECUDA, "md_vacf_get: %s failed", what);
+    };
+    if (cudaMallocAsync(&pad, (size_t)nb * 2 * T * e, ctx->s) != cudaSuccess ||
+        cudaMallocAsync(&X, (size_t)nb * nj * 2 * e, ctx->s) != cudaSuccess ||
+        cudaMallocAsync((void**)&P, nj * sizeof(double), ctx->s) != cudaSuccess ||
+        cudaMallocAsync((void**)&Z, nj * sizeof(double2), ctx->s) != cudaSuccess ||
+        cudaMallocAsync((void**)&r, 2 * T * sizeof(double), ctx->s) != cudaSuccess ||
+        cudaMallocAsync((void**)&C, n_lags * sizeof(double), ctx->s) != cudaSuccess ||
+        cudaMallocAsync((void**)&S, n_lags * sizeof(double), ctx->s) != cudaSuccess)
+        return fail("device allocation");
+    int len = int(2 * T);
+    if (cufftPlanMany(&fw, 1, &len, nullptr, 1, len, nullptr, 1, int(nj), fp64 ? CUFFT_D2Z : CUFFT_R2C, nb) != CUFFT_SUCCESS ||
+        cufftPlan1d(&bw, len, CUFFT_Z2D, 1) != CUFFT_SUCCESS ||
+        cufftSetStream(fw, ctx->s) != CUFFT_SUCCESS || cufftSetStream(bw, ctx->s) != CUFFT_SUCCESS)
+        return fail("cuFFT plan");
+    if (cudaMemsetAsync(P, 0, nj * sizeof(double), ctx->s) != cudaSuccess) return fail("memset");
+    for (int s0 = s_lo; s0 < s_hi; s0 += nb) {
+        const int cnt = std::min(nb, s_hi - s0);
+        launch_vacf_gather(ctx->vr, pad, fp64, T, n3, s0, cnt, ctx->s);
+        const cufftResult fr = fp64 ? cufftExecD2Z(fw, (double*)pad, (cufftDoubleComplex*)X)
+                                    : cufftExecR2C(fw, (float*)pad, (cufftComplex*)X);
+        if (fr != CUFFT_SUCCESS) return fail("forward transform");
+        launch_vacf_power(X, fp64, d.mt, s0, cnt, nj, P, ctx->s);
+    }
+    launch_vacf_to_complex(P, Z, nj, ctx->s);
+    if (cufftExecZ2D(bw, (cufftDoubleComplex*)Z, r) != CUFFT_SUCCESS) return fail("inverse transform");
+    launch_vacf_finish(r, C, T, n_lags, ctx->s);
+    launch_vacf_spectrum(C, S, n_lags, ctx->s);
+    if (cudaGetLastError() != cudaSuccess) return fail("kernel launch");
+    if ((vacf_out && cudaMemcpyAsync(vacf_out, C, n_lags * sizeof(double), cudaMemcpyDeviceToHost, ctx->s) != cudaSuccess) ||
+        (spectrum_out && cudaMemcpyAsync(spectrum_out, S, n_lags * sizeof(double), cudaMemcpyDeviceToHost, ctx->s) != cudaSuccess))
+        return fail("copy to host");
+    cleanup();
+    CK(cudaStreamSynchronize(ctx->s));
+    return MD_OK;
+}
+
 int md_finalize(md_ctx* ctx)
 {
     if (!ctx) return MD_EINVAL;
     if (ctx->gs) cudaStreamSynchronize(ctx->gs);
     drop_graphs(ctx);
+    vacf_stop(ctx);
     free_device(ctx);
     cudaStreamSynchronize(ctx->s);
     for (auto& f : ctx->fft) { cufftDestroy(f.d2z); cufftDestroy(f.z2d); }
