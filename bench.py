@@ -48,6 +48,10 @@ EWALD = dict(dsf_alpha=0.42, coulomb_mode=1, pme_order=6, pme_spacing=0.8, r_spl
 EWALD_EPS0 = [0.1, 1.0]
 EWALD_JUMP_PARAMS = JUMP_PARAMS | EWALD | dict(ring_r=[6.25, 7.0, 8.5], lj_long_mode=1)
 EWALD_BAOAB_PARAMS = BAOAB_PARAMS | EWALD
+DT_FS = 1.0
+METRIC = "ns/day & Gpair-evals/s, JUMP vs BAOAB on 1 GB300 at matched T/D (97k atoms)"
+WORKLOAD = ("water 96,000 atoms (32,000 flexible 3-site waters, 98.6 A cube), LJ+DSF r_E 10 A, "
+            "r_c 5 A, rings at 5.25/6/7.5 A, adaptive eps0 0.1, 300 K, gamma 1/ps; JUMP 1 fs vs BAOAB 1 fs")
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # launch classes of md_profile
 CLASSES = ["pair_force", "bonded", "velocity_phase", "kick_aoa", "list_rebuild", "bookkeeping", "ewald_recip"]
@@ -350,6 +354,51 @@ def ewald_leg(args, M, engine, timed, stream, world, max_over_ranks, barrier):
     return res
 
 
+CM1_PER_INV_FS = 1e15 / 2.99792458e10      # 1/fs in cm^-1
+
+
+def spectra_leg(args, M, engine):
+    """Velocity spectra (mass-weighted VACF, Hann-windowed cosine transform) of
+    BAOAB (1 fs) and of BAOAB-RESPA1 and JUMP-RESPA1 (1:2:Delta fs) under Ewald
+    electrostatics, recorded after every 1 fs step (Sec. 4: resonance peaks of
+    the multiple-time-step integrators). Reports where each spectrum puts its
+    weight: the physical bands (librations < 1000, bend ~1600-2000, O-H stretch
+    ~3000-4000 cm^-1) and the share above 4200 cm^-1, where only integrator
+    artefacts live; and the strongest artefact peak."""
+    T, K = args.spectra, min(2048, args.spectra // 2)
+    out = {"samples": T, "lags": K, "bin_cm1": CM1_PER_INV_FS / (2 * K * DT_FS), "window": "Hann",
+           "electrostatics": "Ewald as in the Ewald leg"}
+    runs = [("baoab_1fs", 7, "baoab", 1, EWALD_BAOAB_PARAMS)]
+    for q in (3, 4):
+        runs += [(f"baoab_respa1_D{2 * q}", 8, "baoab_respa1", q, EWALD_BAOAB_PARAMS),
+                 (f"jump_respa1_D{2 * q}", 9, "jump_respa1", q, EWALD_JUMP_PARAMS | {"eps0": 0.1})]
+    for name, seed, meth, q, params in runs:
+        e = engine(seed, params)
+        per = 1 if meth == "baoab" else 2 * q
+        run = (lambda k: e.baoab(k)) if meth == "baoab" else (lambda k, e=e, m=meth, q=q: getattr(e, m)(k // (2 * q), 1.0, 2, q))
+        try:
+            run(120 // per * per)
+            e.vacf_start(T)
+            run(-(-T // per) * per)
+            C, S, n = e.vacf(K)
+            nu = np.arange(K) * CM1_PER_INV_FS / (2 * K * DT_FS)
+            Sp = np.clip(S, 0, None)
+            tot = Sp.sum()
+            hi = nu > 4200
+            r = {"samples": n, "T": e.observables()["temperature"],
+                 "share_above_4200": float(Sp[hi].sum() / tot),
+                 "stretch_peak_cm1": float(nu[(nu > 3000) & (nu < 4200)][np.argmax(Sp[(nu > 3000) & (nu < 4200)])]),
+                 "bend_peak_cm1": float(nu[(nu > 1200) & (nu < 2400)][np.argmax(Sp[(nu > 1200) & (nu < 2400)])]),
+                 "top_artefact_cm1": float(nu[hi][np.argmax(Sp[hi])]),
+                 "top_artefact_rel": float(Sp[hi].max() / Sp[(nu > 3000) & (nu < 4200)].max())}
+            e.vacf_start(0)
+            out[name] = r
+        except M.MDError as ex:
+            out[name] = {"error": str(ex)}
+        e.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -364,13 +413,15 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--dsteps", type=int, default=4000,
                     help="steps of each integrator for the diffusion constant (0 = skip)")
-    ap.add_argument("--only", default="all", choices=["all", "jump", "baoab", "ewald"])
+    ap.add_argument("--only", default="all", choices=["all", "jump", "baoab", "ewald", "spectra"])
     ap.add_argument("--ewald", type=int, default=1,
                     help="also compare JUMP-RESPA1 with BAOAB-RESPA1 under Ewald electrostatics")
     ap.add_argument("--ewald-eps0", type=float, nargs="*", default=None,
                     help="eps0 values of the Ewald JUMP-RESPA1 runs (default EWALD_EPS0)")
     ap.add_argument("--ewald-alpha", type=float, default=None, help="Ewald splitting parameter (1/A)")
     ap.add_argument("--ewald-spacing", type=float, default=None, help="PME grid spacing (A)")
+    ap.add_argument("--spectra", type=int, default=4096,
+                    help="1 fs samples of the velocity-spectra leg (0 = skip)")
     ap.add_argument("--ewald-lj-long", type=int, default=None,
                     help="lj_long_mode of the Ewald JUMP runs (default 1, the paper's GPU setting)")
     ap.add_argument("--ewald-split", type=float, default=None,
@@ -410,6 +461,12 @@ def main():
         out = ewald_leg(args, M, engine, timed, stream, world, max_over_ranks, barrier)
         if rank == 0:
             print(json.dumps({"ewald": out}), flush=True)
+        ranks.close()
+        return
+    if args.only == "spectra":
+        out = spectra_leg(args, M, engine)
+        if rank == 0:
+            print(json.dumps({"spectra": out}), flush=True)
         ranks.close()
         return
 
@@ -529,6 +586,7 @@ def main():
     ewald = None
     if args.ewald:
         ewald = ewald_leg(args, M, engine, timed, stream, world, max_over_ranks, barrier)
+    spectra = spectra_leg(args, M, engine) if args.spectra > 0 else None
 
     # end to end through the public API with host buffers
     e2e = None
@@ -555,6 +613,7 @@ def main():
                           "short_pairs": pairs_short, "full_pairs": pairs_full},
            "respa1": respa,
            "ewald": ewald,
+           "spectra": spectra,
            "roofline": roof | {"peak_kind": how},
            "e2e": e2e,
            "gpu_launches": launches,

@@ -27,3 +27,32 @@ def test_diffusion_estimate_recovers_brownian_D():
     e = FakeEngine(3 * 4000, 20.0, D, 1.0)
     got = bench.diffusion(e, e.step, 2000, 100, 20.0, 1.0)
     assert abs(got / 2.5 - 1) < 0.05, got
+
+
+def test_bench_functions_name_only_defined_globals():
+    """every global a function of bench.py reads exists (a deleted constant
+    would otherwise only show on the GPU machine)"""
+    import builtins
+    import inspect
+    import types
+
+    import bench
+
+    def code_objects(co):
+        yield co
+        for c in co.co_consts:
+            if isinstance(c, types.CodeType):
+                yield from code_objects(c)
+
+    missing = set()
+    for name, fn in inspect.getmembers(bench, inspect.isfunction):
+        if fn.__module__ != "bench":
+            continue
+        for co in code_objects(fn.__code__):
+            for g in co.co_names:
+                if not hasattr(bench, g) and not hasattr(builtins, g):
+                    # attribute names appear in co_names too: keep only names used as globals
+                    if any(ins.opname in ("LOAD_GLOBAL", "LOAD_NAME") and ins.argval == g
+                           for ins in __import__("dis").get_instructions(co)):
+                        missing.add((name, g))
+    assert not missing, missing
