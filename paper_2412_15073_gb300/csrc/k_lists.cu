@@ -177,30 +177,40 @@ __global__ void k_cell_sort(Dev d)
     if (lane == 0) d.cell_cnt[c] = 0;
 }
 
-// one warp per group of up to 32 atoms of a cell (one atom per lane). The
-// candidates of each neighbour cell (cells visited in increasing linear index,
-// atoms of a cell in increasing index) are loaded 32 at a time, one per lane,
-// and passed to every lane by shuffles; each lane appends its matches to its
-// own list, which therefore comes out in (cell, j) order. Cells have an edge
-// of at least (r_E + skin_outer)/2, so the neighbourhood is +-2 cells per axis.
+// Outer candidate lists. A cell's atoms are split over OUTER_GROUPS warps
+// (home atoms); each warp streams the candidates of the 125 neighbour cells
+// (cells in increasing linear index, atoms of a cell in increasing index), 32
+// per batch, one per lane, and for each home atom in turn ballots which
+// candidates lie within r_E + skin_outer: the matches are appended to that
+// atom's row with coalesced stores, so every row comes out in (cell, j)
+// order. The next batch's candidates load while the current one is tested.
+// Cells have an edge of at least (r_E + skin_outer)/2, so the neighbourhood
+// is +-2 cells per axis.
 constexpr int OUTER_WARPS = 4;
-constexpr int OUTER_GROUPS = 2;                           // warps per cell; each loops over its groups
+constexpr int OUTER_GROUPS = 2;                           // warps per cell, each with a share of its atoms
 
 __global__ void __launch_bounds__(32 * OUTER_WARPS) k_outer_cells(Dev d, int exact)
 {
-    __shared__ int nbs[OUTER_WARPS][125];
-    __shared__ uint4 stage[OUTER_WARPS][32];      // (x, y, z, j) of 32 candidates
+    __shared__ int nbs[OUTER_WARPS][128];
+    __shared__ int cpre[OUTER_WARPS][129];     // candidates before each sorted neighbour cell
+    __shared__ int cbeg[OUTER_WARPS][128];     // first atom of each sorted neighbour cell
+    __shared__ uint4 home[OUTER_WARPS][32];    // (x, y, z, i) of the home atoms of a pass
+    __shared__ int4 hex[OUTER_WARPS][32];      // their first four excluded partners (-1: none)
+    __shared__ uint32_t* hrow[OUTER_WARPS][32];  // their rows of the outer list
+    __shared__ int hmore[OUTER_WARPS][32];     // 1: more than four excluded partners, else -1
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int task = blockIdx.x * OUTER_WARPS + w;       // (cell, first group of 32 atoms)
-    const int c = task / OUTER_GROUPS, group0 = task % OUTER_GROUPS;
+    const int task = blockIdx.x * OUTER_WARPS + w;       // (cell, share of its atoms)
+    const int c = task / OUTER_GROUPS, g = task % OUTER_GROUPS;
     if (c >= d.total_cells) return;
     const int r = d.cell_rep[c];
     if (r < 0 || !d.flags[2 * r + 1]) return;
     const int s_i = d.cell_start[c], e_i = d.cell_start[c + 1];
     const int natoms = e_i - s_i;
-    if (group0 == 0 && natoms > 1024 && lane == 0) { atomicOr(&d.err[r], F_OVERFLOW); atomicOr(&d.ovf[r], OVF_CELL); }
+    if (g == 0 && natoms > 1024 && lane == 0) { atomicOr(&d.err[r], F_OVERFLOW); atomicOr(&d.ovf[r], OVF_CELL); }
     const int nlim = min(natoms, 1024);
-    if (group0 * 32 >= nlim) return;
+    const int share = (nlim + OUTER_GROUPS - 1) / OUTER_GROUPS;
+    const int h_lo = g * share, h_hi = min(nlim, h_lo + share);
+    if (h_lo >= h_hi) return;
     const RepParams& P = d.P[r];
     const int nc = P.nc;
     const int lin = c - P.cell_off;
@@ -230,67 +240,110 @@ __global__ void __launch_bounds__(32 * OUTER_WARPS) k_outer_cells(Dev d, int exa
     for (int u = 0; u < 4; ++u)
         if (lane + 32 * u < ncell) nbs[w][rk[u]] = mine[u];
     __syncwarp();
-    for (int group = group0; group * 32 < nlim; group += OUTER_GROUPS) {
-    // this lane's atom
-    const int ai = group * 32 + lane;
-    const bool live = ai < natoms;
-    const int i = live ? d.cell_atoms[s_i + ai] : -1;
-    const uint4 pi = live ? d.pos[i] : make_uint4(0, 0, 0, 0);
-    int ex[4] = {-1, -1, -1, -1};
-    int e0 = 0, e1 = 0;
-    if (live) {
-        e0 = d.ex_off[i];
-        e1 = d.ex_off[i + 1];
-        for (int e = e0; e < e1 && e - e0 < 4; ++e) ex[e - e0] = d.ex_idx[e];
+    // candidate ranges: lane l holds sorted cells 4l .. 4l+3; warp scan of their counts
+    int cntc[4], sum = 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int m = 4 * lane + u;
+        cntc[u] = 0;
+        if (m < ncell) {
+            const int gc = P.cell_off + nbs[w][m];
+            const int b0 = d.cell_start[gc];
+            cbeg[w][m] = b0;
+            cntc[u] = d.cell_start[gc + 1] - b0;
+        }
+        sum += cntc[u];
     }
-    const double ro = P.R + P.skin_o;
+    int incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    {
+        int run = incl - sum;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int m = 4 * lane + u;
+            if (m <= ncell) cpre[w][m] = run;
+            run += cntc[u];
+        }
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (lane == 31) cpre[w][ncell] = total;
+    __syncwarp();
     // FP32 test in units of the scaled coordinates (no scale multiplies),
     // widened by 4e-6 so that rounding never drops a partner
+    const double ro = P.R + P.skin_o;
     const float r2ou = float(ro * ro * (1.0 + 4e-6) * P.inv_scl * P.inv_scl);
     const double r2o = ro * ro;
-    uint32_t* row = live ? d.olist + (size_t)i * d.ocap : nullptr;
-    int cnt = 0;
-    for (int m = 0; m < ncell; ++m) {
-        const int gc = P.cell_off + nbs[w][m];
-        const int cs0 = d.cell_start[gc], cs1 = d.cell_start[gc + 1];
-        for (int base = cs0; base < cs1; base += 32) {
-            const int nh = min(32, cs1 - base);
-            __syncwarp();
-            if (lane < nh) {
-                const int cand = d.cell_atoms[base + lane];
-                const uint4 cp = d.pos[cand];
-                stage[w][lane] = make_uint4(cp.x, cp.y, cp.z, uint32_t(cand));
+    const unsigned below = (1u << lane) - 1u;
+    // candidate q of the stream: its atom index (-1 past the end)
+    auto cand_of = [&](int q) -> int {
+        if (q >= total) return -1;
+        int lo = 0, hi = ncell - 1;               // last cell m with cpre[m] <= q
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (cpre[w][mid] <= q) lo = mid; else hi = mid - 1;
+        }
+        return d.cell_atoms[cbeg[w][lo] + (q - cpre[w][lo])];
+    };
+    for (int h0 = h_lo; h0 < h_hi; h0 += 32) {
+        const int nh = min(32, h_hi - h0);
+        // home atoms of this pass: lane h holds atom h's count
+        int cnt = 0;
+        __syncwarp();
+        if (lane < nh) {
+            const int i = d.cell_atoms[s_i + h0 + lane];
+            const uint4 pi = d.pos[i];
+            home[w][lane] = make_uint4(pi.x, pi.y, pi.z, uint32_t(i));
+            const int e0 = d.ex_off[i], e1 = d.ex_off[i + 1];
+            hex[w][lane] = make_int4(e0 < e1 ? d.ex_idx[e0] : -1, e0 + 1 < e1 ? d.ex_idx[e0 + 1] : -1,
+                                     e0 + 2 < e1 ? d.ex_idx[e0 + 2] : -1, e0 + 3 < e1 ? d.ex_idx[e0 + 3] : -1);
+            hmore[w][lane] = e1 - e0 > 4 ? 1 : -1;
+            hrow[w][lane] = d.olist + (size_t)i * d.ocap;
+        }
+        __syncwarp();
+        int jn = cand_of(lane);
+        uint4 pn = jn >= 0 ? d.pos[jn] : make_uint4(0, 0, 0, 0);
+        for (int qb = 0; qb < total; qb += 32) {
+            const int j = jn;
+            const uint4 pj = pn;
+            if (qb + 32 < total) {
+                jn = cand_of(qb + 32 + lane);
+                pn = jn >= 0 ? d.pos[jn] : make_uint4(0, 0, 0, 0);
             }
-            __syncwarp();
-            if (!live) continue;
-            for (int t = 0; t < nh; ++t) {
-                const uint4 pj = stage[w][t];
-                const int j = int(pj.w);
-                if (j == i) continue;
+            for (int h = 0; h < nh; ++h) {
+                const uint4 hp = home[w][h];
+                const int i = int(hp.w);
                 bool ok;
-                if (exact) {
-                    ok = dist2_fp64(d.xo, i, j, P) < r2o;
+                if (exact) {            // uniform: the set-up builds
+                    ok = j >= 0 && j != i && dist2_fp64(d.xo, i, j >= 0 ? j : 0, P) < r2o;
                 } else {
-                    const float dx = float(int(pi.x - pj.x)), dy = float(int(pi.y - pj.y)), dz = float(int(pi.z - pj.z));
-                    ok = dx * dx + dy * dy + dz * dz < r2ou;
+                    const float dx = float(int(hp.x - pj.x)), dy = float(int(hp.y - pj.y)),
+                                dz = float(int(hp.z - pj.z));
+                    ok = (j >= 0) & (j != i) & (dx * dx + dy * dy + dz * dz < r2ou);
                 }
-                if (!ok) continue;
-                bool exc = j == ex[0] || j == ex[1] || j == ex[2] || j == ex[3];
-                if (!exc && e1 - e0 > 4)
-                    for (int e = e0 + 4; e < e1; ++e) exc |= d.ex_idx[e] == j;
-                if (exc) continue;
-                if (cnt < d.ocap) row[cnt] = (uint32_t)j;
-                ++cnt;
+                const int4 ex = hex[w][h];
+                ok &= (j != ex.x) & (j != ex.y) & (j != ex.z) & (j != ex.w);
+                if (hmore[w][h] >= 0) {         // uniform and rare: more than four exclusions
+                    const int e1 = d.ex_off[i + 1];
+                    for (int e = d.ex_off[i] + 4; e < e1; ++e) ok &= d.ex_idx[e] != j;
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, ok);
+                const int pos = __shfl_sync(0xffffffffu, cnt, h) + __popc(bal & below);
+                if (ok && pos < d.ocap) hrow[w][h][pos] = (uint32_t)j;
+                if (lane == h) cnt += __popc(bal);
             }
         }
-    }
-    if (live) {
-        d.ocnt[i] = cnt;
-        if (cnt > d.ocap) {
-            atomicOr(&d.err[r], F_OVERFLOW);
-            atomicOr(&d.ovf[r], OVF_OUTER);
+        if (lane < nh) {
+            const int i = int(home[w][lane].w);
+            d.ocnt[i] = cnt;
+            if (cnt > d.ocap) {
+                atomicOr(&d.err[r], F_OVERFLOW);
+                atomicOr(&d.ovf[r], OVF_OUTER);
+            }
         }
-    }
     }
 }
 
