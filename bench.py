@@ -43,10 +43,12 @@ BAOAB_PARAMS = PARAMS
 # The jumps replace only the (1 - chi) real-space part, whose forces the
 # reciprocal sum has made weak; as in the paper's GPU runs the long-range LJ
 # part is deterministic (lj_long_mode 1: LJ bounces reflect velocities and
-# slow diffusion). Multiple-time-step levels 1:2:6 fs as in the paper.
+# slow diffusion). Multiple-time-step levels 1:2:6 fs as in the paper. JUMP
+# takes a 0.4 A skin here (measured best: its proposals are few at eps0 = 1, so
+# fewer list rebuilds pay more than a thinner ring skin saves).
 EWALD = dict(dsf_alpha=0.42, coulomb_mode=1, pme_order=6, pme_spacing=0.8, r_split=6.0)
 EWALD_EPS0 = [0.1, 1.0]
-EWALD_JUMP_PARAMS = JUMP_PARAMS | EWALD | dict(ring_r=[6.25, 7.0, 8.5], lj_long_mode=1)
+EWALD_JUMP_PARAMS = JUMP_PARAMS | EWALD | dict(ring_r=[6.25, 7.0, 8.5], lj_long_mode=1, skin=0.4)
 EWALD_BAOAB_PARAMS = BAOAB_PARAMS | EWALD
 DT_FS = 1.0
 METRIC = "ns/day & Gpair-evals/s, JUMP vs BAOAB on 1 GB300 at matched T/D (97k atoms)"
@@ -61,9 +63,9 @@ CLASSES = ["pair_force", "bonded", "velocity_phase", "kick_aoa", "list_rebuild",
 FLOP_PER_PAIR = 52
 OPS_PER_PROPOSAL = 230
 # DRAM bytes per C' proposal of the velocity-phase kernel: one ncu capture
-# (--set full) of a single-phase launch of this workload read 233.2 MB and
-# wrote 13.6 MB for 3.57 M proposals; scaled to a launch by its proposals
-TRAFFIC_PER_PROPOSAL = (233.197e6 + 13.631e6) / 3.574e6
+# (--set full) of a single-phase launch of this workload read 233.4 MB and
+# wrote 13.5 MB for 3.57 M proposals; scaled to a launch by its proposals
+TRAFFIC_PER_PROPOSAL = (233.391e6 + 13.488e6) / 3.574e6
 
 
 def ns_per_day(fs_simulated: float, seconds: float) -> float:
@@ -300,6 +302,8 @@ def ewald_leg(args, M, engine, timed, stream, world, max_over_ranks, barrier):
     jp, bp = EWALD_JUMP_PARAMS | ew, EWALD_BAOAB_PARAMS | ew
     if args.ewald_lj_long is not None:
         jp = jp | {"lj_long_mode": args.ewald_lj_long}
+    if args.ewald_jump_skin is not None:
+        jp = jp | {"skin": args.ewald_jump_skin}
     if args.ewald_split:
         rc = args.ewald_split
         jp = jp | {"r_split": rc, "ring_r": [rc + 0.25, rc + 1.0, rc + 2.5]}
@@ -307,7 +311,7 @@ def ewald_leg(args, M, engine, timed, stream, world, max_over_ranks, barrier):
     res = {"electrostatics": "Ewald: erfc(a r)/r to 10 A, a = %.2f/A, smooth PME order %d, %.2f A grid"
                              % (ew["dsf_alpha"], ew["pme_order"], ew["pme_spacing"]),
            "split": {"r_c": jp["r_split"], "h": jp["h_switch"], "rings": jp["ring_r"],
-                     "lj_long_mode": jp["lj_long_mode"]},
+                     "lj_long_mode": jp["lj_long_mode"], "jump_skin": jp["skin"], "baoab_skin": bp["skin"]},
            "levels": "delta 1 fs, kappa 2 fs, Delta 6 fs (BAOAB-RESPA1 also 4 fs)"}
     eps_list = args.ewald_eps0 or EWALD_EPS0
     runs = [(f"jump_respa1_eps{e:g}", 5, "jump_respa1", 3, jp | {"eps0": e}) for e in eps_list]
@@ -417,7 +421,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--dsteps", type=int, default=4000,
                     help="steps of each integrator for the diffusion constant (0 = skip)")
-    ap.add_argument("--only", default="all", choices=["all", "jump", "baoab", "ewald", "spectra"])
+    ap.add_argument("--only", default="all",
+                    choices=["all", "jump", "baoab", "ewald", "spectra", "jump_respa1_ewald", "baoab_respa1_ewald"])
     ap.add_argument("--ewald", type=int, default=1,
                     help="also compare JUMP-RESPA1 with BAOAB-RESPA1 under Ewald electrostatics")
     ap.add_argument("--ewald-eps0", type=float, nargs="*", default=None,
@@ -428,6 +433,7 @@ def main():
                     help="1 fs samples of the velocity-spectra leg (0 = skip)")
     ap.add_argument("--ewald-lj-long", type=int, default=None,
                     help="lj_long_mode of the Ewald JUMP runs (default 1, the paper's GPU setting)")
+    ap.add_argument("--ewald-jump-skin", type=float, default=None, help="list skin of the Ewald JUMP runs (A)")
     ap.add_argument("--ewald-split", type=float, default=None,
                     help="short-range split r_c of the Ewald runs (A); rings move with it")
     args = ap.parse_args()
@@ -475,9 +481,21 @@ def main():
         return
 
     if args.only != "all":
-        # profiling run: one integrator only, no side measurements
-        e = engine(1, JUMP_PARAMS if args.only == "jump" else BAOAB_PARAMS)
-        fn = e.jump if args.only == "jump" else e.baoab
+        # profiling run: one integrator only, no side measurements; the RESPA1
+        # runs take the Ewald leg's settings (1:2:6 fs, eps0 1 for JUMP) and
+        # count steps in innermost steps (a multiple of 6)
+        if args.only == "jump":
+            e = engine(1, JUMP_PARAMS)
+            fn = e.jump
+        elif args.only == "baoab":
+            e = engine(1, BAOAB_PARAMS)
+            fn = e.baoab
+        elif args.only == "jump_respa1_ewald":
+            e = engine(1, EWALD_JUMP_PARAMS | {"eps0": 1.0})
+            fn = lambda k: e.jump_respa1(k // 6, 1.0, 2, 3)
+        else:
+            e = engine(1, EWALD_BAOAB_PARAMS)
+            fn = lambda k: e.baoab_respa1(k // 6, 1.0, 2, 3)
         fn(args.warmup)
         torch.cuda.nvtx.range_push("timed")        # ncu --nvtx --nvtx-include timed/ selects these launches
         t = timed(e, fn, args.steps, stream)
