@@ -179,3 +179,25 @@ def test_ewald_weak_force_regime(M, oracle_mod, water648):
     em.jump_respa1(40, 1.0, 2, 3)
     ob = em.observables()
     assert ob["error_flags"] == 0 and ob["jump_proposals"] > 0
+
+
+def test_ewald_batched_replicas_equal_solo_runs_mixed(M, oracle_mod, water648):
+    """mixed precision: replicas with their own grids (24^3 and 27^3, orders 6
+    and 4) advanced in one context give the same bits as each run alone (exact
+    fixed-point charge sums, one transform per replica)"""
+    w2 = perturbed(water648, seed=8)
+    cfgs = [(water648, dict(EWALD)), (w2, dict(EWALD, pme_spacing=0.7, pme_order=4))]
+    e = M.Engine(precision=1, seed=21, max_replicas=2)
+    for r, (s, p) in enumerate(cfgs):
+        e.set_system(r, s, **p)
+    e.jump_respa1(12, 1.0, 2, 3)
+    for r, (s, p) in enumerate(cfgs):
+        solo = M.Engine(precision=1, seed=21, max_replicas=2)
+        # the replica index keys its random streams: run it in the same slot
+        if r == 1:
+            solo.set_system(0, s, **p)
+        solo.set_system(r, s, **p)
+        solo.jump_respa1(12, 1.0, 2, 3)
+        xb, vb, _, _ = e.state(r)
+        xs, vs, _, _ = solo.state(r)
+        assert np.array_equal(xb, xs) and np.array_equal(vb, vs), r

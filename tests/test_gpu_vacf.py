@@ -83,3 +83,22 @@ def test_record_capacity_and_end(M, water648):
     e.vacf_start(0)
     C, S, T = e.vacf(30)
     assert T == 0 and (C == 0).all()
+
+
+def test_vacf_of_each_replica(M, oracle_mod, water648):
+    """two replicas in one context: each replica's VACF is its own (FP64,
+    against the oracle's record of that replica's run)"""
+    from test_gpu_ewald import perturbed
+    w2 = perturbed(water648, seed=5)
+    e = M.Engine(precision=M.MD_FP64, seed=6, max_replicas=2)
+    e.set_system(0, water648, **PARAMS)
+    e.set_system(1, w2, **PARAMS)
+    e.vacf_start(40)
+    e.baoab(40)
+    for r, s in enumerate((water648, w2)):
+        o = oracle_mod.Oracle(s, seed=6, replica=r, **PARAMS)
+        o.vrec_enable(40)
+        o.baoab(40)
+        C, _, T = e.vacf(20, replica=r)
+        assert T == 40
+        np.testing.assert_allclose(C, oracle_mod.vacf(o.vrec(), s.mass, 20), rtol=1e-6)
