@@ -109,7 +109,12 @@ typedef struct {
     double ring_r[3];  /* interior ring edges (A), strictly increasing inside (r_c-h, r_E); MD_EINVAL otherwise */
     int lj_long_mode;  /* 0: the long-range LJ part (1-chi) U_LJ jumps (BPS, J', Sec. 3.2);
                         * 1: it is deterministic in F0, as in the paper's GPU runs (Sec. 4):
-                        * gradient modes 3 and 5 carry the whole LJ, mode 4 only (1-chi) Coulomb */
+                        * gradient modes 3 and 5 carry the whole LJ, mode 4 only (1-chi) Coulomb;
+                        * 2: deterministic at the slow level (the paper's RESPA1 splits van der
+                        * Waals into a short and a long range): modes 3 and 4 split LJ by chi as
+                        * in mode 0, mode 5 (F0 of JUMP, BJAOAJB) adds the (1-chi) LJ part, mode 6
+                        * holds it, and JUMP-RESPA / JUMP-RESPA1 kick it at their outer step.
+                        * No J' in modes 1 and 2. */
     int coulomb_mode;  /* 0: damped shifted force Coulomb (DSF, dsf_alpha);
                         * 1: Ewald (Sec. 3.1 splits its real-space part like DSF): pair term
                         *    erfc(a r)/r cut at r_cut with a = dsf_alpha > 0, no shift; the
@@ -193,9 +198,10 @@ int md_get_state(md_ctx* ctx, int replica, double* x, double* v, int* img,
 /* Gradient of one part of the potential at the current positions, into a
  * host buffer of 3n doubles. mode: 0 full, 1 bonded, 2 nonbonded full,
  * 3 nonbonded short (chi-weighted), 4 nonbonded long ((1-chi)-weighted),
- * 5 F_0 of JUMP (bonded + short), 6 Ewald reciprocal part with the exclusion
- * correction (zero with DSF). With coulomb_mode 1, modes 0, 2, 4 and 5 include
- * the mode-6 part. Uses the current lists (rebuilt first when an atom moved
+ * 5 F_0 of JUMP (bonded + short), 6 the slow level of JUMP-RESPA(1): the Ewald
+ * reciprocal part with the exclusion correction, plus the (1-chi) LJ part with
+ * lj_long_mode 2 (zero with DSF and lj_long_mode 0 or 1). With coulomb_mode 1,
+ * modes 0, 2, 4 and 5 include the reciprocal part. Uses the current lists (rebuilt first when an atom moved
  * more than skin/2). */
 int md_gradient(md_ctx* ctx, int replica, int mode, double* host_grad);
 

@@ -697,7 +697,7 @@ static void nonbonded_atom(const or_sys* s, int i, int weight, double* g3, doubl
         double duc = OR_COULOMB * s->q[i] * s->q[j] * du_coul(s, r);
         double ul = u_ljsf(s, e, sg, r), dul = du_ljsf(s, e, sg, r);
         double f;
-        if (s->p.lj_long_mode && weight != W_FULL) {
+        if (s->p.lj_long_mode == 1 && weight != W_FULL) {
             /* LJ wholly deterministic: all of it in the short part, none in the long */
             double flj = weight == W_SHORT ? dul : 0.0;
             f = (wdudr(s, uc, duc, r, weight) + flj) / r;
@@ -714,6 +714,25 @@ static void nonbonded_atom(const or_sys* s, int i, int weight, double* g3, doubl
     if (e_c) *e_c = ec;
 }
 
+
+/* the (1 - chi) LJ gradient of atom i, pair by pair (lj_long_mode 2: the LJ
+ * long part deterministic at the slow level of the multiple-time-step schemes) */
+static void lj_long_atom(const or_sys* s, int i, double* g3)
+{
+    double R2 = s->p.r_cut * s->p.r_cut;
+    for (int j = 0; j < s->n; ++j) {
+        if (j == i) continue;
+        double d[3];
+        minimage(s, i, j, d);
+        double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        if (r2 >= R2 || excluded(s, i, j)) continue;
+        double r = sqrt(r2);
+        int ti = s->type[i], tj = s->type[j];
+        double e = s->eps[ti * s->ntypes + tj], sg = s->sig[ti * s->ntypes + tj];
+        double f = wdudr(s, u_ljsf(s, e, sg, r), du_ljsf(s, e, sg, r), r, W_LONG) / r;
+        for (int c = 0; c < 3; ++c) g3[c] += f * d[c];
+    }
+}
 
 /* ======================================================================== */
 /* Ewald electrostatics (coulomb_mode 1). The real-space pairs erfc(a r)/r  */
@@ -963,6 +982,10 @@ void or_gradient(or_sys* s, int mode, double* grad, double* energy)
         }
     }
     if (bo) bonded_gradient(s, grad, &eb, &ea);
+    if (s->p.lj_long_mode == 2 && (mode == 5 || mode == 6)) {
+#pragma omp parallel for schedule(dynamic, 16)
+        for (int i = 0; i < n; ++i) lj_long_atom(s, i, &grad[3 * i]);
+    }
     double erec = 0.0;
     if (mode_has_recip(s, mode)) {
         double* g = (double*)malloc(sizeof(double) * 3 * (size_t)n);
@@ -984,6 +1007,7 @@ void or_gradient_atom(or_sys* s, int mode, int i, double* g3)
         for (int c = 0; c < 3; ++c) g3[c] += g[3 * i + c];
         free(g);
     }
+    if (s->p.lj_long_mode == 2 && (mode == 5 || mode == 6)) lj_long_atom(s, i, g3);
     if (mode_has_recip(s, mode)) {
         double* g = (double*)malloc(sizeof(double) * 3 * (size_t)s->n);
         or_ewald_recip_pme(s, g, NULL, NULL);
@@ -1424,7 +1448,9 @@ int or_step_jump_respa(or_sys* s, int64_t nouter, double dt_inner_fs, int n_inne
 {
     if (s->lazy) return -1;   /* the steps rebuild the lists of every atom */
     double dt = dt_inner_fs * 1e-3, D = dt * n_inner;
-    int ew = s->p.coulomb_mode == 1;   /* Ewald: the reciprocal part is kicked at D (Sec. 2.3) */
+    /* the slow deterministic force (the Ewald reciprocal part, and the LJ long
+     * part in lj_long_mode 2) is kicked at D (Sec. 2.3) */
+    int ew = s->p.coulomb_mode == 1 || s->p.lj_long_mode == 2;
     accel(s, 1, s->ab);
     accel(s, 3, s->as);
     if (ew) accel(s, 6, s->al);
@@ -1453,7 +1479,7 @@ int or_step_jump_respa1(or_sys* s, int64_t nouter, double dt_inner_fs, int m_mid
 {
     if (s->lazy) return -1;   /* the steps rebuild the lists of every atom */
     double dt = dt_inner_fs * 1e-3, kap = dt * m_mid, D = kap * n_outer;
-    int ew = s->p.coulomb_mode == 1;
+    int ew = s->p.coulomb_mode == 1 || s->p.lj_long_mode == 2;
     accel(s, 1, s->ab);
     accel(s, 3, s->as);
     if (ew) accel(s, 6, s->al);

@@ -50,7 +50,11 @@ typedef struct {
                           * list build is out of reach); the or_step_* calls then return -1 */
     int lj_long_mode;    /* 0: the long-range LJ part (1-chi) U_LJ is handled by BPS jumps (J');
                           * 1: it is deterministic, in F0 (the paper's GPU runs): gradient modes
-                          * 3 and 5 carry the whole LJ, mode 4 only (1-chi) Coulomb, no J' */
+                          * 3 and 5 carry the whole LJ, mode 4 only (1-chi) Coulomb, no J';
+                          * 2: deterministic at the slow level: modes 3 and 4 split LJ by chi as
+                          * in mode 0, mode 5 adds the (1-chi) LJ part (F0 of JUMP), mode 6 holds
+                          * it (with the Ewald reciprocal part), JUMP-RESPA(1) kick mode 6 at
+                          * their outer step, no J' */
     int coulomb_mode;    /* 0: DSF Coulomb (damping dsf_alpha); 1: Ewald: real-space pairs
                           * erfc(alpha r)/r to r_cut (alpha = dsf_alpha) split by chi as in
                           * Sec. 3.1, plus a smooth-PME reciprocal sum (Essmann et al. 1995),

@@ -37,7 +37,7 @@ enum ListKind { L_SHORT = 0, L_FULL = 1, L_R0 = 2, L_LJ = L_R0 + MAX_RINGS, NKIN
 enum Counter { C_CPROP = 0, C_CACC, C_JPROP, C_JACC, C_SATT, C_REBUILD, C_OUTER, C_GUARD, NCOUNT };
 
 // pair weight: full U, short chi U, long (1 - chi) U
-enum Weight { W_FULL = 0, W_SHORT = 1, W_LONG = 2 };
+enum Weight { W_FULL = 0, W_SHORT = 1, W_LONG = 2, W_LJLONG = 3 };   // W_LJLONG: (1 - chi) LJ alone
 
 struct LJPair {
     double c12, c6, uR, duR;   // 4 eps s^12, 4 eps s^6, U_LJ(R), U_LJ'(R)
@@ -62,7 +62,7 @@ struct RepParams {
     double edge[MAX_RINGS + 1];// ring edges: sw = edge[0] < ... < edge[nr] = R
     float edgef[MAX_RINGS + 1];
     int nr, rings_on, lj_on, eps_mode;
-    int lj_long, lj_jump;      // LJ long part deterministic in F0; LJ bounces (J') on
+    int lj_long, lj_jump;      // lj_long_mode (0 jumped, 1 in F0, 2 at the slow level); LJ bounces (J') on
     double skin, skin_o;
     // DSF: u(r) = erfc(a r)/r - eR + fR (r - R); u'(r) = -erfc(a r)/r^2 - k exp(-a^2 r^2)/r + fR
     double alpha, eR, fR, kexp;     // kexp = 2 a / sqrt(pi)

@@ -90,7 +90,8 @@ void launch_rebuild(const Dev& d, int kinds, int fp64, int keep_refs, int exact_
 void launch_late_lists(const Dev& d, int kinds, cudaStream_t s);
 
 // ---- forces and integrators (k_force.cu) -----------------------------------------
-// mode: 0 full, 1 bonded, 2 nb full, 3 nb short, 4 nb long, 5 F0 (bonded + short)
+// mode: 0 full, 1 bonded, 2 nb full, 3 nb short, 4 nb long, 5 F0 (bonded + short),
+// 7 the (1 - chi) LJ part alone (replicas with lj_long_mode 2, zero elsewhere)
 // returns the number of kernels launched
 int launch_force(const Dev& d, int mode, double* out, int as_grad, int fp64, int tpa, cudaStream_t s);
 void launch_kick(const Dev& d, const double* a, double h, cudaStream_t s);

@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(256) k_force(Dev d, int lk, double* out, int a
         const T sw = T(P.sw), h = T(P.h), sw2 = sw * sw;
         const T C = T(COULOMB);
         const uint32_t* row = d.list[lk] + (size_t)i * d.lcap[lk];
-        const int n = min(d.lcnt[lk][i], d.lcap[lk]);
+        const int n = W == W_LJLONG ? 0 : min(d.lcnt[lk][i], d.lcap[lk]);
         // position of i in the arithmetic type
         uint4 pi = make_uint4(0, 0, 0, 0);
         double3 xi = make_double3(0, 0, 0);
@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(256) k_force(Dev d, int lk, double* out, int a
                 du = C * qq * duc;
             }
             const LJPair& lj = P.lj[ti * MAX_TYPES + d.type[j]];
-            if (lj.on && !(W == W_LONG && P.lj_long)) {    // deterministic LJ long part: not in the long weight
+            if (lj.on && !(W == W_LONG && P.lj_long == 1)) {   // LJ long part in F0: not in the long weight
                 T ul, dul;
                 ljsf<T>(P, lj, rr, rinv, ul, dul);
                 u += ul;
@@ -204,9 +204,10 @@ __global__ void __launch_bounds__(256) k_force(Dev d, int lk, double* out, int a
             }
             acc.add(f * rinv, dx, dy, dz);
         }
-        if (W == W_SHORT && P.lj_long) {
-            // the (1 - chi) LJ part over the LJ list: with the chi part above,
-            // the whole LJ is deterministic (the paper's GPU runs)
+        if ((W == W_SHORT && (P.lj_long == 1 || (P.lj_long == 2 && BONDED))) || (W == W_LJLONG && P.lj_long == 2)) {
+            // the (1 - chi) LJ part over the LJ list: in the short force with
+            // lj_long_mode 1 (the paper's GPU runs), in F0 and alone at the slow
+            // level with lj_long_mode 2
             const uint32_t* lrow = d.list[L_LJ] + (size_t)i * d.lcap[L_LJ];
             const int nl = min(d.lcnt[L_LJ][i], d.lcap[L_LJ]);
             const T R2 = T(P.R) * T(P.R);
@@ -429,6 +430,7 @@ int force_t(const Dev& d, int mode, double* out, int as_grad, int tpa, cudaStrea
     case 2: force_tpa<T, W_FULL, false>(d, L_FULL, out, as_grad, tpa, s); break;
     case 3: force_tpa<T, W_SHORT, false>(d, L_SHORT, out, as_grad, tpa, s); break;
     case 4: force_tpa<T, W_LONG, false>(d, L_FULL, out, as_grad, tpa, s); break;
+    case 7: force_tpa<T, W_LJLONG, false>(d, L_LJ, out, as_grad, tpa, s); break;
     default: force_tpa<T, W_SHORT, true>(d, L_SHORT, out, as_grad, tpa, s); break;
     }
     return nk;

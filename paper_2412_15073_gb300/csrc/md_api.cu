@@ -230,6 +230,14 @@ void free_device(md_ctx* ctx)
 
 // does some replica keep the LJ long part deterministic (its short gradient
 // then also runs over the LJ list)?
+// does some replica keep the LJ long part at the slow level (lj_long_mode 2)?
+bool any_lj_slow(const md_ctx* ctx)
+{
+    for (const RepParams& P : ctx->hp)
+        if (P.lj_long == 2) return true;
+    return false;
+}
+
 bool any_lj_long(const md_ctx* ctx)
 {
     for (const RepParams& P : ctx->hp)
@@ -250,7 +258,8 @@ int lists_needed(const md_ctx* ctx, int family)
 
 int mode_list(const md_ctx* ctx, int mode)
 {
-    if (mode == 1 || mode == 6) return 0;
+    if (mode == 1) return 0;
+    if (mode == 6) return any_lj_slow(ctx) ? 1 << L_LJ : 0;
     if (mode == 3 || mode == 5) return (1 << L_SHORT) | (any_lj_long(ctx) ? 1 << L_LJ : 0);
     return 1 << L_FULL;
 }
@@ -408,8 +417,8 @@ RepParams make_params(const md_ctx* ctx, const RepHost& h, int r, int atom_off, 
     for (double e : h.lj_eps) any_lj |= e > 0.0;
     P.rings_on = (P.sw < P.R) && qmax > 0.0;
     P.lj_on = (P.sw < P.R) && any_lj;
-    P.lj_long = s.lj_long_mode != 0;
-    P.lj_jump = P.lj_on && !P.lj_long;
+    P.lj_long = s.lj_long_mode;
+    P.lj_jump = P.lj_on && P.lj_long == 0;
     P.eps_mode = s.eps_mode;
     P.skin = s.skin; P.skin_o = skin_o;
     HostPair hpair{s.r_cut, P.sw, s.h_switch, s.dsf_alpha, s.coulomb_mode};
@@ -501,8 +510,8 @@ int check_sys(md_ctx* ctx, const md_system* s)
         !(s->dsf_alpha >= 0) || !(s->gamma >= 0) || !(s->temperature > 0) || !(s->eps0 > 0) ||
         (s->eps_mode != 0 && s->eps_mode != 1))
         FAIL(MD_EINVAL, "md_set_system: invalid cutoff, switch, thermostat or jump parameters");
-    if (s->lj_long_mode != 0 && s->lj_long_mode != 1)
-        FAIL(MD_EINVAL, "md_set_system: lj_long_mode must be 0 or 1");
+    if (s->lj_long_mode < 0 || s->lj_long_mode > 2)
+        FAIL(MD_EINVAL, "md_set_system: lj_long_mode must be 0, 1 or 2");
     if (s->coulomb_mode != 0 && s->coulomb_mode != 1)
         FAIL(MD_EINVAL, "md_set_system: coulomb_mode must be 0 (DSF) or 1 (Ewald)");
     if (s->coulomb_mode == 1) {
@@ -1050,7 +1059,13 @@ int pme(md_ctx* ctx, double* out, int as_grad, int energy)
 void force_into(md_ctx* ctx, int mode, double* out, int as_grad)
 {
     if (mode == 6) {
-        cudaMemsetAsync(out, 0, sizeof(double) * 3 * (size_t)ctx->d.N, ctx->s);
+        // the slow level: the (1 - chi) LJ part of lj_long_mode 2 replicas (zero elsewhere), then PME
+        if (any_lj_slow(ctx)) {
+            Prof p(ctx, 0, 1);
+            launch_force(ctx->d, 7, out, as_grad, ctx->fp64, ctx->fp64 ? 1 : 4, ctx->s);
+        } else {
+            cudaMemsetAsync(out, 0, sizeof(double) * 3 * (size_t)ctx->d.N, ctx->s);
+        }
     } else {
         const int t = mode == 1 ? 1 : tpa_for(ctx, mode);
         const bool bonded = mode == 0 || mode == 1 || mode == 5;
@@ -1569,7 +1584,8 @@ int md_step_baoab_respa1(md_ctx* ctx, int64_t n_outer, double dt_inner_fs, int m
 static int jump_respa_cycles(md_ctx* ctx, int64_t n_outer, double dt_inner_fs, int n_inner, int ratio)
 {
     Dev& d = ctx->d;
-    const bool ew = !ctx->ewald_reps.empty();
+    // a slow level exists when some replica has a reciprocal part or keeps its LJ long part there
+    const bool ew = !ctx->ewald_reps.empty() || any_lj_slow(ctx);
     const double dt = dt_inner_fs * 1e-3, kap = dt * n_inner, D = kap * ratio;
     int rc;
     if ((rc = set_stepc(ctx, dt))) return rc;

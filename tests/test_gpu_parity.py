@@ -403,20 +403,23 @@ def test_million_atom_heterogeneous_sampled(M, oracle_mod):
 
 @pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-5)])
 def test_lj_long_mode_gradients(M, oracle_mod, water648, precision, tol):
-    """The paper's GPU variant (LJ long part deterministic in F0): gradient
-    modes 3, 4 and 5 against the oracle's, measured against the total force."""
+    """The LJ long part deterministic: in F0 (mode 1, the paper's GPU
+    variant) or at the slow level (mode 2): gradient modes against the
+    oracle's, partial sums measured against the total force."""
     w = water648.copy()
     w.x = (w.x + np.random.default_rng(3).normal(scale=0.05, size=w.x.shape)) % w.box
-    e, o = make(M, oracle_mod, w, precision, lj_long_mode=1)
-    total, _ = o.gradient(0)
-    for mode in (0, 3, 4, 5):
-        ref, _ = o.gradient(mode)
-        err = force_err(e.gradient(mode), ref, total if mode in (3, 4) else None)
-        assert err <= tol, (mode, err)
+    for lj_long_mode in (1, 2):
+        e, o = make(M, oracle_mod, w, precision, lj_long_mode=lj_long_mode)
+        total, _ = o.gradient(0)
+        for mode in (0, 3, 4, 5, 6):
+            ref, _ = o.gradient(mode)
+            err = force_err(e.gradient(mode), ref, total if mode in (3, 4, 6) else None)
+            assert err <= tol, (lj_long_mode, mode, err)
 
 
 @pytest.mark.parametrize("how,kw", [("jump", dict(lj_long_mode=1)), ("bjaoajb", {}),
-                                    ("bjaoajb", dict(lj_long_mode=1))])
+                                    ("bjaoajb", dict(lj_long_mode=1)), ("jump", dict(lj_long_mode=2)),
+                                    ("jump_respa1", dict(lj_long_mode=2)), ("jump_respa", dict(lj_long_mode=2))])
 def test_variant_trajectories_fp64(M, oracle_mod, water648, how, kw):
     """JUMP with the deterministic LJ long part, and the BJAOAJB splitting,
     follow the oracle in FP64: identical accepted-jump events and positions
@@ -424,8 +427,9 @@ def test_variant_trajectories_fp64(M, oracle_mod, water648, how, kw):
     deterministic."""
     e, o = make(M, oracle_mod, water648, 0, seed=9, **kw)
     o.events_enable(1 << 22)
-    getattr(e, how)(60)
-    getattr(o, how)(60)
+    args = {"jump_respa1": (10, 1.0, 2, 3), "jump_respa": (30, 1.0, 2)}.get(how, (60,))
+    getattr(e, how)(*args)
+    getattr(o, how)(*args)
     assert np.array_equal(sorted_events(e.events()), sorted_events(o.events()))
     assert pos_err(e.state()[0], o.state()[0], water648.box) < 1e-6
     ob = e.observables()

@@ -340,6 +340,36 @@ def test_lj_long_mode_moves_the_lj_long_part_into_f0(oracle_mod, water648):
     assert b.counters()[2] == 0 and b.counters()[0] > 0
 
 
+def test_lj_long_mode_2_holds_the_lj_long_part_at_the_slow_level(oracle_mod, water648):
+    """lj_long_mode 2: modes 3 and 4 are those of mode 0 (LJ split by chi),
+    mode 6 is the (1-chi) LJ gradient that mode 1 moved into the short part,
+    F0 (mode 5) is that of mode 1, no LJ bounces; JUMP-RESPA1 (which kicks
+    the slow part at its outer step) runs without bounces or errors."""
+    w = water648.copy()
+    w.x = (w.x + np.random.default_rng(2).normal(scale=0.05, size=w.x.shape)) % w.box
+    p = dict(r_cut=9.0, r_split=5.0, h_switch=0.5, skin=0.2, skin_outer=0.3)
+    a = oracle_mod.Oracle(w, **p)
+    b = oracle_mod.Oracle(w, lj_long_mode=1, **p)
+    c = oracle_mod.Oracle(w, lj_long_mode=2, **p)
+    ga = {m: a.gradient(m)[0] for m in (0, 3, 4, 5, 6)}
+    gb = {m: b.gradient(m)[0] for m in (0, 3, 4, 5, 6)}
+    gc = {m: c.gradient(m)[0] for m in (0, 1, 3, 4, 5, 6)}
+    for m in (0, 3, 4):
+        assert np.array_equal(gc[m], ga[m]), m
+    assert np.allclose(gc[5], gb[5], rtol=0, atol=1e-10)
+    assert np.allclose(gc[6], gb[3] - ga[3], rtol=0, atol=1e-10)       # the (1-chi) LJ part
+    assert np.allclose(gc[1] + gc[3] + gc[6], gc[5], rtol=0, atol=1e-10)
+    assert not ga[6].any() and not gb[6].any()
+    # per atom, as the atom-wise call computes it
+    i = int(np.flatnonzero(w.type == 0)[5])
+    np.testing.assert_allclose(c.gradient_atom(6, i), gc[6][i], rtol=1e-12, atol=1e-12)
+    d = oracle_mod.Oracle(water648, seed=3, lj_long_mode=2, **p)
+    assert d.jump_respa1(20, 1.0, 2, 3) == 0
+    assert d.counters()[2] == 0 and d.counters()[0] > 0
+    T = 0.5 * (water648.mass[:, None] * d.state()[1] ** 2).sum() / 418.4 * 2 / (3 * w.n * 0.0019872041)
+    assert 200 < T < 1200
+
+
 def test_bjaoajb_is_baoab_without_jumps_and_keeps_temperature(oracle_mod, water648):
     """BJAOAJB with empty jump ranges is BAOAB on F0 = full force bit for bit;
     with jumps it keeps the temperature of the water box near 300 K."""
