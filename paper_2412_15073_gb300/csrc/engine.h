@@ -20,6 +20,7 @@ struct Dev {
     const RepParams* P;
     const int* rep;                 // atom -> replica
     int* vorder;                    // visiting order of the velocity phases (grouped by jump rate)
+    const int* vorder0;             // the order fixed at set-up (expected rates at the thermal speed)
     int *vkey, *vhist, *vofs;       // rate sort: bucket per atom, counts and offsets per (replica, bucket)
     // state (FP64 master copies)
     double *x, *v, *xb, *xo;        // positions, velocities, positions at list build / outer build
@@ -137,6 +138,10 @@ void launch_vacf_spectrum(const double* C, double* S, long long K, cudaStream_t 
 // phase first orders the atoms by their expected number of proposals, and
 // J' runs as a kernel of its own.
 constexpr int NVPHASE_VARIANTS = 4;
+// launch variants of the mixed velocity phase: occupancy variant (v % NVPHASE_VARIANTS),
+// with the rate ordering of the current velocities (v < NVPHASE_VARIANTS) or in the
+// order fixed at set-up (where proposals are few, sorting costs more than it saves)
+constexpr int NVPHASE_LAUNCH_VARIANTS = 2 * NVPHASE_VARIANTS;
 constexpr int RATE_BUCKETS = 128;
 // order 2 (mixed mode only): J' (s_off, half 1), C' (s_off, 1), C' (s_off2, 0), J' (s_off2, 0).
 // hp0: host copy of the parameters of replica 0 when the context holds one

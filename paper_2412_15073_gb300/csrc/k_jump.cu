@@ -781,22 +781,26 @@ static void vphase_any(const Dev& d, const double* a, double tau2, uint32_t s, u
     }
     const int npass = order == 2 ? 2 : 1;
     const int jmode = !doJ ? 0 : (order == 0 ? 1 : (order == 1 ? 2 : 3));
-    rate_order(d, a, tau2 * npass, st);
+    // any visiting order gives the same values: each atom's chain depends on its own draws
+    Dev dv = d;
+    if (variant < NVPHASE_VARIANTS) rate_order(d, a, tau2 * npass, st);
+    else dv.vorder = const_cast<int*>(d.vorder0);
+    variant %= NVPHASE_VARIANTS;
     if (hp0) {
         const JC jc = make_jc(*hp0);
         switch (variant) {
-        case 1: k_cphase_f<4, true><<<nb, 128, 0, st>>>(d, jc, a, tau2, s, s_abs, half, npass, s2, jmode); break;
-        case 2: k_cphase_f<5, true><<<nb, 128, 0, st>>>(d, jc, a, tau2, s, s_abs, half, npass, s2, jmode); break;
-        case 3: k_cphase_f<6, true><<<nb, 128, 0, st>>>(d, jc, a, tau2, s, s_abs, half, npass, s2, jmode); break;
-        default: k_cphase_f<3, true><<<nb, 128, 0, st>>>(d, jc, a, tau2, s, s_abs, half, npass, s2, jmode); break;
+        case 1: k_cphase_f<4, true><<<nb, 128, 0, st>>>(dv, jc, a, tau2, s, s_abs, half, npass, s2, jmode); break;
+        case 2: k_cphase_f<5, true><<<nb, 128, 0, st>>>(dv, jc, a, tau2, s, s_abs, half, npass, s2, jmode); break;
+        case 3: k_cphase_f<6, true><<<nb, 128, 0, st>>>(dv, jc, a, tau2, s, s_abs, half, npass, s2, jmode); break;
+        default: k_cphase_f<3, true><<<nb, 128, 0, st>>>(dv, jc, a, tau2, s, s_abs, half, npass, s2, jmode); break;
         }
     } else {
         const JC jc{};
         switch (variant) {
-        case 1: k_cphase_f<4, false><<<nb, 128, 0, st>>>(d, jc, a, tau2, s, s_abs, half, npass, s2, jmode); break;
-        case 2: k_cphase_f<5, false><<<nb, 128, 0, st>>>(d, jc, a, tau2, s, s_abs, half, npass, s2, jmode); break;
-        case 3: k_cphase_f<6, false><<<nb, 128, 0, st>>>(d, jc, a, tau2, s, s_abs, half, npass, s2, jmode); break;
-        default: k_cphase_f<3, false><<<nb, 128, 0, st>>>(d, jc, a, tau2, s, s_abs, half, npass, s2, jmode); break;
+        case 1: k_cphase_f<4, false><<<nb, 128, 0, st>>>(dv, jc, a, tau2, s, s_abs, half, npass, s2, jmode); break;
+        case 2: k_cphase_f<5, false><<<nb, 128, 0, st>>>(dv, jc, a, tau2, s, s_abs, half, npass, s2, jmode); break;
+        case 3: k_cphase_f<6, false><<<nb, 128, 0, st>>>(dv, jc, a, tau2, s, s_abs, half, npass, s2, jmode); break;
+        default: k_cphase_f<3, false><<<nb, 128, 0, st>>>(dv, jc, a, tau2, s, s_abs, half, npass, s2, jmode); break;
         }
     }
 }

@@ -749,13 +749,13 @@ int commit(md_ctx* ctx)
     }
     // device arrays
     RepParams* dP;
-    int *drep, *dvorder, *dtype, *dimg, *dbi_off, *dex_off, *dex_idx;
+    int *drep, *dvorder, *dvorder0, *dtype, *dimg, *dbi_off, *dex_off, *dex_idx;
     double *dmt, *disqmt, *dq, *dLY, *dLLJ, *dbk, *dbr0, *dak, *dat0;
     float *dLYf, *dLLJf;
     int2 *dbitem, *dbij;
     int4* dang;
 #define AL(p, n) if ((rc = dalloc(ctx, &(p), (n)))) return rc
-    AL(dP, R); AL(drep, N); AL(dvorder, N); AL(dtype, N); AL(dimg, 3 * N); AL(dbi_off, N + 1);
+    AL(dP, R); AL(drep, N); AL(dvorder, N); AL(dvorder0, N); AL(dtype, N); AL(dimg, 3 * N); AL(dbi_off, N + 1);
     AL(dex_off, N + 1); AL(dex_idx, ex_idx.size());
     AL(dmt, N); AL(disqmt, N); AL(dq, N); AL(dLY, MAX_RINGS * N); AL(dLLJ, N);
     AL(dLYf, MAX_RINGS * N); AL(dLLJf, N);
@@ -856,12 +856,12 @@ int commit(md_ctx* ctx)
     AL(d.ev, (size_t)6 * (evcap ? evcap : 1)); AL(d.ev_n, 1);
 #undef AL
     d.ev_cap = evcap;
-    d.P = dP; d.rep = drep; d.vorder = dvorder; d.type = dtype; d.img = dimg; d.bi_off = dbi_off; d.ex_off = dex_off;
+    d.P = dP; d.rep = drep; d.vorder = dvorder; d.vorder0 = dvorder0; d.type = dtype; d.img = dimg; d.bi_off = dbi_off; d.ex_off = dex_off;
     d.ex_idx = dex_idx; d.mt = dmt; d.isqmt = disqmt; d.q = dq; d.LY = dLY; d.LLJ = dLLJ;
     d.LYf = dLYf; d.LLJf = dLLJf; d.bitem = dbitem; d.bond_ij = dbij; d.bond_k = dbk;
     d.bond_r0 = dbr0; d.ang = dang; d.ang_k = dak; d.ang_t0 = dat0;
     if ((rc = upload(ctx, dP, ctx->hp.data(), R)) || (rc = upload(ctx, drep, rep.data(), N)) ||
-        (rc = upload(ctx, dvorder, vorder.data(), N)) ||
+        (rc = upload(ctx, dvorder, vorder.data(), N)) || (rc = upload(ctx, dvorder0, vorder.data(), N)) ||
         (rc = upload(ctx, dtype, type.data(), N)) || (rc = upload(ctx, dimg, img.data(), 3 * (size_t)N)) ||
         (rc = upload(ctx, dbi_off, bi_off.data(), N + 1)) || (rc = upload(ctx, dex_off, ex_off.data(), N + 1)) ||
         (rc = upload(ctx, dex_idx, ex_idx.data(), ex_idx.size())) || (rc = upload(ctx, dmt, mt.data(), N)) ||
@@ -1110,7 +1110,7 @@ int tune_vphase(md_ctx* ctx, const double* a, double tau2)
     Dev& d = ctx->d;
     const char* env = std::getenv("MDJ_VPHASE_VARIANT");
     if (env) {
-        ctx->vvar = std::max(0, std::min(NVPHASE_VARIANTS - 1, std::atoi(env)));
+        ctx->vvar = std::max(0, std::min(NVPHASE_LAUNCH_VARIANTS - 1, std::atoi(env)));
         return MD_OK;
     }
     double* vs;
@@ -1129,7 +1129,7 @@ int tune_vphase(md_ctx* ctx, const double* a, double tau2)
     cudaEventCreate(&e1);
     float best = 1e30f;
     int pick = 0;
-    for (int v = 0; v < NVPHASE_VARIANTS; ++v) {
+    for (int v = 0; v < NVPHASE_LAUNCH_VARIANTS; ++v) {
         float tot = 0;
         for (int rep = 0; rep < 2; ++rep) {
             CK(cudaMemcpyAsync(d.v, vs, sizeof(double) * 3 * d.N, cudaMemcpyDeviceToDevice, ctx->s));
@@ -1157,7 +1157,8 @@ int tune_vphase(md_ctx* ctx, const double* a, double tau2)
 void vphase(md_ctx* ctx, const double* a, double tau2, uint32_t s_off, int half, int order, uint32_t s_off2 = 0)
 {
     if (ctx->vvar < 0) tune_vphase(ctx, a, tau2);
-    Prof p(ctx, 2, ctx->fp64 ? 1 : 4);   // mixed: rate order (3 kernels) + the velocity-phase kernel
+    // mixed: rate order (3 kernels, unless the variant skips it) + the velocity-phase kernel
+    Prof p(ctx, 2, ctx->fp64 ? 1 : (ctx->vvar >= NVPHASE_VARIANTS ? 1 : 4));
     launch_vphase(ctx->d, a, tau2, s_off, half, order, 1, 1, ctx->fp64, ctx->vvar < 0 ? 0 : ctx->vvar, ctx->s,
                   s_off2, single_params(ctx));
 }
@@ -1732,7 +1733,8 @@ int md_run_phase(md_ctx* ctx, int phase, double tau2_ps, int64_t s0, int half, i
     Dev& d = ctx->d;
     if (phase == 0) force(ctx, accel_mode, d.a0);
     {
-        Prof p(ctx, 2, (ctx->fp64 || phase == 1) ? 1 : 4);   // phase 0: rate order (3) + C'; phase 1: J' only
+        // phase 0: rate order (3, unless the variant skips it) + C'; phase 1: J' only
+        Prof p(ctx, 2, (ctx->fp64 || phase == 1 || ctx->vvar >= NVPHASE_VARIANTS) ? 1 : 4);
         launch_vphase_abs(d, phase == 0 ? d.a0 : nullptr, tau2_ps, uint32_t(s0), half, 0, phase == 0, phase == 1,
                           ctx->fp64, ctx->vvar < 0 ? 0 : ctx->vvar, ctx->s, single_params(ctx));
     }

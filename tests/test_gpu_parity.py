@@ -285,10 +285,11 @@ def test_invalid_inputs_are_rejected(M, water648):
 
 
 def test_velocity_phase_variants_are_identical(M, oracle_mod, water648, monkeypatch):
-    """The occupancy variants the autotuner chooses between compute the same
-    values bit for bit (mixed mode, 20 JUMP steps)."""
+    """The launch variants the autotuner chooses between (four occupancy
+    targets, with or without the rate ordering) compute the same values bit
+    for bit (mixed mode, 20 JUMP steps)."""
     ref = None
-    for var in range(4):
+    for var in range(8):
         monkeypatch.setenv("MDJ_VPHASE_VARIANT", str(var))
         e, _ = make(M, oracle_mod, water648, 1, seed=12)
         e.jump(20)
