@@ -143,15 +143,18 @@ def pair_counts(x, box, r, n_mol_atoms=3):
     return int((~same).sum())
 
 
-def diffusion(e, integ, steps, every, box, dt_fs):
+def diffusion(e, integ, steps, every, box, dt_fs, mass=None):
     """Self-diffusion constant of the oxygens (atoms 0, 3, 6, ...) from the
     Einstein relation: MSD of the unwrapped positions over all time origins,
     slope of a linear fit over 20-80 % of the lag window, D = slope / 6.
-    Returns D in 1e-5 cm^2/s."""
-    xs = []
+    Returns D in 1e-5 cm^2/s; with the masses (amu), (D, mean temperature over
+    the same samples, 3N degrees of freedom)."""
+    xs, ts = [], []
     for k in range(steps // every + 1):
-        x, _, img, _ = e.state()
+        x, v, img, _ = e.state()
         xs.append((x + img * box)[::3])
+        if mass is not None:
+            ts.append((mass[:, None] * v * v).sum() / (3 * len(mass) * 0.0019872041 * 418.4))
         if k < steps // every:
             integ(every)
     X = np.stack(xs)
@@ -161,7 +164,8 @@ def diffusion(e, integ, steps, every, box, dt_fs):
     t = lags * every * dt_fs * 1e-3                     # ps
     sel = (lags >= 0.2 * (nt - 1)) & (lags <= 0.8 * (nt - 1))
     slope = np.polyfit(t[sel], msd[sel], 1)[0]          # A^2 / ps
-    return slope / 6.0 * 10.0                           # A^2/ps = 1e-4 cm^2/s -> units of 1e-5 cm^2/s
+    D = slope / 6.0 * 10.0                              # A^2/ps = 1e-4 cm^2/s -> units of 1e-5 cm^2/s
+    return D if mass is None else (D, float(np.mean(ts)))
 
 
 def cpu_oracle_sample(sys_, params, n_sample, n_rounds, seed=0):
@@ -289,7 +293,7 @@ def e2e_run(ej, args, M, torch, stream, n, world, max_over_ranks, barrier):
             "path": "md_set_state(host) + md_step_jump(K) + md_get_state(host) per bench step of K MD steps"}
 
 
-def ewald_leg(args, M, engine, timed, stream, world, max_over_ranks, barrier):
+def ewald_leg(args, M, engine, timed, stream, world, max_over_ranks, barrier, mass):
     """JUMP-RESPA1 against BAOAB-RESPA1 under Ewald electrostatics (smooth PME
     at the outer level of both): ns/day, temperature and oxygen self-diffusion
     of each, on the same equilibrated start. delta 1 fs (bonded), kappa 2 fs
@@ -347,7 +351,8 @@ def ewald_leg(args, M, engine, timed, stream, world, max_over_ranks, barrier):
             r["class_ms_per_fs"] = {c: round(float(m) / (pc * per_cycle), 4) for c, m in zip(CLASSES, ms)}
             if args.dsteps > 0 and r["stable"]:
                 every = 96                          # a multiple of both cycle lengths (4 and 6 fs)
-                r["D"] = diffusion(e, lambda k: run(k // per_cycle), args.dsteps // every * every, every, BOX, DT_FS)
+                nd = 2 * args.dsteps // every * every   # twice the 1 fs window: RESPA1 steps are cheap
+                r["D"], r["T_mean"] = diffusion(e, lambda k: run(k // per_cycle), nd, every, BOX, DT_FS, mass)
             res[name] = r
         except M.MDError as ex:
             res[name] = {"error": str(ex), "stable": False}
@@ -361,6 +366,8 @@ def ewald_leg(args, M, engine, timed, stream, world, max_over_ranks, barrier):
             if "D" in res[k] and b.get("D"):
                 res[k]["D_ratio"] = res[k]["D"] / b["D"]
     res["D_unit"] = "1e-5 cm^2/s"
+    res["D_window_ps"] = 2 * args.dsteps // 96 * 96 * DT_FS * 1e-3
+    res["T_mean_note"] = "mean over the D samples (every 96 fs), 3N degrees of freedom"
     return res
 
 
@@ -477,7 +484,7 @@ def main():
         return e
 
     if args.only == "ewald":
-        out = ewald_leg(args, M, engine, timed, stream, world, max_over_ranks, barrier)
+        out = ewald_leg(args, M, engine, timed, stream, world, max_over_ranks, barrier, w.mass)
         if rank == 0:
             print(json.dumps({"ewald": out}), flush=True)
         ranks.close()
@@ -609,14 +616,16 @@ def main():
     # matched T and D: the self-diffusion constant of both integrators
     dif = None
     if args.dsteps > 0:
-        dif = {"jump_D": diffusion(ej, ej.jump, args.dsteps, 100, BOX, DT_FS),
-               "baoab_D": diffusion(eb, eb.baoab, args.dsteps, 100, BOX, DT_FS),
+        jd, jt = diffusion(ej, ej.jump, args.dsteps, 100, BOX, DT_FS, w.mass)
+        bd, bt = diffusion(eb, eb.baoab, args.dsteps, 100, BOX, DT_FS, w.mass)
+        dif = {"jump_D": jd, "baoab_D": bd, "jump_T_mean": jt, "baoab_T_mean": bt,
                "unit": "1e-5 cm^2/s", "window_ps": args.dsteps * DT_FS * 1e-3,
-               "method": "O atoms, Einstein MSD over all origins, fit over 20-80 % of the lags"}
+               "method": "O atoms, Einstein MSD over all origins, fit over 20-80 % of the lags; "
+                         "T averaged over the same samples"}
 
     ewald = None
     if args.ewald:
-        ewald = ewald_leg(args, M, engine, timed, stream, world, max_over_ranks, barrier)
+        ewald = ewald_leg(args, M, engine, timed, stream, world, max_over_ranks, barrier, w.mass)
     spectra = spectra_leg(args, M, engine) if args.spectra > 0 else None
 
     # end to end through the public API with host buffers
