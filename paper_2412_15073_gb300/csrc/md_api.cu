@@ -153,6 +153,8 @@ struct md_ctx {
     // velocity record (md_vacf_start): [cap][3N] values, FP64 or FP32 as the precision
     void* vr = nullptr;
     long long vr_cap = 0, vr_origin = 0;
+    // error of a call made inside a driver body (cuFFT), reported at the end of the call
+    int deferred = MD_OK;
     // pinned staging
     double* h_stepc = nullptr;
     uint32_t* h_err = nullptr;
@@ -1072,10 +1074,21 @@ void force_into(md_ctx* ctx, int mode, double* out, int as_grad)
         Prof p(ctx, mode == 1 ? 1 : 0, (bonded && ctx->d.nbond + ctx->d.nang > 0) ? 2 : 1);
         launch_force(ctx->d, mode, out, as_grad, ctx->fp64, t, ctx->s);
     }
-    if (mode_has_recip(ctx, mode)) pme(ctx, out, as_grad, 0);
+    if (mode_has_recip(ctx, mode)) {
+        const int rc = pme(ctx, out, as_grad, 0);
+        if (rc && !ctx->deferred) ctx->deferred = rc;
+    }
 }
 
 void force(md_ctx* ctx, int mode, double* out) { force_into(ctx, mode, out, 0); }
+
+// the error a driver body left behind (its message is already in ctx->msg)
+int take_deferred(md_ctx* ctx)
+{
+    const int rc = ctx->deferred;
+    ctx->deferred = MD_OK;
+    return rc;
+}
 
 void rebuild_step(md_ctx* ctx)
 {
@@ -1182,6 +1195,7 @@ int finish(md_ctx* ctx, long long inner_steps)
         launch_advance(ctx->d, inner_steps, ctx->s);
     }
     CK(cudaGetLastError());
+    if (int rc = take_deferred(ctx)) return rc;
     CK(cudaMemcpyAsync(ctx->h_err, ctx->d.err, sizeof(uint32_t) * ctx->d.R, cudaMemcpyDeviceToHost, ctx->s));
     CK(cudaStreamSynchronize(ctx->s));
     collect_profile(ctx);
@@ -1713,6 +1727,7 @@ int md_gradient(md_ctx* ctx, int replica, int mode, double* host_grad)
     Dev& d = ctx->d;
     force_into(ctx, mode, d.gout, 1);
     CK(cudaGetLastError());
+    if ((rc = take_deferred(ctx))) return rc;
     const size_t o = 3 * (size_t)ctx->rep_atom_off[replica], n3 = 3 * (size_t)ctx->reps[replica].n;
     CK(cudaMemcpyAsync(host_grad, d.gout + o, n3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
     CK(cudaStreamSynchronize(ctx->s));
@@ -1739,6 +1754,7 @@ int md_run_phase(md_ctx* ctx, int phase, double tau2_ps, int64_t s0, int half, i
                           ctx->fp64, ctx->vvar < 0 ? 0 : ctx->vvar, ctx->s, single_params(ctx));
     }
     CK(cudaGetLastError());
+    if ((rc = take_deferred(ctx))) return rc;
     CK(cudaMemcpyAsync(ctx->h_err, d.err, sizeof(uint32_t) * d.R, cudaMemcpyDeviceToHost, ctx->s));
     CK(cudaStreamSynchronize(ctx->s));
     return MD_OK;
