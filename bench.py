@@ -373,6 +373,46 @@ def ewald_leg(args, M, engine, timed, stream, world, max_over_ranks, barrier, ma
 
 CM1_PER_INV_FS = 1e15 / 2.99792458e10      # 1/fs in cm^-1
 
+# the batched ensemble: 64 water boxes of 216-2,000 molecules (sizes from seed
+# 1, each its own box and Philox stream), the 648-atom workload's parameters
+ENSEMBLE_PARAMS = dict(r_cut=9.0, r_split=5.0, h_switch=0.5, r_mid=5.5, dsf_alpha=0.2, gamma=1.0,
+                       temperature=300.0, eps0=0.1, eps_mode=1, skin=0.2, skin_outer=0.3)
+
+
+def ensemble_leg(args, M, timed, stream, device):
+    """Aggregate ns/day of JUMP and of BAOAB (1 fs) over the batched ensemble,
+    every replica advanced by the same launches; mean temperature over the
+    replicas after the timed steps."""
+    from paper_2412_15073_gb300 import systems
+    sizes = systems.replica_sizes(64, seed=1)
+    syss = [systems.water_box(n, seed=100 + k) for k, n in enumerate(sizes)]
+    atoms = sum(s.n for s in syss)
+    eq = M.Engine(precision=M.MD_MIXED, seed=77, device=device, stream=stream.cuda_stream, max_replicas=64)
+    for r, s in enumerate(syss):
+        eq.set_system(r, s, **(ENSEMBLE_PARAMS | {"gamma": 20.0}))
+    eq.baoab(max(args.equil // 2, 1))
+    for r, s in enumerate(syss):
+        x, v, _, _ = eq.state(r)
+        s.x, s.v = x, v
+    eq.close()
+    out = {"replicas": 64, "atoms": atoms, "sizes_atoms": [min(sizes) * 3, max(sizes) * 3],
+           "params": "r_E 9 A, r_c 5 A, rings of r_mid 5.5 A, DSF 0.2/A, eps0 0.1, skin 0.2 A, 1 fs, mixed"}
+    steps = max(args.steps // 5, 20)
+    for name, seed, meth in (("jump", 78, "jump"), ("baoab", 79, "baoab")):
+        e = M.Engine(precision=M.MD_MIXED, seed=seed, device=device, stream=stream.cuda_stream, max_replicas=64)
+        for r, s in enumerate(syss):
+            e.set_system(r, s, **ENSEMBLE_PARAMS)
+        fn = getattr(e, meth)
+        fn(args.warmup)
+        t = timed(e, fn, steps, stream)
+        Ts = [e.observables(r)["temperature"] for r in range(64)]
+        out[name] = {"ns_per_day_aggregate": ns_per_day(64 * steps * DT_FS, t), "ms_per_step": t / steps * 1e3,
+                     "T_mean": float(np.mean(Ts)), "T_min": float(np.min(Ts)), "T_max": float(np.max(Ts))}
+        e.close()
+    out["speedup_vs_baoab"] = out["jump"]["ns_per_day_aggregate"] / out["baoab"]["ns_per_day_aggregate"]
+    out["steps"] = steps
+    return out
+
 
 def spectra_leg(args, M, engine):
     """Velocity spectra (mass-weighted VACF, Hann-windowed cosine transform) of
@@ -435,13 +475,15 @@ def main():
     ap.add_argument("--dsteps", type=int, default=4000,
                     help="steps of each integrator for the diffusion constant (0 = skip)")
     ap.add_argument("--only", default="all",
-                    choices=["all", "jump", "baoab", "ewald", "spectra", "jump_respa1_ewald", "baoab_respa1_ewald"])
+                    choices=["all", "jump", "baoab", "ewald", "spectra", "ensemble", "jump_respa1_ewald",
+                             "baoab_respa1_ewald"])
     ap.add_argument("--ewald", type=int, default=1,
                     help="also compare JUMP-RESPA1 with BAOAB-RESPA1 under Ewald electrostatics")
     ap.add_argument("--ewald-eps0", type=float, nargs="*", default=None,
                     help="eps0 values of the Ewald JUMP-RESPA1 runs (default EWALD_EPS0)")
     ap.add_argument("--ewald-alpha", type=float, default=None, help="Ewald splitting parameter (1/A)")
     ap.add_argument("--ewald-spacing", type=float, default=None, help="PME grid spacing (A)")
+    ap.add_argument("--ensemble", type=int, default=1, help="also time the batched 64-replica ensemble")
     ap.add_argument("--spectra", type=int, default=4096,
                     help="1 fs samples of the velocity-spectra leg (0 = skip)")
     ap.add_argument("--ewald-lj-long", type=int, default=None,
@@ -493,6 +535,12 @@ def main():
         out = spectra_leg(args, M, engine)
         if rank == 0:
             print(json.dumps({"spectra": out}), flush=True)
+        ranks.close()
+        return
+    if args.only == "ensemble":
+        out = ensemble_leg(args, M, timed, stream, local)
+        if rank == 0:
+            print(json.dumps({"ensemble": out}), flush=True)
         ranks.close()
         return
 
@@ -627,6 +675,7 @@ def main():
     if args.ewald:
         ewald = ewald_leg(args, M, engine, timed, stream, world, max_over_ranks, barrier, w.mass)
     spectra = spectra_leg(args, M, engine) if args.spectra > 0 else None
+    ensemble = ensemble_leg(args, M, timed, stream, local) if args.ensemble else None
 
     # end to end through the public API with host buffers
     e2e = None
@@ -654,6 +703,7 @@ def main():
            "respa1": respa,
            "ewald": ewald,
            "spectra": spectra,
+           "ensemble": ensemble,
            "roofline": roof | {"peak_kind": how},
            "e2e": e2e,
            "gpu_launches": launches,
