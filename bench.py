@@ -379,6 +379,41 @@ ENSEMBLE_PARAMS = dict(r_cut=9.0, r_split=5.0, h_switch=0.5, r_mid=5.5, dsf_alph
                        temperature=300.0, eps0=0.1, eps_mode=1, skin=0.2, skin_outer=0.3)
 
 
+def million_leg(args, M, timed, stream, device):
+    """The heterogeneous 1,000,000-atom system (water around a dense sphere of
+    50,002 charged LJ beads, 229 A box; r_E 10 A, r_c 5 A, DSF): JUMP-RESPA1
+    against BAOAB-RESPA1 at delta 1, kappa 2, Delta 2 fs (the largest stable
+    outer step of BAOAB-RESPA1 under DSF), after a short relaxation at strong
+    friction; ns/day, temperature and the pair evaluations per second."""
+    from paper_2412_15073_gb300 import systems
+    w = systems.water_with_beads(seed=2)
+    p = PARAMS | {"skin": 0.5}
+    eq = M.Engine(precision=M.MD_MIXED, seed=91, device=device, stream=stream.cuda_stream)
+    eq.set_system(0, w, **(p | {"gamma": 20.0}))
+    eq.baoab(200)
+    w.x, w.v = eq.state()[0], eq.state()[1]
+    eq.close()
+    out = {"atoms": w.n, "box": w.box, "levels": "delta 1 fs, kappa 2 fs, Delta 2 fs"}
+    cyc = max(args.steps // 20, 10)
+    for name, seed, meth, params in (("jump_respa1", 92, "jump_respa1", JUMP_PARAMS),
+                                     ("baoab_respa1", 93, "baoab_respa1", p)):
+        e = M.Engine(precision=M.MD_MIXED, seed=seed, device=device, stream=stream.cuda_stream)
+        e.set_system(0, w, **params)
+        run = lambda k, e=e, m=meth: getattr(e, m)(k, 1.0, 2, 1)
+        run(3)
+        c0 = e.observables()
+        t = timed(e, run, cyc, stream)
+        c1 = e.observables()
+        out[name] = {"ns_per_day": ns_per_day(cyc * 2 * DT_FS, t), "ms_per_fs": t / (cyc * 2) * 1e3,
+                     "T": c1["temperature"], "error_flags": c1["error_flags"]}
+        if meth == "jump_respa1":
+            out[name]["proposals_per_atom_fs"] = (c1["jump_proposals"] - c0["jump_proposals"]) / (w.n * cyc * 2)
+        e.close()
+    out["speedup_vs_baoab_respa1"] = out["jump_respa1"]["ns_per_day"] / out["baoab_respa1"]["ns_per_day"]
+    out["fs_timed"] = cyc * 2
+    return out
+
+
 def ensemble_leg(args, M, timed, stream, device):
     """Aggregate ns/day of JUMP and of BAOAB (1 fs) over the batched ensemble,
     every replica advanced by the same launches; mean temperature over the
@@ -475,8 +510,8 @@ def main():
     ap.add_argument("--dsteps", type=int, default=4000,
                     help="steps of each integrator for the diffusion constant (0 = skip)")
     ap.add_argument("--only", default="all",
-                    choices=["all", "jump", "baoab", "ewald", "spectra", "ensemble", "jump_respa1_ewald",
-                             "baoab_respa1_ewald"])
+                    choices=["all", "jump", "baoab", "ewald", "spectra", "ensemble", "million",
+                             "jump_respa1_ewald", "baoab_respa1_ewald"])
     ap.add_argument("--ewald", type=int, default=1,
                     help="also compare JUMP-RESPA1 with BAOAB-RESPA1 under Ewald electrostatics")
     ap.add_argument("--ewald-eps0", type=float, nargs="*", default=None,
@@ -484,6 +519,7 @@ def main():
     ap.add_argument("--ewald-alpha", type=float, default=None, help="Ewald splitting parameter (1/A)")
     ap.add_argument("--ewald-spacing", type=float, default=None, help="PME grid spacing (A)")
     ap.add_argument("--ensemble", type=int, default=1, help="also time the batched 64-replica ensemble")
+    ap.add_argument("--million", type=int, default=1, help="also time the 1,000,000-atom heterogeneous system")
     ap.add_argument("--spectra", type=int, default=4096,
                     help="1 fs samples of the velocity-spectra leg (0 = skip)")
     ap.add_argument("--ewald-lj-long", type=int, default=None,
@@ -541,6 +577,14 @@ def main():
         out = ensemble_leg(args, M, timed, stream, local)
         if rank == 0:
             print(json.dumps({"ensemble": out}), flush=True)
+        ranks.close()
+        return
+    if args.only == "million":
+        t0 = time.perf_counter()
+        out = million_leg(args, M, timed, stream, local)
+        out["wall_s"] = time.perf_counter() - t0
+        if rank == 0:
+            print(json.dumps({"million": out}), flush=True)
         ranks.close()
         return
 
@@ -676,6 +720,7 @@ def main():
         ewald = ewald_leg(args, M, engine, timed, stream, world, max_over_ranks, barrier, w.mass)
     spectra = spectra_leg(args, M, engine) if args.spectra > 0 else None
     ensemble = ensemble_leg(args, M, timed, stream, local) if args.ensemble else None
+    million = million_leg(args, M, timed, stream, local) if args.million else None
 
     # end to end through the public API with host buffers
     e2e = None
@@ -704,6 +749,7 @@ def main():
            "ewald": ewald,
            "spectra": spectra,
            "ensemble": ensemble,
+           "million": million,
            "roofline": roof | {"peak_kind": how},
            "e2e": e2e,
            "gpu_launches": launches,
