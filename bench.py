@@ -754,6 +754,24 @@ def main():
            "e2e": e2e,
            "gpu_launches": launches,
            "clocks": clk.summary()}
+    # one line per regime: does JUMP beat BAOAB at matched temperature and diffusion?
+    summ = {}
+    if dif:
+        summ["dsf_1fs"] = (f"JUMP {jump_nsday:.1f} vs BAOAB {baoab_nsday:.1f} ns/day; "
+                           f"D ratio {dif['jump_D'] / dif['baoab_D']:.3f}: not matched")
+    if ewald:
+        b = ewald.get("baoab_respa1_D6", {})
+        best = None
+        for k, v in ewald.items():
+            if k.startswith("jump_respa1") and isinstance(v, dict) and "D_ratio" in v and "T_mean" in v and b.get("T_mean"):
+                ok = abs(v["D_ratio"] - 1) <= 0.05 and abs(v["T_mean"] / b["T_mean"] - 1) <= 0.005
+                if ok and (best is None or v["ns_per_day"] > best[1]["ns_per_day"]):
+                    best = (k, v)
+        if best:
+            summ["ewald_respa1"] = (f"{best[0]} {best[1]['ns_per_day']:.1f} vs BAOAB-RESPA1 Delta 6 "
+                                    f"{b['ns_per_day']:.1f} ns/day ({best[1]['ns_per_day'] / b['ns_per_day']:.3f}x) "
+                                    f"at T within 0.5 % and D within 5 %")
+    out["matched_summary"] = summ
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         secs, done, thr = cpu_oracle_sample(w, JUMP_PARAMS, args.cpu_sample, 1)
         out["cpu_baseline"] = {"value": ns_per_day(done / n * DT_FS, secs), "unit": "ns/day", "cores": thr,
