@@ -30,3 +30,23 @@ def test_oracle_repeats_its_record(oracle_mod, integrator):
     else:
         np.testing.assert_allclose(got["energy"], ref["energy"], rtol=1e-6)
         np.testing.assert_allclose(got["x_first"], ref["x_first"], atol=1e-6)
+
+
+@pytest.mark.parametrize("integrator", ["jump_respa1", "baoab_respa1"])
+def test_oracle_repeats_its_ewald_record(oracle_mod, integrator):
+    """the same for the Ewald / smooth-PME path (tests/golden/oracle_648_ewald.json,
+    written by tests/golden/make_golden_ewald.py): 60 innermost steps of the
+    RESPA1 pair at the paper's settings"""
+    import sys
+    sys.path.insert(0, HERE)
+    import make_golden_ewald
+    rec = json.load(open(os.path.join(HERE, "oracle_648_ewald.json")))
+    got = make_golden_ewald.run(integrator)
+    ref = rec[integrator]
+    assert got["rc"] == ref["rc"] == 0 and got["step"] == ref["step"] == 60
+    if platform.machine() == rec["machine"]:
+        np.testing.assert_allclose(got.pop("energy"), ref["energy"], rtol=1e-12)
+        assert got == {k: v for k, v in ref.items() if k != "energy"}
+    else:
+        np.testing.assert_allclose(got["energy"], ref["energy"], rtol=1e-6)
+        np.testing.assert_allclose(got["x_first"], ref["x_first"], atol=1e-6)
