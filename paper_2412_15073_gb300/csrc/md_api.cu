@@ -1140,11 +1140,14 @@ int tune_vphase(md_ctx* ctx, const double* a, double tau2)
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    float best = 1e30f;
-    int pick = 0;
+    // each variant: one warm-up launch, then the fastest of three (robust to
+    // interference); the set-up order replaces the rate ordering only when it
+    // is clearly (2 %) faster, since the tuned phase is a single one
+    float best[2] = {1e30f, 1e30f};
+    int pick[2] = {0, NVPHASE_VARIANTS};
     for (int v = 0; v < NVPHASE_LAUNCH_VARIANTS; ++v) {
-        float tot = 0;
-        for (int rep = 0; rep < 2; ++rep) {
+        float tmin = 1e30f;
+        for (int rep = 0; rep < 4; ++rep) {
             CK(cudaMemcpyAsync(d.v, vs, sizeof(double) * 3 * d.N, cudaMemcpyDeviceToDevice, ctx->s));
             cudaEventRecord(e0, ctx->s);
             launch_vphase(d, a, tau2, 0, 0, 0, 1, 1, 0, v, ctx->s, 0, single_params(ctx));
@@ -1152,10 +1155,12 @@ int tune_vphase(md_ctx* ctx, const double* a, double tau2)
             cudaEventSynchronize(e1);
             float ms = 0;
             cudaEventElapsedTime(&ms, e0, e1);
-            if (rep) tot += ms;
+            if (rep) tmin = std::min(tmin, ms);
         }
-        if (tot < best) { best = tot; pick = v; }
+        const int g = v >= NVPHASE_VARIANTS;
+        if (tmin < best[g]) { best[g] = tmin; pick[g] = v; }
     }
+    const int pick_v = best[1] < 0.98f * best[0] ? pick[1] : pick[0];
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     CK(cudaMemcpyAsync(d.v, vs, sizeof(double) * 3 * d.N, cudaMemcpyDeviceToDevice, ctx->s));
@@ -1163,7 +1168,7 @@ int tune_vphase(md_ctx* ctx, const double* a, double tau2)
     CK(cudaMemcpyAsync(d.ev_n, evs, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, ctx->s));
     CK(cudaMemcpyAsync(d.err, es, sizeof(uint32_t) * d.R, cudaMemcpyDeviceToDevice, ctx->s));
     CK(cudaStreamSynchronize(ctx->s));
-    ctx->vvar = pick;
+    ctx->vvar = pick_v;
     return MD_OK;
 }
 
