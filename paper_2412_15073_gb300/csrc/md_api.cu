@@ -1264,6 +1264,16 @@ int run_units(md_ctx* ctx, int key, double tau, int spu, long long units, Body b
         launch_advance(d, spu, ctx->s);
         ctx->nlaunch[5] += 1;
         done = 1;
+        // graphs of an older device layout can never replay again: release them
+        // (every earlier call ended with a synchronisation; the private stream is idle)
+        for (size_t k = 0; k < ctx->graphs.size();) {
+            if (ctx->graphs[k].gen != ctx->gen) {
+                cudaGraphExecDestroy(ctx->graphs[k].exec);
+                ctx->graphs.erase(ctx->graphs.begin() + (long)k);
+            } else {
+                ++k;
+            }
+        }
         const md_ctx::Graph* g = nullptr;
         for (const auto& x : ctx->graphs)
             if (x.gen == ctx->gen && x.key == key && x.tau == tau && x.n_inner == spu && x.units == G) g = &x;
