@@ -293,13 +293,24 @@ def e2e_run(ej, args, M, torch, stream, n, world, max_over_ranks, barrier):
             "path": "md_set_state(host) + md_step_jump(K) + md_get_state(host) per bench step of K MD steps"}
 
 
+def ewald_equilibrate(args, M, w, stream, device, seed):
+    """Relax the (DSF-equilibrated) start in the Ewald force field at strong
+    friction, so that the Ewald runs start at 300 K in their own potential."""
+    eq = M.Engine(precision=M.MD_MIXED, seed=seed, device=device, stream=stream.cuda_stream)
+    eq.set_system(0, w, **(EWALD_BAOAB_PARAMS | {"gamma": 20.0}))
+    eq.baoab(max(args.equil, 1))
+    w.x, w.v = eq.state()[0], eq.state()[1]
+    eq.close()
+
+
 def ewald_leg(args, M, engine, timed, stream, world, max_over_ranks, barrier, mass):
     """JUMP-RESPA1 against BAOAB-RESPA1 under Ewald electrostatics (smooth PME
     at the outer level of both): ns/day, temperature and oxygen self-diffusion
-    of each, on the same equilibrated start. delta 1 fs (bonded), kappa 2 fs
-    (short pairs, and the jumps of JUMP-RESPA1), Delta = 6 fs (reciprocal part;
-    plus the long real-space pairs for BAOAB-RESPA1, also run at Delta = 4 fs)."""
-    m_mid = 2
+    of each, on the same equilibrated start, with plain BAOAB at 1 fs as the
+    reference both are matched against. delta 1 fs (bonded); kappa 2 fs (the
+    paper's) or 3 fs (short pairs, and the jumps of JUMP-RESPA1); Delta = 6 fs
+    (reciprocal part and the LJ long part; plus the long real-space pairs for
+    BAOAB-RESPA1, which also runs at Delta = 4 fs)."""
     ew = dict(EWALD)
     if args.ewald_alpha:
         ew["dsf_alpha"] = args.ewald_alpha
@@ -322,15 +333,25 @@ def ewald_leg(args, M, engine, timed, stream, world, max_over_ranks, barrier, ma
                              % (ew["dsf_alpha"], ew["pme_order"], ew["pme_spacing"]),
            "split": {"r_c": jp["r_split"], "h": jp["h_switch"], "rings": jp["ring_r"],
                      "lj_long_mode": jp["lj_long_mode"], "jump_skin": jp["skin"], "baoab_skin": bp["skin"]},
-           "levels": "delta 1 fs, kappa 2 fs, Delta 6 fs (BAOAB-RESPA1 also 4 fs)"}
+           "levels": "delta 1 fs; kappa 2 fs or 3 fs (k3); Delta 6 fs or 4 fs (D4)"}
     eps_list = args.ewald_eps0 or EWALD_EPS0
-    runs = [(f"jump_respa1_eps{e:g}", 5, "jump_respa1", 3, jp | {"eps0": e}) for e in eps_list]
-    runs += [(f"baoab_respa1_D{2 * q}", 6, "baoab_respa1", q, bp) for q in (3, 2)]
-    for name, seed, meth, n_out, params in runs:
+    # (name, seed, method, m_mid, n_outer, params); plain BAOAB is the reference
+    runs = [("baoab_1fs", 4, "baoab", 1, 1, bp)]
+    runs += [(f"jump_respa1_eps{e:g}", 5, "jump_respa1", 2, 3, jp | {"eps0": e}) for e in eps_list]
+    runs += [(f"jump_respa1_D4_eps{EWALD_EPS0[-1]:g}", 5, "jump_respa1", 2, 2, jp | {"eps0": EWALD_EPS0[-1]}),
+             (f"jump_respa1_k3_eps{EWALD_EPS0[-1]:g}", 5, "jump_respa1", 3, 2, jp | {"eps0": EWALD_EPS0[-1]})]
+    runs += [("baoab_respa1_D6", 6, "baoab_respa1", 2, 3, bp), ("baoab_respa1_D4", 6, "baoab_respa1", 2, 2, bp),
+             ("baoab_respa1_k3_D6", 6, "baoab_respa1", 3, 2, bp)]
+    if args.ewald_runs:
+        runs = [r for r in runs if r[0] in args.ewald_runs or r[0] == "baoab_1fs"]
+    for name, seed, meth, m_mid, n_out, params in runs:
         per_cycle = m_mid * n_out
         cyc = max(args.steps // per_cycle, 1)
         e = engine(seed, params)
-        run = lambda k, e=e, meth=meth, n_out=n_out: getattr(e, meth)(k, 1.0, m_mid, n_out)
+        if meth == "baoab":
+            run = lambda k, e=e: e.baoab(k)
+        else:
+            run = lambda k, e=e, meth=meth, m_mid=m_mid, n_out=n_out: getattr(e, meth)(k, 1.0, m_mid, n_out)
         try:
             run(max(1, 120 // per_cycle))           # settle in the Ewald force field
             c0 = e.observables()
@@ -350,24 +371,44 @@ def ewald_leg(args, M, engine, timed, stream, world, max_over_ranks, barrier, ma
             ms, _, _ = e.profile(enable=0)
             r["class_ms_per_fs"] = {c: round(float(m) / (pc * per_cycle), 4) for c, m in zip(CLASSES, ms)}
             if args.dsteps > 0 and r["stable"]:
-                every = 96                          # a multiple of both cycle lengths (4 and 6 fs)
-                nd = 2 * args.dsteps // every * every   # twice the 1 fs window: RESPA1 steps are cheap
+                every = 96                          # a multiple of every cycle length (1, 4, 6 fs)
+                nd = 4 * args.dsteps // every * every   # four times the 1 fs leg's window
                 r["D"], r["T_mean"] = diffusion(e, lambda k: run(k // per_cycle), nd, every, BOX, DT_FS, mass)
             res[name] = r
         except M.MDError as ex:
             res[name] = {"error": str(ex), "stable": False}
         e.close()
-    b = res.get("baoab_respa1_D6", {})
-    if not b.get("stable"):
-        b = res.get("baoab_respa1_D4", {})
-    for k in list(res):
-        if k.startswith("jump_respa1") and "ns_per_day" in res[k] and b.get("ns_per_day"):
-            res[k]["speedup_vs_baoab_respa1"] = res[k]["ns_per_day"] / b["ns_per_day"]
-            if "D" in res[k] and b.get("D"):
-                res[k]["D_ratio"] = res[k]["D"] / b["D"]
+    # matched to plain BAOAB at 1 fs (the most accurate integrator here): mean
+    # temperature within 0.5 % and D within 5 %. (The kinetic temperature read
+    # at the end of a step carries an O(dt^2) bias of each splitting on the
+    # stiff O-H modes: the 6 fs outer steps read about 1.5 % above 1 fs.)
+    ref = res.get("baoab_1fs", {})
+    for k, v in res.items():
+        if not isinstance(v, dict) or "ns_per_day" not in v:
+            continue
+        if "D" in v and ref.get("D") and ref.get("T_mean"):
+            v["D_ratio"] = v["D"] / ref["D"]
+            v["T_ratio"] = v["T_mean"] / ref["T_mean"]
+            v["matched"] = bool(abs(v["D_ratio"] - 1) <= 0.05 and abs(v["T_ratio"] - 1) <= 0.005)
+    best = {}
+    for fam in ("jump", "baoab"):
+        cands = [(k, v) for k, v in res.items() if isinstance(v, dict) and k.startswith(fam) and v.get("matched")]
+        if cands:
+            k, v = max(cands, key=lambda kv: kv[1]["ns_per_day"])
+            best[fam] = {"run": k, "ns_per_day": v["ns_per_day"]}
+    if len(best) == 2:
+        best["jump_over_baoab"] = best["jump"]["ns_per_day"] / best["baoab"]["ns_per_day"]
+    res["best_matched"] = best
     res["D_unit"] = "1e-5 cm^2/s"
-    res["D_window_ps"] = 2 * args.dsteps // 96 * 96 * DT_FS * 1e-3
+    res["D_window_ps"] = 4 * args.dsteps // 96 * 96 * DT_FS * 1e-3
     res["T_mean_note"] = "mean over the D samples (every 96 fs), 3N degrees of freedom"
+    res["matched_note"] = "matched: mean T within 0.5 % and D within 5 % of plain BAOAB at 1 fs"
+    # the paper's comparison: the two RESPA1 schemes at the same levels (1:2:6 fs)
+    jb, bb = res.get(f"jump_respa1_eps{EWALD_EPS0[-1]:g}", {}), res.get("baoab_respa1_D6", {})
+    if jb.get("D") and bb.get("D"):
+        res["same_levels"] = {"levels": "1:2:6 fs", "jump": f"jump_respa1_eps{EWALD_EPS0[-1]:g}",
+                              "speed_ratio": jb["ns_per_day"] / bb["ns_per_day"],
+                              "T_ratio": jb["T_mean"] / bb["T_mean"], "D_ratio": jb["D"] / bb["D"]}
     return res
 
 
@@ -526,6 +567,7 @@ def main():
                     help="lj_long_mode of the Ewald JUMP runs (default 1, the paper's GPU setting)")
     ap.add_argument("--ewald-jump-skin", type=float, default=None, help="list skin of the Ewald JUMP runs (A)")
     ap.add_argument("--ewald-baoab-skin", type=float, default=None, help="list skin of the Ewald BAOAB runs (A)")
+    ap.add_argument("--ewald-runs", nargs="*", default=None, help="only these Ewald runs (plus the 1 fs reference)")
     ap.add_argument("--ewald-rings", type=float, nargs="*", default=None,
                     help="interior ring edges of the Ewald JUMP runs (A; none given = one ring)")
     ap.add_argument("--ewald-split", type=float, default=None,
@@ -561,6 +603,8 @@ def main():
         e.set_system(0, w, **params)
         return e
 
+    if args.only in ("ewald", "spectra", "jump_respa1_ewald", "baoab_respa1_ewald") and args.equil > 0:
+        ewald_equilibrate(args, M, w, stream, local, ranks.seed(98))
     if args.only == "ewald":
         out = ewald_leg(args, M, engine, timed, stream, world, max_over_ranks, barrier, w.mass)
         if rank == 0:
@@ -715,6 +759,10 @@ def main():
                "method": "O atoms, Einstein MSD over all origins, fit over 20-80 % of the lags; "
                          "T averaged over the same samples"}
 
+    # the Ewald legs start from the same state relaxed in the Ewald force field
+    # (after the DSF runs above, which keep their own start)
+    if (args.ewald or args.spectra > 0) and args.equil > 0:
+        ewald_equilibrate(args, M, w, stream, local, ranks.seed(98))
     ewald = None
     if args.ewald:
         ewald = ewald_leg(args, M, engine, timed, stream, world, max_over_ranks, barrier, w.mass)
@@ -759,18 +807,12 @@ def main():
     if dif:
         summ["dsf_1fs"] = (f"JUMP {jump_nsday:.1f} vs BAOAB {baoab_nsday:.1f} ns/day; "
                            f"D ratio {dif['jump_D'] / dif['baoab_D']:.3f}: not matched")
-    if ewald:
-        b = ewald.get("baoab_respa1_D6", {})
-        best = None
-        for k, v in ewald.items():
-            if k.startswith("jump_respa1") and isinstance(v, dict) and "D_ratio" in v and "T_mean" in v and b.get("T_mean"):
-                ok = abs(v["D_ratio"] - 1) <= 0.05 and abs(v["T_mean"] / b["T_mean"] - 1) <= 0.005
-                if ok and (best is None or v["ns_per_day"] > best[1]["ns_per_day"]):
-                    best = (k, v)
-        if best:
-            summ["ewald_respa1"] = (f"{best[0]} {best[1]['ns_per_day']:.1f} vs BAOAB-RESPA1 Delta 6 "
-                                    f"{b['ns_per_day']:.1f} ns/day ({best[1]['ns_per_day'] / b['ns_per_day']:.3f}x) "
-                                    f"at T within 0.5 % and D within 5 %")
+    if ewald and ewald.get("best_matched"):
+        bm = ewald["best_matched"]
+        if "jump_over_baoab" in bm:
+            summ["ewald"] = (f"fastest JUMP matched to BAOAB at 1 fs (T within 0.5 %, D within 5 %): "
+                             f"{bm['jump']['run']} {bm['jump']['ns_per_day']:.1f} ns/day; fastest such BAOAB: "
+                             f"{bm['baoab']['run']} {bm['baoab']['ns_per_day']:.1f} ns/day ({bm['jump_over_baoab']:.3f}x)")
     out["matched_summary"] = summ
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         secs, done, thr = cpu_oracle_sample(w, JUMP_PARAMS, args.cpu_sample, 1)
