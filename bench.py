@@ -49,7 +49,7 @@ BAOAB_PARAMS = PARAMS
 # the 1/eps0 floor, not by the ring bounds, and fewer list kinds are built) and
 # a 0.4 A skin; for BAOAB-RESPA1 the 0.5 A skin.
 EWALD = dict(dsf_alpha=0.42, coulomb_mode=1, pme_order=6, pme_spacing=0.8, r_split=6.0)
-EWALD_EPS0 = [0.1, 1.0, 2.0]
+EWALD_EPS0 = [2.0]              # the full sweep (0.1, 1, 2): --ewald-eps0 0.1 1 2
 EWALD_JUMP_PARAMS = JUMP_PARAMS | EWALD | dict(ring_r=[], lj_long_mode=2, skin=0.4)
 EWALD_BAOAB_PARAMS = BAOAB_PARAMS | EWALD
 DT_FS = 1.0
