@@ -119,7 +119,8 @@ typedef struct {
                         * 1: Ewald (Sec. 3.1 splits its real-space part like DSF): pair term
                         *    erfc(a r)/r cut at r_cut with a = dsf_alpha > 0, no shift; the
                         *    reciprocal part by smooth PME (cardinal B-splines of order pme_order
-                        *    in [4, 8], grid of K^3 points, K the smallest 2,3,5-smooth integer
+                        *    4, 6 or 8 (an odd order has |b(m)| = 0 at m = K/2 on even grids),
+                        *    grid of K^3 points, K the smallest 2,3,5-smooth integer
                         *    >= max(box / pme_spacing, 2 pme_order)), the self energy
                         *    -C a / sqrt(pi) sum q^2 and, for excluded pairs, -C q_i q_j erf(a r)/r.
                         *    The reciprocal part is deterministic: it belongs to F0 (gradient

@@ -145,6 +145,8 @@ class Oracle:
         self.n = sys.n
         if skin_outer is None:
             skin_outer = skin
+        if coulomb_mode == 1 and pme_order not in (4, 6, 8):
+            raise ValueError("pme_order must be 4, 6 or 8 (an odd order has b(m) = 0 at m = K/2 on even grids)")
         rr = list(ring_r or [])
         n_rings = len(rr) + 1 if ring_r is not None else 0
         self.params = Params(sys.box, r_cut, r_split, h_switch, r_mid, dsf_alpha, gamma,

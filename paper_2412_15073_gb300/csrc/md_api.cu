@@ -517,8 +517,10 @@ int check_sys(md_ctx* ctx, const md_system* s)
     if (s->coulomb_mode != 0 && s->coulomb_mode != 1)
         FAIL(MD_EINVAL, "md_set_system: coulomb_mode must be 0 (DSF) or 1 (Ewald)");
     if (s->coulomb_mode == 1) {
-        if (!(s->dsf_alpha > 0) || s->pme_order < 4 || s->pme_order > 8 || !(s->pme_spacing > 0))
-            FAIL(MD_EINVAL, "md_set_system: Ewald needs dsf_alpha > 0, pme_order in [4, 8], pme_spacing > 0");
+        // an odd order makes the B-spline factor |b(m)|^2 vanish at m = K/2 on an even grid
+        if (!(s->dsf_alpha > 0) || (s->pme_order != 4 && s->pme_order != 6 && s->pme_order != 8) ||
+            !(s->pme_spacing > 0))
+            FAIL(MD_EINVAL, "md_set_system: Ewald needs dsf_alpha > 0, pme_order 4, 6 or 8, pme_spacing > 0");
         if (!(s->box / s->pme_spacing <= 1024))
             FAIL(MD_EINVAL, "md_set_system: PME grid above 1024 points per edge");
     }

@@ -123,13 +123,16 @@ def test_ewald_graphs_replay_plain_launches(M, oracle_mod, water648, integ, args
 
 def test_ewald_and_dsf_replicas_side_by_side(M, oracle_mod, water648):
     """replicas of one context with different electrostatics and grids: each
-    matches its own oracle (grid offsets, per-replica plans)"""
+    matches its own oracle (grid offsets, per-replica plans); odd B-spline
+    orders are refused"""
     w1 = perturbed(water648, seed=5)
-    cfgs = [dict(EWALD, coulomb_mode=0, dsf_alpha=0.2), dict(EWALD), dict(EWALD, pme_spacing=0.7, pme_order=5)]
+    cfgs = [dict(EWALD, coulomb_mode=0, dsf_alpha=0.2), dict(EWALD), dict(EWALD, pme_spacing=0.7, pme_order=4)]
     syss = [water648, w1, perturbed(water648, seed=9)]
     e = M.Engine(precision=0, seed=3, max_replicas=3)
     for r, (s, p) in enumerate(zip(syss, cfgs)):
         e.set_system(r, s, **p)
+    with pytest.raises(M.MDError):
+        e.set_system(2, syss[2], **dict(EWALD, pme_order=5))
     for r, (s, p) in enumerate(zip(syss, cfgs)):
         o = oracle_mod.Oracle(s, seed=3, replica=r, **p)
         total, _ = o.gradient(0)

@@ -119,3 +119,41 @@ def test_ewald_dynamics_keep_temperature_and_jump_forces_are_weak(oracle_mod, wa
         o = oracle_mod.Oracle(water648, seed=3, **p)
         assert getattr(o, how)(*args) == 0, how
         assert np.isfinite(o.state()[1]).all()
+
+
+@pytest.mark.parametrize("order,spacing,tol", [(4, 0.5, 2e-2), (8, 0.8, 5e-4)])
+def test_smooth_pme_converges_to_the_plain_sum_for_each_order(oracle_mod, water648, order, spacing, tol):
+    """the other B-spline orders the GPU path takes (4 and 8; 6 above)
+    interpolate the plain Ewald sum: energy within tol kcal/mol, gradients
+    within 1e-3 of their rms"""
+    o = oracle_mod.Oracle(water648, r_cut=9.0, r_split=5.0, dsf_alpha=0.35, coulomb_mode=1, skin=0.2,
+                          skin_outer=0.3, pme_order=order, pme_spacing=spacing)
+    g_pme, e_pme, K = o.ewald_recip_pme()
+    g_plain, e_plain = o.ewald_recip_plain(16)
+    assert abs(e_pme - e_plain) < tol
+    rms = np.sqrt((g_plain ** 2).sum(1).mean())
+    assert np.abs(g_pme - g_plain).max() < 1e-3 * rms
+
+
+def test_smooth_pme_gradient_error_falls_with_the_grid(oracle_mod, water648):
+    """refining the grid (order 6) brings the smooth-PME gradient closer to the
+    plain sum's: the interpolation error shrinks with the spacing"""
+    errs = []
+    g_plain = None
+    for spacing in (1.2, 0.9, 0.6, 0.5):
+        o = oracle_mod.Oracle(water648, r_cut=9.0, r_split=5.0, dsf_alpha=0.35, coulomb_mode=1, skin=0.2,
+                              skin_outer=0.3, pme_order=6, pme_spacing=spacing)
+        g, _, _ = o.ewald_recip_pme()
+        if g_plain is None:
+            g_plain, _ = o.ewald_recip_plain(16)
+        errs.append(np.abs(g - g_plain).max())
+    assert errs[0] > errs[1] > errs[2] > errs[3], errs
+    assert errs[0] > 100 * errs[3]
+
+
+def test_odd_pme_orders_are_refused(oracle_mod, water648):
+    """an odd B-spline order makes |b(m)|^2 vanish at m = K/2 on an even grid
+    (the Euler exponential spline has a zero at the Nyquist index), so its
+    G(m) would divide by zero: only the even orders 4, 6, 8 are taken"""
+    with pytest.raises(ValueError):
+        oracle_mod.Oracle(water648, r_cut=9.0, coulomb_mode=1, pme_order=5)
