@@ -203,6 +203,16 @@ template <typename T> int dalloc(md_ctx* ctx, T** p, size_t count)
     return MD_OK;
 }
 
+// release a buffer that a larger one replaced (stream-ordered: launches
+// already queued, and graphs already launched, still see it)
+void dfree(md_ctx* ctx, void* p)
+{
+    auto it = std::find(ctx->bufs.begin(), ctx->bufs.end(), p);
+    if (it == ctx->bufs.end()) return;
+    cudaFreeAsync(p, ctx->s);
+    ctx->bufs.erase(it);
+}
+
 template <typename T> int upload(md_ctx* ctx, T* dst, const T* src, size_t count)
 {
     if (!count) return MD_OK;
@@ -230,8 +240,6 @@ void free_device(md_ctx* ctx)
     ctx->on_device = false;
 }
 
-// does some replica keep the LJ long part deterministic (its short gradient
-// then also runs over the LJ list)?
 // does some replica keep the LJ long part at the slow level (lj_long_mode 2)?
 bool any_lj_slow(const md_ctx* ctx)
 {
@@ -240,6 +248,8 @@ bool any_lj_slow(const md_ctx* ctx)
     return false;
 }
 
+// does some replica keep the LJ long part deterministic (its short gradient
+// then also runs over the LJ list)?
 bool any_lj_long(const md_ctx* ctx)
 {
     for (const RepParams& P : ctx->hp)
@@ -606,6 +616,7 @@ int fit_caps(md_ctx* ctx, int kinds_to_check, bool outer)
                 const int cap = (int(mx * 1.4) + 64 + 31) / 32 * 32;
                 uint32_t* p;
                 if ((rc = dalloc(ctx, &p, (size_t)d.N * cap))) return rc;
+                dfree(ctx, d.olist);
                 d.olist = p; d.ocap = cap;
                 grow = true;
             }
@@ -618,6 +629,7 @@ int fit_caps(md_ctx* ctx, int kinds_to_check, bool outer)
                 const int cap = (int(mx * 1.4) + 64 + 31) / 32 * 32;
                 uint32_t* p;
                 if ((rc = dalloc(ctx, &p, (size_t)d.N * cap))) return rc;
+                dfree(ctx, d.list[k]);
                 d.list[k] = p; d.lcap[k] = cap;
                 grow = true;
             }
@@ -926,8 +938,11 @@ int ensure_kinds(md_ctx* ctx, int mask)
     int rc;
     for (int k = 0; k < NKIND; ++k) {
         if (!(add & (1 << k))) continue;
+        uint32_t* p;
+        if ((rc = dalloc(ctx, &p, (size_t)d.N * kind_cap(ctx, k)))) return rc;
+        dfree(ctx, d.list[k]);
+        d.list[k] = p;
         d.lcap[k] = kind_cap(ctx, k);
-        if ((rc = dalloc(ctx, &d.list[k], (size_t)d.N * d.lcap[k]))) return rc;
     }
     launch_late_lists(d, add, ctx->s);
     CK(cudaGetLastError());
