@@ -158,8 +158,6 @@ struct md_ctx {
     // pinned staging
     double* h_stepc = nullptr;
     uint32_t* h_err = nullptr;
-    void* stage = nullptr;
-    size_t stage_bytes = 0;
 };
 
 static std::string g_init_msg = "no error";
@@ -1185,6 +1183,7 @@ int tune_vphase(md_ctx* ctx, const double* a, double tau2)
     CK(cudaMemcpyAsync(d.ev_n, evs, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, ctx->s));
     CK(cudaMemcpyAsync(d.err, es, sizeof(uint32_t) * d.R, cudaMemcpyDeviceToDevice, ctx->s));
     CK(cudaStreamSynchronize(ctx->s));
+    for (void* p : {(void*)vs, (void*)cs, (void*)evs, (void*)es}) dfree(ctx, p);
     ctx->vvar = pick_v;
     return MD_OK;
 }
@@ -1376,24 +1375,28 @@ extern "C" {
 
 int md_init(md_ctx** out, const md_config* cfg)
 {
-    if (!out || !cfg) { g_init_msg = "md_init: null argument"; return MD_EINVAL; }
+    if (!out || !cfg) { set_global_error("md_init: null argument"); return MD_EINVAL; }
     *out = nullptr;
-    if (cfg->precision != MD_FP64 && cfg->precision != MD_MIXED) { g_init_msg = "md_init: precision must be MD_FP64 or MD_MIXED"; return MD_EINVAL; }
-    if (cfg->max_replicas < 1 || cfg->max_replicas > 65536) { g_init_msg = "md_init: max_replicas out of range"; return MD_EINVAL; }
+    if (cfg->precision != MD_FP64 && cfg->precision != MD_MIXED) { set_global_error("md_init: precision must be MD_FP64 or MD_MIXED"); return MD_EINVAL; }
+    if (cfg->max_replicas < 1 || cfg->max_replicas > 65536) { set_global_error("md_init: max_replicas out of range"); return MD_EINVAL; }
     if (cfg->threads_per_atom != 0 && cfg->threads_per_atom != 1 && cfg->threads_per_atom != 2 &&
-        cfg->threads_per_atom != 4 && cfg->threads_per_atom != 8) { g_init_msg = "md_init: threads_per_atom must be 0, 1, 2, 4 or 8"; return MD_EINVAL; }
-    if (cfg->event_log_cap < 0) { g_init_msg = "md_init: event_log_cap < 0"; return MD_EINVAL; }
+        cfg->threads_per_atom != 4 && cfg->threads_per_atom != 8) { set_global_error("md_init: threads_per_atom must be 0, 1, 2, 4 or 8"); return MD_EINVAL; }
+    if (cfg->event_log_cap < 0) { set_global_error("md_init: event_log_cap < 0"); return MD_EINVAL; }
     cudaError_t e = cudaSetDevice(cfg->device);
-    if (e != cudaSuccess) { g_init_msg = std::string("md_init: cudaSetDevice: ") + cudaGetErrorString(e); return MD_ECUDA; }
+    if (e != cudaSuccess) { set_global_error(std::string("md_init: cudaSetDevice: ") + cudaGetErrorString(e)); return MD_ECUDA; }
     md_ctx* ctx = new md_ctx();
     ctx->cfg = *cfg;
     ctx->s = (cudaStream_t)cfg->cuda_stream;
     ctx->fp64 = cfg->precision == MD_FP64;
     ctx->tpa_cfg = cfg->threads_per_atom;
     ctx->reps.resize(cfg->max_replicas);
-    if (cudaMallocHost((void**)&ctx->h_stepc, sizeof(double) * 2 * cfg->max_replicas) != cudaSuccess ||
-        cudaMallocHost((void**)&ctx->h_err, sizeof(uint32_t) * cfg->max_replicas) != cudaSuccess) {
-        g_init_msg = "md_init: pinned host allocation failed";
+    bool ok = cudaMallocHost((void**)&ctx->h_stepc, sizeof(double) * 2 * cfg->max_replicas) == cudaSuccess;
+    if (ok && cudaMallocHost((void**)&ctx->h_err, sizeof(uint32_t) * cfg->max_replicas) != cudaSuccess) {
+        cudaFreeHost(ctx->h_stepc);
+        ok = false;
+    }
+    if (!ok) {
+        set_global_error("md_init: pinned host allocation failed");
         delete ctx;
         return MD_ENOMEM;
     }
@@ -1956,8 +1959,9 @@ int md_vacf_get(md_ctx* ctx, int replica, int64_t n_lags, double* vacf_out, doub
     if ((vacf_out && cudaMemcpyAsync(vacf_out, C, n_lags * sizeof(double), cudaMemcpyDeviceToHost, ctx->s) != cudaSuccess) ||
         (spectrum_out && cudaMemcpyAsync(spectrum_out, S, n_lags * sizeof(double), cudaMemcpyDeviceToHost, ctx->s) != cudaSuccess))
         return fail("copy to host");
+    const cudaError_t se = cudaStreamSynchronize(ctx->s);
     cleanup();
-    CK(cudaStreamSynchronize(ctx->s));
+    if (se != cudaSuccess) FAIL(MD_ECUDA, "md_vacf_get: %s", cudaGetErrorString(se));
     return MD_OK;
 }
 
