@@ -180,6 +180,15 @@ class Engine:
                     bond_r0=a(sys.bond_r0, np.float64), angles=a(sys.angles, np.int32),
                     angle_k=a(sys.angle_k, np.float64), angle_t0=a(sys.angle_t0, np.float64),
                     excl=a(sys.excl, np.int32))
+        # the library reads these through plain pointers: check their sizes here
+        n, nt = int(sys.n), int(keep["lj_eps"].shape[0])
+        sizes = dict(x=3 * n, v=3 * n, mass=n, charge=n, type=n, lj_eps=nt * nt, lj_sigma=nt * nt,
+                     bonds=2 * len(keep["bond_k"]), bond_r0=len(keep["bond_k"]),
+                     angles=3 * len(keep["angle_k"]), angle_t0=len(keep["angle_k"]),
+                     excl=2 * int(keep["excl"].shape[0]))
+        for name, want in sizes.items():
+            if keep[name].size != want:
+                raise ValueError(f"set_system: {name} has {keep[name].size} values, expected {want}")
         s = MdSystem(sys.n, sys.box, _ptr(keep["x"]), _ptr(keep["v"]), _ptr(keep["mass"]),
                      _ptr(keep["charge"]), _ptr(keep["type"]), int(sys.lj_eps.shape[0]),
                      _ptr(keep["lj_eps"]), _ptr(keep["lj_sigma"]), len(sys.bond_k), _ptr(keep["bonds"]),
@@ -206,6 +215,10 @@ class Engine:
     def set_state(self, replica, x, v, img=None, x_build=None, x_outer=None, step=0):
         f = lambda z, t: None if z is None else np.ascontiguousarray(z, dtype=t)
         x, v, img, xb, xo = f(x, np.float64), f(v, np.float64), f(img, np.int32), f(x_build, np.float64), f(x_outer, np.float64)
+        n3 = 3 * self.n[replica]
+        for name, z in (("x", x), ("v", v), ("img", img), ("x_build", xb), ("x_outer", xo)):
+            if z is not None and z.size != n3:
+                raise ValueError(f"set_state: {name} has {z.size} values, expected {n3}")
         self._ck(self.L.md_set_state(self.h, replica, _ptr(x), _ptr(v), _ptr(img), _ptr(xb), _ptr(xo), int(step)))
 
     def baoab(self, nsteps, dt_fs=1.0):

@@ -64,3 +64,55 @@ def test_no_cpu_fallback_in_the_product_path():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 txt = open(os.path.join(dp, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt and "liboracle" not in txt, f
+
+
+class _StubLib:
+    """stands in for libmdjump.so: records the md_system the binding builds"""
+
+    def __init__(self):
+        self.sys = None
+
+    def md_set_system(self, h, replica, ref):
+        s = ref._obj
+        self.sys = {k: getattr(s, k) for k, _ in s._fields_}
+        self.sys["ring_r"] = list(s.ring_r)
+        return 0
+
+    def md_set_state(self, *args):
+        return 0
+
+
+def _stub_engine():
+    import paper_2412_15073_gb300 as M
+    e = M.Engine.__new__(M.Engine)
+    e.L, e.h, e.n = _StubLib(), None, {}
+    return e
+
+
+def test_binding_marshals_the_system_and_checks_sizes():
+    """argument marshalling of set_system / set_state on the host (no GPU):
+    counts, ring edges and electrostatics reach md_system; arrays whose sizes
+    disagree with n_atoms are refused before the library reads them"""
+    from paper_2412_15073_gb300 import systems
+    w = systems.water_box(8, box=12.0, seed=0)
+    e = _stub_engine()
+    e.set_system(0, w, ring_r=[6.0, 7.5], coulomb_mode=1, pme_order=8, lj_long_mode=2, skin=0.25)
+    s = e.L.sys
+    assert s["n_atoms"] == w.n == 24 and s["n_bonds"] == len(w.bond_k) and s["n_angles"] == len(w.angle_k)
+    assert s["n_excl"] == w.excl.shape[0] and s["n_types"] == w.lj_eps.shape[0]
+    assert s["n_rings"] == 3 and s["ring_r"][:2] == [6.0, 7.5]
+    assert (s["coulomb_mode"], s["pme_order"], s["lj_long_mode"]) == (1, 8, 2)
+    assert s["skin"] == 0.25 and s["skin_outer"] == 0.25
+    with pytest.raises(ValueError):
+        e.set_system(0, w, ring_r=[5.5, 6.0, 7.0, 8.0])
+    bad = w.copy()
+    bad.v = bad.v[:-1]
+    with pytest.raises(ValueError, match="v has"):
+        e.set_system(0, bad)
+    bad = w.copy()
+    bad.charge = bad.charge[:-2]
+    with pytest.raises(ValueError, match="charge has"):
+        e.set_system(0, bad)
+    e.set_state(0, w.x, w.v)
+    with pytest.raises(ValueError, match="v has"):
+        e.set_state(0, w.x, w.v[:3])
