@@ -573,11 +573,10 @@ void launch_pme_bin(const Dev& d, int fp64, cudaStream_t s)
 
 void launch_pme_spread(const Dev& d, int order, int fp64, cudaStream_t s)
 {
+    // even orders only: the host refuses odd ones (|b(m)| vanishes at m = K/2)
     switch (order) {
     case 4: spread_p<4>(d, fp64, s); break;
-    case 5: spread_p<5>(d, fp64, s); break;
     case 6: spread_p<6>(d, fp64, s); break;
-    case 7: spread_p<7>(d, fp64, s); break;
     default: spread_p<8>(d, fp64, s); break;
     }
 }
@@ -599,9 +598,7 @@ void launch_pme_gather(const Dev& d, int order, double* out, int as_grad, int fp
 {
     switch (order) {
     case 4: gather_p<4>(d, out, as_grad, fp64, s); break;
-    case 5: gather_p<5>(d, out, as_grad, fp64, s); break;
     case 6: gather_p<6>(d, out, as_grad, fp64, s); break;
-    case 7: gather_p<7>(d, out, as_grad, fp64, s); break;
     default: gather_p<8>(d, out, as_grad, fp64, s); break;
     }
 }
