@@ -402,6 +402,43 @@ def test_million_atom_heterogeneous_sampled(M, oracle_mod):
     e.close()
 
 
+def test_benchmark_workload_sampled(M, oracle_mod):
+    """The benchmark workload itself (96,000-atom water, 98.6 A, DSF, r_E
+    10 A, rings at 5.25 / 6 / 7.5 A, 0.3 A skin) in the benchmark's mixed
+    precision: full and F0 gradients of 40 sampled atoms within 1e-5 of the
+    oracle's, and one C' phase of 200 sampled atoms (oracle with per-atom
+    lists)."""
+    import bench
+    from paper_2412_15073_gb300 import systems
+    w = systems.water_box(bench.N_MOL, box=bench.BOX, seed=0)
+    p = dict(bench.JUMP_PARAMS)
+    e = M.Engine(precision=1, seed=6)
+    e.set_system(0, w, **p)
+    o = oracle_mod.Oracle(w, seed=6, replica=0, lazy_lists=True, **p)
+    rng = np.random.default_rng(8)
+    idx = rng.choice(w.n, 40, replace=False)
+    tot = e.gradient(0)
+    rms = np.sqrt((tot * tot).sum(1).mean())
+    for mode in (0, 5):
+        g = tot if mode == 0 else e.gradient(mode)
+        for i in idx:
+            ref = o.gradient_atom(mode, int(i))
+            den = max(np.linalg.norm(tot[i]), 0.01 * rms)
+            assert np.linalg.norm(g[i] - ref) / den <= 1e-5, (mode, i)
+    mt = w.mass / 418.4
+    tau2 = 0.0005
+    e.run_phase(0, tau2, s0=17, half=1, accel_mode=M.GRAD_F0)
+    vg = e.state()[1]
+    good = 0
+    for i in rng.choice(w.n, 200, replace=False):
+        a = -o.gradient_atom(oracle_mod.GRAD_F0, int(i)) / mt[i]
+        vo, _, _ = o.cprime_one(int(i), w.v[i], a, tau2, 17, 1)
+        good += np.abs(vg[i] - vo).max() <= 2e-5 * max(np.abs(vo).max(), 1.0)
+    assert good >= 194, good
+    assert e.observables()["error_flags"] == 0
+    e.close()
+
+
 @pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-5)])
 def test_lj_long_mode_gradients(M, oracle_mod, water648, precision, tol):
     """The LJ long part deterministic: in F0 (mode 1, the paper's GPU
