@@ -2,10 +2,11 @@
 
 Workload (the 97k-atom headline configuration): 32,000 flexible 3-site waters
 (96,000 atoms) in a 98.6 A periodic cube, LJ + DSF Coulomb (alpha 0.2/A),
-r_E = 10 A, r_c = 5 A (switch width 0.5 A), ring boundary 5.5 A, adaptive
-eps0 = 0.1, Langevin 300 K, gamma = 1/ps, mixed precision (FP32 pair math,
-64-bit fixed-point sums, FP64 integration). A step is one 1 fs JUMP step
-(C'J'AOAJ'C'); BAOAB runs the same system at 1 fs for comparison.
+r_E = 10 A, r_c = 5 A (switch width 0.5 A), jump rings with edges at 5.25,
+6 and 7.5 A, adaptive eps0 = 0.1, Langevin 300 K, gamma = 1/ps, mixed
+precision (FP32 pair math, 64-bit fixed-point sums, FP64 integration). A
+step is one 1 fs JUMP step (C'J'AOAJ'C'); BAOAB runs the same system at
+1 fs for comparison.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
