@@ -19,6 +19,11 @@
  *   JUMP invariance ............. pinned (Boltzmann law of a 2-body system)
  *   BAOAB ....................... pinned (exact harmonic variance, Verlet order)
  *   RESPA / RESPA1 drivers ...... pinned by reduction (n = 1 equals BAOAB)
+ *   LJ long modes 1, 2 .......... pinned by reduction (moved part = pair sum)
+ *   Ewald, plain reciprocal sum . pinned (rock-salt Madelung constant)
+ *   smooth PME .................. pinned (plain sum per order, grid refinement,
+ *                                 finite differences of its energy)
+ *   VACF, spectrum .............. pinned (closed forms, numpy correlate)
  */
 #ifndef MD_ORACLE_H
 #define MD_ORACLE_H
