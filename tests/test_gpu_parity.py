@@ -284,6 +284,37 @@ def test_invalid_inputs_are_rejected(M, water648):
             e.set_system(0, water648, ring_r=bad)                        # ring edges not inside (r_c-h, r_E)
 
 
+def test_uncharged_lj_fluid_and_degenerate_calls(M, oracle_mod):
+    """Degenerate cases. An uncharged Lennard-Jones lattice (512 argon-like
+    atoms, 30.4 A): the Coulomb rings are empty, so JUMP is BAOAB with the LJ
+    bounces (J') only, and the FP64 bounces and positions equal the oracle's
+    over 100 steps of 2 fs. Zero steps leave the state alone; an empty system
+    is refused."""
+    from paper_2412_15073_gb300 import systems
+    n, a = 8, 3.8
+    g = np.stack(np.meshgrid(*(np.arange(n),) * 3, indexing="ij"), -1).reshape(-1, 3) * a + 0.5
+    w = systems.point_charges(g, n * a, 0.0, 39.948, seed=3, temperature=120.0, lj_eps=0.238, lj_sigma=3.4)
+    p = dict(PARAMS, temperature=120.0, skin=0.3, skin_outer=0.6)
+    e = M.Engine(precision=0, seed=4, event_log_cap=1 << 20)
+    e.set_system(0, w, **p)
+    o = oracle_mod.Oracle(w, seed=4, replica=0, **p)
+    o.events_enable(1 << 20)
+    x0 = e.state()[0]
+    e.jump(0, 2.0)
+    assert np.array_equal(e.state()[0], x0) and e.observables()["step"] == 0
+    e.jump(100, 2.0)
+    o.jump(100, 2.0)
+    ev_g, ev_o = sorted_events(e.events()), sorted_events(o.events())
+    assert len(ev_o) > 50 and np.array_equal(ev_g, ev_o), (len(ev_g), len(ev_o))
+    assert pos_err(e.state()[0], o.state()[0], w.box) < 1e-6
+    ob = e.observables()
+    assert ob["jump_proposals"] == 0 and ob["bps_accepts"] == len(ev_o) and ob["error_flags"] == 0
+    e.close()
+    empty = systems.point_charges(np.zeros((0, 3)), 30.0, 0.0, 1.0)
+    with pytest.raises(M.MDError):
+        M.Engine(precision=1).set_system(0, empty)
+
+
 def test_velocity_phase_variants_are_identical(M, oracle_mod, water648, monkeypatch):
     """The launch variants the autotuner chooses between (four occupancy
     targets, with or without the rate ordering) compute the same values bit
