@@ -56,3 +56,22 @@ def test_bench_functions_name_only_defined_globals():
                            for ins in __import__("dis").get_instructions(co)):
                         missing.add((name, g))
     assert not missing, missing
+
+
+def test_reference_arm_prints_one_consistent_line(capsys):
+    """bench.py --impl reference (the oracle on the host cores, a bounded
+    sample of the benchmark step): one JSON line whose value, ms_per_step,
+    cpu_baseline and e2e agree"""
+    import argparse
+    import json
+
+    bench.run_reference(argparse.Namespace(steps=1, warmup=0))
+    lines = [l for l in capsys.readouterr().out.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "ns/day" and d["metric"] == bench.METRIC
+    assert d["value"] > 0 and d["higher_is_better"] is True
+    assert abs(bench.ns_per_day(bench.DT_FS, d["ms_per_step"] * 1e-3) / d["value"] - 1) < 1e-9
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1 and "96,000" in d["cpu_baseline"]["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "ns/day", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
