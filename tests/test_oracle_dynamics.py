@@ -387,3 +387,33 @@ def test_bjaoajb_is_baoab_without_jumps_and_keeps_temperature(oracle_mod, water6
     v = c.state()[1]
     T = (water648.mass[:, None] * v * v).sum() / 418.4 / (3 * water648.n * 0.0019872042586)
     assert 240 < T < 360, T
+
+
+def test_lists_cover_the_current_shells_during_dynamics(oracle_mod, water648):
+    """Verlet validity of the rebuild rule (reading 11): after 300 JUMP steps
+    behind a thin 0.2 A skin (the rule fires many times; the outer candidates
+    have a wide skin, so their own rule does not mask it), every non-excluded
+    pair whose current distance lies in a ring's range is in that ring's
+    list, every O-O pair in the LJ range is in the LJ list, and every list
+    entry is still within twice the skin of its shell."""
+    skin = 0.2
+    o = oracle_mod.Oracle(water648, r_cut=9.0, r_split=5.0, h_switch=0.5, r_mid=5.5, dsf_alpha=0.2,
+                          skin=skin, skin_outer=1.0, seed=5)
+    o.jump(300)
+    assert o.errors == 0
+    assert o.counters()[5] >= 5                               # list rebuilds (the outer rule, at 0.4 A, fires less)
+    x = o.state()[0]
+    L = water648.box
+    n = water648.n
+    mol = np.arange(n) // 3
+    is_o = water648.type == 0
+    for i in np.random.default_rng(2).choice(n, 40, replace=False):
+        d = x[i] - x
+        d -= L * np.round(d / L)
+        r = np.sqrt((d * d).sum(1))
+        ok = (np.arange(n) != i) & (mol != mol[i])
+        for kind, lo, hi, extra in ((0, 4.5, 5.5, ok), (1, 5.5, 9.0, ok), (4, 4.5, 9.0, ok & is_o & is_o[i])):
+            have = o.list_of(kind, i)
+            need = np.flatnonzero(extra & (r >= lo) & (r < hi))
+            assert np.isin(need, have).all(), (i, kind)
+            assert ((r[have] >= lo - 2 * skin) & (r[have] < hi + 2 * skin)).all(), (i, kind)
