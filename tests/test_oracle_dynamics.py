@@ -219,6 +219,32 @@ def test_verlet_energy_error_second_order(oracle_mod, water648):
     assert 3.0 < ratio < 5.0, (rms, ratio)
 
 
+@pytest.mark.parametrize("integ,per_outer", [("baoab_respa", 2), ("baoab_respa1", 4)])
+def test_multiple_time_step_energy_error_second_order(oracle_mod, water648, integ, per_outer):
+    """At gamma = 0 BAOAB-RESPA (bonded at delta, nonbonded at 2 delta) and
+    BAOAB-RESPA1 (bonded at delta, short pairs at 2 delta, long pairs at
+    4 delta) are impulse multiple-time-step Verlet schemes (Sec. 2.3): the
+    RMS fluctuation of the total energy at the outer steps scales as dt^2
+    (ratio ~ 4 when every step halves). A kick of the wrong size at any level
+    leaves an error that does not shrink with dt."""
+    rms = []
+    for dt in (0.2, 0.1):
+        o = oracle_mod.Oracle(water648, r_cut=9.0, gamma=0.0, skin=0.3)
+        step = (lambda k: o.baoab_respa(k, dt, 2)) if integ == "baoab_respa" else \
+            (lambda k: o.baoab_respa1(k, dt, 2, 2))
+        outer = dt * per_outer
+        step(int(round(4 / outer)))
+        H = []
+        for _ in range(int(round(16 / outer))):
+            step(1)
+            _, v, _, _ = o.state()
+            ke = 0.5 * (water648.mass[:, None] * v * v).sum() / KCAL_AMU
+            H.append(ke + o.energy().sum())
+        rms.append(np.std(H))
+    ratio = rms[0] / rms[1]
+    assert 3.0 < ratio < 5.0, (rms, ratio)
+
+
 # ------------------------------------------------------------ reductions
 def test_jump_equals_baoab_without_jump_range(oracle_mod, water648):
     """r_c - h >= r_E: chi = 1 on all pairs, the rings are empty, C' is the B
