@@ -259,6 +259,25 @@ def test_jump_equals_baoab_without_jump_range(oracle_mod, water648):
     assert np.array_equal(xa, xb) and np.array_equal(va, vb)
 
 
+@pytest.mark.parametrize("jump,baoab,args", [("jump_respa", "baoab_respa", (15, 1.0, 2)),
+                                             ("jump_respa1", "baoab_respa1", (8, 1.0, 2, 2))])
+def test_jump_mts_equals_baoab_mts_without_jump_range(oracle_mod, water648, jump, baoab, args):
+    """r_c - h >= r_E: the rings are empty, C' is the B kick of the short
+    (here the whole) nonbonded force and the long level is empty under DSF:
+    JUMP-RESPA and JUMP-RESPA1 reproduce BAOAB-RESPA and BAOAB-RESPA1 bit for
+    bit, so their multiple-time-step skeletons are those the energy test
+    above pins."""
+    p = dict(r_cut=9.0, r_split=9.6, h_switch=0.5, skin=0.3, seed=4)
+    a = oracle_mod.Oracle(water648, **p)
+    b = oracle_mod.Oracle(water648, **p)
+    getattr(a, jump)(*args)
+    getattr(b, baoab)(*args)
+    xa, va, _, _ = a.state()
+    xb, vb, _, _ = b.state()
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+    assert a.step == b.step
+
+
 def test_respa_one_inner_step_is_baoab(oracle_mod, water648):
     """BAOAB-RESPA with n = 1 and BAOAB-RESPA1 with m = n = 1 are BAOAB, up to
     the order in which the bonded and nonbonded kicks are added."""
