@@ -129,11 +129,14 @@ def test_jprime_single_bounce_law(oracle_mod):
 
 # ------------------------------------------------------------ invariance
 @pytest.mark.slow
-def test_jump_samples_boltzmann_two_body(oracle_mod):
+@pytest.mark.parametrize("eps_mode,eps0", [(1, 0.1), (0, 2.0)])
+def test_jump_samples_boltzmann_two_body(oracle_mod, eps_mode, eps0):
     """JUMP (C'J'AOAJ'C') on two charged LJ atoms: the pair distance follows
     r^2 exp(-beta U(r)) (Gibbs invariance, Sec. 2.2), where U includes the
     long-range part that only the jumps carry. The same data must reject the
-    law of the short part alone, which shows the jumps matter."""
+    law of the short part alone, which shows the jumps matter. Adaptive eps
+    (small here) and a large constant eps, where the 1 + eps^2 of the jump
+    size matters."""
     oracle_mod.set_threads(1)
     L = 12.0
     beta = beta_of()
@@ -144,12 +147,16 @@ def test_jump_samples_boltzmann_two_body(oracle_mod):
         w = systems.point_charges(np.array([[1, 1, 1], [5, 1, 1]]), L, [0.2, -0.2], 4.0,
                                   lj_eps=0.2, lj_sigma=3.0, seed=chain)
         o = oracle_mod.Oracle(w, r_cut=5.5, r_split=3.5, h_switch=0.5, r_mid=4.2, dsf_alpha=0.2,
-                              gamma=5.0, skin=0.4, eps0=0.1, seed=100 + chain)
-        o.jump(2000)
+                              gamma=5.0, skin=0.4, eps0=eps0, eps_mode=eps_mode, seed=100 + chain)
         rs = []
-        for _ in range(25000):
+        for it in range(25100):
             o.jump(20)
-            x = o.state()[0]
+            x, v, _, _ = o.state()
+            # a wrong jump size heats the pair without bound: fail at once
+            ke_T = 4.0 * (v * v).sum() / KCAL_AMU / (6 * KB)
+            assert o.errors == 0 and ke_T < 5000.0, (chain, it, ke_T)
+            if it < 100:
+                continue                                    # 2000 steps of burn-in
             d = x[0] - x[1]
             d -= L * np.round(d / L)
             rs.append(math.sqrt(d @ d))
