@@ -78,13 +78,16 @@ def test_cprime_first_jump_survival_a0(oracle_mod, eps_mode, rings):
     assert props / n > lam * tau2   # a proper bound proposes more than it accepts
 
 
-def test_cprime_first_jump_survival_with_drift(oracle_mod):
+@pytest.mark.parametrize("a", [(-900.0, 1400.0, 600.0), (2700.0, -1400.0, 1800.0)])
+def test_cprime_first_jump_survival_with_drift(oracle_mod, a):
     """With a != 0, v(s) = v + s a until the first jump, so
-    P(no jump in tau/2) = exp(-int_0^{tau/2} sum_j lambda_ij(v + s a) ds)."""
+    P(no jump in tau/2) = exp(-int_0^{tau/2} sum_j lambda_ij(v + s a) ds).
+    The drift slows the atom down first (v.a < 0) or speeds it up (v.a > 0,
+    where the bound on |v| must hold the s^2 |a|^2 term: no ratio above 1)."""
     o = _ring_system(oracle_mod)
     beta, mt = beta_of(), 16.0 / KCAL_AMU
     v = np.array([2.0, -1.0, 1.0])
-    a = np.array([-900.0, 1400.0, 600.0])
+    a = np.array(a)
     lam0 = _pair_rates(o, v, 1, 0.1, beta, mt)
     tau2 = 1.2 / lam0
     integ, _ = integrate.quad(lambda s: _pair_rates(o, v + s * a, 1, 0.1, beta, mt), 0, tau2)
@@ -98,6 +101,7 @@ def test_cprime_first_jump_survival_with_drift(oracle_mod):
     p_exp = math.exp(-integ)
     se = math.sqrt(p_exp * (1 - p_exp) / n)
     assert abs(none / n - p_exp) < 4.5 * se, (none / n, p_exp)
+    assert o.errors == 0
 
 
 def test_jprime_single_bounce_law(oracle_mod):

@@ -186,6 +186,33 @@ def test_four_ring_bounds_and_lists(oracle_mod, water648):
 
 
 # ---------------------------------------------------------------- forces
+def test_single_molecule_has_no_nonbonded_terms(oracle_mod):
+    """Intramolecular pairs are excluded (reading 16): one water alone in
+    its box has zero LJ and Coulomb energy and zero nonbonded gradient
+    (under DSF), its whole gradient is the bonded one, and the oracle's
+    bonded energy is the closed form 1/2 k (r - r0)^2 + 1/2 k_t (t - t0)^2."""
+    w = systems.water_box(1, box=24.0, seed=3)
+    w.x = w.x + np.random.default_rng(4).normal(scale=0.05, size=w.x.shape)     # strained geometry
+    o = oracle_mod.Oracle(w, r_cut=9.0, r_split=5.0, h_switch=0.5, dsf_alpha=0.2, skin=0.3)
+    e_bond, e_angle, e_lj, e_coul = o.energy()
+    assert e_lj == 0.0 and e_coul == 0.0
+    g_nb, _ = o.gradient(oracle_mod.GRAD_NB_FULL)
+    assert np.abs(g_nb).max() == 0.0
+    g_all, _ = o.gradient(oracle_mod.GRAD_FULL)
+    g_b, _ = o.gradient(oracle_mod.GRAD_BONDED)
+    np.testing.assert_array_equal(g_all, g_b)
+    x = w.x
+    ref_b = sum(0.5 * k * (np.linalg.norm(x[i] - x[j]) - r0) ** 2
+                for (i, j), k, r0 in zip(w.bonds, w.bond_k, w.bond_r0))
+    a, c, b = w.angles[0]
+    u, v = x[a] - x[c], x[b] - x[c]
+    th = math.acos(u @ v / np.linalg.norm(u) / np.linalg.norm(v))
+    ref_a = 0.5 * w.angle_k[0] * (th - w.angle_t0[0]) ** 2
+    assert ref_b > 0.1 and ref_a > 1e-3
+    assert e_bond == pytest.approx(ref_b, rel=1e-12)
+    assert e_angle == pytest.approx(ref_a, rel=1e-12)
+
+
 def test_total_gradient_finite_differences(oracle_mod, water648):
     """Gradient of the full potential (bonds, angles, LJ, DSF) against central
     differences of the energy, on a few atoms of the 648-atom water box."""
