@@ -16,6 +16,20 @@ C_COUL = 332.0637
 
 
 # ---------------------------------------------------------------- Philox
+@pytest.mark.parametrize("ctr,key,out", [
+    ((0, 0, 0, 0), (0, 0), (0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8)),
+    ((0xFFFFFFFF,) * 4, (0xFFFFFFFF,) * 2, (0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD)),
+    ((0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344), (0xA4093822, 0x299F31D0),
+     (0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1)),
+])
+def test_philox_known_answers(oracle_mod, ctr, key, out):
+    """Philox4x32-10 against the known-answer vectors published with the
+    generator (Salmon, Moraes, Dror, Shaw, SC'11: zero, all-ones, and the
+    digits of pi as counter and key): the statistics below cannot tell a
+    wrong round count or constant from the real thing, these can."""
+    assert tuple(int(x) for x in oracle_mod.philox(ctr, key)) == out
+
+
 def test_philox_uniform_and_independent(oracle_mod):
     """32-bit outputs: flat histogram, decorrelated words, sensitive to every
     counter word and both key words (avalanche)."""
