@@ -269,25 +269,29 @@ def test_jump_lists_definition(oracle_mod, water648):
     the skin-widened rings, ordered by (cell of j at the outer rebuild, j) on
     the grid of floor(2 L / (r_E + skin_outer)) cells; checked with numpy."""
     skin = 0.2
-    o = oracle_mod.Oracle(water648, r_cut=9.0, r_split=5.0, h_switch=0.5, r_mid=5.5, skin=skin,
+    w = water648.copy()
+    w.charge = w.charge.copy()
+    w.charge[:30] = 0.0                  # ten uncharged molecules: no ring partners (reading 14)
+    o = oracle_mod.Oracle(w, r_cut=9.0, r_split=5.0, h_switch=0.5, r_mid=5.5, skin=skin,
                           skin_outer=0.3)
-    x = water648.x
-    L = water648.box
+    x = w.x
+    L = w.box
     nc = int(math.floor(2 * L / (9.0 + 0.3)))
     cs = L / nc
     cell = np.minimum((x // cs).astype(int), nc - 1)
     lin = (cell[:, 2] * nc + cell[:, 1]) * nc + cell[:, 0]
     mol = np.arange(water648.n) // 3
     rng = np.random.default_rng(0)
-    for i in rng.choice(water648.n, 25, replace=False):
+    for i in np.concatenate([[0, 1, 2], rng.choice(w.n, 25, replace=False)]):
         d = x[i] - x
         d -= L * np.round(d / L)
         r = np.sqrt((d * d).sum(1))
-        ok = (np.arange(water648.n) != i) & (mol != mol[i])
-        for kind, lo, hi, extra in ((0, 4.5 - skin, 5.5 + skin, True),
-                                    (1, 5.5 - skin, 9.0 + skin, True),
-                                    (4, 4.5 - skin, 9.0 + skin, water648.type == 0)):
-            if kind == 4 and water648.type[i] != 0:
+        ok = (np.arange(w.n) != i) & (mol != mol[i])
+        charged = w.charge * w.charge[i] != 0.0
+        for kind, lo, hi, extra in ((0, 4.5 - skin, 5.5 + skin, charged),
+                                    (1, 5.5 - skin, 9.0 + skin, charged),
+                                    (4, 4.5 - skin, 9.0 + skin, w.type == 0)):
+            if kind == 4 and w.type[i] != 0:
                 extra = np.zeros_like(ok)
             sel = np.flatnonzero(ok & (r >= lo) & (r < hi) & extra)
             sel = sel[np.lexsort((sel, lin[sel]))]
