@@ -157,3 +157,49 @@ def test_odd_pme_orders_are_refused(oracle_mod, water648):
     G(m) would divide by zero: only the even orders 4, 6, 8 are taken"""
     with pytest.raises(ValueError):
         oracle_mod.Oracle(water648, r_cut=9.0, coulomb_mode=1, pme_order=5)
+
+
+EW_EMPTY = dict(r_cut=9.0, r_split=9.6, h_switch=0.5, skin=0.3, seed=4, dsf_alpha=0.35, coulomb_mode=1,
+                pme_order=6, pme_spacing=0.8)
+
+
+def test_jump_mts_equals_baoab_mts_under_ewald_without_jump_range(oracle_mod):
+    """Ewald with r_c - h >= r_E: the rings are empty and the (1 - chi) pairs
+    vanish, so the outer level of both RESPA1 schemes holds the reciprocal
+    part alone: JUMP-RESPA1 reproduces BAOAB-RESPA1 bit for bit. JUMP-RESPA
+    kicks the reciprocal part apart from the short pairs that BAOAB-RESPA
+    kicks together with it: equal up to rounding."""
+    w = systems.water_box(216, box=18.643, seed=0)
+    for jump, baoab, args, tol in (("jump_respa1", "baoab_respa1", (4, 1.0, 2, 2), 0.0),
+                                   ("jump_respa", "baoab_respa", (6, 1.0, 2), 1e-10)):
+        a = oracle_mod.Oracle(w, **EW_EMPTY)
+        b = oracle_mod.Oracle(w, **EW_EMPTY)
+        getattr(a, jump)(*args)
+        getattr(b, baoab)(*args)
+        xa, va, _, _ = a.state()
+        xb, vb, _, _ = b.state()
+        assert np.abs(xa - xb).max() <= tol and np.abs(va - vb).max() <= 10 * tol, jump
+
+
+def test_baoab_respa1_energy_error_second_order_under_ewald(oracle_mod):
+    """At gamma = 0 BAOAB-RESPA1 under Ewald (bonded at delta, short pairs at
+    2 delta, the (1 - chi) pairs and the smooth-PME reciprocal part at
+    4 delta) is an impulse multiple-time-step Verlet scheme: its total-energy
+    fluctuation scales as dt^2. A reciprocal force kicked at the wrong level
+    or with the wrong size leaves an error that does not shrink."""
+    w = systems.water_box(216, box=18.643, seed=0)
+    rms = []
+    for dt in (0.2, 0.1):
+        o = oracle_mod.Oracle(w, r_cut=9.0, r_split=5.0, h_switch=0.5, gamma=0.0, skin=0.3, dsf_alpha=0.35,
+                              coulomb_mode=1, pme_order=6, pme_spacing=0.8)
+        outer = 4 * dt
+        o.baoab_respa1(int(round(4 / outer)), dt, 2, 2)
+        H = []
+        for _ in range(int(round(12 / outer))):
+            o.baoab_respa1(1, dt, 2, 2)
+            _, v, _, _ = o.state()
+            ke = 0.5 * (w.mass[:, None] * v * v).sum() / 418.4
+            H.append(ke + o.energy().sum())
+        rms.append(np.std(H))
+    ratio = rms[0] / rms[1]
+    assert 3.0 < ratio < 5.0, (rms, ratio)
