@@ -75,6 +75,20 @@ def ns_per_day(fs_simulated: float, seconds: float) -> float:
     return fs_simulated * 1e-6 / seconds * 86400.0
 
 
+def pair_roofline(ms_total: float, groups: int, pairs: float, clock_mhz: float) -> dict:
+    """FP32 roofline of the pair kernel of one BAOAB force evaluation: the
+    algorithmic FLOPs (FLOP_PER_PAIR per unique pair within the cutoff) over
+    the mean device time of one evaluation (CUDA events of the library's
+    pair-force class, which also holds the term-parallel bonded kernel)."""
+    per_launch_s = ms_total / max(groups, 1) * 1e-3
+    achieved = FLOP_PER_PAIR * pairs / per_launch_s / 1e12
+    peak = 152 * 128 * 2 * clock_mhz * 1e6 / 1e12
+    return {"bound": "fp32", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "kernel": "k_force (BAOAB full pairs) + k_bonded_terms", "units_per_launch": pairs,
+            "ops_per_unit": FLOP_PER_PAIR, "ms_per_launch": per_launch_s * 1e3,
+            "peak_source": f"FP32: 152 SMs x 128 lanes x 2 x {clock_mhz:.0f} MHz (max clock)"}
+
+
 def peaks():
     try:
         return json.load(open(PEAKS)), "measured"
@@ -725,6 +739,16 @@ def main():
                 "peak_source": f"FP32: 152 SMs x 128 lanes x 2 x {clock/1e6:.0f} MHz (max clock)"}
     roof["share_of_step"] = float(ms[top] / ms.sum())
     roof["class_ms_per_step"] = {c: float(m / prof_steps) for c, m in zip(classes, ms)}
+    # the pair kernel of the BAOAB baseline against the FP32 pipe (profiled run of its own)
+    pair_roof = None
+    try:
+        eb.profile(enable=1, reset=True)
+        eb.baoab(prof_steps)
+        msb, gb, _ = eb.profile(enable=0)
+        k = classes.index("pair_force")
+        pair_roof = pair_roofline(float(msb[k]), int(gb[k]), pairs_full, clock / 1e6)
+    except Exception as ex:  # noqa: BLE001  (a side figure: never lose the main line for it)
+        pair_roof = {"error": str(ex)}
 
     # RESPA1: delta 1 fs (bonded), kappa 2 fs (short pairs, and the jumps of
     # JUMP-RESPA1), Delta = 2, 4, 6 fs (the long pairs of BAOAB-RESPA1; the
@@ -802,6 +826,7 @@ def main():
            "ensemble": ensemble,
            "million": million,
            "roofline": roof | {"peak_kind": how},
+           "pair_roofline": pair_roof,
            "e2e": e2e,
            "gpu_launches": launches,
            "clocks": clk.summary()}

@@ -75,3 +75,13 @@ def test_reference_arm_prints_one_consistent_line(capsys):
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["cpu_baseline"]["cores"] >= 1 and "96,000" in d["cpu_baseline"]["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": "ns/day", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_pair_roofline_arithmetic():
+    """52 FLOPs per pair over the mean time of one evaluation, against
+    152 SMs x 128 lanes x 2 x clock"""
+    r = bench.pair_roofline(ms_total=40.0, groups=100, pairs=20e6, clock_mhz=2000.0)
+    assert r["ms_per_launch"] == 0.4
+    assert abs(r["achieved"] - 52 * 20e6 / 0.4e-3 / 1e12) < 1e-12
+    assert abs(r["peak"] - 152 * 128 * 2 * 2e9 / 1e12) < 1e-9
+    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-15 and r["unit"] == "TFLOP/s"
