@@ -743,8 +743,10 @@ def main():
     pair_roof = None
     try:
         eb.profile(enable=1, reset=True)
-        eb.baoab(prof_steps)
-        msb, gb, _ = eb.profile(enable=0)
+        try:
+            eb.baoab(prof_steps)
+        finally:
+            msb, gb, _ = eb.profile(enable=0)
         k = classes.index("pair_force")
         pair_roof = pair_roofline(float(msb[k]), int(gb[k]), pairs_full, clock / 1e6)
     except Exception as ex:  # noqa: BLE001  (a side figure: never lose the main line for it)
