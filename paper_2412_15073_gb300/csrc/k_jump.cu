@@ -693,7 +693,8 @@ __global__ void k_rate_key(Dev d, const double* a, double tau2)
             lam += float(N[y]) * (P.eps_mode == 1 ? beta * LYv[y] * B + c0 : LYv[y] * (beta * B + c0));
         mu = lam * s;
     }
-    const int b = min(RATE_BUCKETS - 1, int(mu * 0.25f));
+    // a non-finite velocity (flagged by the A O A update) gives mu = NaN: bucket 0
+    const int b = mu > 0.f ? min(RATE_BUCKETS - 1, int(mu * 0.25f)) : 0;
     const int key = r * RATE_BUCKETS + (RATE_BUCKETS - 1 - b);
     d.vkey[i] = key;
     // one atomic per distinct key in the warp

@@ -69,6 +69,7 @@ __device__ __forceinline__ void grid_coord(const RepParams& P, double x, int& k0
     k0 = int(fl);
     f = u - fl;
     if (k0 >= P.pme_K) k0 -= P.pme_K;     // x rounded up to L: the point 0, same weights
+    if (!(k0 >= 0 && k0 < P.pme_K)) k0 = 0;   // non-finite x (flagged by the A O A update): in range
 }
 
 __device__ __forceinline__ int wrap_k(int g, int K) { return g < 0 ? g + K : (g >= K ? g - K : g); }

@@ -315,6 +315,28 @@ def test_uncharged_lj_fluid_and_degenerate_calls(M, oracle_mod):
         M.Engine(precision=1).set_system(0, empty)
 
 
+def test_failures_are_reported_as_status(M, water648):
+    """Failure detection without a GPU fault, the failure made on the host:
+    an event log smaller than the run's accepted jumps makes md_get_events
+    return MD_EOVERFLOW (the kernels stop writing at its end), and a
+    non-finite velocity handed to md_set_state is caught by the A O A
+    update's check, so the step call returns MD_ENONFINITE. Every device
+    loop is bounded (proposal and sampler caps), so neither case hangs."""
+    e = M.Engine(precision=1, seed=2, event_log_cap=16)
+    e.set_system(0, water648, **PARAMS)
+    e.jump(5)
+    with pytest.raises(M.MDError) as ex:
+        e.events()
+    assert ex.value.code == -3
+    x, v, img, xb = e.state()
+    v[7] = np.nan
+    e.set_state(0, x, v, img, xb)
+    with pytest.raises(M.MDError) as ex:
+        e.jump(1)
+    assert ex.value.code == -6
+    e.close()
+
+
 def test_velocity_phase_variants_are_identical(M, oracle_mod, water648, monkeypatch):
     """The launch variants the autotuner chooses between (four occupancy
     targets, with or without the rate ordering) compute the same values bit
