@@ -15,6 +15,12 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB = os.path.join(HERE, "liboracle.so")
+# a library built elsewhere from an edited oracle.c (the planted-mistake
+# checks of tests/test_oracle_mutations.py); never set in normal use
+EXTERNAL_LIB = os.environ.get("ORACLE_MUTANT_LIB")
+if EXTERNAL_LIB:
+    LIB = EXTERNAL_LIB
+CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off"]
 
 GRAD_FULL, GRAD_BONDED, GRAD_NB_FULL, GRAD_NB_SHORT, GRAD_NB_LONG, GRAD_F0 = range(6)
 KIND_RING_M, KIND_RING_L, KIND_LJ = 0, 1, 4     # ring y is kind y (0..3); LJ partners kind 4
@@ -23,14 +29,15 @@ E_BOUND, E_LIMIT, E_NONFIN = 1, 2, 4
 
 def build(force: bool = False) -> str:
     """Compile liboracle.so with gcc (FP contraction off, OpenMP on)."""
+    if EXTERNAL_LIB:
+        return LIB
     src = os.path.join(HERE, "oracle.c")
     if (not force and os.path.exists(LIB)
             and os.path.getmtime(LIB) >= max(os.path.getmtime(src),
                                              os.path.getmtime(os.path.join(HERE, "oracle.h")))):
         return LIB
     tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-           "-o", tmp, src, "-lm"]
+    cmd = ["gcc", *CFLAGS, "-o", tmp, src, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB)
     return LIB
