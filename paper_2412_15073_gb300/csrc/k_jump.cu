@@ -201,7 +201,9 @@ __device__ void cprime(const Dev& d, const RepParams& P, int i, int il, double v
         tl.cprop++;
         const int Y = ring_pick<T>(w, unif<T>(u.y) * Lam, P.nr);
         const uint32_t* row = d.list[L_R0 + Y] + (size_t)i * d.lcap[L_R0 + Y];
-        const int J = int(row[__umulhi(u.z, uint32_t(ring_sel(N, Y)))]);
+        // an empty ring only from an infinite bound (flagged as non-finite): the atom itself, outside every ring
+        const uint32_t NY = uint32_t(ring_sel(N, Y));
+        const int J = NY ? int(row[__umulhi(u.z, NY)]) : i;
         T dx, dy, dz;
         JD<T>::get(d, P, i, pi, J, dx, dy, dz);
         const T r = d_sqrt(dx * dx + dy * dy + dz * dz);
@@ -433,14 +435,17 @@ __device__ __forceinline__ void cprime_f(const Dev& d, const JC& c, const RepPar
         for (int y = 0; y < MAX_RINGS; ++y) {
             const float wy = float(N[y]) * lamy(y, B);
             cum += wy;
-            if (y < c.nr && wy > 0.f) last = y;
+            if (y < c.nr && N[y] > 0) last = y;     // for finite bounds: exactly the rings with weight
             if (Y < 0 && y < c.nr && target < cum) Y = y;
         }
         return Y < 0 ? last : Y;
     };
+    // list entry of a proposal; an empty ring (reachable only from a non-finite
+    // state, which the A O A update flags) gives the atom itself: outside every ring
     auto entry = [&](int Y, uint32_t uz) -> uint32_t {
         const uint32_t* row = d.list[L_R0 + Y] + (size_t)i * d.lcap[L_R0 + Y];
-        return __ldg(row + __umulhi(uz, uint32_t(ring_sel(N, Y))));
+        const uint32_t NY = uint32_t(ring_sel(N, Y));
+        return NY ? __ldg(row + __umulhi(uz, NY)) : uint32_t(i);
     };
     uint32_t k = 0;
     U4 u = philox(uint32_t(il), s0, ctag, 0, c.key0, c.key1);
