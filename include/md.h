@@ -155,7 +155,10 @@ int md_set_system(md_ctx* ctx, int replica, const md_system* sys);
  * image counts. x_build / x_outer (may be NULL = x) are the positions at which
  * the lists and the outer candidate grid were last built; passing the values
  * from md_get_state makes a resumed run repeat an uninterrupted one bit for
- * bit. */
+ * bit. The values are taken as given: a non-finite position or velocity is
+ * reported by the next step call as MD_ENONFINITE (the device check of the
+ * A O A update), without a fault. Errors: MD_EINVAL (replica, NULL x or v),
+ * MD_ENOSYSTEM, MD_ECUDA. */
 int md_set_state(md_ctx* ctx, int replica, const double* x, const double* v, const int* img,
                  const double* x_build, const double* x_outer, int64_t step);
 
