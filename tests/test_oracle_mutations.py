@@ -74,6 +74,15 @@ MUTANTS = [
      "        if (ew) { accel(s, 6, s->al); kick(s, s->al, 0.5 * D); }",
      "        if (ew) { kick(s, s->al, 0.5 * D); }",
      "tests/test_oracle_ewald.py::test_jump_mts_equals_baoab_mts_under_ewald_without_jump_range"),
+    ("BJAOAJB jumps with the drift of F0",
+     "        cphase(s, zero, 0.5 * tau, s0, 0);", "        cphase(s, s->a0, 0.5 * tau, s0, 0);",
+     "tests/test_oracle_dynamics.py::test_bjaoajb_is_baoab_without_jumps_and_keeps_temperature"),
+    ("BAOAB velocity recorded before the closing kick",
+     "        kick(s, s->a0, 0.5 * tau);\n        s->step++;\n        vrec(s);\n    }\n    check_finite(s);\n"
+     "    return (int)s->err;\n}\n\n/* JUMP: C'",
+     "        vrec(s);\n        kick(s, s->a0, 0.5 * tau);\n        s->step++;\n    }\n    check_finite(s);\n"
+     "    return (int)s->err;\n}\n\n/* JUMP: C'",
+     "tests/test_oracle_vacf.py::test_record_places_follow_the_integrator_identities"),
     ("VACF normalised by T instead of T - k",
      "acc /= (double)(T - k);", "acc /= (double)(T);",
      "tests/test_oracle_vacf.py::test_vacf_of_a_cosine_matches_its_closed_form"),
