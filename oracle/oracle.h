@@ -18,7 +18,11 @@
  *   thinning (C', J') ........... pinned (survival laws, BPS bounce law)
  *   JUMP invariance ............. pinned (Boltzmann law of a 2-body system)
  *   BAOAB ....................... pinned (exact harmonic variance, Verlet order)
- *   RESPA / RESPA1 drivers ...... pinned by reduction (n = 1 equals BAOAB)
+ *   RESPA / RESPA1 drivers ...... pinned by reduction (n = 1 equals BAOAB) and
+ *                                 by their energy error at gamma 0 (second order)
+ *   JUMP-RESPA, JUMP-RESPA1 ..... pinned (Boltzmann laws of the three bond
+ *                                 lengths of a harmonic chain whose bonded pair
+ *                                 also jumps; with an LJ slow level as well)
  *   LJ long modes 1, 2 .......... pinned by reduction (moved part = pair sum)
  *   Ewald, plain reciprocal sum . pinned (rock-salt Madelung constant)
  *   smooth PME .................. pinned (plain sum per order, grid refinement,

@@ -184,6 +184,91 @@ def test_jump_samples_boltzmann_two_body(oracle_mod, eps_mode, eps0):
     assert np.abs(z_short).max() > 15.0
 
 
+def _harmonic_chain(seed):
+    """Four atoms bonded in a chain 0-1-2-3 (no angles, no exclusions).
+    Atoms 0 and 1 carry charges +-0.3 and LJ (eps 0.8, sigma 3.0), so the pair
+    (0, 1) is bonded and also interacts through LJ + DSF; atoms 2 and 3 have no
+    nonbonded terms. The Gibbs density then factorises over the three bond
+    vectors: bond 0-1 has the length law r^2 exp(-beta (k/2 (r - 4.2)^2 + U(r))),
+    bonds 1-2 and 2-3 that of a free harmonic spring, r^2 exp(-beta k/2 (r - 3)^2)."""
+    x = np.array([[2.0, 7.0, 7.0], [6.2, 7.0, 7.0], [9.2, 7.0, 7.0], [12.2, 7.0, 7.0]])
+    w = systems.point_charges(x, 14.0, [0.3, -0.3, 0.0, 0.0], 4.0, seed=seed)
+    w.type = np.array([0, 0, 1, 1], dtype=np.int32)
+    w.lj_eps = np.array([[0.8, 0.0], [0.0, 0.0]])
+    w.lj_sigma = np.array([[3.0, 1.0], [1.0, 1.0]])
+    w.bonds = np.array([[0, 1], [1, 2], [2, 3]], dtype=np.int32)
+    w.bond_k = np.array([3.0, 3.0, 3.0])
+    w.bond_r0 = np.array([4.2, 3.0, 3.0])
+    return w
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("integ,lj_long_mode", [("jump", 0), ("jump_respa", 0), ("jump_respa1", 0),
+                                                ("jump_respa1", 2)])
+def test_multiple_time_step_jumps_sample_boltzmann_harmonic_chain(oracle_mod, integ, lj_long_mode):
+    """Gibbs invariance (Sec. 2.2) of the JUMP family with its multiple time
+    steps (Sec. 2.3) on a harmonic chain: bonds in F0 at the inner step delta,
+    the short pair part and the pair jumps at Delta = 2 delta (JUMP-RESPA) or
+    at kappa = 2 delta with an outer level at 2 kappa (JUMP-RESPA1; with
+    lj_long_mode 2 that level kicks the (1 - chi) LJ part). The three bond
+    lengths must follow their exact laws (the long-range pair part of bond
+    0-1 is carried by the jumps alone); the law of the short pair part alone
+    must be rejected. Bin z-scores use one variance inflation factor for the
+    correlation of the samples, pooled over the bins of a bond."""
+    oracle_mod.set_threads(1)
+    beta = beta_of()
+    L = 14.0
+    p = dict(r_cut=5.5, r_split=3.6, h_switch=0.5, r_mid=4.4, dsf_alpha=0.2, gamma=5.0, skin=0.4,
+             eps0=0.1, eps_mode=1, lj_long_mode=lj_long_mode)
+    run = {"jump": lambda o: o.jump(20), "jump_respa": lambda o: o.jump_respa(10, 1.0, 2),
+           "jump_respa1": lambda o: o.jump_respa1(5, 1.0, 2, 2)}[integ]
+    edges = [np.linspace(2.8, 6.0, 17), np.linspace(1.6, 4.4, 15), np.linspace(1.6, 4.4, 15)]
+    bonds = ((0, 1), (1, 2), (2, 3))
+    hists = [[], [], []]
+    o = None
+    for chain in range(16):
+        o = oracle_mod.Oracle(_harmonic_chain(chain), seed=200 + chain, **p)
+        rs = []
+        for it in range(6500):
+            run(o)                                          # 20 fs
+            assert o.errors == 0, (chain, it)
+            if it < 100:
+                continue                                    # 2 ps of burn-in
+            x = o.state()[0]
+            row = []
+            for a, b in bonds:
+                d = x[a] - x[b]
+                d -= L * np.round(d / L)
+                row.append(math.sqrt(d @ d))
+            rs.append(row)
+        rs = np.array(rs)
+        for k in range(3):
+            h, _ = np.histogram(rs[:, k], bins=edges[k])
+            hists[k].append(h / len(rs))
+    oracle_mod.set_threads(0)
+
+    def law(u, e):
+        pr = lambda r: r * r * math.exp(-beta * u(r))
+        Z = integrate.quad(pr, 0.5, 6.9, limit=200)[0]
+        return np.array([integrate.quad(pr, a, b)[0] / Z for a, b in zip(e[:-1], e[1:])])
+
+    def zscores(h, pb):
+        h = np.asarray(h)
+        use = pb > 0.01
+        tau = np.mean(h[:, use].var(0, ddof=1) / (pb[use] * (1 - pb[use])))
+        return np.where(use, (h.mean(0) - pb) / np.sqrt(tau * pb * (1 - pb) / len(h)), 0.0)
+
+    full = lambda r: 1.5 * (r - 4.2) ** 2 + o.pair_u(0, 0, -0.09, r, 0)
+    short = lambda r: 1.5 * (r - 4.2) ** 2 + o.pair_u(0, 0, -0.09, r, 1)
+    spring = lambda r: 1.5 * (r - 3.0) ** 2
+    z01 = zscores(hists[0], law(full, edges[0]))
+    assert np.abs(z01).max() < 5.0, z01
+    for k in (1, 2):
+        zk = zscores(hists[k], law(spring, edges[k]))
+        assert np.abs(zk).max() < 5.0, (k, zk)
+    assert np.abs(zscores(hists[0], law(short, edges[0]))).max() > 10.0
+
+
 # ------------------------------------------------------------ BAOAB
 def test_baoab_exact_harmonic_configurations(oracle_mod):
     """BAOAB samples the configurational law of a harmonic oscillator exactly

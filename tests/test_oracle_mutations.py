@@ -12,6 +12,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "oracle.c")
+CHAIN = "tests/test_oracle_dynamics.py::test_multiple_time_step_jumps_sample_boltzmann_harmonic_chain"
 
 # (name, text in oracle.c, replacement, pin to run)
 MUTANTS = [
@@ -74,6 +75,27 @@ MUTANTS = [
      "        if (ew) { accel(s, 6, s->al); kick(s, s->al, 0.5 * D); }",
      "        if (ew) { kick(s, s->al, 0.5 * D); }",
      "tests/test_oracle_ewald.py::test_jump_mts_equals_baoab_mts_under_ewald_without_jump_range"),
+    ("JUMP-RESPA jumps over the inner half step",
+     "cphase(s, s->as, 0.5 * D, s0", "cphase(s, s->as, 0.5 * dt, s0",
+     CHAIN + "[jump_respa-0]"),
+    ("JUMP-RESPA C' drift that still holds the bonded force",
+     "accel(s, 3, s->as);\n        jphase(s, 0.5 * D, s0, 1);",
+     "accel(s, 5, s->as);\n        jphase(s, 0.5 * D, s0, 1);",
+     CHAIN + "[jump_respa-0]"),
+    ("JUMP-RESPA LJ bounces over the inner half step",
+     "jphase(s, 0.5 * D, s0", "jphase(s, 0.5 * dt, s0",
+     CHAIN + "[jump_respa-0]"),
+    ("JUMP-RESPA1 jumps over the outer half step",
+     "cphase(s, s->as, 0.5 * kap, s0", "cphase(s, s->as, 0.5 * D, s0",
+     CHAIN + "[jump_respa1-0]"),
+    ("JUMP-RESPA1 C' drift that still holds the bonded force",
+     "accel(s, 3, s->as);\n            jphase(s, 0.5 * kap, s0, 1);",
+     "accel(s, 5, s->as);\n            jphase(s, 0.5 * kap, s0, 1);",
+     CHAIN + "[jump_respa1-0]"),
+    ("JUMP-RESPA1 opening slow kick over the mid half step",
+     "        if (ew) kick(s, s->al, 0.5 * D);\n        for (int j = 0; j < n_outer; ++j) {",
+     "        if (ew) kick(s, s->al, 0.5 * kap);\n        for (int j = 0; j < n_outer; ++j) {",
+     CHAIN + "[jump_respa1-2]"),
     ("BJAOAJB jumps with the drift of F0",
      "        cphase(s, zero, 0.5 * tau, s0, 0);", "        cphase(s, s->a0, 0.5 * tau, s0, 0);",
      "tests/test_oracle_dynamics.py::test_bjaoajb_is_baoab_without_jumps_and_keeps_temperature"),
