@@ -89,6 +89,8 @@ def lib():
         L.or_rebuild.argtypes = [vp]
         L.or_cprime_one.argtypes = [vp, i, vp, vp, d, u32, i, vp, vp, vp]
         L.or_jprime_one.argtypes = [vp, i, vp, d, u32, i, vp, vp, vp]
+        L.or_sample_atom_work.restype = i
+        L.or_sample_atom_work.argtypes = [vp, i, vp, i, i, i, d, u32, i]
         for name in ("or_step_baoab", "or_step_jump", "or_step_bjaoajb"):
             getattr(L, name).restype = i
             getattr(L, name).argtypes = [vp, i64, d]
@@ -264,6 +266,12 @@ class Oracle:
         self.L.or_jprime_one(self.h, int(i), _p(v), float(tau2), int(s0), int(half),
                              _p(out), C.byref(np_), C.byref(na))
         return out, np_.value, na.value
+
+    def sample_atom_work(self, atoms, mode, n_grad, n_phase, tau2, s0, nthreads):
+        """timing workload of the CPU baseline (see or_sample_atom_work); returns the threads used"""
+        a = np.ascontiguousarray(atoms, dtype=np.int32)
+        return self.L.or_sample_atom_work(self.h, len(a), _p(a), int(mode), int(n_grad), int(n_phase),
+                                          float(tau2), int(s0), int(nthreads))
 
     # integrators ---------------------------------------------------------
     def baoab(self, nsteps, dt_fs=1.0):

@@ -1299,6 +1299,35 @@ void or_jprime_one(or_sys* s, int i, const double* v_in, double tau2,
     if (nacc) *nacc = na;
 }
 
+int or_sample_atom_work(or_sys* s, int n, const int* atoms, int mode, int n_grad, int n_phase,
+                        double tau2, uint32_t s0, int nthreads)
+{
+    if (s->lazy) return -1;
+    int used = 1;
+    int weight = mode == 3 ? W_SHORT : W_FULL;
+#ifdef _OPENMP
+    int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+#endif
+    for (int k = 0; k < n; ++k) {
+        int i = atoms[k];
+        double g[3] = { 0.0, 0.0, 0.0 }, v[3], a[3];
+        for (int r = 0; r < n_grad; ++r) nonbonded_atom(s, i, weight, g, NULL, NULL);
+        for (int c = 0; c < 3; ++c) { v[c] = s->v[3 * i + c]; a[c] = -g[c] / s->mt[i]; }
+        int64_t np = 0, na = 0, nat = 0;
+        uint32_t err = 0;
+        for (int ph = 0; ph < n_phase; ++ph) {
+            cprime_atom(s, i, v, a, tau2, s0, ph & 1, &np, &na, &nat, &err);
+            if (!s->p.lj_long_mode) jprime_atom(s, i, v, tau2, s0, ph & 1, &np, &na, &err);
+        }
+#ifdef _OPENMP
+        if (k == 0) used = omp_get_num_threads();
+#endif
+    }
+    (void)nthreads;
+    return used;
+}
+
 static void check_finite(or_sys* s)
 {
     for (int i = 0; i < 3 * s->n; ++i)

@@ -131,6 +131,16 @@ void or_cprime_one(or_sys* s, int i, const double* v_in, const double* a_in, dou
 void or_jprime_one(or_sys* s, int i, const double* v_in, double tau2,
                    uint32_t s0, int half, double* v_out, int64_t* nprop, int64_t* nacc);
 
+/* timing workload of the CPU baseline: the per-atom work of one step for a
+ * sample of atoms. For each listed atom: n_grad brute-force evaluations of its
+ * nonbonded gradient of weight mode (2 full, 3 short), then n_phase C' phases
+ * over tau2 (drift by the last gradient over m~), each followed by a J' phase
+ * when the LJ long part jumps. Velocities and counters are left untouched.
+ * The atoms are spread over nthreads OpenMP threads (<= 0: all available);
+ * returns the number of threads that ran. Needs lists of all atoms (not lazy). */
+int or_sample_atom_work(or_sys* s, int n, const int* atoms, int mode, int n_grad, int n_phase,
+                        double tau2, uint32_t s0, int nthreads);
+
 /* integrators (dt in fs) */
 int or_step_baoab(or_sys* s, int64_t nsteps, double dt_fs);
 int or_step_baoab_respa(or_sys* s, int64_t nouter, double dt_inner_fs, int n_inner);
