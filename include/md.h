@@ -42,7 +42,8 @@ extern "C" {
 #define MD_OK           0
 #define MD_EINVAL      -1   /* an argument is out of range or inconsistent */
 #define MD_ECUDA       -2   /* a CUDA runtime call failed */
-#define MD_EOVERFLOW   -3   /* fixed-point accumulator or neighbour-list capacity exceeded */
+#define MD_EOVERFLOW   -3   /* a pair term outside the fixed-point range (|component| >= 2^20 kcal/mol/A,
+                             * or not finite), or a neighbour-list capacity exceeded */
 #define MD_EBOUND      -4   /* thinning ratio p > 1: a rate bound was violated */
 #define MD_ELIMIT      -5   /* sampler attempt cap or per-phase proposal cap reached */
 #define MD_ENONFINITE  -6   /* NaN or Inf in positions or velocities */
@@ -73,10 +74,13 @@ typedef struct {
     int max_replicas;      /* replicas advanced together by each md_step_* call (>= 1) */
     int64_t event_log_cap; /* capacity of the accepted-jump log (0 = off) */
     int threads_per_atom;  /* pair kernel: 0 = autotune at the first step, else 1, 2, 4 or 8 */
-    int no_graphs;         /* 0: md_step_* calls of 32 or more steps replay CUDA graphs of 16-step
-                            * (or one-cycle) chunks, captured once per time step and system layout
-                            * on a private stream ordered after cuda_stream; nonzero: plain launches.
-                            * Results are identical either way. */
+    int no_graphs;         /* 0: md_step_* calls replay CUDA graphs of chunks of about four innermost
+                            * steps (four steps, two RESPA cycles of two, or one longer cycle),
+                            * captured on a private stream ordered after cuda_stream the first time a
+                            * call of that integrator, time step and system layout has more than one
+                            * chunk's worth of steps; later calls of at least one chunk replay the
+                            * graph from their first step on. Nonzero: plain launches. Results are
+                            * identical either way. */
 } md_config;
 
 /* One periodic system (cubic box). All pointers are host pointers, copied. */
@@ -227,17 +231,22 @@ int md_get_list(md_ctx* ctx, int replica, int kind, int atom, int* host_out, int
  * empties the log. */
 int64_t md_get_events(md_ctx* ctx, int replica, int64_t* host_out6, int64_t cap, int clear);
 
-/* Kernel launch accounting of this context. Classes: 0 pair force, 1 bonded
- * force, 2 velocity phases (C' and J' jumps), 3 kicks and A-O-A updates,
- * 4 list rebuild chain, 5 bookkeeping (step counters, energies), 6 Ewald
- * reciprocal part (PME kernels; the cuFFT transforms are not counted).
- * launches_out[7] (may be NULL) receives the cumulative number of kernels
- * launched per class since md_init. enable = 1 starts timing every launch
- * group with CUDA events on the context's stream, 0 stops it, -1 leaves it
- * as it is; ms_out[7] (may be NULL) receives the accumulated device time per
- * class while timing was on (summed at the end of each md_step_* call) and
- * groups_out[7] (may be NULL) the number of timed launch groups. reset != 0
- * clears the times. */
+/* Kernel launch accounting of this context. Classes (MD_PROFILE_CLASSES):
+ * 0 pair force, 1 bonded force, 2 velocity phases (the C' and J' jump
+ * kernels), 3 kicks and A-O-A updates, 4 list rebuild: cell grid, outer
+ * candidates and flag reset, 5 bookkeeping (step counters, energies), 6 Ewald
+ * reciprocal part (PME kernels; the cuFFT transforms are not counted),
+ * 7 list rebuild: the inner list filter, 8 rate ordering of the atoms before
+ * a mixed-mode C' phase. launches_out[MD_PROFILE_CLASSES] (may be NULL)
+ * receives the cumulative number of kernels launched per class since md_init
+ * (kernels replayed inside CUDA graphs included). enable = 1 starts timing
+ * every launch group with CUDA events on the context's stream (graphs are
+ * not used while timing is on), 0 stops it, -1 leaves it as it is;
+ * ms_out[MD_PROFILE_CLASSES] (may be NULL) receives the accumulated device
+ * time per class while timing was on (summed at the end of each md_step_*
+ * call) and groups_out[MD_PROFILE_CLASSES] (may be NULL) the number of timed
+ * launch groups. reset != 0 clears the times. */
+#define MD_PROFILE_CLASSES 9
 int md_profile(md_ctx* ctx, int enable, int reset, double* ms_out, int64_t* groups_out,
                int64_t* launches_out);
 
@@ -265,7 +274,11 @@ int md_profile(md_ctx* ctx, int enable, int reset, double* ms_out, int64_t* grou
  * [1, MD_NOALLOC_MAX_ATOMS], more than MD_NOALLOC_MAX_CELLS cells of edge
  * >= r_cut, bad parameters) or MD_ECUDA; the message is md_last_error(NULL).
  *
- * Scratch: one static device array (about 1.4 MB, every GPU that loads the
+ * The atoms of each cell are put in increasing index order before the pair
+ * sums, so every call sums the pairs of an atom in the same order: two calls
+ * on the same input return the same bits.
+ *
+ * Scratch: one static device array (about 2 MB, every GPU that loads the
  * library holds it until the process exits) shared by all calls. It keeps the
  * last call's contents; each call clears what must start at zero. Calls that
  * overlap on the GPU (different streams, or different host threads on the

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(HERE, "libmdjump.so")
 MD_FP64, MD_MIXED = 0, 1
 GRAD_FULL, GRAD_BONDED, GRAD_NB_FULL, GRAD_NB_SHORT, GRAD_NB_LONG, GRAD_F0, GRAD_RECIP = range(7)
 COULOMB_DSF, COULOMB_EWALD = 0, 1
-N_PROFILE_CLASSES = 7
+N_PROFILE_CLASSES = 9
 FLAG_BOUND, FLAG_LIMIT, FLAG_NONFINITE, FLAG_OVERFLOW = 1, 2, 4, 8
 ERRORS = {-1: "MD_EINVAL", -2: "MD_ECUDA", -3: "MD_EOVERFLOW", -4: "MD_EBOUND",
           -5: "MD_ELIMIT", -6: "MD_ENONFINITE", -7: "MD_ENOSYSTEM", -8: "MD_ENOMEM"}
@@ -270,8 +270,8 @@ class Engine:
 
     def profile(self, enable=-1, reset=False):
         """(ms per class, timed groups per class, kernels launched per class);
-        classes: pair force, bonded, velocity phases, kicks/AOA, rebuild chain, bookkeeping,
-        Ewald reciprocal (PME)."""
+        classes: pair force, bonded, velocity phases, kicks/AOA, list cells and outer candidates,
+        bookkeeping, Ewald reciprocal (PME), inner list filter, rate ordering."""
         ms = np.zeros(N_PROFILE_CLASSES)
         groups = np.zeros(N_PROFILE_CLASSES, dtype=np.int64)
         launches = np.zeros(N_PROFILE_CLASSES, dtype=np.int64)

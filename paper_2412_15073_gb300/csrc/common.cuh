@@ -107,6 +107,8 @@ constexpr int PME_BRICK = 8;
 // bits of the per-replica overflow word: list kind k sets bit k; these two
 // are the outer candidate list and a cell above the in-block sort capacity
 constexpr uint32_t OVF_OUTER = 1u << 16, OVF_CELL = 1u << 17;
+// a pair term outside the range of the 64-bit fixed-point sums (or not finite)
+constexpr uint32_t OVF_FIX = 1u << 18;
 constexpr uint16_t SHELL_AMB = 0x8000;
 
 // ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) ---------------------
@@ -269,6 +271,11 @@ __device__ __forceinline__ bool gtilde_attempt(T eta, const U4& u, T& y)
 // ---- fixed point (2^32 units of kcal/mol/A) -----------------------------------
 constexpr double FIX_SCALE = 4294967296.0;
 constexpr double FIX_INV = 1.0 / 4294967296.0;
+// largest |component| of one pair term that the sums accept: 2^20 kcal/mol/A
+// is 2^52 fixed-point units, so 2^11 terms per atom stay inside int64 (list
+// rows are far shorter); a term at or above it, or a non-finite one, is
+// flagged as an overflow (real forces stay below ~10^4 kcal/mol/A)
+constexpr float FIX_TERM_MAX = 1048576.0f;
 
 __device__ __forceinline__ long long to_fix(float f)
 {

@@ -10,8 +10,10 @@
 namespace mdj {
 
 // launch classes of the accounting (md_profile): 0 pair force, 1 bonded, 2 velocity
-// phases, 3 kicks and A-O-A, 4 list rebuild, 5 bookkeeping, 6 Ewald reciprocal (PME)
-constexpr int NPROF = 7;
+// phases (C', J' kernels), 3 kicks and A-O-A, 4 cell grid and outer candidates of the
+// list rebuild, 5 bookkeeping, 6 Ewald reciprocal (PME), 7 inner list filter,
+// 8 rate ordering of the velocity phases
+constexpr int NPROF = 9;
 
 // Device pointers of one context, passed by value to every kernel. All atom
 // arrays are concatenated over replicas (replica r owns [atom_off, atom_off+n)).
@@ -82,22 +84,56 @@ struct Dev {
     long long* ev;
     unsigned long long* ev_n;
     long long ev_cap;
+    int* qctr;                      // work counter of the queue-fed velocity-phase kernel
+    long long* facc;                // [N][3] fixed-point pair sums of the half-list force kernels (kept at zero)
+    int lj_long_mask;               // bit 0: some replica has lj_long_mode 1, bit 1: lj_long_mode 2
+    const int* ib_start;            // blocks of whole bonded groups for the fused inner steps ([n_ib + 1])
+    const int *ib_bond_off, *ib_bond;   // per block: its bonds (global term indices)
+    const int *ib_ang_off, *ib_ang;     // per block: its angles
+    const int* item_slot;           // per bonded item: slot of its term in its block's list
+    int n_ib;                       // 0: the bonded groups do not allow the fused inner steps
+    int lj_symmetric;               // every replica's LJ tables are symmetric (eps_ab = eps_ba, sigma_ab = sigma_ba)
 };
+
+// can gradient mode `mode` run as half-list kernels? (full, short and long
+// pair weights; not the short weight of replicas whose short force also runs
+// over the LJ list: lj_long_mode 1 in modes 3 and 5, lj_long_mode 2 in mode 5)
+inline bool force_half_ok(const Dev& d, int mode)
+{
+    if (!d.lj_symmetric) return false;
+    if (mode == 0 || mode == 2 || mode == 4) return true;
+    if (mode == 3) return !(d.lj_long_mask & 1);
+    if (mode == 5) return d.lj_long_mask == 0;
+    return false;
+}
 
 // ---- lists (k_lists.cu) ---------------------------------------------------------
 void launch_check(const Dev& d, int force_inner, int force_outer, cudaStream_t s);
 void launch_rebuild(const Dev& d, int kinds, int fp64, int keep_refs, int exact_outer,
                     int max_cells_per_rep, cudaStream_t s);
+// the same chain in three parts: cells and outer candidates (5 kernels), the
+// inner list filter (1 kernel, none when kinds is 0), the flag reset (1 kernel)
+void launch_rebuild_cells(const Dev& d, int keep_refs, int exact_outer, cudaStream_t s);
+void launch_rebuild_inner(const Dev& d, int kinds, int exact, cudaStream_t s);
+void launch_rebuild_done(const Dev& d, cudaStream_t s);
 void launch_late_lists(const Dev& d, int kinds, cudaStream_t s);
 
 // ---- forces and integrators (k_force.cu) -----------------------------------------
 // mode: 0 full, 1 bonded, 2 nb full, 3 nb short, 4 nb long, 5 F0 (bonded + short),
 // 7 the (1 - chi) LJ part alone (replicas with lj_long_mode 2, zero elsewhere)
+// tpa: threads per atom (1, 2, 4, 8), | FORCE_HALF for the half-list kernels
+// (mixed mode; the same values bit for bit, see k_force_half).
 // returns the number of kernels launched
+constexpr int FORCE_HALF = 16;
 int launch_force(const Dev& d, int mode, double* out, int as_grad, int fp64, int tpa, cudaStream_t s);
 void launch_kick(const Dev& d, const double* a, double h, cudaStream_t s);
 void launch_kick2(const Dev& d, const double* a, double h, const double* b, double hb, cudaStream_t s);
 void launch_aoa(const Dev& d, double tau, uint32_t s_off, int do_check, int fp64, cudaStream_t s);
+// nsteps inner steps B A O A [bonded] B at dt in one launch (blocks of whole
+// bonded groups, d.n_ib > 0); the list check runs on the last step when check_last
+constexpr int IB_MAX = 128;
+constexpr int IB_TERMS = 256;       // bonds, and angles, of one block at most
+void launch_inner_steps(const Dev& d, double dt, uint32_t s_off, int nsteps, int check_last, int fp64, cudaStream_t s);
 void launch_energy(const Dev& d, cudaStream_t s);
 void launch_advance(const Dev& d, long long nsteps, cudaStream_t s);
 
@@ -138,18 +174,28 @@ void launch_vacf_spectrum(const double* C, double* S, long long K, cudaStream_t 
 // phase first orders the atoms by their expected number of proposals, and
 // J' runs as a kernel of its own.
 constexpr int NVPHASE_VARIANTS = 4;
-// launch variants of the mixed velocity phase: occupancy variant (v % NVPHASE_VARIANTS),
-// with the rate ordering of the current velocities (v < NVPHASE_VARIANTS) or in the
-// order fixed at set-up (where proposals are few, sorting costs more than it saves)
-constexpr int NVPHASE_LAUNCH_VARIANTS = 2 * NVPHASE_VARIANTS;
+// launch variants of the mixed velocity phase, v in [0, NVPHASE_LAUNCH_VARIANTS):
+// occupancy variant v % NVPHASE_VARIANTS; with the rate ordering of the current
+// velocities ((v / NVPHASE_VARIANTS) % 2 == 0) or in the order fixed at set-up
+// (where proposals are few, sorting costs more than it saves); one thread per
+// atom (v < 2 NVPHASE_VARIANTS) or lanes fed from a queue of atoms (the rest)
+constexpr int NVPHASE_LAUNCH_VARIANTS = 4 * NVPHASE_VARIANTS;
+inline bool vphase_sorted(int v) { return (v / NVPHASE_VARIANTS) % 2 == 0; }
+inline bool vphase_queue(int v) { return v >= 2 * NVPHASE_VARIANTS; }
 constexpr int RATE_BUCKETS = 128;
 // order 2 (mixed mode only): J' (s_off, half 1), C' (s_off, 1), C' (s_off2, 0), J' (s_off2, 0).
 // hp0: host copy of the parameters of replica 0 when the context holds one
 // replica (its constants then travel as a kernel parameter), else null.
+// presorted: the caller has already run launch_rate_order for this phase (mixed
+// mode, variants < NVPHASE_VARIANTS); otherwise the launch orders the atoms itself.
 void launch_vphase(const Dev& d, const double* a, double tau2, uint32_t s_off, int half, int order,
-                   int doC, int doJ, int fp64, int variant, cudaStream_t s, uint32_t s_off2, const RepParams* hp0);
+                   int doC, int doJ, int fp64, int variant, cudaStream_t s, uint32_t s_off2, const RepParams* hp0,
+                   int presorted = 0);
 // same with an absolute stream index s0 (md_run_phase)
 void launch_vphase_abs(const Dev& d, const double* a, double tau2, uint32_t s0, int half, int order,
-                       int doC, int doJ, int fp64, int variant, cudaStream_t s, const RepParams* hp0);
+                       int doC, int doJ, int fp64, int variant, cudaStream_t s, const RepParams* hp0,
+                       int presorted = 0);
+// visiting order of a mixed-mode C' phase over tau2_total (3 kernels)
+void launch_rate_order(const Dev& d, const double* a, double tau2_total, cudaStream_t s);
 
 }  // namespace mdj

@@ -36,44 +36,69 @@ template <> struct Disp<double> {
     }
 };
 
-// bonded terms, one thread per term, FP64 in both modes (with k_b ~ 10^3
-// kcal/mol/A^2 an FP32 bond length would put ~10^-4 kcal/mol/A of error on
-// the force); the per-term gradients are gathered per atom afterwards, so
-// every atom sums its terms in a fixed order
-__global__ void k_bonded_terms(Dev d)
+// bonded terms, FP64 in both modes (with k_b ~ 10^3 kcal/mol/A^2 an FP32 bond
+// length would put ~10^-4 kcal/mol/A of error on the force). bond_term: the
+// gradient on the bond's first atom; angle_term: the gradients on the two end
+// atoms (the centre takes minus their sum)
+__device__ __forceinline__ void bond_term_x(const RepParams& P, const double* xa, const double* xb, double k,
+                                            double r0, double o[3])
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < d.nbond) {
-        const int2 ij = d.bond_ij[t];
-        const RepParams& P = d.P[d.rep[ij.x]];
-        double dx, dy, dz;
-        Disp<double>::get(d, P, ij.x, ij.y, dx, dy, dz);
-        const double r = sqrt(dx * dx + dy * dy + dz * dz);
-        const double f = r > 0.0 ? d.bond_k[t] * (r - d.bond_r0[t]) / r : 0.0;
-        d.bterm[3 * t] = f * dx; d.bterm[3 * t + 1] = f * dy; d.bterm[3 * t + 2] = f * dz;
-        return;
-    }
-    const int ta = t - d.nbond;
-    if (ta >= d.nang) return;
-    const int4 a = d.ang[ta];
-    const RepParams& P = d.P[d.rep[a.y]];
-    double ax, ay, az, bx, by, bz;
-    Disp<double>::get(d, P, a.x, a.y, ax, ay, az);
-    Disp<double>::get(d, P, a.z, a.y, bx, by, bz);
+    const double dx = mimg(xa[0] - xb[0], P), dy = mimg(xa[1] - xb[1], P), dz = mimg(xa[2] - xb[2], P);
+    const double r = sqrt(dx * dx + dy * dy + dz * dz);
+    const double f = r > 0.0 ? k * (r - r0) / r : 0.0;
+    o[0] = f * dx; o[1] = f * dy; o[2] = f * dz;
+}
+
+// xa, xc: the end atoms, xm: the centre
+__device__ __forceinline__ void angle_term_x(const RepParams& P, const double* xa, const double* xm, const double* xc,
+                                             double k, double t0, double o[6])
+{
+    const double ax = mimg(xa[0] - xm[0], P), ay = mimg(xa[1] - xm[1], P), az = mimg(xa[2] - xm[2], P);
+    const double bx = mimg(xc[0] - xm[0], P), by = mimg(xc[1] - xm[1], P), bz = mimg(xc[2] - xm[2], P);
     const double ra = sqrt(ax * ax + ay * ay + az * az), rb = sqrt(bx * bx + by * by + bz * bz);
     double cth = (ax * bx + ay * by + az * bz) / (ra * rb);
     cth = fmin(1.0, fmax(-1.0, cth));
     const double th = acos(cth);
     const double sth = sin(th);
-    double* o = d.aterm + 6 * (size_t)ta;
     if (sth < 1e-12) {
         for (int c = 0; c < 6; ++c) o[c] = 0.0;
         return;
     }
-    const double pre = d.ang_k[ta] * (th - d.ang_t0[ta]);
+    const double pre = k * (th - t0);
     const double ia = pre / (ra * sth), ib = pre / (rb * sth);
     o[0] = (cth * ax / ra - bx / rb) * ia; o[1] = (cth * ay / ra - by / rb) * ia; o[2] = (cth * az / ra - bz / rb) * ia;
     o[3] = (cth * bx / rb - ax / ra) * ib; o[4] = (cth * by / rb - ay / ra) * ib; o[5] = (cth * bz / rb - az / ra) * ib;
+}
+
+__device__ __forceinline__ void bond_term(const Dev& d, int t, double o[3])
+{
+    const int2 ij = d.bond_ij[t];
+    bond_term_x(d.P[d.rep[ij.x]], d.x + 3 * ij.x, d.x + 3 * ij.y, d.bond_k[t], d.bond_r0[t], o);
+}
+
+__device__ __forceinline__ void angle_term(const Dev& d, int ta, double o[6])
+{
+    const int4 a = d.ang[ta];
+    angle_term_x(d.P[d.rep[a.y]], d.x + 3 * a.x, d.x + 3 * a.y, d.x + 3 * a.z, d.ang_k[ta], d.ang_t0[ta], o);
+}
+
+// one thread per term; the per-term gradients are gathered per atom
+// afterwards, so every atom sums its terms in a fixed order
+__global__ void k_bonded_terms(Dev d)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < d.nbond) {
+        double o[3];
+        bond_term(d, t, o);
+        d.bterm[3 * t] = o[0]; d.bterm[3 * t + 1] = o[1]; d.bterm[3 * t + 2] = o[2];
+        return;
+    }
+    const int ta = t - d.nbond;
+    if (ta >= d.nang) return;
+    double o[6];
+    angle_term(d, ta, o);
+    double* out = d.aterm + 6 * (size_t)ta;
+    for (int c = 0; c < 6; ++c) out[c] = o[c];
 }
 
 // sum of the bonded gradients on atom i (items in a fixed order)
@@ -99,10 +124,14 @@ __device__ __forceinline__ void bonded_gather(const Dev& d, int i, double& gx, d
 template <typename T> struct Acc;
 template <> struct Acc<float> {
     long long x = 0, y = 0, z = 0;
+    bool bad = false;          // a term outside the fixed-point range (or not finite)
     __device__ void add(float f, float dx, float dy, float dz)
     {
-        x += to_fix(f * dx); y += to_fix(f * dy); z += to_fix(f * dz);
+        const float gx = f * dx, gy = f * dy, gz = f * dz;
+        bad |= !(fabsf(gx) + fabsf(gy) + fabsf(gz) < FIX_TERM_MAX);
+        x += to_fix(gx); y += to_fix(gy); z += to_fix(gz);
     }
+    __device__ bool overflow() const { return bad; }
     __device__ void combine_shfl(int tpa)
     {
         for (int o = tpa >> 1; o > 0; o >>= 1) {
@@ -121,6 +150,7 @@ template <> struct Acc<double> {
     {
         x += f * dx; y += f * dy; z += f * dz;
     }
+    __device__ bool overflow() const { return false; }
     __device__ void combine_shfl(int tpa)
     {
         for (int o = tpa >> 1; o > 0; o >>= 1) {
@@ -235,9 +265,120 @@ __global__ void __launch_bounds__(256) k_force(Dev d, int lk, double* out, int a
             }
         }
     }
+    if (live && acc.overflow()) {
+        atomicOr(&d.err[r], F_OVERFLOW);
+        atomicOr(&d.ovf[r], OVF_FIX);
+    }
     if (TPA > 1) acc.combine_shfl(TPA);
     if (!live || sub != 0) return;
     double gx = acc.gx(), gy = acc.gy(), gz = acc.gz();
+    if (BONDED) bonded_gather(d, i, gx, gy, gz);
+    if (as_grad) {
+        out[3 * i] = gx; out[3 * i + 1] = gy; out[3 * i + 2] = gz;
+    } else {
+        const double s = -1.0 / d.mt[i];
+        out[3 * i] = s * gx; out[3 * i + 1] = s * gy; out[3 * i + 2] = s * gz;
+    }
+}
+
+// The same pair gradient over half of each list: the threads of atom i take
+// only the partners j > i and add the pair's fixed-point contribution to both
+// atoms (64-bit integer atomics into d.facc), so every unique pair is
+// evaluated once. The lists are symmetric (j is in the list of i exactly when
+// i is in the list of j: membership is decided from r^2, which the exact
+// integer displacement makes the same both ways), the displacement j - i is
+// the exact negation of i - j, the pair terms depend on r, q_i q_j and the
+// (symmetric) LJ table only, and round-to-nearest conversion to fixed point
+// is odd, so each atom receives exactly the terms the full-list kernel sums,
+// and integer sums do not depend on their order: the results are bit for bit
+// those of k_force<float>. k_force_finish converts the sums and clears d.facc.
+template <int W, int TPA>
+__global__ void __launch_bounds__(256) k_force_half(Dev d, int lk)
+{
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = gt / TPA, sub = gt % TPA;
+    const bool live = i < d.N;
+    const int ii = live ? i : d.N - 1;
+    const int r = d.rep[ii];
+    const RepParams& P = d.P[r];
+    Acc<float> acc;
+    if (live) {
+        const int ti = d.type[i];
+        const uint4 pi = d.pos[i];
+        const float qi = __uint_as_float(pi.w);
+        const float cut = W == W_SHORT ? float(fmin(P.rc, P.R)) : float(P.R);
+        const float cut2 = cut * cut;
+        const float sw = float(P.sw), h = float(P.h), sw2 = sw * sw;
+        const float C = float(COULOMB);
+        const uint32_t* row = d.list[lk] + (size_t)i * d.lcap[lk];
+        const int n = min(d.lcnt[lk][i], d.lcap[lk]);
+        const float sc = P.sclf;
+        for (int k = sub; k < n; k += TPA) {
+            const int j = int(row[k]);
+            if (j <= i) continue;
+            const uint4 pj = d.pos[j];
+            float dx, dy, dz;
+            sdisp(pi, pj, sc, P.sclf_lo, dx, dy, dz);
+            const float qj = __uint_as_float(pj.w);
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 >= cut2) continue;
+            if (W == W_LONG && r2 <= sw2) continue;
+            const float rr = sqrtf(r2);
+            const float rinv = 1.f / rr;
+            float u = 0.f, du = 0.f;
+            const float qq = qi * qj;
+            if (qq != 0.f) {
+                float uc, duc;
+                dsf<float>(P, rr, rinv, uc, duc);
+                u = C * qq * uc;
+                du = C * qq * duc;
+            }
+            const LJPair& lj = P.lj[ti * MAX_TYPES + d.type[j]];
+            if (lj.on && !(W == W_LONG && P.lj_long == 1)) {
+                float ul, dul;
+                ljsf<float>(P, lj, rr, rinv, ul, dul);
+                u += ul;
+                du += dul;
+            }
+            float f;
+            if (W == W_FULL) {
+                f = du;
+            } else {
+                float c, dc;
+                chi_and_slope<float>(rr, sw, h, c, dc);
+                f = W == W_SHORT ? dc * u + c * du : -dc * u + (1.f - c) * du;
+            }
+            f *= rinv;
+            const float gx = f * dx, gy = f * dy, gz = f * dz;
+            acc.add(f, dx, dy, dz);
+            unsigned long long* fj = reinterpret_cast<unsigned long long*>(d.facc) + 3 * (size_t)j;
+            atomicAdd(fj, (unsigned long long)(-to_fix(gx)));
+            atomicAdd(fj + 1, (unsigned long long)(-to_fix(gy)));
+            atomicAdd(fj + 2, (unsigned long long)(-to_fix(gz)));
+        }
+    }
+    if (live && acc.overflow()) {
+        atomicOr(&d.err[r], F_OVERFLOW);
+        atomicOr(&d.ovf[r], OVF_FIX);
+    }
+    if (TPA > 1) acc.combine_shfl(TPA);
+    if (!live || sub != 0) return;
+    unsigned long long* fi = reinterpret_cast<unsigned long long*>(d.facc) + 3 * (size_t)i;
+    if (acc.x) atomicAdd(fi, (unsigned long long)acc.x);
+    if (acc.y) atomicAdd(fi + 1, (unsigned long long)acc.y);
+    if (acc.z) atomicAdd(fi + 2, (unsigned long long)acc.z);
+}
+
+// fixed-point sums of k_force_half to the output (plus the bonded terms),
+// clearing the sums for the next evaluation
+template <bool BONDED>
+__global__ void k_force_finish(Dev d, double* out, int as_grad)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.N) return;
+    long long* f = d.facc + 3 * (size_t)i;
+    double gx = double(f[0]) * FIX_INV, gy = double(f[1]) * FIX_INV, gz = double(f[2]) * FIX_INV;
+    f[0] = 0; f[1] = 0; f[2] = 0;
     if (BONDED) bonded_gather(d, i, gx, gy, gz);
     if (as_grad) {
         out[3 * i] = gx; out[3 * i + 1] = gy; out[3 * i + 2] = gz;
@@ -334,6 +475,132 @@ __global__ void k_aoa(Dev d, double tau, uint32_t s_off, int do_check)
     }
 }
 
+// Inner steps of the multiple-time-step drivers, fused: n steps of B(dt/2)
+// A(dt/2) O(dt) A(dt/2) [bonded gradient] B(dt/2) on the bonded force alone
+// (the innermost level of Sec. 2.3). Bonded terms couple only the atoms of
+// one connected group (a molecule), so a block that holds whole groups runs
+// all n steps with block barriers and no grid-wide step: positions stay in
+// shared memory, velocities and accelerations in registers, each term of the
+// block is evaluated once per step into shared memory and every atom sums its
+// terms in its item order. The operations are those of the separate kicks,
+// A-O-A update, term-parallel bonded kernel and gather, in the same order, so
+// the results are the same bits. Blocks: atoms [ib_start[b], ib_start[b+1])
+// (at most IB_MAX), their bonds ib_bond[ib_bond_off[b] ...] and angles
+// ib_ang[ib_ang_off[b] ...] (at most IB_TERMS each); item_slot gives the slot
+// of an item's term within its block's list.
+template <typename T>
+__global__ void __launch_bounds__(IB_MAX) k_inner_steps(Dev d, double dt, uint32_t s_off, int nsteps, int check_last)
+{
+    __shared__ double sx[IB_MAX][3];
+    __shared__ double sb[IB_TERMS][3];
+    __shared__ double sa[IB_TERMS][6];
+    const int blk = blockIdx.x, tid = threadIdx.x;
+    const int b0 = d.ib_start[blk], b1 = d.ib_start[blk + 1];
+    const int tb0 = d.ib_bond_off[blk], nbt = d.ib_bond_off[blk + 1] - tb0;
+    const int ta0 = d.ib_ang_off[blk], nat = d.ib_ang_off[blk + 1] - ta0;
+    const int i = b0 + tid;
+    const bool live = i < b1;
+    const int ic = live ? i : b0;
+    const int r = d.rep[ic];
+    const RepParams& P = d.P[r];
+    const double h = 0.5 * dt;
+    double x[3], v[3], ab[3];
+    int img[3] = {0, 0, 0};
+    bool fin = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        x[a] = d.x[3 * ic + a];
+        v[a] = d.v[3 * ic + a];
+        ab[a] = d.ab[3 * ic + a];
+    }
+    const double c1 = d.stepc[2 * r], c2 = d.stepc[2 * r + 1] * d.isqmt[ic];
+    const double smt = -1.0 / d.mt[ic];
+    for (int st = 0; st < nsteps; ++st) {
+        if (live) {
+            // B: the kick of the bonded acceleration of the previous step
+#pragma unroll
+            for (int a = 0; a < 3; ++a) v[a] += h * ab[a];
+            // A O A and wrap (as k_aoa)
+            const uint32_t s0 = uint32_t(d.step_base[r]) + s_off + uint32_t(st);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) x[a] += h * v[a];
+            const U4 u = draw(P, uint32_t(i - P.atom_off), s0, TAG_O, 0, 0, 0);
+            const T r0 = d_sqrt(T(-2) * d_log(unif<T>(u.x)));
+            const T r1 = d_sqrt(T(-2) * d_log(unif<T>(u.z)));
+            T s1, c1v, s2, c2v;
+            d_sincospi(T(2) * unif<T>(u.y), &s1, &c1v);
+            d_sincospi(T(2) * unif<T>(u.w), &s2, &c2v);
+            const double G[3] = {double(r0 * c1v), double(r0 * s1), double(r1 * c2v)};
+#pragma unroll
+            for (int a = 0; a < 3; ++a) v[a] = c1 * v[a] + c2 * G[a];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                x[a] += h * v[a];
+                if (x[a] < 0.0) { x[a] += P.L; img[a] -= 1; }
+                if (x[a] >= P.L) { x[a] -= P.L; img[a] += 1; }
+                fin = fin && isfinite(x[a]) && isfinite(v[a]);
+                sx[tid][a] = x[a];
+            }
+        }
+        __syncthreads();                // the block's new positions are in shared memory
+        for (int k = tid; k < nbt; k += IB_MAX) {
+            const int t = d.ib_bond[tb0 + k];
+            const int2 ij = d.bond_ij[t];
+            bond_term_x(d.P[d.rep[ij.x]], sx[ij.x - b0], sx[ij.y - b0], d.bond_k[t], d.bond_r0[t], sb[k]);
+        }
+        for (int k = tid; k < nat; k += IB_MAX) {
+            const int t = d.ib_ang[ta0 + k];
+            const int4 an = d.ang[t];
+            angle_term_x(d.P[d.rep[an.y]], sx[an.x - b0], sx[an.y - b0], sx[an.z - b0], d.ang_k[t], d.ang_t0[t], sa[k]);
+        }
+        __syncthreads();                // every term of the block is evaluated
+        if (live) {
+            // bonded gradient of atom i: its items in order (as bonded_gather)
+            double gx = 0, gy = 0, gz = 0;
+            for (int it = d.bi_off[i]; it < d.bi_off[i + 1]; ++it) {
+                const int2 item = d.bitem[it];
+                const int kind = item.x & 15, role = item.x >> 4, sl = d.item_slot[it];
+                if (kind == 0) {
+                    const double sgn = role == 0 ? 1.0 : -1.0;
+                    gx += sgn * sb[sl][0]; gy += sgn * sb[sl][1]; gz += sgn * sb[sl][2];
+                } else {
+                    const double* o = sa[sl];
+                    if (role == 0) { gx += o[0]; gy += o[1]; gz += o[2]; }
+                    else if (role == 2) { gx += o[3]; gy += o[4]; gz += o[5]; }
+                    else { gx -= o[0] + o[3]; gy -= o[1] + o[4]; gz -= o[2] + o[5]; }
+                }
+            }
+            ab[0] = smt * gx; ab[1] = smt * gy; ab[2] = smt * gz;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) v[a] += h * ab[a];
+        }
+    }
+    if (!live) return;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        d.x[3 * i + a] = x[a];
+        d.v[3 * i + a] = v[a];
+        d.ab[3 * i + a] = ab[a];
+        if (img[a]) d.img[3 * i + a] += img[a];
+    }
+    if (!fin) atomicOr(&d.err[r], F_NONFIN);
+    uint4 sp = d.pos[i];
+    sp.x = to_scaled(x[0], P); sp.y = to_scaled(x[1], P); sp.z = to_scaled(x[2], P);
+    d.pos[i] = sp;
+    if (check_last) {
+        const double lo = 0.5 * (P.skin_o - P.skin), li = 0.5 * P.skin;
+        double t0 = mimg(x[0] - d.xo[3 * i], P), t1 = mimg(x[1] - d.xo[3 * i + 1], P),
+               t2 = mimg(x[2] - d.xo[3 * i + 2], P);
+        if (t0 * t0 + t1 * t1 + t2 * t2 > lo * lo) {
+            d.flags[2 * r + 1] = 1;
+            d.flags[2 * r] = 1;
+        }
+        t0 = mimg(x[0] - d.xb[3 * i], P); t1 = mimg(x[1] - d.xb[3 * i + 1], P);
+        t2 = mimg(x[2] - d.xb[3 * i + 2], P);
+        if (t0 * t0 + t1 * t1 + t2 * t2 > li * li) d.flags[2 * r] = 1;
+    }
+}
+
 // energies of the full potential (FP64), kinetic energy; one pass per atom
 __global__ void k_energy(Dev d)
 {
@@ -417,21 +684,51 @@ void force_tpa(const Dev& d, int lk, double* out, int as_grad, int tpa, cudaStre
     }
 }
 
+// half-list form (mixed mode): the pair kernel, then the conversion
+template <int W, bool B>
+void force_half(const Dev& d, int lk, double* out, int as_grad, int tpa, cudaStream_t s)
+{
+    const long long threads = (long long)d.N * tpa;
+    switch (tpa) {
+    case 1: k_force_half<W, 1><<<blocks(threads, 128), 128, 0, s>>>(d, lk); break;
+    case 2: k_force_half<W, 2><<<blocks(threads, 128), 128, 0, s>>>(d, lk); break;
+    case 4: k_force_half<W, 4><<<blocks(threads, 128), 128, 0, s>>>(d, lk); break;
+    default: k_force_half<W, 8><<<blocks(threads, 128), 128, 0, s>>>(d, lk); break;
+    }
+    k_force_finish<B><<<blocks(d.N, 256), 256, 0, s>>>(d, out, as_grad);
+}
+
 template <typename T>
 int force_t(const Dev& d, int mode, double* out, int as_grad, int tpa, cudaStream_t s)
 {
     const bool bonded = mode == 0 || mode == 1 || mode == 5;
     if (bonded && d.nbond + d.nang > 0)
         k_bonded_terms<<<blocks(d.nbond + d.nang, 128), 128, 0, s>>>(d);
-    const int nk = (bonded && d.nbond + d.nang > 0) ? 2 : 1;
+    int nk = (bonded && d.nbond + d.nang > 0) ? 2 : 1;
+    // the half-list kernels (tpa | FORCE_HALF) serve the full, short and long
+    // pair weights of mixed mode; the short weight of replicas that keep the LJ
+    // long part deterministic also runs over the LJ list and stays full
+    const bool half = (tpa & FORCE_HALF) && sizeof(T) == 4 && force_half_ok(d, mode);
+    const int t = tpa & ~FORCE_HALF;
+    if (half) {
+        nk += 1;
+        switch (mode) {
+        case 0: force_half<W_FULL, true>(d, L_FULL, out, as_grad, t, s); break;
+        case 2: force_half<W_FULL, false>(d, L_FULL, out, as_grad, t, s); break;
+        case 3: force_half<W_SHORT, false>(d, L_SHORT, out, as_grad, t, s); break;
+        case 4: force_half<W_LONG, false>(d, L_FULL, out, as_grad, t, s); break;
+        default: force_half<W_SHORT, true>(d, L_SHORT, out, as_grad, t, s); break;
+        }
+        return nk;
+    }
     switch (mode) {
-    case 0: force_tpa<T, W_FULL, true>(d, L_FULL, out, as_grad, tpa, s); break;
+    case 0: force_tpa<T, W_FULL, true>(d, L_FULL, out, as_grad, t, s); break;
     case 1: k_bonded<<<blocks(d.N, 256), 256, 0, s>>>(d, out, as_grad); break;
-    case 2: force_tpa<T, W_FULL, false>(d, L_FULL, out, as_grad, tpa, s); break;
-    case 3: force_tpa<T, W_SHORT, false>(d, L_SHORT, out, as_grad, tpa, s); break;
-    case 4: force_tpa<T, W_LONG, false>(d, L_FULL, out, as_grad, tpa, s); break;
-    case 7: force_tpa<T, W_LJLONG, false>(d, L_LJ, out, as_grad, tpa, s); break;
-    default: force_tpa<T, W_SHORT, true>(d, L_SHORT, out, as_grad, tpa, s); break;
+    case 2: force_tpa<T, W_FULL, false>(d, L_FULL, out, as_grad, t, s); break;
+    case 3: force_tpa<T, W_SHORT, false>(d, L_SHORT, out, as_grad, t, s); break;
+    case 4: force_tpa<T, W_LONG, false>(d, L_FULL, out, as_grad, t, s); break;
+    case 7: force_tpa<T, W_LJLONG, false>(d, L_LJ, out, as_grad, t, s); break;
+    default: force_tpa<T, W_SHORT, true>(d, L_SHORT, out, as_grad, t, s); break;
     }
     return nk;
 }
@@ -451,6 +748,12 @@ void launch_kick(const Dev& d, const double* a, double h, cudaStream_t s)
 void launch_kick2(const Dev& d, const double* a, double h, const double* b, double hb, cudaStream_t s)
 {
     k_kick2<<<blocks(3LL * d.N, 256), 256, 0, s>>>(d, a, h, b, hb);
+}
+
+void launch_inner_steps(const Dev& d, double dt, uint32_t s_off, int nsteps, int check_last, int fp64, cudaStream_t s)
+{
+    if (fp64) k_inner_steps<double><<<d.n_ib, IB_MAX, 0, s>>>(d, dt, s_off, nsteps, check_last);
+    else k_inner_steps<float><<<d.n_ib, IB_MAX, 0, s>>>(d, dt, s_off, nsteps, check_last);
 }
 
 void launch_aoa(const Dev& d, double tau, uint32_t s_off, int do_check, int fp64, cudaStream_t s)

@@ -8,6 +8,8 @@
 // thinning chain (the jumps of F_ij change v_i only, Sec. 3.1), so atoms run
 // in parallel. Between proposals the velocity drifts as v0 + t a + J, with J
 // the sum of the jumps so far; the phase ends at v0 + (tau/2) a + J.
+#include <algorithm>
+
 #include "engine.h"
 
 namespace mdj {
@@ -381,159 +383,213 @@ __host__ __device__ inline JC make_jc(const RepParams& P)
     return c;
 }
 
-// C' for atom i in FP32 (Algorithm 4, adaptive or constant eps, up to four rings).
-// Software-pipelined: right after proposal k is placed in time, the bound at
-// the new state and the ring of proposal k+1 are computed and the list entry
-// of k+1 is fetched; its position is fetched once proposal k is decided. If
-// proposal k jumps, the bound and ring of k+1 are recomputed (and the entry
-// refetched when the ring changed), so the sequence is that of Algorithm 4.
-// Only B and Lam of the bound are kept; ring weights are recomputed from B.
+// C' for atom i in FP32 (Algorithm 4, adaptive or constant eps, up to four rings),
+// written as an initialisation and a step so that a lane can run a chain one
+// proposal at a time (the queue kernel below interleaves the chains of the
+// atoms a lane takes one after the other). Software-pipelined: right after
+// proposal k is placed in time, the bound at the new state and the ring of
+// proposal k+1 are computed and the list entry of k+1 is fetched; its
+// position is fetched once proposal k is decided. If proposal k jumps, the
+// bound and ring of k+1 are recomputed (and the entry refetched when the ring
+// changed), so the sequence is that of Algorithm 4. Only B and Lam of the
+// bound are kept; ring weights are recomputed from B.
+struct CAtom {                             // constants of one atom's C' pass
+    int i, il;
+    int N[MAX_RINGS];
+    float LYv[MAX_RINGS];
+    uint4 pi;
+    float qiC, mt, sbm, sbom, c0, aa, T2;
+    float3 v0, a;
+    uint32_t s0, ctag;
+    int half;
+};
+struct CChain {                            // running state of the chain
+    float t, B, Lam, vx, vy, vz;
+    float3 jv;
+    uint32_t k, Jn;
+    U4 u;
+    int Yn;
+    uint4 pjn;
+};
+
+// per-pair rate bound of ring y at speed bound B
+__device__ __forceinline__ float c_lamy(const JC& c, const CAtom& A, float Ly, float B)
+{
+    return c.adaptive ? fmaf(c.beta * Ly, B, A.c0) : Ly * fmaf(c.beta, B, A.c0);
+}
+
+// bound at the current state: B and Lam = sum_y N_y Lam_y
+__device__ __forceinline__ void c_bound(const JC& c, const CAtom& A, CChain& S)
+{
+    const float s = A.T2 - S.t;
+    const float vv = S.vx * S.vx + S.vy * S.vy + S.vz * S.vz;
+    const float va = S.vx * A.a.x + S.vy * A.a.y + S.vz * A.a.z;
+    S.B = sqrtf(vv + s * s * A.aa + 2.f * s * fmaxf(va, 0.f));
+    float Lam = 0.f;
+#pragma unroll
+    for (int y = 0; y < MAX_RINGS; ++y) Lam += float(A.N[y]) * c_lamy(c, A, A.LYv[y], S.B);
+    S.Lam = Lam;
+}
+
+// ring of a proposal: first ring whose cumulative weight exceeds U Lam; a
+// target that rounds up to Lam falls back to the outermost ring with weight
+__device__ __forceinline__ int c_pick(const JC& c, const CAtom& A, const CChain& S, uint32_t uy)
+{
+    const float target = unif<float>(uy) * S.Lam;
+    int Y = -1, last = 0;
+    float cum = 0.f;
+#pragma unroll
+    for (int y = 0; y < MAX_RINGS; ++y) {
+        const float wy = float(A.N[y]) * c_lamy(c, A, A.LYv[y], S.B);
+        cum += wy;
+        if (y < c.nr && A.N[y] > 0) last = y;     // for finite bounds: exactly the rings with weight
+        if (Y < 0 && y < c.nr && target < cum) Y = y;
+    }
+    return Y < 0 ? last : Y;
+}
+
+// list entry of a proposal; an empty ring (reachable only from a non-finite
+// state, which the A O A update flags) gives the atom itself: outside every ring
+__device__ __forceinline__ uint32_t c_entry(const Dev& d, const CAtom& A, int Y, uint32_t uz)
+{
+    const uint32_t* row = d.list[L_R0 + Y] + (size_t)A.i * d.lcap[L_R0 + Y];
+    const uint32_t NY = uint32_t(ring_sel(A.N, Y));
+    return NY ? __ldg(row + __umulhi(uz, NY)) : uint32_t(A.i);
+}
+
+// constants of atom i's pass and the first proposal's draw, bound, ring and
+// partner; returns false when the atom has no ring partner (no proposal)
+__device__ __forceinline__ bool c_init(const Dev& d, const JC& c, int i, int il, float3 v0, float3 a, float T2,
+                                       uint32_t s0, int half, CAtom& A, CChain& S)
+{
+    int ntot = 0;
+#pragma unroll
+    for (int y = 0; y < MAX_RINGS; ++y) {
+        A.N[y] = y < c.nr ? min(d.lcnt[L_R0 + y][i], d.lcap[L_R0 + y]) : 0;
+        ntot += A.N[y];
+    }
+    if (ntot == 0) return false;
+    A.i = i; A.il = il; A.s0 = s0; A.half = half;
+    A.ctag = (uint32_t(TAG_C) << 24) | (uint32_t(half) << 20);
+    A.mt = float(d.mt[i]);
+    A.sbm = sqrtf(c.beta * A.mt);
+    A.sbom = sqrtf(c.beta / A.mt);
+    const float4 ly4 = __ldg(reinterpret_cast<const float4*>(d.LYf) + i);
+    A.LYv[0] = ly4.x; A.LYv[1] = ly4.y; A.LYv[2] = ly4.z; A.LYv[3] = ly4.w;
+    A.pi = d.pos[i];
+    A.qiC = float(COULOMB) * __uint_as_float(A.pi.w);
+    A.c0 = A.sbom / (c.eps0 * 2.5066282746310002f);
+    A.aa = a.x * a.x + a.y * a.y + a.z * a.z;
+    A.T2 = T2; A.v0 = v0; A.a = a;
+    S.t = 0.f;
+    S.jv = make_float3(0.f, 0.f, 0.f);
+    S.vx = v0.x; S.vy = v0.y; S.vz = v0.z;
+    S.k = 0;
+    S.u = philox(uint32_t(il), s0, A.ctag, 0, c.key0, c.key1);
+    c_bound(c, A, S);
+    S.Yn = c_pick(c, A, S, S.u.y);
+    S.Jn = c_entry(d, A, S.Yn, S.u.z);
+    S.pjn = __ldg(d.pos + S.Jn);
+    return true;
+}
+
+// proposal k of the chain (its time, ring, partner and position are ready):
+// place it, prepare proposal k+1, decide proposal k. Returns true when the
+// pass has ended (the next arrival falls past tau/2, or the proposal cap)
+__device__ __forceinline__ bool c_step(const Dev& d, const JC& c, const RepParams& P, const CAtom& A, CChain& S,
+                                       Tally& tl, uint32_t& err)
+{
+    const float Tn = __fdividef(-__logf(unif<float>(S.u.x)), S.Lam);
+    if (!(S.Lam > 0.f) || S.t + Tn > A.T2) return true;
+    const float tprev = S.t;
+    S.t += Tn;
+    S.vx = fmaf(S.t, A.a.x, A.v0.x) + S.jv.x;
+    S.vy = fmaf(S.t, A.a.y, A.v0.y) + S.jv.y;
+    S.vz = fmaf(S.t, A.a.z, A.v0.z) + S.jv.z;
+    tl.cprop++;
+    const int Y = S.Yn;
+    const int J = int(S.Jn);
+    const uint4 pj = S.pjn;
+    const float Bk = S.B;
+    const uint32_t uacc = S.u.w;
+    const uint32_t kk = S.k;
+    ++S.k;
+    // next proposal: draw, bound at the new state, ring and list entry
+    S.u = philox(uint32_t(A.il), A.s0, A.ctag, S.k, c.key0, c.key1);
+    c_bound(c, A, S);
+    S.Yn = c_pick(c, A, S, S.u.y);
+    S.Jn = c_entry(d, A, S.Yn, S.u.z);
+    // decide proposal kk
+    float dx, dy, dz;
+    sdisp(A.pi, pj, c.sc, c.sclo, dx, dy, dz);
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    const float rinv = rsqrtf(r2);
+    const float r = r2 * rinv;
+    if (r >= ring_sel(c.elo, Y) && r < ring_sel(c.ehi, Y)) {
+        const float f = A.qiC * __uint_as_float(pj.w) *
+                        coul_long_f(r, rinv, c.alpha, c.kexp, c.eR, c.fR, c.R, c.sw, c.h) * rinv;
+        const float gx = f * dx, gy = f * dy, gz = f * dz;
+        const float gn = fabsf(f) * r;
+        if (gn > 0.f) {
+            const float vg = S.vx * gx + S.vy * gy + S.vz * gz;
+            float eps, eta, p;
+            if (c.adaptive) {
+                eps = c.eps0 * gn;
+                eta = c.eps0 * A.sbm * vg;
+                p = __fdividef(A.sbom * theta<float>(eta), c.eps0 * c_lamy(c, A, ring_sel(A.LYv, Y), Bk));
+            } else {
+                eps = c.eps0;
+                eta = __fdividef(c.eps0 * A.sbm * vg, gn);
+                p = __fdividef(gn * theta<float>(eta), ring_sel(A.LYv, Y) * (c.eps0 * A.sbm * Bk + 0.3989422804014327f));
+            }
+            bool acc;
+            const float U = unif<float>(uacc);
+            if (fabsf(U - p) < 2e-6f) {
+                const double v0d[3] = {d.v[3 * A.i], d.v[3 * A.i + 1], d.v[3 * A.i + 2]};
+                const double ad[3] = {double(A.a.x), double(A.a.y), double(A.a.z)};
+                const float jac[3] = {S.jv.x, S.jv.y, S.jv.z};
+                const double p64 = cprime_p64(d, P, A.i, J, Y, v0d, ad, double(tprev), double(S.t), jac,
+                                              double(A.aa), double(A.T2));
+                acc = unif<double>(uacc) <= p64;
+                if (p64 > 1.0) err |= F_BOUND;
+                tl.guard++;
+            } else {
+                acc = U <= p;
+                if (p > 1.f + P_TOL32) err |= F_BOUND;
+            }
+            if (acc) {
+                int att;
+                bool ok;
+                const float G = sample_gtilde_f(P, uint32_t(A.il), A.s0, A.half, kk, eta, &att, &ok);
+                tl.satt += att;
+                if (!ok) err |= F_LIMIT;
+                const float coef = 2.f * eps / (A.sbm * (1.f + eps * eps)) * (eta + G) / gn;
+                S.jv.x -= coef * gx; S.jv.y -= coef * gy; S.jv.z -= coef * gz;
+                S.vx -= coef * gx; S.vy -= coef * gy; S.vz -= coef * gz;
+                tl.cacc++;
+                log_event(d, (long long)A.s0, A.half, int(TAG_C), d.rep[A.i], A.il, kk, J - c.atom_off);
+                // the velocity changed: bound and ring of the next proposal again
+                c_bound(c, A, S);
+                const int Y2 = c_pick(c, A, S, S.u.y);
+                if (Y2 != S.Yn) { S.Yn = Y2; S.Jn = c_entry(d, A, S.Yn, S.u.z); }
+            }
+        }
+    }
+    S.pjn = __ldg(d.pos + S.Jn);
+    if (S.k >= uint32_t(KMAX)) { err |= F_LIMIT; return true; }
+    return false;
+}
+
+// C' for atom i in FP32: the whole chain in one loop; jv receives the sum of the jumps
 __device__ __forceinline__ void cprime_f(const Dev& d, const JC& c, const RepParams& P, int i, int il, float3& jv,
                                          const float3 v0, const float3 a, float T2, uint32_t s0, int half,
                                          Tally& tl, uint32_t& err)
 {
-    int N[MAX_RINGS];
-    if (ring_counts(d, P, i, N) == 0) return;
-    const uint32_t ctag = (uint32_t(TAG_C) << 24) | (uint32_t(half) << 20);
-    const float mt = float(d.mt[i]);
-    const float sbm = sqrtf(c.beta * mt), sbom = sqrtf(c.beta / mt);
-    const float4 ly4 = __ldg(reinterpret_cast<const float4*>(d.LYf) + i);
-    const float LYv[MAX_RINGS] = {ly4.x, ly4.y, ly4.z, ly4.w};
-    const uint4 pi = d.pos[i];
-    const float qiC = float(COULOMB) * __uint_as_float(pi.w);
-    const float c0 = sbom / (c.eps0 * 2.5066282746310002f);
-    const float aa = a.x * a.x + a.y * a.y + a.z * a.z;
-
-    float t = 0.f;
-    float vx = v0.x + jv.x, vy = v0.y + jv.y, vz = v0.z + jv.z;
-    // per-pair rate bound of ring y at speed bound B
-    auto lamy = [&](int y, float B) -> float {
-        return c.adaptive ? fmaf(c.beta * LYv[y], B, c0) : LYv[y] * fmaf(c.beta, B, c0);
-    };
-    auto lamy_sel = [&](int Y, float B) -> float {
-        const float L = ring_sel(LYv, Y);
-        return c.adaptive ? fmaf(c.beta * L, B, c0) : L * fmaf(c.beta, B, c0);
-    };
-    // bound at the current state: B and Lam = sum_y N_y Lam_y
-    float B, Lam;
-    auto bound = [&]() {
-        const float s = T2 - t;
-        const float vv = vx * vx + vy * vy + vz * vz;
-        const float va = vx * a.x + vy * a.y + vz * a.z;
-        B = sqrtf(vv + s * s * aa + 2.f * s * fmaxf(va, 0.f));
-        Lam = 0.f;
-#pragma unroll
-        for (int y = 0; y < MAX_RINGS; ++y) Lam += float(N[y]) * lamy(y, B);
-    };
-    // ring of a proposal: first ring whose cumulative weight exceeds U Lam;
-    // a target that rounds up to Lam falls back to the outermost ring with weight
-    auto pick = [&](uint32_t uy) -> int {
-        const float target = unif<float>(uy) * Lam;
-        int Y = -1, last = 0;
-        float cum = 0.f;
-#pragma unroll
-        for (int y = 0; y < MAX_RINGS; ++y) {
-            const float wy = float(N[y]) * lamy(y, B);
-            cum += wy;
-            if (y < c.nr && N[y] > 0) last = y;     // for finite bounds: exactly the rings with weight
-            if (Y < 0 && y < c.nr && target < cum) Y = y;
-        }
-        return Y < 0 ? last : Y;
-    };
-    // list entry of a proposal; an empty ring (reachable only from a non-finite
-    // state, which the A O A update flags) gives the atom itself: outside every ring
-    auto entry = [&](int Y, uint32_t uz) -> uint32_t {
-        const uint32_t* row = d.list[L_R0 + Y] + (size_t)i * d.lcap[L_R0 + Y];
-        const uint32_t NY = uint32_t(ring_sel(N, Y));
-        return NY ? __ldg(row + __umulhi(uz, NY)) : uint32_t(i);
-    };
-    uint32_t k = 0;
-    U4 u = philox(uint32_t(il), s0, ctag, 0, c.key0, c.key1);
-    bound();
-    int Yn = pick(u.y);
-    uint32_t Jn = entry(Yn, u.z);
-    uint4 pjn = __ldg(d.pos + Jn);
-    for (;;) {
-        // proposal k: its time, ring Yn, partner Jn and position pjn are ready
-        const float Tn = __fdividef(-__logf(unif<float>(u.x)), Lam);
-        if (!(Lam > 0.f) || t + Tn > T2) break;
-        const float tprev = t;
-        t += Tn;
-        vx = fmaf(t, a.x, v0.x) + jv.x;
-        vy = fmaf(t, a.y, v0.y) + jv.y;
-        vz = fmaf(t, a.z, v0.z) + jv.z;
-        tl.cprop++;
-        const int Y = Yn;
-        const int J = int(Jn);
-        const uint4 pj = pjn;
-        const float Bk = B;
-        const uint32_t uacc = u.w;
-        const uint32_t kk = k;
-        ++k;
-        // next proposal: draw, bound at the new state, ring and list entry
-        u = philox(uint32_t(il), s0, ctag, k, c.key0, c.key1);
-        bound();
-        Yn = pick(u.y);
-        Jn = entry(Yn, u.z);
-        // decide proposal kk
-        float dx, dy, dz;
-        sdisp(pi, pj, c.sc, c.sclo, dx, dy, dz);
-        const float r2 = dx * dx + dy * dy + dz * dz;
-        const float rinv = rsqrtf(r2);
-        const float r = r2 * rinv;
-        if (r >= ring_sel(c.elo, Y) && r < ring_sel(c.ehi, Y)) {
-            const float f = qiC * __uint_as_float(pj.w) *
-                            coul_long_f(r, rinv, c.alpha, c.kexp, c.eR, c.fR, c.R, c.sw, c.h) * rinv;
-            const float gx = f * dx, gy = f * dy, gz = f * dz;
-            const float gn = fabsf(f) * r;
-            if (gn > 0.f) {
-                const float vg = vx * gx + vy * gy + vz * gz;
-                float eps, eta, p;
-                if (c.adaptive) {
-                    eps = c.eps0 * gn;
-                    eta = c.eps0 * sbm * vg;
-                    p = __fdividef(sbom * theta<float>(eta), c.eps0 * lamy_sel(Y, Bk));
-                } else {
-                    eps = c.eps0;
-                    eta = __fdividef(c.eps0 * sbm * vg, gn);
-                    p = __fdividef(gn * theta<float>(eta), ring_sel(LYv, Y) * (c.eps0 * sbm * Bk + 0.3989422804014327f));
-                }
-                bool acc;
-                const float U = unif<float>(uacc);
-                if (fabsf(U - p) < 2e-6f) {
-                    const double v0d[3] = {d.v[3 * i], d.v[3 * i + 1], d.v[3 * i + 2]};
-                    const double ad[3] = {double(a.x), double(a.y), double(a.z)};
-                    const float jac[3] = {jv.x, jv.y, jv.z};
-                    const double p64 = cprime_p64(d, P, i, J, Y, v0d, ad, double(tprev), double(t), jac,
-                                                  double(aa), double(T2));
-                    acc = unif<double>(uacc) <= p64;
-                    if (p64 > 1.0) err |= F_BOUND;
-                    tl.guard++;
-                } else {
-                    acc = U <= p;
-                    if (p > 1.f + P_TOL32) err |= F_BOUND;
-                }
-                if (acc) {
-                    int att;
-                    bool ok;
-                    const float G = sample_gtilde_f(P, uint32_t(il), s0, half, kk, eta, &att, &ok);
-                    tl.satt += att;
-                    if (!ok) err |= F_LIMIT;
-                    const float coef = 2.f * eps / (sbm * (1.f + eps * eps)) * (eta + G) / gn;
-                    jv.x -= coef * gx; jv.y -= coef * gy; jv.z -= coef * gz;
-                    vx -= coef * gx; vy -= coef * gy; vz -= coef * gz;
-                    tl.cacc++;
-                    log_event(d, (long long)s0, half, int(TAG_C), d.rep[i], il, kk, J - c.atom_off);
-                    // the velocity changed: bound and ring of the next proposal again
-                    bound();
-                    const int Y2 = pick(u.y);
-                    if (Y2 != Yn) { Yn = Y2; Jn = entry(Yn, u.z); }
-                }
-            }
-        }
-        pjn = __ldg(d.pos + Jn);
-        if (k >= uint32_t(KMAX)) { err |= F_LIMIT; break; }
-    }
+    CAtom A;
+    CChain S;
+    if (!c_init(d, c, i, il, v0, a, T2, s0, half, A, S)) return;
+    while (!c_step(d, c, P, A, S, tl, err)) {}
+    jv = S.jv;
 }
 
 // mixed-mode velocity phase; threads visit atoms in the order vorder (atoms
@@ -600,6 +656,133 @@ __global__ void __launch_bounds__(128, MINB) k_cphase_f(Dev d, const __grid_cons
     warp_add(&C[C_GUARD], tl.guard, uniform, lane);
     warp_add(&C[C_JPROP], tl.jprop, uniform, lane);
     warp_add(&C[C_JACC], tl.jacc, uniform, lane);
+}
+
+// The same velocity phase with lanes fed from a queue. In the kernel above a
+// warp runs 32 chains to the end of the longest one: the Poisson counts of
+// the 32 atoms differ even when their expected counts match, so lanes idle.
+// Here every lane runs one proposal per loop turn, and a lane whose atom is
+// finished (J' before, its C' passes, J' after) takes the next atom of the
+// visiting order from a warp pool refilled 32 atoms at a time from a global
+// counter (qctr, zero at launch). Each atom's chain is the same sequence of
+// draws and decisions as above, so the results are identical; only the
+// assignment of atoms to lanes differs. Counters are flushed whenever a lane
+// moves to another replica (the order groups atoms by replica).
+template <int MINB, bool SINGLE>
+__global__ void __launch_bounds__(128, MINB) k_cphase_q(Dev d, const __grid_constant__ JC jc0, const double* a,
+                                                        double tau2, uint32_t s_off, int s_abs, int half, int npass,
+                                                        uint32_t s_off2, int jmode, int* qctr)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned lower = (1u << lane) - 1u;
+    int pool_base = 0, pool_left = 0;          // warp-uniform
+    bool drained = false;                      // warp-uniform
+    int i = -1, pass = 0, tr = -1;             // atom, pass, replica of the tallied work
+    bool chain = false;                        // the current pass has been set up
+    bool live = false;                         // ... and has proposals to run
+    double v[3] = {0.0, 0.0, 0.0}, ad[3] = {0.0, 0.0, 0.0};
+    JC jcl{};
+    CAtom A;
+    CChain S;
+    Tally tl;
+    uint32_t err = 0;
+    const RepParams* P = d.P;
+    auto flush = [&](int r) {
+        unsigned long long* C = d.cnt + (size_t)r * NCOUNT;
+        if (tl.cprop) atomicAdd(&C[C_CPROP], (unsigned long long)tl.cprop);
+        if (tl.cacc) atomicAdd(&C[C_CACC], (unsigned long long)tl.cacc);
+        if (tl.satt) atomicAdd(&C[C_SATT], (unsigned long long)tl.satt);
+        if (tl.guard) atomicAdd(&C[C_GUARD], (unsigned long long)tl.guard);
+        if (tl.jprop) atomicAdd(&C[C_JPROP], (unsigned long long)tl.jprop);
+        if (tl.jacc) atomicAdd(&C[C_JACC], (unsigned long long)tl.jacc);
+        tl = Tally();
+    };
+    for (;;) {
+        // idle lanes take the next atoms of the order
+        unsigned need = __ballot_sync(0xffffffffu, i < 0);
+        while (need && !drained) {
+            if (pool_left == 0) {
+                int b = 0;
+                if (lane == 0) b = atomicAdd(qctr, 32);
+                b = __shfl_sync(0xffffffffu, b, 0);
+                pool_base = b;
+                pool_left = b < d.N ? min(32, d.N - b) : 0;
+                if (pool_left == 0) { drained = true; break; }
+            }
+            const int take = min(__popc(need), pool_left);
+            const int rank = __popc(need & lower);
+            if (((need >> lane) & 1u) && rank < take) i = d.vorder[pool_base + rank];
+            pool_base += take;
+            pool_left -= take;
+            need = __ballot_sync(0xffffffffu, i < 0);
+        }
+        if (!__any_sync(0xffffffffu, i >= 0)) break;
+        if (i >= 0 && !chain) {
+            // a new atom (pass 0), or the next pass of the current one
+            const int r = d.rep[i];
+            P = d.P + r;
+            const int il = i - P->atom_off;
+            const uint32_t sb = s_abs ? 0u : uint32_t(d.step_base[r]);
+            if (pass == 0) {
+                if (tr != r) {
+                    if (tr >= 0) flush(tr);
+                    tr = r;
+                }
+                v[0] = d.v[3 * i]; v[1] = d.v[3 * i + 1]; v[2] = d.v[3 * i + 2];
+                ad[0] = a ? a[3 * i] : 0.0; ad[1] = a ? a[3 * i + 1] : 0.0; ad[2] = a ? a[3 * i + 2] : 0.0;
+                if ((jmode & 2) && P->lj_jump) jprime<float>(d, *P, i, il, v, tau2, sb + s_off, half, tl, err);
+                if (!SINGLE) jcl = make_jc(*P);
+            }
+            const uint32_t s0 = sb + (pass ? s_off2 : s_off);
+            const int hp = pass ? 0 : half;
+            live = false;
+            if (P->rings_on) {
+                // the FP64 guard of an acceptance reads the velocity at the start of the pass
+                d.v[3 * i] = v[0]; d.v[3 * i + 1] = v[1]; d.v[3 * i + 2] = v[2];
+                const float3 v0 = make_float3(float(v[0]), float(v[1]), float(v[2]));
+                const float3 af = make_float3(float(ad[0]), float(ad[1]), float(ad[2]));
+                live = c_init(d, SINGLE ? jc0 : jcl, i, il, v0, af, float(tau2), s0, hp, A, S);
+            }
+            if (!live) S.jv = make_float3(0.f, 0.f, 0.f);    // no partner: the pass is a plain drift
+            chain = true;
+        }
+        bool ended = false;
+        if (i >= 0) ended = !live || c_step(d, SINGLE ? jc0 : jcl, *P, A, S, tl, err);
+        if (ended) {
+            // FP64 end of the pass: (v0 + (tau/2) a) + sum of the jumps
+            v[0] = fma(tau2, ad[0], v[0]) + double(S.jv.x);
+            v[1] = fma(tau2, ad[1], v[1]) + double(S.jv.y);
+            v[2] = fma(tau2, ad[2], v[2]) + double(S.jv.z);
+            chain = false;
+            if (++pass >= npass) {
+                const int r = d.rep[i];
+                if (jmode & 1 && P->lj_jump) {
+                    const uint32_t sb = s_abs ? 0u : uint32_t(d.step_base[r]);
+                    jprime<float>(d, *P, i, i - P->atom_off, v, tau2, sb + (jmode == 3 ? s_off2 : s_off),
+                                  jmode == 3 ? 0 : half, tl, err);
+                }
+                d.v[3 * i] = v[0]; d.v[3 * i + 1] = v[1]; d.v[3 * i + 2] = v[2];
+                if (err) { atomicOr(&d.err[r], err); err = 0; }
+                i = -1;
+                pass = 0;
+            }
+        }
+    }
+    // counters: one reduction per warp when its lanes' last work was on one replica
+    const unsigned has = __ballot_sync(0xffffffffu, tr >= 0);
+    if (!has) return;
+    const int t0 = __shfl_sync(0xffffffffu, tr, __ffs(has) - 1);
+    if (__all_sync(0xffffffffu, tr == t0 || tr < 0)) {
+        unsigned long long* C = d.cnt + (size_t)t0 * NCOUNT;
+        warp_add(&C[C_CPROP], tl.cprop, true, lane);
+        warp_add(&C[C_CACC], tl.cacc, true, lane);
+        warp_add(&C[C_SATT], tl.satt, true, lane);
+        warp_add(&C[C_GUARD], tl.guard, true, lane);
+        warp_add(&C[C_JPROP], tl.jprop, true, lane);
+        warp_add(&C[C_JACC], tl.jacc, true, lane);
+    } else if (tr >= 0) {
+        flush(tr);
+    }
 }
 
 // mixed-mode J' phase: one thread per atom (BPS bounces, FP64 velocity)
@@ -772,8 +955,41 @@ static void rate_order(const Dev& d, const double* a, double tau2, cudaStream_t 
     k_rate_scatter<<<nb, 256, 0, st>>>(d);
 }
 
+// resident blocks of a queue kernel over the whole GPU (the grid of a
+// persistent launch), at most the blocks a plain launch would take
+template <int MINB, bool SINGLE>
+static int queue_blocks()
+{
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cphase_q<MINB, SINGLE>, 128, 0);
+    return std::max(1, sms * std::max(per, 1));
+}
+
+static int queue_grid(int occ, bool single, int nb)
+{
+    static int cache[2][NVPHASE_VARIANTS] = {};
+    int& g = cache[single ? 1 : 0][occ];
+    if (!g) {
+        switch (occ) {
+        case 1: g = single ? queue_blocks<4, true>() : queue_blocks<4, false>(); break;
+        case 2: g = single ? queue_blocks<5, true>() : queue_blocks<5, false>(); break;
+        case 3: g = single ? queue_blocks<6, true>() : queue_blocks<6, false>(); break;
+        default: g = single ? queue_blocks<3, true>() : queue_blocks<3, false>(); break;
+        }
+    }
+    return std::min(g, nb);
+}
+
+void launch_rate_order(const Dev& d, const double* a, double tau2_total, cudaStream_t st)
+{
+    rate_order(d, a, tau2_total, st);
+}
+
 static void vphase_any(const Dev& d, const double* a, double tau2, uint32_t s, uint32_t s2, int s_abs, int half,
-                       int order, int doC, int doJ, int fp64, int variant, cudaStream_t st, const RepParams* hp0)
+                       int order, int doC, int doJ, int fp64, int variant, cudaStream_t st, const RepParams* hp0,
+                       int presorted)
 {
     const int nb = (d.N + 127) / 128;
     if (fp64) {
@@ -789,20 +1005,43 @@ static void vphase_any(const Dev& d, const double* a, double tau2, uint32_t s, u
     const int jmode = !doJ ? 0 : (order == 0 ? 1 : (order == 1 ? 2 : 3));
     // any visiting order gives the same values: each atom's chain depends on its own draws
     Dev dv = d;
-    if (variant < NVPHASE_VARIANTS) rate_order(d, a, tau2 * npass, st);
-    else dv.vorder = const_cast<int*>(d.vorder0);
-    variant %= NVPHASE_VARIANTS;
+    if (vphase_sorted(variant)) {
+        if (!presorted) rate_order(d, a, tau2 * npass, st);
+    } else {
+        dv.vorder = const_cast<int*>(d.vorder0);
+    }
+    const bool queue = vphase_queue(variant);
+    const int occ = variant % NVPHASE_VARIANTS;
+    const JC jc = hp0 ? make_jc(*hp0) : JC{};
+    if (queue) {
+        cudaMemsetAsync(d.qctr, 0, sizeof(int), st);
+        const int g = queue_grid(occ, hp0 != nullptr, nb);
+        if (hp0) {
+            switch (occ) {
+            case 1: k_cphase_q<4, true><<<g, 128, 0, st>>>(dv, jc, a, tau2, s, s_abs, half, npass, s2, jmode, d.qctr); break;
+            case 2: k_cphase_q<5, true><<<g, 128, 0, st>>>(dv, jc, a, tau2, s, s_abs, half, npass, s2, jmode, d.qctr); break;
+            case 3: k_cphase_q<6, true><<<g, 128, 0, st>>>(dv, jc, a, tau2, s, s_abs, half, npass, s2, jmode, d.qctr); break;
+            default: k_cphase_q<3, true><<<g, 128, 0, st>>>(dv, jc, a, tau2, s, s_abs, half, npass, s2, jmode, d.qctr); break;
+            }
+        } else {
+            switch (occ) {
+            case 1: k_cphase_q<4, false><<<g, 128, 0, st>>>(dv, jc, a, tau2, s, s_abs, half, npass, s2, jmode, d.qctr); break;
+            case 2: k_cphase_q<5, false><<<g, 128, 0, st>>>(dv, jc, a, tau2, s, s_abs, half, npass, s2, jmode, d.qctr); break;
+            case 3: k_cphase_q<6, false><<<g, 128, 0, st>>>(dv, jc, a, tau2, s, s_abs, half, npass, s2, jmode, d.qctr); break;
+            default: k_cphase_q<3, false><<<g, 128, 0, st>>>(dv, jc, a, tau2, s, s_abs, half, npass, s2, jmode, d.qctr); break;
+            }
+        }
+        return;
+    }
     if (hp0) {
-        const JC jc = make_jc(*hp0);
-        switch (variant) {
+        switch (occ) {
         case 1: k_cphase_f<4, true><<<nb, 128, 0, st>>>(dv, jc, a, tau2, s, s_abs, half, npass, s2, jmode); break;
         case 2: k_cphase_f<5, true><<<nb, 128, 0, st>>>(dv, jc, a, tau2, s, s_abs, half, npass, s2, jmode); break;
         case 3: k_cphase_f<6, true><<<nb, 128, 0, st>>>(dv, jc, a, tau2, s, s_abs, half, npass, s2, jmode); break;
         default: k_cphase_f<3, true><<<nb, 128, 0, st>>>(dv, jc, a, tau2, s, s_abs, half, npass, s2, jmode); break;
         }
     } else {
-        const JC jc{};
-        switch (variant) {
+        switch (occ) {
         case 1: k_cphase_f<4, false><<<nb, 128, 0, st>>>(dv, jc, a, tau2, s, s_abs, half, npass, s2, jmode); break;
         case 2: k_cphase_f<5, false><<<nb, 128, 0, st>>>(dv, jc, a, tau2, s, s_abs, half, npass, s2, jmode); break;
         case 3: k_cphase_f<6, false><<<nb, 128, 0, st>>>(dv, jc, a, tau2, s, s_abs, half, npass, s2, jmode); break;
@@ -812,15 +1051,17 @@ static void vphase_any(const Dev& d, const double* a, double tau2, uint32_t s, u
 }
 
 void launch_vphase(const Dev& d, const double* a, double tau2, uint32_t s_off, int half, int order,
-                   int doC, int doJ, int fp64, int variant, cudaStream_t s, uint32_t s_off2, const RepParams* hp0)
+                   int doC, int doJ, int fp64, int variant, cudaStream_t s, uint32_t s_off2, const RepParams* hp0,
+                   int presorted)
 {
-    vphase_any(d, a, tau2, s_off, s_off2, 0, half, order, doC, doJ, fp64, variant, s, hp0);
+    vphase_any(d, a, tau2, s_off, s_off2, 0, half, order, doC, doJ, fp64, variant, s, hp0, presorted);
 }
 
 void launch_vphase_abs(const Dev& d, const double* a, double tau2, uint32_t s0, int half, int order,
-                       int doC, int doJ, int fp64, int variant, cudaStream_t s, const RepParams* hp0)
+                       int doC, int doJ, int fp64, int variant, cudaStream_t s, const RepParams* hp0,
+                       int presorted)
 {
-    vphase_any(d, a, tau2, s0, 0, 1, half, order, doC, doJ, fp64, variant, s, hp0);
+    vphase_any(d, a, tau2, s0, 0, 1, half, order, doC, doJ, fp64, variant, s, hp0, presorted);
 }
 
 }  // namespace mdj

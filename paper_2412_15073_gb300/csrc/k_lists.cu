@@ -12,6 +12,8 @@
 //          x_b, when an atom moved more than skin/2 since the last build.
 // Every rebuild kernel reads the per-replica flags and returns at once when
 // its replica does not rebuild, so the chain can be launched every step.
+#include <algorithm>
+
 #include "engine.h"
 
 namespace mdj {
@@ -199,18 +201,20 @@ __global__ void __launch_bounds__(32 * OUTER_WARPS) k_outer_cells(Dev d, int exa
     __shared__ uint32_t* hrow[OUTER_WARPS][32];  // their rows of the outer list
     __shared__ int hmore[OUTER_WARPS][32];     // 1: more than four excluded partners, else -1
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int task = blockIdx.x * OUTER_WARPS + w;       // (cell, share of its atoms)
+    const int ntask = d.total_cells * OUTER_GROUPS;
+    // the warps stride over the tasks (cell, share of its atoms): a launch in
+    // which no replica rebuilds costs one flag read per task
+    for (int task = blockIdx.x * OUTER_WARPS + w; task < ntask; task += gridDim.x * OUTER_WARPS) {
     const int c = task / OUTER_GROUPS, g = task % OUTER_GROUPS;
-    if (c >= d.total_cells) return;
     const int r = d.cell_rep[c];
-    if (r < 0 || !d.flags[2 * r + 1]) return;
+    if (r < 0 || !d.flags[2 * r + 1]) continue;
     const int s_i = d.cell_start[c], e_i = d.cell_start[c + 1];
     const int natoms = e_i - s_i;
     if (g == 0 && natoms > 1024 && lane == 0) { atomicOr(&d.err[r], F_OVERFLOW); atomicOr(&d.ovf[r], OVF_CELL); }
     const int nlim = min(natoms, 1024);
     const int share = (nlim + OUTER_GROUPS - 1) / OUTER_GROUPS;
     const int h_lo = g * share, h_hi = min(nlim, h_lo + share);
-    if (h_lo >= h_hi) return;
+    if (h_lo >= h_hi) continue;
     const RepParams& P = d.P[r];
     const int nc = P.nc;
     const int lin = c - P.cell_off;
@@ -345,119 +349,170 @@ __global__ void __launch_bounds__(32 * OUTER_WARPS) k_outer_cells(Dev d, int exa
             }
         }
     }
+    }
 }
 
 // one warp per atom: filter the outer list into the inner lists, keeping its
 // order. Ring and LJ membership (which decides the partner a jump picks) comes
 // from the replica's shell table; candidates in a bin that holds a shell limit
-// are decided in FP64 from the build positions, as in exact mode.
-__global__ void __launch_bounds__(32 * WARPS) k_inner_lists(Dev d, int kinds, int exact, int late)
+// are decided in FP64 from the build positions, as in exact mode. KM is the
+// set of list kinds the context builds, known at compile time for the usual
+// sets (0: any, read from `kinds`). The warps stride over the atoms, so a
+// launch in which no replica rebuilds costs one flag read per atom and no
+// block of its own.
+template <uint32_t KM>
+__global__ void __launch_bounds__(32 * WARPS) k_inner_lists(Dev d, int kinds_rt, int exact, int late)
 {
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int i = blockIdx.x * WARPS + w;
-    if (i >= d.N) return;
-    const int r = d.rep[i];
-    if (!late && !d.flags[2 * r]) return;
-    const RepParams& P = d.P[r];
-    const uint4 pi = d.pos[i];
-    const float qi = __uint_as_float(pi.w);
-    const int ti = d.type[i];
-    constexpr uint32_t RING_BITS = ((1u << MAX_RINGS) - 1u) << L_R0;
-    // lists this atom takes: rings (y < nr) need a charge, LJ an LJ type pair
-    uint32_t want = uint32_t(kinds) & ((1u << L_SHORT) | (1u << L_FULL));
+    const uint32_t kinds = KM ? KM : uint32_t(kinds_rt);
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * WARPS;
+    for (int i = blockIdx.x * WARPS + (threadIdx.x >> 5); i < d.N; i += nw) {
+        const int r = d.rep[i];
+        if (!late && !d.flags[2 * r]) continue;
+        const RepParams& P = d.P[r];
+        const uint4 pi = d.pos[i];
+        const float qi = __uint_as_float(pi.w);
+        const int ti = d.type[i];
+        constexpr uint32_t RING_BITS = ((1u << MAX_RINGS) - 1u) << L_R0;
+        // lists this atom takes: rings (y < nr) need a charge, LJ an LJ type pair
+        uint32_t want = kinds & ((1u << L_SHORT) | (1u << L_FULL));
 #pragma unroll
-    for (int y = 0; y < MAX_RINGS; ++y)
-        if ((kinds & (1 << (L_R0 + y))) && y < P.nr && P.rings_on && qi != 0.f) want |= 1u << (L_R0 + y);
-    unsigned ljmask = 0;
-    if ((kinds & (1 << L_LJ)) && P.lj_on) {
-        for (int t = 0; t < P.ntypes; ++t) ljmask |= (P.lj[ti * MAX_TYPES + t].on ? 1u : 0u) << t;
-        if (ljmask) want |= 1u << L_LJ;
-    }
-    const bool need_type = (want >> L_LJ) & 1u;
-    const float r2s = P.r2s, r2f = P.r2f;
-    const uint16_t* tab = d.shell_tab + (size_t)r * SHELL_BINS;
-    const float invw = P.shell_invw;
-    const float sc = P.sclf, sclo = P.sclf_lo;
-    int cnt[NKIND] = {};
-    const int n_o = min(d.ocnt[i], d.ocap);
-    const uint32_t* orow = d.olist + (size_t)i * d.ocap;
-    // three batches of 32 candidates in flight: the entries of batch b+2 and
-    // the positions (and types) of batch b+1 load while batch b is filtered
-    uint32_t j1 = lane < n_o ? __ldg(orow + lane) : 0u;
-    uint32_t j2 = lane + 32 < n_o ? __ldg(orow + lane + 32) : 0u;
-    uint4 p1 = lane < n_o ? d.pos[j1] : make_uint4(0, 0, 0, 0);
-    int t1 = (lane < n_o && need_type) ? __ldg(d.type + j1) : 0;
-    for (int base = 0; base < n_o; base += 32) {
-        const int k = base + lane;
-        const uint32_t j = j1;
-        const uint4 pj = p1;
-        const int tj = t1;
-        j1 = j2;
-        if (k + 64 < n_o) j2 = __ldg(orow + k + 64);
-        if (k + 32 < n_o) {
-            p1 = d.pos[j1];
-            if (need_type) t1 = __ldg(d.type + j1);
+        for (int y = 0; y < MAX_RINGS; ++y)
+            if ((kinds & (1u << (L_R0 + y))) && y < P.nr && P.rings_on && qi != 0.f) want |= 1u << (L_R0 + y);
+        unsigned ljmask = 0;
+        if ((kinds & (1u << L_LJ)) && P.lj_on) {
+            for (int t = 0; t < P.ntypes; ++t) ljmask |= (P.lj[ti * MAX_TYPES + t].on ? 1u : 0u) << t;
+            if (ljmask) want |= 1u << L_LJ;
         }
-        uint32_t m = 0;
-        if (k < n_o) {
-            uint32_t cand = want;
-            if (__uint_as_float(pj.w) == 0.f) cand &= ~RING_BITS;
-            if (need_type && !((ljmask >> tj) & 1u)) cand &= ~(1u << L_LJ);
-            bool fp64 = exact != 0;
-            if (!fp64) {
-                float dx, dy, dz;
-                sdisp(pi, pj, sc, sclo, dx, dy, dz);
-                const float r2 = dx * dx + dy * dy + dz * dz;
-                m = (r2 < r2s ? 1u << L_SHORT : 0u) | (r2 < r2f ? 1u << L_FULL : 0u);
-                const uint16_t t = __ldg(tab + min(SHELL_BINS - 1, int(r2 * invw)));
-                if (!(t & SHELL_AMB)) {
-                    m |= t;
-                } else if (cand & ~((1u << L_SHORT) | (1u << L_FULL))) {
-                    // a shell limit is near this bin: decide in FP32 unless r^2 is
-                    // within 2e-6 (relative) of a limit, far above its FP32 error
-                    bool near = false;
+        const bool need_type = (want >> L_LJ) & 1u;
+        const float r2s = P.r2s, r2f = P.r2f;
+        const uint16_t* tab = d.shell_tab + (size_t)r * SHELL_BINS;
+        const float invw = P.shell_invw;
+        const float sc = P.sclf, sclo = P.sclf_lo;
+        int cnt[NKIND] = {};
+        uint32_t* row[NKIND];
 #pragma unroll
-                    for (int y = 0; y <= MAX_RINGS; ++y) {
-                        const float lo = P.shell_lo2f[y], hi = P.shell_hi2f[y];
-                        near |= fabsf(r2 - lo) <= 2e-6f * lo + 1e-7f || fabsf(r2 - hi) <= 2e-6f * hi + 1e-7f;
-                        if (r2 >= lo && r2 < hi) m |= 1u << (y < MAX_RINGS ? L_R0 + y : L_LJ);
-                    }
-                    if (near) {
-                        fp64 = true;
-                        m &= (1u << L_SHORT) | (1u << L_FULL);
+        for (int kind = 0; kind < NKIND; ++kind)
+            row[kind] = (kinds >> kind) & 1u ? d.list[kind] + (size_t)i * d.lcap[kind] : nullptr;
+        const int n_o = min(d.ocnt[i], d.ocap);
+        const uint32_t* orow = d.olist + (size_t)i * d.ocap;
+        // three batches of 32 candidates in flight: the entries of batch b+2 and
+        // the positions (and types) of batch b+1 load while batch b is filtered
+        uint32_t j1 = lane < n_o ? __ldg(orow + lane) : 0u;
+        uint32_t j2 = lane + 32 < n_o ? __ldg(orow + lane + 32) : 0u;
+        uint4 p1 = lane < n_o ? d.pos[j1] : make_uint4(0, 0, 0, 0);
+        int t1 = (lane < n_o && need_type) ? __ldg(d.type + j1) : 0;
+        for (int base = 0; base < n_o; base += 32) {
+            const int k = base + lane;
+            const uint32_t j = j1;
+            const uint4 pj = p1;
+            const int tj = t1;
+            j1 = j2;
+            if (k + 64 < n_o) j2 = __ldg(orow + k + 64);
+            if (k + 32 < n_o) {
+                p1 = d.pos[j1];
+                if (need_type) t1 = __ldg(d.type + j1);
+            }
+            uint32_t m = 0;
+            if (k < n_o) {
+                uint32_t cand = want;
+                if (__uint_as_float(pj.w) == 0.f) cand &= ~RING_BITS;
+                if (need_type && !((ljmask >> tj) & 1u)) cand &= ~(1u << L_LJ);
+                bool fp64 = exact != 0;
+                if (!fp64) {
+                    float dx, dy, dz;
+                    sdisp(pi, pj, sc, sclo, dx, dy, dz);
+                    const float r2 = dx * dx + dy * dy + dz * dz;
+                    m = (r2 < r2s ? 1u << L_SHORT : 0u) | (r2 < r2f ? 1u << L_FULL : 0u);
+                    if (kinds & ~((1u << L_SHORT) | (1u << L_FULL))) {
+                        const uint16_t t = __ldg(tab + min(SHELL_BINS - 1, int(r2 * invw)));
+                        if (!(t & SHELL_AMB)) {
+                            m |= t;
+                        } else if (cand & ~((1u << L_SHORT) | (1u << L_FULL))) {
+                            // a shell limit is near this bin: decide in FP32 unless r^2 is
+                            // within 2e-6 (relative) of a limit, far above its FP32 error
+                            bool near = false;
+#pragma unroll
+                            for (int y = 0; y <= MAX_RINGS; ++y) {
+                                const float lo = P.shell_lo2f[y], hi = P.shell_hi2f[y];
+                                near |= fabsf(r2 - lo) <= 2e-6f * lo + 1e-7f || fabsf(r2 - hi) <= 2e-6f * hi + 1e-7f;
+                                if (r2 >= lo && r2 < hi) m |= 1u << (y < MAX_RINGS ? L_R0 + y : L_LJ);
+                            }
+                            if (near) {
+                                fp64 = true;
+                                m &= (1u << L_SHORT) | (1u << L_FULL);
+                            }
+                        }
                     }
                 }
-            }
-            if (fp64) {
-                const double r2 = dist2_fp64(d.xb, i, (int)j, P);
-                if (exact) m = (r2 < double(r2s) ? 1u << L_SHORT : 0u) | (r2 < double(r2f) ? 1u << L_FULL : 0u);
+                if (fp64) {
+                    const double r2 = dist2_fp64(d.xb, i, (int)j, P);
+                    if (exact) m = (r2 < double(r2s) ? 1u << L_SHORT : 0u) | (r2 < double(r2f) ? 1u << L_FULL : 0u);
 #pragma unroll
-                for (int y = 0; y <= MAX_RINGS; ++y)
-                    if (r2 >= P.shell_lo2[y] && r2 < P.shell_hi2[y]) m |= 1u << (y < MAX_RINGS ? L_R0 + y : L_LJ);
+                    for (int y = 0; y <= MAX_RINGS; ++y)
+                        if (r2 >= P.shell_lo2[y] && r2 < P.shell_hi2[y]) m |= 1u << (y < MAX_RINGS ? L_R0 + y : L_LJ);
+                }
+                m &= cand;
             }
-            m &= cand;
+            const unsigned below = (1u << lane) - 1u;
+#pragma unroll
+            for (int kind = 0; kind < NKIND; ++kind) {
+                if (!((kinds >> kind) & 1u) || !((want >> kind) & 1u)) continue;   // warp-uniform
+                const bool in = (m >> kind) & 1u;
+                const unsigned b = __ballot_sync(0xffffffffu, in);
+                const int pos = cnt[kind] + __popc(b & below);
+                if (in && pos < d.lcap[kind]) row[kind][pos] = j;
+                cnt[kind] += __popc(b);
+            }
         }
-        const unsigned below = (1u << lane) - 1u;
+        if (lane == 0) {
 #pragma unroll
-        for (int kind = 0; kind < NKIND; ++kind) {
-            if (!((want >> kind) & 1u)) continue;        // warp-uniform: one atom per warp
-            const bool in = (m >> kind) & 1u;
-            const unsigned b = __ballot_sync(0xffffffffu, in);
-            const int pos = cnt[kind] + __popc(b & below);
-            if (in && pos < d.lcap[kind]) d.list[kind][(size_t)i * d.lcap[kind] + pos] = j;
-            cnt[kind] += __popc(b);
+            for (int kind = 0; kind < NKIND; ++kind) {
+                if (!((kinds >> kind) & 1u)) continue;
+                d.lcnt[kind][i] = cnt[kind];
+                if (cnt[kind] > d.lcap[kind]) {
+                    atomicOr(&d.err[r], F_OVERFLOW);
+                    atomicOr(&d.ovf[r], 1u << kind);
+                }
+            }
         }
     }
-    if (lane == 0) {
-#pragma unroll
-        for (int kind = 0; kind < NKIND; ++kind) {
-            if (!(kinds & (1 << kind))) continue;
-            d.lcnt[kind][i] = cnt[kind];
-            if (cnt[kind] > d.lcap[kind]) {
-                atomicOr(&d.err[r], F_OVERFLOW);
-                atomicOr(&d.ovf[r], 1u << kind);
-            }
-        }
+}
+
+// the usual kind sets of the drivers (BAOAB; BAOAB-RESPA1, with the LJ list
+// when the LJ long part is deterministic; the JUMP family; all kinds)
+constexpr uint32_t KM_FULL = 1u << L_FULL;
+constexpr uint32_t KM_RESPA1 = (1u << L_FULL) | (1u << L_SHORT);
+constexpr uint32_t KM_RESPA1_LJ = KM_RESPA1 | (1u << L_LJ);
+constexpr uint32_t KM_JUMP = (1u << L_SHORT) | (((1u << MAX_RINGS) - 1u) << L_R0) | (1u << L_LJ);
+constexpr uint32_t KM_ALL = (1u << NKIND) - 1u;
+
+// warps of a strided launch over the atoms: the resident warps of the GPU,
+// at most one per atom
+int inner_grid(const Dev& d)
+{
+    static int per_sm = 0, sms = 0;
+    if (!per_sm) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_inner_lists<KM_JUMP>, 32 * WARPS, 0);
+        per_sm = std::max(per_sm, 1);
+    }
+    return std::max(1, std::min((d.N + WARPS - 1) / WARPS, sms * per_sm));
+}
+
+void inner_lists(const Dev& d, int kinds, int exact, int late, cudaStream_t s)
+{
+    if (!kinds) return;
+    const int g = inner_grid(d);
+    switch (uint32_t(kinds)) {
+    case KM_FULL: k_inner_lists<KM_FULL><<<g, 32 * WARPS, 0, s>>>(d, kinds, exact, late); break;
+    case KM_RESPA1: k_inner_lists<KM_RESPA1><<<g, 32 * WARPS, 0, s>>>(d, kinds, exact, late); break;
+    case KM_RESPA1_LJ: k_inner_lists<KM_RESPA1_LJ><<<g, 32 * WARPS, 0, s>>>(d, kinds, exact, late); break;
+    case KM_JUMP: k_inner_lists<KM_JUMP><<<g, 32 * WARPS, 0, s>>>(d, kinds, exact, late); break;
+    case KM_ALL: k_inner_lists<KM_ALL><<<g, 32 * WARPS, 0, s>>>(d, kinds, exact, late); break;
+    default: k_inner_lists<0><<<g, 32 * WARPS, 0, s>>>(d, kinds, exact, late); break;
     }
 }
 
@@ -480,8 +535,22 @@ void launch_check(const Dev& d, int force_inner, int force_outer, cudaStream_t s
     k_check<<<blocks(d.N, 256), 256, 0, s>>>(d, force_inner, force_outer);
 }
 
-void launch_rebuild(const Dev& d, int kinds, int exact, int keep_refs, int exact_outer,
-                    int /*max_cells_per_rep*/, cudaStream_t s)
+// blocks of a strided outer-candidate launch: the resident blocks of the GPU,
+// at most one warp per task
+static int outer_grid(long long tasks)
+{
+    static int per_sm = 0, sms = 0;
+    if (!per_sm) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_outer_cells, 32 * OUTER_WARPS, 0);
+        per_sm = std::max(per_sm, 1);
+    }
+    return (int)std::max(1LL, std::min((tasks + OUTER_WARPS - 1) / OUTER_WARPS, (long long)sms * per_sm));
+}
+
+void launch_rebuild_cells(const Dev& d, int keep_refs, int exact_outer, cudaStream_t s)
 {
     k_rehome<<<blocks(d.N, 256), 256, 0, s>>>(d, keep_refs);
     k_cell_scan<<<d.R, 1024, 0, s>>>(d);
@@ -489,14 +558,30 @@ void launch_rebuild(const Dev& d, int kinds, int exact, int keep_refs, int exact
     k_cell_sort<<<blocks(d.total_cells, WARPS), 32 * WARPS, 0, s>>>(d);
     // OUTER_GROUPS warps per cell, each looping over its groups of 32 atoms
     const long long tasks = (long long)d.total_cells * OUTER_GROUPS;
-    k_outer_cells<<<(int)((tasks + OUTER_WARPS - 1) / OUTER_WARPS), 32 * OUTER_WARPS, 0, s>>>(d, exact_outer);
-    if (kinds) k_inner_lists<<<blocks(d.N, WARPS), 32 * WARPS, 0, s>>>(d, kinds, exact, 0);
+    k_outer_cells<<<outer_grid(tasks), 32 * OUTER_WARPS, 0, s>>>(d, exact_outer);
+}
+
+void launch_rebuild_inner(const Dev& d, int kinds, int exact, cudaStream_t s)
+{
+    inner_lists(d, kinds, exact, 0, s);
+}
+
+void launch_rebuild_done(const Dev& d, cudaStream_t s)
+{
     k_flags_clear<<<blocks(d.R, 128), 128, 0, s>>>(d);
+}
+
+void launch_rebuild(const Dev& d, int kinds, int exact, int keep_refs, int exact_outer,
+                    int /*max_cells_per_rep*/, cudaStream_t s)
+{
+    launch_rebuild_cells(d, keep_refs, exact_outer, s);
+    launch_rebuild_inner(d, kinds, exact, s);
+    launch_rebuild_done(d, s);
 }
 
 void launch_late_lists(const Dev& d, int kinds, cudaStream_t s)
 {
-    if (kinds) k_inner_lists<<<blocks(d.N, WARPS), 32 * WARPS, 0, s>>>(d, kinds, 1, 1);
+    inner_lists(d, kinds, 1, 1, s);
 }
 
 }  // namespace mdj

@@ -21,6 +21,8 @@
 
 using namespace mdj;
 
+static_assert(NPROF == MD_PROFILE_CLASSES, "launch classes of md_profile");
+
 namespace {
 
 // ---- host pair terms for the rate bounds (FP64) --------------------------------
@@ -123,6 +125,8 @@ struct md_ctx {
     int tpa_cfg = 0;
     int tpa[6] = {0, 0, 0, 0, 0, 0};
     int vvar = -1;          // chosen variant of the mixed-mode velocity-phase kernel
+    bool tune_log = false;  // report the autotuners' choices on stderr (MDJ_TUNE_LOG)
+    bool fuse_inner = false;      // run the inner steps fused (MDJ_FUSED_INNER; separate launches otherwise)
     Dev d{};
     std::vector<void*> bufs;
     std::vector<RepParams> hp;
@@ -143,6 +147,7 @@ struct md_ctx {
                    long long launches[NPROF]; };
     std::vector<Graph> graphs;
     bool graphs_broken = false;
+    long long ngraph_launches = 0;  // graph replays issued (each replays a chunk of a driver)
     // smooth PME: one pair of cuFFT plans (real to complex, complex to real) per grid size
     struct FftPlan { int K; cufftHandle d2z, z2d; };
     std::vector<FftPlan> fft;
@@ -755,6 +760,80 @@ int commit(md_ctx* ctx)
             return rep[x] != rep[y] ? rep[x] < rep[y] : est[x] > est[y];
         });
     }
+    // blocks of whole bonded groups (connected by bonds and angles) for the
+    // fused inner steps: each group must be a contiguous index range of at
+    // most IB_MAX atoms; groups are packed in index order
+    std::vector<int> ib_start;
+    {
+        std::vector<int> root(N);
+        for (int i = 0; i < N; ++i) root[i] = i;
+        auto find = [&](int a) {
+            while (root[a] != a) { root[a] = root[root[a]]; a = root[a]; }
+            return a;
+        };
+        auto unite = [&](int a, int b) {
+            a = find(a); b = find(b);
+            if (a != b) root[std::max(a, b)] = std::min(a, b);
+        };
+        for (const int2& bij : bond_ij) unite(bij.x, bij.y);
+        for (const int4& an : ang) { unite(an.x, an.y); unite(an.z, an.y); }
+        bool ok = true;
+        int start = 0;
+        ib_start.push_back(0);
+        for (int i = 0; i < N && ok;) {
+            // group of i: the contiguous run of atoms with the same root
+            const int g = find(i);
+            int j = i + 1;
+            while (j < N && find(j) == g) ++j;
+            if (g != i || j - i > IB_MAX) ok = false;          // a group must start its run and fit a block
+            if (j - start > IB_MAX) { ib_start.push_back(i); start = i; }
+            i = j;
+        }
+        // a group that reappears after another one is not contiguous
+        if (ok) {
+            std::vector<int> last(N, -1);
+            for (int i = 0; i < N && ok; ++i) {
+                const int g = find(i);
+                if (last[g] >= 0 && last[g] != i - 1) ok = false;
+                last[g] = i;
+            }
+        }
+        ib_start.push_back(N);
+        if (!ok) ib_start.clear();
+    }
+    // the terms of each block, and the slot of every item's term in its block's list
+    std::vector<int> ib_bond_off, ib_bond, ib_ang_off, ib_ang, item_slot;
+    if (!ib_start.empty()) {
+        const int nb = (int)ib_start.size() - 1;
+        std::vector<int> blk(N);
+        for (int b = 0; b < nb; ++b)
+            for (int i = ib_start[b]; i < ib_start[b + 1]; ++i) blk[i] = b;
+        std::vector<std::vector<int>> bl(nb), al(nb);
+        std::vector<int> bslot(bond_ij.size()), aslot(ang.size());
+        for (int t = 0; t < (int)bond_ij.size(); ++t) {
+            const int b = blk[bond_ij[t].x];
+            bslot[t] = (int)bl[b].size();
+            bl[b].push_back(t);
+        }
+        for (int t = 0; t < (int)ang.size(); ++t) {
+            const int b = blk[ang[t].y];
+            aslot[t] = (int)al[b].size();
+            al[b].push_back(t);
+        }
+        bool fit = true;
+        ib_bond_off.push_back(0);
+        ib_ang_off.push_back(0);
+        for (int b = 0; b < nb; ++b) {
+            fit = fit && (int)bl[b].size() <= IB_TERMS && (int)al[b].size() <= IB_TERMS;
+            ib_bond.insert(ib_bond.end(), bl[b].begin(), bl[b].end());
+            ib_ang.insert(ib_ang.end(), al[b].begin(), al[b].end());
+            ib_bond_off.push_back((int)ib_bond.size());
+            ib_ang_off.push_back((int)ib_ang.size());
+        }
+        for (int i = 0; i < N; ++i)
+            for (const int2& it : items[i]) item_slot.push_back((it.x & 15) == 0 ? bslot[it.y] : aslot[it.y]);
+        if (!fit) ib_start.clear();
+    }
     for (int i = 0; i < N; ++i) {
         bi_off[i + 1] = bi_off[i] + (int)items[i].size();
         for (auto& it : items[i]) bitem.push_back(it);
@@ -793,7 +872,36 @@ int commit(md_ctx* ctx)
     }
     AL(d.flags, 2 * R); AL(d.err, R); AL(d.ovf, R); AL(d.cnt, (size_t)R * NCOUNT); AL(d.energy, 6 * R);
     AL(d.step_base, R); AL(d.stepc, 2 * R);
-    AL(d.vkey, N); AL(d.vhist, (size_t)R * RATE_BUCKETS); AL(d.vofs, (size_t)R * RATE_BUCKETS);
+    AL(d.vkey, N); AL(d.vhist, (size_t)R * RATE_BUCKETS); AL(d.vofs, (size_t)R * RATE_BUCKETS); AL(d.qctr, 1);
+    AL(d.facc, 3 * (size_t)N);
+    {
+        int *dib, *dbo, *dbl, *dao, *dal, *dsl;
+        const bool on = !ib_start.empty();
+        AL(dib, std::max<size_t>(ib_start.size(), 1)); AL(dbo, std::max<size_t>(ib_bond_off.size(), 1));
+        AL(dbl, std::max<size_t>(ib_bond.size(), 1)); AL(dao, std::max<size_t>(ib_ang_off.size(), 1));
+        AL(dal, std::max<size_t>(ib_ang.size(), 1)); AL(dsl, std::max<size_t>(item_slot.size(), 1));
+        if (on && ((rc = upload(ctx, dib, ib_start.data(), ib_start.size())) ||
+                   (rc = upload(ctx, dbo, ib_bond_off.data(), ib_bond_off.size())) ||
+                   (rc = upload(ctx, dbl, ib_bond.data(), ib_bond.size())) ||
+                   (rc = upload(ctx, dao, ib_ang_off.data(), ib_ang_off.size())) ||
+                   (rc = upload(ctx, dal, ib_ang.data(), ib_ang.size())) ||
+                   (rc = upload(ctx, dsl, item_slot.data(), item_slot.size()))))
+            return rc;
+        d.ib_start = dib; d.ib_bond_off = dbo; d.ib_bond = dbl; d.ib_ang_off = dao; d.ib_ang = dal; d.item_slot = dsl;
+        d.n_ib = on ? (int)ib_start.size() - 1 : 0;
+    }
+    d.lj_long_mask = 0;
+    d.lj_symmetric = 1;
+    for (int r = 0; r < R; ++r) {
+        const RepHost& h = ctx->reps[r];
+        if (h.sys.lj_long_mode == 1) d.lj_long_mask |= 1;
+        if (h.sys.lj_long_mode == 2) d.lj_long_mask |= 2;
+        for (int a = 0; a < h.ntypes; ++a)
+            for (int b = 0; b < h.ntypes; ++b)
+                if (h.lj_eps[a * h.ntypes + b] != h.lj_eps[b * h.ntypes + a] ||
+                    h.lj_sig[a * h.ntypes + b] != h.lj_sig[b * h.ntypes + a])
+                    d.lj_symmetric = 0;
+    }
     // smooth PME grids of the Ewald replicas, each part starting on a 512-byte boundary
     ctx->ewald_reps.clear();
     ctx->pme_orders.clear();
@@ -901,6 +1009,7 @@ int commit(md_ctx* ctx)
     CK(cudaMemsetAsync(d.err, 0, sizeof(uint32_t) * R, ctx->s));
     CK(cudaMemsetAsync(d.ovf, 0, sizeof(uint32_t) * R, ctx->s));
     CK(cudaMemsetAsync(d.vhist, 0, sizeof(int) * R * RATE_BUCKETS, ctx->s));
+    CK(cudaMemsetAsync(d.facc, 0, sizeof(long long) * 3 * (size_t)N, ctx->s));
     ctx->on_device = true;
     // initial build at the stored reference positions
     launch_check(d, 1, 1, ctx->s);
@@ -1002,13 +1111,25 @@ int tpa_for(md_ctx* ctx, int mode)
     if (ctx->fp64) return 1;
     if (ctx->tpa_cfg > 0) return ctx->tpa_cfg;
     if (ctx->tpa[mode]) return ctx->tpa[mode];
-    // autotune: time each width on the current lists (results do not depend on it)
+    if (const char* env = std::getenv("MDJ_FORCE_VARIANT")) {
+        // a fixed kernel choice (tests): threads per atom, | 16 for the half-list kernels
+        int t = std::atoi(env);
+        if (!force_half_ok(ctx->d, mode)) t &= ~FORCE_HALF;
+        const int w = t & ~FORCE_HALF;
+        ctx->tpa[mode] = (w == 1 || w == 2 || w == 4 || w == 8) ? t : 1;
+        return ctx->tpa[mode];
+    }
+    // autotune: time each width, with the full and (where allowed) the
+    // half-list kernels, on the current lists (results do not depend on it)
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
     int pick = 1;
-    for (int t : {1, 2, 4, 8}) {
+    std::vector<int> cands = {1, 2, 4, 8};
+    if (force_half_ok(ctx->d, mode))
+        for (int t : {1, 2, 4, 8}) cands.push_back(t | FORCE_HALF);
+    for (int t : cands) {
         launch_force(ctx->d, mode, ctx->d.gout, 1, 0, t, ctx->s);
         cudaEventRecord(e0, ctx->s);
         for (int k = 0; k < 5; ++k) launch_force(ctx->d, mode, ctx->d.gout, 1, 0, t, ctx->s);
@@ -1021,6 +1142,9 @@ int tpa_for(md_ctx* ctx, int mode)
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     ctx->tpa[mode] = pick;
+    if (ctx->tune_log)
+        std::fprintf(stderr, "mdjump tune: gradient mode %d: %d threads per atom%s (%.4f ms for 5 evaluations)\n", mode,
+                     pick & ~FORCE_HALF, (pick & FORCE_HALF) ? ", half list" : "", best);
     return pick;
 }
 
@@ -1086,7 +1210,8 @@ void force_into(md_ctx* ctx, int mode, double* out, int as_grad)
     } else {
         const int t = mode == 1 ? 1 : tpa_for(ctx, mode);
         const bool bonded = mode == 0 || mode == 1 || mode == 5;
-        Prof p(ctx, mode == 1 ? 1 : 0, (bonded && ctx->d.nbond + ctx->d.nang > 0) ? 2 : 1);
+        const bool half = !ctx->fp64 && (t & FORCE_HALF) && force_half_ok(ctx->d, mode);
+        Prof p(ctx, mode == 1 ? 1 : 0, ((bonded && ctx->d.nbond + ctx->d.nang > 0) ? 2 : 1) + (half ? 1 : 0));
         launch_force(ctx->d, mode, out, as_grad, ctx->fp64, t, ctx->s);
     }
     if (mode_has_recip(ctx, mode)) {
@@ -1107,8 +1232,16 @@ int take_deferred(md_ctx* ctx)
 
 void rebuild_step(md_ctx* ctx)
 {
-    Prof p(ctx, 4, ctx->kinds ? 7 : 6);
-    launch_rebuild(ctx->d, ctx->kinds, ctx->fp64, 0, ctx->fp64, 0, ctx->s);
+    {
+        Prof p(ctx, 4, 5);
+        launch_rebuild_cells(ctx->d, 0, ctx->fp64, ctx->s);
+    }
+    if (ctx->kinds) {
+        Prof p(ctx, 7, 1);
+        launch_rebuild_inner(ctx->d, ctx->kinds, ctx->fp64, ctx->s);
+    }
+    Prof p(ctx, 4, 1);
+    launch_rebuild_done(ctx->d, ctx->s);
 }
 
 void kick(md_ctx* ctx, const double* a, double h)
@@ -1172,7 +1305,7 @@ int tune_vphase(md_ctx* ctx, const double* a, double tau2)
             cudaEventElapsedTime(&ms, e0, e1);
             if (rep) tmin = std::min(tmin, ms);
         }
-        const int g = v >= NVPHASE_VARIANTS;
+        const int g = vphase_sorted(v) ? 0 : 1;
         if (tmin < best[g]) { best[g] = tmin; pick[g] = v; }
     }
     const int pick_v = best[1] < 0.98f * best[0] ? pick[1] : pick[0];
@@ -1185,16 +1318,26 @@ int tune_vphase(md_ctx* ctx, const double* a, double tau2)
     CK(cudaStreamSynchronize(ctx->s));
     for (void* p : {(void*)vs, (void*)cs, (void*)evs, (void*)es}) dfree(ctx, p);
     ctx->vvar = pick_v;
+    if (ctx->tune_log)
+        std::fprintf(stderr, "mdjump tune: velocity phase variant %d (%s, %s, occupancy %d): best rate-ordered %.4f ms, "
+                     "best set-up order %.4f ms\n", pick_v, vphase_queue(pick_v) ? "queue" : "thread per atom",
+                     vphase_sorted(pick_v) ? "rate order" : "set-up order", pick_v % NVPHASE_VARIANTS, best[0], best[1]);
     return MD_OK;
 }
 
 void vphase(md_ctx* ctx, const double* a, double tau2, uint32_t s_off, int half, int order, uint32_t s_off2 = 0)
 {
     if (ctx->vvar < 0) tune_vphase(ctx, a, tau2);
-    // mixed: rate order (3 kernels, unless the variant skips it) + the velocity-phase kernel
-    Prof p(ctx, 2, ctx->fp64 ? 1 : (ctx->vvar >= NVPHASE_VARIANTS ? 1 : 4));
-    launch_vphase(ctx->d, a, tau2, s_off, half, order, 1, 1, ctx->fp64, ctx->vvar < 0 ? 0 : ctx->vvar, ctx->s,
-                  s_off2, single_params(ctx));
+    const int var = ctx->vvar < 0 ? 0 : ctx->vvar;
+    // mixed: the rate order (3 kernels, unless the variant keeps the set-up order), then the phase kernel
+    const bool sort = !ctx->fp64 && vphase_sorted(var);
+    if (sort) {
+        Prof p(ctx, 8, 3);
+        launch_rate_order(ctx->d, a, tau2 * (order == 2 ? 2 : 1), ctx->s);
+    }
+    Prof p(ctx, 2, 1);
+    launch_vphase(ctx->d, a, tau2, s_off, half, order, 1, 1, ctx->fp64, var, ctx->s, s_off2, single_params(ctx),
+                  sort ? 1 : 0);
 }
 
 int set_stepc(md_ctx* ctx, double tau)
@@ -1237,6 +1380,10 @@ int finish(md_ctx* ctx, long long inner_steps)
             if (m & (1u << b)) which += std::string(which.empty() ? "" : ", ") + names[b];
         if (m & OVF_OUTER) which += std::string(which.empty() ? "" : ", ") + "outer";
         if (m & OVF_CELL) which += std::string(which.empty() ? "" : ", ") + "cell";
+        if (m & OVF_FIX)
+            FAIL(MD_EOVERFLOW, "a pair force term left the range of the 64-bit fixed-point sums "
+                               "(|component| >= 2^20 kcal/mol/A, or not finite)%s%s",
+                 which.empty() ? "" : "; capacity exceeded too: ", which.c_str());
         FAIL(MD_EOVERFLOW, "capacity exceeded: %s (lists are sized at set-up; an unstable run "
                            "packs atoms denser than that)", which.c_str());
     }
@@ -1263,23 +1410,22 @@ void drop_graphs(md_ctx* ctx)
 
 // Runs `units` units of a driver (a step, or a RESPA cycle of spu inner
 // steps). body(u0, n) issues n units whose random streams are offset from
-// the replicas' step bases by u0 units. With graphs on, the first unit runs
-// as plain launches (it runs the autotuners, which time real launches) and
-// advances the step bases; then chunks of G units replay a graph captured
-// once (the chunk at offset 0, then the step bases advanced by G units);
-// the rest runs plainly at offset 0 and finish() advances the step bases
-// past it. The streams, and so the results, are those of a plain run.
+// the replicas' step bases by u0 units. With graphs on, chunks of G units
+// (about four innermost steps) replay a graph captured once per time step,
+// driver and device layout. The first call of a kind runs its first unit as
+// plain launches (it runs the autotuners, which time real launches) and
+// advances the step bases, then captures the chunk (at offset 0, with the
+// step bases advanced by G units inside it); later calls, such as the timed
+// steps after a warm-up, replay it from their first unit on. What is left
+// runs plainly at offset 0 and finish() advances the step bases past it. The
+// streams, and so the results, are those of a plain run.
 template <typename Body>
 int run_units(md_ctx* ctx, int key, double tau, int spu, long long units, Body body)
 {
     Dev& d = ctx->d;
-    const long long G = std::max(1, 16 / spu);
+    const long long G = std::max(1, 4 / spu);
     long long done = 0;
-    if (!ctx->cfg.no_graphs && !ctx->prof && !ctx->graphs_broken && units >= 2 * G + 1) {
-        body(0, 1);
-        launch_advance(d, spu, ctx->s);
-        ctx->nlaunch[5] += 1;
-        done = 1;
+    if (!ctx->cfg.no_graphs && !ctx->prof && !ctx->graphs_broken && units >= G) {
         // graphs of an older device layout can never replay again: release them
         // (every earlier call ended with a synchronisation; the private stream is idle)
         for (size_t k = 0; k < ctx->graphs.size();) {
@@ -1293,7 +1439,11 @@ int run_units(md_ctx* ctx, int key, double tau, int spu, long long units, Body b
         const md_ctx::Graph* g = nullptr;
         for (const auto& x : ctx->graphs)
             if (x.gen == ctx->gen && x.key == key && x.tau == tau && x.n_inner == spu && x.units == G) g = &x;
-        if (!g) {
+        if (!g && units >= G + 1) {
+            body(0, 1);
+            launch_advance(d, spu, ctx->s);
+            ctx->nlaunch[5] += 1;
+            done = 1;
             if (!ctx->gs) CK(cudaStreamCreateWithFlags(&ctx->gs, cudaStreamNonBlocking));
             // capture on the private stream (the caller's may be the legacy default stream)
             cudaEvent_t e = take_event(ctx);
@@ -1336,6 +1486,7 @@ int run_units(md_ctx* ctx, int key, double tau, int spu, long long units, Body b
             while (units - done >= G) {
                 CK(cudaGraphLaunch(g->exec, ctx->gs));
                 for (int c = 0; c < NPROF; ++c) ctx->nlaunch[c] += g->launches[c];
+                ctx->ngraph_launches += 1;
                 done += G;
             }
             CK(cudaEventRecord(e, ctx->gs));
@@ -1366,6 +1517,22 @@ void inner_bonded(md_ctx* ctx, double dt, uint32_t s_off, int check)
     kick(ctx, d.ab, 0.5 * dt);
 }
 
+// n inner steps from s_off: fused into one launch when the bonded groups
+// allow it and no velocity record needs the steps one by one; the list check
+// runs on the last step
+void inner_steps(md_ctx* ctx, double dt, uint32_t s_off, int n)
+{
+    if (ctx->d.n_ib > 0 && !ctx->vr && ctx->fuse_inner) {
+        Prof p(ctx, 3, 1);
+        launch_inner_steps(ctx->d, dt, s_off, n, 1, ctx->fp64, ctx->s);
+        return;
+    }
+    for (int k = 0; k < n; ++k) {
+        inner_bonded(ctx, dt, s_off + uint32_t(k), k == n - 1);
+        if (k < n - 1) record(ctx, s_off + uint32_t(k));
+    }
+}
+
 }  // namespace
 
 // ============================================================================
@@ -1389,6 +1556,8 @@ int md_init(md_ctx** out, const md_config* cfg)
     ctx->s = (cudaStream_t)cfg->cuda_stream;
     ctx->fp64 = cfg->precision == MD_FP64;
     ctx->tpa_cfg = cfg->threads_per_atom;
+    ctx->fuse_inner = std::getenv("MDJ_FUSED_INNER") != nullptr;
+    ctx->tune_log = std::getenv("MDJ_TUNE_LOG") != nullptr;
     ctx->reps.resize(cfg->max_replicas);
     bool ok = cudaMallocHost((void**)&ctx->h_stepc, sizeof(double) * 2 * cfg->max_replicas) == cudaSuccess;
     if (ok && cudaMallocHost((void**)&ctx->h_err, sizeof(uint32_t) * cfg->max_replicas) != cudaSuccess) {
@@ -1581,10 +1750,8 @@ int md_step_baoab_respa(md_ctx* ctx, int64_t n_outer, double dt_inner_fs, int n_
         uint32_t s = uint32_t(u0 * n_inner);
         for (long long o = 0; o < n; ++o) {
             kick(ctx, d.al, 0.5 * D);
-            for (int k = 0; k < n_inner; ++k, ++s) {
-                inner_bonded(ctx, dt, s, k == n_inner - 1);
-                if (k < n_inner - 1) record(ctx, s);
-            }
+            inner_steps(ctx, dt, s, n_inner);
+            s += n_inner;
             rebuild_step(ctx);
             force(ctx, 2, d.al);
             kick(ctx, d.al, 0.5 * D);
@@ -1611,10 +1778,8 @@ int md_step_baoab_respa1(md_ctx* ctx, int64_t n_outer, double dt_inner_fs, int m
             kick(ctx, d.al, 0.5 * D);
             for (int j = 0; j < n_outer_ratio; ++j) {
                 kick(ctx, d.as, 0.5 * kap);
-                for (int k = 0; k < m_mid; ++k, ++s) {
-                    inner_bonded(ctx, dt, s, k == m_mid - 1);
-                    if (k < m_mid - 1) record(ctx, s);
-                }
+                inner_steps(ctx, dt, s, m_mid);
+                s += m_mid;
                 rebuild_step(ctx);
                 force(ctx, 3, d.as);
                 kick(ctx, d.as, 0.5 * kap);
@@ -1657,10 +1822,8 @@ static int jump_respa_cycles(md_ctx* ctx, int64_t n_outer, double dt_inner_fs, i
                 const bool carried = fuse && (ew ? j > 0 : o > 0);
                 const bool pass_on = fuse && (ew ? j + 1 < per : o + 1 < n);
                 if (!carried) vphase(ctx, d.as, 0.5 * kap, s0, 0, 0);
-                for (int k = 0; k < n_inner; ++k, ++s) {
-                    inner_bonded(ctx, dt, s, k == n_inner - 1);
-                    if (k < n_inner - 1) record(ctx, s);
-                }
+                inner_steps(ctx, dt, s, n_inner);
+                s += n_inner;
                 rebuild_step(ctx);
                 force(ctx, 3, d.as);
                 if (pass_on) vphase(ctx, d.as, 0.5 * kap, s0, 1, 2, s);
@@ -1783,10 +1946,16 @@ int md_run_phase(md_ctx* ctx, int phase, double tau2_ps, int64_t s0, int half, i
     Dev& d = ctx->d;
     if (phase == 0) force(ctx, accel_mode, d.a0);
     {
-        // phase 0: rate order (3, unless the variant skips it) + C'; phase 1: J' only
-        Prof p(ctx, 2, (ctx->fp64 || phase == 1 || ctx->vvar >= NVPHASE_VARIANTS) ? 1 : 4);
+        // phase 0: rate order (3 kernels, unless the variant keeps the set-up order), then C'; phase 1: J' only
+        const int var = ctx->vvar < 0 ? 0 : ctx->vvar;
+        const bool sort = !ctx->fp64 && phase == 0 && vphase_sorted(var);
+        if (sort) {
+            Prof p(ctx, 8, 3);
+            launch_rate_order(d, d.a0, tau2_ps, ctx->s);
+        }
+        Prof p(ctx, 2, 1);
         launch_vphase_abs(d, phase == 0 ? d.a0 : nullptr, tau2_ps, uint32_t(s0), half, 0, phase == 0, phase == 1,
-                          ctx->fp64, ctx->vvar < 0 ? 0 : ctx->vvar, ctx->s, single_params(ctx));
+                          ctx->fp64, var, ctx->s, single_params(ctx), sort ? 1 : 0);
     }
     CK(cudaGetLastError());
     if ((rc = take_deferred(ctx))) return rc;

@@ -26,8 +26,8 @@ using namespace mdj;
 
 constexpr int NA_MAX_ATOMS = MD_NOALLOC_MAX_ATOMS;
 constexpr int NA_MAX_CELLS = MD_NOALLOC_MAX_CELLS;
-// layout (ints): count[C] | cursor[C] | start[C + 1] | atoms[N] | cell of atom[N]
-constexpr size_t NA_INTS = 3 * (size_t)NA_MAX_CELLS + 1 + 2 * (size_t)NA_MAX_ATOMS;
+// layout (ints): count[C] | cursor[C] | start[C + 1] | atoms[N] | cell of atom[N] | fill[N]
+constexpr size_t NA_INTS = 3 * (size_t)NA_MAX_CELLS + 1 + 3 * (size_t)NA_MAX_ATOMS;
 
 static __device__ __align__(256) int g_na_scratch[NA_INTS];
 
@@ -41,7 +41,7 @@ struct NaParams {
 };
 
 struct Scratch {
-    int *count, *cursor, *start, *atoms, *cell;
+    int *count, *cursor, *start, *atoms, *cell, *fill;
 };
 
 __device__ __forceinline__ Scratch view(int* base)
@@ -52,6 +52,7 @@ __device__ __forceinline__ Scratch view(int* base)
     s.start = base + 2 * NA_MAX_CELLS;
     s.atoms = base + 3 * NA_MAX_CELLS + 1;
     s.cell = s.atoms + NA_MAX_ATOMS;
+    s.fill = s.cell + NA_MAX_ATOMS;
     return s;
 }
 
@@ -119,13 +120,30 @@ __global__ void k_na_scan(int* base, int ncell)
     if (threadIdx.x == 0) s.start[ncell] = carry;
 }
 
+// atoms into their cells' ranges of `fill`, in the order the atomics give
 __global__ void k_na_fill(int* base, int n)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const Scratch s = view(base);
     const int c = s.cell[i];
-    s.atoms[s.start[c] + atomicAdd(&s.cursor[c], 1)] = i;
+    s.fill[s.start[c] + atomicAdd(&s.cursor[c], 1)] = i;
+}
+
+// one warp per cell: the cell's atoms into `atoms` in increasing index (rank
+// sort), so that every call sums the pairs of an atom in the same order
+__global__ void k_na_sort(int* base, int ncell)
+{
+    const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (c >= ncell) return;
+    const Scratch s = view(base);
+    const int b = s.start[c], n = s.start[c + 1] - b;
+    for (int k = lane; k < n; k += 32) {
+        const int v = s.fill[b + k];
+        int rank = 0;
+        for (int m = 0; m < n; ++m) rank += s.fill[b + m] < v;
+        s.atoms[b + rank] = v;
+    }
 }
 
 // pair gradient of atom i over the 27 (or fewer, unique) neighbour cells
@@ -270,6 +288,7 @@ extern "C" int md_nb_gradient_noalloc(const double* d_x, const double* d_charge,
     k_na_count<<<nb, 128, 0, s>>>(d_x, scratch, p);
     k_na_scan<<<1, 1024, 0, s>>>(scratch, p.ncell);
     k_na_fill<<<nb, 128, 0, s>>>(scratch, n_atoms);
+    k_na_sort<<<(p.ncell + 3) / 4, 128, 0, s>>>(scratch, p.ncell);
     k_na_force<<<nb, 128, 0, s>>>(d_x, d_charge, d_type, d_mol, scratch, p, d_grad);
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(MD_ECUDA, cudaGetErrorString(e));

@@ -172,9 +172,10 @@ def water_with_beads(n_total: int = 1_000_000, n_beads: int = 50_002, seed: int 
                      box: float | None = None) -> System:
     """Water with an embedded dense sphere of charged LJ beads.
 
-    The beads (half +bead_q, half -bead_q) fill a sphere at reduced density
-    rho sigma^3 = bead_rho_sigma3 at the box centre on a jittered cubic
-    lattice; water molecules fill the rest of the box at liquid density. LJ
+    The beads (half +bead_q, half -bead_q, in rock-salt order on their lattice)
+    fill a sphere at reduced density rho sigma^3 = bead_rho_sigma3 at the box
+    centre on a jittered cubic lattice; water molecules fill the rest of the
+    box at liquid density. LJ
     cross terms use Lorentz-Berthelot mixing with the water oxygen.
     """
     n_mol = (n_total - n_beads) // 3
@@ -188,9 +189,9 @@ def water_with_beads(n_total: int = 1_000_000, n_beads: int = 50_002, seed: int 
     # beads: jittered cubic lattice inside the sphere
     a_b = rho_b ** (-1.0 / 3.0)
     k = int(math.ceil(2 * r_b / a_b)) + 2
-    g = (np.stack(np.meshgrid(*[np.arange(-k // 2, k // 2 + 1)] * 3, indexing="ij"), -1)
-         .reshape(-1, 3) * a_b)
-    g = g[np.argsort((g * g).sum(1), kind="stable")][:n_beads]
+    lat = np.stack(np.meshgrid(*[np.arange(-k // 2, k // 2 + 1)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    lat = lat[np.argsort((lat * lat).sum(1), kind="stable")][:n_beads]
+    g = lat * a_b
     xb = centre + g + rng.uniform(-0.05, 0.05, size=g.shape) * a_b
     # water: a lattice over the box slightly denser than the liquid; sites
     # inside the bead sphere (+ margin) are removed and n_mol of the rest kept
@@ -210,7 +211,13 @@ def water_with_beads(n_total: int = 1_000_000, n_beads: int = 50_002, seed: int 
     n_w = xw.shape[0]
     x = np.concatenate([xw, xb % box])
     mass = np.concatenate([w.mass[atoms], np.full(n_beads, bead_mass)])
-    qb = np.where(np.arange(n_beads) % 2 == 0, bead_q, -bead_q)
+    # rock-salt order on the bead lattice (nearest neighbours of opposite
+    # sign), balanced by flipping the outermost beads of the larger sign
+    qb = np.where(lat.sum(1) % 2 == 0, bead_q, -bead_q)
+    excess = int((qb > 0).sum() - (qb < 0).sum())
+    if excess:
+        big = np.flatnonzero(qb > 0 if excess > 0 else qb < 0)
+        qb[big[-(abs(excess) // 2):]] *= -1.0
     charge = np.concatenate([w.charge[atoms], qb])
     typ = np.concatenate([w.type[atoms], np.full(n_beads, 2, dtype=np.int32)]).astype(np.int32)
     eo, so = w.lj_eps[0, 0], w.lj_sigma[0, 0]

@@ -116,3 +116,23 @@ def test_binding_marshals_the_system_and_checks_sizes():
     e.set_state(0, w.x, w.v)
     with pytest.raises(ValueError, match="v has"):
         e.set_state(0, w.x, w.v[:3])
+
+
+def test_noalloc_rejects_oversized_inputs_before_any_device_call(libpath):
+    """md_nb_gradient_noalloc checks its scratch limits on the host: too many
+    atoms, or a box / r_cut ratio that needs more cells than the static
+    array holds, is refused with MD_EINVAL before any pointer is read."""
+    import numpy as np
+    import paper_2412_15073_gb300 as M
+    L = M.load_library(libpath)
+    one = np.zeros(8)
+    p = M._ptr(one)
+    # 200,000 atoms: above MD_NOALLOC_MAX_ATOMS
+    assert L.md_nb_gradient_noalloc(p, p, p, None, 200_000, 1000.0, 1, p, p, 9.0, 5.0, 0.5, 0.2, 0, p, None) == -1
+    assert b"MD_NOALLOC_MAX_ATOMS" in L.md_last_error(None)
+    # 10 atoms in a 330 A box at r_cut 9 A: 36^3 = 46,656 cells, above MD_NOALLOC_MAX_CELLS
+    assert L.md_nb_gradient_noalloc(p, p, p, None, 10, 330.0, 1, p, p, 9.0, 5.0, 0.5, 0.2, 0, p, None) == -1
+    assert b"MD_NOALLOC_MAX_CELLS" in L.md_last_error(None)
+    # an unknown weight is refused as well
+    assert L.md_nb_gradient_noalloc(p, p, p, None, 10, 100.0, 1, p, p, 9.0, 5.0, 0.5, 0.2, 3, p, None) == -1
+    assert b"weight" in L.md_last_error(None)

@@ -68,13 +68,33 @@ def test_gradients(M, oracle_mod, water648, precision, tol):
     assert max(errs.values()) <= tol, errs
 
 
-def test_fixed_point_forces_do_not_depend_on_threads_per_atom(M, oracle_mod, water648):
+def test_fixed_point_forces_do_not_depend_on_threads_per_atom(M, oracle_mod, water648, monkeypatch):
+    """Mixed mode: the pair gradients are the same bits for every number of
+    threads per atom, and for the half-list kernels (each unique pair once,
+    both atoms served by integer atomics) as for the full-list ones: gradient
+    modes 0, 2, 3, 4 and 5, and with the LJ long part deterministic at the slow
+    level (lj_long_mode 2, where mode 3 may run half and mode 5 may not)."""
     gs = []
     for tpa in (1, 2, 4, 8):
         e, _ = make(M, oracle_mod, water648, 1, tpa=tpa)
-        gs.append(np.stack([e.gradient(0), e.gradient(5)]))
-    for g in gs[1:]:
-        assert np.array_equal(g, gs[0])
+        gs.append(np.stack([e.gradient(m) for m in (0, 2, 3, 4, 5)]))
+    for var in (17, 18, 20, 24):
+        monkeypatch.setenv("MDJ_FORCE_VARIANT", str(var))
+        e, _ = make(M, oracle_mod, water648, 1)
+        gs.append(np.stack([e.gradient(m) for m in (0, 2, 3, 4, 5)]))
+        e.close()
+    for k, g in enumerate(gs[1:]):
+        assert np.array_equal(g, gs[0]), k
+    ref2 = None
+    for var in (2, 20):
+        monkeypatch.setenv("MDJ_FORCE_VARIANT", str(var))
+        e, _ = make(M, oracle_mod, water648, 1, lj_long_mode=2)
+        g = np.stack([e.gradient(m) for m in (0, 3, 4, 5, 6)])
+        e.close()
+        if ref2 is None:
+            ref2 = g
+        else:
+            assert np.array_equal(g, ref2)
 
 
 RINGS = [None, [], [4.8, 6.0, 7.5]]     # rings of r_mid (two), one ring, four rings
@@ -137,6 +157,32 @@ def test_multiple_time_step_family_fp64(M, oracle_mod, water648, how):
     assert e.observables()["step"] == o.step
     assert pos_err(xg, xo, water648.box) < 1e-6, how
     assert np.abs(vg - vo).max() < 1e-5, how
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_fused_inner_steps_equal_separate_launches(M, oracle_mod, water648, monkeypatch, precision):
+    """The inner steps of the multiple-time-step drivers run fused (one launch
+    for all inner steps of a cycle, blocks of whole molecules): the same bits
+    as the separate kick, A-O-A and bonded launches, for the four drivers."""
+    runs = {"baoab_respa": (12, 1.0, 2), "baoab_respa1": (5, 1.0, 2, 3), "jump_respa": (12, 1.0, 3),
+            "jump_respa1": (5, 1.0, 2, 2)}
+    for how, args in runs.items():
+        got = []
+        for fused in (True, False):
+            if fused:
+                monkeypatch.setenv("MDJ_FUSED_INNER", "1")
+            else:
+                monkeypatch.delenv("MDJ_FUSED_INNER", raising=False)
+            e, _ = make(M, oracle_mod, water648, precision, seed=14)
+            getattr(e, how)(*args)
+            x, v, img, xb = e.state()
+            ob = e.observables()
+            got.append((x, v, img, xb, ob["list_rebuilds"], ob["step"]))
+            e.close()
+        a, b = got
+        for k in range(4):
+            assert np.array_equal(a[k], b[k]), (how, k)
+        assert a[4:] == b[4:], how
 
 
 def test_jump_mixed_precision_tracks_oracle(M, oracle_mod, water648):
@@ -339,18 +385,39 @@ def test_failures_are_reported_as_status(M, water648):
 
 def test_velocity_phase_variants_are_identical(M, oracle_mod, water648, monkeypatch):
     """The launch variants the autotuner chooses between (four occupancy
-    targets, with or without the rate ordering) compute the same values bit
-    for bit (mixed mode, 20 JUMP steps)."""
+    targets, with or without the rate ordering, one thread per atom or lanes
+    fed from a queue of atoms) compute the same values bit for bit (mixed
+    mode, 20 JUMP steps), on one system and on a batch of three replicas
+    (where the queue kernel moves lanes between replicas)."""
+    from paper_2412_15073_gb300 import systems
     ref = None
-    for var in range(8):
+    for var in range(16):
         monkeypatch.setenv("MDJ_VPHASE_VARIANT", str(var))
         e, _ = make(M, oracle_mod, water648, 1, seed=12)
         e.jump(20)
         x, v, _, _ = e.state()
+        ob = e.observables()
+        got = (x, v, ob["jump_proposals"], ob["jump_accepts"], ob["bps_proposals"])
         if ref is None:
-            ref = (x, v)
+            ref = got
         else:
-            assert np.array_equal(x, ref[0]) and np.array_equal(v, ref[1]), var
+            assert np.array_equal(x, ref[0]) and np.array_equal(v, ref[1]) and got[2:] == ref[2:], var
+        e.close()
+    syss = [systems.water_box(n, seed=20 + k) for k, n in enumerate([216, 343, 250])]
+    refb = None
+    for var in (0, 4, 8, 9, 12):
+        monkeypatch.setenv("MDJ_VPHASE_VARIANT", str(var))
+        e = M.Engine(precision=1, seed=13, max_replicas=3)
+        for r, s in enumerate(syss):
+            e.set_system(r, s, **PARAMS)
+        e.jump(15)
+        got = [e.state(r)[1] for r in range(3)] + [e.observables(r)["jump_proposals"] for r in range(3)]
+        if refb is None:
+            refb = got
+        else:
+            for r in range(3):
+                assert np.array_equal(got[r], refb[r]), (var, r)
+            assert got[3:] == refb[3:], var
         e.close()
 
 
@@ -455,41 +522,77 @@ def test_million_atom_heterogeneous_sampled(M, oracle_mod):
     e.close()
 
 
-def test_benchmark_workload_sampled(M, oracle_mod):
-    """The benchmark workload itself (96,000-atom water, 98.6 A, DSF, r_E
-    10 A, rings at 5.25 / 6 / 7.5 A, 0.3 A skin) in the benchmark's mixed
-    precision: full and F0 gradients of 40 sampled atoms within 1e-5 of the
-    oracle's, and one C' phase of 200 sampled atoms (oracle with per-atom
-    lists)."""
+@pytest.mark.parametrize("workload", ["dsf_jump", "ewald_jump_respa1"])
+def test_benchmark_workloads_sampled(M, oracle_mod, workload):
+    """The benchmark workloads themselves (96,000-atom water, 98.6 A, with the
+    benchmark's list settings): the DSF JUMP step (r_E 10 A, rings at 5.25 / 6
+    / 7.5 A, 0.3 A skin) and the Ewald JUMP-RESPA1 cycle of the headline
+    (a 0.42/A, PME order 6 on 125^3, r_c 6 A, one ring, LJ long part at the
+    slow level). Gradients of 40 sampled atoms (F0 and full, or the short
+    part and the slow level) within 1e-12 of the oracle's in FP64 and 1e-5 in
+    mixed precision; one C' phase of 200 sampled atoms: in FP64 the accepted
+    jumps are the oracle's and the velocities agree to 1e-10, in mixed
+    precision at most one atom of the 200 ends differently (a decision flipped
+    by FP32 rounding; about none are expected) and the count is printed.
+    The oracle builds lists per atom (its O(N^2) build is out of reach here)."""
     import bench
     from paper_2412_15073_gb300 import systems
     w = systems.water_box(bench.N_MOL, box=bench.BOX, seed=0)
-    p = dict(bench.JUMP_PARAMS)
-    e = M.Engine(precision=1, seed=6)
-    e.set_system(0, w, **p)
+    ewald = workload == "ewald_jump_respa1"
+    p = dict(bench.EW_JUMP if ewald else bench.DSF_JUMP)
     o = oracle_mod.Oracle(w, seed=6, replica=0, lazy_lists=True, **p)
     rng = np.random.default_rng(8)
     idx = rng.choice(w.n, 40, replace=False)
-    tot = e.gradient(0)
-    rms = np.sqrt((tot * tot).sum(1).mean())
-    for mode in (0, 5):
-        g = tot if mode == 0 else e.gradient(mode)
-        for i in idx:
-            ref = o.gradient_atom(mode, int(i))
-            den = max(np.linalg.norm(tot[i]), 0.01 * rms)
-            assert np.linalg.norm(g[i] - ref) / den <= 1e-5, (mode, i)
+    phase_atoms = rng.choice(w.n, 200, replace=False)
+    modes = (3, 6) if ewald else (0, 5)
+    accel = M.GRAD_NB_SHORT if ewald else M.GRAD_F0
+    tau2, s0, half = (0.001, 21, 0) if ewald else (0.0005, 17, 1)
+    recip = None
+    if ewald:
+        # the slow level = the (1 - chi) LJ part (an oracle without Ewald gives it alone)
+        # + the reciprocal part, computed once for all atoms
+        o_lj = oracle_mod.Oracle(w, seed=6, replica=0, lazy_lists=True, **(p | {"coulomb_mode": 0}))
+        recip = o.ewald_recip_pme()[0]
+
+    def ref_grad(mode, i):
+        if mode == 6:
+            return o_lj.gradient_atom(6, int(i)) + recip[i]
+        return o.gradient_atom(mode, int(i))
+
+    refs = {mode: {int(i): ref_grad(mode, i) for i in idx} for mode in modes}
+    o.events_enable(1 << 20)
     mt = w.mass / 418.4
-    tau2 = 0.0005
-    e.run_phase(0, tau2, s0=17, half=1, accel_mode=M.GRAD_F0)
-    vg = e.state()[1]
-    good = 0
-    for i in rng.choice(w.n, 200, replace=False):
-        a = -o.gradient_atom(oracle_mod.GRAD_F0, int(i)) / mt[i]
-        vo, _, _ = o.cprime_one(int(i), w.v[i], a, tau2, 17, 1)
-        good += np.abs(vg[i] - vo).max() <= 2e-5 * max(np.abs(vo).max(), 1.0)
-    assert good >= 194, good
-    assert e.observables()["error_flags"] == 0
-    e.close()
+    vo = {}
+    for i in phase_atoms:
+        a = -o.gradient_atom(int(accel), int(i)) / mt[i]
+        vo[int(i)] = o.cprime_one(int(i), w.v[i], a, tau2, s0, half)[0]
+    ev_o = {tuple(r) for r in o.events().tolist()}
+    for precision, tol in ((0, 1e-12), (1, 1e-5)):
+        e = M.Engine(precision=precision, seed=6, event_log_cap=1 << 22)
+        e.set_system(0, w, **p)
+        tot = e.gradient(0)
+        rms = np.sqrt((tot * tot).sum(1).mean())
+        for mode in modes:
+            g = tot if mode == 0 else e.gradient(mode)
+            for i in idx:
+                den = max(np.linalg.norm(tot[i]), 0.01 * rms)
+                err = np.linalg.norm(g[i] - refs[mode][int(i)]) / den
+                assert err <= tol, (precision, mode, i, err)
+        e.run_phase(0, tau2, s0=s0, half=half, accel_mode=accel)
+        vg = e.state()[1]
+        sel = set(int(i) for i in phase_atoms)
+        ev_g = {tuple(r) for r in e.events().tolist() if r[3] in sel}
+        differ = [int(i) for i in phase_atoms
+                  if np.abs(vg[i] - vo[int(i)]).max() > (1e-10 if precision == 0 else 2e-5) * max(np.abs(vo[int(i)]).max(), 1.0)]
+        print(f"{workload} precision {precision}: {len(ev_o)} oracle events on 200 atoms, "
+              f"{len(ev_g ^ ev_o)} differing events, {len(differ)} atoms ending differently")
+        if precision == 0:
+            assert ev_g == ev_o
+            assert not differ, differ
+        else:
+            assert len(differ) <= 1, differ
+        assert e.observables()["error_flags"] == 0
+        e.close()
 
 
 @pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-5)])
@@ -591,16 +694,32 @@ def _rdf_oo(frames, box, rmax=9.0, dr=0.05):
     return h / ideal, dr, rmax
 
 
+def _diffusion_groups(U, every_fs, groups=8):
+    """D (1e-5 cm^2/s) of each of `groups` interleaved subsets of the oxygens
+    from their unwrapped positions U[frame, oxygen, 3]: Einstein MSD over all
+    time origins, linear fit over 20-80 % of the lags"""
+    nt = U.shape[0]
+    lags = np.arange(1, nt)
+    t = lags * every_fs * 1e-3
+    sel = (lags >= 0.2 * (nt - 1)) & (lags <= 0.8 * (nt - 1))
+    out = []
+    for g in range(groups):
+        X = U[:, g::groups]
+        msd = np.array([((X[l:] - X[:-l]) ** 2).sum(-1).mean() for l in lags])
+        out.append(np.polyfit(t[sel], msd[sel], 1)[0] / 6.0 * 10.0)
+    return np.array(out)
+
+
 @pytest.mark.slow
 @pytest.mark.parametrize("how", ["baoab", "jump", "jump_respa1_ewald"])
 def test_mixed_precision_long_run_observables(M, how):
-    """24,000-atom water, 3000 steps from one equilibrated state in mixed
-    precision and in FP64 (the FP64 mode follows the oracle event for event;
-    the oracle itself cannot run this long at this size): mean temperature
-    within 0.5 %, O-O radial distribution L1 distance <= 1e-2, and (BAOAB, and
-    JUMP-RESPA1 under Ewald with the paper's settings, where diffusion is not
-    damped) oxygen self-diffusion within 5 %."""
-    import bench
+    """24,000-atom water from one equilibrated state in mixed precision and in
+    FP64 (the FP64 mode follows the oracle event for event; the oracle itself
+    cannot run this long at this size): mean temperature within 0.5 %, O-O
+    radial distribution L1 distance <= 1e-2, and the oxygen self-diffusion
+    within 5 %. D is estimated on eight interleaved groups of oxygens; the
+    window (3000 fs, 6000 fs for JUMP under DSF, whose jumps damp diffusion)
+    is long enough that the standard error of the FP64 estimate is below 2 %."""
     from paper_2412_15073_gb300 import systems
     w = systems.water_box(8000, box=62.1, seed=0)
     p = dict(PARAMS, skin=0.5, skin_outer=1.5)
@@ -610,7 +729,9 @@ def test_mixed_precision_long_run_observables(M, how):
     w.x, w.v = eq.state()[0], eq.state()[1]
     eq.close()
     res = {}
-    every = 150
+    every, steps = 150, 3000
+    if how == "jump":
+        steps = 6000
     if how == "jump_respa1_ewald":
         # the paper's 96,000-atom settings (one ring, LJ long part at the outer level), 1:2:6 fs
         p = p | dict(dsf_alpha=0.42, coulomb_mode=1, pme_order=6, pme_spacing=0.8, r_split=6.0,
@@ -620,15 +741,22 @@ def test_mixed_precision_long_run_observables(M, how):
         e = M.Engine(precision=prec, seed=32)
         e.set_system(0, w, **p)
         fn = (lambda k, e=e: e.jump_respa1(k // 6, 1.0, 2, 3)) if how == "jump_respa1_ewald" else getattr(e, how)
-        T, frames = [], []
-        D = bench.diffusion(e, lambda k: (fn(k), T.append(e.observables()["temperature"]),
-                                          frames.append(e.state()[0])), 3000 // every * every, every, w.box, 1.0)
-        res[prec] = (np.mean(T), _rdf_oo(frames[::2], w.box), D)
+        T, frames, U = [], [], []
+        for k in range(steps // every + 1):
+            x, _, img, _ = e.state()
+            frames.append(x)
+            U.append((x + img * w.box)[::3])
+            if k < steps // every:
+                fn(every)
+                T.append(e.observables()["temperature"])
+        Dg = _diffusion_groups(np.stack(U), every)
+        res[prec] = (np.mean(T), _rdf_oo(frames[1::2], w.box), Dg.mean(), Dg.std(ddof=1) / np.sqrt(len(Dg)))
         e.close()
-    (T64, (g64, dr, rmax), D64), (T32, (g32, _, _), D32) = res[0], res[1]
+    (T64, (g64, dr, rmax), D64, se64), (T32, (g32, _, _), D32, se32) = res[0], res[1]
     l1 = np.abs(g32 - g64).sum() * dr / rmax
-    print(f"{how}: T {T32:.2f} vs {T64:.2f} K, RDF L1 {l1:.2e}, D {D32:.3f} vs {D64:.3f}")
+    print(f"{how}: T {T32:.2f} vs {T64:.2f} K, RDF L1 {l1:.2e}, D {D32:.4f} +- {se32:.4f} vs "
+          f"{D64:.4f} +- {se64:.4f} (1e-5 cm^2/s)")
     assert abs(T32 / T64 - 1) < 0.005
     assert l1 <= 1e-2
-    if how != "jump":
-        assert abs(D32 / D64 - 1) < 0.05
+    assert se64 / D64 < 0.02, (se64, D64)
+    assert abs(D32 / D64 - 1) < 0.05
