@@ -53,10 +53,11 @@ DSF_JUMP = DSF | dict(ring_r=[5.25, 6.0, 7.5], skin=0.3)
 DSF_BAOAB = DSF
 # Ewald water (the paper's electrostatics and 96,000-atom JUMP settings). With
 # weak jumped forces the proposal count is set by the 1/eps0 floor, not by the
-# ring bounds: one ring, fewer list kinds; 0.4 A skin for JUMP, 0.5 A for BAOAB
+# ring bounds: one ring, fewer list kinds; a 0.4 A skin for both (the fastest
+# of 0.3 - 0.8 A for each integrator, --only skin_sweep)
 EWALD = dict(dsf_alpha=0.42, coulomb_mode=1, pme_order=6, pme_spacing=0.8, r_split=6.0)
 EW_JUMP = DSF_JUMP | EWALD | dict(ring_r=[], lj_long_mode=2, skin=0.4, eps0=2.0)
-EW_BAOAB = DSF_BAOAB | EWALD
+EW_BAOAB = DSF_BAOAB | EWALD | dict(skin=0.4)     # the measured best skin of BAOAB-RESPA1 (--only skin_sweep)
 M_MID, N_OUT = 2, 2                       # kappa = 2 delta, Delta = 2 kappa
 CYCLE_FS = M_MID * N_OUT * DT_FS          # one headline step
 EW_WINDOW_FS = 480                        # timing window of the Ewald comparison runs
@@ -249,14 +250,15 @@ def best_matched(res: dict) -> dict:
 
 
 # ---------------------------------------------------------------- CPU oracle
-def oracle_cycle_cost(sys_, params, mode, n_grad, n_phase, n_bonded, n_recip, tau2, samples, nthreads, seed=0):
+def oracle_cycle_cost(sys_, params, mode, n_grad, n_phase, n_bonded, n_recip, tau2, runs, seed=0):
     """Time the FP64 oracle on a bounded sample of one step of the workload.
     The O(N^2) per-atom part (n_grad brute-force nonbonded gradients and
-    n_phase C' phases, each followed by J' when LJ jumps) runs for `samples`
-    lists of atoms drawn at random, spread over nthreads OpenMP threads; the
-    whole-system parts (n_bonded bonded gradients, n_recip smooth-PME sums)
-    are timed once. Returns (seconds of one full step, threads used, seconds
-    of each sampled step, atoms per sample)."""
+    n_phase C' phases, each followed by J' when LJ jumps) runs for lists of
+    atoms drawn at random; the whole-system parts (n_bonded bonded gradients,
+    n_recip smooth-PME sums) are timed once. runs: (atoms per sample, samples,
+    OpenMP threads, 0 = all) per configuration. Returns, per configuration,
+    (seconds of one full step, threads used, seconds of each sampled step), and
+    the seconds of the whole-system parts."""
     import oracle
     oracle.build()
     o = oracle.Oracle(sys_, seed=seed, **params)
@@ -267,23 +269,25 @@ def oracle_cycle_cost(sys_, params, mode, n_grad, n_phase, n_bonded, n_recip, ta
     for _ in range(n_recip):
         o.ewald_recip_pme()
     t_global = time.perf_counter() - t0
-    per, thr = [], 1
-    for s_idx, n_at in enumerate(samples):
-        atoms = rng.choice(sys_.n, n_at, replace=False)
-        t1 = time.perf_counter()
-        thr = o.sample_atom_work(atoms, mode, n_grad, n_phase, tau2, s_idx, nthreads)
-        per.append(time.perf_counter() - t1)
-    t_atom = sum(per) / sum(samples)
-    return t_global + sys_.n * t_atom, thr, per, t_global
+    out = []
+    for n_at, n_samples, nthreads in runs:
+        per, thr = [], 1
+        for s_idx in range(n_samples):
+            atoms = rng.choice(sys_.n, n_at, replace=False)
+            t1 = time.perf_counter()
+            thr = o.sample_atom_work(atoms, mode, n_grad, n_phase, tau2, s_idx, nthreads)
+            per.append(time.perf_counter() - t1)
+        out.append((t_global + sys_.n * sum(per) / (n_at * n_samples), thr, per))
+    return out, t_global
 
 
-def headline_oracle_cost(sys_, samples, nthreads):
+def headline_oracle_cost(sys_, runs):
     """One JUMP-RESPA1 cycle (1:2:4 fs) of the headline workload on the
     oracle: per atom two short-range gradients (one per kappa step), the
     (1 - chi) LJ part of the slow level (one more brute-force pass) and four
     C' phases (two per kappa step); whole system four bonded gradients (one
     per delta step) and one smooth-PME sum (the slow level)."""
-    return oracle_cycle_cost(sys_, EW_JUMP, 3, 3, 4, 4, 1, M_MID * DT_FS * 0.5e-3, samples, nthreads)
+    return oracle_cycle_cost(sys_, EW_JUMP, 3, 3, 4, 4, 1, M_MID * DT_FS * 0.5e-3, runs)
 
 
 def run_reference(args):
@@ -297,7 +301,8 @@ def run_reference(args):
     import oracle
     oracle.build()
     t_start = time.perf_counter()
-    t_cycle, thr, per, t_global = headline_oracle_cost(w, [n_sample] * (args.warmup + args.steps), 0)
+    (res, t_global) = headline_oracle_cost(w, [(n_sample, args.warmup + args.steps, 0)])
+    t_cycle, thr, per = res[0]
     timed = per[args.warmup:]
     secs = sum(timed)
     steps_equiv = len(timed) * n_sample / w.n
@@ -816,6 +821,34 @@ def spectra_leg(args, M, engine):
     return out
 
 
+def skin_sweep(args, M, engine, stream):
+    """List skins of the headline runs: JUMP-RESPA1 and BAOAB-RESPA1 (1:2:4 fs,
+    Ewald) timed over EW_WINDOW_FS for each inner skin and each width of the
+    outer candidate shell beyond it (the headline settings: 0.4 A and 1.1 A)"""
+    out = {"window_fs": EW_WINDOW_FS}
+    for name, seed, meth, params in (("jump_respa1", 5, "jump_respa1", EW_JUMP),
+                                     ("baoab_respa1", 6, "baoab_respa1", EW_BAOAB)):
+        res = {}
+        for skin, extra in [(sk, ex) for sk in args.sweep_skin for ex in args.sweep_outer]:
+            e = engine(seed, params | {"skin": skin, "skin_outer": skin + extra})
+            run = lambda k, e=e, m=meth: getattr(e, m)(k, 1.0, M_MID, N_OUT)
+            try:
+                run(30)
+                cyc = EW_WINDOW_FS // CYCLE_FS
+                c0 = e.observables()
+                t = timed(run, int(cyc), stream)
+                c1 = e.observables()
+                res[f"{skin:g}+{extra:g}"] = {"ns_per_day": ns_per_day(cyc * CYCLE_FS, t),
+                                    "rebuilds_per_ps": (c1["list_rebuilds"] - c0["list_rebuilds"]) / (cyc * CYCLE_FS * 1e-3),
+                                    "outer_rebuilds_per_ps": (c1["outer_rebuilds"] - c0["outer_rebuilds"]) /
+                                                             (cyc * CYCLE_FS * 1e-3)}
+            except M.MDError as ex:
+                res[f"{skin:g}+{extra:g}"] = {"error": str(ex)}
+            e.close()
+        out[name] = res
+    return out
+
+
 def list_entry_counts(e, n_atoms, kinds=(0, 4), sample=400, seed=3):
     """mean jump-list lengths (ring 0, LJ) over sampled atoms"""
     rng = np.random.default_rng(seed)
@@ -823,12 +856,13 @@ def list_entry_counts(e, n_atoms, kinds=(0, 4), sample=400, seed=3):
     return {k: float(np.mean([len(e.get_list(k, int(i))) for i in at])) for k in kinds}
 
 
-def inner_list_roofline(ms_total, groups, w, x, e, hbm, peak_kind):
+def inner_list_roofline(ms_total, groups, rebuilds, w, x, e, hbm, peak_kind):
     """HBM roofline of the inner list filter of the headline JUMP-RESPA1
-    run: per launch it streams every atom's outer candidates and stores the
-    kept entries of its short, ring and LJ lists (algorithmic bytes: see the
-    INNER_BYTES constants) over its mean device time (launches that found no
-    atom to rebuild return at once and are counted too)."""
+    run: a rebuild streams every atom's outer candidates and stores the kept
+    entries of its short, ring and LJ lists (algorithmic bytes: see the
+    INNER_BYTES constants); achieved = those bytes times the rebuilds over the
+    device time of all the kernel's launches (the launches that found no list
+    to rebuild cost a flag read per atom and are included)."""
     from scipy.spatial import cKDTree
     n = w.n
     t = cKDTree(np.mod(x, BOX), boxsize=BOX)
@@ -839,13 +873,14 @@ def inner_list_roofline(ms_total, groups, w, x, e, hbm, peak_kind):
     n_short = per_atom(p["r_split"] + p["skin"])
     lists = list_entry_counts(e, n)
     n_inner = n_short + lists[0] + lists[4]
-    per_launch_s = ms_total / max(groups, 1) * 1e-3
+    per_rebuild_s = ms_total / max(rebuilds, 1) * 1e-3
     nbytes = n * (INNER_BYTES_PER_CAND * n_outer + INNER_BYTES_PER_ENTRY * n_inner + INNER_BYTES_PER_ATOM)
-    achieved = nbytes / per_launch_s / 1e9
+    achieved = nbytes / per_rebuild_s / 1e9
     return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
             "traffic": None, "kernel": "k_inner_lists (inner list filter of the list rebuild)",
             "bytes_per_launch": nbytes, "outer_candidates_per_atom": n_outer, "inner_entries_per_atom": n_inner,
-            "ms_per_launch": per_launch_s * 1e3, "launches": int(groups), "peak_kind": peak_kind,
+            "ms_per_launch": per_rebuild_s * 1e3, "launches": int(groups), "rebuilds": int(rebuilds),
+            "ms_all_launches": ms_total, "peak_kind": peak_kind,
             "bytes_model": f"{INNER_BYTES_PER_CAND} B per outer candidate + {INNER_BYTES_PER_ENTRY} B per kept "
                            f"entry + {INNER_BYTES_PER_ATOM} B per atom"}
 
@@ -865,7 +900,7 @@ def main():
     ap.add_argument("--ens-dwindow", type=int, default=6000, help="fs of each ensemble run for D (0 = skip)")
     ap.add_argument("--mil-dwindow", type=int, default=2400, help="fs of each 10^6-atom run for D (0 = skip)")
     ap.add_argument("--only", default="all",
-                    choices=["all", "headline", "ewald", "dsf", "dsf_sweep", "spectra", "ensemble", "million",
+                    choices=["all", "headline", "ewald", "dsf", "dsf_sweep", "skin_sweep", "spectra", "ensemble", "million",
                              "jump", "baoab", "jump_respa1_ewald", "baoab_respa1_ewald"])
     ap.add_argument("--ensemble", type=int, default=1, help="also time the batched 64-replica ensemble")
     ap.add_argument("--million", type=int, default=1, help="also time the 1,000,000-atom heterogeneous system")
@@ -873,6 +908,8 @@ def main():
     ap.add_argument("--ewald-runs", nargs="*", default=None, help="only these Ewald runs (plus the 1 fs reference)")
     ap.add_argument("--sweep-rc", type=float, nargs="*", default=[5.0, 6.0, 7.0])
     ap.add_argument("--sweep-eps0", type=float, nargs="*", default=[0.1, 1.0, 2.0])
+    ap.add_argument("--sweep-skin", type=float, nargs="*", default=[0.3, 0.4, 0.5, 0.6, 0.8])
+    ap.add_argument("--sweep-outer", type=float, nargs="*", default=[1.1])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -963,6 +1000,12 @@ def main():
             print(json.dumps({"spectra": out}), flush=True)
         ranks.close()
         return
+    if args.only == "skin_sweep":
+        out = skin_sweep(args, M, eng_ew, stream)
+        if rank == 0:
+            print(json.dumps({"skin_sweep": out}), flush=True)
+        ranks.close()
+        return
     if args.only == "dsf_sweep":
         out = dsf_sweep(args, M, eng_dsf, stream, w.mass)
         if rank == 0:
@@ -1011,11 +1054,13 @@ def main():
     gpe = {"jump_respa1": world * (N_OUT * pairs_short + props) * args.steps / t_jump / 1e9,
            "baoab_respa1": world * (N_OUT * pairs_short_b + pairs_full_b) * args.steps / t_baoab / 1e9}
     # per-class device time of the headline JUMP-RESPA1 cycle (profiled run, plain launches)
+    r0 = ej.observables()["list_rebuilds"]
     ms, groups = profiled(ej, run_j, 60)
+    rebuilds = ej.observables()["list_rebuilds"] - r0
     top = int(np.argmax(ms))
     hbm = pk["hbm_gbs"]
     if CLASSES[top] == "list_inner":
-        roof = inner_list_roofline(float(ms[top]), int(groups[top]), w_ew, x_j, ej, hbm, peak_kind)
+        roof = inner_list_roofline(float(ms[top]), int(groups[top]), rebuilds, w_ew, x_j, ej, hbm, peak_kind)
     elif CLASSES[top] == "pair_force":
         roof = pair_roofline(float(ms[top]), int(groups[top]), pairs_short, sms, clock_mhz)
         roof["kernel"] = "k_force (short pairs of JUMP-RESPA1, and its slow-level LJ part)"
@@ -1098,13 +1143,13 @@ def main():
     out["matched_summary"] = summ
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
-        t_one, thr1, _, tg = headline_oracle_cost(w_ew, [args.cpu_sample], 1)
-        t_all, thr, _, _ = headline_oracle_cost(w_ew, [args.cpu_sample * oracle.get_threads()], 0)
+        n_all = args.cpu_sample * oracle.get_threads()
+        ((t_one, thr1, _), (t_all, thr, _)), tg = headline_oracle_cost(w_ew, [(args.cpu_sample, 1, 1), (n_all, 1, 0)])
         sample = (f"{{n}} of 96,000 atoms, each with its per-atom work of one JUMP-RESPA1 cycle (three O(N) "
                   f"nonbonded passes, four C' phases), plus the whole-system parts timed once (four bonded "
                   f"gradients, one smooth-PME sum: {tg:.1f} s); list builds excluded; scaled to the full cycle")
         out["cpu_baseline"] = {"value": ns_per_day(CYCLE_FS, t_all), "unit": "ns/day", "cores": thr, "kind": "oracle",
-                               "sample": sample.format(n=args.cpu_sample * oracle.get_threads()),
+                               "sample": sample.format(n=n_all),
                                "single_thread": {"value": ns_per_day(CYCLE_FS, t_one), "unit": "ns/day",
                                                  "cores": thr1, "sample": sample.format(n=args.cpu_sample)}}
     if rank == 0:

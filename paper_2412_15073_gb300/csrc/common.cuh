@@ -39,11 +39,11 @@ enum Counter { C_CPROP = 0, C_CACC, C_JPROP, C_JACC, C_SATT, C_REBUILD, C_OUTER,
 // pair weight: full U, short chi U, long (1 - chi) U
 enum Weight { W_FULL = 0, W_SHORT = 1, W_LONG = 2, W_LJLONG = 3 };   // W_LJLONG: (1 - chi) LJ alone
 
-struct LJPair {
+struct alignas(16) LJPair {
     double c12, c6, uR, duR;   // 4 eps s^12, 4 eps s^6, U_LJ(R), U_LJ'(R)
-    float c12f, c6f, uRf, duRf;
+    float c12f, c6f, uRf, duRf;   // the same in FP32 (one 16-byte load)
     int on;                    // eps > 0
-    int pad;
+    int pad[3];
 };
 
 // Everything a kernel needs about one replica. Device resident, one per replica.
@@ -218,6 +218,29 @@ __device__ __forceinline__ void ljsf(const RepParams& P, const LJPair& l, T r, T
     const T c12 = PT<T>::c12(l), c6 = PT<T>::c6(l);
     u = r6i * (c12 * r6i - c6) - PT<T>::uR(l) - (r - T(P.R)) * PT<T>::duR(l);
     du = r6i * rinv * (T(6) * c6 - T(12) * c12 * r6i) - PT<T>::duR(l);
+}
+template <>
+__device__ __forceinline__ void ljsf<float>(const RepParams& P, const LJPair& l, float r, float rinv, float& u,
+                                            float& du)
+{
+    const float4 c = *reinterpret_cast<const float4*>(&l.c12f);    // c12, c6, U(R), U'(R)
+    const float r2i = rinv * rinv;
+    const float r6i = r2i * r2i * r2i;
+    u = r6i * (c.x * r6i - c.y) - c.z - (r - float(P.R)) * c.w;
+    du = r6i * rinv * (6.f * c.y - 12.f * c.x * r6i) - c.w;
+}
+
+// distance and its reciprocal from r^2: FP64 by square root and division; FP32
+// by the reciprocal square root (one MUFU operation and a multiply)
+__device__ __forceinline__ void rdist(double r2, double& r, double& rinv)
+{
+    r = sqrt(r2);
+    rinv = 1.0 / r;
+}
+__device__ __forceinline__ void rdist(float r2, float& r, float& rinv)
+{
+    rinv = rsqrtf(r2);
+    r = r2 * rinv;
 }
 
 // ---- normal law --------------------------------------------------------------

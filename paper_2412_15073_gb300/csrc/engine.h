@@ -96,12 +96,13 @@ struct Dev {
 };
 
 // can gradient mode `mode` run as half-list kernels? (full, short and long
-// pair weights; not the short weight of replicas whose short force also runs
-// over the LJ list: lj_long_mode 1 in modes 3 and 5, lj_long_mode 2 in mode 5)
+// pair weights and the (1 - chi) LJ part alone (7); not the short weight of
+// replicas whose short force also runs over the LJ list: lj_long_mode 1 in
+// modes 3 and 5, lj_long_mode 2 in mode 5)
 inline bool force_half_ok(const Dev& d, int mode)
 {
     if (!d.lj_symmetric) return false;
-    if (mode == 0 || mode == 2 || mode == 4) return true;
+    if (mode == 0 || mode == 2 || mode == 4 || mode == 7) return true;
     if (mode == 3) return !(d.lj_long_mask & 1);
     if (mode == 5) return d.lj_long_mask == 0;
     return false;

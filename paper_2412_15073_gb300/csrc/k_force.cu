@@ -125,11 +125,11 @@ template <typename T> struct Acc;
 template <> struct Acc<float> {
     long long x = 0, y = 0, z = 0;
     bool bad = false;          // a term outside the fixed-point range (or not finite)
-    __device__ void add(float f, float dx, float dy, float dz)
+    // the term (f dx, f dy, f dz) with f = (dU/dr) / r; fr = dU/dr is its length
+    __device__ void add(float f, float dx, float dy, float dz, float fr)
     {
-        const float gx = f * dx, gy = f * dy, gz = f * dz;
-        bad |= !(fabsf(gx) + fabsf(gy) + fabsf(gz) < FIX_TERM_MAX);
-        x += to_fix(gx); y += to_fix(gy); z += to_fix(gz);
+        bad |= !(fabsf(fr) < 0.5f * FIX_TERM_MAX);      // each component, and their sum, below the limit
+        x += to_fix(f * dx); y += to_fix(f * dy); z += to_fix(f * dz);
     }
     __device__ bool overflow() const { return bad; }
     __device__ void combine_shfl(int tpa)
@@ -146,7 +146,7 @@ template <> struct Acc<float> {
 };
 template <> struct Acc<double> {
     double x = 0, y = 0, z = 0;
-    __device__ void add(double f, double dx, double dy, double dz)
+    __device__ void add(double f, double dx, double dy, double dz, double)
     {
         x += f * dx; y += f * dy; z += f * dz;
     }
@@ -207,8 +207,8 @@ __global__ void __launch_bounds__(256) k_force(Dev d, int lk, double* out, int a
             const T r2 = dx * dx + dy * dy + dz * dz;
             if (r2 >= cut2) continue;
             if (W == W_LONG && r2 <= sw2) continue;
-            const T rr = d_sqrt(r2);
-            const T rinv = T(1) / rr;
+            T rr, rinv;
+            rdist(r2, rr, rinv);
             T u = T(0), du = T(0);
             const T qq = qi * qj;
             if (qq != T(0)) {
@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(256) k_force(Dev d, int lk, double* out, int a
                 chi_and_slope<T>(rr, sw, h, c, dc);
                 f = W == W_SHORT ? dc * u + c * du : -dc * u + (T(1) - c) * du;
             }
-            acc.add(f * rinv, dx, dy, dz);
+            acc.add(f * rinv, dx, dy, dz, f);
         }
         if ((W == W_SHORT && (P.lj_long == 1 || (P.lj_long == 2 && BONDED))) || (W == W_LJLONG && P.lj_long == 2)) {
             // the (1 - chi) LJ part over the LJ list: in the short force with
@@ -256,12 +256,13 @@ __global__ void __launch_bounds__(256) k_force(Dev d, int lk, double* out, int a
                 if (r2 >= R2 || r2 <= sw2) continue;
                 const LJPair& lj = P.lj[ti * MAX_TYPES + d.type[j]];
                 if (!lj.on) continue;
-                const T rr = d_sqrt(r2);
-                const T rinv = T(1) / rr;
+                T rr, rinv;
+                rdist(r2, rr, rinv);
                 T ul, dul, c, dc;
                 ljsf<T>(P, lj, rr, rinv, ul, dul);
                 chi_and_slope<T>(rr, sw, h, c, dc);
-                acc.add((-dc * ul + (T(1) - c) * dul) * rinv, dx, dy, dz);
+                const T fl = -dc * ul + (T(1) - c) * dul;
+                acc.add(fl * rinv, dx, dy, dz, fl);
             }
         }
     }
@@ -311,8 +312,11 @@ __global__ void __launch_bounds__(256) k_force_half(Dev d, int lk)
         const float sw = float(P.sw), h = float(P.h), sw2 = sw * sw;
         const float C = float(COULOMB);
         const uint32_t* row = d.list[lk] + (size_t)i * d.lcap[lk];
-        const int n = min(d.lcnt[lk][i], d.lcap[lk]);
+        // the (1 - chi) LJ part alone (W_LJLONG) runs over the LJ list of replicas
+        // with lj_long_mode 2 only (zero elsewhere, as in k_force)
+        const int n = (W == W_LJLONG && P.lj_long != 2) ? 0 : min(d.lcnt[lk][i], d.lcap[lk]);
         const float sc = P.sclf;
+        const float R2 = float(P.R) * float(P.R);
         for (int k = sub; k < n; k += TPA) {
             const int j = int(row[k]);
             if (j <= i) continue;
@@ -321,36 +325,49 @@ __global__ void __launch_bounds__(256) k_force_half(Dev d, int lk)
             sdisp(pi, pj, sc, P.sclf_lo, dx, dy, dz);
             const float qj = __uint_as_float(pj.w);
             const float r2 = dx * dx + dy * dy + dz * dz;
-            if (r2 >= cut2) continue;
-            if (W == W_LONG && r2 <= sw2) continue;
-            const float rr = sqrtf(r2);
-            const float rinv = 1.f / rr;
-            float u = 0.f, du = 0.f;
-            const float qq = qi * qj;
-            if (qq != 0.f) {
-                float uc, duc;
-                dsf<float>(P, rr, rinv, uc, duc);
-                u = C * qq * uc;
-                du = C * qq * duc;
-            }
-            const LJPair& lj = P.lj[ti * MAX_TYPES + d.type[j]];
-            if (lj.on && !(W == W_LONG && P.lj_long == 1)) {
-                float ul, dul;
+            float f, fr;
+            if (W == W_LJLONG) {
+                if (r2 >= R2 || r2 <= sw2) continue;
+                const LJPair& lj = P.lj[ti * MAX_TYPES + d.type[j]];
+                if (!lj.on) continue;
+                float rr, rinv;
+                rdist(r2, rr, rinv);
+                float ul, dul, c, dc;
                 ljsf<float>(P, lj, rr, rinv, ul, dul);
-                u += ul;
-                du += dul;
-            }
-            float f;
-            if (W == W_FULL) {
-                f = du;
-            } else {
-                float c, dc;
                 chi_and_slope<float>(rr, sw, h, c, dc);
-                f = W == W_SHORT ? dc * u + c * du : -dc * u + (1.f - c) * du;
+                fr = -dc * ul + (1.f - c) * dul;
+                f = fr * rinv;
+            } else {
+                if (r2 >= cut2) continue;
+                if (W == W_LONG && r2 <= sw2) continue;
+                float rr, rinv;
+                rdist(r2, rr, rinv);
+                float u = 0.f, du = 0.f;
+                const float qq = qi * qj;
+                if (qq != 0.f) {
+                    float uc, duc;
+                    dsf<float>(P, rr, rinv, uc, duc);
+                    u = C * qq * uc;
+                    du = C * qq * duc;
+                }
+                const LJPair& lj = P.lj[ti * MAX_TYPES + d.type[j]];
+                if (lj.on && !(W == W_LONG && P.lj_long == 1)) {
+                    float ul, dul;
+                    ljsf<float>(P, lj, rr, rinv, ul, dul);
+                    u += ul;
+                    du += dul;
+                }
+                if (W == W_FULL) {
+                    fr = du;
+                } else {
+                    float c, dc;
+                    chi_and_slope<float>(rr, sw, h, c, dc);
+                    fr = W == W_SHORT ? dc * u + c * du : -dc * u + (1.f - c) * du;
+                }
+                f = fr * rinv;
             }
-            f *= rinv;
             const float gx = f * dx, gy = f * dy, gz = f * dz;
-            acc.add(f, dx, dy, dz);
+            acc.add(f, dx, dy, dz, fr);
             unsigned long long* fj = reinterpret_cast<unsigned long long*>(d.facc) + 3 * (size_t)j;
             atomicAdd(fj, (unsigned long long)(-to_fix(gx)));
             atomicAdd(fj + 1, (unsigned long long)(-to_fix(gy)));
@@ -717,6 +734,7 @@ int force_t(const Dev& d, int mode, double* out, int as_grad, int tpa, cudaStrea
         case 2: force_half<W_FULL, false>(d, L_FULL, out, as_grad, t, s); break;
         case 3: force_half<W_SHORT, false>(d, L_SHORT, out, as_grad, t, s); break;
         case 4: force_half<W_LONG, false>(d, L_FULL, out, as_grad, t, s); break;
+        case 7: force_half<W_LJLONG, false>(d, L_LJ, out, as_grad, t, s); break;
         default: force_half<W_SHORT, true>(d, L_SHORT, out, as_grad, t, s); break;
         }
         return nk;

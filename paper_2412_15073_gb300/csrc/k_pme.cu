@@ -25,8 +25,9 @@ namespace mdj {
 
 namespace {
 
-// fixed-point unit of the charge grid: 2^-48 e (grid values up to 2^15 e in magnitude)
-constexpr double PME_FIX = 281474976710656.0;
+// fixed-point unit of the FP64 charge grid: 2^-50 e (grid values up to 2^13 e in
+// magnitude: hundreds of times the charge a grid point gathers in a liquid)
+constexpr double PME_FIX = 1125899906842624.0;
 constexpr int PME_THREADS = 128;
 constexpr int PME_CHUNK = 64;           // atoms staged in shared memory at a time
 

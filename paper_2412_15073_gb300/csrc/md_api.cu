@@ -123,7 +123,7 @@ struct md_ctx {
     int kinds = 0;          // inner list kinds built so far
     int fp64 = 0;
     int tpa_cfg = 0;
-    int tpa[6] = {0, 0, 0, 0, 0, 0};
+    int tpa[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // pair kernel choice per gradient mode (7: the LJ long part alone)
     int vvar = -1;          // chosen variant of the mixed-mode velocity-phase kernel
     bool tune_log = false;  // report the autotuners' choices on stderr (MDJ_TUNE_LOG)
     bool fuse_inner = false;      // run the inner steps fused (MDJ_FUSED_INNER; separate launches otherwise)
@@ -1202,8 +1202,10 @@ void force_into(md_ctx* ctx, int mode, double* out, int as_grad)
     if (mode == 6) {
         // the slow level: the (1 - chi) LJ part of lj_long_mode 2 replicas (zero elsewhere), then PME
         if (any_lj_slow(ctx)) {
-            Prof p(ctx, 0, 1);
-            launch_force(ctx->d, 7, out, as_grad, ctx->fp64, ctx->fp64 ? 1 : 4, ctx->s);
+            const int t = tpa_for(ctx, 7);
+            const bool half = !ctx->fp64 && (t & FORCE_HALF) && force_half_ok(ctx->d, 7);
+            Prof p(ctx, 0, half ? 2 : 1);
+            launch_force(ctx->d, 7, out, as_grad, ctx->fp64, t, ctx->s);
         } else {
             cudaMemsetAsync(out, 0, sizeof(double) * 3 * (size_t)ctx->d.N, ctx->s);
         }

@@ -488,9 +488,14 @@ def test_batched_ensemble_of_64_replicas(M, oracle_mod):
 
 def test_million_atom_heterogeneous_sampled(M, oracle_mod):
     """The 1,000,000-atom system (water around a dense sphere of 50,002
-    charged LJ beads, 229 A box) in mixed precision: gradients of 40 sampled
-    atoms within 1e-5 of the oracle's, and one C' phase of 100 sampled atoms
-    (oracle with per-atom lists, since its O(N^2) list build is out of reach)."""
+    charged LJ beads in rock-salt order, 229 A box) in mixed precision:
+    gradients of 40 sampled atoms within 1e-5 of the oracle's, and one C'
+    phase of 100 sampled atoms (oracle with per-atom lists, since its O(N^2)
+    list build is out of reach). On a bead the net force is a small difference
+    of pair forces about ten times larger (its six nearest neighbours carry the
+    opposite charge), so the error is measured against the larger of the net
+    force and one tenth of the sum of the pair-force magnitudes (the error of
+    an FP32 sum scales with the magnitudes summed)."""
     from paper_2412_15073_gb300 import systems
     w = systems.water_with_beads()
     p = dict(PARAMS, r_cut=10.0, skin=0.5, skin_outer=1.5)
@@ -500,13 +505,24 @@ def test_million_atom_heterogeneous_sampled(M, oracle_mod):
     rng = np.random.default_rng(7)
     n_w = 3 * 316_666
     idx = np.concatenate([rng.choice(n_w, 30, replace=False), n_w + rng.choice(w.n - n_w, 10, replace=False)])
+    def abs_sum(i, weight):
+        """sum over the partners of atom i of |d/dr (weighted U)| (oracle pair terms)"""
+        d = w.x - w.x[i]
+        d -= w.box * np.round(d / w.box)
+        r = np.sqrt((d * d).sum(1))
+        mol = np.arange(w.n) // 3
+        near = np.flatnonzero((r < p["r_cut"]) & (np.arange(w.n) != i) &
+                              ~((mol == mol[i]) & (i < n_w) & (np.arange(w.n) < n_w)))
+        return sum(abs(o.pair_dudr(int(w.type[i]), int(w.type[j]), w.charge[i] * w.charge[j], r[j], weight))
+                   for j in near)
+
     for mode in (0, 3):
         g = e.gradient(mode)
         tot = e.gradient(0) if mode == 3 else g
         rms = np.sqrt((tot * tot).sum(1).mean())
         for i in idx:
             ref = o.gradient_atom(mode, int(i))
-            den = max(np.linalg.norm(tot[i]), 0.01 * rms)
+            den = max(np.linalg.norm(tot[i]), 0.01 * rms, 0.1 * abs_sum(int(i), 0 if mode == 0 else 1))
             assert np.linalg.norm(g[i] - ref) / den <= 1e-5, (mode, i)
     mt = w.mass / 418.4
     tau2 = 0.0005
