@@ -398,7 +398,7 @@ struct CAtom {                             // constants of one atom's C' pass
     int N[MAX_RINGS];
     float LYv[MAX_RINGS];
     uint4 pi;
-    float qiC, mt, sbm, sbom, c0, aa, T2;
+    float qiC, sbm, sbom, c0, aa, T2;
     float3 v0, a;
     uint32_t s0, ctag;
     int half;
@@ -471,9 +471,9 @@ __device__ __forceinline__ bool c_init(const Dev& d, const JC& c, int i, int il,
     if (ntot == 0) return false;
     A.i = i; A.il = il; A.s0 = s0; A.half = half;
     A.ctag = (uint32_t(TAG_C) << 24) | (uint32_t(half) << 20);
-    A.mt = float(d.mt[i]);
-    A.sbm = sqrtf(c.beta * A.mt);
-    A.sbom = sqrtf(c.beta / A.mt);
+    const float mt = float(d.mt[i]);
+    A.sbm = sqrtf(c.beta * mt);
+    A.sbom = sqrtf(c.beta / mt);
     const float4 ly4 = __ldg(reinterpret_cast<const float4*>(d.LYf) + i);
     A.LYv[0] = ly4.x; A.LYv[1] = ly4.y; A.LYv[2] = ly4.z; A.LYv[3] = ly4.w;
     A.pi = d.pos[i];
@@ -617,7 +617,7 @@ __global__ void __launch_bounds__(128, MINB) k_cphase_f(Dev d, const __grid_cons
         const int il = i - P.atom_off;
         const uint32_t sb = s_abs ? 0u : uint32_t(d.step_base[r]);
         double v[3] = {d.v[3 * i], d.v[3 * i + 1], d.v[3 * i + 2]};
-        const double ad[3] = {a ? a[3 * i] : 0.0, a ? a[3 * i + 1] : 0.0, a ? a[3 * i + 2] : 0.0};
+        double ad[3] = {a ? a[3 * i] : 0.0, a ? a[3 * i + 1] : 0.0, a ? a[3 * i + 2] : 0.0};
         if ((jmode & 2) && P.lj_jump) jprime<float>(d, P, i, il, v, tau2, sb + s_off, half, tl, err);
         for (int pass = 0; pass < npass; ++pass) {
             const uint32_t s0 = sb + (pass ? s_off2 : s_off);
@@ -634,6 +634,10 @@ __global__ void __launch_bounds__(128, MINB) k_cphase_f(Dev d, const __grid_cons
                     const JC jc = make_jc(P);
                     cprime_f(d, jc, P, i, il, jv, v0, af, float(tau2), s0, hp, tl, err);
                 }
+                // the FP64 velocity and acceleration come back from memory after the
+                // chain instead of occupying registers during it
+                v[0] = d.v[3 * i]; v[1] = d.v[3 * i + 1]; v[2] = d.v[3 * i + 2];
+                ad[0] = a ? a[3 * i] : 0.0; ad[1] = a ? a[3 * i + 1] : 0.0; ad[2] = a ? a[3 * i + 2] : 0.0;
             }
             // FP64 end of the phase: (v0 + (tau/2) a) + sum of the jumps; the
             // first sum rounds like a B kick, so a phase without jumps is one
