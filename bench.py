@@ -154,10 +154,15 @@ class Clocks:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # the timed region starts once the sampler is running (its first line is out)
+            t0 = time.time()
+            while not self.out and time.time() - t0 < 5.0 and self.proc.poll() is None:
+                time.sleep(0.01)
+            self.n0 = len(self.out)
         except Exception:
             self.proc = None
         return self
@@ -177,7 +182,8 @@ class Clocks:
     def summary(self):
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.out:
+        # the lines written after the timed region began (the first one may predate it)
+        for line in self.out[getattr(self, "n0", 0):] or self.out:
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue

@@ -15,9 +15,11 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libmdjump.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 SOURCES = ["md_api.cu", "k_lists.cu", "k_force.cu", "k_jump.cu", "k_pme.cu", "k_vacf.cu", "noalloc.cu"]
-# the velocity-phase kernel comes in several occupancy variants that must give
-# identical results: no mul/add contraction there, every FMA is written out
-PER_FILE = {"k_jump.cu": ["-fmad=false"]}
+# the velocity-phase kernel comes in several occupancy variants, and the pair
+# kernels in thread-per-atom and half-list variants, that must give identical
+# results: no mul/add contraction there (the compiler would fuse differently
+# in each variant), every FMA is written out
+PER_FILE = {"k_jump.cu": ["-fmad=false"], "k_force.cu": ["-fmad=false"]}
 HEADERS = ["common.cuh", "engine.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",

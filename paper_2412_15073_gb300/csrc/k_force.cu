@@ -184,6 +184,7 @@ __global__ void __launch_bounds__(256) k_force(Dev d, int lk, double* out, int a
         const T C = T(COULOMB);
         const uint32_t* row = d.list[lk] + (size_t)i * d.lcap[lk];
         const int n = W == W_LJLONG ? 0 : min(d.lcnt[lk][i], d.lcap[lk]);
+        if (sub == 0) prefetch_row_l2(row, n);
         // position of i in the arithmetic type
         uint4 pi = make_uint4(0, 0, 0, 0);
         double3 xi = make_double3(0, 0, 0);
@@ -240,6 +241,7 @@ __global__ void __launch_bounds__(256) k_force(Dev d, int lk, double* out, int a
             // level with lj_long_mode 2
             const uint32_t* lrow = d.list[L_LJ] + (size_t)i * d.lcap[L_LJ];
             const int nl = min(d.lcnt[L_LJ][i], d.lcap[L_LJ]);
+            if (sub == 0) prefetch_row_l2(lrow, nl);
             const T R2 = T(P.R) * T(P.R);
             for (int k = sub; k < nl; k += TPA) {
                 const int j = int(lrow[k]);
@@ -315,6 +317,7 @@ __global__ void __launch_bounds__(256) k_force_half(Dev d, int lk)
         // the (1 - chi) LJ part alone (W_LJLONG) runs over the LJ list of replicas
         // with lj_long_mode 2 only (zero elsewhere, as in k_force)
         const int n = (W == W_LJLONG && P.lj_long != 2) ? 0 : min(d.lcnt[lk][i], d.lcap[lk]);
+        if (sub == 0) prefetch_row_l2(row, n);
         const float sc = P.sclf;
         const float R2 = float(P.R) * float(P.R);
         for (int k = sub; k < n; k += TPA) {

@@ -366,9 +366,18 @@ __global__ void __launch_bounds__(32 * WARPS) k_inner_lists(Dev d, int kinds_rt,
     const uint32_t kinds = KM ? KM : uint32_t(kinds_rt);
     const int lane = threadIdx.x & 31;
     const int nw = gridDim.x * WARPS;
-    for (int i = blockIdx.x * WARPS + (threadIdx.x >> 5); i < d.N; i += nw) {
+    const int i0 = blockIdx.x * WARPS + (threadIdx.x >> 5);
+    for (int i = i0; i < d.N; i += nw) {
         const int r = d.rep[i];
         if (!late && !d.flags[2 * r]) continue;
+        // the outer rows stream from DRAM: this warp's next row goes to L2
+        // while the current one is filtered (and the first row right away)
+        if (lane == 0) {
+            if (i == i0) prefetch_row_l2(d.olist + (size_t)i * d.ocap, min(d.ocnt[i], d.ocap));
+            const int nx = i + nw;
+            if (nx < d.N && (late || d.flags[2 * d.rep[nx]]))
+                prefetch_row_l2(d.olist + (size_t)nx * d.ocap, min(d.ocnt[nx], d.ocap));
+        }
         const RepParams& P = d.P[r];
         const uint4 pi = d.pos[i];
         const float qi = __uint_as_float(pi.w);
