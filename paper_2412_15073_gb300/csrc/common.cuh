@@ -57,6 +57,8 @@ struct RepParams {
     // integer differences give the minimum image exactly
     double scl, inv_scl;       // L / 2^32, 2^32 / L
     float sclf, sclf_lo;       // L / 2^32 as a sum of two floats (hi + lo)
+    float scl2f;               // (L / 2^32)^2
+    unsigned long long sw2u;   // (r_c - h)^2 in squared scaled units, rounded
     // cutoffs
     double R, rc, h, sw;       // r_E, r_c, h, r_c - h
     double edge[MAX_RINGS + 1];// ring edges: sw = edge[0] < ... < edge[nr] = R
@@ -186,16 +188,42 @@ template <> struct PT<float> {
 };
 
 // ---- switch chi (quintic step on [r_c - h, r_c]) ----------------------------
+// chi and its slope at s = (r - sw) / h in [0, 1]
+template <typename T>
+__device__ __forceinline__ void chi_of_s(T s, T h, T& c, T& dc)
+{
+    const T s2 = s * s;
+    c = T(1) - s2 * s * (T(10) - T(15) * s + T(6) * s2);
+    const T om = T(1) - s;
+    dc = T(-30) * s2 * om * om / h;
+}
+
 template <typename T>
 __device__ __forceinline__ void chi_and_slope(T r, T sw, T h, T& c, T& dc)
 {
     if (r <= sw) { c = T(1); dc = T(0); return; }
     if (r >= sw + h) { c = T(0); dc = T(0); return; }
-    const T s = (r - sw) / h;
-    const T s2 = s * s;
-    c = T(1) - s2 * s * (T(10) - T(15) * s + T(6) * s2);
-    const T om = T(1) - s;
-    dc = T(-30) * s2 * om * om / h;
+    chi_of_s<T>((r - sw) / h, h, c, dc);
+}
+
+// The same in FP32 for a pair given by its scaled coordinates a, b, with s
+// taken from the exact integer displacement: r - sw = (r^2 - sw^2) / (r + sw),
+// where r^2 - sw^2 is formed exactly in 64-bit integers and rounded once.
+// An FP32 distance near sw is off by up to half an ulp of r (2.4e-7 A at
+// 4.5 A), and the switch's slope (up to 15/(8h) per unit of s) turns that
+// into the largest error of a chi-weighted pair force, chi' U; this form
+// leaves about a tenth of it. r is the FP32 distance that decides the region.
+__device__ __forceinline__ void chi_and_slope_x(const uint4& a, const uint4& b, const RepParams& P, float r,
+                                                float sw, float h, float& c, float& dc)
+{
+    if (r <= sw) { c = 1.f; dc = 0.f; return; }
+    if (r >= sw + h) { c = 0.f; dc = 0.f; return; }
+    const long long ix = int(a.x - b.x), iy = int(a.y - b.y), iz = int(a.z - b.z);
+    const unsigned long long q =
+        (unsigned long long)(ix * ix) + (unsigned long long)(iy * iy) + (unsigned long long)(iz * iz);
+    const float dq = __ll2float_rn((long long)(q - P.sw2u));
+    const float s = fminf(1.f, fmaxf(0.f, dq * P.scl2f / ((r + sw) * h)));
+    chi_of_s<float>(s, h, c, dc);
 }
 
 // DSF Coulomb per unit C q_i q_j: value and radial derivative, r < R

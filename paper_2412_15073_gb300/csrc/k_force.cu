@@ -120,6 +120,18 @@ __device__ __forceinline__ void bonded_gather(const Dev& d, int i, double& gx, d
     }
 }
 
+// switch of a pair: FP32 from the exact integer displacement, FP64 from r
+__device__ __forceinline__ void chi_t(const uint4& a, const uint4& b, const RepParams& P, float r, float sw, float h,
+                                      float& c, float& dc)
+{
+    chi_and_slope_x(a, b, P, r, sw, h, c, dc);
+}
+__device__ __forceinline__ void chi_t(const uint4&, const uint4&, const RepParams&, double r, double sw, double h,
+                                      double& c, double& dc)
+{
+    chi_and_slope<double>(r, sw, h, c, dc);
+}
+
 // pair gradient accumulators: fixed point for float, double for double
 template <typename T> struct Acc;
 template <> struct Acc<float> {
@@ -194,8 +206,9 @@ __global__ void __launch_bounds__(256) k_force(Dev d, int lk, double* out, int a
         for (int k = sub; k < n; k += TPA) {
             const int j = int(row[k]);
             T dx, dy, dz, qj;
+            uint4 pj = make_uint4(0, 0, 0, 0);
             if (sizeof(T) == 4) {
-                const uint4 pj = d.pos[j];
+                pj = d.pos[j];
                 float fx, fy, fz;
                 sdisp(pi, pj, sc, P.sclf_lo, fx, fy, fz);
                 dx = T(fx); dy = T(fy); dz = T(fz);
@@ -230,7 +243,7 @@ __global__ void __launch_bounds__(256) k_force(Dev d, int lk, double* out, int a
                 f = du;
             } else {
                 T c, dc;
-                chi_and_slope<T>(rr, sw, h, c, dc);
+                chi_t(pi, pj, P, rr, sw, h, c, dc);
                 f = W == W_SHORT ? dc * u + c * du : -dc * u + (T(1) - c) * du;
             }
             acc.add(f * rinv, dx, dy, dz, f);
@@ -246,9 +259,11 @@ __global__ void __launch_bounds__(256) k_force(Dev d, int lk, double* out, int a
             for (int k = sub; k < nl; k += TPA) {
                 const int j = int(lrow[k]);
                 T dx, dy, dz;
+                uint4 pj = make_uint4(0, 0, 0, 0);
                 if (sizeof(T) == 4) {
+                    pj = d.pos[j];
                     float fx, fy, fz;
-                    sdisp(pi, d.pos[j], sc, P.sclf_lo, fx, fy, fz);
+                    sdisp(pi, pj, sc, P.sclf_lo, fx, fy, fz);
                     dx = T(fx); dy = T(fy); dz = T(fz);
                 } else {
                     const double3 xj = ld3(d.x, j);
@@ -262,7 +277,7 @@ __global__ void __launch_bounds__(256) k_force(Dev d, int lk, double* out, int a
                 rdist(r2, rr, rinv);
                 T ul, dul, c, dc;
                 ljsf<T>(P, lj, rr, rinv, ul, dul);
-                chi_and_slope<T>(rr, sw, h, c, dc);
+                chi_t(pi, pj, P, rr, sw, h, c, dc);
                 const T fl = -dc * ul + (T(1) - c) * dul;
                 acc.add(fl * rinv, dx, dy, dz, fl);
             }
@@ -337,7 +352,7 @@ __global__ void __launch_bounds__(256) k_force_half(Dev d, int lk)
                 rdist(r2, rr, rinv);
                 float ul, dul, c, dc;
                 ljsf<float>(P, lj, rr, rinv, ul, dul);
-                chi_and_slope<float>(rr, sw, h, c, dc);
+                chi_and_slope_x(pi, pj, P, rr, sw, h, c, dc);
                 fr = -dc * ul + (1.f - c) * dul;
                 f = fr * rinv;
             } else {
@@ -364,7 +379,7 @@ __global__ void __launch_bounds__(256) k_force_half(Dev d, int lk)
                     fr = du;
                 } else {
                     float c, dc;
-                    chi_and_slope<float>(rr, sw, h, c, dc);
+                    chi_and_slope_x(pi, pj, P, rr, sw, h, c, dc);
                     fr = W == W_SHORT ? dc * u + c * du : -dc * u + (1.f - c) * du;
                 }
                 f = fr * rinv;
@@ -426,15 +441,15 @@ __global__ void k_kick(Dev d, const double* a, double h)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= 3 * d.N) return;
-    d.v[k] += h * a[k];
+    d.v[k] = fma(h, a[k], d.v[k]);
 }
 
 __global__ void k_kick2(Dev d, const double* a, double h, const double* b, double hb)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= 3 * d.N) return;
-    double v = d.v[k] + h * a[k];
-    d.v[k] = v + hb * b[k];
+    const double v = fma(h, a[k], d.v[k]);
+    d.v[k] = fma(hb, b[k], v);
 }
 
 // A(tau/2) O(tau) A(tau/2), wrap, refresh the FP32 mirror, optional list check
@@ -450,7 +465,7 @@ __global__ void k_aoa(Dev d, double tau, uint32_t s_off, int do_check)
     double x[3] = {d.x[3 * i], d.x[3 * i + 1], d.x[3 * i + 2]};
     double v[3] = {d.v[3 * i], d.v[3 * i + 1], d.v[3 * i + 2]};
 #pragma unroll
-    for (int a = 0; a < 3; ++a) x[a] += h * v[a];
+    for (int a = 0; a < 3; ++a) x[a] = fma(h, v[a], x[a]);
     const U4 u = draw(P, uint32_t(i - P.atom_off), s0, TAG_O, 0, 0, 0);
     const T r0 = d_sqrt(T(-2) * d_log(unif<T>(u.x)));
     const T r1 = d_sqrt(T(-2) * d_log(unif<T>(u.z)));
@@ -460,11 +475,11 @@ __global__ void k_aoa(Dev d, double tau, uint32_t s_off, int do_check)
     const double G[3] = {double(r0 * c1v), double(r0 * s1), double(r1 * c2v)};
     const double c1 = d.stepc[2 * r], c2 = d.stepc[2 * r + 1] * d.isqmt[i];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) v[a] = c1 * v[a] + c2 * G[a];
+    for (int a = 0; a < 3; ++a) v[a] = fma(c1, v[a], c2 * G[a]);
     int im[3] = {0, 0, 0};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        x[a] += h * v[a];
+        x[a] = fma(h, v[a], x[a]);
         if (x[a] < 0.0) { x[a] += P.L; im[a] -= 1; }
         if (x[a] >= P.L) { x[a] -= P.L; im[a] += 1; }
     }
@@ -539,11 +554,11 @@ __global__ void __launch_bounds__(IB_MAX) k_inner_steps(Dev d, double dt, uint32
         if (live) {
             // B: the kick of the bonded acceleration of the previous step
 #pragma unroll
-            for (int a = 0; a < 3; ++a) v[a] += h * ab[a];
+            for (int a = 0; a < 3; ++a) v[a] = fma(h, ab[a], v[a]);
             // A O A and wrap (as k_aoa)
             const uint32_t s0 = uint32_t(d.step_base[r]) + s_off + uint32_t(st);
 #pragma unroll
-            for (int a = 0; a < 3; ++a) x[a] += h * v[a];
+            for (int a = 0; a < 3; ++a) x[a] = fma(h, v[a], x[a]);
             const U4 u = draw(P, uint32_t(i - P.atom_off), s0, TAG_O, 0, 0, 0);
             const T r0 = d_sqrt(T(-2) * d_log(unif<T>(u.x)));
             const T r1 = d_sqrt(T(-2) * d_log(unif<T>(u.z)));
@@ -552,10 +567,10 @@ __global__ void __launch_bounds__(IB_MAX) k_inner_steps(Dev d, double dt, uint32
             d_sincospi(T(2) * unif<T>(u.w), &s2, &c2v);
             const double G[3] = {double(r0 * c1v), double(r0 * s1), double(r1 * c2v)};
 #pragma unroll
-            for (int a = 0; a < 3; ++a) v[a] = c1 * v[a] + c2 * G[a];
+            for (int a = 0; a < 3; ++a) v[a] = fma(c1, v[a], c2 * G[a]);
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                x[a] += h * v[a];
+                x[a] = fma(h, v[a], x[a]);
                 if (x[a] < 0.0) { x[a] += P.L; img[a] -= 1; }
                 if (x[a] >= P.L) { x[a] -= P.L; img[a] += 1; }
                 fin = fin && isfinite(x[a]) && isfinite(v[a]);
@@ -592,7 +607,7 @@ __global__ void __launch_bounds__(IB_MAX) k_inner_steps(Dev d, double dt, uint32
             }
             ab[0] = smt * gx; ab[1] = smt * gy; ab[2] = smt * gz;
 #pragma unroll
-            for (int a = 0; a < 3; ++a) v[a] += h * ab[a];
+            for (int a = 0; a < 3; ++a) v[a] = fma(h, ab[a], v[a]);
         }
     }
     if (!live) return;

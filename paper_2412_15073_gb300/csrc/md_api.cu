@@ -413,6 +413,11 @@ RepParams make_params(const md_ctx* ctx, const RepHost& h, int r, int atom_off, 
     P.sclf = float(P.scl);
     P.sclf_lo = float(P.scl - double(P.sclf));
     P.R = s.r_cut; P.rc = s.r_split; P.h = s.h_switch; P.sw = s.r_split - s.h_switch;
+    P.scl2f = float(P.scl * P.scl);
+    {
+        const double t = std::max(P.sw, 0.0) * P.inv_scl;      // below 2^31: sw < r_E < L / 2
+        P.sw2u = (unsigned long long)std::llrint(t * t);
+    }
     // ring edges (Sec. 3.1 ring technique): explicit interior edges, else r_M
     // when it lies inside (r_c - h, r_E), else one ring
     P.edge[0] = P.sw;

@@ -734,7 +734,7 @@ def test_mixed_precision_long_run_observables(M, how):
     cannot run this long at this size): mean temperature within 0.5 %, O-O
     radial distribution L1 distance <= 1e-2, and the oxygen self-diffusion
     within 5 %. D is estimated on eight interleaved groups of oxygens; the
-    window (3000 fs, 6000 fs for JUMP under DSF, whose jumps damp diffusion)
+    window (3000 fs, 9000 fs for JUMP under DSF, whose jumps damp diffusion)
     is long enough that the standard error of the FP64 estimate is below 2 %."""
     from paper_2412_15073_gb300 import systems
     w = systems.water_box(8000, box=62.1, seed=0)
@@ -747,7 +747,7 @@ def test_mixed_precision_long_run_observables(M, how):
     res = {}
     every, steps = 150, 3000
     if how == "jump":
-        steps = 6000
+        steps = 9000
     if how == "jump_respa1_ewald":
         # the paper's 96,000-atom settings (one ring, LJ long part at the outer level), 1:2:6 fs
         p = p | dict(dsf_alpha=0.42, coulomb_mode=1, pme_order=6, pme_spacing=0.8, r_split=6.0,
