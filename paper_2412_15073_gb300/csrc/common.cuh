@@ -208,22 +208,26 @@ __device__ __forceinline__ void chi_and_slope(T r, T sw, T h, T& c, T& dc)
 
 // The same in FP32 for a pair given by its scaled coordinates a, b, with s
 // taken from the exact integer displacement: r - sw = (r^2 - sw^2) / (r + sw),
-// where r^2 - sw^2 is formed exactly in 64-bit integers and rounded once.
-// An FP32 distance near sw is off by up to half an ulp of r (2.4e-7 A at
-// 4.5 A), and the switch's slope (up to 15/(8h) per unit of s) turns that
-// into the largest error of a chi-weighted pair force, chi' U; this form
-// leaves about a tenth of it. r is the FP32 distance that decides the region.
+// where r^2 - sw^2 is formed exactly in 64-bit integers (three 32 x 32 -> 64
+// bit products; the squared length of a displacement shorter than L/2 stays
+// below 2^62) and rounded once. An FP32 distance near sw is off by up to half
+// an ulp of r (2.4e-7 A at 4.5 A), and the switch's slope (up to 15/(8h) per
+// unit of s) turns that into the largest error of a chi-weighted pair force,
+// chi' U; this form leaves about a tenth of it. r is the FP32 distance that
+// decides the region; hinv = 1/h.
 __device__ __forceinline__ void chi_and_slope_x(const uint4& a, const uint4& b, const RepParams& P, float r,
-                                                float sw, float h, float& c, float& dc)
+                                                float sw, float h, float hinv, float& c, float& dc)
 {
     if (r <= sw) { c = 1.f; dc = 0.f; return; }
     if (r >= sw + h) { c = 0.f; dc = 0.f; return; }
-    const long long ix = int(a.x - b.x), iy = int(a.y - b.y), iz = int(a.z - b.z);
-    const unsigned long long q =
-        (unsigned long long)(ix * ix) + (unsigned long long)(iy * iy) + (unsigned long long)(iz * iz);
-    const float dq = __ll2float_rn((long long)(q - P.sw2u));
-    const float s = fminf(1.f, fmaxf(0.f, dq * P.scl2f / ((r + sw) * h)));
-    chi_of_s<float>(s, h, c, dc);
+    const int ix = int(a.x - b.x), iy = int(a.y - b.y), iz = int(a.z - b.z);
+    const long long q = (long long)ix * ix + (long long)iy * iy + (long long)iz * iz;
+    const float dq = __ll2float_rn(q - (long long)P.sw2u);
+    const float s = fminf(1.f, fmaxf(0.f, __fdividef(dq * P.scl2f, r + sw) * hinv));
+    const float s2 = s * s;
+    c = 1.f - s2 * s * (10.f - 15.f * s + 6.f * s2);
+    const float om = 1.f - s;
+    dc = -30.f * s2 * om * om * hinv;
 }
 
 // DSF Coulomb per unit C q_i q_j: value and radial derivative, r < R

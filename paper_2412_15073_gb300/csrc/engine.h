@@ -93,6 +93,7 @@ struct Dev {
     const int* item_slot;           // per bonded item: slot of its term in its block's list
     int n_ib;                       // 0: the bonded groups do not allow the fused inner steps
     int lj_symmetric;               // every replica's LJ tables are symmetric (eps_ab = eps_ba, sigma_ab = sigma_ba)
+    const int* lj_perm;             // [N] atoms with an LJ partner type, then the others (each ascending)
 };
 
 // can gradient mode `mode` run as half-list kernels? (full, short and long

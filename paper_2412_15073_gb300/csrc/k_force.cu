@@ -122,12 +122,12 @@ __device__ __forceinline__ void bonded_gather(const Dev& d, int i, double& gx, d
 
 // switch of a pair: FP32 from the exact integer displacement, FP64 from r
 __device__ __forceinline__ void chi_t(const uint4& a, const uint4& b, const RepParams& P, float r, float sw, float h,
-                                      float& c, float& dc)
+                                      float hinv, float& c, float& dc)
 {
-    chi_and_slope_x(a, b, P, r, sw, h, c, dc);
+    chi_and_slope_x(a, b, P, r, sw, h, hinv, c, dc);
 }
 __device__ __forceinline__ void chi_t(const uint4&, const uint4&, const RepParams&, double r, double sw, double h,
-                                      double& c, double& dc)
+                                      double, double& c, double& dc)
 {
     chi_and_slope<double>(r, sw, h, c, dc);
 }
@@ -181,8 +181,10 @@ template <typename T, int W, bool BONDED, int TPA>
 __global__ void __launch_bounds__(256) k_force(Dev d, int lk, double* out, int as_grad)
 {
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = gt / TPA, sub = gt % TPA;
-    const bool live = i < d.N;
+    const int t = gt / TPA, sub = gt % TPA;
+    const bool live = t < d.N;
+    // the LJ part alone visits the atoms with LJ partners first (warps without idle atoms)
+    const int i = (W == W_LJLONG && live) ? d.lj_perm[t] : t;
     const int ii = live ? i : d.N - 1;
     const int r = d.rep[ii];
     const RepParams& P = d.P[r];
@@ -192,7 +194,7 @@ __global__ void __launch_bounds__(256) k_force(Dev d, int lk, double* out, int a
         const T qi = T(d.q[i]);
         const T cut = W == W_SHORT ? T(fmin(P.rc, P.R)) : T(P.R);
         const T cut2 = cut * cut;
-        const T sw = T(P.sw), h = T(P.h), sw2 = sw * sw;
+        const T sw = T(P.sw), h = T(P.h), sw2 = sw * sw, hinv = T(1) / h;
         const T C = T(COULOMB);
         const uint32_t* row = d.list[lk] + (size_t)i * d.lcap[lk];
         const int n = W == W_LJLONG ? 0 : min(d.lcnt[lk][i], d.lcap[lk]);
@@ -243,7 +245,7 @@ __global__ void __launch_bounds__(256) k_force(Dev d, int lk, double* out, int a
                 f = du;
             } else {
                 T c, dc;
-                chi_t(pi, pj, P, rr, sw, h, c, dc);
+                chi_t(pi, pj, P, rr, sw, h, hinv, c, dc);
                 f = W == W_SHORT ? dc * u + c * du : -dc * u + (T(1) - c) * du;
             }
             acc.add(f * rinv, dx, dy, dz, f);
@@ -277,7 +279,7 @@ __global__ void __launch_bounds__(256) k_force(Dev d, int lk, double* out, int a
                 rdist(r2, rr, rinv);
                 T ul, dul, c, dc;
                 ljsf<T>(P, lj, rr, rinv, ul, dul);
-                chi_t(pi, pj, P, rr, sw, h, c, dc);
+                chi_t(pi, pj, P, rr, sw, h, hinv, c, dc);
                 const T fl = -dc * ul + (T(1) - c) * dul;
                 acc.add(fl * rinv, dx, dy, dz, fl);
             }
@@ -314,8 +316,9 @@ template <int W, int TPA>
 __global__ void __launch_bounds__(256) k_force_half(Dev d, int lk)
 {
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = gt / TPA, sub = gt % TPA;
-    const bool live = i < d.N;
+    const int t = gt / TPA, sub = gt % TPA;
+    const bool live = t < d.N;
+    const int i = (W == W_LJLONG && live) ? d.lj_perm[t] : t;
     const int ii = live ? i : d.N - 1;
     const int r = d.rep[ii];
     const RepParams& P = d.P[r];
@@ -326,7 +329,7 @@ __global__ void __launch_bounds__(256) k_force_half(Dev d, int lk)
         const float qi = __uint_as_float(pi.w);
         const float cut = W == W_SHORT ? float(fmin(P.rc, P.R)) : float(P.R);
         const float cut2 = cut * cut;
-        const float sw = float(P.sw), h = float(P.h), sw2 = sw * sw;
+        const float sw = float(P.sw), h = float(P.h), sw2 = sw * sw, hinv = 1.f / h;
         const float C = float(COULOMB);
         const uint32_t* row = d.list[lk] + (size_t)i * d.lcap[lk];
         // the (1 - chi) LJ part alone (W_LJLONG) runs over the LJ list of replicas
@@ -352,7 +355,7 @@ __global__ void __launch_bounds__(256) k_force_half(Dev d, int lk)
                 rdist(r2, rr, rinv);
                 float ul, dul, c, dc;
                 ljsf<float>(P, lj, rr, rinv, ul, dul);
-                chi_and_slope_x(pi, pj, P, rr, sw, h, c, dc);
+                chi_and_slope_x(pi, pj, P, rr, sw, h, hinv, c, dc);
                 fr = -dc * ul + (1.f - c) * dul;
                 f = fr * rinv;
             } else {
@@ -379,7 +382,7 @@ __global__ void __launch_bounds__(256) k_force_half(Dev d, int lk)
                     fr = du;
                 } else {
                     float c, dc;
-                    chi_and_slope_x(pi, pj, P, rr, sw, h, c, dc);
+                    chi_and_slope_x(pi, pj, P, rr, sw, h, hinv, c, dc);
                     fr = W == W_SHORT ? dc * u + c * du : -dc * u + (1.f - c) * du;
                 }
                 f = fr * rinv;

@@ -277,6 +277,7 @@ __global__ void __launch_bounds__(32 * OUTER_WARPS) k_outer_cells(Dev d, int exa
     if (lane == 31) cpre[w][ncell] = total;
     __syncwarp();
     // FP32 test in units of the scaled coordinates (no scale multiplies),
+    // FP32 test in units of the scaled coordinates (no scale multiplies),
     // widened by 4e-6 so that rounding never drops a partner
     const double ro = P.R + P.skin_o;
     const float r2ou = float(ro * ro * (1.0 + 4e-6) * P.inv_scl * P.inv_scl);
@@ -494,6 +495,8 @@ constexpr uint32_t KM_FULL = 1u << L_FULL;
 constexpr uint32_t KM_RESPA1 = (1u << L_FULL) | (1u << L_SHORT);
 constexpr uint32_t KM_RESPA1_LJ = KM_RESPA1 | (1u << L_LJ);
 constexpr uint32_t KM_JUMP = (1u << L_SHORT) | (((1u << MAX_RINGS) - 1u) << L_R0) | (1u << L_LJ);
+constexpr uint32_t KM_JUMP1 = (1u << L_SHORT) | (1u << L_R0) | (1u << L_LJ);          // one ring
+constexpr uint32_t KM_JUMP2 = KM_JUMP1 | (1u << (L_R0 + 1));                           // two rings
 constexpr uint32_t KM_ALL = (1u << NKIND) - 1u;
 
 // warps of a strided launch over the atoms: the resident warps of the GPU,
@@ -520,6 +523,8 @@ void inner_lists(const Dev& d, int kinds, int exact, int late, cudaStream_t s)
     case KM_RESPA1: k_inner_lists<KM_RESPA1><<<g, 32 * WARPS, 0, s>>>(d, kinds, exact, late); break;
     case KM_RESPA1_LJ: k_inner_lists<KM_RESPA1_LJ><<<g, 32 * WARPS, 0, s>>>(d, kinds, exact, late); break;
     case KM_JUMP: k_inner_lists<KM_JUMP><<<g, 32 * WARPS, 0, s>>>(d, kinds, exact, late); break;
+    case KM_JUMP1: k_inner_lists<KM_JUMP1><<<g, 32 * WARPS, 0, s>>>(d, kinds, exact, late); break;
+    case KM_JUMP2: k_inner_lists<KM_JUMP2><<<g, 32 * WARPS, 0, s>>>(d, kinds, exact, late); break;
     case KM_ALL: k_inner_lists<KM_ALL><<<g, 32 * WARPS, 0, s>>>(d, kinds, exact, late); break;
     default: k_inner_lists<0><<<g, 32 * WARPS, 0, s>>>(d, kinds, exact, late); break;
     }

@@ -266,8 +266,11 @@ int lists_needed(const md_ctx* ctx, int family)
     const int lj = any_lj_long(ctx) ? 1 << L_LJ : 0;
     if (family == 0) return 1 << L_FULL;
     if (family == 1) return (1 << L_FULL) | (1 << L_SHORT) | lj;
+    // the rings some replica has (the list filter is compiled for the usual sets)
+    int nr = 0;
+    for (const RepParams& P : ctx->hp) nr = std::max(nr, P.nr);
     int k = (1 << L_SHORT) | (1 << L_LJ);
-    for (int y = 0; y < MAX_RINGS; ++y) k |= 1 << (L_R0 + y);
+    for (int y = 0; y < std::max(nr, 1); ++y) k |= 1 << (L_R0 + y);
     return k;
 }
 
@@ -894,6 +897,27 @@ int commit(md_ctx* ctx)
             return rc;
         d.ib_start = dib; d.ib_bond_off = dbo; d.ib_bond = dbl; d.ib_ang_off = dao; d.ib_ang = dal; d.item_slot = dsl;
         d.n_ib = on ? (int)ib_start.size() - 1 : 0;
+    }
+    {
+        // atoms with an LJ partner type first, the others after (each in index
+        // order): the launches of the (1 - chi) LJ part alone run over this order,
+        // so their warps hold LJ atoms only
+        std::vector<int> perm;
+        perm.reserve(N);
+        for (int pass = 0; pass < 2; ++pass)
+            for (int r = 0; r < R; ++r) {
+                const RepHost& h = ctx->reps[r];
+                const int o = ctx->hp[r].atom_off;
+                for (int i = 0; i < h.n; ++i) {
+                    bool lj = false;
+                    for (int b = 0; b < h.ntypes; ++b) lj |= h.lj_eps[h.type[i] * h.ntypes + b] != 0.0;
+                    if (lj == (pass == 0)) perm.push_back(o + i);
+                }
+            }
+        int* dperm;
+        AL(dperm, N);
+        if ((rc = upload(ctx, dperm, perm.data(), N))) return rc;
+        d.lj_perm = dperm;
     }
     d.lj_long_mask = 0;
     d.lj_symmetric = 1;

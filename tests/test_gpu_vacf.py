@@ -67,7 +67,9 @@ def test_mixed_record_equals_the_states_of_single_steps(M, oracle_mod, water648)
     assert T1 == T2 == 64
     np.testing.assert_array_equal(C1, C2)
     np.testing.assert_array_equal(S1, S2)
-    np.testing.assert_allclose(C1, Co, rtol=2e-6)
+    # the FP32 record rounds each velocity once, an error on the scale of C(0)
+    # (the lags near a zero crossing of C have no relative accuracy to keep)
+    np.testing.assert_allclose(C1, Co, rtol=0, atol=1e-6 * Co[0])
 
 
 def test_record_capacity_and_end(M, water648):
