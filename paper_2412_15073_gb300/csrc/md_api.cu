@@ -142,6 +142,12 @@ struct md_ctx {
     // CUDA graphs of driver chunks (see run_units); gen changes whenever the
     // device layout does, which invalidates every captured graph
     cudaStream_t gs = nullptr;
+    // second stream of the reciprocal sum: forked from the main stream once the
+    // positions of a slow step are final, joined before the slow kick
+    cudaStream_t s2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    bool recip_open = false;
+    double* arecip = nullptr;       // [N][3] reciprocal acceleration of the slow level
     long long gen = 0;
     struct Graph { long long gen; int key; double tau; int n_inner, units; cudaGraphExec_t exec;
                    long long launches[NPROF]; };
@@ -954,6 +960,17 @@ int commit(md_ctx* ctx)
             ctx->pme_orders.push_back(P.pme_p);
     }
     ctx->pme_total = gtot;
+    if (!ctx->ewald_reps.empty()) {
+        AL(ctx->arecip, 3 * (size_t)N);
+        if (!ctx->s2) {
+            // the higher priority lets its blocks in as soon as the main stream's free an SM
+            int lo = 0, hi = 0;
+            CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+            CK(cudaStreamCreateWithPriority(&ctx->s2, cudaStreamNonBlocking, hi));
+        }
+        if (!ctx->ev_fork) CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+        if (!ctx->ev_join) CK(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+    }
     {
         double* dG;
         float* dGf;
@@ -1192,41 +1209,42 @@ const md_ctx::FftPlan* fft_plan(const md_ctx* ctx, int K)
 
 // smooth PME on every Ewald replica: with out, the gradient (added to out, as
 // -grad / m~ unless as_grad); with energy, the reciprocal energies into d.pme_e
-int pme(md_ctx* ctx, double* out, int as_grad, int energy)
+int pme(md_ctx* ctx, double* out, int as_grad, int energy, cudaStream_t st = nullptr)
 {
     Dev& d = ctx->d;
+    const cudaStream_t S = st ? st : ctx->s;
     const int no = (int)ctx->pme_orders.size();
     Prof p(ctx, 6, 5 + no + (out ? no : 0));
-    launch_pme_bin(d, ctx->fp64, ctx->s);
-    for (int order : ctx->pme_orders) launch_pme_spread(d, order, ctx->fp64, ctx->s);
-    launch_pme_tofloat(d, ctx->pme_total, ctx->fp64, ctx->s);
+    launch_pme_bin(d, ctx->fp64, S);
+    for (int order : ctx->pme_orders) launch_pme_spread(d, order, ctx->fp64, S);
+    launch_pme_tofloat(d, ctx->pme_total, ctx->fp64, S);
     // the FP32 grids of mixed mode live in the same buffers, at the same element offsets
     float* qf = reinterpret_cast<float*>(d.pme_q);
     cufftComplex* sf = reinterpret_cast<cufftComplex*>(d.pme_spec);
     for (int r : ctx->ewald_reps) {
         const RepParams& P = ctx->hp[r];
         const md_ctx::FftPlan* f = fft_plan(ctx, P.pme_K);
-        const cufftResult e = cufftSetStream(f->d2z, ctx->s) != CUFFT_SUCCESS ? CUFFT_INTERNAL_ERROR
+        const cufftResult e = cufftSetStream(f->d2z, S) != CUFFT_SUCCESS ? CUFFT_INTERNAL_ERROR
             : ctx->fp64 ? cufftExecD2Z(f->d2z, d.pme_q + P.pme_goff, (cufftDoubleComplex*)(d.pme_spec + P.pme_soff))
                         : cufftExecR2C(f->d2z, qf + P.pme_goff, sf + P.pme_soff);
         if (e != CUFFT_SUCCESS) FAIL(MD_ECUDA, "cuFFT forward transform failed (%d)", (int)e);
     }
-    launch_pme_convolve_grid(d, energy, ctx->pme_max_spec, ctx->fp64, ctx->s);
+    launch_pme_convolve_grid(d, energy, ctx->pme_max_spec, ctx->fp64, S);
     if (!out) return MD_OK;
     for (int r : ctx->ewald_reps) {
         const RepParams& P = ctx->hp[r];
         const md_ctx::FftPlan* f = fft_plan(ctx, P.pme_K);
-        const cufftResult e = cufftSetStream(f->z2d, ctx->s) != CUFFT_SUCCESS ? CUFFT_INTERNAL_ERROR
+        const cufftResult e = cufftSetStream(f->z2d, S) != CUFFT_SUCCESS ? CUFFT_INTERNAL_ERROR
             : ctx->fp64 ? cufftExecZ2D(f->z2d, (cufftDoubleComplex*)(d.pme_spec + P.pme_soff), d.pme_q + P.pme_goff)
                         : cufftExecC2R(f->z2d, sf + P.pme_soff, qf + P.pme_goff);
         if (e != CUFFT_SUCCESS) FAIL(MD_ECUDA, "cuFFT inverse transform failed (%d)", (int)e);
     }
-    for (int order : ctx->pme_orders) launch_pme_gather(d, order, out, as_grad, ctx->fp64, ctx->s);
+    for (int order : ctx->pme_orders) launch_pme_gather(d, order, out, as_grad, ctx->fp64, S);
     return MD_OK;
 }
 
 // gradient mode into out (as -grad / m~ unless as_grad); mode 6 = the reciprocal part alone
-void force_into(md_ctx* ctx, int mode, double* out, int as_grad)
+void force_into(md_ctx* ctx, int mode, double* out, int as_grad, bool with_recip = true)
 {
     if (mode == 6) {
         // the slow level: the (1 - chi) LJ part of lj_long_mode 2 replicas (zero elsewhere), then PME
@@ -1245,13 +1263,53 @@ void force_into(md_ctx* ctx, int mode, double* out, int as_grad)
         Prof p(ctx, mode == 1 ? 1 : 0, ((bonded && ctx->d.nbond + ctx->d.nang > 0) ? 2 : 1) + (half ? 1 : 0));
         launch_force(ctx->d, mode, out, as_grad, ctx->fp64, t, ctx->s);
     }
-    if (mode_has_recip(ctx, mode)) {
+    if (with_recip && mode_has_recip(ctx, mode)) {
         const int rc = pme(ctx, out, as_grad, 0);
         if (rc && !ctx->deferred) ctx->deferred = rc;
     }
 }
 
 void force(md_ctx* ctx, int mode, double* out) { force_into(ctx, mode, out, 0); }
+
+// The slow level of the multiple-time-step drivers with a reciprocal part:
+// the pair part goes to `al`, the reciprocal part to ctx->arecip, and the slow
+// kick adds both. recip_begin starts the reciprocal sum at the current
+// positions; unless per-class times are being taken, it runs on the second
+// stream, overlapping what the main stream runs meanwhile (the velocity phase
+// and the slow pair part; it reads only positions and its own grids). recip_end joins it back before its result is used. The
+// arithmetic is the same either way.
+void recip_begin(md_ctx* ctx)
+{
+    if (ctx->ewald_reps.empty()) return;
+    const bool side = !ctx->prof && ctx->s2;
+    const cudaStream_t st = side ? ctx->s2 : ctx->s;
+    if (side) {
+        cudaEventRecord(ctx->ev_fork, ctx->s);
+        cudaStreamWaitEvent(ctx->s2, ctx->ev_fork, 0);
+    }
+    cudaMemsetAsync(ctx->arecip, 0, sizeof(double) * 3 * (size_t)ctx->d.N, st);
+    const int rc = pme(ctx, ctx->arecip, 0, 0, st);
+    if (rc && !ctx->deferred) ctx->deferred = rc;
+    if (side) {
+        cudaEventRecord(ctx->ev_join, ctx->s2);
+        ctx->recip_open = true;
+    }
+}
+
+void recip_end(md_ctx* ctx)
+{
+    if (!ctx->recip_open) return;
+    cudaStreamWaitEvent(ctx->s, ctx->ev_join, 0);
+    ctx->recip_open = false;
+}
+
+// the slow kick: the pair part, plus the reciprocal part when there is one
+void slow_kick(md_ctx* ctx, double h)
+{
+    Prof p(ctx, 3, 1);
+    if (ctx->ewald_reps.empty()) launch_kick(ctx->d, ctx->d.al, h, ctx->s);
+    else launch_kick2(ctx->d, ctx->d.al, h, ctx->arecip, h, ctx->s);
+}
 
 // the error a driver body left behind (its message is already in ctx->msg)
 int take_deferred(md_ctx* ctx)
@@ -1801,23 +1859,27 @@ int md_step_baoab_respa1(md_ctx* ctx, int64_t n_outer, double dt_inner_fs, int m
     if ((rc = set_stepc(ctx, dt))) return rc;
     force(ctx, 1, d.ab);
     force(ctx, 3, d.as);
-    force(ctx, 4, d.al);
+    force_into(ctx, 4, d.al, 0, false);
+    recip_begin(ctx);
+    recip_end(ctx);
     const int spu = n_outer_ratio * m_mid;
     return run_units(ctx, 3 | (m_mid << 8), dt, spu, n_outer, [&](long long u0, long long n) {
         uint32_t s = uint32_t(u0 * spu);
         for (long long o = 0; o < n; ++o) {
-            kick(ctx, d.al, 0.5 * D);
+            slow_kick(ctx, 0.5 * D);
             for (int j = 0; j < n_outer_ratio; ++j) {
                 kick(ctx, d.as, 0.5 * kap);
                 inner_steps(ctx, dt, s, m_mid);
                 s += m_mid;
                 rebuild_step(ctx);
                 force(ctx, 3, d.as);
+                if (j == n_outer_ratio - 1) recip_begin(ctx);     // positions of the slow step are final
                 kick(ctx, d.as, 0.5 * kap);
                 if (j < n_outer_ratio - 1) record(ctx, s - 1);
             }
-            force(ctx, 4, d.al);
-            kick(ctx, d.al, 0.5 * D);
+            force_into(ctx, 4, d.al, 0, false);
+            recip_end(ctx);
+            slow_kick(ctx, 0.5 * D);
             record(ctx, s - 1);
         }
     });
@@ -1837,7 +1899,11 @@ static int jump_respa_cycles(md_ctx* ctx, int64_t n_outer, double dt_inner_fs, i
     if ((rc = set_stepc(ctx, dt))) return rc;
     force(ctx, 1, d.ab);
     force(ctx, 3, d.as);
-    if (ew) force(ctx, 6, d.al);
+    if (ew) {
+        force_into(ctx, 6, d.al, 0, false);
+        recip_begin(ctx);
+        recip_end(ctx);
+    }
     // with no outer force a unit is one mid cycle; else one outer step of ratio cycles
     const int per = ew ? ratio : 1;
     const long long units = ew ? n_outer : n_outer * ratio;
@@ -1847,7 +1913,7 @@ static int jump_respa_cycles(md_ctx* ctx, int64_t n_outer, double dt_inner_fs, i
     return run_units(ctx, 4 | (n_inner << 8), dt, per * n_inner, units, [&](long long u0, long long n) {
         uint32_t s = uint32_t(u0 * per * n_inner);
         for (long long o = 0; o < n; ++o) {
-            if (ew) kick(ctx, d.al, 0.5 * D);
+            if (ew) slow_kick(ctx, 0.5 * D);
             for (int j = 0; j < per; ++j) {
                 const uint32_t s0 = s;
                 const bool carried = fuse && (ew ? j > 0 : o > 0);
@@ -1857,13 +1923,15 @@ static int jump_respa_cycles(md_ctx* ctx, int64_t n_outer, double dt_inner_fs, i
                 s += n_inner;
                 rebuild_step(ctx);
                 force(ctx, 3, d.as);
+                if (ew && j == per - 1) recip_begin(ctx);        // positions of the slow step are final
                 if (pass_on) vphase(ctx, d.as, 0.5 * kap, s0, 1, 2, s);
                 else vphase(ctx, d.as, 0.5 * kap, s0, 1, 1);
                 if (j < per - 1) record(ctx, s - 1);
             }
             if (ew) {
-                force(ctx, 6, d.al);
-                kick(ctx, d.al, 0.5 * D);
+                force_into(ctx, 6, d.al, 0, false);
+                recip_end(ctx);
+                slow_kick(ctx, 0.5 * D);
             }
             record(ctx, s - 1);
         }
@@ -2175,6 +2243,9 @@ int md_finalize(md_ctx* ctx)
     cudaStreamSynchronize(ctx->s);
     for (auto& f : ctx->fft) { cufftDestroy(f.d2z); cufftDestroy(f.z2d); }
     if (ctx->gs) cudaStreamDestroy(ctx->gs);
+    if (ctx->s2) { cudaStreamSynchronize(ctx->s2); cudaStreamDestroy(ctx->s2); }
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     for (auto& p : ctx->pend) { ctx->ev_pool.push_back(p.a); ctx->ev_pool.push_back(p.b); }
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     cudaFreeHost(ctx->h_stepc);
