@@ -90,6 +90,11 @@ CPHASE_INST_PER_PROPOSAL = 148.3e6 * 13.7 / 3.574e6
 INNER_BYTES_PER_CAND = 4
 INNER_BYTES_PER_ENTRY = 4
 INNER_BYTES_PER_ATOM = 16 + 12
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) that one ncu
+# capture measured for one rebuild launch of k_inner_lists<69> (short list, one
+# ring, LJ list) on the headline workload; taken again whenever that kernel
+# changes
+INNER_TRAFFIC_NCU = 265.834e6 + 183.101e6
 
 
 def ns_per_day(fs_simulated: float, seconds: float) -> float:
@@ -208,12 +213,24 @@ def pair_counts(x, box, r, n_mol_atoms=3):
     return int((~same).sum())
 
 
-def diffusion(e, integ, steps, every, box, dt_fs, mass=None, replica=0):
+def _einstein_D(X, every, dt_fs):
+    """D (1e-5 cm^2/s) from unwrapped positions X[t, atom, 3] sampled every `every` steps"""
+    nt = X.shape[0]
+    lags = np.arange(1, nt)
+    msd = np.array([((X[l:] - X[:-l]) ** 2).sum(-1).mean() for l in lags])
+    t = lags * every * dt_fs * 1e-3                     # ps
+    sel = (lags >= 0.2 * (nt - 1)) & (lags <= 0.8 * (nt - 1))
+    slope = np.polyfit(t[sel], msd[sel], 1)[0]          # A^2 / ps
+    return slope / 6.0 * 10.0                           # A^2/ps = 1e-4 cm^2/s -> units of 1e-5 cm^2/s
+
+
+def diffusion(e, integ, steps, every, box, dt_fs, mass=None, replica=0, se=False):
     """Self-diffusion constant of the oxygens (atoms 0, 3, 6, ...) from the
     Einstein relation: MSD of the unwrapped positions over all time origins,
     slope of a linear fit over 20-80 % of the lag window, D = slope / 6.
     Returns D in 1e-5 cm^2/s; with the masses (amu), (D, mean temperature over
-    the same samples, 3N degrees of freedom)."""
+    the same samples, 3N degrees of freedom); with se, also the standard error
+    of D from eight interleaved groups of oxygens."""
     xs, ts = [], []
     for k in range(steps // every + 1):
         x, v, img, _ = e.state(replica) if replica else e.state()
@@ -223,14 +240,13 @@ def diffusion(e, integ, steps, every, box, dt_fs, mass=None, replica=0):
         if k < steps // every:
             integ(every)
     X = np.stack(xs)
-    nt = X.shape[0]
-    lags = np.arange(1, nt)
-    msd = np.array([((X[l:] - X[:-l]) ** 2).sum(-1).mean() for l in lags])
-    t = lags * every * dt_fs * 1e-3                     # ps
-    sel = (lags >= 0.2 * (nt - 1)) & (lags <= 0.8 * (nt - 1))
-    slope = np.polyfit(t[sel], msd[sel], 1)[0]          # A^2 / ps
-    D = slope / 6.0 * 10.0                              # A^2/ps = 1e-4 cm^2/s -> units of 1e-5 cm^2/s
-    return D if mass is None else (D, float(np.mean(ts)))
+    D = _einstein_D(X, every, dt_fs)
+    if mass is None:
+        return D
+    if not se:
+        return D, float(np.mean(ts))
+    Dg = np.array([_einstein_D(X[:, g::8], every, dt_fs) for g in range(8)])
+    return D, float(np.mean(ts)), float(Dg.std(ddof=1) / np.sqrt(8))
 
 
 def matched_flags(run: dict, ref: dict) -> None:
@@ -238,6 +254,9 @@ def matched_flags(run: dict, ref: dict) -> None:
     if run.get("D") and ref.get("D") and ref.get("T_mean"):
         run["D_ratio"] = run["D"] / ref["D"]
         run["T_ratio"] = run["T_mean"] / ref["T_mean"]
+        if run.get("D_se") is not None and ref.get("D_se") is not None:
+            # standard error of the ratio (the two runs are independent)
+            run["D_ratio_se"] = run["D_ratio"] * float(np.hypot(run["D_se"] / run["D"], ref["D_se"] / ref["D"]))
         run["matched"] = bool(abs(run["D_ratio"] - 1) <= 0.05 and abs(run["T_ratio"] - 1) <= 0.005)
 
 
@@ -472,7 +491,8 @@ def ewald_runs(args, M, engine, stream, world, max_over_ranks, barrier, mass, bo
             if d_fs > 0 and r["stable"]:
                 every = 96 if d_fs >= 960 else 24       # a multiple of every cycle length (1, 4, 6 fs)
                 nd = d_fs // every * every
-                r["D"], r["T_mean"] = diffusion(e, lambda k: run(k // per_cycle), nd, every, box, DT_FS, mass)
+                r["D"], r["T_mean"], r["D_se"] = diffusion(e, lambda k: run(k // per_cycle), nd, every, box,
+                                                           DT_FS, mass, se=True)
             res[name] = r
         except M.MDError as ex:
             res[name] = {"error": str(ex), "stable": False}
@@ -883,7 +903,9 @@ def inner_list_roofline(ms_total, groups, rebuilds, w, x, e, hbm, peak_kind):
     nbytes = n * (INNER_BYTES_PER_CAND * n_outer + INNER_BYTES_PER_ENTRY * n_inner + INNER_BYTES_PER_ATOM)
     achieved = nbytes / per_rebuild_s / 1e9
     return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": None, "kernel": "k_inner_lists (inner list filter of the list rebuild)",
+            "traffic": INNER_TRAFFIC_NCU, "traffic_source": "ncu, one rebuild launch of k_inner_lists<69> "
+                                                             "(one-ring JUMP lists) on this workload",
+            "kernel": "k_inner_lists (inner list filter of the list rebuild)",
             "bytes_per_launch": nbytes, "outer_candidates_per_atom": n_outer, "inner_entries_per_atom": n_inner,
             "ms_per_launch": per_rebuild_s * 1e3, "launches": int(groups), "rebuilds": int(rebuilds),
             "ms_all_launches": ms_total, "peak_kind": peak_kind,
