@@ -94,7 +94,27 @@ struct Dev {
     int n_ib;                       // 0: the bonded groups do not allow the fused inner steps
     int lj_symmetric;               // every replica's LJ tables are symmetric (eps_ab = eps_ba, sigma_ab = sigma_ba)
     const int* lj_perm;             // [N] atoms with an LJ partner type, then the others (each ascending)
+    // cluster tiles of the mixed-mode pair kernels (k_lists.cu builds them):
+    // the atoms of each outer cell in clusters of TILE_CL, ordered by sub-cell
+    // (Morton code) and index; replica r owns clusters [cl_roff[r], cl_roff[r + 1])
+    int ncl_cap;
+    const int* cl_roff;             // [R + 1]
+    int* cl_start;                  // [total_cells] first cluster of each cell
+    int* cl_atom;                   // [ncl_cap][TILE_CL] atom in each slot (-1: empty)
+    int* cl_of;                     // [N] cluster of each atom
+    int* cl_slot;                   // [N] its slot
+    int* cl_cell;                   // [ncl_cap] cell of each cluster (-1: unused)
+    uint4* cl_ref;                  // [ncl_cap] scaled position of slot 0
+    int4 *cl_lo, *cl_hi;            // [ncl_cap] box of the members, scaled units relative to cl_ref
+    // half lists of cluster pairs (J >= I) at the short (0) and full (1) list radii
+    int* cpl_j[2];
+    unsigned long long* cpl_mask[2];
+    int* cpl_n[2];
+    int cpl_cap[2];
+    int tiles;                      // bit t: list t is kept up to date with the lists
 };
+
+constexpr int TILE_CL = 8;          // atoms per cluster
 
 // can gradient mode `mode` run as half-list kernels? (full, short and long
 // pair weights and the (1 - chi) LJ part alone (7); not the short weight of
@@ -119,6 +139,12 @@ void launch_rebuild_cells(const Dev& d, int keep_refs, int exact_outer, cudaStre
 void launch_rebuild_inner(const Dev& d, int kinds, int exact, cudaStream_t s);
 void launch_rebuild_done(const Dev& d, cudaStream_t s);
 void launch_late_lists(const Dev& d, int kinds, cudaStream_t s);
+// cluster tiles: clusters of the outer cells (where an outer rebuild happens),
+// then their boxes and the cluster-pair lists `tiles` (bit 0 short, bit 1 full)
+// where an inner rebuild happens
+void launch_tiles(const Dev& d, int tiles, cudaStream_t s);
+void launch_tiles_late(const Dev& d, int tiles, cudaStream_t s);     // whatever the flags say
+constexpr uint32_t OVF_TILE = 1u << 19;
 
 // ---- forces and integrators (k_force.cu) -----------------------------------------
 // mode: 0 full, 1 bonded, 2 nb full, 3 nb short, 4 nb long, 5 F0 (bonded + short),
@@ -127,6 +153,7 @@ void launch_late_lists(const Dev& d, int kinds, cudaStream_t s);
 // (mixed mode; the same values bit for bit, see k_force_half).
 // returns the number of kernels launched
 constexpr int FORCE_HALF = 16;
+constexpr int FORCE_TILE = 32;      // the cluster-tile kernels (mixed mode; the same values bit for bit)
 int launch_force(const Dev& d, int mode, double* out, int as_grad, int fp64, int tpa, cudaStream_t s);
 void launch_kick(const Dev& d, const double* a, double h, cudaStream_t s);
 void launch_kick2(const Dev& d, const double* a, double h, const double* b, double hb, cudaStream_t s);

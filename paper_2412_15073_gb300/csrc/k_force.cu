@@ -301,6 +301,62 @@ __global__ void __launch_bounds__(256) k_force(Dev d, int lk, double* out, int a
     }
 }
 
+// One pair of the half-list and tile kernels (mixed mode), i - j from the
+// scaled coordinates: false when it does not contribute (beyond the cutoff of
+// the weight, inside r_c - h for the long weight, no LJ pair for the LJ part
+// alone); else f = (dU/dr)/r, fr = dU/dr and the displacement (dx, dy, dz).
+template <int W>
+__device__ __forceinline__ bool pair_term(const Dev& d, const RepParams& P, const uint4& pi, int ti, const uint4& pj,
+                                          int j, float sc, float cut2, float sw, float h, float sw2, float hinv,
+                                          float R2, float& dx, float& dy, float& dz, float& f, float& fr)
+{
+    const float C = float(COULOMB);
+    sdisp(pi, pj, sc, P.sclf_lo, dx, dy, dz);
+    const float qi = __uint_as_float(pi.w), qj = __uint_as_float(pj.w);
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    if (W == W_LJLONG) {
+        if (r2 >= R2 || r2 <= sw2) return false;
+        const LJPair& lj = P.lj[ti * MAX_TYPES + d.type[j]];
+        if (!lj.on) return false;
+        float rr, rinv;
+        rdist(r2, rr, rinv);
+        float ul, dul, c, dc;
+        ljsf<float>(P, lj, rr, rinv, ul, dul);
+        chi_and_slope_x(pi, pj, P, rr, sw, h, hinv, c, dc);
+        fr = -dc * ul + (1.f - c) * dul;
+        f = fr * rinv;
+        return true;
+    }
+    if (r2 >= cut2) return false;
+    if (W == W_LONG && r2 <= sw2) return false;
+    float rr, rinv;
+    rdist(r2, rr, rinv);
+    float u = 0.f, du = 0.f;
+    const float qq = qi * qj;
+    if (qq != 0.f) {
+        float uc, duc;
+        dsf<float>(P, rr, rinv, uc, duc);
+        u = C * qq * uc;
+        du = C * qq * duc;
+    }
+    const LJPair& lj = P.lj[ti * MAX_TYPES + d.type[j]];
+    if (lj.on && !(W == W_LONG && P.lj_long == 1)) {
+        float ul, dul;
+        ljsf<float>(P, lj, rr, rinv, ul, dul);
+        u += ul;
+        du += dul;
+    }
+    if (W == W_FULL) {
+        fr = du;
+    } else {
+        float c, dc;
+        chi_and_slope_x(pi, pj, P, rr, sw, h, hinv, c, dc);
+        fr = W == W_SHORT ? dc * u + c * du : -dc * u + (1.f - c) * du;
+    }
+    f = fr * rinv;
+    return true;
+}
+
 // The same pair gradient over half of each list: the threads of atom i take
 // only the partners j > i and add the pair's fixed-point contribution to both
 // atoms (64-bit integer atomics into d.facc), so every unique pair is
@@ -326,11 +382,9 @@ __global__ void __launch_bounds__(256) k_force_half(Dev d, int lk)
     if (live) {
         const int ti = d.type[i];
         const uint4 pi = d.pos[i];
-        const float qi = __uint_as_float(pi.w);
         const float cut = W == W_SHORT ? float(fmin(P.rc, P.R)) : float(P.R);
         const float cut2 = cut * cut;
         const float sw = float(P.sw), h = float(P.h), sw2 = sw * sw, hinv = 1.f / h;
-        const float C = float(COULOMB);
         const uint32_t* row = d.list[lk] + (size_t)i * d.lcap[lk];
         // the (1 - chi) LJ part alone (W_LJLONG) runs over the LJ list of replicas
         // with lj_long_mode 2 only (zero elsewhere, as in k_force)
@@ -342,51 +396,8 @@ __global__ void __launch_bounds__(256) k_force_half(Dev d, int lk)
             const int j = int(row[k]);
             if (j <= i) continue;
             const uint4 pj = d.pos[j];
-            float dx, dy, dz;
-            sdisp(pi, pj, sc, P.sclf_lo, dx, dy, dz);
-            const float qj = __uint_as_float(pj.w);
-            const float r2 = dx * dx + dy * dy + dz * dz;
-            float f, fr;
-            if (W == W_LJLONG) {
-                if (r2 >= R2 || r2 <= sw2) continue;
-                const LJPair& lj = P.lj[ti * MAX_TYPES + d.type[j]];
-                if (!lj.on) continue;
-                float rr, rinv;
-                rdist(r2, rr, rinv);
-                float ul, dul, c, dc;
-                ljsf<float>(P, lj, rr, rinv, ul, dul);
-                chi_and_slope_x(pi, pj, P, rr, sw, h, hinv, c, dc);
-                fr = -dc * ul + (1.f - c) * dul;
-                f = fr * rinv;
-            } else {
-                if (r2 >= cut2) continue;
-                if (W == W_LONG && r2 <= sw2) continue;
-                float rr, rinv;
-                rdist(r2, rr, rinv);
-                float u = 0.f, du = 0.f;
-                const float qq = qi * qj;
-                if (qq != 0.f) {
-                    float uc, duc;
-                    dsf<float>(P, rr, rinv, uc, duc);
-                    u = C * qq * uc;
-                    du = C * qq * duc;
-                }
-                const LJPair& lj = P.lj[ti * MAX_TYPES + d.type[j]];
-                if (lj.on && !(W == W_LONG && P.lj_long == 1)) {
-                    float ul, dul;
-                    ljsf<float>(P, lj, rr, rinv, ul, dul);
-                    u += ul;
-                    du += dul;
-                }
-                if (W == W_FULL) {
-                    fr = du;
-                } else {
-                    float c, dc;
-                    chi_and_slope_x(pi, pj, P, rr, sw, h, hinv, c, dc);
-                    fr = W == W_SHORT ? dc * u + c * du : -dc * u + (1.f - c) * du;
-                }
-                f = fr * rinv;
-            }
+            float dx, dy, dz, f, fr;
+            if (!pair_term<W>(d, P, pi, ti, pj, j, sc, cut2, sw, h, sw2, hinv, R2, dx, dy, dz, f, fr)) continue;
             const float gx = f * dx, gy = f * dy, gz = f * dz;
             acc.add(f, dx, dy, dz, fr);
             unsigned long long* fj = reinterpret_cast<unsigned long long*>(d.facc) + 3 * (size_t)j;
@@ -405,6 +416,97 @@ __global__ void __launch_bounds__(256) k_force_half(Dev d, int lk)
     if (acc.x) atomicAdd(fi, (unsigned long long)acc.x);
     if (acc.y) atomicAdd(fi + 1, (unsigned long long)acc.y);
     if (acc.z) atomicAdd(fi + 2, (unsigned long long)acc.z);
+}
+
+// The same half-list pair gradient over cluster tiles. The atoms of each
+// outer cell form clusters of TILE_CL (k_lists.cu); list `tl` holds, for each
+// cluster I, the clusters J >= I whose boxes come within the list radius, with
+// a 64-bit mask of the slot pairs (a, b) to take (both slots occupied, not an
+// excluded pair, b > a when J = I). One warp per cluster I: lane (a, g) holds
+// atom a of I and takes slots b = g and g + 4 of each J, so the eight i atoms
+// and a J's positions are loaded once per tile instead of once per pair. Each
+// pair is the pair_term of k_force_half with the displacement i - j, and each
+// atom receives the same fixed-point terms (the j side negated exactly) into
+// d.facc: the sums are bit for bit those of the per-atom kernels.
+// Measured on 96,000-atom water: 2-2.5 times slower than the per-atom
+// half-list kernels (short list 0.27 against 0.11 ms, full list 0.70 against
+// 0.36 ms). Most of a tile's 64 slot pairs lie beyond the cutoff (clusters of
+// eight atoms span ~4 A; 15-35 % of the slots are pairs within it), and every
+// slot pays the j-side shuffle reduction whether it contributes or not; a
+// version that loaded the next tile's atoms ahead was slower still. The
+// tiles are therefore opt-in (MDJ_TILES) and the autotuner times them only
+// then.
+template <int W>
+__global__ void __launch_bounds__(128) k_force_tile(Dev d, int tl)
+{
+    const int lane = threadIdx.x & 31, a = lane & 7, g = lane >> 3;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    for (int I = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); I < d.ncl_cap; I += nw) {
+        const int cell = d.cl_cell[I];
+        if (cell < 0) continue;
+        const int r = d.cell_rep[cell];
+        const RepParams& P = d.P[r];
+        const int i = d.cl_atom[TILE_CL * (size_t)I + a];
+        const uint4 pi = i >= 0 ? d.pos[i] : make_uint4(0, 0, 0, 0);
+        const int ti = i >= 0 ? d.type[i] : 0;
+        const float cut = W == W_SHORT ? float(fmin(P.rc, P.R)) : float(P.R);
+        const float cut2 = cut * cut;
+        const float sw = float(P.sw), h = float(P.h), sw2 = sw * sw, hinv = 1.f / h;
+        const float sc = P.sclf;
+        const float R2 = float(P.R) * float(P.R);
+        const int n = min(d.cpl_n[tl][I], d.cpl_cap[tl]);
+        const int* jrow = d.cpl_j[tl] + (size_t)I * d.cpl_cap[tl];
+        const unsigned long long* mrow = d.cpl_mask[tl] + (size_t)I * d.cpl_cap[tl];
+        Acc<float> acc;
+        for (int t = 0; t < n; ++t) {
+            const int J = jrow[t];
+            const unsigned long long mask = mrow[t];
+#pragma unroll
+            for (int pass = 0; pass < 2; ++pass) {
+                const int b = g + 4 * pass;
+                const int j = d.cl_atom[TILE_CL * (size_t)J + b];
+                long long jx = 0, jy = 0, jz = 0;
+                if ((mask >> (TILE_CL * a + b)) & 1ull) {
+                    const uint4 pj = d.pos[j];
+                    float dx, dy, dz, f, fr;
+                    if (pair_term<W>(d, P, pi, ti, pj, j, sc, cut2, sw, h, sw2, hinv, R2, dx, dy, dz, f, fr)) {
+                        const float gx = f * dx, gy = f * dy, gz = f * dz;
+                        acc.add(f, dx, dy, dz, fr);
+                        jx = -to_fix(gx); jy = -to_fix(gy); jz = -to_fix(gz);
+                    }
+                }
+                // the terms on atom j, summed over the eight i atoms of its lane group
+#pragma unroll
+                for (int o = 1; o < TILE_CL; o <<= 1) {
+                    jx += __shfl_xor_sync(0xffffffffu, jx, o);
+                    jy += __shfl_xor_sync(0xffffffffu, jy, o);
+                    jz += __shfl_xor_sync(0xffffffffu, jz, o);
+                }
+                if (a == 0 && j >= 0 && (jx | jy | jz)) {
+                    unsigned long long* fj = reinterpret_cast<unsigned long long*>(d.facc) + 3 * (size_t)j;
+                    if (jx) atomicAdd(fj, (unsigned long long)jx);
+                    if (jy) atomicAdd(fj + 1, (unsigned long long)jy);
+                    if (jz) atomicAdd(fj + 2, (unsigned long long)jz);
+                }
+            }
+        }
+        if (acc.overflow()) {
+            atomicOr(&d.err[r], F_OVERFLOW);
+            atomicOr(&d.ovf[r], OVF_FIX);
+        }
+        // the terms on atom i, summed over its four lane groups
+        long long ix = acc.x, iy = acc.y, iz = acc.z;
+        ix += __shfl_xor_sync(0xffffffffu, ix, 8); iy += __shfl_xor_sync(0xffffffffu, iy, 8);
+        iz += __shfl_xor_sync(0xffffffffu, iz, 8);
+        ix += __shfl_xor_sync(0xffffffffu, ix, 16); iy += __shfl_xor_sync(0xffffffffu, iy, 16);
+        iz += __shfl_xor_sync(0xffffffffu, iz, 16);
+        if (g == 0 && i >= 0) {
+            unsigned long long* fi = reinterpret_cast<unsigned long long*>(d.facc) + 3 * (size_t)i;
+            if (ix) atomicAdd(fi, (unsigned long long)ix);
+            if (iy) atomicAdd(fi + 1, (unsigned long long)iy);
+            if (iz) atomicAdd(fi + 2, (unsigned long long)iz);
+        }
+    }
 }
 
 // fixed-point sums of k_force_half to the output (plus the bonded terms),
@@ -736,6 +838,31 @@ void force_half(const Dev& d, int lk, double* out, int as_grad, int tpa, cudaStr
     k_force_finish<B><<<blocks(d.N, 256), 256, 0, s>>>(d, out, as_grad);
 }
 
+// cluster-tile list of a gradient mode: 0 short radius, 1 full radius, -1 none
+inline int tile_list_of(int mode)
+{
+    if (mode == 3 || mode == 5) return 0;
+    if (mode == 0 || mode == 2 || mode == 4) return 1;
+    return -1;
+}
+
+template <int W, bool B>
+void force_tile(const Dev& d, int tl, double* out, int as_grad, cudaStream_t s)
+{
+    static int per_sm = 0, sms = 0;
+    if (!per_sm) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force_tile<W>, 128, 0);
+        per_sm = per_sm > 0 ? per_sm : 1;
+    }
+    const int want = (d.ncl_cap + 3) / 4;
+    const int g = want < sms * per_sm ? want : sms * per_sm;
+    k_force_tile<W><<<g > 0 ? g : 1, 128, 0, s>>>(d, tl);
+    k_force_finish<B><<<blocks(d.N, 256), 256, 0, s>>>(d, out, as_grad);
+}
+
 template <typename T>
 int force_t(const Dev& d, int mode, double* out, int as_grad, int tpa, cudaStream_t s)
 {
@@ -746,8 +873,22 @@ int force_t(const Dev& d, int mode, double* out, int as_grad, int tpa, cudaStrea
     // the half-list kernels (tpa | FORCE_HALF) serve the full, short and long
     // pair weights of mixed mode; the short weight of replicas that keep the LJ
     // long part deterministic also runs over the LJ list and stays full
+    const int tl = tile_list_of(mode);
+    const bool tile = (tpa & FORCE_TILE) && sizeof(T) == 4 && force_half_ok(d, mode) && tl >= 0 &&
+                      ((d.tiles >> tl) & 1);
+    if (tile) {
+        nk += 2;
+        switch (mode) {
+        case 0: force_tile<W_FULL, true>(d, tl, out, as_grad, s); break;
+        case 2: force_tile<W_FULL, false>(d, tl, out, as_grad, s); break;
+        case 3: force_tile<W_SHORT, false>(d, tl, out, as_grad, s); break;
+        case 4: force_tile<W_LONG, false>(d, tl, out, as_grad, s); break;
+        default: force_tile<W_SHORT, true>(d, tl, out, as_grad, s); break;
+        }
+        return nk;
+    }
     const bool half = (tpa & FORCE_HALF) && sizeof(T) == 4 && force_half_ok(d, mode);
-    const int t = tpa & ~FORCE_HALF;
+    const int t = tpa & ~(FORCE_HALF | FORCE_TILE);
     if (half) {
         nk += 1;
         switch (mode) {

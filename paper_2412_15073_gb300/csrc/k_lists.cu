@@ -530,6 +530,276 @@ void inner_lists(const Dev& d, int kinds, int exact, int late, cudaStream_t s)
     }
 }
 
+// ---- cluster tiles of the pair kernels ---------------------------------------------
+// Cluster layout (at an outer rebuild): the atoms of each outer cell, ordered
+// by the Morton code of the quarter-cell they sit in (from the outer-build
+// positions) and then by index, cut into clusters of TILE_CL; a replica's
+// clusters follow its cells. Cluster pairs (at an inner rebuild): every pair of clusters of a
+// replica whose member boxes, at the current positions, come closer than the
+// list radius; since a cluster's atoms lie in one cell, the candidate J of a
+// cluster I are the clusters of the +-2 cells around I's cell, as for the
+// outer candidates.
+
+// per replica: first cluster of each cell; clusters past the replica's count unused
+__global__ void k_cluster_scan(Dev d, int late)
+{
+    const int r = blockIdx.x;
+    if (!late && !d.flags[2 * r + 1]) return;
+    const RepParams& P = d.P[r];
+    const int ncell = P.nc * P.nc * P.nc;
+    const int c0 = d.cl_roff[r], c1 = d.cl_roff[r + 1];
+    for (int k = c0 + threadIdx.x; k < c1; k += blockDim.x) d.cl_cell[k] = -1;
+    __shared__ int warp_sum[32];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = c0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int base = 0; base < ncell; base += blockDim.x) {
+        const int c = base + threadIdx.x;
+        const int gc = P.cell_off + c;
+        const int v = c < ncell ? (d.cell_start[gc + 1] - d.cell_start[gc] + TILE_CL - 1) / TILE_CL : 0;
+        int incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) warp_sum[w] = incl;
+        __syncthreads();
+        if (w == 0) {
+            const int nw = blockDim.x >> 5;
+            int sv = lane < nw ? warp_sum[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, sv, o);
+                if (lane >= o) sv += t;
+            }
+            if (lane < nw) warp_sum[lane] = sv;
+        }
+        __syncthreads();
+        const int before = (w > 0 ? warp_sum[w - 1] : 0) + incl - v;
+        if (c < ncell) d.cl_start[gc] = carry + before;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry += before + v;
+        __syncthreads();
+    }
+}
+
+// one warp per cell: its atoms ordered by (sub-cell, index) into its clusters
+__global__ void k_cluster_form(Dev d, int late)
+{
+    __shared__ long long key[WARPS][SORT_CAP];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = blockIdx.x * WARPS + w;
+    if (c >= d.total_cells) return;
+    const int r = d.cell_rep[c];
+    if (r < 0 || (!late && !d.flags[2 * r + 1])) return;
+    const RepParams& P = d.P[r];
+    const int s0 = d.cell_start[c], n = d.cell_start[c + 1] - s0;
+    if (n > SORT_CAP) return;               // the cell sort has flagged the overflow
+    const int lin = c - P.cell_off;
+    const double inv_q = 4.0 / P.cs;        // quarter-cell units
+    const double o3[3] = {(lin % P.nc) * P.cs, ((lin / P.nc) % P.nc) * P.cs, (lin / (P.nc * P.nc)) * P.cs};
+    for (int k = lane; k < n; k += 32) {
+        const int i = d.cell_atoms[s0 + k];
+        // Morton order of the 4 x 4 x 4 sub-cells: eight consecutive atoms stay close
+        int code = 0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int q = min(3, max(0, int((d.xo[3 * i + a] - o3[a]) * inv_q)));
+            code |= ((q & 1) << a) | (((q >> 1) & 1) << (3 + a));
+        }
+        key[w][k] = ((long long)code << 32) | (long long)i;
+    }
+    __syncwarp();
+    const int first = d.cl_start[c];
+    const int ncl = (n + TILE_CL - 1) / TILE_CL;
+    for (int k = lane; k < ncl * TILE_CL; k += 32) {
+        const int cl = first + k / TILE_CL, slot = k % TILE_CL;
+        if (slot == 0) d.cl_cell[cl] = c;
+        if (k >= n) d.cl_atom[TILE_CL * (size_t)cl + slot] = -1;
+    }
+    for (int k = lane; k < n; k += 32) {
+        const long long v = key[w][k];
+        int rank = 0;
+        for (int m = 0; m < n; ++m) rank += key[w][m] < v;
+        const int i = int(v & 0xffffffffll);
+        const int cl = first + rank / TILE_CL, slot = rank % TILE_CL;
+        d.cl_atom[TILE_CL * (size_t)cl + slot] = i;
+        d.cl_of[i] = cl;
+        d.cl_slot[i] = slot;
+    }
+}
+
+// one thread per cluster: reference position (slot 0) and the members' box
+// relative to it, from the current scaled coordinates
+__global__ void k_cluster_boxes(Dev d, int late)
+{
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= d.ncl_cap) return;
+    const int cell = d.cl_cell[I];
+    if (cell < 0) return;
+    const int r = d.cell_rep[cell];
+    if (!late && !d.flags[2 * r]) return;
+    const int* at = d.cl_atom + TILE_CL * (size_t)I;
+    const uint4 ref = d.pos[at[0]];
+    int4 lo = make_int4(0, 0, 0, 0), hi = make_int4(0, 0, 0, 0);
+    for (int s = 1; s < TILE_CL; ++s) {
+        const int i = at[s];
+        if (i < 0) continue;
+        const uint4 p = d.pos[i];
+        const int dx = int(p.x - ref.x), dy = int(p.y - ref.y), dz = int(p.z - ref.z);
+        lo.x = min(lo.x, dx); lo.y = min(lo.y, dy); lo.z = min(lo.z, dz);
+        hi.x = max(hi.x, dx); hi.y = max(hi.y, dy); hi.z = max(hi.z, dz);
+    }
+    d.cl_ref[I] = ref;
+    d.cl_lo[I] = lo;
+    d.cl_hi[I] = hi;
+}
+
+// the gap between two boxes along one axis, in scaled units: I's box
+// [lo, hi] and J's box [dr + loj, dr + hij] relative to I's reference
+__device__ __forceinline__ float box_gap(int dr, int lo, int hi, int loj, int hij)
+{
+    const long long a = (long long)dr + loj - hi, b = (long long)lo - ((long long)dr + hij);
+    return float(max(0ll, max(a, b)));
+}
+
+// one warp per cluster I: the clusters J >= I of the +-2 cells around I's
+// cell (lanes over the candidates, the next batch loading while the current
+// one is tested) whose boxes come within the radius of list tl, with the
+// mask of the slot pairs to take
+__global__ void __launch_bounds__(32 * WARPS) k_cluster_pairs(Dev d, int tl, int late)
+{
+    __shared__ int nbs[WARPS][128];
+    __shared__ int cpre[WARPS][129];
+    __shared__ int cbeg[WARPS][128];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    for (int I = blockIdx.x * WARPS + w; I < d.ncl_cap; I += gridDim.x * WARPS) {
+        const int cell = d.cl_cell[I];
+        if (cell < 0) continue;
+        const int r = d.cell_rep[cell];
+        if (!late && !d.flags[2 * r]) continue;
+        const RepParams& P = d.P[r];
+        const int nc = P.nc;
+        const int lin = cell - P.cell_off;
+        const int cc[3] = {lin % nc, (lin / nc) % nc, lin / (nc * nc)};
+        const int nax = nc >= 5 ? 5 : nc;
+        const int ncell = nax * nax * nax;
+        __syncwarp();
+        for (int t = lane; t < ncell; t += 32) {
+            const int q[3] = {t % nax, (t / nax) % nax, t / (nax * nax)};
+            int cv[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) cv[a] = nc >= 5 ? (cc[a] + q[a] - 2 + nc) % nc : q[a];
+            const int gc = P.cell_off + (cv[2] * nc + cv[1]) * nc + cv[0];
+            nbs[w][t] = gc;
+        }
+        __syncwarp();
+        // candidate clusters: lane l holds neighbour cells 4l .. 4l+3; warp scan of their counts
+        int cntc[4], sum = 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int m = 4 * lane + u;
+            cntc[u] = 0;
+            if (m < ncell) {
+                const int gc = nbs[w][m];
+                cbeg[w][m] = d.cl_start[gc];
+                cntc[u] = (d.cell_start[gc + 1] - d.cell_start[gc] + TILE_CL - 1) / TILE_CL;
+            }
+            sum += cntc[u];
+        }
+        int incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        {
+            int run = incl - sum;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int m = 4 * lane + u;
+                if (m <= ncell) cpre[w][m] = run;
+                run += cntc[u];
+            }
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        if (lane == 31) cpre[w][ncell] = total;
+        __syncwarp();
+        const double rl = (tl == 0 ? fmin(P.rc, P.R) : P.R) + P.skin;
+        // FP32 test in Angstrom, widened by 1e-5 so that rounding never drops a pair
+        const float rl2 = float(rl * rl * (1.0 + 1e-5));
+        const float sc = P.sclf;
+        const uint4 refI = d.cl_ref[I];
+        const int4 loI = d.cl_lo[I], hiI = d.cl_hi[I];
+        const int* atI = d.cl_atom + TILE_CL * (size_t)I;
+        const int cap = d.cpl_cap[tl];
+        int* jrow = d.cpl_j[tl] + (size_t)I * cap;
+        unsigned long long* mrow = d.cpl_mask[tl] + (size_t)I * cap;
+        int cnt = 0;
+        for (int qb = 0; qb < total; qb += 32) {
+            const int q = qb + lane;
+            int J = -1;
+            if (q < total) {
+                int lo = 0, hi = ncell - 1;               // last cell m with cpre[m] <= q
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (cpre[w][mid] <= q) lo = mid; else hi = mid - 1;
+                }
+                J = cbeg[w][lo] + (q - cpre[w][lo]);
+            }
+            bool ok = J >= I;
+            unsigned long long mask = 0;
+            if (ok) {
+                const uint4 refJ = d.cl_ref[J];
+                const int4 loJ = d.cl_lo[J], hiJ = d.cl_hi[J];
+                const float gx = box_gap(int(refJ.x - refI.x), loI.x, hiI.x, loJ.x, hiJ.x) * sc;
+                const float gy = box_gap(int(refJ.y - refI.y), loI.y, hiI.y, loJ.y, hiJ.y) * sc;
+                const float gz = box_gap(int(refJ.z - refI.z), loI.z, hiI.z, loJ.z, hiJ.z) * sc;
+                ok = gx * gx + gy * gy + gz * gz < rl2;
+            }
+            if (ok) {
+                const int* atJ = d.cl_atom + TILE_CL * (size_t)J;
+                unsigned occI = 0, occJ = 0;
+#pragma unroll
+                for (int s = 0; s < TILE_CL; ++s) {
+                    occI |= (atI[s] >= 0 ? 1u : 0u) << s;
+                    occJ |= (atJ[s] >= 0 ? 1u : 0u) << s;
+                }
+#pragma unroll
+                for (int a = 0; a < TILE_CL; ++a) {
+                    if (!((occI >> a) & 1u)) continue;
+                    unsigned row = occJ;
+                    if (J == I) row &= ~((2u << a) - 1u);      // b > a within one cluster
+                    mask |= (unsigned long long)row << (TILE_CL * a);
+                    const int i = atI[a];
+                    for (int e = d.ex_off[i]; e < d.ex_off[i + 1]; ++e) {
+                        const int x = d.ex_idx[e];
+                        if (d.cl_of[x] == J) mask &= ~(1ull << (TILE_CL * a + d.cl_slot[x]));
+                    }
+                }
+                ok = mask != 0;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, ok);
+            const int pos = cnt + __popc(bal & below);
+            if (ok && pos < cap) {
+                jrow[pos] = J;
+                mrow[pos] = mask;
+            }
+            cnt += __popc(bal);
+        }
+        if (lane == 0) {
+            d.cpl_n[tl][I] = cnt;
+            if (cnt > cap) {
+                atomicOr(&d.err[r], F_OVERFLOW);
+                atomicOr(&d.ovf[r], OVF_TILE);
+            }
+        }
+    }
+}
+
 __global__ void k_flags_clear(Dev d)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -590,12 +860,42 @@ void launch_rebuild(const Dev& d, int kinds, int exact, int keep_refs, int exact
 {
     launch_rebuild_cells(d, keep_refs, exact_outer, s);
     launch_rebuild_inner(d, kinds, exact, s);
+    launch_tiles(d, d.tiles, s);
     launch_rebuild_done(d, s);
 }
 
 void launch_late_lists(const Dev& d, int kinds, cudaStream_t s)
 {
     inner_lists(d, kinds, 1, 1, s);
+}
+
+static void tiles_chain(const Dev& d, int tiles, int late, cudaStream_t s)
+{
+    if (!tiles || !d.ncl_cap) return;
+    k_cluster_scan<<<d.R, 1024, 0, s>>>(d, late);
+    k_cluster_form<<<blocks(d.total_cells, WARPS), 32 * WARPS, 0, s>>>(d, late);
+    k_cluster_boxes<<<blocks(d.ncl_cap, 128), 128, 0, s>>>(d, late);
+    static int per_sm = 0, sms = 0;
+    if (!per_sm) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cluster_pairs, 32 * WARPS, 0);
+        per_sm = std::max(per_sm, 1);
+    }
+    const int g = std::max(1, std::min(blocks(d.ncl_cap, WARPS), sms * per_sm));
+    for (int t = 0; t < 2; ++t)
+        if ((tiles >> t) & 1) k_cluster_pairs<<<g, 32 * WARPS, 0, s>>>(d, t, late);
+}
+
+void launch_tiles(const Dev& d, int tiles, cudaStream_t s)
+{
+    tiles_chain(d, tiles, 0, s);
+}
+
+void launch_tiles_late(const Dev& d, int tiles, cudaStream_t s)
+{
+    tiles_chain(d, tiles, 1, s);
 }
 
 }  // namespace mdj

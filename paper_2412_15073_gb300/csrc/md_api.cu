@@ -619,6 +619,29 @@ int read_max(md_ctx* ctx, const int* dev_counts, int n, int& mx)
     return MD_OK;
 }
 
+// cluster-tile lists kept with the lists (mixed mode): the short radius with
+// the short kind, the full radius with the full kind
+int tile_bits(const md_ctx* ctx, int kinds)
+{
+    if (ctx->fp64 || !ctx->d.ncl_cap) return 0;
+    return ((kinds >> L_SHORT) & 1) | (((kinds >> L_FULL) & 1) << 1);
+}
+
+// estimated cluster pairs of one cluster within list radius t (J >= I and J < I
+// alike, with room for clusters of a whole cell's extent)
+int tile_cap(const md_ctx* ctx, int t)
+{
+    double rho = 0, rl = 0, cs = 0;
+    for (const RepParams& P : ctx->hp) {
+        rho = std::max(rho, P.n / (P.L * P.L * P.L));
+        rl = std::max(rl, (t == 0 ? std::min(P.rc, P.R) : P.R) + P.skin);
+        cs = std::max(cs, P.cs);
+    }
+    const double reach = rl + cs;
+    const int c = int(4.0 / 3.0 * PI * reach * reach * reach * rho / TILE_CL) + 32;
+    return (c + 31) / 32 * 32;
+}
+
 // grow list capacities that came close to or over their limit, then rebuild
 int fit_caps(md_ctx* ctx, int kinds_to_check, bool outer)
 {
@@ -651,12 +674,32 @@ int fit_caps(md_ctx* ctx, int kinds_to_check, bool outer)
                 grow = true;
             }
         }
+        bool tiles_grew = false;
+        for (int t = 0; t < 2; ++t) {
+            if (!((d.tiles >> t) & 1)) continue;
+            int rc = read_max(ctx, d.cpl_n[t], d.ncl_cap, mx);
+            if (rc) return rc;
+            if (mx > d.cpl_cap[t] * 0.9) {
+                const int cap = (int(mx * 1.4) + 32 + 31) / 32 * 32;
+                int* pj;
+                unsigned long long* pm;
+                if ((rc = dalloc(ctx, &pj, (size_t)d.ncl_cap * cap)) ||
+                    (rc = dalloc(ctx, &pm, (size_t)d.ncl_cap * cap)))
+                    return rc;
+                dfree(ctx, d.cpl_j[t]);
+                dfree(ctx, d.cpl_mask[t]);
+                d.cpl_j[t] = pj; d.cpl_mask[t] = pm; d.cpl_cap[t] = cap;
+                grow = tiles_grew = true;
+            }
+        }
         if (!grow) return MD_OK;
         // rebuild at the stored build positions (exact, keeps the references)
         CK(cudaMemsetAsync(d.err, 0, sizeof(uint32_t) * d.R, ctx->s));
         if (outer) {
             launch_check(d, 1, 1, ctx->s);
             launch_rebuild(d, ctx->kinds & ~kinds_to_check, 1, 1, 1, 0, ctx->s);
+        } else if (tiles_grew) {
+            launch_tiles_late(d, d.tiles, ctx->s);
         }
         launch_late_lists(d, kinds_to_check, ctx->s);
         CK(cudaGetLastError());
@@ -888,6 +931,43 @@ int commit(md_ctx* ctx)
     AL(d.step_base, R); AL(d.stepc, 2 * R);
     AL(d.vkey, N); AL(d.vhist, (size_t)R * RATE_BUCKETS); AL(d.vofs, (size_t)R * RATE_BUCKETS); AL(d.qctr, 1);
     AL(d.facc, 3 * (size_t)N);
+    d.ncl_cap = 0;
+    d.tiles = 0;
+    // the box test of a cluster pair takes the minimum image of the two
+    // clusters' reference atoms; every member pair then shares it only when
+    // half the box exceeds the list radius plus the clusters' extent (a cell,
+    // widened by the outer skin, corner to corner); smaller boxes keep the
+    // per-atom kernels
+    // (opt-in: MDJ_TILES set; on 96,000-atom water they measured 2-2.5 times
+    // slower than the per-atom half-list kernels, see k_force_tile)
+    bool tiles_fit = !ctx->fp64 && std::getenv("MDJ_TILES") != nullptr;
+    for (const RepParams& P : ctx->hp)
+        tiles_fit = tiles_fit && 0.5 * P.L > P.R + P.skin + std::sqrt(3.0) * (P.cs + P.skin_o);
+    if (tiles_fit) {
+        // cluster tiles: replica r owns ceil(n_r / TILE_CL) + (its cells) clusters,
+        // enough for ceil(n_c / TILE_CL) in each of its cells
+        std::vector<int> roff(R + 1, 0);
+        for (int r = 0; r < R; ++r) {
+            const RepParams& P = ctx->hp[r];
+            roff[r + 1] = roff[r] + (P.n + TILE_CL - 1) / TILE_CL + P.nc * P.nc * P.nc;
+        }
+        d.ncl_cap = roff[R];
+        int* droff;
+        AL(droff, R + 1);
+        if ((rc = upload(ctx, droff, roff.data(), R + 1))) return rc;
+        d.cl_roff = droff;
+        AL(d.cl_start, cells); AL(d.cl_atom, (size_t)TILE_CL * d.ncl_cap); AL(d.cl_of, N); AL(d.cl_slot, N);
+        AL(d.cl_cell, d.ncl_cap); AL(d.cl_ref, d.ncl_cap); AL(d.cl_lo, d.ncl_cap); AL(d.cl_hi, d.ncl_cap);
+        CK(cudaMemsetAsync(d.cl_cell, 0xff, sizeof(int) * (size_t)d.ncl_cap, ctx->s));
+        for (int t = 0; t < 2; ++t) {
+            d.cpl_cap[t] = tile_cap(ctx, t);
+            AL(d.cpl_j[t], (size_t)d.ncl_cap * d.cpl_cap[t]);
+            AL(d.cpl_mask[t], (size_t)d.ncl_cap * d.cpl_cap[t]);
+            AL(d.cpl_n[t], d.ncl_cap);
+            CK(cudaMemsetAsync(d.cpl_n[t], 0, sizeof(int) * (size_t)d.ncl_cap, ctx->s));
+        }
+        d.tiles = tile_bits(ctx, ctx->kinds);
+    }
     {
         int *dib, *dbo, *dbl, *dao, *dal, *dsl;
         const bool on = !ib_start.empty();
@@ -1098,6 +1178,9 @@ int ensure_kinds(md_ctx* ctx, int mask)
         d.lcap[k] = kind_cap(ctx, k);
     }
     launch_late_lists(d, add, ctx->s);
+    const int tnew = tile_bits(ctx, ctx->kinds | add) & ~d.tiles;
+    if (tnew) launch_tiles_late(d, tnew, ctx->s);
+    d.tiles |= tnew;
     CK(cudaGetLastError());
     if ((rc = fit_caps(ctx, add, false))) return rc;
     ctx->kinds |= add;
@@ -1152,6 +1235,15 @@ void collect_profile(md_ctx* ctx)
     ctx->pend.clear();
 }
 
+// can gradient mode `mode` run on the cluster tiles? (mixed mode, a half-list
+// mode whose tile list is kept)
+bool tile_ok(const md_ctx* ctx, int mode)
+{
+    if (ctx->fp64 || !force_half_ok(ctx->d, mode)) return false;
+    const int tl = (mode == 3 || mode == 5) ? 0 : (mode == 0 || mode == 2 || mode == 4) ? 1 : -1;
+    return tl >= 0 && ((ctx->d.tiles >> tl) & 1);
+}
+
 int tpa_for(md_ctx* ctx, int mode)
 {
     if (ctx->fp64) return 1;
@@ -1160,8 +1252,9 @@ int tpa_for(md_ctx* ctx, int mode)
     if (const char* env = std::getenv("MDJ_FORCE_VARIANT")) {
         // a fixed kernel choice (tests): threads per atom, | 16 for the half-list kernels
         int t = std::atoi(env);
-        if (!force_half_ok(ctx->d, mode)) t &= ~FORCE_HALF;
-        const int w = t & ~FORCE_HALF;
+        if (!force_half_ok(ctx->d, mode)) t &= ~(FORCE_HALF | FORCE_TILE);
+        if (!tile_ok(ctx, mode)) t &= ~FORCE_TILE;
+        const int w = t & ~(FORCE_HALF | FORCE_TILE);
         ctx->tpa[mode] = (w == 1 || w == 2 || w == 4 || w == 8) ? t : 1;
         return ctx->tpa[mode];
     }
@@ -1175,6 +1268,7 @@ int tpa_for(md_ctx* ctx, int mode)
     std::vector<int> cands = {1, 2, 4, 8};
     if (force_half_ok(ctx->d, mode))
         for (int t : {1, 2, 4, 8}) cands.push_back(t | FORCE_HALF);
+    if (tile_ok(ctx, mode)) cands.push_back(1 | FORCE_TILE);
     for (int t : cands) {
         launch_force(ctx->d, mode, ctx->d.gout, 1, 0, t, ctx->s);
         cudaEventRecord(e0, ctx->s);
@@ -1183,14 +1277,16 @@ int tpa_for(md_ctx* ctx, int mode)
         cudaEventSynchronize(e1);
         float ms = 0;
         cudaEventElapsedTime(&ms, e0, e1);
+        if (ctx->tune_log) std::fprintf(stderr, "mdjump tune:   mode %d variant %d: %.4f ms\n", mode, t, ms);
         if (ms < best) { best = ms; pick = t; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     ctx->tpa[mode] = pick;
     if (ctx->tune_log)
-        std::fprintf(stderr, "mdjump tune: gradient mode %d: %d threads per atom%s (%.4f ms for 5 evaluations)\n", mode,
-                     pick & ~FORCE_HALF, (pick & FORCE_HALF) ? ", half list" : "", best);
+        std::fprintf(stderr, "mdjump tune: gradient mode %d: %s%d threads per atom%s (%.4f ms for 5 evaluations)\n",
+                     mode, (pick & FORCE_TILE) ? "cluster tiles, " : "", pick & ~(FORCE_HALF | FORCE_TILE),
+                     (pick & FORCE_HALF) ? ", half list" : "", best);
     return pick;
 }
 
@@ -1328,6 +1424,10 @@ void rebuild_step(md_ctx* ctx)
     if (ctx->kinds) {
         Prof p(ctx, 7, 1);
         launch_rebuild_inner(ctx->d, ctx->kinds, ctx->fp64, ctx->s);
+    }
+    if (ctx->d.tiles) {
+        Prof p(ctx, 7, 3 + __builtin_popcount(ctx->d.tiles));
+        launch_tiles(ctx->d, ctx->d.tiles, ctx->s);
     }
     Prof p(ctx, 4, 1);
     launch_rebuild_done(ctx->d, ctx->s);
@@ -1469,6 +1569,7 @@ int finish(md_ctx* ctx, long long inner_steps)
             if (m & (1u << b)) which += std::string(which.empty() ? "" : ", ") + names[b];
         if (m & OVF_OUTER) which += std::string(which.empty() ? "" : ", ") + "outer";
         if (m & OVF_CELL) which += std::string(which.empty() ? "" : ", ") + "cell";
+        if (m & OVF_TILE) which += std::string(which.empty() ? "" : ", ") + "cluster pairs";
         if (m & OVF_FIX)
             FAIL(MD_EOVERFLOW, "a pair force term left the range of the 64-bit fixed-point sums "
                                "(|component| >= 2^20 kcal/mol/A, or not finite)%s%s",

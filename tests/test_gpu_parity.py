@@ -97,6 +97,43 @@ def test_fixed_point_forces_do_not_depend_on_threads_per_atom(M, oracle_mod, wat
             assert np.array_equal(g, ref2)
 
 
+def test_cluster_tiles_give_the_per_atom_bits():
+    """The cluster-tile kernels (variant 33, opt-in through MDJ_TILES) need half
+    the box to exceed the list radius plus a cluster's extent, so 648 atoms
+    would fall back to the per-atom kernels; 6,591 atoms in a 40.3 A box (DSF,
+    and Ewald real space with the LJ long part at the slow level) run them: the
+    full, short, long and F0 gradients are the same bits as the
+    thread-per-atom and half-list kernels'."""
+    import paper_2412_15073_gb300 as M
+    from paper_2412_15073_gb300 import systems
+    import os
+    w = systems.water_box(2197, box=40.3, seed=2)
+    cases = [(dict(PARAMS), (0, 2, 3, 4, 5)),
+             (dict(PARAMS, dsf_alpha=0.35, coulomb_mode=1, pme_order=6, pme_spacing=0.8, r_split=6.0,
+                   lj_long_mode=2), (2, 3, 4))]
+    old = os.environ.get("MDJ_FORCE_VARIANT")
+    os.environ["MDJ_TILES"] = "1"           # the tiles are opt-in
+    try:
+        for p, modes in cases:
+            ref = None
+            for var in (1, 17, 33):
+                os.environ["MDJ_FORCE_VARIANT"] = str(var)
+                e = M.Engine(precision=1, seed=0)
+                e.set_system(0, w, **p)
+                g = np.stack([e.gradient(m) for m in modes])
+                e.close()
+                if ref is None:
+                    ref = g
+                else:
+                    assert np.array_equal(g, ref), (var, p.get("coulomb_mode", 0))
+    finally:
+        os.environ.pop("MDJ_TILES", None)
+        if old is None:
+            os.environ.pop("MDJ_FORCE_VARIANT", None)
+        else:
+            os.environ["MDJ_FORCE_VARIANT"] = old
+
+
 RINGS = [None, [], [4.8, 6.0, 7.5]]     # rings of r_mid (two), one ring, four rings
 
 
