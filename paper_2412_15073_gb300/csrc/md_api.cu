@@ -1840,7 +1840,11 @@ int md_set_state(md_ctx* ctx, int replica, const double* x, const double* v, con
     const int fl[2] = {1, 1};
     CK(cudaMemsetAsync(d.flags, 0, sizeof(int) * 2 * d.R, ctx->s));
     CK(cudaMemcpyAsync(d.flags + 2 * replica, fl, sizeof fl, cudaMemcpyHostToDevice, ctx->s));
-    launch_rebuild(d, ctx->kinds, 1, 1, 1, 0, ctx->s);
+    // lists at the given build positions; in mixed mode the run's own decisions
+    // (FP32, with the ring and LJ limits re-decided in FP64), which give the
+    // same ring and LJ lists as the exact set-up build at a fraction of its
+    // cost (FP64 runs at a small fraction of the FP32 rate on this GPU)
+    launch_rebuild(d, ctx->kinds, ctx->fp64, 1, ctx->fp64, 0, ctx->s);
     CK(cudaGetLastError());
     // the list build is not a rebuild of the run: undo the counter increments
     std::vector<unsigned long long> c(NCOUNT);
