@@ -55,19 +55,25 @@ __device__ __forceinline__ void angle_term_x(const RepParams& P, const double* x
 {
     const double ax = mimg(xa[0] - xm[0], P), ay = mimg(xa[1] - xm[1], P), az = mimg(xa[2] - xm[2], P);
     const double bx = mimg(xc[0] - xm[0], P), by = mimg(xc[1] - xm[1], P), bz = mimg(xc[2] - xm[2], P);
+    // FP64 division and the trigonometric functions run at a small fraction of
+    // the FP32 rate on this GPU: one reciprocal per length, sin(theta) as
+    // sqrt(1 - cos^2) (theta stays far from 0 and pi in these molecules; the
+    // guard below covers the degenerate case), and one division for the prefactor
     const double ra = sqrt(ax * ax + ay * ay + az * az), rb = sqrt(bx * bx + by * by + bz * bz);
-    double cth = (ax * bx + ay * by + az * bz) / (ra * rb);
+    const double ira = 1.0 / ra, irb = 1.0 / rb;
+    double cth = (ax * bx + ay * by + az * bz) * (ira * irb);
     cth = fmin(1.0, fmax(-1.0, cth));
     const double th = acos(cth);
-    const double sth = sin(th);
+    const double sth = sqrt(fmax(0.0, 1.0 - cth * cth));
     if (sth < 1e-12) {
         for (int c = 0; c < 6; ++c) o[c] = 0.0;
         return;
     }
-    const double pre = k * (th - t0);
-    const double ia = pre / (ra * sth), ib = pre / (rb * sth);
-    o[0] = (cth * ax / ra - bx / rb) * ia; o[1] = (cth * ay / ra - by / rb) * ia; o[2] = (cth * az / ra - bz / rb) * ia;
-    o[3] = (cth * bx / rb - ax / ra) * ib; o[4] = (cth * by / rb - ay / ra) * ib; o[5] = (cth * bz / rb - az / ra) * ib;
+    const double q = k * (th - t0) / sth;
+    const double ia = q * ira, ib = q * irb;
+    const double ux = ax * ira, uy = ay * ira, uz = az * ira, vx = bx * irb, vy = by * irb, vz = bz * irb;
+    o[0] = (cth * ux - vx) * ia; o[1] = (cth * uy - vy) * ia; o[2] = (cth * uz - vz) * ia;
+    o[3] = (cth * vx - ux) * ib; o[4] = (cth * vy - uy) * ib; o[5] = (cth * vz - uz) * ib;
 }
 
 __device__ __forceinline__ void bond_term(const Dev& d, int t, double o[3])
