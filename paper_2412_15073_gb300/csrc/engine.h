@@ -33,6 +33,7 @@ struct Dev {
     uint4* pos;
     // per-atom constants
     const double *mt, *isqmt, *q;   // m/418.4, 1/sqrt(m~), charge
+    const double* nimt;             // -1/m~ (acceleration from gradient without an FP64 division per use)
     const int* type;
     const double *LY, *LLJ;         // rate bounds per atom: rings (n x MAX_RINGS), LJ
     const float *LYf, *LLJf;

@@ -116,7 +116,8 @@ __device__ __forceinline__ void bonded_gather(const Dev& d, int i, double& gx, d
         const int kind = item.x & 15, role = item.x >> 4, t = item.y;
         if (kind == 0) {
             const double sgn = role == 0 ? 1.0 : -1.0;
-            gx += sgn * d.bterm[3 * t]; gy += sgn * d.bterm[3 * t + 1]; gz += sgn * d.bterm[3 * t + 2];
+            // sgn = +-1: the product is exact and the fused form adds it with one rounding, as before
+            gx = fma(sgn, d.bterm[3 * t], gx); gy = fma(sgn, d.bterm[3 * t + 1], gy); gz = fma(sgn, d.bterm[3 * t + 2], gz);
         } else {
             const double* o = d.aterm + 6 * (size_t)t;
             if (role == 0) { gx += o[0]; gy += o[1]; gz += o[2]; }
@@ -302,7 +303,7 @@ __global__ void __launch_bounds__(256) k_force(Dev d, int lk, double* out, int a
     if (as_grad) {
         out[3 * i] = gx; out[3 * i + 1] = gy; out[3 * i + 2] = gz;
     } else {
-        const double s = -1.0 / d.mt[i];
+        const double s = d.nimt[i];
         out[3 * i] = s * gx; out[3 * i + 1] = s * gy; out[3 * i + 2] = s * gz;
     }
 }
@@ -529,7 +530,7 @@ __global__ void k_force_finish(Dev d, double* out, int as_grad)
     if (as_grad) {
         out[3 * i] = gx; out[3 * i + 1] = gy; out[3 * i + 2] = gz;
     } else {
-        const double s = -1.0 / d.mt[i];
+        const double s = d.nimt[i];
         out[3 * i] = s * gx; out[3 * i + 1] = s * gy; out[3 * i + 2] = s * gz;
     }
 }
@@ -543,7 +544,7 @@ __global__ void k_bonded(Dev d, double* out, int as_grad)
     if (as_grad) {
         out[3 * i] = gx; out[3 * i + 1] = gy; out[3 * i + 2] = gz;
     } else {
-        const double s = -1.0 / d.mt[i];
+        const double s = d.nimt[i];
         out[3 * i] = s * gx; out[3 * i + 1] = s * gy; out[3 * i + 2] = s * gz;
     }
 }
@@ -660,7 +661,7 @@ __global__ void __launch_bounds__(IB_MAX) k_inner_steps(Dev d, double dt, uint32
         ab[a] = d.ab[3 * ic + a];
     }
     const double c1 = d.stepc[2 * r], c2 = d.stepc[2 * r + 1] * d.isqmt[ic];
-    const double smt = -1.0 / d.mt[ic];
+    const double smt = d.nimt[ic];
     for (int st = 0; st < nsteps; ++st) {
         if (live) {
             // B: the kick of the bonded acceleration of the previous step
@@ -708,7 +709,7 @@ __global__ void __launch_bounds__(IB_MAX) k_inner_steps(Dev d, double dt, uint32
                 const int kind = item.x & 15, role = item.x >> 4, sl = d.item_slot[it];
                 if (kind == 0) {
                     const double sgn = role == 0 ? 1.0 : -1.0;
-                    gx += sgn * sb[sl][0]; gy += sgn * sb[sl][1]; gz += sgn * sb[sl][2];
+                    gx = fma(sgn, sb[sl][0], gx); gy = fma(sgn, sb[sl][1], gy); gz = fma(sgn, sb[sl][2], gz);
                 } else {
                     const double* o = sa[sl];
                     if (role == 0) { gx += o[0]; gy += o[1]; gz += o[2]; }

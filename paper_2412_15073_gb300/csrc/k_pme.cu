@@ -450,7 +450,7 @@ __global__ void __launch_bounds__(PME_THREADS) k_pme_gather(Dev d, double* out, 
                 gx += double(s * x); gy += double(s * y); gz += double(s * z);
             }
         }
-        const double m = as_grad ? 1.0 : -1.0 / d.mt[i];
+        const double m = as_grad ? 1.0 : d.nimt[i];
         out[3 * i] += m * gx; out[3 * i + 1] += m * gy; out[3 * i + 2] += m * gz;
     }
 }

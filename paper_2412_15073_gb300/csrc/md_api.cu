@@ -739,7 +739,8 @@ int commit(md_ctx* ctx)
     d = Dev{};
     d.N = N; d.R = R;
     // host arrays
-    std::vector<double> x(3 * N), v(3 * N), xb(3 * N), xo(3 * N), mt(N), isqmt(N), q(N), LY(MAX_RINGS * N), LLJ(N);
+    std::vector<double> x(3 * N), v(3 * N), xb(3 * N), xo(3 * N), mt(N), isqmt(N), nimt(N), q(N), LY(MAX_RINGS * N),
+        LLJ(N);
     std::vector<float> LYf(MAX_RINGS * N), LLJf(N);
     std::vector<int> img(3 * N), type(N), rep(N), cell_rep(cells, -1);
     std::vector<int> bi_off(N + 1, 0), ex_off(N + 1, 0), ex_idx;
@@ -764,6 +765,7 @@ int commit(md_ctx* ctx)
         for (int i = 0; i < h.n; ++i) {
             mt[o + i] = h.mass[i] / KCAL_AMU;
             isqmt[o + i] = 1.0 / std::sqrt(mt[o + i]);
+            nimt[o + i] = -1.0 / mt[o + i];
             q[o + i] = h.charge[i];
             type[o + i] = h.type[i];
             rep[o + i] = r;
@@ -908,6 +910,12 @@ int commit(md_ctx* ctx)
     AL(dP, R); AL(drep, N); AL(dvorder, N); AL(dvorder0, N); AL(dtype, N); AL(dimg, 3 * N); AL(dbi_off, N + 1);
     AL(dex_off, N + 1); AL(dex_idx, ex_idx.size());
     AL(dmt, N); AL(disqmt, N); AL(dq, N); AL(dLY, MAX_RINGS * N); AL(dLLJ, N);
+    {
+        double* dnimt;
+        AL(dnimt, N);
+        if ((rc = upload(ctx, dnimt, nimt.data(), N))) return rc;
+        d.nimt = dnimt;
+    }
     AL(dLYf, MAX_RINGS * N); AL(dLLJf, N);
     AL(dbitem, bitem.size()); AL(dbij, bond_ij.size()); AL(dbk, bond_k.size()); AL(dbr0, bond_r0.size());
     AL(dang, ang.size()); AL(dak, ang_k.size()); AL(dat0, ang_t0.size());
