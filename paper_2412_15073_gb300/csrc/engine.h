@@ -158,7 +158,11 @@ constexpr int FORCE_TILE = 32;      // the cluster-tile kernels (mixed mode; the
 int launch_force(const Dev& d, int mode, double* out, int as_grad, int fp64, int tpa, cudaStream_t s);
 void launch_kick(const Dev& d, const double* a, double h, cudaStream_t s);
 void launch_kick2(const Dev& d, const double* a, double h, const double* b, double hb, cudaStream_t s);
-void launch_aoa(const Dev& d, double tau, uint32_t s_off, int do_check, int fp64, cudaStream_t s);
+// pre_a (may be null): the kick v += pre_h pre_a that precedes the A O A, in the same launch
+void launch_aoa(const Dev& d, double tau, uint32_t s_off, int do_check, int fp64, cudaStream_t s,
+                const double* pre_a = nullptr, double pre_h = 0.0);
+// the bonded acceleration into out, then the kick v += kick_h out (one launch after the terms)
+void launch_bonded_kick(const Dev& d, double* out, double kick_h, cudaStream_t s);
 // nsteps inner steps B A O A [bonded] B at dt in one launch (blocks of whole
 // bonded groups, d.n_ib > 0); the list check runs on the last step when check_last
 constexpr int IB_MAX = 128;

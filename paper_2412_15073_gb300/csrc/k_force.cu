@@ -535,7 +535,10 @@ __global__ void k_force_finish(Dev d, double* out, int as_grad)
     }
 }
 
-__global__ void k_bonded(Dev d, double* out, int as_grad)
+// the bonded gradient of each atom; with kick_h != 0 (as an acceleration),
+// also the kick v += kick_h a that follows it in an inner step, with the same
+// rounding as k_kick
+__global__ void k_bonded(Dev d, double* out, int as_grad, double kick_h)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.N) return;
@@ -545,7 +548,12 @@ __global__ void k_bonded(Dev d, double* out, int as_grad)
         out[3 * i] = gx; out[3 * i + 1] = gy; out[3 * i + 2] = gz;
     } else {
         const double s = d.nimt[i];
-        out[3 * i] = s * gx; out[3 * i + 1] = s * gy; out[3 * i + 2] = s * gz;
+        const double a[3] = {s * gx, s * gy, s * gz};
+        out[3 * i] = a[0]; out[3 * i + 1] = a[1]; out[3 * i + 2] = a[2];
+        if (kick_h != 0.0) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) d.v[3 * i + c] = fma(kick_h, a[c], d.v[3 * i + c]);
+        }
     }
 }
 
@@ -566,7 +574,7 @@ __global__ void k_kick2(Dev d, const double* a, double h, const double* b, doubl
 
 // A(tau/2) O(tau) A(tau/2), wrap, refresh the FP32 mirror, optional list check
 template <typename T>
-__global__ void k_aoa(Dev d, double tau, uint32_t s_off, int do_check)
+__global__ void k_aoa(Dev d, double tau, uint32_t s_off, int do_check, const double* pre_a, double pre_h)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.N) return;
@@ -576,6 +584,11 @@ __global__ void k_aoa(Dev d, double tau, uint32_t s_off, int do_check)
     const double h = 0.5 * tau;
     double x[3] = {d.x[3 * i], d.x[3 * i + 1], d.x[3 * i + 2]};
     double v[3] = {d.v[3 * i], d.v[3 * i + 1], d.v[3 * i + 2]};
+    // the kick that precedes the A O A in an inner step (as k_kick)
+    if (pre_a) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) v[a] = fma(pre_h, pre_a[3 * i + a], v[a]);
+    }
 #pragma unroll
     for (int a = 0; a < 3; ++a) x[a] = fma(h, v[a], x[a]);
     const U4 u = draw(P, uint32_t(i - P.atom_off), s0, TAG_O, 0, 0, 0);
@@ -910,7 +923,7 @@ int force_t(const Dev& d, int mode, double* out, int as_grad, int tpa, cudaStrea
     }
     switch (mode) {
     case 0: force_tpa<T, W_FULL, true>(d, L_FULL, out, as_grad, t, s); break;
-    case 1: k_bonded<<<blocks(d.N, 256), 256, 0, s>>>(d, out, as_grad); break;
+    case 1: k_bonded<<<blocks(d.N, 256), 256, 0, s>>>(d, out, as_grad, 0.0); break;
     case 2: force_tpa<T, W_FULL, false>(d, L_FULL, out, as_grad, t, s); break;
     case 3: force_tpa<T, W_SHORT, false>(d, L_SHORT, out, as_grad, t, s); break;
     case 4: force_tpa<T, W_LONG, false>(d, L_FULL, out, as_grad, t, s); break;
@@ -943,10 +956,17 @@ void launch_inner_steps(const Dev& d, double dt, uint32_t s_off, int nsteps, int
     else k_inner_steps<float><<<d.n_ib, IB_MAX, 0, s>>>(d, dt, s_off, nsteps, check_last);
 }
 
-void launch_aoa(const Dev& d, double tau, uint32_t s_off, int do_check, int fp64, cudaStream_t s)
+void launch_aoa(const Dev& d, double tau, uint32_t s_off, int do_check, int fp64, cudaStream_t s,
+                const double* pre_a, double pre_h)
 {
-    if (fp64) k_aoa<double><<<blocks(d.N, 256), 256, 0, s>>>(d, tau, s_off, do_check);
-    else k_aoa<float><<<blocks(d.N, 256), 256, 0, s>>>(d, tau, s_off, do_check);
+    if (fp64) k_aoa<double><<<blocks(d.N, 256), 256, 0, s>>>(d, tau, s_off, do_check, pre_a, pre_h);
+    else k_aoa<float><<<blocks(d.N, 256), 256, 0, s>>>(d, tau, s_off, do_check, pre_a, pre_h);
+}
+
+void launch_bonded_kick(const Dev& d, double* out, double kick_h, cudaStream_t s)
+{
+    if (d.nbond + d.nang > 0) k_bonded_terms<<<blocks(d.nbond + d.nang, 128), 128, 0, s>>>(d);
+    k_bonded<<<blocks(d.N, 256), 256, 0, s>>>(d, out, 0, kick_h);
 }
 
 void launch_energy(const Dev& d, cudaStream_t s)

@@ -1709,10 +1709,13 @@ void record(md_ctx* ctx, uint32_t s_off)
 void inner_bonded(md_ctx* ctx, double dt, uint32_t s_off, int check)
 {
     Dev& d = ctx->d;
-    kick(ctx, d.ab, 0.5 * dt);
-    aoa(ctx, dt, s_off, check);
-    force(ctx, 1, d.ab);
-    kick(ctx, d.ab, 0.5 * dt);
+    // the two kicks ride in the A O A and bonded-gather launches (same arithmetic)
+    {
+        Prof p(ctx, 3, 1);
+        launch_aoa(d, dt, s_off, check, ctx->fp64, ctx->s, d.ab, 0.5 * dt);
+    }
+    Prof p(ctx, 1, d.nbond + d.nang > 0 ? 2 : 1);
+    launch_bonded_kick(d, d.ab, 0.5 * dt, ctx->s);
 }
 
 // n inner steps from s_off: fused into one launch when the bonded groups
