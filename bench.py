@@ -229,8 +229,10 @@ def diffusion(e, integ, steps, every, box, dt_fs, mass=None, replica=0, se=False
     Einstein relation: MSD of the unwrapped positions over all time origins,
     slope of a linear fit over 20-80 % of the lag window, D = slope / 6.
     Returns D in 1e-5 cm^2/s; with the masses (amu), (D, mean temperature over
-    the same samples, 3N degrees of freedom); with se, also the standard error
-    of D from eight interleaved groups of oxygens."""
+    the same samples, 3N degrees of freedom); with se, also a standard error
+    of D from four consecutive time blocks of the window (D of each block,
+    their spread over sqrt(4)), which also holds the slow, collective part
+    of the fluctuations that a split of the oxygens into groups misses."""
     xs, ts = [], []
     for k in range(steps // every + 1):
         x, v, img, _ = e.state(replica) if replica else e.state()
@@ -245,8 +247,9 @@ def diffusion(e, integ, steps, every, box, dt_fs, mass=None, replica=0, se=False
         return D
     if not se:
         return D, float(np.mean(ts))
-    Dg = np.array([_einstein_D(X[:, g::8], every, dt_fs) for g in range(8)])
-    return D, float(np.mean(ts)), float(Dg.std(ddof=1) / np.sqrt(8))
+    nb = X.shape[0] // 4
+    Db = np.array([_einstein_D(X[b * nb:(b + 1) * nb + 1], every, dt_fs) for b in range(4)])
+    return D, float(np.mean(ts)), float(Db.std(ddof=1) / np.sqrt(4))
 
 
 def matched_flags(run: dict, ref: dict) -> None:
@@ -924,7 +927,7 @@ def main():
     ap.add_argument("--equil", type=int, default=1000,
                     help="BAOAB steps at gamma = 20/ps from the lattice start before timing (0 = none)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--dwindow", type=int, default=16000, help="fs of each 96,000-atom run for D (0 = skip)")
+    ap.add_argument("--dwindow", type=int, default=40000, help="fs of each 96,000-atom run for D (0 = skip)")
     ap.add_argument("--ens-dwindow", type=int, default=6000, help="fs of each ensemble run for D (0 = skip)")
     ap.add_argument("--mil-dwindow", type=int, default=2400, help="fs of each 10^6-atom run for D (0 = skip)")
     ap.add_argument("--only", default="all",
