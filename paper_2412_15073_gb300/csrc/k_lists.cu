@@ -201,6 +201,7 @@ __global__ void __launch_bounds__(32 * OUTER_WARPS) k_outer_cells(Dev d, int exa
     __shared__ uint32_t* hrow[OUTER_WARPS][32];  // their rows of the outer list
     __shared__ int hmore[OUTER_WARPS][32];     // 1: more than four excluded partners, else -1
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (d.R == 1 && !d.flags[1]) return;        // the only replica does not rebuild its outer list
     const int ntask = d.total_cells * OUTER_GROUPS;
     // the warps stride over the tasks (cell, share of its atoms): a launch in
     // which no replica rebuilds costs one flag read per task
@@ -364,6 +365,8 @@ __global__ void __launch_bounds__(32 * OUTER_WARPS) k_outer_cells(Dev d, int exa
 template <uint32_t KM>
 __global__ void __launch_bounds__(32 * WARPS) k_inner_lists(Dev d, int kinds_rt, int exact, int late)
 {
+    // a single replica that does not rebuild: every thread sees the same flag
+    if (!late && d.R == 1 && !d.flags[0]) return;
     const uint32_t kinds = KM ? KM : uint32_t(kinds_rt);
     const int lane = threadIdx.x & 31;
     const int nw = gridDim.x * WARPS;
