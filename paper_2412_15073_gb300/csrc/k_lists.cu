@@ -69,6 +69,7 @@ __global__ void k_check(Dev d, int force_inner, int force_outer)
 // ---- refresh the scaled coordinates; assign outer cells ----------------------------
 __global__ void k_rehome(Dev d, int keep_refs)
 {
+    if (d.R == 1 && !d.flags[0]) return;        // the only replica does not rebuild
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.N) return;
     const int r = d.rep[i];
@@ -145,6 +146,7 @@ __global__ void k_cell_scan(Dev d)
 
 __global__ void k_cell_fill(Dev d)
 {
+    if (d.R == 1 && !d.flags[1]) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.N) return;
     const int r = d.rep[i];
@@ -158,6 +160,7 @@ __global__ void k_cell_fill(Dev d)
 __global__ void k_cell_sort(Dev d)
 {
     __shared__ int buf[WARPS][SORT_CAP];
+    if (d.R == 1 && !d.flags[1]) return;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c = blockIdx.x * WARPS + w;
     if (c >= d.total_cells) return;
