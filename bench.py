@@ -600,6 +600,74 @@ def dsf_sweep(args, M, engine, stream, mass):
     return out
 
 
+def _rdf_oo(frames, box, rmax=9.0, dr=0.05):
+    """O-O radial distribution over the frames (periodic cKDTree)"""
+    from scipy.spatial import cKDTree
+    edges = np.arange(0.0, rmax + dr, dr)
+    h = np.zeros(len(edges) - 1)
+    n_o = frames[0].shape[0] // 3
+    for x in frames:
+        o = np.mod(x[::3], box)
+        p = cKDTree(o, boxsize=box).query_pairs(rmax, output_type="ndarray")
+        d = o[p[:, 0]] - o[p[:, 1]]
+        d -= box * np.round(d / box)
+        h += np.histogram(np.sqrt((d * d).sum(1)), edges)[0]
+    shell = 4.0 / 3.0 * np.pi * (edges[1:] ** 3 - edges[:-1] ** 3)
+    return h / (shell * n_o / box ** 3 * n_o / 2 * len(frames)), dr, rmax
+
+
+def precision_leg(args, M, stream, local):
+    """The 24,000-atom water of the precision study (8,000 molecules, 62.1 A,
+    DSF 0.2/A to 9 A, split 5 A): BAOAB, JUMP and JUMP-RESPA (1:2 fs) from
+    one equilibrated state, each in FP64 and in mixed precision for the same
+    number of steps; the error of each observable of the mixed run against
+    the FP64 run (the FP64 mode follows the FP64 oracle event for event, which
+    is too slow to run this long at this size): mean temperature, O-O radial
+    distribution (L1 distance), oxygen self-diffusion, and the wall time."""
+    from paper_2412_15073_gb300 import systems
+    box = 62.1
+    w = systems.water_box(8000, box=box, seed=0)
+    p = dict(r_cut=9.0, r_split=5.0, h_switch=0.5, r_mid=5.5, dsf_alpha=0.2, gamma=1.0, temperature=300.0,
+             eps0=0.1, eps_mode=1, skin=0.5, skin_outer=1.5)
+    eq = M.Engine(precision=M.MD_MIXED, seed=31, device=local, stream=stream.cuda_stream)
+    eq.set_system(0, w, **(p | {"gamma": 20.0}))
+    eq.baoab(500)
+    w.x, w.v = eq.state()[0], eq.state()[1]
+    eq.close()
+    steps, every = args.psteps // 150 * 150, 150
+    out = {"workload": "water 24,000 atoms (8,000 flexible 3-site waters, 62.1 A), DSF 0.2/A to 9 A, split 5 A, "
+                       "300 K, gamma 1/ps, 1 fs; JUMP-RESPA 1:2 fs", "steps": steps}
+    runs = [("baoab", lambda e, k: e.baoab(k)), ("jump", lambda e, k: e.jump(k)),
+            ("jump_respa", lambda e, k: e.jump_respa(k // 2, 1.0, 2))]
+    for name, fn in runs:
+        res = {}
+        for prec in (M.MD_FP64, M.MD_MIXED):
+            e = M.Engine(precision=prec, seed=32, device=local, stream=stream.cuda_stream)
+            e.set_system(0, w, **p)
+            T, frames, U = [], [], []
+            t0 = time.perf_counter()
+            for k in range(steps // every + 1):
+                x, _, img, _ = e.state()
+                frames.append(x)
+                U.append((x + img * box)[::3])
+                if k < steps // every:
+                    fn(e, every)
+                    T.append(e.observables()["temperature"])
+            wall = time.perf_counter() - t0
+            X = np.stack(U)
+            D = _einstein_D(X, every, DT_FS)
+            nb = X.shape[0] // 4
+            Db = np.array([_einstein_D(X[b * nb:(b + 1) * nb + 1], every, DT_FS) for b in range(4)])
+            res[prec] = (float(np.mean(T)), _rdf_oo(frames[1::2], box), D, float(Db.std(ddof=1) / 2), wall)
+            e.close()
+        (T64, (g64, dr, rmax), D64, se64, w64), (T32, (g32, _, _), D32, se32, w32) = res[M.MD_FP64], res[M.MD_MIXED]
+        out[name] = {"T_fp64": T64, "T_mixed": T32, "T_rel_err": T32 / T64 - 1,
+                     "rdf_L1": float(np.abs(g32 - g64).sum() * dr / rmax),
+                     "D_fp64": D64, "D_fp64_se": se64, "D_mixed": D32, "D_mixed_se": se32, "D_rel_err": D32 / D64 - 1,
+                     "wall_s_fp64": w64, "wall_s_mixed": w32}
+    return out
+
+
 def dsf_respa1(args, M, engine, stream, world, max_over_ranks, barrier):
     """DSF RESPA1 stability: delta 1, kappa 2, Delta 2/4/6 fs; the outer level
     of JUMP-RESPA1 is empty without a reciprocal part. A run whose temperature
@@ -928,10 +996,12 @@ def main():
                     help="BAOAB steps at gamma = 20/ps from the lattice start before timing (0 = none)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--dwindow", type=int, default=40000, help="fs of each 96,000-atom run for D (0 = skip)")
+    ap.add_argument("--psteps", type=int, default=10000, help="steps of each run of the precision leg")
     ap.add_argument("--ens-dwindow", type=int, default=6000, help="fs of each ensemble run for D (0 = skip)")
     ap.add_argument("--mil-dwindow", type=int, default=2400, help="fs of each 10^6-atom run for D (0 = skip)")
     ap.add_argument("--only", default="all",
                     choices=["all", "headline", "ewald", "dsf", "dsf_sweep", "skin_sweep", "spectra", "ensemble", "million",
+                             "precision",
                              "jump", "baoab", "jump_respa1_ewald", "baoab_respa1_ewald"])
     ap.add_argument("--ensemble", type=int, default=1, help="also time the batched 64-replica ensemble")
     ap.add_argument("--million", type=int, default=1, help="also time the 1,000,000-atom heterogeneous system")
@@ -963,6 +1033,12 @@ def main():
         out = ensemble_leg(args, M, stream, local)
         if rank == 0:
             print(json.dumps({"ensemble": out}), flush=True)
+        ranks.close()
+        return
+    if args.only == "precision":
+        out = precision_leg(args, M, stream, local)
+        if rank == 0:
+            print(json.dumps({"precision": out}), flush=True)
         ranks.close()
         return
     if args.only == "million":
