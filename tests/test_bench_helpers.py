@@ -29,6 +29,32 @@ def test_diffusion_estimate_recovers_brownian_D():
     assert abs(got / 2.5 - 1) < 0.05, got
 
 
+def test_diffusion_block_standard_error_covers_the_estimate():
+    """the block standard error of D (four consecutive time blocks) is of the
+    size of the spread of D over independent walks of the same length"""
+    D = 0.25
+    est, ses = [], []
+    for seed in range(6):
+        e = FakeEngine(3 * 600, 20.0, D, 1.0, seed=seed)
+        d, _, se = bench.diffusion(e, e.step, 4000, 100, 20.0, 1.0, mass=np.ones(3 * 600), se=True)
+        est.append(d)
+        ses.append(se)
+    spread = np.std(est, ddof=1)
+    assert 0.3 < np.mean(ses) / spread < 3.0, (np.mean(ses), spread)
+    assert abs(np.mean(est) / 2.5 - 1) < 0.05
+
+
+def test_oxygen_rdf_of_an_ideal_gas_is_one():
+    """_rdf_oo of uniformly scattered points (every third atom an 'oxygen')
+    is 1 within its counting noise from 3 to 9 A"""
+    rng = np.random.default_rng(4)
+    frames = [rng.uniform(0, 40.0, size=(3 * 3000, 3)) for _ in range(4)]
+    g, dr, rmax = bench._rdf_oo(frames, 40.0)
+    r = (np.arange(len(g)) + 0.5) * dr
+    sel = (r > 3.0) & (r < rmax)
+    assert abs(g[sel].mean() - 1.0) < 0.02, g[sel].mean()
+
+
 def test_bench_functions_name_only_defined_globals():
     """every global a function of bench.py reads exists (a deleted constant
     would otherwise only show on the GPU machine)"""
