@@ -42,7 +42,7 @@ sys.path.insert(0, ROOT)
 
 N_MOL, BOX = 32000, 98.6
 DT_FS = 1.0
-# DSF water: the benchmark spec's electrostatics
+# DSF water: the specified electrostatics (damped shifted force Coulomb)
 DSF = dict(r_cut=10.0, r_split=5.0, h_switch=0.5, r_mid=5.5, dsf_alpha=0.2, gamma=1.0,
            temperature=300.0, eps0=0.1, eps_mode=1, skin=0.5, skin_outer=1.5)
 # list parameters tuned per integrator (both measured on this workload): JUMP
@@ -1212,7 +1212,7 @@ def main():
         if ewald.get(k, {}).get("D_ratio_se") is not None:
             matched[k + "_D_ratio"] = [ewald[k]["D_ratio"], ewald[k]["D_ratio_se"]]
 
-    # ---- DSF water (the benchmark spec's electrostatics): 1 fs JUMP vs BAOAB, rooflines
+    # ---- DSF water (damped shifted force Coulomb): 1 fs JUMP vs BAOAB, rooflines
     dsf = dsf_leg(args, M, eng_dsf, stream, world, max_over_ranks, barrier, w.mass, sms, clock_mhz, hbm,
                   peak_kind)
     dsf["respa1"] = dsf_respa1(args, M, eng_dsf, stream, world, max_over_ranks, barrier)
