@@ -96,6 +96,16 @@ MUTANTS = [
      "        if (ew) kick(s, s->al, 0.5 * D);\n        for (int j = 0; j < n_outer; ++j) {",
      "        if (ew) kick(s, s->al, 0.5 * kap);\n        for (int j = 0; j < n_outer; ++j) {",
      CHAIN + "[jump_respa1-2]"),
+    ("Ewald exclusion correction with the wrong sign",
+     "if (j > i) e -= qq * erf(a * r) / r;", "if (j > i) e += qq * erf(a * r) / r;",
+     "tests/test_oracle_ewald.py::test_total_ewald_energy_does_not_depend_on_alpha"),
+    ("C' acceptance with sqrt(beta m) for sqrt(beta / m)",
+     "p = sqrt(beta / mt) * or_theta(eta) / eps0 / LamY[Y];", "p = sqrt(beta * mt) * or_theta(eta) / eps0 / LamY[Y];",
+     "tests/test_oracle_dynamics.py::test_cprime_first_jump_survival_a0"),
+    ("C' jump kernel without the eps^2 of its normalisation",
+     "double coef = 2.0 * eps / (sqrt(beta * mt) * (1.0 + eps * eps)) * (eta + Gt) / gn;",
+     "double coef = 2.0 * eps / (sqrt(beta * mt) * (1.0 + eps)) * (eta + Gt) / gn;",
+     "tests/test_oracle_dynamics.py::test_jump_samples_boltzmann_two_body"),
     ("BJAOAJB jumps with the drift of F0",
      "        cphase(s, zero, 0.5 * tau, s0, 0);", "        cphase(s, s->a0, 0.5 * tau, s0, 0);",
      "tests/test_oracle_dynamics.py::test_bjaoajb_is_baoab_without_jumps_and_keeps_temperature"),
