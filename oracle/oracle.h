@@ -24,7 +24,8 @@
  *                                 lengths of a harmonic chain whose bonded pair
  *                                 also jumps; with an LJ slow level as well)
  *   LJ long modes 1, 2 .......... pinned by reduction (moved part = pair sum)
- *   Ewald, plain reciprocal sum . pinned (rock-salt Madelung constant)
+ *   Ewald, plain reciprocal sum . pinned (rock-salt Madelung constant; the
+ *                                 full gradient is the derivative of its energy)
  *   smooth PME .................. pinned (plain sum per order, grid refinement,
  *                                 finite differences of its energy)
  *   VACF, spectrum .............. pinned (closed forms, numpy correlate)

@@ -99,6 +99,10 @@ MUTANTS = [
     ("Ewald exclusion correction with the wrong sign",
      "if (j > i) e -= qq * erf(a * r) / r;", "if (j > i) e += qq * erf(a * r) / r;",
      "tests/test_oracle_ewald.py::test_total_ewald_energy_does_not_depend_on_alpha"),
+    ("Ewald real-space derivative with half its Gaussian term",
+     "return -(erfc(a * r) / r + 2.0 * a / sqrt(OR_PI) * exp(-a * a * r * r)) / r;",
+     "return -(erfc(a * r) / r + 1.0 * a / sqrt(OR_PI) * exp(-a * a * r * r)) / r;",
+     "tests/test_oracle_ewald.py::test_total_ewald_gradient_is_the_derivative_of_its_energy"),
     ("C' acceptance with sqrt(beta m) for sqrt(beta / m)",
      "p = sqrt(beta / mt) * or_theta(eta) / eps0 / LamY[Y];", "p = sqrt(beta * mt) * or_theta(eta) / eps0 / LamY[Y];",
      "tests/test_oracle_dynamics.py::test_cprime_first_jump_survival_a0"),
