@@ -110,6 +110,14 @@ MUTANTS = [
      "double coef = 2.0 * eps / (sqrt(beta * mt) * (1.0 + eps * eps)) * (eta + Gt) / gn;",
      "double coef = 2.0 * eps / (sqrt(beta * mt) * (1.0 + eps)) * (eta + Gt) / gn;",
      "tests/test_oracle_dynamics.py::test_jump_samples_boltzmann_two_body"),
+    ("JUMP's closing C' with the opening step's force",
+     "        maybe_rebuild(s);\n        accel(s, 5, s->a0);\n        jphase(s, 0.5 * tau, s0, 1);",
+     "        maybe_rebuild(s);\n        jphase(s, 0.5 * tau, s0, 1);",
+     "tests/test_oracle_dynamics.py::test_jump_samples_boltzmann_two_body"),
+    ("BAOAB-RESPA1 closing mid-level kick 0.6 kappa",
+     "            accel(s, 3, s->as);\n            kick(s, s->as, 0.5 * kap);\n            if (j < n_outer - 1) vrec(s);",
+     "            accel(s, 3, s->as);\n            kick(s, s->as, 0.6 * kap);\n            if (j < n_outer - 1) vrec(s);",
+     "tests/test_oracle_dynamics.py::test_multiple_time_step_energy_error_second_order"),
     ("BJAOAJB jumps with the drift of F0",
      "        cphase(s, zero, 0.5 * tau, s0, 0);", "        cphase(s, s->a0, 0.5 * tau, s0, 0);",
      "tests/test_oracle_dynamics.py::test_bjaoajb_is_baoab_without_jumps_and_keeps_temperature"),
